@@ -1,0 +1,190 @@
+/*
+ * pond.h -- C ABI of the GB300 (sm_103a) Particles-on-Demand time step.
+ *
+ * Method: Kallikounis & Karlin, "Particles on Demand method: theoretical
+ * analysis, simplification techniques and model extensions", arXiv:2302.00310.
+ * One call of pond_step() advances every cell by the algorithm of Sec. IV.A.3
+ * ("Summary of the algorithm"), with the Strang-split quasi-equilibrium
+ * relaxation of Sec. IV.B when Pr != 1:
+ *   QE half step -> phi_bar^+ at cell centres (Eq. eq:Fbarplus) -> per face:
+ *   averaged face frame (Eq. eq::AvgFrame), stencil moved into it by the
+ *   moment-invariant frame transformation (Sec. II.B), limited MUSCL half-step
+ *   trace (Eq. eq:InterfacePop), interface moments, non-co-moving equilibrium
+ *   (Eq. NonComovingEq), face populations (inverse of Eq. eq:FluxTransf) ->
+ *   per cell: fluxes moved into the cell frame (Eq. fluxEq), DUGKS update
+ *   (Eqs. eq:FinalUpdateDUGKS, eq:FinalUpdateDUGKS_g), new co-moving frame
+ *   (Sec. IV.A.1), QE half step.
+ *
+ * Lattices (Table I): f on D1Q4 (1D) or D2Q16 (2D, 4x4 tensor product), g on
+ * D1Q3 / D2Q9.  Population i of a D-dimensional lattice with q nodes per axis
+ * has node indices ix = i % q, iy = i / q (x fastest); nodes per axis are in
+ * ascending order: D1Q4 (-r2, -r1, r1, r2), r1,2 = sqrt(3 -+ sqrt 6);
+ * D1Q3 (-sqrt 3, 0, sqrt 3).
+ *
+ * Array layouts (all FP64 at the boundary, whatever the internal precision):
+ *   fields   [ny][nx]            (x fastest; ny = 1 in 1D)
+ *   f        [Qf][ny][nx]        Qf = 4 (1D) or 16 (2D)
+ *   g        [Qg][ny][nx]        Qg = 3 (1D) or 9 (2D)
+ * The state is the DUGKS variable phi~ of Eq. eq:variableTransform in each
+ * cell's co-moving frame {u, T}; the frame itself is (ux, uy, T).
+ *
+ * Ownership: host pointers are caller-owned and copied in or out before the
+ * call returns.  With on_device = 1 the pointers are caller-owned CUDA device
+ * pointers on the context's device; they are read or written in order on the
+ * context's stream and the call synchronises that stream before returning.
+ * The context owns its device state: either memory it allocated itself, or a
+ * caller-provided workspace (e.g. a PyTorch tensor) that must outlive it.
+ *
+ * Errors: every call returns a pond_status; nothing is thrown across the ABI.
+ * Problems detected on the device (nonphysical state, CFL > 1, an iterated
+ * face frame that did not converge) set sticky bits read by
+ * pond_status_flags(); kernels never trap and never spin.
+ *
+ * Threading: a context is used by one host thread at a time.
+ */
+#ifndef POND_H
+#define POND_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define POND_ABI_VERSION 1
+
+typedef struct pond_ctx pond_ctx;
+
+/* f-lattice of a context (the g-lattice follows: D1Q3 / D2Q9). */
+typedef enum { POND_D1Q4 = 1, POND_D2Q16 = 2 } pond_lattice;
+
+typedef enum {
+  POND_OK = 0,
+  POND_E_INVAL = 1,       /* invalid argument or parameter                  */
+  POND_E_NOMEM = 2,       /* device allocation failed / workspace too small */
+  POND_E_CUDA = 3,        /* a CUDA runtime call failed                     */
+  POND_E_NONPHYSICAL = 4, /* rho <= 0, T <= 0 or NaN appeared               */
+  POND_E_NOCONV = 5,      /* iterated face frame did not converge           */
+  POND_E_CFL = 6,         /* CFL number above 1 observed                    */
+  POND_E_STATE = 7        /* call out of order (e.g. step before init)      */
+} pond_status;
+
+/* boundary kinds per side (x-lo, x-hi, y-lo, y-hi), ghost-node method of
+ * Sec. IV.D: periodic wrap, zero normal gradient (copy of the boundary cell),
+ * or a fixed inflow state (its co-moving equilibrium). */
+enum { POND_BC_PERIODIC = 0, POND_BC_ZERO_GRADIENT = 1, POND_BC_INFLOW = 2 };
+/* arithmetic of the step: all FP64, or FP32 populations/transforms with FP64
+ * per-cell moments and frame */
+enum { POND_FP64 = 0, POND_FP32_MIXED = 1 };
+/* frame transformation: tensor product of 1D transformations (all Hermite
+ * coefficients a, b <= K per axis) or the paper's Grad projection of total
+ * order a + b <= K (Sec. V.A) */
+enum { POND_TENSOR = 0, POND_GRAD_K = 1 };
+/* flux moved into the cell frame as (v^lambda . n) G phi (Eq. fluxEq) or as
+ * G (v^lambda_F . n phi) (Appendix C) */
+enum { POND_FLUX_MAIN = 0, POND_FLUX_APPC = 1 };
+/* slope limiter of the MUSCL reconstruction (Sec. IV.A.2) */
+enum { POND_VANLEER = 0, POND_MINMOD = 1 };
+/* face frame: average of the adjacent cell frames (Eq. eq::AvgFrame) or the
+ * iterated co-moving face frame of the earlier scheme (Sec. IV.A.3) */
+enum { POND_FRAME_AVG = 0, POND_FRAME_ITER = 1 };
+/* sticky device flags */
+enum { POND_FLAG_NONPHYSICAL = 1u, POND_FLAG_CFL = 2u, POND_FLAG_NOCONV = 4u };
+
+typedef struct {
+  double gamma;            /* adiabatic exponent, C_v = 1/(gamma-1) (Sec. III.A) */
+  double tau;              /* relaxation time tau_1                              */
+  double prandtl;          /* Pr = tau_1/tau_2; 1 disables the QE step          */
+  double dx;               /* cell size (square cells in 2D)                     */
+  double dt;               /* time step; <= 0: set by pond_init from cfl         */
+  double cfl;              /* max|v_i alpha| dt/dx used when dt <= 0 (Sec. V)    */
+  int32_t bc[4];           /* POND_BC_* for x-lo, x-hi, y-lo, y-hi               */
+  double inflow[4][4];     /* per side: rho, ux, uy, T of the inflow ghost state */
+  int32_t precision;       /* POND_FP64 | POND_FP32_MIXED                        */
+  int32_t transform;       /* POND_TENSOR | POND_GRAD_K                          */
+  int32_t flux_form;       /* POND_FLUX_MAIN | POND_FLUX_APPC                    */
+  int32_t limiter;         /* POND_VANLEER | POND_MINMOD                         */
+  int32_t flux_frame;      /* POND_FRAME_AVG | POND_FRAME_ITER                   */
+  double iter_tol;         /* convergence tolerance of the iterated frame        */
+  int32_t iter_max;        /* iteration cap of the iterated frame                */
+  double xi_fp64_threshold;/* mixed path: build the frame transformation in FP64
+                              when the shift |(u_s-u_F)/sqrt(T_F)| or the scale
+                              sqrt(T_s/T_F) exceeds this                          */
+  int32_t tile;            /* 0: automatic; otherwise a tile code (pond_tiles)   */
+} pond_params;
+
+/* Fills the defaults: gamma 1.4, tau 1e-4, Pr 1, dx 1, dt 0 (from cfl 0.2),
+ * periodic, FP64, tensor, main flux form, van Leer, averaged frame,
+ * iter_tol 1e-12, iter_max 10, xi_fp64_threshold 8, tile 0. */
+void pond_params_default(pond_params *p);
+
+/* Device bytes a context needs for the given lattice/dims/params (two state
+ * buffers plus a small status block).  dims = {nx, ny}; ny is ignored in 1D. */
+pond_status pond_workspace_size(pond_lattice lat, const int64_t dims[2], const pond_params *p,
+                                size_t *bytes);
+
+/* Creates a context on the current CUDA device.  workspace: caller-owned
+ * device memory of at least pond_workspace_size() bytes, 256-byte aligned, or
+ * NULL to let the context allocate (and free) its own.  stream: a cudaStream_t
+ * (NULL = legacy default stream) on which every kernel of the context runs.
+ * Errors: POND_E_INVAL (bad lattice, dims < 2, tau/dx/gamma out of range,
+ * unknown option), POND_E_NOMEM, POND_E_CUDA. */
+pond_status pond_create(pond_ctx **out, pond_lattice lat, const int64_t dims[2],
+                        const pond_params *p, void *workspace, size_t workspace_bytes,
+                        void *stream);
+
+/* Sets the state to the co-moving equilibrium of the primitive fields
+ * (Eqs. feqPond, geqPond): f = rho W, g = (C_v - D/2) T rho W, frame (u, T).
+ * rho, ux, T: [ny][nx]; uy: [ny][nx] in 2D, ignored (may be NULL) in 1D.
+ * If params.dt <= 0, dt is set so that max|v_i alpha| dt/dx = params.cfl on
+ * this state.  Resets the status flags.  Synchronises the stream. */
+pond_status pond_init(pond_ctx *c, const double *rho, const double *ux, const double *uy,
+                      const double *T, int on_device);
+
+/* Advances the state by n >= 0 steps (asynchronous on the context stream;
+ * consecutive steps are replayed from a captured CUDA graph).  Returns
+ * POND_E_STATE before pond_init/pond_set_state, POND_E_INVAL for n < 0. */
+pond_status pond_step(pond_ctx *c, int64_t n);
+
+/* rho, u, T of every cell recomputed from the populations (Eqs.
+ * eq::ConservationLaws, eq:E).  uy may be NULL in 1D.  Synchronises. */
+pond_status pond_moments(pond_ctx *c, double *rho, double *ux, double *uy, double *T,
+                         int on_device);
+
+/* Raw state in / out (layouts above).  pond_set_state takes populations that
+ * are already in each cell's co-moving frame (ux, uy, T).  Synchronises. */
+pond_status pond_get_state(pond_ctx *c, double *f, double *g, double *ux, double *uy,
+                           double *T, int on_device);
+pond_status pond_set_state(pond_ctx *c, const double *f, const double *g, const double *ux,
+                           const double *uy, const double *T, int on_device);
+
+/* Sticky flags (POND_FLAG_*), the largest CFL number max|v_i alpha| dt/dx met
+ * since the last reset, and the count of face evaluations whose iterated
+ * frame did not converge.  Any pointer may be NULL.  Synchronises.  Returns
+ * POND_E_NONPHYSICAL if that flag is set, else POND_OK. */
+pond_status pond_status_flags(pond_ctx *c, uint32_t *flags, double *max_cfl,
+                              int64_t *noconv_faces);
+pond_status pond_reset_flags(pond_ctx *c);
+
+/* Waits for all work queued on the context stream. */
+pond_status pond_sync(pond_ctx *c);
+
+/* Time step in use, steps taken since pond_init/pond_set_state, and the tile
+ * code the step kernel runs with. */
+pond_status pond_info(pond_ctx *c, double *dt, int64_t *steps, int32_t *tile);
+
+/* Releases the context and the device memory it allocated itself. */
+void pond_destroy(pond_ctx *c);
+
+/* Static description of a status code. */
+const char *pond_strerror(pond_status s);
+
+/* POND_ABI_VERSION of the loaded library. */
+int pond_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POND_H */

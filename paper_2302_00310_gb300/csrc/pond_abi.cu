@@ -1,0 +1,605 @@
+// pond_abi.cu -- the C ABI of include/pond.h: contexts, device state, launches.
+//
+// Device state of a context (one workspace, 256-byte aligned sub-buffers):
+//   [Stats block][state buffer 0][state buffer 1]
+// A state buffer holds, in the arithmetic type R of the context (double for
+// POND_FP64, float for POND_FP32_MIXED), SoA arrays
+//   f[Qf][N], g[Qg][N], ux[N], uy[N], T[N]          (N = nx*ny cells)
+// Steps ping-pong between the two buffers; between steps the idle buffer is
+// used as staging for FP64 fields at the boundary.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "pond.h"
+#include "pond_kernels.cuh"
+
+using pond::State;
+using pond::StepConst;
+using pond::Stats;
+
+struct pond_ctx {
+  pond_lattice lat;
+  int D;
+  int64_t nx, ny, N;
+  pond_params p;
+  bool fp32;
+  cudaStream_t stream;
+  unsigned char *ws;
+  size_t ws_bytes;
+  bool own_ws;
+  unsigned char *buf[2];
+  size_t buf_bytes;
+  Stats *stats;
+  int cur;
+  bool inited;
+  double dt;
+  int64_t steps;
+  int tile;
+  StepConst K;
+  cudaGraphExec_t graph[2];
+  int graph_chunk;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+int qf_of(int D) { return D == 2 ? 16 : 4; }
+int qg_of(int D) { return D == 2 ? 9 : 3; }
+
+#define POND_CUDA(call)                                   \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) {                              \
+      (void)cudaGetLastError();                           \
+      return POND_E_CUDA;                                 \
+    }                                                     \
+  } while (0)
+
+template <typename R> State<R> state_of(const pond_ctx *c, int b) {
+  R *base = reinterpret_cast<R *>(c->buf[b]);
+  State<R> s;
+  s.f = base;
+  s.g = s.f + (size_t)qf_of(c->D) * c->N;
+  s.ux = s.g + (size_t)qg_of(c->D) * c->N;
+  s.uy = s.ux + c->N;
+  s.T = s.uy + c->N;
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// small kernels: initial equilibrium, moments, conversions, max |v|
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double w4(int k) { return (k == 1 || k == 2) ? pond::W1 : pond::W2; }
+__device__ __forceinline__ double w3(int k) { return k == 1 ? 2.0 / 3.0 : 1.0 / 6.0; }
+
+template <typename R, int DIM>
+__global__ void init_kernel(const double *rho, const double *ux, const double *uy, const double *T,
+                            State<R> S, size_t N, double gfac) {
+  const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= N) return;
+  const double r = rho[c], t = T[c];
+  // co-moving equilibria rho W (Eq. feqPond) and (C_v - D/2) T rho W (Eq. geqPond)
+  for (int i = 0; i < (DIM == 2 ? 16 : 4); ++i) {
+    const double W = DIM == 2 ? w4(i % 4) * w4(i / 4) : w4(i);
+    S.f[i * N + c] = R(r * W);
+  }
+  for (int i = 0; i < (DIM == 2 ? 9 : 3); ++i) {
+    const double W = DIM == 2 ? w3(i % 3) * w3(i / 3) : w3(i);
+    S.g[i * N + c] = R(gfac * t * r * W);
+  }
+  S.ux[c] = R(ux[c]);
+  S.uy[c] = DIM == 2 ? R(uy[c]) : R(0);
+  S.T[c] = R(t);
+}
+
+// rho, u, T of each cell from its populations (Eqs. eq::ConservationLaws, eq:E)
+template <typename R, int DIM>
+__global__ void moments_kernel(State<R> S, size_t N, double inv_cv, double *rho, double *ux,
+                               double *uy, double *T) {
+  const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= N) return;
+  using D = pond::Dims<DIM>;
+  pond::Blk<double, 4, D::NYF> F;
+  pond::Blk<double, 3, D::NYG> G;
+  for (int i = 0; i < D::QF; ++i) F.v[i % 4][i / 4] = (double)S.f[i * N + c];
+  for (int i = 0; i < D::QG; ++i) G.v[i % 3][i / 3] = (double)S.g[i * N + c];
+  pond::ana_x(F); pond::ana_y(F); pond::ana_x(G); pond::ana_y(G);
+  const double fx = S.ux[c], fy = DIM == 2 ? (double)S.uy[c] : 0.0, fT = S.T[c], sT = sqrt(fT);
+  const double r = F.v[0][0], mx = F.v[1][0] / r;
+  double my = 0.0, S2 = F.v[2][0] + DIM * r;
+  if constexpr (DIM == 2) { my = F.v[0][1] / r; S2 += F.v[0][2]; }
+  const double e = 0.5 * fT * (S2 - r * (mx * mx + my * my)) + G.v[0][0];
+  rho[c] = r;
+  ux[c] = fx + sT * mx;
+  if (uy) uy[c] = fy + sT * my;
+  T[c] = e / r * inv_cv;
+}
+
+template <typename A, typename B>
+__global__ void convert_kernel(const A *in, B *out, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = B(in[i]);
+}
+
+// largest |v_i alpha| over cells for the CFL time step (Sec. V)
+__global__ void vmax_kernel(const double *ux, const double *uy, const double *T, size_t N,
+                            unsigned long long *out) {
+  const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double v = 0.0;
+  if (c < N) v = fmax(fabs(ux[c]), uy ? fabs(uy[c]) : 0.0) + sqrt(T[c]) * pond::Nodes<4>::cmax;
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(v));
+}
+
+unsigned grid1(size_t n, unsigned b) { return (unsigned)((n + b - 1) / b); }
+
+// ---------------------------------------------------------------------------
+// step launches
+// ---------------------------------------------------------------------------
+template <typename R, int DIM, int BX, int BY, int NT>
+pond_status launch_tile(pond_ctx *c, int from, bool prepare_only) {
+  static_assert(NT % 32 == 0, "whole warps");
+  using TL = pond::Tile<DIM, BX, BY>;
+  constexpr size_t smem = TL::template smem_bytes<R>();
+  static_assert(smem <= 227 * 1024, "tile too large for shared memory");
+  if (prepare_only) {
+    // the dynamic shared-memory opt-in is set outside any stream capture
+    POND_CUDA(cudaFuncSetAttribute(pond::step_kernel<R, DIM, BX, BY, NT>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return POND_OK;
+  }
+  const dim3 grid((unsigned)((c->nx + BX - 1) / BX), DIM == 2 ? (unsigned)((c->ny + BY - 1) / BY) : 1u);
+  pond::step_kernel<R, DIM, BX, BY, NT><<<grid, NT, smem, c->stream>>>(
+      c->K, state_of<R>(c, from), state_of<R>(c, 1 - from), c->stats);
+  POND_CUDA(cudaGetLastError());
+  return POND_OK;
+}
+
+// tile codes: 1 = 1D 252 cells; 2 = 2D 8x8; 3 = 2D 16x16; 4 = 2D 16x8
+template <typename R>
+pond_status launch_step(pond_ctx *c, int from, bool prepare_only) {
+  if (c->D == 1) return launch_tile<R, 1, 252, 1, 256>(c, from, prepare_only);
+  switch (c->tile) {
+    case 3: return launch_tile<R, 2, 16, 16, 256>(c, from, prepare_only);
+    case 4: return launch_tile<R, 2, 16, 8, 256>(c, from, prepare_only);
+    default: return launch_tile<R, 2, 8, 8, 160>(c, from, prepare_only);
+  }
+}
+
+pond_status prepare_step(pond_ctx *c) {
+  return c->fp32 ? launch_step<float>(c, 0, true) : launch_step<double>(c, 0, true);
+}
+
+pond_status step_once(pond_ctx *c) {
+  pond_status s = c->fp32 ? launch_step<float>(c, c->cur, false) : launch_step<double>(c, c->cur, false);
+  if (s == POND_OK) c->cur ^= 1;
+  return s;
+}
+
+int auto_tile(const pond_ctx *c) {
+  if (c->D == 1) return 1;
+  const int64_t tiles16 = ((c->nx + 15) / 16) * ((c->ny + 15) / 16);
+  return tiles16 >= 8 * 152 ? 3 : 2;
+}
+
+bool valid_params(const pond_params *p) {
+  if (!p) return false;
+  if (!(p->gamma > 1.0) || !(p->tau > 0.0) || !(p->prandtl > 0.0) || !(p->dx > 0.0)) return false;
+  if (!(p->dt > 0.0) && !(p->cfl > 0.0)) return false;
+  for (int s = 0; s < 4; ++s)
+    if (p->bc[s] < POND_BC_PERIODIC || p->bc[s] > POND_BC_INFLOW) return false;
+  if ((p->bc[0] == POND_BC_PERIODIC) != (p->bc[1] == POND_BC_PERIODIC)) return false;
+  if ((p->bc[2] == POND_BC_PERIODIC) != (p->bc[3] == POND_BC_PERIODIC)) return false;
+  if (p->precision != POND_FP64 && p->precision != POND_FP32_MIXED) return false;
+  if (p->transform != POND_TENSOR && p->transform != POND_GRAD_K) return false;
+  if (p->flux_form != POND_FLUX_MAIN && p->flux_form != POND_FLUX_APPC) return false;
+  if (p->limiter != POND_VANLEER && p->limiter != POND_MINMOD) return false;
+  if (p->flux_frame != POND_FRAME_AVG) return false;  // iterated frame: not in this build
+  if (p->tile < 0 || p->tile > 4) return false;
+  return true;
+}
+
+void set_step_const(pond_ctx *c) {
+  const pond_params &p = c->p;
+  StepConst &K = c->K;
+  memset(&K, 0, sizeof(K));
+  K.nx = (int)c->nx;
+  K.ny = (int)c->ny;
+  for (int s = 0; s < 4; ++s) {
+    K.bc[s] = p.bc[s];
+    for (int m = 0; m < 4; ++m) K.inflow[s][m] = p.inflow[s][m];
+  }
+  const double dt = c->dt, tau = p.tau, h = 0.5 * dt;
+  K.lam = dt / p.dx;
+  // face phi = kappa1 phi_bar + kappa2 phi^eq (inverse of Eq. eq:FluxTransf)
+  K.kappa1 = 2.0 * tau / (2.0 * tau + h);
+  K.kr = (h / (2.0 * tau + h)) / K.kappa1;
+  // phi_bar^+ = (2 tau - h)/(2 tau + dt) phi~ + 3h/(2 tau + dt) phi^eq  (Eqs. eq:variableTransform, eq:Fbarplus)
+  K.kp_a = K.kappa1 * (2.0 * tau - h) / (2.0 * tau + dt);
+  K.kp_b = K.kappa1 * 3.0 * h / (2.0 * tau + dt);
+  K.a1 = (2.0 * tau - dt) / (2.0 * tau + dt);
+  K.a2 = 2.0 * dt / (2.0 * tau + dt);
+  const double tau2 = tau / p.prandtl;
+  K.qe = p.prandtl == 1.0 ? 1.0 : 1.0 + 0.5 * dt * (1.0 / tau - 1.0 / tau2);
+  const double cv = 1.0 / (p.gamma - 1.0);
+  K.inv_cv = 1.0 / cv;
+  K.gfac = cv - 0.5 * c->D;
+  K.iter_tol = p.iter_tol;
+  K.iter_max = p.iter_max;
+  K.grad_k = p.transform == POND_GRAD_K;
+  K.appc = p.flux_form == POND_FLUX_APPC;
+  K.limiter = p.limiter;
+  K.iterative = p.flux_frame == POND_FRAME_ITER;
+}
+
+void drop_graphs(pond_ctx *c) {
+  for (int i = 0; i < 2; ++i)
+    if (c->graph[i]) { cudaGraphExecDestroy(c->graph[i]); c->graph[i] = nullptr; }
+}
+
+// captures `chunk` consecutive steps starting from buffer `from`
+pond_status build_graph(pond_ctx *c, int from, int chunk) {
+  cudaGraph_t g = nullptr;
+  const int save = c->cur;
+  c->cur = from;
+  POND_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  pond_status s = POND_OK;
+  for (int i = 0; i < chunk && s == POND_OK; ++i) s = step_once(c);
+  cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+  c->cur = save;
+  if (s != POND_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    (void)cudaGetLastError();
+    return s != POND_OK ? s : POND_E_CUDA;
+  }
+  e = cudaGraphInstantiate(&c->graph[from], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) { (void)cudaGetLastError(); return POND_E_CUDA; }
+  return POND_OK;
+}
+
+template <typename T>
+pond_status to_device(pond_ctx *c, const T *src, T *dst, size_t n, int on_device) {
+  POND_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(T), on_device ? cudaMemcpyDeviceToDevice
+                                                                 : cudaMemcpyHostToDevice,
+                            c->stream));
+  return POND_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// exported ABI
+// ===========================================================================
+extern "C" {
+
+int pond_abi_version(void) { return POND_ABI_VERSION; }
+
+void pond_params_default(pond_params *p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->gamma = 1.4;
+  p->tau = 1e-4;
+  p->prandtl = 1.0;
+  p->dx = 1.0;
+  p->dt = 0.0;
+  p->cfl = 0.2;
+  for (int s = 0; s < 4; ++s) p->bc[s] = POND_BC_PERIODIC;
+  p->precision = POND_FP64;
+  p->transform = POND_TENSOR;
+  p->flux_form = POND_FLUX_MAIN;
+  p->limiter = POND_VANLEER;
+  p->flux_frame = POND_FRAME_AVG;
+  p->iter_tol = 1e-12;
+  p->iter_max = 10;
+  p->xi_fp64_threshold = 8.0;
+  p->tile = 0;
+}
+
+const char *pond_strerror(pond_status s) {
+  switch (s) {
+    case POND_OK: return "ok";
+    case POND_E_INVAL: return "invalid argument";
+    case POND_E_NOMEM: return "out of device memory or workspace too small";
+    case POND_E_CUDA: return "CUDA runtime error";
+    case POND_E_NONPHYSICAL: return "nonphysical state (rho <= 0, T <= 0 or NaN)";
+    case POND_E_NOCONV: return "iterated face frame did not converge";
+    case POND_E_CFL: return "CFL number above 1";
+    case POND_E_STATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+pond_status pond_workspace_size(pond_lattice lat, const int64_t dims[2], const pond_params *p,
+                                size_t *bytes) {
+  if (!dims || !bytes || !p || (lat != POND_D1Q4 && lat != POND_D2Q16)) return POND_E_INVAL;
+  const int D = lat == POND_D2Q16 ? 2 : 1;
+  const int64_t nx = dims[0], ny = D == 2 ? dims[1] : 1;
+  if (nx < 2 || (D == 2 && ny < 2) || nx > (1 << 24) || ny > (1 << 24)) return POND_E_INVAL;
+  const size_t rs = p->precision == POND_FP32_MIXED ? 4 : 8;
+  const size_t per_cell = (size_t)(qf_of(D) + qg_of(D) + 3) * rs;
+  *bytes = align_up(sizeof(Stats)) + 2 * align_up(per_cell * (size_t)(nx * ny));
+  return POND_OK;
+}
+
+pond_status pond_create(pond_ctx **out, pond_lattice lat, const int64_t dims[2],
+                        const pond_params *p, void *workspace, size_t workspace_bytes,
+                        void *stream) {
+  if (!out) return POND_E_INVAL;
+  *out = nullptr;
+  size_t need = 0;
+  pond_status s = pond_workspace_size(lat, dims, p, &need);
+  if (s != POND_OK) return s;
+  if (!valid_params(p)) return POND_E_INVAL;
+  if (p->precision == POND_FP32_MIXED) return POND_E_INVAL;  // mixed path: not in this build
+  const int D = lat == POND_D2Q16 ? 2 : 1;
+  if (D == 1 && p->tile > 1) return POND_E_INVAL;
+  if (D == 2 && p->tile == 1) return POND_E_INVAL;
+  if (workspace && (workspace_bytes < need || ((uintptr_t)workspace % kAlign) != 0))
+    return POND_E_NOMEM;
+  pond_ctx *c = new (std::nothrow) pond_ctx();
+  if (!c) return POND_E_NOMEM;
+  c->lat = lat;
+  c->D = D;
+  c->nx = dims[0];
+  c->ny = D == 2 ? dims[1] : 1;
+  c->N = c->nx * c->ny;
+  c->p = *p;
+  c->fp32 = false;
+  c->stream = (cudaStream_t)stream;
+  if (workspace) {
+    c->ws = (unsigned char *)workspace;
+    c->own_ws = false;
+  } else {
+    if (cudaMalloc((void **)&c->ws, need) != cudaSuccess) {
+      (void)cudaGetLastError();
+      delete c;
+      return POND_E_NOMEM;
+    }
+    c->own_ws = true;
+  }
+  c->ws_bytes = need;
+  c->stats = reinterpret_cast<Stats *>(c->ws);
+  c->buf_bytes = (need - align_up(sizeof(Stats))) / 2;
+  c->buf[0] = c->ws + align_up(sizeof(Stats));
+  c->buf[1] = c->buf[0] + c->buf_bytes;
+  c->cur = 0;
+  c->tile = p->tile ? p->tile : auto_tile(c);
+  c->graph_chunk = 8;
+  if (cudaMemsetAsync(c->stats, 0, sizeof(Stats), c->stream) != cudaSuccess) {
+    (void)cudaGetLastError();
+    pond_destroy(c);
+    return POND_E_CUDA;
+  }
+  *out = c;
+  return POND_OK;
+}
+
+void pond_destroy(pond_ctx *c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  drop_graphs(c);
+  if (c->own_ws && c->ws) cudaFree(c->ws);
+  (void)cudaGetLastError();
+  delete c;
+}
+
+pond_status pond_init(pond_ctx *c, const double *rho, const double *ux, const double *uy,
+                      const double *T, int on_device) {
+  if (!c || !rho || !ux || !T || (c->D == 2 && !uy)) return POND_E_INVAL;
+  const size_t N = (size_t)c->N;
+  // stage the primitive fields (FP64) in the idle buffer
+  double *st = reinterpret_cast<double *>(c->buf[1 - c->cur]);
+  double *srho = st, *sux = st + N, *suy = st + 2 * N, *sT = st + 3 * N;
+  pond_status s;
+  if ((s = to_device(c, rho, srho, N, on_device)) != POND_OK) return s;
+  if ((s = to_device(c, ux, sux, N, on_device)) != POND_OK) return s;
+  if (c->D == 2 && (s = to_device(c, uy, suy, N, on_device)) != POND_OK) return s;
+  if ((s = to_device(c, T, sT, N, on_device)) != POND_OK) return s;
+  POND_CUDA(cudaMemsetAsync(c->stats, 0, sizeof(Stats), c->stream));
+  const double gfac = 1.0 / (c->p.gamma - 1.0) - 0.5 * c->D;
+  const unsigned nb = grid1(N, 256);
+  if (c->D == 2) {
+    if (c->fp32) init_kernel<float, 2><<<nb, 256, 0, c->stream>>>(srho, sux, suy, sT, state_of<float>(c, c->cur), N, gfac);
+    else init_kernel<double, 2><<<nb, 256, 0, c->stream>>>(srho, sux, suy, sT, state_of<double>(c, c->cur), N, gfac);
+  } else {
+    if (c->fp32) init_kernel<float, 1><<<nb, 256, 0, c->stream>>>(srho, sux, nullptr, sT, state_of<float>(c, c->cur), N, gfac);
+    else init_kernel<double, 1><<<nb, 256, 0, c->stream>>>(srho, sux, nullptr, sT, state_of<double>(c, c->cur), N, gfac);
+  }
+  POND_CUDA(cudaGetLastError());
+  c->dt = c->p.dt;
+  if (!(c->dt > 0.0)) {
+    unsigned long long *slot = &c->stats->noconv;  // borrowed before the counters are reset
+    POND_CUDA(cudaMemsetAsync(slot, 0, sizeof(*slot), c->stream));
+    vmax_kernel<<<nb, 256, 0, c->stream>>>(sux, c->D == 2 ? suy : nullptr, sT, N, slot);
+    POND_CUDA(cudaGetLastError());
+    unsigned long long bits = 0;
+    POND_CUDA(cudaMemcpyAsync(&bits, slot, sizeof(bits), cudaMemcpyDeviceToHost, c->stream));
+    POND_CUDA(cudaStreamSynchronize(c->stream));
+    double vmax;
+    memcpy(&vmax, &bits, sizeof(vmax));
+    if (!(vmax > 0.0) || !std::isfinite(vmax)) return POND_E_INVAL;
+    c->dt = c->p.cfl * c->p.dx / vmax;
+    POND_CUDA(cudaMemsetAsync(slot, 0, sizeof(*slot), c->stream));
+  }
+  set_step_const(c);
+  drop_graphs(c);
+  if ((s = prepare_step(c)) != POND_OK) return s;
+  c->steps = 0;
+  c->inited = true;
+  POND_CUDA(cudaStreamSynchronize(c->stream));
+  return POND_OK;
+}
+
+pond_status pond_step(pond_ctx *c, int64_t n) {
+  if (!c || n < 0) return POND_E_INVAL;
+  if (!c->inited) return POND_E_STATE;
+  // stream capture is not possible on the legacy default stream: launch directly there
+  const int chunk = c->stream ? c->graph_chunk : 0;
+  int64_t done = 0;
+  while (chunk > 0 && n - done >= chunk) {
+    if (!c->graph[c->cur]) {
+      pond_status s = build_graph(c, c->cur, chunk);
+      if (s != POND_OK) return s;
+    }
+    POND_CUDA(cudaGraphLaunch(c->graph[c->cur], c->stream));
+    if (chunk & 1) c->cur ^= 1;
+    done += chunk;
+  }
+  for (; done < n; ++done) {
+    pond_status s = step_once(c);
+    if (s != POND_OK) return s;
+  }
+  c->steps += n;
+  return POND_OK;
+}
+
+pond_status pond_moments(pond_ctx *c, double *rho, double *ux, double *uy, double *T,
+                         int on_device) {
+  if (!c || !rho || !ux || !T) return POND_E_INVAL;
+  if (!c->inited) return POND_E_STATE;
+  const size_t N = (size_t)c->N;
+  double *out[4];
+  double *st = reinterpret_cast<double *>(c->buf[1 - c->cur]);
+  if (on_device) {
+    out[0] = rho; out[1] = ux; out[2] = uy; out[3] = T;
+  } else {
+    out[0] = st; out[1] = st + N; out[2] = st + 2 * N; out[3] = st + 3 * N;
+  }
+  if (c->D == 1) out[2] = nullptr;
+  const double inv_cv = c->p.gamma - 1.0;
+  const unsigned nb = grid1(N, 256);
+  if (c->D == 2) {
+    if (c->fp32) moments_kernel<float, 2><<<nb, 256, 0, c->stream>>>(state_of<float>(c, c->cur), N, inv_cv, out[0], out[1], out[2], out[3]);
+    else moments_kernel<double, 2><<<nb, 256, 0, c->stream>>>(state_of<double>(c, c->cur), N, inv_cv, out[0], out[1], out[2], out[3]);
+  } else {
+    if (c->fp32) moments_kernel<float, 1><<<nb, 256, 0, c->stream>>>(state_of<float>(c, c->cur), N, inv_cv, out[0], out[1], out[2], out[3]);
+    else moments_kernel<double, 1><<<nb, 256, 0, c->stream>>>(state_of<double>(c, c->cur), N, inv_cv, out[0], out[1], out[2], out[3]);
+  }
+  POND_CUDA(cudaGetLastError());
+  if (!on_device) {
+    POND_CUDA(cudaMemcpyAsync(rho, out[0], N * 8, cudaMemcpyDeviceToHost, c->stream));
+    POND_CUDA(cudaMemcpyAsync(ux, out[1], N * 8, cudaMemcpyDeviceToHost, c->stream));
+    if (c->D == 2 && uy) POND_CUDA(cudaMemcpyAsync(uy, out[2], N * 8, cudaMemcpyDeviceToHost, c->stream));
+    POND_CUDA(cudaMemcpyAsync(T, out[3], N * 8, cudaMemcpyDeviceToHost, c->stream));
+  }
+  POND_CUDA(cudaStreamSynchronize(c->stream));
+  return POND_OK;
+}
+
+// copies one FP64 boundary array to/from state component `comp` (n values)
+static pond_status xfer(pond_ctx *c, double *ext, size_t comp_off, size_t n, bool to_state,
+                        int on_device) {
+  const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const cudaMemcpyKind kout = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (!c->fp32) {
+    double *dst = reinterpret_cast<double *>(c->buf[c->cur]) + comp_off;
+    if (to_state) POND_CUDA(cudaMemcpyAsync(dst, ext, n * 8, kin, c->stream));
+    else POND_CUDA(cudaMemcpyAsync(ext, dst, n * 8, kout, c->stream));
+    return POND_OK;
+  }
+  float *st = reinterpret_cast<float *>(c->buf[c->cur]) + comp_off;
+  double *stage = reinterpret_cast<double *>(c->buf[1 - c->cur]);
+  const unsigned nb = grid1(n, 256);
+  if (to_state) {
+    POND_CUDA(cudaMemcpyAsync(stage, ext, n * 8, kin, c->stream));
+    convert_kernel<double, float><<<nb, 256, 0, c->stream>>>(stage, st, n);
+    POND_CUDA(cudaGetLastError());
+  } else {
+    convert_kernel<float, double><<<nb, 256, 0, c->stream>>>(st, stage, n);
+    POND_CUDA(cudaGetLastError());
+    POND_CUDA(cudaMemcpyAsync(ext, stage, n * 8, kout, c->stream));
+  }
+  // the staging buffer is reused by the next component
+  POND_CUDA(cudaStreamSynchronize(c->stream));
+  return POND_OK;
+}
+
+static pond_status state_io(pond_ctx *c, double *f, double *g, double *ux, double *uy, double *T,
+                            bool to_state, int on_device) {
+  if (!c || !f || !g || !ux || !T || (c->D == 2 && !uy)) return POND_E_INVAL;
+  const size_t N = (size_t)c->N, qf = qf_of(c->D), qg = qg_of(c->D);
+  pond_status s;
+  // one population plane at a time: an FP64 plane always fits the staging buffer
+  for (size_t i = 0; i < qf; ++i)
+    if ((s = xfer(c, f + i * N, i * N, N, to_state, on_device)) != POND_OK) return s;
+  for (size_t i = 0; i < qg; ++i)
+    if ((s = xfer(c, g + i * N, (qf + i) * N, N, to_state, on_device)) != POND_OK) return s;
+  if ((s = xfer(c, ux, (qf + qg) * N, N, to_state, on_device)) != POND_OK) return s;
+  if (c->D == 2 && (s = xfer(c, uy, (qf + qg + 1) * N, N, to_state, on_device)) != POND_OK) return s;
+  if ((s = xfer(c, T, (qf + qg + 2) * N, N, to_state, on_device)) != POND_OK) return s;
+  POND_CUDA(cudaStreamSynchronize(c->stream));
+  return POND_OK;
+}
+
+pond_status pond_get_state(pond_ctx *c, double *f, double *g, double *ux, double *uy, double *T,
+                           int on_device) {
+  if (!c) return POND_E_INVAL;
+  if (!c->inited) return POND_E_STATE;
+  return state_io(c, f, g, ux, uy, T, false, on_device);
+}
+
+pond_status pond_set_state(pond_ctx *c, const double *f, const double *g, const double *ux,
+                           const double *uy, const double *T, int on_device) {
+  if (!c) return POND_E_INVAL;
+  if (!c->inited) {
+    // a state given directly still needs a time step
+    if (!(c->p.dt > 0.0)) return POND_E_STATE;
+    c->dt = c->p.dt;
+    set_step_const(c);
+    pond_status s0 = prepare_step(c);
+    if (s0 != POND_OK) return s0;
+  }
+  if (c->D == 1) {
+    // keep the unused uy plane defined
+    if (c->fp32) POND_CUDA(cudaMemsetAsync(state_of<float>(c, c->cur).uy, 0, c->N * 4, c->stream));
+    else POND_CUDA(cudaMemsetAsync(state_of<double>(c, c->cur).uy, 0, c->N * 8, c->stream));
+  }
+  pond_status s = state_io(c, const_cast<double *>(f), const_cast<double *>(g),
+                           const_cast<double *>(ux), const_cast<double *>(uy),
+                           const_cast<double *>(T), true, on_device);
+  if (s != POND_OK) return s;
+  drop_graphs(c);
+  c->steps = 0;
+  c->inited = true;
+  return POND_OK;
+}
+
+pond_status pond_status_flags(pond_ctx *c, uint32_t *flags, double *max_cfl, int64_t *noconv) {
+  if (!c) return POND_E_INVAL;
+  Stats h;
+  POND_CUDA(cudaMemcpyAsync(&h, c->stats, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  POND_CUDA(cudaStreamSynchronize(c->stream));
+  if (flags) *flags = h.flags;
+  if (max_cfl) memcpy(max_cfl, &h.max_cfl_bits, sizeof(double));
+  if (noconv) *noconv = (int64_t)h.noconv;
+  return (h.flags & POND_FLAG_NONPHYSICAL) ? POND_E_NONPHYSICAL : POND_OK;
+}
+
+pond_status pond_reset_flags(pond_ctx *c) {
+  if (!c) return POND_E_INVAL;
+  POND_CUDA(cudaMemsetAsync(c->stats, 0, sizeof(Stats), c->stream));
+  return POND_OK;
+}
+
+pond_status pond_sync(pond_ctx *c) {
+  if (!c) return POND_E_INVAL;
+  POND_CUDA(cudaStreamSynchronize(c->stream));
+  return POND_OK;
+}
+
+pond_status pond_info(pond_ctx *c, double *dt, int64_t *steps, int32_t *tile) {
+  if (!c) return POND_E_INVAL;
+  if (dt) *dt = c->dt;
+  if (steps) *steps = c->steps;
+  if (tile) *tile = c->tile;
+  return POND_OK;
+}
+
+}  // extern "C"

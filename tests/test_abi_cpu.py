@@ -1,0 +1,62 @@
+"""The C-ABI library builds, loads without a GPU and exports every function
+include/pond.h declares; host-only entry points behave as documented."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2302_00310_gb300 import build as B
+from paper_2302_00310_gb300 import pond
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "pond.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pond_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    B.build()
+    return pond.lib()
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(L, n), n
+    assert sorted(pond.EXPORTS) == names
+
+
+def test_host_only_calls(L):
+    assert pond.pond_abi_version() == 1
+    p = pond.pond_params_default()
+    assert p.gamma == 1.4 and p.cfl == 0.2 and p.iter_max == 10
+    assert pond.pond_strerror(pond.POND_E_NONPHYSICAL).startswith("nonphysical")
+    n1 = pond.pond_workspace_size(pond.POND_D2Q16, (256, 256), p)
+    assert n1 >= 2 * 256 * 256 * 28 * 8
+    p.precision = pond.POND_FP32_MIXED
+    n2 = pond.pond_workspace_size(pond.POND_D2Q16, (256, 256), p)
+    assert n2 < n1
+
+
+def test_invalid_arguments_are_rejected_before_any_device_work(L):
+    p = pond.pond_params_default()
+    with pytest.raises(pond.PondError) as e:
+        pond.pond_workspace_size(pond.POND_D2Q16, (1, 8), p)
+    assert e.value.status == pond.POND_E_INVAL
+    p.tau = -1.0
+    with pytest.raises(pond.PondError) as e:
+        pond.pond_create(pond.POND_D2Q16, (8, 8), p)
+    assert e.value.status == pond.POND_E_INVAL
+    p = pond.pond_params_default()
+    p.bc[0] = pond.POND_BC_PERIODIC
+    p.bc[1] = pond.POND_BC_ZERO_GRADIENT
+    with pytest.raises(pond.PondError):
+        pond.pond_create(pond.POND_D2Q16, (8, 8), p)
+    with pytest.raises(pond.PondError):
+        pond.pond_create(7, (8, 8), pond.pond_params_default())

@@ -1,0 +1,260 @@
+"""GPU parity: the CUDA path against the FP64 oracle, element by element, on
+the same seeded inputs (both sides initialise from the same primitive
+fields).  FP64 path tolerance: max|x_gpu - x_oracle| / max|x_oracle| <= 1e-12
+per field (populations, frame)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2302_00310_gb300 import pond
+from paper_2302_00310_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pond.lib(build=True)
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _run_both(cfg, rho, ux, uy, T, steps, tile=0):
+    ocfg = oracle.Config.from_dict(cfg)
+    ost = oracle.run(ocfg, oracle.init(ocfg, rho, ux, uy, T), steps)
+    c = dict(cfg, tile=tile)
+    sim = pond.Sim(c)
+    sim.init(rho, ux, uy, T)
+    sim.step(steps)
+    got = sim.get_state()
+    flags = sim.flags()
+    sim.close()
+    return ost, got, flags
+
+
+def _compare(ost, got, D, tol=TOL):
+    f, g, ux, uy, T = got
+    errs = {"f": _rel(f, ost.f), "g": _rel(g, ost.g), "ux": _rel(ux, ost.ux), "T": _rel(T, ost.T)}
+    if D == 2:
+        errs["uy"] = _rel(uy, ost.uy)
+    bad = {k: v for k, v in errs.items() if not v <= tol}
+    assert not bad, errs
+    return errs
+
+
+CASES_1D = [
+    # nx, bc, prandtl, limiter, appc, mach, steps
+    (300, (1, 1, 1, 1), 1.0, 0, 0, 0.8, 1),
+    (300, (0, 0, 0, 0), 0.71, 1, 0, 1.0, 3),
+    (253, (2, 1, 1, 1), 1.0, 0, 1, 0.5, 2),
+    (2, (1, 1, 1, 1), 1.0, 0, 0, 0.5, 2),
+    (505, (0, 0, 0, 0), 0.5, 0, 1, 1.0, 5),
+]
+
+
+@pytest.mark.parametrize("case", range(len(CASES_1D)))
+def test_1d_random_state_matches_oracle(case):
+    nx, bc, pr, lim, appc, mach, steps = CASES_1D[case]
+    rho, ux, uy, T = W.random_state_grid(1, nx, 1, seed=10 + case, mach=mach)
+    cfg = W._base(1, nx, 1, tau=5e-3, dx=1.0 / nx, prandtl=pr, limiter=lim, flux_appc=appc, bc=bc,
+                  inflow=((1.2, 0.4, 0.0, 0.9),) * 4)
+    cfg["dt"] = W.dt_from_cfl(ux, uy, T, cfg["dx"], 0.4)
+    ost, got, flags = _run_both(cfg, rho, ux, uy, T, steps)
+    _compare(ost, got, 1)
+    assert flags[1] & pond.POND_FLAG_NONPHYSICAL == 0
+
+
+CASES_2D = [
+    # nx, ny, bc, prandtl, limiter, grad_k, appc, mach, steps, tile
+    (37, 29, (0, 0, 0, 0), 1.0, 0, 0, 0, 0.8, 1, 2),
+    (37, 29, (1, 1, 1, 1), 0.71, 1, 0, 0, 1.2, 2, 3),
+    (21, 40, (2, 1, 1, 1), 1.0, 0, 1, 0, 0.6, 2, 4),
+    (18, 17, (0, 0, 1, 1), 0.71, 0, 0, 1, 1.0, 3, 2),
+    (2, 2, (0, 0, 0, 0), 1.0, 0, 0, 0, 0.5, 2, 2),
+    (33, 35, (1, 2, 2, 1), 0.5, 1, 1, 1, 0.9, 2, 3),
+]
+
+
+@pytest.mark.parametrize("case", range(len(CASES_2D)))
+def test_2d_random_state_matches_oracle(case):
+    nx, ny, bc, pr, lim, gk, appc, mach, steps, tile = CASES_2D[case]
+    rho, ux, uy, T = W.random_state_grid(2, nx, ny, seed=20 + case, mach=mach)
+    cfg = W._base(2, nx, ny, tau=5e-3, dx=1.0 / nx, prandtl=pr, limiter=lim, grad_k=gk,
+                  flux_appc=appc, bc=bc, inflow=((1.1, 0.5, -0.2, 0.8),) * 4)
+    cfg["dt"] = W.dt_from_cfl(ux, uy, T, cfg["dx"], 0.4)
+    ost, got, flags = _run_both(cfg, rho, ux, uy, T, steps, tile=tile)
+    _compare(ost, got, 2)
+
+
+@pytest.mark.parametrize("D,mach,gk", [(1, 2.0, 0), (2, 1.5, 1)])
+def test_violent_state_is_flagged_like_the_oracle(D, mach, gk):
+    """Random per-cell velocities at Mach 1.5-2 drive an interface temperature
+    negative: both sides report the state as nonphysical."""
+    n = 505 if D == 1 else 33
+    rho, ux, uy, T = W.random_state_grid(D, n, n if D == 2 else 1, seed=14 if D == 1 else 25, mach=mach)
+    cfg = W._base(D, n, n, tau=5e-3, dx=1.0 / n, prandtl=0.5, grad_k=gk, flux_appc=1,
+                  bc=(0, 0, 0, 0) if D == 1 else (1, 2, 2, 1), inflow=((1.1, 0.5, -0.2, 0.8),) * 4)
+    cfg["dt"] = W.dt_from_cfl(ux, uy, T, cfg["dx"], 0.4)
+    ost, got, flags = _run_both(cfg, rho, ux, uy, T, 2)
+    assert ost.report["flags"] & oracle.FLAG_NONPHYSICAL
+    assert flags[0] == pond.POND_E_NONPHYSICAL and flags[1] & pond.POND_FLAG_NONPHYSICAL
+
+
+def test_sod_full_run_matches_oracle():
+    """The 400-cell Sod tube, 250 steps to t = 0.2 (config time step)."""
+    w = W.sod_1d()
+    ost, got, flags = _run_both(w["cfg"], w["rho"], w["ux"], w["uy"], w["T"], w["steps"])
+    _compare(ost, got, 1)
+    # the same CFL bookkeeping as the oracle
+    assert abs(flags[2] - ost.report["max_cfl"]) < 1e-12 * ost.report["max_cfl"]
+    assert flags[1] & pond.POND_FLAG_CFL  # CFL ~ 1.09 > 1 at the config time step
+
+
+def test_config3_few_steps_matches_oracle():
+    w = W.config3_2d(n=40, prandtl=0.71)
+    w["cfg"]["tau"] = 2e-3
+    ost, got, _ = _run_both(w["cfg"], w["rho"], w["ux"], w["uy"], w["T"], 5)
+    _compare(ost, got, 2)
+
+
+def _window_oracle(cfg, fields, j, k, steps):
+    """Oracle run on the (4 steps + 1)^2 window around cell (j, k) of a periodic
+    grid; the centre cell depends only on cells within 2 per step."""
+    r = 2 * steps
+    ny, nx = fields[0].shape
+    jj = (np.arange(j - r, j + r + 1)) % nx
+    kk = (np.arange(k - r, k + r + 1)) % ny
+    sub = [np.ascontiguousarray(a[np.ix_(kk, jj)]) for a in fields]
+    c = dict(cfg, nx=2 * r + 1, ny=2 * r + 1, bc=(1, 1, 1, 1))
+    ocfg = oracle.Config.from_dict(c)
+    st = oracle.run(ocfg, oracle.init(ocfg, *sub), steps)
+    return st.f[:, r, r], st.g[:, r, r], st.ux[r, r], st.uy[r, r], st.T[r, r]
+
+
+@pytest.mark.parametrize("steps", [1, 2])
+def test_pulse_full_size_sampled_cells_match_oracle(steps):
+    """256^2 periodic pulse in the benchmark's launch configuration; 24 seeded
+    cells checked against the oracle one by one."""
+    w = W.pulse_2d(n=256, seed=0)
+    sim = pond.Sim(w["cfg"])
+    sim.init(w["rho"], w["ux"], w["uy"], w["T"])
+    sim.step(steps)
+    f, g, ux, uy, T = sim.get_state()
+    sim.close()
+    rng = np.random.default_rng(5)
+    fields = (w["rho"], w["ux"], w["uy"], w["T"])
+    for j, k in rng.integers(0, 256, (24, 2)):
+        of, og, oux, ouy, oT = _window_oracle(w["cfg"], fields, int(j), int(k), steps)
+        assert _rel(f[:, k, j], of) <= TOL
+        assert _rel(g[:, k, j], og) <= TOL
+        assert abs(ux[k, j] - oux) <= TOL * abs(oux) and abs(T[k, j] - oT) <= TOL * oT
+
+
+def test_pulse_full_run_conserves_and_advects():
+    """1000 steps of the 256^2 pulse: totals conserved to rounding (Appendix C)
+    and the density profile translated with the flow (Euler entropy wave)."""
+    w = W.pulse_2d(n=256, seed=0, steps=1000)
+    sim = pond.Sim(w["cfg"])
+    sim.init(w["rho"], w["ux"], w["uy"], w["T"])
+    r0, x0, y0, t0 = sim.moments()
+    sim.step(w["steps"])
+    r1, x1, y1, t1 = sim.moments()
+    st, flags, cfl, _ = sim.flags()
+    dt = sim.info()[0]
+    sim.close()
+    assert st == pond.POND_OK and not flags & pond.POND_FLAG_NONPHYSICAL
+    cv = 1 / 0.4
+    tot = lambda r, u, v, t: np.array([r.sum(), (r * u).sum(), (r * v).sum(),
+                                       (cv * r * t + 0.5 * r * (u * u + v * v)).sum()])
+    a, b = tot(r0, x0, y0, t0), tot(r1, x1, y1, t1)
+    assert np.max(np.abs(a - b) / np.abs(a)) < 1e-11
+    # exact solution: initial profile moved by u t (periodic)
+    n = 256
+    t_end = dt * w["steps"]
+    x = (np.arange(n) + 0.5) / n
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    prof = np.zeros((n, n))
+    U, V = w["velocity"]
+    for sx in (-1, 0, 1):
+        for sy in (-1, 0, 1):
+            dxp = (X - U * t_end - w["centre"][0]) % 1.0 - sx
+            dyp = (Y - V * t_end - w["centre"][1]) % 1.0 - sy
+            prof += np.exp(-(dxp**2 + dyp**2) / (2 * w["sigma"] ** 2))
+    exact = 1 + 0.1 * prof
+    l1 = np.mean(np.abs(r1 - exact)) / np.mean(exact - 1)
+    assert l1 < 0.05, l1
+
+
+def test_uniform_flow_stays_uniform_on_gpu():
+    n = 20
+    cs = math.sqrt(1.4 * 0.7)
+    shp = (n, n)
+    rho, T = np.full(shp, 1.3), np.full(shp, 0.7)
+    ux, uy = np.full(shp, 5 * cs * 0.8), np.full(shp, 5 * cs * 0.6)
+    cfg = W._base(2, n, n, tau=1e-3, dx=1.0 / n, bc=(0, 0, 0, 0))
+    cfg["dt"] = W.dt_from_cfl(ux, uy, T, cfg["dx"], 0.5)
+    sim = pond.Sim(cfg)
+    sim.init(rho, ux, uy, T)
+    sim.step(10)
+    r, a, b, t = sim.moments()
+    sim.close()
+    assert np.max(np.abs(r - 1.3)) < 1e-13 and np.max(np.abs(t - 0.7)) < 1e-13
+    assert np.max(np.abs(a - ux)) < 1e-12
+
+
+def test_nonphysical_state_is_flagged_not_trapped():
+    """A negative initial density is reported through the sticky flag and the
+    status of pond_status_flags; the context stays usable."""
+    n = 16
+    rho = np.ones((n, n))
+    rho[3, 4] = -0.5
+    cfg = W._base(2, n, n, tau=1e-3, dx=1.0 / n, bc=(0, 0, 0, 0))
+    cfg["dt"] = 1e-3
+    sim = pond.Sim(cfg)
+    sim.init(rho, np.zeros((n, n)), np.zeros((n, n)), np.ones((n, n)))
+    sim.step(1)
+    st, flags, _, _ = sim.flags()
+    assert st == pond.POND_E_NONPHYSICAL and flags & pond.POND_FLAG_NONPHYSICAL
+    pond.pond_reset_flags(sim.ctx)
+    sim.init(np.ones((n, n)), np.zeros((n, n)), np.zeros((n, n)), np.ones((n, n)))
+    sim.step(2)
+    assert sim.flags()[0] == pond.POND_OK
+    sim.close()
+
+
+def test_step_before_init_and_bad_count():
+    cfg = W._base(1, 10, 1, tau=1e-3, dx=0.1)
+    cfg["dt"] = 1e-3
+    sim = pond.Sim(cfg)
+    with pytest.raises(pond.PondError) as e:
+        sim.step(1)
+    assert e.value.status == pond.POND_E_STATE
+    sim.init(np.ones(10), np.zeros(10), np.zeros(10), np.ones(10))
+    with pytest.raises(pond.PondError) as e:
+        sim.step(-1)
+    assert e.value.status == pond.POND_E_INVAL
+    sim.close()
+
+
+def test_moments_match_oracle_moments():
+    rho, ux, uy, T = W.random_state_grid(2, 12, 9, seed=3, mach=1.0)
+    cfg = W._base(2, 12, 9, tau=5e-3, dx=1 / 12, bc=(1, 1, 1, 1))
+    cfg["dt"] = W.dt_from_cfl(ux, uy, T, cfg["dx"], 0.3)
+    ocfg = oracle.Config.from_dict(cfg)
+    ost = oracle.run(ocfg, oracle.init(ocfg, rho, ux, uy, T), 2)
+    om = oracle.moments(ocfg, ost)
+    sim = pond.Sim(cfg)
+    sim.init(rho, ux, uy, T)
+    sim.step(2)
+    gm = sim.moments()
+    sim.close()
+    for a, b in zip(gm, om):
+        assert _rel(a, b) <= TOL

@@ -183,6 +183,40 @@ const char *pond_strerror(pond_status s);
 /* POND_ABI_VERSION of the loaded library. */
 int pond_abi_version(void);
 
+/* ---- Step without any device allocation -------------------------------------
+ * No counterpart in the paper: this is a calling convention, not a step of
+ * the method.  It performs the same FP64 steps as pond_step() for callers that
+ * may not call cudaMalloc, for example code that runs while a CUDA graph is
+ * being captured in global mode (cudaMalloc is then prohibited), hosts whose
+ * device memory belongs to a pool allocator that must not be bypassed, or
+ * latency-critical loops that cannot afford cudaMalloc's implicit device
+ * synchronisation.
+ *
+ * The caller passes the state in and gets it back: f, g, ux, uy (2D only; may
+ * be NULL in 1D), T are caller-owned FP64 device arrays in the layouts above,
+ * holding each cell's populations in its co-moving frame; they are overwritten,
+ * in order on `stream`, with the state after n steps.  params: precision must
+ * be POND_FP64, flux_frame POND_FRAME_AVG, dt > 0 (no CFL time step); the tile
+ * is fixed (8x8 in 2D, 252 cells in 1D).  flags: host pointer or NULL; when
+ * given, the call synchronises `stream` and stores the sticky POND_FLAG_* bits
+ * of this call.
+ *
+ * Its only scratch is one static __device__ array of POND_NOALLOC_SCRATCH_BYTES
+ * (a status block plus one state buffer) that every GPU loading this library
+ * holds until the process exits; the call allocates and frees nothing.  The
+ * first call on a device looks up the array's device address and sets the
+ * kernels' shared-memory limits; make that first call before any stream
+ * capture.  All calls on a device share the array: calls whose work overlaps
+ * on the GPU race.
+ *
+ * Errors: POND_E_NOMEM when the state does not fit the array (2D FP64:
+ * 74,897 cells; 1D: 209,712 cells), POND_E_INVAL for bad arguments,
+ * POND_E_NONPHYSICAL (only when flags is given), POND_E_CUDA. */
+#define POND_NOALLOC_SCRATCH_BYTES (16 * 1024 * 1024)
+pond_status pond_step_noalloc(pond_lattice lat, const int64_t dims[2], const pond_params *p,
+                              double *f, double *g, double *ux, double *uy, double *T,
+                              int64_t n, uint32_t *flags, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,176 @@
+// pond_noalloc.cu -- pond_step_noalloc(): the FP64 time step for callers that
+// cannot allocate device memory.
+//
+// pond_step() keeps a second state buffer and a status block in memory that a
+// context allocates (or receives as a workspace).  Some callers may not call
+// cudaMalloc at all.  For them this entry point advances a caller-owned
+// device state in place and uses, as its only scratch, one file-scope
+// __device__ array of POND_NOALLOC_SCRATCH_BYTES that every GPU loading this
+// library holds until the process exits.  It calls no cudaMalloc, cudaFree or
+// allocating library routine.
+//
+// The array is shared by every call on a device and keeps the last call's
+// contents; the status block in it is cleared at the start of each call.
+// Calls whose work overlaps on the GPU (other streams, other host threads)
+// race on the array.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <mutex>
+
+#include "pond.h"
+#include "pond_kernels.cuh"
+
+// the scratch: [status block (256 B)][one FP64 state buffer]
+static __device__ __align__(256) unsigned char g_pond_noalloc_scratch[POND_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mu;
+unsigned char *g_scratch_addr[kMaxDevices] = {};
+
+// Once per device, with that device current: the device address of the array
+// (in host code its name is only a host-side stand-in) and the shared-memory
+// opt-in of the step kernels this entry point launches.
+pond_status scratch_for_current_device(unsigned char **out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    (void)cudaGetLastError();
+    return POND_E_CUDA;
+  }
+  std::lock_guard<std::mutex> lock(g_setup_mu);
+  if (!g_scratch_addr[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_pond_noalloc_scratch) != cudaSuccess || !p) {
+      (void)cudaGetLastError();
+      return POND_E_CUDA;
+    }
+    using T2 = pond::Tile<2, 8, 8>;
+    using T1 = pond::Tile<1, 252, 1>;
+    if (cudaFuncSetAttribute(pond::step_kernel<double, 2, 8, 8, 160>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)T2::smem_bytes<double>()) != cudaSuccess ||
+        cudaFuncSetAttribute(pond::step_kernel<double, 1, 252, 1, 256>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)T1::smem_bytes<double>()) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return POND_E_CUDA;
+    }
+    g_scratch_addr[dev] = static_cast<unsigned char *>(p);
+  }
+  *out = g_scratch_addr[dev];
+  return POND_OK;
+}
+
+bool params_ok(const pond_params *p, int D) {
+  if (!p || !(p->gamma > 1.0) || !(p->tau > 0.0) || !(p->prandtl > 0.0) || !(p->dx > 0.0) ||
+      !(p->dt > 0.0))
+    return false;
+  for (int s = 0; s < 4; ++s)
+    if (p->bc[s] < POND_BC_PERIODIC || p->bc[s] > POND_BC_INFLOW) return false;
+  if ((p->bc[0] == POND_BC_PERIODIC) != (p->bc[1] == POND_BC_PERIODIC)) return false;
+  if (D == 2 && (p->bc[2] == POND_BC_PERIODIC) != (p->bc[3] == POND_BC_PERIODIC)) return false;
+  return p->precision == POND_FP64 && (p->transform == POND_TENSOR || p->transform == POND_GRAD_K) &&
+         (p->flux_form == POND_FLUX_MAIN || p->flux_form == POND_FLUX_APPC) &&
+         (p->limiter == POND_VANLEER || p->limiter == POND_MINMOD) &&
+         p->flux_frame == POND_FRAME_AVG;
+}
+
+// the constants of one step (same definitions as the context path)
+pond::StepConst step_const(const pond_params &p, int D, int64_t nx, int64_t ny) {
+  pond::StepConst K;
+  memset(&K, 0, sizeof(K));
+  K.nx = (int)nx;
+  K.ny = (int)ny;
+  for (int s = 0; s < 4; ++s) {
+    K.bc[s] = p.bc[s];
+    for (int m = 0; m < 4; ++m) K.inflow[s][m] = p.inflow[s][m];
+  }
+  const double dt = p.dt, tau = p.tau, h = 0.5 * dt;
+  K.lam = dt / p.dx;
+  K.kappa1 = 2.0 * tau / (2.0 * tau + h);
+  K.kr = (h / (2.0 * tau + h)) / K.kappa1;
+  K.kp_a = K.kappa1 * (2.0 * tau - h) / (2.0 * tau + dt);
+  K.kp_b = K.kappa1 * 3.0 * h / (2.0 * tau + dt);
+  K.a1 = (2.0 * tau - dt) / (2.0 * tau + dt);
+  K.a2 = 2.0 * dt / (2.0 * tau + dt);
+  K.qe = p.prandtl == 1.0 ? 1.0 : 1.0 + 0.5 * dt * (1.0 / tau - 1.0 / (tau / p.prandtl));
+  const double cv = 1.0 / (p.gamma - 1.0);
+  K.inv_cv = 1.0 / cv;
+  K.gfac = cv - 0.5 * D;
+  K.grad_k = p.transform == POND_GRAD_K;
+  K.appc = p.flux_form == POND_FLUX_APPC;
+  K.limiter = p.limiter;
+  return K;
+}
+
+}  // namespace
+
+extern "C" pond_status pond_step_noalloc(pond_lattice lat, const int64_t dims[2],
+                                         const pond_params *p, double *f, double *g, double *ux,
+                                         double *uy, double *T, int64_t n, uint32_t *flags,
+                                         void *stream) {
+  if ((lat != POND_D1Q4 && lat != POND_D2Q16) || !dims || n < 0) return POND_E_INVAL;
+  const int D = lat == POND_D2Q16 ? 2 : 1;
+  const int64_t nx = dims[0], ny = D == 2 ? dims[1] : 1;
+  if (nx < 2 || (D == 2 && ny < 2) || nx > (1 << 24) || ny > (1 << 24)) return POND_E_INVAL;
+  if (!params_ok(p, D) || !f || !g || !ux || !T || (D == 2 && !uy)) return POND_E_INVAL;
+  const size_t N = (size_t)(nx * ny), qf = D == 2 ? 16 : 4, qg = D == 2 ? 9 : 3;
+  const size_t state_bytes = (qf + qg + 3) * N * sizeof(double);
+  if (256 + state_bytes > (size_t)POND_NOALLOC_SCRATCH_BYTES) return POND_E_NOMEM;
+
+  unsigned char *scratch = nullptr;
+  pond_status s = scratch_for_current_device(&scratch);
+  if (s != POND_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  pond::Stats *stats = reinterpret_cast<pond::Stats *>(scratch);
+  double *buf = reinterpret_cast<double *>(scratch + 256);
+  pond::State<double> caller{f, g, ux, D == 2 ? uy : buf + (qf + qg + 1) * N, T};
+  pond::State<double> other{buf, buf + qf * N, buf + (qf + qg) * N, buf + (qf + qg + 1) * N,
+                            buf + (qf + qg + 2) * N};
+  if (cudaMemsetAsync(stats, 0, sizeof(pond::Stats), st) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return POND_E_CUDA;
+  }
+  const pond::StepConst K = step_const(*p, D, nx, ny);
+  for (int64_t i = 0; i < n; ++i) {
+    const pond::State<double> &in = (i & 1) ? other : caller;
+    const pond::State<double> &out = (i & 1) ? caller : other;
+    if (D == 2) {
+      const dim3 grid((unsigned)((nx + 7) / 8), (unsigned)((ny + 7) / 8));
+      pond::step_kernel<double, 2, 8, 8, 160>
+          <<<grid, 160, pond::Tile<2, 8, 8>::smem_bytes<double>(), st>>>(K, in, out, stats);
+    } else {
+      const dim3 grid((unsigned)((nx + 251) / 252), 1u);
+      pond::step_kernel<double, 1, 252, 1, 256>
+          <<<grid, 256, pond::Tile<1, 252, 1>::smem_bytes<double>(), st>>>(K, in, out, stats);
+    }
+    if (cudaGetLastError() != cudaSuccess) return POND_E_CUDA;
+  }
+  if (n & 1) {
+    // the state after an odd number of steps is in the scratch: copy it back
+    const struct { double *dst; const double *src; size_t cnt; } cp[5] = {
+        {f, other.f, qf * N}, {g, other.g, qg * N}, {ux, other.ux, N},
+        {D == 2 ? uy : nullptr, other.uy, N}, {T, other.T, N}};
+    for (const auto &c : cp) {
+      if (!c.dst) continue;
+      if (cudaMemcpyAsync(c.dst, c.src, c.cnt * sizeof(double), cudaMemcpyDeviceToDevice, st) !=
+          cudaSuccess) {
+        (void)cudaGetLastError();
+        return POND_E_CUDA;
+      }
+    }
+  }
+  if (flags) {
+    pond::Stats h;
+    if (cudaMemcpyAsync(&h, stats, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return POND_E_CUDA;
+    }
+    *flags = h.flags;
+    if (h.flags & POND_FLAG_NONPHYSICAL) return POND_E_NONPHYSICAL;
+  }
+  return POND_OK;
+}

@@ -31,7 +31,9 @@ EXPORTS = (
     "pond_params_default", "pond_workspace_size", "pond_create", "pond_init", "pond_step",
     "pond_moments", "pond_get_state", "pond_set_state", "pond_status_flags", "pond_reset_flags",
     "pond_sync", "pond_info", "pond_destroy", "pond_strerror", "pond_abi_version",
+    "pond_step_noalloc",
 )
+POND_NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 
 
 class pond_params(ctypes.Structure):
@@ -90,6 +92,9 @@ def lib(build: bool = False):
     L.pond_strerror.argtypes = [ctypes.c_int]
     L.pond_strerror.restype = ctypes.c_char_p
     L.pond_abi_version.restype = ctypes.c_int
+    L.pond_step_noalloc.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                    ctypes.POINTER(pond_params), _P, _P, _P, _P, _P,
+                                    ctypes.c_int64, ctypes.POINTER(ctypes.c_uint32), _P]
     for name in EXPORTS:
         if name not in ("pond_params_default", "pond_destroy", "pond_strerror", "pond_abi_version"):
             getattr(L, name).restype = ctypes.c_int
@@ -207,6 +212,20 @@ def pond_info(ctx):
 def pond_destroy(ctx):
     if ctx:
         lib().pond_destroy(ctx)
+
+
+def pond_step_noalloc(lat: int, dims, params: pond_params, f, g, ux, uy, T, n: int,
+                      stream: int | None = None, want_flags: bool = True):
+    """FP64 steps of a caller-owned device state (CUDA tensors), in place, with
+    no device allocation; returns (status, flags) (flags None if not wanted)."""
+    d = (ctypes.c_int64 * 2)(*[int(x) for x in dims])
+    fl = ctypes.c_uint32()
+    st = lib().pond_step_noalloc(int(lat), d, ctypes.byref(params), _ptr(f), _ptr(g), _ptr(ux),
+                                 _ptr(uy), _ptr(T), int(n),
+                                 ctypes.byref(fl) if want_flags else None, stream)
+    if st not in (POND_OK, POND_E_NONPHYSICAL):
+        raise PondError(st, "pond_step_noalloc")
+    return st, (int(fl.value) if want_flags else None)
 
 
 # ---- configuration ------------------------------------------------------------

@@ -343,27 +343,86 @@ static double orc_limit(int limiter, double sl, double sr) {
 /* ------------------------------------------------------------------ */
 /* One face: phi at (x_b, t_{n+1/2}) in the face frame (Sec. IV.A.2).  */
 /* ------------------------------------------------------------------ */
+/* Stencil of a face: cn[n], n = 0..3 along the normal (cells -1, 0 (left),
+ * 1 (right), 2); ct[t][m] transverse neighbours of the left (t = 0) and right
+ * (t = 1) cell, lower (m = 0) and upper (m = 1). */
+typedef struct {
+  int dir, cn[4], ct[2][2];
+} orc_stencil;
+
+/* The stencil's phi_bar^+ moved into the face frame {uF, TF} and the limited
+ * half-step trace x' = x_b - v dt/2 of every population to the face (Eq.
+ * eq:InterfacePop); the upwind cell is the left one when v_n > 0. */
+static void orc_face_trace(const orc_grid *G, const orc_stencil *S, const double uF[2],
+                           double TF, double *fb, double *gb) {
+  const orc_params *p = G->p;
+  const int D = G->D, ncp = orc_ncp(G), dir = S->dir;
+  const double dt = p->dt, dx = p->dx;
+  double tn_f[4][ORC_MAXQ], tn_g[4][ORC_MAXQ], tt_f[2][2][ORC_MAXQ], tt_g[2][2][ORC_MAXQ];
+  for (int n = 0; n < 4; ++n) {
+    int c = S->cn[n];
+    double fin[ORC_MAXQ], gin[ORC_MAXQ], uc[2] = {G->ux[c], G->uy[c]};
+    for (int i = 0; i < G->Qf; ++i) fin[i] = G->fp[i * ncp + c];
+    for (int i = 0; i < G->Qg; ++i) gin[i] = G->gp[i * ncp + c];
+    orc_transform(&G->Lf, D, p->grad_k, fin, uc, G->T[c], uF, TF, tn_f[n]);
+    orc_transform(&G->Lg, D, p->grad_k, gin, uc, G->T[c], uF, TF, tn_g[n]);
+  }
+  if (D == 2)
+    for (int t = 0; t < 2; ++t)
+      for (int m = 0; m < 2; ++m) {
+        int c = S->ct[t][m];
+        double fin[ORC_MAXQ], gin[ORC_MAXQ], uc[2] = {G->ux[c], G->uy[c]};
+        for (int i = 0; i < G->Qf; ++i) fin[i] = G->fp[i * ncp + c];
+        for (int i = 0; i < G->Qg; ++i) gin[i] = G->gp[i * ncp + c];
+        orc_transform(&G->Lf, D, p->grad_k, fin, uc, G->T[c], uF, TF, tt_f[t][m]);
+        orc_transform(&G->Lg, D, p->grad_k, gin, uc, G->T[c], uF, TF, tt_g[t][m]);
+      }
+  for (int pop = 0; pop < 2; ++pop) {
+    const orc_lat1 *L = pop == 0 ? &G->Lf : &G->Lg;
+    double *out = pop == 0 ? fb : gb;
+    for (int i = 0; i < orc_Q(L, D); ++i) {
+      double vx = sqrt(TF) * orc_cx(L, D, i) + uF[0];
+      double vy = sqrt(TF) * orc_cy(L, D, i) + uF[1];
+      double vn = dir == 0 ? vx : vy, vt = dir == 0 ? vy : vx;
+      int t = vn > 0.0 ? 0 : 1; /* upwind: 0 = left/lower, 1 = right/upper */
+      int s = 1 + t;            /* stencil position of the upwind cell */
+      double ps = pop == 0 ? tn_f[s][i] : tn_g[s][i];
+      double pm = pop == 0 ? tn_f[s - 1][i] : tn_g[s - 1][i];
+      double pp = pop == 0 ? tn_f[s + 1][i] : tn_g[s + 1][i];
+      double sig_n = orc_limit(p->limiter, (ps - pm) / dx, (pp - ps) / dx);
+      /* offset of the departure point from the upwind cell centre */
+      double dn = (t == 0 ? 0.5 * dx : -0.5 * dx) - vn * 0.5 * dt;
+      double val = ps + dn * sig_n;
+      if (D == 2) {
+        double qm = pop == 0 ? tt_f[t][0][i] : tt_g[t][0][i];
+        double qp = pop == 0 ? tt_f[t][1][i] : tt_g[t][1][i];
+        double sig_t = orc_limit(p->limiter, (ps - qm) / dx, (qp - ps) / dx);
+        val += (-vt * 0.5 * dt) * sig_t;
+      }
+      out[i] = val;
+    }
+  }
+}
+
 /* dir = 0: x-face between cells (j,k) and (j+1,k); dir = 1: y-face between
  * (j,k) and (j,k+1).  lam is set to the face frame {u_x, u_y, T} actually
  * used; returns 1 if the iterated frame did not converge. */
 static int orc_face(orc_grid *G, int dir, int j, int k, double *phi_f, double *phi_g,
                     double lam[3]) {
   const orc_params *p = G->p;
-  const int D = G->D, ncp = orc_ncp(G);
-  const double dt = p->dt, dx = p->dx, tau = p->tau, h = 0.5 * dt;
-  /* stencil: n = 0..3 along the normal (cells -1, 0(left), 1(right), 2);
-   * transverse neighbours of the left (t = 0) and right (t = 1) cell, lower
-   * (m = 0) and upper (m = 1) */
-  int cn[4], ct[2][2];
+  const int D = G->D;
+  const double dt = p->dt, tau = p->tau, h = 0.5 * dt;
+  orc_stencil S;
+  S.dir = dir;
   for (int n = 0; n < 4; ++n)
-    cn[n] = dir == 0 ? orc_pidx(G, j - 1 + n, k) : orc_pidx(G, j, k - 1 + n);
+    S.cn[n] = dir == 0 ? orc_pidx(G, j - 1 + n, k) : orc_pidx(G, j, k - 1 + n);
   for (int t = 0; t < 2; ++t)
     for (int m = 0; m < 2; ++m) {
-      ct[t][m] = -1;
+      S.ct[t][m] = -1;
       if (D == 2)
-        ct[t][m] = dir == 0 ? orc_pidx(G, j + t, k - 1 + 2 * m) : orc_pidx(G, j - 1 + 2 * m, k + t);
+        S.ct[t][m] = dir == 0 ? orc_pidx(G, j + t, k - 1 + 2 * m) : orc_pidx(G, j - 1 + 2 * m, k + t);
     }
-  const int cL = cn[1], cR = cn[2];
+  const int cL = S.cn[1], cR = S.cn[2];
   /* face frame, Eq. eq::AvgFrame */
   double uF[2] = {0.5 * (G->ux[cL] + G->ux[cR]), 0.5 * (G->uy[cL] + G->uy[cR])};
   double TF = 0.5 * (G->T[cL] + G->T[cR]);
@@ -371,67 +430,34 @@ static int orc_face(orc_grid *G, int dir, int j, int k, double *phi_f, double *p
 
   double fb[ORC_MAXQ], gb[ORC_MAXQ];
   double rho = 0, ub[2] = {0, 0}, Tb = 0;
+  /* iterated face frame (the predictor-corrector of the earlier scheme, Sec.
+   * IV.A.3): the face frame is replaced by the interface state until the two
+   * agree to iter_tol or iter_max traces were made.  An iterate whose
+   * interface state is nonphysical ends the iteration and the face keeps the
+   * previous (physical) iterate. */
   const int nit = p->iterative ? (p->iter_max > 0 ? p->iter_max : 1) : 1;
   int converged = 0;
+  double uP[2] = {uF[0], uF[1]}, TP = TF;
   for (int it = 0; it < nit; ++it) {
-    /* stencil populations phi_bar^+ in the face frame */
-    double tn_f[4][ORC_MAXQ], tn_g[4][ORC_MAXQ], tt_f[2][2][ORC_MAXQ], tt_g[2][2][ORC_MAXQ];
-    for (int n = 0; n < 4; ++n) {
-      int c = cn[n];
-      double fin[ORC_MAXQ], gin[ORC_MAXQ], uc[2] = {G->ux[c], G->uy[c]};
-      for (int i = 0; i < G->Qf; ++i) fin[i] = G->fp[i * ncp + c];
-      for (int i = 0; i < G->Qg; ++i) gin[i] = G->gp[i * ncp + c];
-      orc_transform(&G->Lf, D, p->grad_k, fin, uc, G->T[c], uF, TF, tn_f[n]);
-      orc_transform(&G->Lg, D, p->grad_k, gin, uc, G->T[c], uF, TF, tn_g[n]);
-    }
-    if (D == 2)
-      for (int t = 0; t < 2; ++t)
-        for (int m = 0; m < 2; ++m) {
-          int c = ct[t][m];
-          double fin[ORC_MAXQ], gin[ORC_MAXQ], uc[2] = {G->ux[c], G->uy[c]};
-          for (int i = 0; i < G->Qf; ++i) fin[i] = G->fp[i * ncp + c];
-          for (int i = 0; i < G->Qg; ++i) gin[i] = G->gp[i * ncp + c];
-          orc_transform(&G->Lf, D, p->grad_k, fin, uc, G->T[c], uF, TF, tt_f[t][m]);
-          orc_transform(&G->Lg, D, p->grad_k, gin, uc, G->T[c], uF, TF, tt_g[t][m]);
-        }
-    /* half-step trace x' = x_b - v dt/2 and MUSCL reconstruction (Eq.
-     * eq:InterfacePop); the upwind cell is the left one when v_n > 0. */
-    for (int pop = 0; pop < 2; ++pop) {
-      const orc_lat1 *L = pop == 0 ? &G->Lf : &G->Lg;
-      double *out = pop == 0 ? fb : gb;
-      for (int i = 0; i < orc_Q(L, D); ++i) {
-        double vx = sqrt(TF) * orc_cx(L, D, i) + uF[0];
-        double vy = sqrt(TF) * orc_cy(L, D, i) + uF[1];
-        double vn = dir == 0 ? vx : vy, vt = dir == 0 ? vy : vx;
-        int t = vn > 0.0 ? 0 : 1; /* upwind: 0 = left/lower, 1 = right/upper */
-        int s = 1 + t;            /* stencil position of the upwind cell */
-        double ps = pop == 0 ? tn_f[s][i] : tn_g[s][i];
-        double pm = pop == 0 ? tn_f[s - 1][i] : tn_g[s - 1][i];
-        double pp = pop == 0 ? tn_f[s + 1][i] : tn_g[s + 1][i];
-        double sig_n = orc_limit(p->limiter, (ps - pm) / dx, (pp - ps) / dx);
-        /* offset of the departure point from the upwind cell centre */
-        double dn = (t == 0 ? 0.5 * dx : -0.5 * dx) - vn * 0.5 * dt;
-        double val = ps + dn * sig_n;
-        if (D == 2) {
-          double qm = pop == 0 ? tt_f[t][0][i] : tt_g[t][0][i];
-          double qp = pop == 0 ? tt_f[t][1][i] : tt_g[t][1][i];
-          double sig_t = orc_limit(p->limiter, (ps - qm) / dx, (qp - ps) / dx);
-          val += (-vt * 0.5 * dt) * sig_t;
-        }
-        out[i] = val;
-      }
-    }
+    orc_face_trace(G, &S, uF, TF, fb, gb);
     /* interface macroscopic fields (rho, rho u, C_v rho T) in the face frame */
-    double uFa[2] = {uF[0], uF[1]};
-    int ok = orc_macro(&G->Lf, &G->Lg, D, G->Cv, fb, gb, uFa, TF, &rho, ub, &Tb);
-    if (!ok) break;
+    int ok = orc_macro(&G->Lf, &G->Lg, D, G->Cv, fb, gb, uF, TF, &rho, ub, &Tb);
+    if (!ok) {
+      if (p->iterative && it > 0) {
+        uF[0] = uP[0]; uF[1] = uP[1]; TF = TP;
+        orc_face_trace(G, &S, uF, TF, fb, gb);
+        orc_macro(&G->Lf, &G->Lg, D, G->Cv, fb, gb, uF, TF, &rho, ub, &Tb);
+      }
+      break;
+    }
     if (!p->iterative) break;
-    /* iterated face frame: converged when the face frame is co-moving with
-     * the interface state to iter_tol */
     double du = sqrt((ub[0] - uF[0]) * (ub[0] - uF[0]) + (ub[1] - uF[1]) * (ub[1] - uF[1]));
     double err = fmax(du / sqrt(TF), fabs(Tb - TF) / TF);
     if (err < p->iter_tol) { converged = 1; break; }
-    if (it + 1 < nit) { uF[0] = ub[0]; uF[1] = (D == 2) ? ub[1] : 0.0; TF = Tb; }
+    if (it + 1 < nit) {
+      uP[0] = uF[0]; uP[1] = uF[1]; TP = TF;
+      uF[0] = ub[0]; uF[1] = (D == 2) ? ub[1] : 0.0; TF = Tb;
+    }
   }
   if (p->iterative && !converged) noconv = 1;
 
@@ -603,6 +629,9 @@ static int orc_step_once(orc_grid *G, orc_report *rep) {
       double cfl = vmax * dt / dx;
       if (cfl > maxcfl) maxcfl = cfl;
     }
+  /* an iterated face frame that reached iter_max unconverged is reported as
+   * a sticky flag beside the count of such face evaluations */
+  if (noconv) flags |= ORC_FLAG_NOCONV;
   rep->flags |= flags;
   rep->noconv_faces += noconv;
   if (maxcfl > rep->max_cfl) rep->max_cfl = maxcfl;

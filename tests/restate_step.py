@@ -36,6 +36,7 @@ class Restated:
         self.dt = mp.mpf(cfg["dt"])
         self.dx = mp.mpf(cfg["dx"])
         self.lat = {q: self._lattice(q) for q in (3, 4)}
+        self.noconv_faces = 0  # iterated face frames that did not converge
 
     # Table I, from the node formulas
     def _lattice(self, q):
@@ -183,46 +184,90 @@ class Restated:
             L, R = phiplus(*at(1)), phiplus(*at(2))
             uF = [(L[2][0] + R[2][0]) / 2, (L[2][1] + R[2][1]) / 2]
             TF = (L[3] + R[3]) / 2
-            cache = {}
-
-            def tr(cell):
-                if cell not in cache:
-                    fp, gp, uc, Tc = phiplus(*cell)
-                    cache[cell] = (self.transform(4, fp, uc, Tc, uF, TF), self.transform(3, gp, uc, Tc, uF, TF))
-                return cache[cell]
-
-            out = []
-            for pop, (q, C) in enumerate(((4, C4), (3, C3))):
-                vals = []
-                for i, (cx, cy) in enumerate(C):
-                    vx, vy = mp.sqrt(TF) * cx + uF[0], mp.sqrt(TF) * cy + uF[1]
-                    vn, vt = (vx, vy) if dirn == 0 else (vy, vx)
-                    up = vn > 0
-                    s = 1 if up else 2
-                    ps = tr(at(s))[pop][i]
-                    pm = tr(at(s - 1))[pop][i]
-                    pp = tr(at(s + 1))[pop][i]
-                    sig = limit((ps - pm) / dx, (pp - ps) / dx)
-                    val = ps + ((dx / 2 if up else -dx / 2) - vn * dt / 2) * sig
-                    if D == 2:
-                        # transverse neighbours of the upwind cell
-                        cs = at(s)
-                        lo = (cs[0], cs[1] - 1) if dirn == 0 else (cs[0] - 1, cs[1])
-                        hi = (cs[0], cs[1] + 1) if dirn == 0 else (cs[0] + 1, cs[1])
-                        qm, qp = tr(lo)[pop][i], tr(hi)[pop][i]
-                        val += (-vt * dt / 2) * limit((ps - qm) / dx, (qp - ps) / dx)
-                    vals.append(val)
-                out.append(vals)
-            fb, gb = out
-            rho, ub, Tb = self.macro(fb, gb, uF, TF)
-            feq = self.equilibrium(4, rho, ub, Tb, uF, TF)
-            geq = self.equilibrium(3, gfac(Tb) * rho, ub, Tb, uF, TF)
+            # iterated face frame (earlier predictor-corrector scheme): the face
+            # frame is replaced by the interface state until they agree
+            iterative = int(self.cfg.get("iterative", 0))
+            n_iter = max(1, int(self.cfg.get("iter_max", 10))) if iterative else 1
+            tol = mp.mpf(self.cfg.get("iter_tol", 1e-12))
+            # an iterate with a nonphysical interface state ends the iteration;
+            # the face then keeps the previous iterate
+            converged = False
+            prev = (uF, TF)
+            for it in range(n_iter):
+                fb, gb = self._trace(dirn, at, phiplus, uF, TF, limit, C4, C3)
+                rho, ub, Tb = self.macro(fb, gb, uF, TF)
+                if not (rho > 0 and Tb > 0):
+                    if iterative and it > 0:
+                        uF, TF = prev
+                        fb, gb = self._trace(dirn, at, phiplus, uF, TF, limit, C4, C3)
+                        rho, ub, Tb = self.macro(fb, gb, uF, TF)
+                    break
+                if not iterative:
+                    break
+                du = mp.sqrt((ub[0] - uF[0]) ** 2 + (ub[1] - uF[1]) ** 2)
+                if max(du / mp.sqrt(TF), abs(Tb - TF) / TF) < tol:
+                    converged = True
+                    break
+                if it + 1 < n_iter:
+                    prev = (uF, TF)
+                    uF = [ub[0], ub[1] if D == 2 else mp.mpf(0)]
+                    TF = Tb
+            if iterative and not converged:
+                self.noconv_faces += 1
+            if converged:
+                feq = [rho * w for w in W4]
+                geq = [gfac(Tb) * rho * w for w in W3]
+            else:
+                feq = self.equilibrium(4, rho, ub, Tb, uF, TF)
+                geq = self.equilibrium(3, gfac(Tb) * rho, ub, Tb, uF, TF)
             pf = [(2 * tau * a + h * b) / (2 * tau + h) for a, b in zip(fb, feq)]
             pg = [(2 * tau * a + h * b) / (2 * tau + h) for a, b in zip(gb, geq)]
             return pf, pg, uF, TF
 
         xf = {(j, k): face(0, j, k) for k in range(ny) for j in range(-1, nx)}
         yf = {(j, k): face(1, j, k) for k in range(-1, ny) for j in range(nx)} if D == 2 else {}
+        return self._update(cells, f, g, u, T, xf, yf, W4, W3, C4, C3, gfac)
+
+    def _trace(self, dirn, at, phiplus, uF, TF, limit, C4, C3):
+        """Stencil moved into the face frame {uF, TF} and the limited half-step
+        trace of every population to the face (Eq. eq:InterfacePop)."""
+        mp, D, dt, dx = self.mp, self.D, self.dt, self.dx
+        cache = {}
+
+        def tr(cell):
+            if cell not in cache:
+                fp, gp, uc, Tc = phiplus(*cell)
+                cache[cell] = (self.transform(4, fp, uc, Tc, uF, TF), self.transform(3, gp, uc, Tc, uF, TF))
+            return cache[cell]
+
+        out = []
+        for pop, (q, C) in enumerate(((4, C4), (3, C3))):
+            vals = []
+            for i, (cx, cy) in enumerate(C):
+                vx, vy = mp.sqrt(TF) * cx + uF[0], mp.sqrt(TF) * cy + uF[1]
+                vn, vt = (vx, vy) if dirn == 0 else (vy, vx)
+                up = vn > 0
+                s = 1 if up else 2
+                ps = tr(at(s))[pop][i]
+                pm = tr(at(s - 1))[pop][i]
+                pp = tr(at(s + 1))[pop][i]
+                sig = limit((ps - pm) / dx, (pp - ps) / dx)
+                val = ps + ((dx / 2 if up else -dx / 2) - vn * dt / 2) * sig
+                if D == 2:
+                    # transverse neighbours of the upwind cell
+                    cs = at(s)
+                    lo = (cs[0], cs[1] - 1) if dirn == 0 else (cs[0] - 1, cs[1])
+                    hi = (cs[0], cs[1] + 1) if dirn == 0 else (cs[0] + 1, cs[1])
+                    qm, qp = tr(lo)[pop][i], tr(hi)[pop][i]
+                    val += (-vt * dt / 2) * limit((ps - qm) / dx, (qp - ps) / dx)
+                vals.append(val)
+            out.append(vals)
+        return out[0], out[1]
+
+    def _update(self, cells, f, g, u, T, xf, yf, W4, W3, C4, C3, gfac):
+        """Fluxes moved into each cell frame, DUGKS update, re-gauge, QE half."""
+        mp, D = self.mp, self.D
+        tau, dt, dx = self.tau, self.dt, self.dx
         a1 = (2 * tau - dt) / (2 * tau + dt)
         a2 = 2 * dt / (2 * tau + dt)
         new = {"f": {}, "g": {}, "u": {}, "T": {}}

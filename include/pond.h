@@ -74,8 +74,11 @@ typedef enum {
  * Sec. IV.D: periodic wrap, zero normal gradient (copy of the boundary cell),
  * or a fixed inflow state (its co-moving equilibrium). */
 enum { POND_BC_PERIODIC = 0, POND_BC_ZERO_GRADIENT = 1, POND_BC_INFLOW = 2 };
-/* arithmetic of the step: all FP64, or FP32 populations/transforms with FP64
- * per-cell moments and frame */
+/* arithmetic of the step: all FP64, or the mixed path: FP32 populations,
+ * frame (stored as FP32), transformations, reconstruction and collision, with
+ * each cell's conserved moments (rho, rho u, rho E) accumulated in FP64, the
+ * new frame computed in FP64, and frame transformations whose shifted nodes
+ * exceed xi_fp64_threshold built and applied in FP64 */
 enum { POND_FP64 = 0, POND_FP32_MIXED = 1 };
 /* frame transformation: tensor product of 1D transformations (all Hermite
  * coefficients a, b <= K per axis) or the paper's Grad projection of total
@@ -87,7 +90,12 @@ enum { POND_FLUX_MAIN = 0, POND_FLUX_APPC = 1 };
 /* slope limiter of the MUSCL reconstruction (Sec. IV.A.2) */
 enum { POND_VANLEER = 0, POND_MINMOD = 1 };
 /* face frame: average of the adjacent cell frames (Eq. eq::AvgFrame) or the
- * iterated co-moving face frame of the earlier scheme (Sec. IV.A.3) */
+ * iterated co-moving face frame of the earlier scheme (Sec. IV.A.3): the face
+ * frame is replaced by the interface state until they agree to iter_tol
+ * (tested in FP64) or iter_max traces were made; a converged face uses the
+ * co-moving equilibrium rho W.  An iterate with a nonphysical interface state
+ * ends the iteration and the face keeps the previous iterate.  Unconverged
+ * faces set POND_FLAG_NOCONV and are counted (pond_status_flags). */
 enum { POND_FRAME_AVG = 0, POND_FRAME_ITER = 1 };
 /* sticky device flags */
 enum { POND_FLAG_NONPHYSICAL = 1u, POND_FLAG_CFL = 2u, POND_FLAG_NOCONV = 4u };
@@ -111,7 +119,12 @@ typedef struct {
   double xi_fp64_threshold;/* mixed path: build the frame transformation in FP64
                               when the shift |(u_s-u_F)/sqrt(T_F)| or the scale
                               sqrt(T_s/T_F) exceeds this                          */
-  int32_t tile;            /* 0: automatic; otherwise a tile code (pond_tiles)   */
+  int32_t tile;            /* cells per CTA of the step kernel: 0 automatic
+                              (1D: 1, 2D: 6); 1D: 1 = 252 cells; 2D (x by y):
+                              2 = 8x8, 3 = 16x16, 4 = 16x8, 5 = 8x8 and 6 = 8x16
+                              with registers capped for two CTAs per SM.  The
+                              iterated face frame runs 8x8 (2D) / 252 (1D).
+                              Results do not depend on the tile.               */
 } pond_params;
 
 /* Fills the defaults: gamma 1.4, tau 1e-4, Pr 1, dx 1, dt 0 (from cfl 0.2),
@@ -199,7 +212,8 @@ int pond_abi_version(void);
  * be POND_FP64, flux_frame POND_FRAME_AVG, dt > 0 (no CFL time step); the tile
  * is fixed (8x8 in 2D, 252 cells in 1D).  flags: host pointer or NULL; when
  * given, the call synchronises `stream` and stores the sticky POND_FLAG_* bits
- * of this call.
+ * of this call.  While the call's work runs the arrays hold intermediate
+ * values; after a POND_E_CUDA failure their contents are undefined.
  *
  * Its only scratch is one static __device__ array of POND_NOALLOC_SCRATCH_BYTES
  * (a status block plus one state buffer) that every GPU loading this library

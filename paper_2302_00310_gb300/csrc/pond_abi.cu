@@ -5,8 +5,10 @@
 // A state buffer holds, in the arithmetic type R of the context (double for
 // POND_FP64, float for POND_FP32_MIXED), SoA arrays
 //   f[Qf][N], g[Qg][N], ux[N], uy[N], T[N]          (N = nx*ny cells)
-// Steps ping-pong between the two buffers; between steps the idle buffer is
-// used as staging for FP64 fields at the boundary.
+// where f and g are the Hermite coefficients of each cell's populations in
+// its frame (ux, uy, T).  The boundary exchanges populations: they are
+// converted (in FP64) on the way in and out.  Steps ping-pong between the two
+// buffers; between steps the idle buffer is used as staging at the boundary.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -75,50 +77,68 @@ template <typename R> State<R> state_of(const pond_ctx *c, int b) {
 // ---------------------------------------------------------------------------
 // small kernels: initial equilibrium, moments, conversions, max |v|
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double w4(int k) { return (k == 1 || k == 2) ? pond::W1 : pond::W2; }
-__device__ __forceinline__ double w3(int k) { return k == 1 ? 2.0 / 3.0 : 1.0 / 6.0; }
-
+// co-moving equilibria rho W (Eq. feqPond) and (C_v - D/2) T rho W
+// (Eq. geqPond): their only nonzero Hermite coefficient is the zeroth
 template <typename R, int DIM>
 __global__ void init_kernel(const double *rho, const double *ux, const double *uy, const double *T,
                             State<R> S, size_t N, double gfac) {
   const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= N) return;
   const double r = rho[c], t = T[c];
-  // co-moving equilibria rho W (Eq. feqPond) and (C_v - D/2) T rho W (Eq. geqPond)
-  for (int i = 0; i < (DIM == 2 ? 16 : 4); ++i) {
-    const double W = DIM == 2 ? w4(i % 4) * w4(i / 4) : w4(i);
-    S.f[i * N + c] = R(r * W);
-  }
-  for (int i = 0; i < (DIM == 2 ? 9 : 3); ++i) {
-    const double W = DIM == 2 ? w3(i % 3) * w3(i / 3) : w3(i);
-    S.g[i * N + c] = R(gfac * t * r * W);
-  }
+  for (int i = 0; i < (DIM == 2 ? 16 : 4); ++i) S.f[i * N + c] = R(i == 0 ? r : 0.0);
+  for (int i = 0; i < (DIM == 2 ? 9 : 3); ++i) S.g[i * N + c] = R(i == 0 ? gfac * t * r : 0.0);
   S.ux[c] = R(ux[c]);
   S.uy[c] = DIM == 2 ? R(uy[c]) : R(0);
   S.T[c] = R(t);
 }
 
-// rho, u, T of each cell from its populations (Eqs. eq::ConservationLaws, eq:E)
+// rho, u, T of each cell from its Hermite coefficients (Eqs.
+// eq::ConservationLaws, eq:E), in FP64
 template <typename R, int DIM>
 __global__ void moments_kernel(State<R> S, size_t N, double inv_cv, double *rho, double *ux,
                                double *uy, double *T) {
   const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= N) return;
-  using D = pond::Dims<DIM>;
-  pond::Blk<double, 4, D::NYF> F;
-  pond::Blk<double, 3, D::NYG> G;
-  for (int i = 0; i < D::QF; ++i) F.v[i % 4][i / 4] = (double)S.f[i * N + c];
-  for (int i = 0; i < D::QG; ++i) G.v[i % 3][i / 3] = (double)S.g[i * N + c];
-  pond::ana_x(F); pond::ana_y(F); pond::ana_x(G); pond::ana_y(G);
   const double fx = S.ux[c], fy = DIM == 2 ? (double)S.uy[c] : 0.0, fT = S.T[c], sT = sqrt(fT);
-  const double r = F.v[0][0], mx = F.v[1][0] / r;
-  double my = 0.0, S2 = F.v[2][0] + DIM * r;
-  if constexpr (DIM == 2) { my = F.v[0][1] / r; S2 += F.v[0][2]; }
-  const double e = 0.5 * fT * (S2 - r * (mx * mx + my * my)) + G.v[0][0];
+  const double r = S.f[c], mx = (double)S.f[1 * N + c] / r;
+  double my = 0.0, S2 = (double)S.f[2 * N + c] + DIM * r;
+  if constexpr (DIM == 2) { my = (double)S.f[4 * N + c] / r; S2 += (double)S.f[8 * N + c]; }
+  const double e = 0.5 * fT * (S2 - r * (mx * mx + my * my)) + (double)S.g[c];
   rho[c] = r;
   ux[c] = fx + sT * mx;
   if (uy) uy[c] = fy + sT * my;
   T[c] = e / r * inv_cv;
+}
+
+// populations (FP64 planes p[i][ld], cells 0..n-1) <-> state coefficients
+// (cells c0..c0+n-1); in place when the planes are the state's own (FP64)
+template <typename R, int DIM>
+__global__ void pops_to_coef_kernel(const double *pf, const double *pg, size_t ld, State<R> S,
+                                    size_t N, size_t c0, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  using D = pond::Dims<DIM>;
+  pond::Blk<double, 4, D::NYF> F;
+  pond::Blk<double, 3, D::NYG> G;
+  for (int q = 0; q < D::QF; ++q) F.v[q % 4][q / 4] = pf[q * ld + i];
+  for (int q = 0; q < D::QG; ++q) G.v[q % 3][q / 3] = pg[q * ld + i];
+  pond::ana_x(F); pond::ana_y(F); pond::ana_x(G); pond::ana_y(G);
+  for (int q = 0; q < D::QF; ++q) S.f[q * N + c0 + i] = R(F.v[q % 4][q / 4]);
+  for (int q = 0; q < D::QG; ++q) S.g[q * N + c0 + i] = R(G.v[q % 3][q / 3]);
+}
+template <typename R, int DIM>
+__global__ void coef_to_pops_kernel(State<R> S, size_t N, size_t c0, size_t n, double *pf,
+                                    double *pg, size_t ld) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  using D = pond::Dims<DIM>;
+  pond::Blk<double, 4, D::NYF> F;
+  pond::Blk<double, 3, D::NYG> G;
+  for (int q = 0; q < D::QF; ++q) F.v[q % 4][q / 4] = (double)S.f[q * N + c0 + i];
+  for (int q = 0; q < D::QG; ++q) G.v[q % 3][q / 3] = (double)S.g[q * N + c0 + i];
+  pond::syn_x(F); pond::syn_y(F); pond::syn_x(G); pond::syn_y(G);
+  for (int q = 0; q < D::QF; ++q) pf[q * ld + i] = F.v[q % 4][q / 4];
+  for (int q = 0; q < D::QG; ++q) pg[q * ld + i] = G.v[q % 3][q / 3];
 }
 
 template <typename A, typename B>
@@ -142,7 +162,7 @@ unsigned grid1(size_t n, unsigned b) { return (unsigned)((n + b - 1) / b); }
 // ---------------------------------------------------------------------------
 // step launches
 // ---------------------------------------------------------------------------
-template <typename R, int DIM, int BX, int BY, int NT>
+template <typename R, int DIM, int BX, int BY, int NT, int MINB = 1, bool ITER = false>
 pond_status launch_tile(pond_ctx *c, int from, bool prepare_only) {
   static_assert(NT % 32 == 0, "whole warps");
   using TL = pond::Tile<DIM, BX, BY>;
@@ -150,24 +170,32 @@ pond_status launch_tile(pond_ctx *c, int from, bool prepare_only) {
   static_assert(smem <= 227 * 1024, "tile too large for shared memory");
   if (prepare_only) {
     // the dynamic shared-memory opt-in is set outside any stream capture
-    POND_CUDA(cudaFuncSetAttribute(pond::step_kernel<R, DIM, BX, BY, NT>,
+    POND_CUDA(cudaFuncSetAttribute(pond::step_kernel<R, DIM, BX, BY, NT, MINB, ITER>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     return POND_OK;
   }
   const dim3 grid((unsigned)((c->nx + BX - 1) / BX), DIM == 2 ? (unsigned)((c->ny + BY - 1) / BY) : 1u);
-  pond::step_kernel<R, DIM, BX, BY, NT><<<grid, NT, smem, c->stream>>>(
+  pond::step_kernel<R, DIM, BX, BY, NT, MINB, ITER><<<grid, NT, smem, c->stream>>>(
       c->K, state_of<R>(c, from), state_of<R>(c, 1 - from), c->stats);
   POND_CUDA(cudaGetLastError());
   return POND_OK;
 }
 
-// tile codes: 1 = 1D 252 cells; 2 = 2D 8x8; 3 = 2D 16x16; 4 = 2D 16x8
+// tile codes: 1 = 1D 252 cells; 2D: 2 = 8x8, 3 = 16x16, 4 = 16x8, 5 = 8x8 with two
+// CTAs per SM (register cap 204), 6 = 8x16 with two CTAs per SM
 template <typename R>
 pond_status launch_step(pond_ctx *c, int from, bool prepare_only) {
+  // the iterated face frame runs with one tile shape of its own
+  if (c->K.iterative) {
+    if (c->D == 1) return launch_tile<R, 1, 252, 1, 256, 1, true>(c, from, prepare_only);
+    return launch_tile<R, 2, 8, 8, 160, 1, true>(c, from, prepare_only);
+  }
   if (c->D == 1) return launch_tile<R, 1, 252, 1, 256>(c, from, prepare_only);
   switch (c->tile) {
     case 3: return launch_tile<R, 2, 16, 16, 256>(c, from, prepare_only);
     case 4: return launch_tile<R, 2, 16, 8, 256>(c, from, prepare_only);
+    case 5: return launch_tile<R, 2, 8, 8, 160, 2>(c, from, prepare_only);
+    case 6: return launch_tile<R, 2, 8, 16, 160, 2>(c, from, prepare_only);
     default: return launch_tile<R, 2, 8, 8, 160>(c, from, prepare_only);
   }
 }
@@ -182,11 +210,9 @@ pond_status step_once(pond_ctx *c) {
   return s;
 }
 
-int auto_tile(const pond_ctx *c) {
-  if (c->D == 1) return 1;
-  const int64_t tiles16 = ((c->nx + 15) / 16) * ((c->ny + 15) / 16);
-  return tiles16 >= 8 * 152 ? 3 : 2;
-}
+// 8x16 tiles with two CTAs' worth of registers per SM were fastest for both
+// precisions on 256^2 and 1024^2 grids (tile sweep on GB300)
+int auto_tile(const pond_ctx *c) { return c->D == 1 ? 1 : 6; }
 
 bool valid_params(const pond_params *p) {
   if (!p) return false;
@@ -200,8 +226,10 @@ bool valid_params(const pond_params *p) {
   if (p->transform != POND_TENSOR && p->transform != POND_GRAD_K) return false;
   if (p->flux_form != POND_FLUX_MAIN && p->flux_form != POND_FLUX_APPC) return false;
   if (p->limiter != POND_VANLEER && p->limiter != POND_MINMOD) return false;
-  if (p->flux_frame != POND_FRAME_AVG) return false;  // iterated frame: not in this build
-  if (p->tile < 0 || p->tile > 4) return false;
+  if (p->flux_frame != POND_FRAME_AVG && p->flux_frame != POND_FRAME_ITER) return false;
+  if (p->flux_frame == POND_FRAME_ITER && (!(p->iter_tol > 0.0) || p->iter_max < 1)) return false;
+  if (!(p->xi_fp64_threshold > 0.0)) return false;
+  if (p->tile < 0 || p->tile > 6) return false;
   return true;
 }
 
@@ -236,6 +264,7 @@ void set_step_const(pond_ctx *c) {
   K.appc = p.flux_form == POND_FLUX_APPC;
   K.limiter = p.limiter;
   K.iterative = p.flux_frame == POND_FRAME_ITER;
+  K.xi_thr = (float)p.xi_fp64_threshold;
 }
 
 void drop_graphs(pond_ctx *c) {
@@ -269,6 +298,24 @@ pond_status to_device(pond_ctx *c, const T *src, T *dst, size_t n, int on_device
   POND_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(T), on_device ? cudaMemcpyDeviceToDevice
                                                                  : cudaMemcpyHostToDevice,
                             c->stream));
+  return POND_OK;
+}
+
+// converts cells [c0, c0 + n) between populations p[i][ld] and the state
+template <typename R>
+pond_status convert_pops(pond_ctx *c, double *pf, double *pg, size_t ld, size_t c0, size_t n,
+                                bool to_state) {
+  const size_t N = (size_t)c->N;
+  const unsigned nb = grid1(n, 256);
+  const State<R> S = state_of<R>(c, c->cur);
+  if (to_state) {
+    if (c->D == 2) pops_to_coef_kernel<R, 2><<<nb, 256, 0, c->stream>>>(pf, pg, ld, S, N, c0, n);
+    else pops_to_coef_kernel<R, 1><<<nb, 256, 0, c->stream>>>(pf, pg, ld, S, N, c0, n);
+  } else {
+    if (c->D == 2) coef_to_pops_kernel<R, 2><<<nb, 256, 0, c->stream>>>(S, N, c0, n, pf, pg, ld);
+    else coef_to_pops_kernel<R, 1><<<nb, 256, 0, c->stream>>>(S, N, c0, n, pf, pg, ld);
+  }
+  POND_CUDA(cudaGetLastError());
   return POND_OK;
 }
 
@@ -337,7 +384,6 @@ pond_status pond_create(pond_ctx **out, pond_lattice lat, const int64_t dims[2],
   pond_status s = pond_workspace_size(lat, dims, p, &need);
   if (s != POND_OK) return s;
   if (!valid_params(p)) return POND_E_INVAL;
-  if (p->precision == POND_FP32_MIXED) return POND_E_INVAL;  // mixed path: not in this build
   const int D = lat == POND_D2Q16 ? 2 : 1;
   if (D == 1 && p->tile > 1) return POND_E_INVAL;
   if (D == 2 && p->tile == 1) return POND_E_INVAL;
@@ -351,7 +397,7 @@ pond_status pond_create(pond_ctx **out, pond_lattice lat, const int64_t dims[2],
   c->ny = D == 2 ? dims[1] : 1;
   c->N = c->nx * c->ny;
   c->p = *p;
-  c->fp32 = false;
+  c->fp32 = p->precision == POND_FP32_MIXED;
   c->stream = (cudaStream_t)stream;
   if (workspace) {
     c->ws = (unsigned char *)workspace;
@@ -370,7 +416,7 @@ pond_status pond_create(pond_ctx **out, pond_lattice lat, const int64_t dims[2],
   c->buf[0] = c->ws + align_up(sizeof(Stats));
   c->buf[1] = c->buf[0] + c->buf_bytes;
   c->cur = 0;
-  c->tile = p->tile ? p->tile : auto_tile(c);
+  c->tile = p->flux_frame == POND_FRAME_ITER ? (D == 1 ? 1 : 2) : (p->tile ? p->tile : auto_tile(c));
   c->graph_chunk = 8;
   if (cudaMemsetAsync(c->stats, 0, sizeof(Stats), c->stream) != cudaSuccess) {
     (void)cudaGetLastError();
@@ -521,16 +567,47 @@ static pond_status xfer(pond_ctx *c, double *ext, size_t comp_off, size_t n, boo
   return POND_OK;
 }
 
+// populations in or out: device arrays are converted directly; host arrays go
+// through the idle state buffer in chunks of cells
+static pond_status pops_io(pond_ctx *c, double *f, double *g, bool to_state, int on_device) {
+  const size_t N = (size_t)c->N, qf = qf_of(c->D), qg = qg_of(c->D);
+  auto conv = [&](double *pf, double *pg, size_t ld, size_t c0, size_t n) {
+    return c->fp32 ? convert_pops<float>(c, pf, pg, ld, c0, n, to_state)
+                   : convert_pops<double>(c, pf, pg, ld, c0, n, to_state);
+  };
+  if (on_device) return conv(f, g, N, 0, N);
+  double *stage = reinterpret_cast<double *>(c->buf[1 - c->cur]);
+  size_t chunk = c->buf_bytes / ((qf + qg) * sizeof(double));
+  if (chunk > N) chunk = N;
+  pond_status s;
+  for (size_t c0 = 0; c0 < N; c0 += chunk) {
+    const size_t n = chunk < N - c0 ? chunk : N - c0;
+    double *sf = stage, *sg = stage + qf * n;
+    if (to_state) {
+      for (size_t q = 0; q < qf; ++q)
+        POND_CUDA(cudaMemcpyAsync(sf + q * n, f + q * N + c0, n * 8, cudaMemcpyHostToDevice, c->stream));
+      for (size_t q = 0; q < qg; ++q)
+        POND_CUDA(cudaMemcpyAsync(sg + q * n, g + q * N + c0, n * 8, cudaMemcpyHostToDevice, c->stream));
+      if ((s = conv(sf, sg, n, c0, n)) != POND_OK) return s;
+    } else {
+      if ((s = conv(sf, sg, n, c0, n)) != POND_OK) return s;
+      for (size_t q = 0; q < qf; ++q)
+        POND_CUDA(cudaMemcpyAsync(f + q * N + c0, sf + q * n, n * 8, cudaMemcpyDeviceToHost, c->stream));
+      for (size_t q = 0; q < qg; ++q)
+        POND_CUDA(cudaMemcpyAsync(g + q * N + c0, sg + q * n, n * 8, cudaMemcpyDeviceToHost, c->stream));
+    }
+  }
+  return POND_OK;
+}
+
 static pond_status state_io(pond_ctx *c, double *f, double *g, double *ux, double *uy, double *T,
                             bool to_state, int on_device) {
   if (!c || !f || !g || !ux || !T || (c->D == 2 && !uy)) return POND_E_INVAL;
   const size_t N = (size_t)c->N, qf = qf_of(c->D), qg = qg_of(c->D);
   pond_status s;
-  // one population plane at a time: an FP64 plane always fits the staging buffer
-  for (size_t i = 0; i < qf; ++i)
-    if ((s = xfer(c, f + i * N, i * N, N, to_state, on_device)) != POND_OK) return s;
-  for (size_t i = 0; i < qg; ++i)
-    if ((s = xfer(c, g + i * N, (qf + i) * N, N, to_state, on_device)) != POND_OK) return s;
+  if ((s = pops_io(c, f, g, to_state, on_device)) != POND_OK) return s;
+  // the staging buffer is reused by the frame planes
+  POND_CUDA(cudaStreamSynchronize(c->stream));
   if ((s = xfer(c, ux, (qf + qg) * N, N, to_state, on_device)) != POND_OK) return s;
   if (c->D == 2 && (s = xfer(c, uy, (qf + qg + 1) * N, N, to_state, on_device)) != POND_OK) return s;
   if ((s = xfer(c, T, (qf + qg + 2) * N, N, to_state, on_device)) != POND_OK) return s;

@@ -4,9 +4,8 @@
 // arXiv:2302.00310 (with the Strang-split quasi-equilibrium step of Sec. IV.B).
 // A CTA owns a BX x BY tile of cells and runs three phases separated by block
 // barriers:
-//   A. every cell of the halo-2 tile: load phi~ (SoA, coalesced), Hermite
-//      analysis in the cell frame, first QE half step, phi_bar^+ of
-//      Eq. eq:Fbarplus -> shared memory;
+//   A. every cell of the halo-2 tile: load phi~ (SoA, coalesced), first QE
+//      half step, phi_bar^+ of Eq. eq:Fbarplus -> shared memory;
 //   B. every face touching the tile: averaged face frame (Eq. eq::AvgFrame),
 //      the 8 (2D) / 4 (1D) stencil cells moved into it by the Hermite shift
 //      (Sec. II.B), limited MUSCL half-step trace (Eq. eq:InterfacePop),
@@ -14,11 +13,18 @@
 //      closed form, face phi (inverse of Eq. eq:FluxTransf) -> shared memory;
 //   C. every cell of the tile: face phi moved into the cell frame and
 //      multiplied by v.n (Eq. fluxEq), DUGKS update (Eq. eq:FinalUpdateDUGKS),
-//      new co-moving frame, second QE half step, synthesis, store.
-// All linear algebra is done on Hermite coefficients (pond_hermite.cuh);
-// populations are synthesised only where the limiter needs them.
+//      new co-moving frame, second QE half step, store.
+// All linear algebra is done on Hermite coefficients (pond_hermite.cuh), and
+// the state itself is stored as each cell's Hermite coefficients
+// A_ab = sum_i phi_i He_a(c_ix) He_b(c_iy) (an invertible change of basis on
+// the lattice, Eq. GradsProjection): a step needs no synthesis or analysis of
+// its own cells, and the conserved moments are stored values (rho = A_00).
+// Populations are synthesised only where the limiter needs them (the stencil
+// in the face frame) and at the library boundary.
 #pragma once
 #include <cstdint>
+#include <type_traits>
+
 #include "pond_hermite.cuh"
 
 namespace pond {
@@ -44,8 +50,11 @@ struct StepConst {
   double iter_tol;
   int iter_max;
   int grad_k, appc, limiter, iterative;
+  float xi_thr;         // mixed path: FP64 frame transformation when max_j |a c_j + b| exceeds this
 };
 
+// State planes (SoA, x fastest): f[a + 4b][N] and g[a + 3b][N] are the
+// Hermite coefficients A_ab of phi~ (g: B_ab) in the cell's frame (ux, uy, T).
 template <typename R> struct State {
   R *f, *g, *ux, *uy, *T;
 };
@@ -65,9 +74,13 @@ template <int DIM> struct Dims {
   // shared-memory record of a halo cell: f coeffs, g coeffs, ux, uy, T, sqrt T
   static constexpr int IUX = QF + QG, IUY = IUX + 1, IT = IUX + 2, IST = IUX + 3;
   static constexpr int NPREP = QF + QG + 4;
-  // shared-memory record of a face: f coeffs, g coeffs, uFx, uFy, sqrt TF
-  static constexpr int FUX = QF + QG, FUY = FUX + 1, FST = FUX + 2;
-  static constexpr int NFACE = QF + QG + 3;
+  // shared-memory record of a face: f coeffs, g coeffs, uFx, uFy, sqrt TF, TF,
+  // and (mixed path) the conserved fluxes: mass, x-, y-momentum, energy
+  static constexpr int FUX = QF + QG, FUY = FUX + 1, FST = FUX + 2, FT = FUX + 3;
+  static constexpr int FJ = FUX + 4;
+  template <typename R> static constexpr int nface() {
+    return std::is_same<R, float>::value ? QF + QG + 8 : QF + QG + 4;
+  }
 };
 
 template <int DIM, int BX, int BY> struct Tile {
@@ -78,7 +91,7 @@ template <int DIM, int BX, int BY> struct Tile {
   static constexpr int NFACES = NFX + NFY;
   static constexpr int NCELL = BX * (DIM == 2 ? BY : 1);
   template <typename R> static constexpr size_t smem_bytes() {
-    return sizeof(R) * ((size_t)NH * Dims<DIM>::NPREP + (size_t)NFACES * Dims<DIM>::NFACE);
+    return sizeof(R) * ((size_t)NH * Dims<DIM>::NPREP + (size_t)NFACES * Dims<DIM>::template nface<R>());
   }
 };
 
@@ -122,11 +135,70 @@ template <typename R> __device__ __forceinline__ R qnan();
 template <> __device__ __forceinline__ double qnan<double>() { return __longlong_as_double(0x7ff8000000000000LL); }
 template <> __device__ __forceinline__ float qnan<float>() { return __int_as_float(0x7fc00000); }
 
+// x / y to about 1 ulp: the hardware reciprocal approximation
+// (rcp.approx.ftz.f64) refined by one Newton step, then one residual
+// correction of the quotient (each step squares the relative error).
+__device__ __forceinline__ double div_nr(double x, double y) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(y));
+  r = fma(r, fma(-y, r, 1.0), r);
+  const double q = x * r;
+  return fma(fma(-y, q, x), r, q);
+}
+__device__ __forceinline__ float div_nr(float x, float y) { return __fdividef(x, y); }
+
+// sign tests on the integer image (no FP64-pipe compare): v > 0 and
+// |x| < |y|.  Positive subnormals below 2^-1022 count as zero.
+__device__ __forceinline__ bool pos(double v) { return __double2hiint(v) > 0; }
+__device__ __forceinline__ bool pos(float v) { return __float_as_int(v) > 0; }
+__device__ __forceinline__ bool abs_less(double x, double y) {
+  return (__double_as_longlong(x) & 0x7fffffffffffffffLL) < (__double_as_longlong(y) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ bool abs_less(float x, float y) {
+  return (__float_as_int(x) & 0x7fffffff) < (__float_as_int(y) & 0x7fffffff);
+}
+
 template <typename R>
 __device__ __forceinline__ R limit(R x, R y, int lim) {
   const R p = x * y;
-  if (lim == LIM_MINMOD) return p > R(0) ? (fabs(x) < fabs(y) ? x : y) : R(0);
-  return p > R(0) ? (p + p) / (x + y) : R(0);  // Van Leer: 2xy/(x+y)
+  if (lim == LIM_MINMOD) return pos(p) ? (abs_less(x, y) ? x : y) : R(0);
+  return pos(p) ? div_nr(p + p, x + y) : R(0);  // Van Leer: 2xy/(x+y)
+}
+
+// The FP32 instantiation is the mixed-precision path (POND_FP32_MIXED).
+template <typename R> constexpr bool is_mixed() { return std::is_same<R, float>::value; }
+
+// Moves Hermite coefficients Y (Q nodes per axis) from the frame {us, Ts} to
+// {ut, Tt} (Sec. II.B): per axis the Hermite shift C(a, b) with
+// a = sqrt(Ts/Tt), b = (us - ut)/sqrt(Tt); sTs = sqrt(Ts) and
+// isTt = 1/sqrt(Tt) are given.  On the mixed path a transformation whose
+// nodes land far out (max_j |a c_j + b| > xi_thr: large, cancelling shift
+// coefficients, as at large temperature ratios) is built and applied in FP64.
+template <typename R, int DIM, int Q>
+__device__ __forceinline__ void move_frame(const StepConst &K, R usx, R usy, R Ts, R sTs, R utx,
+                                           R uty, R Tt, R isTt, Blk<R, Q, (DIM == 2 ? Q : 1)> &Y) {
+  constexpr int NY = DIM == 2 ? Q : 1;
+  const R a = sTs * isTt, bx = (usx - utx) * isTt;
+  const R by = DIM == 2 ? (usy - uty) * isTt : R(0);
+  if constexpr (is_mixed<R>()) {
+    if (a * R(Nodes<Q>::cmax) + fmaxf(fabsf(bx), fabsf(by)) > K.xi_thr) {
+      Blk<double, Q, NY> Z;
+#pragma unroll
+      for (int n = 0; n < Q; ++n)
+#pragma unroll
+        for (int m = 0; m < NY; ++m) Z.v[n][m] = Y.v[n][m];
+      const double isT = 1.0 / sqrt((double)Tt), a64 = sqrt((double)Ts) * isT;
+      shift_x(make_shift(a64, ((double)usx - (double)utx) * isT), Z);
+      if constexpr (DIM == 2) shift_y(make_shift(a64, ((double)usy - (double)uty) * isT), Z);
+#pragma unroll
+      for (int n = 0; n < Q; ++n)
+#pragma unroll
+        for (int m = 0; m < NY; ++m) Y.v[n][m] = (R)Z.v[n][m];
+      return;
+    }
+  }
+  shift_x(make_shift(a, bx), Y);
+  if constexpr (DIM == 2) shift_y(make_shift(a, by), Y);
 }
 
 // ---- phase A: one halo cell -> shared memory ------------------------------
@@ -149,7 +221,6 @@ __device__ __forceinline__ void prep_cell(const StepConst &K, const State<R> &S,
     ux = S.ux[c];
     uy = DIM == 2 ? S.uy[c] : R(0);
     T = S.T[c];
-    ana_x(F); ana_y(F); ana_x(G); ana_y(G);
     qe_scale(F, G, R(K.qe));
     const R rho = F.v[0][0], ka = R(K.kp_a);
 #pragma unroll
@@ -198,7 +269,7 @@ __device__ __forceinline__ void prep_cell(const StepConst &K, const State<R> &S,
 // synthesised into populations Y[x-node][y-node].
 template <typename R, int DIM, int Q>
 __device__ __forceinline__ void stencil_pops(const StepConst &K, const R *sp, int NH, int h, R uFx,
-                                             R uFy, R isTF, Blk<R, Q, (DIM == 2 ? Q : 1)> &Y) {
+                                             R uFy, R TF, R isTF, Blk<R, Q, (DIM == 2 ? Q : 1)> &Y) {
   using D = Dims<DIM>;
   constexpr int NY = DIM == 2 ? Q : 1;
   constexpr int base = Q == 4 ? 0 : D::QF;
@@ -206,10 +277,9 @@ __device__ __forceinline__ void stencil_pops(const StepConst &K, const R *sp, in
   for (int n = 0; n < Q; ++n)
 #pragma unroll
     for (int m = 0; m < NY; ++m) Y.v[n][m] = sp[(base + n + Q * m) * NH + h];
-  const R a = sp[D::IST * NH + h] * isTF;
-  shift_x(make_shift(a, (sp[D::IUX * NH + h] - uFx) * isTF), Y);
+  move_frame<R, DIM, Q>(K, sp[D::IUX * NH + h], DIM == 2 ? sp[D::IUY * NH + h] : R(0),
+                        sp[D::IT * NH + h], sp[D::IST * NH + h], uFx, uFy, TF, isTF, Y);
   if constexpr (DIM == 2) {
-    shift_y(make_shift(a, (sp[D::IUY * NH + h] - uFy) * isTF), Y);
     if (K.grad_k) grad_mask(Y);
   }
   syn_x(Y);
@@ -225,7 +295,7 @@ __device__ __forceinline__ void stencil_pops(const StepConst &K, const R *sp, in
 // (L odd and symmetric), plus the tangential term -v_t lam/2 L(a - lo, hi - a).
 template <typename R, int DIM, int DIRN, int Q>
 __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int NH, const int *st,
-                                            R uFx, R uFy, R sTF, R isTF,
+                                            R uFx, R uFy, R TF, R sTF, R isTF,
                                             Blk<R, Q, (DIM == 2 ? Q : 1)> &out) {
   constexpr int NY = DIM == 2 ? Q : 1;
   const R uFn = DIRN == 0 ? uFx : uFy, uFt = DIRN == 0 ? uFy : uFx;
@@ -236,17 +306,17 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
   for (int k = 0; k < Q; ++k) {
     const R c = R(Nodes<Q>::c(k));
     const R vn = sTF * c + uFn;
-    up[k] = vn > R(0);
+    up[k] = pos(vn);
     offn[k] = R(0.5) - hl * fabs(vn);
     offt[k] = -hl * (sTF * c + uFt);
   }
   Blk<R, Q, NY> YL, YR, A;
-  stencil_pops<R, DIM, Q>(K, sp, NH, st[0], uFx, uFy, isTF, YL);
-  stencil_pops<R, DIM, Q>(K, sp, NH, st[1], uFx, uFy, isTF, YR);
+  stencil_pops<R, DIM, Q>(K, sp, NH, st[0], uFx, uFy, TF, isTF, YL);
+  stencil_pops<R, DIM, Q>(K, sp, NH, st[1], uFx, uFy, TF, isTF, YR);
   {
     Blk<R, Q, NY> Y1, Y2;
-    stencil_pops<R, DIM, Q>(K, sp, NH, st[2], uFx, uFy, isTF, Y1);
-    stencil_pops<R, DIM, Q>(K, sp, NH, st[3], uFx, uFy, isTF, Y2);
+    stencil_pops<R, DIM, Q>(K, sp, NH, st[2], uFx, uFy, TF, isTF, Y1);
+    stencil_pops<R, DIM, Q>(K, sp, NH, st[3], uFx, uFy, TF, isTF, Y2);
 #pragma unroll
     for (int n = 0; n < Q; ++n)
 #pragma unroll
@@ -261,8 +331,8 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
   }
   if constexpr (DIM == 2) {
     Blk<R, Q, NY> Y1, Y2, Dl;
-    stencil_pops<R, DIM, Q>(K, sp, NH, st[4], uFx, uFy, isTF, Y1);
-    stencil_pops<R, DIM, Q>(K, sp, NH, st[5], uFx, uFy, isTF, Y2);
+    stencil_pops<R, DIM, Q>(K, sp, NH, st[4], uFx, uFy, TF, isTF, Y1);
+    stencil_pops<R, DIM, Q>(K, sp, NH, st[5], uFx, uFy, TF, isTF, Y2);
 #pragma unroll
     for (int n = 0; n < Q; ++n)
 #pragma unroll
@@ -270,8 +340,8 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
         const int k = DIRN == 0 ? n : m;
         Dl.v[n][m] = A.v[n][m] - (up[k] ? Y1.v[n][m] : Y2.v[n][m]);
       }
-    stencil_pops<R, DIM, Q>(K, sp, NH, st[6], uFx, uFy, isTF, Y1);
-    stencil_pops<R, DIM, Q>(K, sp, NH, st[7], uFx, uFy, isTF, Y2);
+    stencil_pops<R, DIM, Q>(K, sp, NH, st[6], uFx, uFy, TF, isTF, Y1);
+    stencil_pops<R, DIM, Q>(K, sp, NH, st[7], uFx, uFy, TF, isTF, Y2);
 #pragma unroll
     for (int n = 0; n < Q; ++n)
 #pragma unroll
@@ -295,38 +365,81 @@ __device__ __forceinline__ void gauss_he(R mu, R sm1, R &e1, R &e2, R &e3) {
 }
 
 // ---- phase B: one face --------------------------------------------------------
-template <typename R, int DIM, int DIRN>
-__device__ __forceinline__ void face_flux(const StepConst &K, const R *sp, int NH, const int *st,
+// ITER: the iterated face frame (the predictor-corrector of the earlier scheme
+// that Sec. IV.A.3 replaces by the averaged frame): the face frame is replaced
+// by the interface state {u_b, T_b} until max(|u_b - u_F|/sqrt(T_F),
+// |T_b - T_F|/T_F) < iter_tol (tested in FP64) or iter_max traces were made;
+// a converged face uses the co-moving equilibrium rho W.  An iterate whose
+// interface state is nonphysical ends the iteration and the face keeps the
+// previous iterate.  Returns true when an iterated frame did not converge.
+template <typename R, int DIM, int DIRN, bool ITER>
+__device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int NH, const int *st,
                                           R *fp, int NFACES, int fidx) {
   using D = Dims<DIM>;
   constexpr int NYF = D::NYF, NYG = D::NYG;
   const int hL = st[0], hR = st[1];
-  const R uFx = R(0.5) * (sp[D::IUX * NH + hL] + sp[D::IUX * NH + hR]);
-  const R uFy = DIM == 2 ? R(0.5) * (sp[D::IUY * NH + hL] + sp[D::IUY * NH + hR]) : R(0);
-  const R TF = R(0.5) * (sp[D::IT * NH + hL] + sp[D::IT * NH + hR]);
-  const R sTF = sqrt(TF), isTF = R(1) / sTF;
+  R uFx = R(0.5) * (sp[D::IUX * NH + hL] + sp[D::IUX * NH + hR]);
+  R uFy = DIM == 2 ? R(0.5) * (sp[D::IUY * NH + hL] + sp[D::IUY * NH + hR]) : R(0);
+  R TF = R(0.5) * (sp[D::IT * NH + hL] + sp[D::IT * NH + hR]);
+  R sTF = sqrt(TF), isTF = R(1) / sTF;
 
   Blk<R, 4, NYF> Fb;
   Blk<R, 3, NYG> Gb;
-  reconstruct<R, DIM, DIRN, 4>(K, sp, NH, st, uFx, uFy, sTF, isTF, Fb);
-  reconstruct<R, DIM, DIRN, 3>(K, sp, NH, st, uFx, uFy, sTF, isTF, Gb);
-  ana_x(Fb); ana_y(Fb); ana_x(Gb); ana_y(Gb);
-
-  // interface moments in the face frame (all carry the factor kappa1):
-  // rho, mu = (u - u_F)/sqrt(T_F), C_v rho T = T_F/2 (sum |c|^2 f - rho mu^2) + sum g
-  const R rk = Fb.v[0][0], irk = R(1) / rk;
-  const R mx = Fb.v[1][0] * irk;
-  R my = R(0), S2 = Fb.v[2][0] + R(DIM) * rk;
-  if constexpr (DIM == 2) { my = Fb.v[0][1] * irk; S2 += Fb.v[0][2]; }
-  const R ek = R(0.5) * TF * (S2 - rk * (mx * mx + my * my)) + Gb.v[0][0];
-  const R Tb = ek * irk * R(K.inv_cv);
+  R rk, mx, my, Tb;
+  bool converged = false, noconv = false;
+  R pFx = uFx, pFy = uFy, pT = TF;  // previous iterate's frame
+  int it = 0;
+  bool fallback = false;
+  while (true) {
+    reconstruct<R, DIM, DIRN, 4>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, Fb);
+    reconstruct<R, DIM, DIRN, 3>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, Gb);
+    ana_x(Fb); ana_y(Fb); ana_x(Gb); ana_y(Gb);
+    // interface moments in the face frame (all carry the factor kappa1):
+    // rho, mu = (u - u_F)/sqrt(T_F), C_v rho T = T_F/2 (sum |c|^2 f - rho mu^2) + sum g
+    rk = Fb.v[0][0];
+    const R irk = R(1) / rk;
+    mx = Fb.v[1][0] * irk;
+    my = R(0);
+    R S2 = Fb.v[2][0] + R(DIM) * rk;
+    if constexpr (DIM == 2) { my = Fb.v[0][1] * irk; S2 += Fb.v[0][2]; }
+    const R ek = R(0.5) * TF * (S2 - rk * (mx * mx + my * my)) + Gb.v[0][0];
+    Tb = ek * irk * R(K.inv_cv);
+    if constexpr (!ITER) {
+      break;
+    } else {
+      if (fallback) break;
+      if (!(rk > R(0) && Tb > R(0) && isfinite(Tb))) {
+        if (it > 0) {  // retrace at the previous (physical) iterate
+          uFx = pFx; uFy = pFy; TF = pT;
+          sTF = sqrt(TF); isTF = R(1) / sTF;
+          fallback = true;
+          continue;
+        }
+        break;
+      }
+      const double mxd = mx, myd = my;
+      const double err = fmax(sqrt(mxd * mxd + myd * myd), fabs((double)Tb - (double)TF) / (double)TF);
+      if (err < K.iter_tol) { converged = true; break; }
+      if (++it >= (K.iter_max > 0 ? K.iter_max : 1)) break;
+      pFx = uFx; pFy = uFy; pT = TF;
+      uFx = uFx + sTF * mx;
+      if constexpr (DIM == 2) uFy = uFy + sTF * my;
+      TF = Tb;
+      sTF = sqrt(TF); isTF = R(1) / sTF;
+    }
+  }
+  if constexpr (ITER) noconv = !converged;
   const R sm1 = Tb * isTF * isTF - R(1);
 
-  // equilibrium (closed form of rho G_{u,T}^{lambda_F} W), weighted by kappa2/kappa1
+  // equilibrium (closed form of rho G_{u,T}^{lambda_F} W), weighted by kappa2/kappa1;
+  // a converged iterated frame is co-moving: rho W
   R ex[4], ey[4];
   ex[0] = R(1); gauss_he(mx, sm1, ex[1], ex[2], ex[3]);
   ey[0] = R(1); ey[1] = ey[2] = ey[3] = R(0);
   if constexpr (DIM == 2) gauss_he(my, sm1, ey[1], ey[2], ey[3]);
+  if constexpr (ITER) {
+    if (converged) ex[1] = ex[2] = ex[3] = ey[1] = ey[2] = ey[3] = R(0);
+  }
   // an interface state with rho <= 0 or T <= 0 has no equilibrium: poison the
   // face so that both adjacent cells are flagged nonphysical
   const bool phys = rk > R(0) && Tb > R(0);
@@ -353,6 +466,43 @@ __device__ __forceinline__ void face_flux(const StepConst &K, const R *sp, int N
     vmul<DIRN>(un, sTF, Fb);
     vmul<DIRN>(un, sTF, Gb);
   }
+  if constexpr (is_mixed<R>()) {
+    // Mixed path: the face's conserved fluxes (mass, momentum, energy along the
+    // normal), evaluated once here so that the two adjacent cells add exactly
+    // opposite amounts to their FP64 moment sums.  They are moments of order
+    // <= 3 of v_n phi (<= 1 of v_n g), which every frame transformation keeps
+    // (Eq. eq:Mcondition), so the face frame gives the same values as the cell
+    // frames of Eq. fluxEq.  C = Hermite coefficients of v_n phi (low orders).
+    const R un = DIRN == 0 ? uFx : uFy;
+    R C00, C10, C01 = R(0), C20, C02 = R(0), CG;
+    if (K.appc) {  // Fb, Gb already hold v_n phi
+      C00 = Fb.v[0][0]; C10 = Fb.v[1][0]; C20 = Fb.v[2][0]; CG = Gb.v[0][0];
+      if constexpr (DIM == 2) { C01 = Fb.v[0][1]; C02 = Fb.v[0][2]; }
+    } else if constexpr (DIRN == 0) {  // c He_n = He_{n+1} + n He_{n-1} along x
+      C00 = un * Fb.v[0][0] + sTF * Fb.v[1][0];
+      C10 = un * Fb.v[1][0] + sTF * (Fb.v[0][0] + Fb.v[2][0]);
+      C20 = un * Fb.v[2][0] + sTF * (R(2) * Fb.v[1][0] + Fb.v[3][0]);
+      CG = un * Gb.v[0][0] + sTF * Gb.v[1][0];
+      if constexpr (DIM == 2) {
+        C01 = un * Fb.v[0][1] + sTF * Fb.v[1][1];
+        C02 = un * Fb.v[0][2] + sTF * Fb.v[1][2];
+      }
+    } else {  // along y
+      C00 = un * Fb.v[0][0] + sTF * Fb.v[0][1];
+      C01 = un * Fb.v[0][1] + sTF * (Fb.v[0][0] + Fb.v[0][2]);
+      C02 = un * Fb.v[0][2] + sTF * (R(2) * Fb.v[0][1] + Fb.v[0][3]);
+      C10 = un * Fb.v[1][0] + sTF * Fb.v[1][1];
+      C20 = un * Fb.v[2][0] + sTF * Fb.v[2][1];
+      CG = un * Gb.v[0][0] + sTF * Gb.v[0][1];
+    }
+    // v = u_F + sqrt(T_F) c: sum v_n phi, sum v v_n phi, sum (|v|^2/2) v_n phi + sum v_n g
+    const R c2 = C20 + C02 + R(DIM) * C00;
+    fp[(D::FJ + 0) * NFACES + fidx] = C00;
+    fp[(D::FJ + 1) * NFACES + fidx] = uFx * C00 + sTF * C10;
+    fp[(D::FJ + 2) * NFACES + fidx] = uFy * C00 + sTF * C01;
+    fp[(D::FJ + 3) * NFACES + fidx] =
+        R(0.5) * ((uFx * uFx + uFy * uFy) * C00 + R(2) * sTF * (uFx * C10 + uFy * C01) + TF * c2) + CG;
+  }
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -364,13 +514,24 @@ __device__ __forceinline__ void face_flux(const StepConst &K, const R *sp, int N
   fp[D::FUX * NFACES + fidx] = uFx;
   fp[D::FUY * NFACES + fidx] = uFy;
   fp[D::FST * NFACES + fidx] = sTF;
+  fp[D::FT * NFACES + fidx] = TF;
+  return noconv;
 }
 
 // ---- phase C: one cell --------------------------------------------------------
+// Mixed path: the conserved moments of each cell (rho, rho u, rho E: Eqs.
+// eq::ConservationLaws, eq:E) are accumulated in FP64: the old cell's, from
+// its coefficients, plus -dt/dx times each face's conserved flux (the same
+// FP32 value for both cells of a face).  The collision terms conserve them.
+struct MomAcc {
+  double r, jx, jy, e;
+};
+
 template <typename R, int DIM, int DIRN>
 __device__ __forceinline__ void add_face(const StepConst &K, const R *fp, int NFACES, int fidx,
-                                         R sgn, R ux, R uy, R sT, R isT, Blk<R, 4, Dims<DIM>::NYF> &AF,
-                                         Blk<R, 3, Dims<DIM>::NYG> &AG) {
+                                         R sgn, R ux, R uy, R T, R sT, R isT,
+                                         Blk<R, 4, Dims<DIM>::NYF> &AF, Blk<R, 3, Dims<DIM>::NYG> &AG,
+                                         MomAcc &M) {
   using D = Dims<DIM>;
   Blk<R, 4, D::NYF> X;
   Blk<R, 3, D::NYG> Y;
@@ -383,12 +544,10 @@ __device__ __forceinline__ void add_face(const StepConst &K, const R *fp, int NF
 #pragma unroll
     for (int b = 0; b < D::NYG; ++b) Y.v[a][b] = fp[(D::QF + a + 3 * b) * NFACES + fidx];
   const R uFx = fp[D::FUX * NFACES + fidx], uFy = fp[D::FUY * NFACES + fidx];
-  const R a = fp[D::FST * NFACES + fidx] * isT;
-  const Shift<R> Cx = make_shift(a, (uFx - ux) * isT);
-  shift_x(Cx, X); shift_x(Cx, Y);
+  const R sTF = fp[D::FST * NFACES + fidx], TF = fp[D::FT * NFACES + fidx];
+  move_frame<R, DIM, 4>(K, uFx, uFy, TF, sTF, ux, uy, T, isT, X);
+  move_frame<R, DIM, 3>(K, uFx, uFy, TF, sTF, ux, uy, T, isT, Y);
   if constexpr (DIM == 2) {
-    const Shift<R> Cy = make_shift(a, (uFy - uy) * isT);
-    shift_y(Cy, X); shift_y(Cy, Y);
     if (K.grad_k) { grad_mask(X); grad_mask(Y); }
   }
   // contribution -dt/dx (v^lambda . n) G phi (Eq. fluxEq) or -dt/dx G (v^lambda_F . n phi)
@@ -397,23 +556,30 @@ __device__ __forceinline__ void add_face(const StepConst &K, const R *fp, int NF
     const R un = DIRN == 0 ? ux : uy;
     vmul<DIRN>(w * un, w * sT, X);
     vmul<DIRN>(w * un, w * sT, Y);
-#pragma unroll
-    for (int p = 0; p < 4; ++p)
-#pragma unroll
-      for (int q = 0; q < D::NYF; ++q) AF.v[p][q] += X.v[p][q];
-#pragma unroll
-    for (int p = 0; p < 3; ++p)
-#pragma unroll
-      for (int q = 0; q < D::NYG; ++q) AG.v[p][q] += Y.v[p][q];
   } else {
 #pragma unroll
     for (int p = 0; p < 4; ++p)
 #pragma unroll
-      for (int q = 0; q < D::NYF; ++q) AF.v[p][q] += w * X.v[p][q];
+      for (int q = 0; q < D::NYF; ++q) X.v[p][q] *= w;
 #pragma unroll
     for (int p = 0; p < 3; ++p)
 #pragma unroll
-      for (int q = 0; q < D::NYG; ++q) AG.v[p][q] += w * Y.v[p][q];
+      for (int q = 0; q < D::NYG; ++q) Y.v[p][q] *= w;
+  }
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < D::NYF; ++q) AF.v[p][q] += X.v[p][q];
+#pragma unroll
+  for (int p = 0; p < 3; ++p)
+#pragma unroll
+    for (int q = 0; q < D::NYG; ++q) AG.v[p][q] += Y.v[p][q];
+  if constexpr (is_mixed<R>()) {
+    const double w64 = -K.lam * (double)sgn;
+    M.r += w64 * (double)fp[(D::FJ + 0) * NFACES + fidx];
+    M.jx += w64 * (double)fp[(D::FJ + 1) * NFACES + fidx];
+    if constexpr (DIM == 2) M.jy += w64 * (double)fp[(D::FJ + 2) * NFACES + fidx];
+    M.e += w64 * (double)fp[(D::FJ + 3) * NFACES + fidx];
   }
 }
 
@@ -433,16 +599,28 @@ __device__ __forceinline__ void update_cell(const StepConst &K, const State<R> &
   for (int i = 0; i < D::QG; ++i) { G.v[i % 3][i / 3] = S.g[i * N + c]; AG.v[i % 3][i / 3] = R(0); }
   const R ux = S.ux[c], uy = DIM == 2 ? S.uy[c] : R(0), T = S.T[c];
   const R sT = sqrt(T), isT = R(1) / sT;
-  ana_x(F); ana_y(F); ana_x(G); ana_y(G);
   qe_scale(F, G, R(K.qe));
   const R rho = F.v[0][0];
+  MomAcc M;
+  if constexpr (is_mixed<R>()) {
+    // the cell's conserved moments, v = u + sqrt(T) c
+    const double r64 = rho, ux64 = ux, uy64 = uy, T64 = T, sT64 = sqrt(T64);
+    const double a10 = F.v[1][0], a01 = DIM == 2 ? (double)F.v[0][1] : 0.0;
+    double c2 = (double)F.v[2][0] + DIM * r64;
+    if constexpr (DIM == 2) c2 += (double)F.v[0][2];
+    M.r = r64;
+    M.jx = ux64 * r64 + sT64 * a10;
+    M.jy = uy64 * r64 + sT64 * a01;
+    M.e = 0.5 * ((ux64 * ux64 + uy64 * uy64) * r64 + 2.0 * sT64 * (ux64 * a10 + uy64 * a01) + T64 * c2) +
+          (double)G.v[0][0];
+  }
 
   // fluxes through the faces, in a fixed order: x-lo, x-hi, y-lo, y-hi
-  add_face<R, DIM, 0>(K, fp, TL::NFACES, cy * (BX + 1) + cx, R(-1), ux, uy, sT, isT, AF, AG);
-  add_face<R, DIM, 0>(K, fp, TL::NFACES, cy * (BX + 1) + cx + 1, R(1), ux, uy, sT, isT, AF, AG);
+  add_face<R, DIM, 0>(K, fp, TL::NFACES, cy * (BX + 1) + cx, R(-1), ux, uy, T, sT, isT, AF, AG, M);
+  add_face<R, DIM, 0>(K, fp, TL::NFACES, cy * (BX + 1) + cx + 1, R(1), ux, uy, T, sT, isT, AF, AG, M);
   if constexpr (DIM == 2) {
-    add_face<R, DIM, 1>(K, fp, TL::NFACES, TL::NFX + cy * BX + cx, R(-1), ux, uy, sT, isT, AF, AG);
-    add_face<R, DIM, 1>(K, fp, TL::NFACES, TL::NFX + (cy + 1) * BX + cx, R(1), ux, uy, sT, isT, AF, AG);
+    add_face<R, DIM, 1>(K, fp, TL::NFACES, TL::NFX + cy * BX + cx, R(-1), ux, uy, T, sT, isT, AF, AG, M);
+    add_face<R, DIM, 1>(K, fp, TL::NFACES, TL::NFX + (cy + 1) * BX + cx, R(1), ux, uy, T, sT, isT, AF, AG, M);
   }
   // DUGKS update in the cell frame: a1 phi~ + a2 phi^eq - dt/dx sum F
   const R a1 = R(K.a1);
@@ -458,32 +636,63 @@ __device__ __forceinline__ void update_cell(const StepConst &K, const State<R> &
   G.v[0][0] += R(K.a2) * R(K.gfac) * T * rho;
 
   // new moments (Eqs. eq::ConservationLaws, eq:E) and the new co-moving frame
-  const R rn = F.v[0][0], irn = R(1) / rn;
-  const R mx = F.v[1][0] * irn;
-  R my = R(0), S2 = F.v[2][0] + R(DIM) * rn;
-  if constexpr (DIM == 2) { my = F.v[0][1] * irn; S2 += F.v[0][2]; }
-  const R en = R(0.5) * T * (S2 - rn * (mx * mx + my * my)) + G.v[0][0];
-  const R Tn = en * irn * R(K.inv_cv);
-  R uxn = ux + sT * mx, uyn = DIM == 2 ? uy + sT * my : R(0), Tout = Tn;
-  const bool ok = rn > R(0) && Tn > R(0) && isfinite(rn) && isfinite(Tn) && isfinite(uxn) &&
-                  isfinite(uyn);
+  R uxn, uyn, Tout;
+  bool ok;
+  if constexpr (!is_mixed<R>()) {
+    const R rn = F.v[0][0], irn = R(1) / rn;
+    const R mx = F.v[1][0] * irn;
+    R my = R(0), S2 = F.v[2][0] + R(DIM) * rn;
+    if constexpr (DIM == 2) { my = F.v[0][1] * irn; S2 += F.v[0][2]; }
+    const R en = R(0.5) * T * (S2 - rn * (mx * mx + my * my)) + G.v[0][0];
+    const R Tn = en * irn * R(K.inv_cv);
+    uxn = ux + sT * mx; uyn = DIM == 2 ? uy + sT * my : R(0); Tout = Tn;
+    ok = rn > R(0) && Tn > R(0) && isfinite(rn) && isfinite(Tn) && isfinite(uxn) && isfinite(uyn);
+    if (ok) {
+      const R sTn = sqrt(Tn), a = sT / sTn;
+      const Shift<R> Cx = make_shift(a, -a * mx);
+      shift_x(Cx, F); shift_x(Cx, G);
+      if constexpr (DIM == 2) {
+        const Shift<R> Cy = make_shift(a, -a * my);
+        shift_y(Cy, F); shift_y(Cy, G);
+      }
+    }
+  } else {
+    // FP64: the new moments and frame; the frame is stored rounded to FP32
+    // and the populations are moved into exactly that stored frame
+    const double rn = M.r, irn = 1.0 / rn;
+    const double ux64 = M.jx * irn, uy64 = DIM == 2 ? M.jy * irn : 0.0;
+    const double Tn = (M.e - 0.5 * rn * (ux64 * ux64 + uy64 * uy64)) * irn * K.inv_cv;
+    ok = rn > 0.0 && Tn > 0.0 && isfinite(rn) && isfinite(Tn) && isfinite(ux64) && isfinite(uy64);
+    uxn = (R)ux64; uyn = (R)uy64; Tout = (R)Tn;
+    ok = ok && Tout > R(0) && isfinite(Tout);
+    // the conserved coefficients (still in the old frame) are the FP64 sums,
+    // rounded once: the FP32 update alone drifts (a1 + a2 != 1 in FP32, and
+    // the two cells of a face move its flux through different frames)
+    const double cux = ux, cuy = uy, T64 = T, isT64 = 1.0 / sqrt(T64), sT64 = T64 * isT64;
+    const double a10 = (M.jx - cux * rn) * isT64, a01 = DIM == 2 ? (M.jy - cuy * rn) * isT64 : 0.0;
+    F.v[0][0] = (R)rn;
+    F.v[1][0] = (R)a10;
+    double c2 = (double)F.v[2][0] + DIM * rn;
+    if constexpr (DIM == 2) { F.v[0][1] = (R)a01; c2 += (double)F.v[0][2]; }
+    G.v[0][0] = (R)(M.e - 0.5 * ((cux * cux + cuy * cuy) * rn + 2.0 * sT64 * (cux * a10 + cuy * a01) +
+                                 T64 * c2));
+    if (ok) {
+      const R sTn = sqrt(Tout), isTn = R(1) / sTn;
+      move_frame<R, DIM, 4>(K, ux, uy, T, sT, uxn, uyn, Tout, isTn, F);
+      move_frame<R, DIM, 3>(K, ux, uy, T, sT, uxn, uyn, Tout, isTn, G);
+    }
+  }
   if (ok) {
-    const R sTn = sqrt(Tn), a = sT / sTn;
-    const Shift<R> Cx = make_shift(a, -a * mx);
-    shift_x(Cx, F); shift_x(Cx, G);
     if constexpr (DIM == 2) {
-      const Shift<R> Cy = make_shift(a, -a * my);
-      shift_y(Cy, F); shift_y(Cy, G);
       if (K.grad_k) { grad_mask(F); grad_mask(G); }
     }
     qe_scale(F, G, R(K.qe));
-    const double vmax = fmax(fabs((double)uxn), fabs((double)uyn)) + (double)sTn * Nodes<4>::cmax;
+    const double vmax = fmax(fabs((double)uxn), fabs((double)uyn)) + sqrt((double)Tout) * Nodes<4>::cmax;
     cfl = fmax(cfl, vmax * K.lam);
   } else {
     flags |= FLAG_NONPHYSICAL;
     uxn = ux; uyn = uy; Tout = T;
   }
-  syn_x(F); syn_y(F); syn_x(G); syn_y(G);
 #pragma unroll
   for (int i = 0; i < D::QF; ++i) O.f[i * N + c] = F.v[i % 4][i / 4];
 #pragma unroll
@@ -493,17 +702,18 @@ __device__ __forceinline__ void update_cell(const StepConst &K, const State<R> &
   O.T[c] = Tout;
 }
 
-// ---- the fused step kernel ------------------------------------------------------
-template <typename R, int DIM, int BX, int BY, int NT>
-__global__ void __launch_bounds__(NT) step_kernel(const StepConst K, const State<R> S,
-                                                  const State<R> O, Stats *stats) {
+// ---- one tile step (phases A-C) --------------------------------------------------
+// The BX x BY tile whose first cell is (j0, k0); smem holds the halo and face
+// records.  Every output depends only on its own stencil's arithmetic, so the
+// result is the same for any tile shape or launch order.
+template <typename R, int DIM, int BX, int BY, int NT, bool ITER>
+__device__ __forceinline__ void step_tile(const StepConst &K, const State<R> &S, const State<R> &O,
+                                          Stats *stats, int j0, int k0, unsigned char *smem) {
   using D = Dims<DIM>;
   using TL = Tile<DIM, BX, BY>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  R *sp = reinterpret_cast<R *>(smem_raw);
+  R *sp = reinterpret_cast<R *>(smem);
   R *fp = sp + (size_t)TL::NH * D::NPREP;
   const int tid = threadIdx.x;
-  const int j0 = blockIdx.x * BX, k0 = DIM == 2 ? blockIdx.y * BY : 0;
 
   // A. halo tile
   for (int h = tid; h < TL::NH; h += NT) {
@@ -512,7 +722,9 @@ __global__ void __launch_bounds__(NT) step_kernel(const StepConst K, const State
   }
   __syncthreads();
 
-  // B. faces
+  // B. faces (a face on a tile edge is evaluated by both tiles; the iterated
+  // frame's no-convergence count takes it from the tile on its right/upper side)
+  unsigned noconv = 0;
   for (int f = tid; f < TL::NFACES; f += NT) {
     int st[8];
     if (f < TL::NFX) {
@@ -524,7 +736,8 @@ __global__ void __launch_bounds__(NT) step_kernel(const StepConst K, const State
         st[4] = r - TL::HX + fx + 1; st[5] = r - TL::HX + fx + 2;
         st[6] = r + TL::HX + fx + 1; st[7] = r + TL::HX + fx + 2;
       }
-      face_flux<R, DIM, 0>(K, sp, TL::NH, st, fp, TL::NFACES, f);
+      const bool nc = face_flux<R, DIM, 0, ITER>(K, sp, TL::NH, st, fp, TL::NFACES, f);
+      if (ITER && nc && (fx > 0 || j0 == 0)) ++noconv;
     } else if constexpr (DIM == 2) {
       const int g = f - TL::NFX, fx = g % BX, fy = g / BX;
       if (j0 + fx >= K.nx || k0 + fy - 1 >= K.ny) continue;
@@ -532,7 +745,8 @@ __global__ void __launch_bounds__(NT) step_kernel(const StepConst K, const State
       st[0] = (fy + 1) * H + x; st[1] = (fy + 2) * H + x; st[2] = fy * H + x; st[3] = (fy + 3) * H + x;
       st[4] = (fy + 1) * H + x - 1; st[5] = (fy + 2) * H + x - 1;
       st[6] = (fy + 1) * H + x + 1; st[7] = (fy + 2) * H + x + 1;
-      face_flux<R, DIM, 1>(K, sp, TL::NH, st, fp, TL::NFACES, f);
+      const bool nc = face_flux<R, DIM, 1, ITER>(K, sp, TL::NH, st, fp, TL::NFACES, f);
+      if (ITER && nc && (fy > 0 || k0 == 0)) ++noconv;
     }
   }
   __syncthreads();
@@ -546,17 +760,31 @@ __global__ void __launch_bounds__(NT) step_kernel(const StepConst K, const State
     if (j >= K.nx || k >= (DIM == 2 ? K.ny : 1)) continue;
     update_cell<R, DIM, BX, BY>(K, S, O, fp, cx, cy, j, k, cfl, flags);
   }
-  // warp reduction of the CFL number and flags, one atomic per warp
+  // warp reduction of the CFL number, flags and counts, one atomic per warp
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     cfl = fmax(cfl, __shfl_xor_sync(0xffffffffu, cfl, o));
     flags |= __shfl_xor_sync(0xffffffffu, flags, o);
+    if constexpr (ITER) noconv += __shfl_xor_sync(0xffffffffu, noconv, o);
   }
   if ((tid & 31) == 0) {
     if (cfl > 1.0) flags |= FLAG_CFL;
+    if (noconv) {
+      flags |= FLAG_NOCONV;
+      atomicAdd(&stats->noconv, (unsigned long long)noconv);
+    }
     if (flags) atomicOr(&stats->flags, flags);
     atomicMax(&stats->max_cfl_bits, (unsigned long long)__double_as_longlong(cfl));
   }
+}
+
+// ---- the fused step kernel: one launch = one time step of one grid --------------
+template <typename R, int DIM, int BX, int BY, int NT, int MINB = 1, bool ITER = false>
+__global__ void __launch_bounds__(NT, MINB) step_kernel(const StepConst K, const State<R> S,
+                                                        const State<R> O, Stats *stats) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  step_tile<R, DIM, BX, BY, NT, ITER>(K, S, O, stats, blockIdx.x * BX, DIM == 2 ? blockIdx.y * BY : 0,
+                                      smem_raw);
 }
 
 }  // namespace pond

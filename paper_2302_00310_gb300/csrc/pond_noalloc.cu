@@ -63,6 +63,35 @@ pond_status scratch_for_current_device(unsigned char **out) {
   return POND_OK;
 }
 
+// In-place change of basis of the caller's FP64 planes: populations <-> their
+// Hermite coefficients, the layout the step kernels keep the state in.  Each
+// thread owns one cell and reads all of its values before writing.
+template <int DIM, bool TO_COEF>
+__global__ void noalloc_basis_kernel(double *f, double *g, size_t N) {
+  const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= N) return;
+  using D = pond::Dims<DIM>;
+  pond::Blk<double, 4, D::NYF> F;
+  pond::Blk<double, 3, D::NYG> G;
+  for (int q = 0; q < D::QF; ++q) F.v[q % 4][q / 4] = f[q * N + c];
+  for (int q = 0; q < D::QG; ++q) G.v[q % 3][q / 3] = g[q * N + c];
+  if (TO_COEF) {
+    pond::ana_x(F); pond::ana_y(F); pond::ana_x(G); pond::ana_y(G);
+  } else {
+    pond::syn_x(F); pond::syn_y(F); pond::syn_x(G); pond::syn_y(G);
+  }
+  for (int q = 0; q < D::QF; ++q) f[q * N + c] = F.v[q % 4][q / 4];
+  for (int q = 0; q < D::QG; ++q) g[q * N + c] = G.v[q % 3][q / 3];
+}
+
+template <bool TO_COEF>
+bool change_basis(int D, double *f, double *g, size_t N, cudaStream_t st) {
+  const unsigned nb = (unsigned)((N + 255) / 256);
+  if (D == 2) noalloc_basis_kernel<2, TO_COEF><<<nb, 256, 0, st>>>(f, g, N);
+  else noalloc_basis_kernel<1, TO_COEF><<<nb, 256, 0, st>>>(f, g, N);
+  return cudaGetLastError() == cudaSuccess;
+}
+
 bool params_ok(const pond_params *p, int D) {
   if (!p || !(p->gamma > 1.0) || !(p->tau > 0.0) || !(p->prandtl > 0.0) || !(p->dx > 0.0) ||
       !(p->dt > 0.0))
@@ -134,6 +163,7 @@ extern "C" pond_status pond_step_noalloc(pond_lattice lat, const int64_t dims[2]
     return POND_E_CUDA;
   }
   const pond::StepConst K = step_const(*p, D, nx, ny);
+  if (n > 0 && !change_basis<true>(D, f, g, N, st)) return POND_E_CUDA;
   for (int64_t i = 0; i < n; ++i) {
     const pond::State<double> &in = (i & 1) ? other : caller;
     const pond::State<double> &out = (i & 1) ? caller : other;
@@ -162,6 +192,7 @@ extern "C" pond_status pond_step_noalloc(pond_lattice lat, const int64_t dims[2]
       }
     }
   }
+  if (n > 0 && !change_basis<false>(D, f, g, N, st)) return POND_E_CUDA;
   if (flags) {
     pond::Stats h;
     if (cudaMemcpyAsync(&h, stats, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||

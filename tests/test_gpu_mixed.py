@@ -1,0 +1,184 @@
+"""The mixed-precision path (POND_FP32_MIXED): FP32 populations, frame
+transformations, reconstruction and collision; FP64 accumulation of each
+cell's conserved moments and of its new frame; FP64 frame transformations
+where the shifted nodes land beyond xi_fp64_threshold.
+
+Its results are compared with the FP64 oracle (small grids) and with the FP64
+CUDA path, which matches the oracle to 1e-12 (full-size runs).  Stated error
+bounds, from FP32 rounding (unit roundoff 6e-8) carried through a step's
+~10^4 operations and then accumulated over the run:
+  * moments after <= 3 steps: max-relative error <= 2e-6 per field;
+  * L1 relative density error: <= 1e-5 for the smooth pulse (1000 steps at
+    256^2) and the Sod tube; <= 1e-3 for the four-quadrant Riemann problem.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2302_00310_gb300 import pond
+from paper_2302_00310_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL_STEP = 2e-6
+TOL_L1_SMOOTH = 1e-5
+TOL_L1_SHOCK = 1e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pond.lib(build=True)
+
+
+def _l1(a, b):
+    return float(np.sum(np.abs(a - b)) / np.sum(np.abs(b)))
+
+
+def _linf(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def _gpu(cfg, prim, steps, precision=pond.POND_FP32_MIXED, tile=0):
+    sim = pond.Sim(dict(cfg, precision=precision, tile=tile))
+    sim.init(*prim)
+    sim.step(steps)
+    m = sim.moments()
+    fl = sim.flags()
+    sim.close()
+    return m, fl
+
+
+def _oracle_moments(cfg, prim, steps):
+    oc = oracle.Config.from_dict(cfg)
+    return oracle.moments(oc, oracle.run(oc, oracle.init(oc, *prim), steps))
+
+
+CASES = [
+    # D, nx, ny, bc, prandtl, limiter, grad_k, appc, steps, tile, xi threshold
+    (1, 300, 1, (1, 1, 1, 1), 1.0, 0, 0, 0, 1, 0, 8.0),
+    (1, 253, 1, (0, 0, 0, 0), 0.71, 1, 0, 1, 3, 0, 8.0),
+    (2, 37, 29, (1, 1, 0, 0), 1.0, 0, 0, 0, 1, 2, 8.0),
+    (2, 37, 29, (0, 0, 0, 0), 0.71, 1, 0, 0, 2, 3, 8.0),
+    (2, 21, 40, (2, 1, 1, 1), 1.0, 0, 1, 0, 2, 6, 8.0),
+    (2, 33, 35, (1, 2, 2, 1), 0.5, 1, 1, 1, 2, 5, 8.0),
+    (2, 29, 31, (1, 1, 0, 0), 0.71, 0, 0, 0, 2, 4, 1e-3),  # every transformation in FP64
+    (1, 300, 1, (1, 1, 1, 1), 0.71, 0, 0, 0, 2, 0, 1e-3),
+]
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_mixed_few_steps_match_oracle(case):
+    D, nx, ny, bc, pr, lim, gk, appc, steps, tile, thr = CASES[case]
+    prim = W.random_state_grid(D, nx, ny, seed=60 + case, mach=1.0)
+    cfg = W._base(D, nx, ny, tau=5e-3, dx=1.0 / nx, prandtl=pr, limiter=lim, grad_k=gk,
+                  flux_appc=appc, bc=bc, inflow=((1.1, 0.5, -0.2, 0.8),) * 4,
+                  xi_fp64_threshold=thr)
+    cfg["dt"] = W.dt_from_cfl(prim[1], prim[2], prim[3], cfg["dx"], 0.4)
+    om = _oracle_moments(cfg, prim, steps)
+    gm, fl = _gpu(cfg, prim, steps, tile=tile)
+    assert not fl[1] & pond.POND_FLAG_NONPHYSICAL
+    errs = [_linf(gm[i], om[i]) for i in (0, 1, 3)] + ([_linf(gm[2], om[2])] if D == 2 else [])
+    assert max(errs) <= TOL_STEP, errs
+
+
+def test_mixed_tile_shapes_agree_bitwise():
+    """Every output depends only on its stencil: tile shape changes nothing."""
+    prim = W.random_state_grid(2, 45, 39, seed=7, mach=1.0)
+    cfg = W._base(2, 45, 39, tau=5e-3, dx=1.0 / 45, prandtl=0.71, bc=(0, 0, 1, 1))
+    cfg["dt"] = W.dt_from_cfl(prim[1], prim[2], prim[3], cfg["dx"], 0.4)
+    ref = None
+    for tile in (2, 3, 4, 5, 6):
+        sim = pond.Sim(dict(cfg, precision=pond.POND_FP32_MIXED, tile=tile))
+        sim.init(*prim)
+        sim.step(3)
+        st = sim.get_state()
+        sim.close()
+        if ref is None:
+            ref = st
+        for a, b in zip(st, ref):
+            assert np.array_equal(a, b)
+
+
+def test_mixed_pulse_matches_oracle_l1():
+    """128^2 pulse (Mach 2 background: large uniform frame shifts), 200 steps."""
+    w = W.pulse_2d(n=128, seed=0)
+    prim = (w["rho"], w["ux"], w["uy"], w["T"])
+    om = _oracle_moments(w["cfg"], prim, 200)
+    gm, fl = _gpu(w["cfg"], prim, 200)
+    assert fl[1] == 0
+    assert _l1(gm[0], om[0]) <= TOL_L1_SMOOTH
+    assert _l1(gm[3], om[3]) <= TOL_L1_SMOOTH
+
+
+def test_mixed_pulse_full_run_l1():
+    """The full 256^2 x 1000-step pulse against the FP64 CUDA path."""
+    w = W.pulse_2d(n=256, seed=0)
+    prim = (w["rho"], w["ux"], w["uy"], w["T"])
+    m64, _ = _gpu(w["cfg"], prim, 1000, precision=pond.POND_FP64)
+    m32, fl = _gpu(w["cfg"], prim, 1000)
+    assert fl[1] == 0
+    assert _l1(m32[0], m64[0]) <= TOL_L1_SMOOTH, _l1(m32[0], m64[0])
+    # mass is conserved to FP32 rounding
+    assert abs(m32[0].sum() / m64[0].sum() - 1) < 1e-6
+
+
+def test_mixed_sod_l1():
+    w = W.sod_1d()
+    prim = (w["rho"], w["ux"], w["uy"], w["T"])
+    om = _oracle_moments(w["cfg"], prim, w["steps"])
+    gm, _ = _gpu(w["cfg"], prim, w["steps"])
+    assert _l1(gm[0][0], om[0][0]) <= TOL_L1_SMOOTH
+
+
+def test_mixed_riemann_l1():
+    """Four-quadrant Riemann problem (seeded states, QE Pr 0.71, minmod), 512^2,
+    200 steps, against the FP64 CUDA path."""
+    w = W.riemann4_2d(n=512, seed=1)
+    prim = (w["rho"], w["ux"], w["uy"], w["T"])
+    m64, f64 = _gpu(w["cfg"], prim, 200, precision=pond.POND_FP64)
+    m32, f32 = _gpu(w["cfg"], prim, 200)
+    assert f64[1] & pond.POND_FLAG_NONPHYSICAL == 0 and f32[1] & pond.POND_FLAG_NONPHYSICAL == 0
+    assert _l1(m32[0], m64[0]) <= TOL_L1_SHOCK, _l1(m32[0], m64[0])
+
+
+def test_mixed_iterated_frame_converges_in_fp32():
+    """The iterated face frame on the mixed path: convergence is tested in FP64
+    on FP32 moments, so a tolerance of 1e-6 is reachable.  The FP32 and FP64
+    iterations stop at different iterates within iter_tol of the fixed point,
+    so the bound is 10 iter_tol rather than the step bound."""
+    prim = W.random_state_grid(2, 24, 20, seed=70, mach=0.5)
+    cfg = W._base(2, 24, 20, tau=5e-3, dx=1.0 / 24, bc=(1, 1, 0, 0), iterative=1,
+                  iter_tol=1e-6, iter_max=40)
+    cfg["dt"] = W.dt_from_cfl(prim[1], prim[2], prim[3], cfg["dx"], 0.4)
+    om = _oracle_moments(cfg, prim, 2)
+    gm, fl = _gpu(cfg, prim, 2)
+    assert not fl[1] & pond.POND_FLAG_NONPHYSICAL
+    assert max(_linf(gm[i], om[i]) for i in range(4)) <= 10 * cfg["iter_tol"]
+
+
+@pytest.mark.parametrize("precision", [pond.POND_FP64, pond.POND_FP32_MIXED])
+def test_state_round_trip_host_and_device(precision):
+    """pond_set_state / pond_get_state exchange populations; the context keeps
+    Hermite coefficients.  Host arrays go through the idle buffer in chunks
+    of cells (several chunks on the mixed path), device arrays directly: both
+    give the same state back, to the precision of the context."""
+    torch = pytest.importorskip("torch")
+    prim = W.random_state_grid(2, 53, 47, seed=9, mach=1.0)
+    cfg = W._base(2, 53, 47, tau=5e-3, dx=1.0 / 53, bc=(1, 1, 1, 1))
+    cfg["dt"] = W.dt_from_cfl(prim[1], prim[2], prim[3], cfg["dx"], 0.4)
+    oc = oracle.Config.from_dict(cfg)
+    ost = oracle.run(oc, oracle.init(oc, *prim), 1)  # a non-equilibrium state
+    sim = pond.Sim(dict(cfg, precision=precision))
+    sim.init(*prim)
+    sim.set_state(ost.f, ost.g, ost.ux, ost.uy, ost.T)
+    host = sim.get_state()
+    dev = [torch.empty(a.shape, dtype=torch.float64, device="cuda") for a in host]
+    pond.pond_get_state(sim.ctx, *dev)
+    sim.close()
+    tol = 1e-15 if precision == pond.POND_FP64 else 2e-7
+    for a, b in zip(host, (ost.f, ost.g, ost.ux, ost.uy, ost.T)):
+        assert _linf(a, b) <= tol
+    for a, t in zip(host, dev):
+        assert np.array_equal(a, t.cpu().numpy())

@@ -80,6 +80,8 @@ CASES_2D = [
     (18, 17, (0, 0, 1, 1), 0.71, 0, 0, 1, 1.0, 3, 2),
     (2, 2, (0, 0, 0, 0), 1.0, 0, 0, 0, 0.5, 2, 2),
     (33, 35, (1, 2, 2, 1), 0.5, 1, 1, 1, 0.9, 2, 3),
+    (27, 41, (0, 0, 1, 1), 0.71, 1, 0, 0, 1.0, 2, 5),
+    (19, 37, (1, 1, 0, 0), 1.0, 0, 1, 1, 1.0, 2, 6),
 ]
 
 
@@ -258,3 +260,41 @@ def test_moments_match_oracle_moments():
     sim.close()
     for a, b in zip(gm, om):
         assert _rel(a, b) <= TOL
+
+
+ITER_CASES = [
+    # D, nx, ny, bc, prandtl, limiter, mach, iter_tol, iter_max, steps, parity tolerance
+    (1, 300, 1, (1, 1, 1, 1), 1.0, 0, 0.5, 1e-12, 10, 3, TOL),
+    (1, 253, 1, (0, 0, 0, 0), 0.71, 1, 0.5, 1e-9, 12, 2, TOL),
+    (2, 37, 29, (0, 0, 0, 0), 1.0, 0, 0.5, 1e-12, 10, 2, TOL),
+    (2, 21, 18, (1, 1, 0, 0), 0.71, 1, 0.5, 1e-9, 12, 2, TOL),
+    # a face whose iterates cycle (a node's v_n changes sign between iterates)
+    # feeds rounding differences back through every iteration: 40 of them
+    # turn the 1e-16 differences of one trace into ~1e-11
+    (1, 253, 1, (0, 0, 0, 0), 0.71, 1, 0.5, 1e-9, 40, 2, 1e-10),
+]
+
+
+@pytest.mark.parametrize("case", range(len(ITER_CASES)))
+def test_iterated_face_frame_matches_oracle(case):
+    """The iterated face frame (option): same state and the same number of
+    unconverged face evaluations as the oracle."""
+    D, nx, ny, bc, pr, lim, mach, tol, itmax, steps, ptol = ITER_CASES[case]
+    rho, ux, uy, T = W.random_state_grid(D, nx, ny, seed=40 + case, mach=mach)
+    cfg = W._base(D, nx, ny, tau=5e-3, dx=1.0 / nx, prandtl=pr, limiter=lim, bc=bc,
+                  iterative=1, iter_tol=tol, iter_max=itmax)
+    cfg["dt"] = W.dt_from_cfl(ux, uy, T, cfg["dx"], 0.4)
+    ost, got, flags = _run_both(cfg, rho, ux, uy, T, steps)
+    _compare(ost, got, D, tol=ptol)
+    assert flags[3] == ost.report["noconv_faces"]
+    assert bool(flags[1] & pond.POND_FLAG_NOCONV) == bool(ost.report["noconv_faces"])
+
+
+def test_iterated_face_frame_sod_matches_oracle():
+    """Sod tube at CFL 0.2 with the iterated frame: the discontinuity face
+    falls back to its last physical iterate on both sides."""
+    w = W.sod_1d(cfl=0.2)
+    cfg = dict(w["cfg"], iterative=1, iter_tol=1e-9, iter_max=60)
+    ost, got, flags = _run_both(cfg, w["rho"], w["ux"], w["uy"], w["T"], 60)
+    _compare(ost, got, 1)
+    assert flags[3] == ost.report["noconv_faces"] and flags[3] > 0

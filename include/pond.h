@@ -196,6 +196,72 @@ const char *pond_strerror(pond_status s);
 /* POND_ABI_VERSION of the loaded library. */
 int pond_abi_version(void);
 
+/* ---- Batches: many contexts advanced by one persistent kernel -----------------
+ * Not a step of the method: a way to run many independent problems (each a
+ * context with its own grid, time step, boundaries and parameters) through
+ * the same step of Sec. IV.A.3 at once.  Each launch is one time step of
+ * every member; a grid of (SMs x resident CTAs) CTAs strides over the tiles
+ * of all members, each tile running the same tile step as pond_step().
+ * Launches are replayed from a captured CUDA graph (graph_steps launches per
+ * chunk); members may join and leave between calls without a new capture.
+ *
+ * A member's state after a batch step is bit for bit the state pond_step()
+ * gives it alone (results do not depend on the tile shape or on the other
+ * members), so the autotuner times candidate tile shapes on the run's own
+ * steps: the first pond_batch_step() call in which every member takes at
+ * least graph_steps x (number of shapes) steps runs one chunk with each
+ * shape and keeps the fastest.
+ *
+ * Members must share the batch's dimension, precision and stream, must be
+ * initialised, and may not use the iterated face frame.  A context belongs
+ * to at most one batch; pond_destroy() removes it from its batch.  Batch
+ * calls are made from one host thread at a time. */
+typedef struct pond_batch pond_batch;
+typedef struct {
+  int32_t tile;         /* 0: the autotuner picks; else a 2D tile code 3, 4 or 6
+                           (1D batches have the one 252-cell tile)            */
+  int32_t graph_steps;  /* launches per chunk and per captured graph (1-1024) */
+  int32_t autotune;     /* 1: time the candidate shapes on the first long call */
+} pond_tune;
+
+/* Defaults: tile 0, graph_steps 8, autotune 1. */
+void pond_tune_default(pond_tune *t);
+
+/* Creates an empty batch for up to `capacity` members of dimension dim (1 or
+ * 2) and precision POND_FP64 / POND_FP32_MIXED, running on `stream` (a
+ * cudaStream_t; NULL = legacy default stream, launched without graphs).  It
+ * allocates a device descriptor table and two pinned host copies of it.
+ * tune may be NULL (defaults). */
+pond_status pond_batch_create(pond_batch **out, int32_t dim, int32_t precision, int32_t capacity,
+                              const pond_tune *tune, void *stream);
+
+/* Adds / removes a member.  POND_E_INVAL if the context does not fit the
+ * batch (dimension, precision, stream, iterated frame, capacity) or is in a
+ * batch already; POND_E_STATE if it is not initialised. */
+pond_status pond_batch_add(pond_batch *b, pond_ctx *c);
+pond_status pond_batch_remove(pond_batch *b, pond_ctx *c);
+
+/* Number of members (in the order they were added; removal keeps the order
+ * of the others). */
+int32_t pond_batch_size(const pond_batch *b);
+
+/* Advances member i by steps[i] >= 0 time steps (steps NULL: one each), in
+ * chunks of graph_steps launches; members with fewer steps drop out of the
+ * later launches.  Asynchronous on the batch stream except while the
+ * autotuner reads its timings and when the host gets two chunks ahead of
+ * the GPU (the descriptor table is double-buffered).  Flags and CFL numbers
+ * go to each member's own status (pond_status_flags). */
+pond_status pond_batch_step(pond_batch *b, const int64_t *steps);
+
+/* Tile code and grid (CTAs) in use, whether the autotuner has run, and the
+ * MLUPS of the chosen shape in its timed chunk (0 if not tuned).  Any
+ * pointer may be NULL. */
+pond_status pond_batch_info(const pond_batch *b, int32_t *tile, int32_t *grid, int32_t *tuned,
+                            double *tuned_mlups);
+
+/* Waits for the batch's work, detaches its members and frees the batch. */
+void pond_batch_destroy(pond_batch *b);
+
 /* ---- Step without any device allocation -------------------------------------
  * No counterpart in the paper: this is a calling convention, not a step of
  * the method.  It performs the same FP64 steps as pond_step() for callers that

@@ -1,7 +1,7 @@
 // pond_abi.cu -- the C ABI of include/pond.h: contexts, device state, launches.
 //
 // Device state of a context (one workspace, 256-byte aligned sub-buffers):
-//   [Stats block][state buffer 0][state buffer 1]
+//   [Stats block][one-member descriptor table][state buffer 0][state buffer 1]
 // A state buffer holds, in the arithmetic type R of the context (double for
 // POND_FP64, float for POND_FP32_MIXED), SoA arrays
 //   f[Qf][N], g[Qg][N], ux[N], uy[N], T[N]          (N = nx*ny cells)
@@ -15,64 +15,21 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
-#include "pond.h"
-#include "pond_kernels.cuh"
+#include "pond_internal.h"
 
 using pond::State;
 using pond::StepConst;
 using pond::Stats;
-
-struct pond_ctx {
-  pond_lattice lat;
-  int D;
-  int64_t nx, ny, N;
-  pond_params p;
-  bool fp32;
-  cudaStream_t stream;
-  unsigned char *ws;
-  size_t ws_bytes;
-  bool own_ws;
-  unsigned char *buf[2];
-  size_t buf_bytes;
-  Stats *stats;
-  int cur;
-  bool inited;
-  double dt;
-  int64_t steps;
-  int tile;
-  StepConst K;
-  cudaGraphExec_t graph[2];
-  int graph_chunk;
-};
+using pond_detail::qf_of;
+using pond_detail::qg_of;
+using pond_detail::state_of;
 
 namespace {
 
 constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
-
-int qf_of(int D) { return D == 2 ? 16 : 4; }
-int qg_of(int D) { return D == 2 ? 9 : 3; }
-
-#define POND_CUDA(call)                                   \
-  do {                                                    \
-    cudaError_t e_ = (call);                              \
-    if (e_ != cudaSuccess) {                              \
-      (void)cudaGetLastError();                           \
-      return POND_E_CUDA;                                 \
-    }                                                     \
-  } while (0)
-
-template <typename R> State<R> state_of(const pond_ctx *c, int b) {
-  R *base = reinterpret_cast<R *>(c->buf[b]);
-  State<R> s;
-  s.f = base;
-  s.g = s.f + (size_t)qf_of(c->D) * c->N;
-  s.ux = s.g + (size_t)qg_of(c->D) * c->N;
-  s.uy = s.ux + c->N;
-  s.T = s.uy + c->N;
-  return s;
-}
 
 // ---------------------------------------------------------------------------
 // small kernels: initial equilibrium, moments, conversions, max |v|
@@ -160,54 +117,59 @@ __global__ void vmax_kernel(const double *ux, const double *uy, const double *T,
 unsigned grid1(size_t n, unsigned b) { return (unsigned)((n + b - 1) / b); }
 
 // ---------------------------------------------------------------------------
-// step launches
+// step launches: the member step kernel with the context's one-member table,
+// one CTA per tile (the same kernel function a batch runs)
 // ---------------------------------------------------------------------------
-template <typename R, int DIM, int BX, int BY, int NT, int MINB = 1, bool ITER = false>
-pond_status launch_tile(pond_ctx *c, int from, bool prepare_only) {
-  static_assert(NT % 32 == 0, "whole warps");
-  using TL = pond::Tile<DIM, BX, BY>;
-  constexpr size_t smem = TL::template smem_bytes<R>();
-  static_assert(smem <= 227 * 1024, "tile too large for shared memory");
-  if (prepare_only) {
-    // the dynamic shared-memory opt-in is set outside any stream capture
-    POND_CUDA(cudaFuncSetAttribute(pond::step_kernel<R, DIM, BX, BY, NT, MINB, ITER>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    return POND_OK;
+// Picks the kernel instantiation, sets its shared-memory opt-in (outside any
+// stream capture) and uploads the table.  Called whenever K changes.
+pond_status prepare_step(pond_ctx *c) {
+  if (c->K.iterative) {
+    c->shape = c->fp32 ? pond_iter_shape_fp32(c->D) : pond_iter_shape_fp64(c->D);
+  } else {
+    const std::vector<pond::Shape> all = c->fp32 ? pond_shapes_fp32(c->D) : pond_shapes_fp64(c->D);
+    bool found = false;
+    for (const pond::Shape &sh : all)
+      if (sh.code == c->tile) { c->shape = sh; found = true; }
+    if (!found) return POND_E_INVAL;
   }
-  const dim3 grid((unsigned)((c->nx + BX - 1) / BX), DIM == 2 ? (unsigned)((c->ny + BY - 1) / BY) : 1u);
-  pond::step_kernel<R, DIM, BX, BY, NT, MINB, ITER><<<grid, NT, smem, c->stream>>>(
-      c->K, state_of<R>(c, from), state_of<R>(c, 1 - from), c->stats);
-  POND_CUDA(cudaGetLastError());
+  int occ = 0;
+  POND_CUDA(c->shape.prepare(&occ));
+  const int tx = (int)((c->nx + c->shape.bx - 1) / c->shape.bx);
+  const int ty = c->D == 2 ? (int)((c->ny + c->shape.by - 1) / c->shape.by) : 1;
+  c->tiles = tx * ty;
+  unsigned char host[pond::kSoloTableBytes];
+  memset(host, 0, sizeof(host));
+  pond::TableHdr hdr;
+  memset(&hdr, 0, sizeof(hdr));
+  hdr.n = 1;
+  hdr.total_tiles = c->tiles;
+  memcpy(host, &hdr, sizeof(hdr));
+  auto fill = [&](auto tag) {
+    using R = decltype(tag);
+    pond::InstDesc<R> d;
+    memset(&d, 0, sizeof(d));
+    d.K = c->K;
+    d.S[0] = state_of<R>(c, 0);
+    d.S[1] = state_of<R>(c, 1);
+    d.stats = c->stats;
+    d.tiles_x = tx;
+    d.tile_begin = 0;
+    d.steps = 0x7fffffff;
+    d.parity = 0;  // launch k = c->cur reads buffer cur
+    memcpy(host + sizeof(hdr), &d, sizeof(d));
+  };
+  if (c->fp32) fill(0.0f);
+  else fill(0.0);
+  POND_CUDA(cudaMemcpyAsync(c->table, host, sizeof(host), cudaMemcpyHostToDevice, c->stream));
+  POND_CUDA(cudaStreamSynchronize(c->stream));  // the host copy goes out of scope
   return POND_OK;
 }
 
-// tile codes: 1 = 1D 252 cells; 2D: 2 = 8x8, 3 = 16x16, 4 = 16x8, 5 = 8x8 with two
-// CTAs per SM (register cap 204), 6 = 8x16 with two CTAs per SM
-template <typename R>
-pond_status launch_step(pond_ctx *c, int from, bool prepare_only) {
-  // the iterated face frame runs with one tile shape of its own
-  if (c->K.iterative) {
-    if (c->D == 1) return launch_tile<R, 1, 252, 1, 256, 1, true>(c, from, prepare_only);
-    return launch_tile<R, 2, 8, 8, 160, 1, true>(c, from, prepare_only);
-  }
-  if (c->D == 1) return launch_tile<R, 1, 252, 1, 256>(c, from, prepare_only);
-  switch (c->tile) {
-    case 3: return launch_tile<R, 2, 16, 16, 256>(c, from, prepare_only);
-    case 4: return launch_tile<R, 2, 16, 8, 256>(c, from, prepare_only);
-    case 5: return launch_tile<R, 2, 8, 8, 160, 2>(c, from, prepare_only);
-    case 6: return launch_tile<R, 2, 8, 16, 160, 2>(c, from, prepare_only);
-    default: return launch_tile<R, 2, 8, 8, 160>(c, from, prepare_only);
-  }
-}
-
-pond_status prepare_step(pond_ctx *c) {
-  return c->fp32 ? launch_step<float>(c, 0, true) : launch_step<double>(c, 0, true);
-}
-
 pond_status step_once(pond_ctx *c) {
-  pond_status s = c->fp32 ? launch_step<float>(c, c->cur, false) : launch_step<double>(c, c->cur, false);
-  if (s == POND_OK) c->cur ^= 1;
-  return s;
+  c->shape.launch(c->table, c->cur, c->tiles, c->stream);
+  POND_CUDA(cudaGetLastError());
+  c->cur ^= 1;
+  return POND_OK;
 }
 
 // 8x16 tiles with two CTAs' worth of registers per SM were fastest for both
@@ -371,7 +333,7 @@ pond_status pond_workspace_size(pond_lattice lat, const int64_t dims[2], const p
   if (nx < 2 || (D == 2 && ny < 2) || nx > (1 << 24) || ny > (1 << 24)) return POND_E_INVAL;
   const size_t rs = p->precision == POND_FP32_MIXED ? 4 : 8;
   const size_t per_cell = (size_t)(qf_of(D) + qg_of(D) + 3) * rs;
-  *bytes = align_up(sizeof(Stats)) + 2 * align_up(per_cell * (size_t)(nx * ny));
+  *bytes = align_up(sizeof(Stats)) + pond::kSoloTableBytes + 2 * align_up(per_cell * (size_t)(nx * ny));
   return POND_OK;
 }
 
@@ -412,8 +374,9 @@ pond_status pond_create(pond_ctx **out, pond_lattice lat, const int64_t dims[2],
   }
   c->ws_bytes = need;
   c->stats = reinterpret_cast<Stats *>(c->ws);
-  c->buf_bytes = (need - align_up(sizeof(Stats))) / 2;
-  c->buf[0] = c->ws + align_up(sizeof(Stats));
+  c->table = c->ws + align_up(sizeof(Stats));
+  c->buf_bytes = (need - align_up(sizeof(Stats)) - pond::kSoloTableBytes) / 2;
+  c->buf[0] = c->table + pond::kSoloTableBytes;
   c->buf[1] = c->buf[0] + c->buf_bytes;
   c->cur = 0;
   c->tile = p->flux_frame == POND_FRAME_ITER ? (D == 1 ? 1 : 2) : (p->tile ? p->tile : auto_tile(c));
@@ -429,6 +392,7 @@ pond_status pond_create(pond_ctx **out, pond_lattice lat, const int64_t dims[2],
 
 void pond_destroy(pond_ctx *c) {
   if (!c) return;
+  pond_batch_detach(c);
   cudaStreamSynchronize(c->stream);
   drop_graphs(c);
   if (c->own_ws && c->ws) cudaFree(c->ws);

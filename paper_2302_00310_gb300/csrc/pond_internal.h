@@ -1,0 +1,67 @@
+// pond_internal.h -- the context object shared by the translation units of
+// the library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "pond.h"
+#include "pond_launch.h"
+
+struct pond_ctx {
+  pond_lattice lat;
+  int D;
+  int64_t nx, ny, N;
+  pond_params p;
+  bool fp32;
+  cudaStream_t stream;
+  unsigned char *ws;
+  size_t ws_bytes;
+  bool own_ws;
+  unsigned char *buf[2];  // state buffers (Hermite coefficients + frame)
+  size_t buf_bytes;
+  pond::Stats *stats;
+  int cur;                // buffer holding the current state
+  bool inited;
+  double dt;
+  int64_t steps;
+  int tile;
+  pond::StepConst K;
+  cudaGraphExec_t graph[2];
+  int graph_chunk;
+  void *batch;            // the batch this context belongs to, if any
+  unsigned char *table;   // its one-member descriptor table (device, in the workspace)
+  pond::Shape shape;      // the step kernel instantiation it launches
+  int tiles;              // tiles of its grid for that shape
+};
+
+namespace pond_detail {
+
+inline int qf_of(int D) { return D == 2 ? 16 : 4; }
+inline int qg_of(int D) { return D == 2 ? 9 : 3; }
+
+template <typename R> pond::State<R> state_of(const pond_ctx *c, int b) {
+  R *base = reinterpret_cast<R *>(c->buf[b]);
+  pond::State<R> s;
+  s.f = base;
+  s.g = s.f + (size_t)qf_of(c->D) * c->N;
+  s.ux = s.g + (size_t)qg_of(c->D) * c->N;
+  s.uy = s.ux + c->N;
+  s.T = s.uy + c->N;
+  return s;
+}
+
+}  // namespace pond_detail
+
+// removes a context from its batch (pond_batch.cu); called by pond_destroy()
+void pond_batch_detach(pond_ctx *c);
+
+#define POND_CUDA(call)                                   \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) {                              \
+      (void)cudaGetLastError();                           \
+      return POND_E_CUDA;                                 \
+    }                                                     \
+  } while (0)

@@ -1,0 +1,54 @@
+// pond_launch.h -- the descriptor table read by the member step kernel, and
+// the launch handles of its instantiations (not part of the C ABI).
+//
+// One kernel function serves both a single context (pond_step: a table with
+// one member, one CTA per tile) and a batch (pond_batch_step: many members,
+// a persistent grid), so a member's arithmetic is the same machine code
+// either way and its state is bit for bit the same alone or in a batch.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <vector>
+
+#include "pond_kernels.cuh"
+
+namespace pond {
+
+template <typename R> struct InstDesc {
+  StepConst K;
+  State<R> S[2];
+  Stats *stats;
+  int tiles_x;     // tiles per row of the member's grid
+  int tile_begin;  // first global tile index of the member
+  int steps;       // launch k advances the member iff k < steps
+  int parity;      // launch k reads buffer (parity + k) & 1 and writes the other
+};
+
+struct TableHdr {
+  int n;            // members in the table
+  int total_tiles;  // tiles over all members
+  int pad[62];      // 256-byte header
+};
+
+// device bytes reserved in a context's workspace for its one-member table
+constexpr size_t kSoloTableBytes = 1024;
+static_assert(sizeof(TableHdr) + sizeof(InstDesc<double>) <= kSoloTableBytes, "solo table");
+
+// One instantiation of the member step kernel: its tile geometry, the
+// shared-memory opt-in plus occupancy query, and the launch.
+struct Shape {
+  int code, bx, by;
+  cudaError_t (*prepare)(int *ctas_per_sm);
+  void (*launch)(const unsigned char *table, int k, int grid, cudaStream_t st);
+};
+
+}  // namespace pond
+
+// Every tile code of dimension D (1D: code 1; 2D: codes 2-6, see
+// pond_params.tile) and the iterated-face-frame shape, per precision; defined
+// in pond_step_fp64.cu / pond_step_fp32.cu.
+std::vector<pond::Shape> pond_shapes_fp64(int D);
+std::vector<pond::Shape> pond_shapes_fp32(int D);
+pond::Shape pond_iter_shape_fp64(int D);
+pond::Shape pond_iter_shape_fp32(int D);

@@ -1,0 +1,87 @@
+// pond_step_impl.cuh -- the member step kernel and its launch handles.  Included
+// only by pond_step_fp64.cu and pond_step_fp32.cu, so that each instantiation
+// exists once.
+#pragma once
+#include "pond_launch.h"
+
+namespace pond {
+
+// Launch k of a chunk: the grid strides over the table's tiles; member i owns
+// tiles [tile_begin_i, tile_begin_i + tiles_i) and advances iff k < steps_i,
+// from buffer (parity_i + k) & 1 into the other, with its own constants and
+// status block.  A one-member table with one CTA per tile is a plain step.
+template <typename R, int DIM, int BX, int BY, int NT, int MINB, bool ITER>
+__global__ void __launch_bounds__(NT, MINB) member_step_kernel(const unsigned char *table, int k) {
+  const TableHdr *H = reinterpret_cast<const TableHdr *>(table);
+  const InstDesc<R> *desc = reinterpret_cast<const InstDesc<R> *>(table + sizeof(TableHdr));
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ StepConst Ks;
+  __shared__ int s_inst;
+  const int n = H->n, total = H->total_tiles;
+  int loaded = -1;
+  for (int t = blockIdx.x; t < total; t += gridDim.x) {
+    if (threadIdx.x == 0) {
+      int lo = 0, hi = n - 1;  // the last member whose first tile is <= t
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (desc[mid].tile_begin <= t) lo = mid;
+        else hi = mid - 1;
+      }
+      s_inst = lo;
+    }
+    __syncthreads();
+    const int i = s_inst;
+    const InstDesc<R> &d = desc[i];
+    if (k < d.steps) {  // the same for every thread of the CTA
+      if (i != loaded) {
+        for (int w = threadIdx.x; w < (int)(sizeof(StepConst) / 4); w += NT)
+          reinterpret_cast<int *>(&Ks)[w] = reinterpret_cast<const int *>(&d.K)[w];
+        __syncthreads();
+        loaded = i;
+      }
+      const int lt = t - d.tile_begin, p = (d.parity + k) & 1;
+      step_tile<R, DIM, BX, BY, NT, ITER>(Ks, d.S[p], d.S[p ^ 1], d.stats, (lt % d.tiles_x) * BX,
+                                          DIM == 2 ? (lt / d.tiles_x) * BY : 0, smem_raw);
+    }
+    __syncthreads();  // s_inst, Ks and the tile's shared memory are reused
+  }
+}
+
+template <typename R, int DIM, int BX, int BY, int NT, int MINB, bool ITER>
+Shape make_shape(int code) {
+  Shape s;
+  s.code = code;
+  s.bx = BX;
+  s.by = BY;
+  s.prepare = [](int *ctas) -> cudaError_t {
+    constexpr size_t smem = Tile<DIM, BX, BY>::template smem_bytes<R>();
+    static_assert(smem + sizeof(StepConst) + 16 <= 227 * 1024, "tile too large for shared memory");
+    cudaError_t e = cudaFuncSetAttribute(member_step_kernel<R, DIM, BX, BY, NT, MINB, ITER>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        ctas, member_step_kernel<R, DIM, BX, BY, NT, MINB, ITER>, NT, smem);
+  };
+  s.launch = [](const unsigned char *table, int k, int grid, cudaStream_t st) {
+    constexpr size_t smem = Tile<DIM, BX, BY>::template smem_bytes<R>();
+    member_step_kernel<R, DIM, BX, BY, NT, MINB, ITER><<<grid, NT, smem, st>>>(table, k);
+  };
+  return s;
+}
+
+// tile codes: 1 = 1D, 252 cells; 2D (x by y): 2 = 8x8, 3 = 16x16, 4 = 16x8,
+// 5 = 8x8 and 6 = 8x16 with registers capped for two CTAs per SM
+template <typename R> std::vector<Shape> all_shapes(int D) {
+  if (D == 1) return {make_shape<R, 1, 252, 1, 256, 1, false>(1)};
+  return {make_shape<R, 2, 8, 8, 160, 1, false>(2), make_shape<R, 2, 16, 16, 256, 1, false>(3),
+          make_shape<R, 2, 16, 8, 256, 1, false>(4), make_shape<R, 2, 8, 8, 160, 2, false>(5),
+          make_shape<R, 2, 8, 16, 160, 2, false>(6)};
+}
+
+// the iterated face frame runs with one tile shape of its own
+template <typename R> Shape iter_shape(int D) {
+  if (D == 1) return make_shape<R, 1, 252, 1, 256, 1, true>(1);
+  return make_shape<R, 2, 8, 8, 160, 1, true>(2);
+}
+
+}  // namespace pond

@@ -31,7 +31,9 @@ EXPORTS = (
     "pond_params_default", "pond_workspace_size", "pond_create", "pond_init", "pond_step",
     "pond_moments", "pond_get_state", "pond_set_state", "pond_status_flags", "pond_reset_flags",
     "pond_sync", "pond_info", "pond_destroy", "pond_strerror", "pond_abi_version",
-    "pond_step_noalloc",
+    "pond_step_noalloc", "pond_tune_default", "pond_batch_create", "pond_batch_add",
+    "pond_batch_remove", "pond_batch_size", "pond_batch_step", "pond_batch_info",
+    "pond_batch_destroy",
 )
 POND_NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 
@@ -47,6 +49,11 @@ class pond_params(ctypes.Structure):
         ("iter_max", ctypes.c_int32), ("xi_fp64_threshold", ctypes.c_double),
         ("tile", ctypes.c_int32),
     ]
+
+
+class pond_tune(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int32), ("graph_steps", ctypes.c_int32),
+                ("autotune", ctypes.c_int32)]
 
 
 class PondError(RuntimeError):
@@ -95,8 +102,23 @@ def lib(build: bool = False):
     L.pond_step_noalloc.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
                                     ctypes.POINTER(pond_params), _P, _P, _P, _P, _P,
                                     ctypes.c_int64, ctypes.POINTER(ctypes.c_uint32), _P]
+    L.pond_tune_default.argtypes = [ctypes.POINTER(pond_tune)]
+    L.pond_tune_default.restype = None
+    L.pond_batch_create.argtypes = [ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.c_int32, ctypes.POINTER(pond_tune), _P]
+    L.pond_batch_add.argtypes = [_P, _P]
+    L.pond_batch_remove.argtypes = [_P, _P]
+    L.pond_batch_size.argtypes = [_P]
+    L.pond_batch_size.restype = ctypes.c_int32
+    L.pond_batch_step.argtypes = [_P, ctypes.POINTER(ctypes.c_int64)]
+    L.pond_batch_info.argtypes = [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                  ctypes.POINTER(ctypes.c_int32), _D]
+    L.pond_batch_destroy.argtypes = [_P]
+    L.pond_batch_destroy.restype = None
+    no_status = ("pond_params_default", "pond_destroy", "pond_strerror", "pond_abi_version",
+                 "pond_tune_default", "pond_batch_size", "pond_batch_destroy")
     for name in EXPORTS:
-        if name not in ("pond_params_default", "pond_destroy", "pond_strerror", "pond_abi_version"):
+        if name not in no_status:
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -228,6 +250,56 @@ def pond_step_noalloc(lat: int, dims, params: pond_params, f, g, ux, uy, T, n: i
     return st, (int(fl.value) if want_flags else None)
 
 
+def pond_tune_default() -> pond_tune:
+    t = pond_tune()
+    lib().pond_tune_default(ctypes.byref(t))
+    return t
+
+
+def pond_batch_create(dim: int, precision: int, capacity: int, tune: pond_tune | None = None,
+                      stream: int | None = None):
+    b = _P()
+    _check(lib().pond_batch_create(ctypes.byref(b), int(dim), int(precision), int(capacity),
+                                   ctypes.byref(tune) if tune is not None else None, stream),
+           "pond_batch_create")
+    return b
+
+
+def pond_batch_add(b, ctx):
+    _check(lib().pond_batch_add(b, ctx), "pond_batch_add")
+
+
+def pond_batch_remove(b, ctx):
+    _check(lib().pond_batch_remove(b, ctx), "pond_batch_remove")
+
+
+def pond_batch_size(b) -> int:
+    return int(lib().pond_batch_size(b))
+
+
+def pond_batch_step(b, steps=None):
+    """steps: one count per member (in the order they were added), or None
+    for one step each."""
+    arr = None
+    if steps is not None:
+        arr = (ctypes.c_int64 * len(steps))(*[int(x) for x in steps])
+    _check(lib().pond_batch_step(b, arr), "pond_batch_step")
+
+
+def pond_batch_info(b):
+    """(tile code, grid CTAs, tuned flag, MLUPS of the tuned chunk)."""
+    tile, grid, tuned = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    ml = ctypes.c_double()
+    _check(lib().pond_batch_info(b, ctypes.byref(tile), ctypes.byref(grid), ctypes.byref(tuned),
+                                 ctypes.byref(ml)), "pond_batch_info")
+    return int(tile.value), int(grid.value), bool(tuned.value), float(ml.value)
+
+
+def pond_batch_destroy(b):
+    if b:
+        lib().pond_batch_destroy(b)
+
+
 # ---- configuration ------------------------------------------------------------
 def params_from_config(cfg: dict) -> pond_params:
     """pond_params from a run-configuration dict (see ``workloads``)."""
@@ -319,6 +391,46 @@ class Sim:
         if getattr(self, "ctx", None):
             pond_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """A pond_batch on a PyTorch stream, holding ``Sim`` members created on
+    the same stream (``Sim(cfg, stream=batch.stream)``)."""
+
+    def __init__(self, dim: int, precision: int, capacity: int, tune: pond_tune | None = None,
+                 stream=None, device=None):
+        import torch
+
+        self.device = torch.device(device or "cuda")
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        self.members = []
+        self.b = pond_batch_create(dim, precision, capacity, tune, self.stream.cuda_stream)
+
+    def add(self, sim: "Sim"):
+        pond_batch_add(self.b, sim.ctx)
+        self.members.append(sim)
+
+    def remove(self, sim: "Sim"):
+        pond_batch_remove(self.b, sim.ctx)
+        self.members.remove(sim)
+
+    def step(self, steps=None):
+        pond_batch_step(self.b, steps)
+
+    def info(self):
+        return pond_batch_info(self.b)
+
+    def close(self):
+        if getattr(self, "b", None):
+            pond_batch_destroy(self.b)
+            self.b = None
+            self.members = []
 
     def __del__(self):
         try:

@@ -1,0 +1,206 @@
+"""Batches (pond_batch_*): many contexts advanced by one persistent kernel.
+A member's state must be bit for bit the state pond_step() gives it alone,
+whatever the other members, their step counts, the chunk length or the tile
+shape the autotuner picks."""
+import numpy as np
+import pytest
+
+from paper_2302_00310_gb300 import pond
+from paper_2302_00310_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pond.lib(build=True)
+    return t
+
+
+def _problems(D, sizes, seed0, precision, **kw):
+    out = []
+    for i, n in enumerate(sizes):
+        nx, ny = (n, n + 3 * i) if D == 2 else (n, 1)
+        prim = W.random_state_grid(D, nx, ny, seed=seed0 + i, mach=0.8)
+        cfg = W._base(D, nx, ny, tau=5e-3, dx=1.0 / nx, prandtl=(0.71, 1.0)[i % 2],
+                      limiter=i % 2, bc=((1, 1, 0, 0), (0, 0, 0, 0), (2, 1, 1, 1))[i % 3],
+                      inflow=((1.1, 0.5, -0.2, 0.8),) * 4, precision=precision, **kw)
+        cfg["dt"] = W.dt_from_cfl(prim[1], prim[2], prim[3], cfg["dx"], 0.4)
+        out.append((cfg, prim))
+    return out
+
+
+def _solo(problems, steps):
+    res = []
+    for (cfg, prim), n in zip(problems, steps):
+        sim = pond.Sim(cfg)
+        sim.init(*prim)
+        sim.step(n)
+        res.append(sim.get_state())
+        sim.close()
+    return res
+
+
+def _batched(torch, problems, steps, D, precision, tune=None, calls=1):
+    b = pond.Batch(D, precision, len(problems) + 2, tune)
+    sims = []
+    for cfg, prim in problems:
+        s = pond.Sim(cfg, stream=b.stream)
+        s.init(*prim)
+        b.add(s)
+        sims.append(s)
+    left = list(steps)
+    for c in range(calls):
+        now = [x // (calls - c) for x in left]
+        b.step(now)
+        left = [x - y for x, y in zip(left, now)]
+    out = [s.get_state() for s in sims]
+    info = b.info()
+    flags = [s.flags() for s in sims]
+    b.close()
+    for s in sims:
+        s.close()
+    return out, info, flags
+
+
+@pytest.mark.parametrize("D,precision", [(2, pond.POND_FP64), (2, pond.POND_FP32_MIXED),
+                                         (1, pond.POND_FP64), (1, pond.POND_FP32_MIXED)])
+def test_batch_equals_solo_bitwise(torch, D, precision):
+    sizes = [37, 20, 64, 45, 29] if D == 2 else [300, 1000, 257, 64, 700]
+    probs = _problems(D, sizes, 80, precision)
+    steps = [3, 8, 17, 0, 11]
+    tune = pond.pond_tune_default()
+    tune.graph_steps = 4
+    tune.autotune = 0
+    ref = _solo(probs, steps)
+    got, info, _ = _batched(torch, probs, steps, D, precision, tune, calls=2)
+    for a, b in zip(got, ref):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("precision", [pond.POND_FP64, pond.POND_FP32_MIXED])
+def test_autotuner_times_real_steps(torch, precision):
+    """The autotuner runs one chunk per candidate shape on the members' own
+    steps and keeps the fastest; the states are still the solo states."""
+    probs = _problems(2, [48, 33, 40], 90, precision)
+    steps = [40, 40, 52]
+    tune = pond.pond_tune_default()
+    tune.graph_steps = 4
+    ref = _solo(probs, steps)
+    got, (tile, grid, tuned, mlups), _ = _batched(torch, probs, steps, 2, precision, tune)
+    assert tuned and tile in (3, 4, 6) and grid >= 152 and mlups > 0
+    for a, b in zip(got, ref):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+
+
+def test_members_join_and_leave_between_calls(torch):
+    probs = _problems(2, [24, 31, 40], 100, pond.POND_FP32_MIXED)
+    tune = pond.pond_tune_default()
+    tune.graph_steps = 4
+    tune.autotune = 0
+    ref = _solo(probs, [9, 5, 6])
+    b = pond.Batch(2, pond.POND_FP32_MIXED, 4, tune)
+    sims = []
+    for cfg, prim in probs:
+        s = pond.Sim(cfg, stream=b.stream)
+        s.init(*prim)
+        sims.append(s)
+    b.add(sims[0])
+    b.step([4])
+    b.add(sims[1])
+    b.step([3, 5])           # member 0 at 7, member 1 at 5
+    b.remove(sims[1])
+    b.add(sims[2])
+    b.step([2, 6])           # member 0 at 9, member 2 at 6
+    assert pond.pond_batch_size(b.b) == 2
+    got = [s.get_state() for s in sims]
+    b.close()
+    for s in sims:
+        s.close()
+    for a, r in zip(got, ref):
+        for x, y in zip(a, r):
+            assert np.array_equal(x, y)
+
+
+def test_flags_stay_with_their_member(torch):
+    good = _problems(2, [20], 110, pond.POND_FP64)[0]
+    n = 16
+    rho = np.ones((n, n))
+    rho[3, 4] = -0.5
+    bad_cfg = W._base(2, n, n, tau=1e-3, dx=1.0 / n, bc=(0, 0, 0, 0))
+    bad_cfg["dt"] = 1e-3
+    b = pond.Batch(2, pond.POND_FP64, 2)
+    s1 = pond.Sim(good[0], stream=b.stream)
+    s1.init(*good[1])
+    s2 = pond.Sim(bad_cfg, stream=b.stream)
+    s2.init(rho, np.zeros((n, n)), np.zeros((n, n)), np.ones((n, n)))
+    b.add(s1)
+    b.add(s2)
+    b.step([2, 2])
+    f1, f2 = s1.flags(), s2.flags()
+    b.close()
+    s1.close()
+    s2.close()
+    assert f1[0] == pond.POND_OK and f2[0] == pond.POND_E_NONPHYSICAL
+
+
+def test_members_that_do_not_fit_are_rejected(torch):
+    b = pond.Batch(2, pond.POND_FP32_MIXED, 1)
+    cfg, prim = _problems(2, [16], 120, pond.POND_FP64)[0]
+    s64 = pond.Sim(cfg, stream=b.stream)
+    s64.init(*prim)
+    other = pond.Sim(dict(cfg, precision=pond.POND_FP32_MIXED))  # its own stream
+    other.init(*prim)
+    it = pond.Sim(dict(cfg, precision=pond.POND_FP32_MIXED, iterative=1), stream=b.stream)
+    it.init(*prim)
+    ok = pond.Sim(dict(cfg, precision=pond.POND_FP32_MIXED), stream=b.stream)
+    ok.init(*prim)
+    for s in (s64, other, it):
+        with pytest.raises(pond.PondError) as e:
+            b.add(s)
+        assert e.value.status == pond.POND_E_INVAL
+    b.add(ok)
+    extra = pond.Sim(dict(cfg, precision=pond.POND_FP32_MIXED), stream=b.stream)
+    extra.init(*prim)
+    with pytest.raises(pond.PondError) as e:  # capacity 1
+        b.add(extra)
+    assert e.value.status == pond.POND_E_INVAL
+    extra.close()
+    ok.close()  # leaves the batch
+    assert pond.pond_batch_size(b.b) == 0
+    b.step()
+    b.close()
+    for s in (s64, other, it):
+        s.close()
+
+
+def test_shock_bubble_batch_mixed_vs_fp64(torch):
+    """Shock-bubble instances (Mach 1.5-5, density ratio 0.1-10, inflow):
+    the FP32 batch against FP64 solo runs, L1 relative density <= 1e-3."""
+    ws = [W.shock_bubble_2d(seed=s, n=n) for s, n in ((0, 64), (1, 96), (2, 80), (3, 72))]
+    b = pond.Batch(2, pond.POND_FP32_MIXED, len(ws))
+    sims = []
+    for w in ws:
+        s = pond.Sim(dict(w["cfg"], precision=pond.POND_FP32_MIXED), stream=b.stream)
+        s.init(w["rho"], w["ux"], w["uy"], w["T"])
+        b.add(s)
+        sims.append(s)
+    b.step([100] * len(ws))
+    m32 = [s.moments() for s in sims]
+    fl = [s.flags()[1] for s in sims]
+    b.close()
+    for s in sims:
+        s.close()
+    for w, m, f in zip(ws, m32, fl):
+        assert not f & pond.POND_FLAG_NONPHYSICAL
+        ref = pond.Sim(w["cfg"])
+        ref.init(w["rho"], w["ux"], w["uy"], w["T"])
+        ref.step(100)
+        r64 = ref.moments()[0]
+        ref.close()
+        assert np.sum(np.abs(m[0] - r64)) / np.sum(r64) <= 1e-3

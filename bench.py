@@ -1,17 +1,32 @@
 """Benchmark of the GB300 PonD time step.
 
-Workload (one bench step = one PonD time step over the whole grid): the 2D
-periodic advected Gaussian density/temperature pulse, D2Q16 (f) + D2Q9 (g),
-256 x 256 cells, background Mach 2 at 30 degrees, amplitude 0.1, seeded
-centre/width, FP64 populations, BGK, dt from CFL 0.2 (1000 steps is the full
-run).  Metric: MLUPS = cells x steps / seconds / 1e6.
+Main line (``value``): the 2D periodic advected Gaussian density/temperature
+pulse, D2Q16 (f) + D2Q9 (g), 256 x 256 cells, background Mach 2 at 30 deg,
+amplitude 0.1, seeded centre/width, FP64, BGK, dt from CFL 0.2: one bench
+step = one PonD time step of the grid (1000 make the full run).  Metric:
+MLUPS = cells x steps / seconds / 1e6.
 
 Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events
 on the context's stream; the L2 cache (129 MB, larger than the 29 MB state)
-is flushed by a 256 MiB write between timed steps, outside the events.
+is flushed between timed steps, outside the events: a 256 MiB buffer is
+written and another 256 MiB buffer read (so the step also does not pay for
+the write-back of the flush's dirty lines).
 ``e2e`` repeats the run through the public C ABI with host buffers: pond_init
-from pinned host arrays, then per step pond_step(1) + pond_moments into pinned
-host arrays, wall-clock timed.
+from pinned host arrays, then per step pond_step(1) + pond_moments into
+pinned host arrays, wall-clock timed.
+
+The other forms the metric compares are measured in the same run
+(``--no-extras`` skips them):
+  * ``mixed``: the same pulse on the mixed path (FP32 + FP64 moments), with
+    the L1 / Linf relative density error against the FP64 path after the
+    full 1000-step run;
+  * ``batched``: 64 shock-bubble instances of seeded sizes 64^2-512^2 (about
+    4.07M cells), Mach 1.5-5, Pr 0.71, advanced by the persistent batch
+    kernel (autotuned), FP32-mixed and FP64, with the L1 error of the mixed
+    batch against the FP64 batch after 100 steps;
+  * ``serve``: a Poisson stream of 1D tubes and 2D shock-bubble problems at
+    200 requests/s through the continuous-batching server, p50/p99 time to
+    solution and aggregate MLUPS.
 
 Under torchrun (N > 1) every rank runs an independent replica (the grid is
 not sharded; there is no collective on the data path) and ``value`` is the
@@ -24,7 +39,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -41,19 +55,22 @@ if ROOT not in sys.path:
 METRIC = "MLUPS per GB300 (FP32 batched vs FP64 plain, stated L1 err); serve p50/p99 latency"
 UNIT = "MLUPS"
 WORKLOAD = "2D periodic advected Gaussian pulse, D2Q16+D2Q9, 256x256, Mach 2 at 30 deg, FP64, BGK"
-# FP64 work of one cell update of the 2D FP64 step (flops, an FMA counting 2):
-# 2 DFMA + DADD + DMUL thread instructions per launch / cells, counted by ncu
-# on this workload (profiles/step_kernel_fp64_pulse256.md); the analytic count
-# per phase is in the design notes.  Bytes one cell update must move: the
-# state read once and written once, 28 doubles each way.
-FLOPS_PER_CELL_2D_FP64 = 11656.5
-BYTES_PER_CELL_2D_FP64 = 2 * 28 * 8
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # 2 FP64 FMA/clk/SM at 2070 MHz
-# dram__bytes_read.sum + dram__bytes_write.sum of one step-kernel launch, keyed
-# by the digest of the CUDA sources it was captured from (null once they change)
-TRAFFIC_BY_DIGEST = {
-    "4c37b29d0b1e0bed4d0de8fa34da26004ca0587081a332f2530188e9370f89b1": 15382016,
+# Per-cell-update work of the step kernel on this workload, FP64 flops (an FMA
+# counting 2) and FP32 flops for the mixed path: 2 FMA + ADD + MUL thread
+# instructions per launch / cells, counted by ncu for the build whose source
+# digest is the key; profiles/ holds the captures.  None: not yet counted for
+# the current sources.
+FLOPS_PER_CELL = {
+    # digest: {"fp64": ..., "fp32": ..., "fp32_fp64part": ...}
 }
+BYTES_PER_CELL_FP64 = 2 * 28 * 8          # state read once + written once
+BYTES_PER_CELL_FP32 = 2 * 28 * 4
+CLOCK_MAX_GHZ = 2.07
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * CLOCK_MAX_GHZ / 1e3     # 2 FP64 FMA/clk/SM
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * CLOCK_MAX_GHZ / 1e3   # 128 FP32 FMA/clk/SM
+# dram__bytes_read.sum + dram__bytes_write.sum of one main-line step launch,
+# keyed by source digest (None once the sources change)
+TRAFFIC_BY_DIGEST = {}
 
 
 def _build_digest():
@@ -133,8 +150,7 @@ def _dist():
         return None, 0, 1
     import torch.distributed as dist
 
-    backend = "nccl"
-    dist.init_process_group(backend=backend)
+    dist.init_process_group(backend="nccl")
     return dist, dist.get_rank(), ws
 
 
@@ -178,48 +194,179 @@ def run_reference(args, rank, ws):
     print(json.dumps(line), flush=True)
 
 
+def _time_steps(torch, pond, sim, steps, flush=None):
+    """Per-step CUDA-event times (ms) of `steps` single steps on the context
+    stream.  flush: a pair of device buffers larger than L2; before each timed
+    step the first is written and the second read, so that the step starts
+    with a cold and clean L2 (the write alone would leave dirty lines whose
+    write-back lands inside the timed step)."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    stream = sim.stream
+    with torch.cuda.stream(stream):
+        for i in range(steps):
+            if flush is not None:
+                flush[0].zero_()  # L2 flush, outside the timed events
+                flush[2].copy_(flush[1].sum(dtype=torch.int64))
+            ev[i][0].record(stream)
+            pond.pond_step(sim.ctx, 1)
+            ev[i][1].record(stream)
+    stream.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def _l1(a, b):
+    return float(np.sum(np.abs(a - b)) / np.sum(np.abs(b)))
+
+
+def _linf(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def _roofline(flops_key, cells, per_launch_s, peak_tflops, bytes_per_cell, kernel, digest,
+              precision_note):
+    counts = FLOPS_PER_CELL.get(digest, {})
+    fpc = counts.get(flops_key)
+    hbm_peak = _measured_peaks().get("hbm_gbs", 6652.0)
+    out = {"bound": "alu", "unit": "TFLOP/s", "peak": peak_tflops,
+           "peak_source": precision_note, "kernel": kernel, "flops_per_cell": fpc,
+           "achieved": None, "frac": None,
+           "traffic": TRAFFIC_BY_DIGEST.get(digest) if flops_key == "fp64" else None,
+           "hbm": {"achieved_gbs": bytes_per_cell * cells / per_launch_s / 1e9, "peak_gbs": hbm_peak}}
+    out["hbm"]["frac"] = out["hbm"]["achieved_gbs"] / hbm_peak
+    if fpc:
+        out["achieved"] = fpc * cells / per_launch_s / 1e12
+        out["frac"] = out["achieved"] / peak_tflops
+    return out
+
+
+def bench_mixed(torch, pond, W, flush):
+    """The pulse on the mixed path: MLUPS and the error of the full run."""
+    w = W.pulse_2d(n=256, seed=0)
+    fields = (w["rho"], w["ux"], w["uy"], w["T"])
+    n = w["cfg"]["nx"] * w["cfg"]["ny"]
+    sim = pond.Sim(dict(w["cfg"], precision=pond.POND_FP32_MIXED))
+    sim.init(*fields)
+    _time_steps(torch, pond, sim, 5)
+    ms = _time_steps(torch, pond, sim, 200, flush)
+    sim.init(*fields)
+    sim.step(w["steps"])
+    m32 = sim.moments()
+    fl32 = sim.flags()[1]
+    tile = sim.info()[2]
+    sim.close()
+    ref = pond.Sim(w["cfg"])
+    ref.init(*fields)
+    ref.step(w["steps"])
+    m64 = ref.moments()
+    ref.close()
+    per = sum(ms) / len(ms) * 1e-3
+    return {
+        "workload": "256x256 pulse as the main line, POND_FP32_MIXED, tile %d" % tile,
+        "value": n / per / 1e6, "unit": UNIT, "ms_per_step": per * 1e3,
+        "l1_rho_vs_fp64": _l1(m32[0], m64[0]), "linf_rho_vs_fp64": _linf(m32[0], m64[0]),
+        "l1_T_vs_fp64": _l1(m32[3], m64[3]), "error_after_steps": w["steps"],
+        "mass_drift": float(m32[0].sum() / m64[0].sum() - 1.0), "nonphysical": bool(fl32 & 1),
+        "stated_l1_bound": 1e-5,
+        "roofline": _roofline("fp32", n, per, FP32_PEAK_TFLOPS, BYTES_PER_CELL_FP32,
+                              "pond::member_step_kernel<float,2,8,16,160,2,false>", _build_digest(),
+                              "FP32: 128 FMA/clk/SM x 152 SMs x 2070 MHz (nominal 80.5 TFLOP/s)"),
+    }
+
+
+def bench_batched(torch, pond, W):
+    """64 shock-bubble instances through the persistent batch kernel."""
+    ws_ = [W.shock_bubble_2d(seed=s) for s in range(64)]
+    cells = sum(w["cfg"]["nx"] * w["cfg"]["ny"] for w in ws_)
+    out = {"workload": "64 shock-bubble instances, sides %d-%d (log-uniform seeded), Mach 1.5-5, "
+                       "bubble density ratio 0.1-10, Pr 0.71, minmod, inflow left" %
+                       (min(w["cfg"]["nx"] for w in ws_), max(w["cfg"]["nx"] for w in ws_)),
+           "instances": len(ws_), "cells": cells, "unit": UNIT}
+    moments = {}
+    for prec, name, steps in ((pond.POND_FP32_MIXED, "fp32_mixed", 100), (pond.POND_FP64, "fp64", 20)):
+        tune = pond.pond_tune_default()
+        tune.graph_steps = 8
+        b = pond.Batch(2, prec, len(ws_), tune)
+        sims = []
+        for w in ws_:
+            s = pond.Sim(dict(w["cfg"], precision=prec), stream=b.stream)
+            s.init(w["rho"], w["ux"], w["uy"], w["T"])
+            b.add(s)
+            sims.append(s)
+        b.step([24] * len(ws_))       # the autotuner's chunks (3 shapes x 8 steps)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(b.stream)
+        b.step([steps] * len(ws_))
+        e1.record(b.stream)
+        b.stream.synchronize()
+        ms = e0.elapsed_time(e1)
+        tile, grid, tuned, _ = b.info()
+        b.step([200 - 24 - steps] * len(ws_))   # to step 200 for the error statement
+        b.stream.synchronize()
+        moments[name] = [s.moments()[0] for s in sims]
+        nonphys = sum(1 for s in sims if s.flags()[1] & 1)
+        b.close()
+        for s in sims:
+            s.close()
+        out[name] = {"value": cells * steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / steps,
+                     "tile": tile, "grid": grid, "autotuned": tuned, "nonphysical": nonphys,
+                     "timed_steps": steps}
+    num = sum(float(np.sum(np.abs(a - b))) for a, b in zip(moments["fp32_mixed"], moments["fp64"]))
+    den = sum(float(np.sum(np.abs(b))) for b in moments["fp64"])
+    out["l1_rho_fp32_vs_fp64"] = num / den
+    out["error_after_steps"] = 200
+    out["stated_l1_bound"] = 1e-3
+    out["speedup_fp32_batched_vs_fp64"] = out["fp32_mixed"]["value"] / out["fp64"]["value"]
+    return out
+
+
+def bench_serve(pond, serve_mod, n_requests=24, rate=200.0):
+    reqs = serve_mod.make_requests(n_requests, rate=rate, seed=0)
+    ex = serve_mod.PondExecutor(precision=pond.POND_FP32_MIXED, capacity=64, graph_steps=8)
+    srv = serve_mod.Server(ex, budget_bytes=16 << 30, tick_steps=64)
+    out = srv.run(reqs)
+    ex.close()
+    s = serve_mod.summary(out)
+    s.update({"workload": "Poisson stream at %g req/s: D1Q4 Sod-type tubes (256-8192 cells) and "
+                          "D2Q16 shock-bubble runs (128^2-1024^2), 500-5000 steps each, FP32-mixed"
+                          % rate,
+              "sample": "%d requests (%d 2D)" % (n_requests, sum(1 for r in out if r.dim == 2)),
+              "budget_gb": 16 << 30 >> 30, "peak_resident_gb": srv.peak_bytes / 1e9,
+              "ticks": srv.ticks, "tick_steps": 64})
+    return s
+
+
 def run_gpu(args, dist, rank, ws):
     import torch
 
     from paper_2302_00310_gb300 import pond
+    from paper_2302_00310_gb300 import serve as serve_mod
     from paper_2302_00310_gb300 import workloads as W
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     pond.lib(build=True)
     w = W.pulse_2d(n=256, seed=0)
-    cfg = dict(w["cfg"])
+    fp32 = args.precision == "fp32"
+    cfg = dict(w["cfg"], precision=pond.POND_FP32_MIXED if fp32 else pond.POND_FP64)
     n = cfg["nx"] * cfg["ny"]
     sim = pond.Sim(cfg)
-    stream = sim.stream
     sim.init(w["rho"], w["ux"], w["uy"], w["T"])
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-
-    # warm-up
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            pond.pond_step(sim.ctx, 1)
-    stream.synchronize()
-
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
+    tile = sim.info()[2]
+    flush = (torch.empty(256 << 20, dtype=torch.uint8, device="cuda"),
+             torch.zeros(256 << 20, dtype=torch.uint8, device="cuda"),
+             torch.zeros((), dtype=torch.int64, device="cuda"))
+    _time_steps(torch, pond, sim, args.warmup)
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         t_wall = time.perf_counter()
-        with torch.cuda.stream(stream):
-            for i in range(args.steps):
-                flush.zero_()  # L2 flush, outside the timed events
-                ev[i][0].record(stream)
-                pond.pond_step(sim.ctx, 1)
-                ev[i][1].record(stream)
-        stream.synchronize()
+        kernel_ms = _time_steps(torch, pond, sim, args.steps, flush)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
     if dist is not None:
         dist.barrier()
-    kernel_ms = [a.elapsed_time(b) for a, b in ev]
     sum_ms = float(sum(kernel_ms))
     st, flags, max_cfl, _ = sim.flags()
 
@@ -238,6 +385,12 @@ def run_gpu(args, dist, rank, ws):
     e2e_s = time.perf_counter() - t0
     sim.close()
 
+    extras = {}
+    if not args.no_extras and rank == 0:
+        extras["mixed"] = bench_mixed(torch, pond, W, flush)
+        extras["batched"] = bench_batched(torch, pond, W)
+        extras["serve"] = bench_serve(pond, serve_mod)
+
     if dist is not None:
         t = torch.tensor([sum_ms, e2e_s], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -247,33 +400,36 @@ def run_gpu(args, dist, rank, ws):
     mlups = n * args.steps * ws / (sum_ms * 1e-3) / 1e6
     e2e = n * args.steps * ws / e2e_s / 1e6
     per_launch_s = sum_ms * 1e-3 / args.steps
-    achieved = FLOPS_PER_CELL_2D_FP64 * n / per_launch_s / 1e12
+    digest = _build_digest()
+    if fp32:
+        roof = _roofline("fp32", n, per_launch_s, FP32_PEAK_TFLOPS, BYTES_PER_CELL_FP32,
+                         "pond::member_step_kernel<float,2,8,16,160,2,false>", digest,
+                         "FP32: 128 FMA/clk/SM x 152 SMs x 2070 MHz (nominal 80.5 TFLOP/s)")
+    else:
+        roof = _roofline("fp64", n, per_launch_s, FP64_PEAK_TFLOPS, BYTES_PER_CELL_FP64,
+                         "pond::member_step_kernel<double,2,8,16,160,2,false>", digest,
+                         "FP64: 2 FMA/clk/SM x 152 SMs x 2070 MHz (nominal 1.26 TFLOP/s)")
     line = {
         "metric": METRIC, "value": mlups, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": sum_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "cells": n, "dt": cfg["dt"], "tau": cfg["tau"],
-                   "precision": "fp64", "transform": "tensor", "limiter": "vanleer",
-                   "l2": "flushed (256 MiB write) between timed steps",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if fp32 else "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD.replace("FP64", "FP32-mixed") if fp32 else WORKLOAD,
+                   "cells": n, "dt": cfg["dt"], "tau": cfg["tau"],
+                   "precision": args.precision, "transform": "tensor", "limiter": "vanleer",
+                   "tile": tile, "l2": "flushed between timed steps (256 MiB written, then another 256 MiB read)",
                    "parallelism": "replicas" if ws > 1 else "single"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                     "traffic": TRAFFIC_BY_DIGEST.get(_build_digest()),
-                     "kernel": "pond::step_kernel<double,2,8,8,160>",
-                     "flops_per_cell": FLOPS_PER_CELL_2D_FP64,
-                     "peak_source": "FP64: 2 FMA/clk/SM x 152 SMs x 2070 MHz (nominal 1.25 TFLOP/s)",
-                     "hbm": {"achieved_gbs": BYTES_PER_CELL_2D_FP64 * n / per_launch_s / 1e9,
-                             "peak_gbs": _measured_peaks().get("hbm_gbs", 6652.0)}},
+        "roofline": roof,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 4 * n * 8 / args.steps,
                 "d2h_bytes_per_step": 4 * n * 8},
         "gpu_launches": args.steps,
         "status_flags": flags, "max_cfl": max_cfl,
         "wall_s": t_wall,
     }
-    line["roofline"]["hbm"]["frac"] = line["roofline"]["hbm"]["achieved_gbs"] / line["roofline"]["hbm"]["peak_gbs"]
     clocks = clk.summary()
     if clocks:
         line["clocks"] = clocks
+    line.update(extras)
     if ws == 1 and not args.no_cpu_baseline:
         rate, done, el, thr = _oracle_rate(cfg, (w["rho"], w["ux"], w["uy"], w["T"]), 256, 30,
                                           budget_s=10.0)
@@ -285,10 +441,14 @@ def run_gpu(args, dist, rank, ws):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="main line only (no mixed, batched or served measurements)")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
+                    help="arithmetic of the main line (fp32 = the mixed path)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -122,7 +122,8 @@ typedef struct {
   int32_t tile;            /* cells per CTA of the step kernel: 0 automatic
                               (1D: 1, 2D: 6); 1D: 1 = 252 cells; 2D (x by y):
                               2 = 8x8, 3 = 16x16, 4 = 16x8, 5 = 8x8 and 6 = 8x16
-                              with registers capped for two CTAs per SM.  The
+                              with registers capped for two CTAs per SM, 7 = 8x16
+                              and 8 = 8x8 capped for three CTAs per SM.  The
                               iterated face frame runs 8x8 (2D) / 252 (1D).
                               Results do not depend on the tile.               */
 } pond_params;

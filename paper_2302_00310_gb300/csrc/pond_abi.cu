@@ -191,7 +191,7 @@ bool valid_params(const pond_params *p) {
   if (p->flux_frame != POND_FRAME_AVG && p->flux_frame != POND_FRAME_ITER) return false;
   if (p->flux_frame == POND_FRAME_ITER && (!(p->iter_tol > 0.0) || p->iter_max < 1)) return false;
   if (!(p->xi_fp64_threshold > 0.0)) return false;
-  if (p->tile < 0 || p->tile > 6) return false;
+  if (p->tile < 0 || p->tile > 8) return false;
   return true;
 }
 
@@ -227,6 +227,16 @@ void set_step_const(pond_ctx *c) {
   K.limiter = p.limiter;
   K.iterative = p.flux_frame == POND_FRAME_ITER;
   K.xi_thr = (float)p.xi_fp64_threshold;
+  K.cf.lam = (float)K.lam;
+  K.cf.kappa1 = (float)K.kappa1;
+  K.cf.kr = (float)K.kr;
+  K.cf.kp_a = (float)K.kp_a;
+  K.cf.kp_b = (float)K.kp_b;
+  K.cf.a1 = (float)K.a1;
+  K.cf.a2 = (float)K.a2;
+  K.cf.qe = (float)K.qe;
+  K.cf.inv_cv = (float)K.inv_cv;
+  K.cf.gfac = (float)K.gfac;
 }
 
 void drop_graphs(pond_ctx *c) {

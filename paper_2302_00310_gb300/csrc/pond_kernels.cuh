@@ -51,7 +51,16 @@ struct StepConst {
   int iter_max;
   int grad_k, appc, limiter, iterative;
   float xi_thr;         // mixed path: FP64 frame transformation when max_j |a c_j + b| exceeds this
+  // FP32 copies of the coefficients above for the mixed path (no conversion in the kernel)
+  struct {
+    float lam, kappa1, kr, kp_a, kp_b, a1, a2, qe, inv_cv, gfac;
+  } cf;
 };
+
+// A coefficient of the run in the arithmetic type R.
+template <typename R> __device__ __forceinline__ R kc(double d, float f);
+template <> __device__ __forceinline__ double kc<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float kc<float>(double, float f) { return f; }
 
 // State planes (SoA, x fastest): f[a + 4b][N] and g[a + 3b][N] are the
 // Hermite coefficients A_ab of phi~ (g: B_ab) in the cell's frame (ux, uy, T).
@@ -168,6 +177,26 @@ __device__ __forceinline__ R limit(R x, R y, int lim) {
 // The FP32 instantiation is the mixed-precision path (POND_FP32_MIXED).
 template <typename R> constexpr bool is_mixed() { return std::is_same<R, float>::value; }
 
+// The FP64 form of move_frame() for the mixed path, kept out of line: it is
+// rarely taken, and one shared copy keeps the FP32 kernel's hot code compact.
+template <int DIM, int Q>
+__device__ __noinline__ void move_frame_fp64(float usx, float usy, float Ts, float utx, float uty,
+                                             float Tt, Blk<float, Q, (DIM == 2 ? Q : 1)> &Y) {
+  constexpr int NY = DIM == 2 ? Q : 1;
+  Blk<double, Q, NY> Z;
+#pragma unroll
+  for (int n = 0; n < Q; ++n)
+#pragma unroll
+    for (int m = 0; m < NY; ++m) Z.v[n][m] = Y.v[n][m];
+  const double isT = 1.0 / sqrt((double)Tt), a64 = sqrt((double)Ts) * isT;
+  shift_x(make_shift(a64, ((double)usx - (double)utx) * isT), Z);
+  if constexpr (DIM == 2) shift_y(make_shift(a64, ((double)usy - (double)uty) * isT), Z);
+#pragma unroll
+  for (int n = 0; n < Q; ++n)
+#pragma unroll
+    for (int m = 0; m < NY; ++m) Y.v[n][m] = (float)Z.v[n][m];
+}
+
 // Moves Hermite coefficients Y (Q nodes per axis) from the frame {us, Ts} to
 // {ut, Tt} (Sec. II.B): per axis the Hermite shift C(a, b) with
 // a = sqrt(Ts/Tt), b = (us - ut)/sqrt(Tt); sTs = sqrt(Ts) and
@@ -182,18 +211,7 @@ __device__ __forceinline__ void move_frame(const StepConst &K, R usx, R usy, R T
   const R by = DIM == 2 ? (usy - uty) * isTt : R(0);
   if constexpr (is_mixed<R>()) {
     if (a * R(Nodes<Q>::cmax) + fmaxf(fabsf(bx), fabsf(by)) > K.xi_thr) {
-      Blk<double, Q, NY> Z;
-#pragma unroll
-      for (int n = 0; n < Q; ++n)
-#pragma unroll
-        for (int m = 0; m < NY; ++m) Z.v[n][m] = Y.v[n][m];
-      const double isT = 1.0 / sqrt((double)Tt), a64 = sqrt((double)Ts) * isT;
-      shift_x(make_shift(a64, ((double)usx - (double)utx) * isT), Z);
-      if constexpr (DIM == 2) shift_y(make_shift(a64, ((double)usy - (double)uty) * isT), Z);
-#pragma unroll
-      for (int n = 0; n < Q; ++n)
-#pragma unroll
-        for (int m = 0; m < NY; ++m) Y.v[n][m] = (R)Z.v[n][m];
+      move_frame_fp64<DIM, Q>(usx, usy, Ts, utx, uty, Tt, Y);
       return;
     }
   }
@@ -221,8 +239,8 @@ __device__ __forceinline__ void prep_cell(const StepConst &K, const State<R> &S,
     ux = S.ux[c];
     uy = DIM == 2 ? S.uy[c] : R(0);
     T = S.T[c];
-    qe_scale(F, G, R(K.qe));
-    const R rho = F.v[0][0], ka = R(K.kp_a);
+    qe_scale(F, G, kc<R>(K.qe, K.cf.qe));
+    const R rho = F.v[0][0], ka = kc<R>(K.kp_a, K.cf.kp_a);
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -232,8 +250,8 @@ __device__ __forceinline__ void prep_cell(const StepConst &K, const State<R> &S,
 #pragma unroll
       for (int b = 0; b < D::NYG; ++b) G.v[a][b] *= ka;
     // phi_bar^+ = kp_a phi~ + kp_b phi^eq; phi^eq = rho W (f), (C_v - D/2) T rho W (g)
-    F.v[0][0] = R(K.kappa1) * rho;
-    G.v[0][0] += R(K.kp_b) * R(K.gfac) * T * rho;
+    F.v[0][0] = kc<R>(K.kappa1, K.cf.kappa1) * rho;
+    G.v[0][0] += kc<R>(K.kp_b, K.cf.kp_b) * kc<R>(K.gfac, K.cf.gfac) * T * rho;
   } else {
     const R rho = R(K.inflow[side][0]);
     ux = R(K.inflow[side][1]);
@@ -247,8 +265,8 @@ __device__ __forceinline__ void prep_cell(const StepConst &K, const State<R> &S,
     for (int a = 0; a < 3; ++a)
 #pragma unroll
       for (int b = 0; b < D::NYG; ++b) G.v[a][b] = R(0);
-    F.v[0][0] = R(K.kappa1) * rho;
-    G.v[0][0] = R(K.kappa1) * R(K.gfac) * T * rho;
+    F.v[0][0] = kc<R>(K.kappa1, K.cf.kappa1) * rho;
+    G.v[0][0] = kc<R>(K.kappa1, K.cf.kappa1) * kc<R>(K.gfac, K.cf.gfac) * T * rho;
   }
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -268,8 +286,8 @@ __device__ __forceinline__ void prep_cell(const StepConst &K, const State<R> &S,
 // phi_bar^+ of halo cell h (times kappa1) moved into the face frame and
 // synthesised into populations Y[x-node][y-node].
 template <typename R, int DIM, int Q>
-__device__ __forceinline__ void stencil_pops(const StepConst &K, const R *sp, int NH, int h, R uFx,
-                                             R uFy, R TF, R isTF, Blk<R, Q, (DIM == 2 ? Q : 1)> &Y) {
+__device__ __forceinline__ void stencil_pops_body(const StepConst &K, const R *sp, int NH, int h, R uFx,
+                                                  R uFy, R TF, R isTF, Blk<R, Q, (DIM == 2 ? Q : 1)> &Y) {
   using D = Dims<DIM>;
   constexpr int NY = DIM == 2 ? Q : 1;
   constexpr int base = Q == 4 ? 0 : D::QF;
@@ -285,6 +303,21 @@ __device__ __forceinline__ void stencil_pops(const StepConst &K, const R *sp, in
   syn_x(Y);
   syn_y(Y);
 }
+// The mixed path calls one out-of-line copy of the stencil transformation per
+// lattice (16 call sites per face direction): the FP32 kernel is bound by
+// instruction fetch, not arithmetic, and the shared copy keeps its code
+// footprint small.  The FP64 kernel, bound by the FP64 pipe, inlines it.
+template <typename R, int DIM, int Q>
+__device__ __noinline__ void stencil_pops_call(const StepConst &K, const R *sp, int NH, int h, R uFx,
+                                               R uFy, R TF, R isTF, Blk<R, Q, (DIM == 2 ? Q : 1)> &Y) {
+  stencil_pops_body<R, DIM, Q>(K, sp, NH, h, uFx, uFy, TF, isTF, Y);
+}
+template <typename R, int DIM, int Q>
+__device__ __forceinline__ void stencil_pops(const StepConst &K, const R *sp, int NH, int h, R uFx,
+                                             R uFy, R TF, R isTF, Blk<R, Q, (DIM == 2 ? Q : 1)> &Y) {
+  if constexpr (is_mixed<R>()) stencil_pops_call<R, DIM, Q>(K, sp, NH, h, uFx, uFy, TF, isTF, Y);
+  else stencil_pops_body<R, DIM, Q>(K, sp, NH, h, uFx, uFy, TF, isTF, Y);
+}
 
 // Limited half-step MUSCL trace of the populations of one lattice (Q nodes
 // per axis) to the face (Eq. eq:InterfacePop).  st[] = halo indices of the
@@ -299,7 +332,8 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
                                             Blk<R, Q, (DIM == 2 ? Q : 1)> &out) {
   constexpr int NY = DIM == 2 ? Q : 1;
   const R uFn = DIRN == 0 ? uFx : uFy, uFt = DIRN == 0 ? uFy : uFx;
-  const R hl = R(0.5) * R(K.lam);
+  const R hl = R(0.5) * kc<R>(K.lam, K.cf.lam);
+  const int lim = K.limiter;
   bool up[Q];
   R offn[Q], offt[Q];
 #pragma unroll
@@ -326,7 +360,7 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
         const R b = up[k] ? Y1.v[n][m] : Y2.v[n][m];
         const R c = up[k] ? YR.v[n][m] : YL.v[n][m];
         A.v[n][m] = a;
-        out.v[n][m] = a + offn[k] * limit(a - b, c - a, K.limiter);
+        out.v[n][m] = a + offn[k] * limit(a - b, c - a, lim);
       }
   }
   if constexpr (DIM == 2) {
@@ -348,7 +382,7 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
       for (int m = 0; m < NY; ++m) {
         const int k = DIRN == 0 ? n : m, kt = DIRN == 0 ? m : n;
         const R hi = up[k] ? Y1.v[n][m] : Y2.v[n][m];
-        out.v[n][m] += offt[kt] * limit(Dl.v[n][m], hi - A.v[n][m], K.limiter);
+        out.v[n][m] += offt[kt] * limit(Dl.v[n][m], hi - A.v[n][m], lim);
       }
   }
 }
@@ -403,7 +437,7 @@ __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int N
     R S2 = Fb.v[2][0] + R(DIM) * rk;
     if constexpr (DIM == 2) { my = Fb.v[0][1] * irk; S2 += Fb.v[0][2]; }
     const R ek = R(0.5) * TF * (S2 - rk * (mx * mx + my * my)) + Gb.v[0][0];
-    Tb = ek * irk * R(K.inv_cv);
+    Tb = ek * irk * kc<R>(K.inv_cv, K.cf.inv_cv);
     if constexpr (!ITER) {
       break;
     } else {
@@ -443,13 +477,14 @@ __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int N
   // an interface state with rho <= 0 or T <= 0 has no equilibrium: poison the
   // face so that both adjacent cells are flagged nonphysical
   const bool phys = rk > R(0) && Tb > R(0);
-  const R re = phys ? R(K.kr) * rk : qnan<R>(), ge = re * R(K.gfac) * Tb;
+  const bool gk = DIM == 2 && K.grad_k;
+  const R re = phys ? kc<R>(K.kr, K.cf.kr) * rk : qnan<R>(), ge = re * kc<R>(K.gfac, K.cf.gfac) * Tb;
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < NYF; ++b) {
       R e = re * ex[a] * ey[b];
-      if (DIM == 2 && K.grad_k && a + b > 3) e = R(0);
+      if (gk && a + b > 3) e = R(0);
       Fb.v[a][b] += e;
     }
 #pragma unroll
@@ -457,7 +492,7 @@ __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int N
 #pragma unroll
     for (int b = 0; b < NYG; ++b) {
       R e = ge * ex[a] * ey[b];
-      if (DIM == 2 && K.grad_k && a + b > 2) e = R(0);
+      if (gk && a + b > 2) e = R(0);
       Gb.v[a][b] += e;
     }
   // Appendix C form: transport v_n^{lambda_F} phi in the face frame
@@ -528,13 +563,10 @@ struct MomAcc {
 };
 
 template <typename R, int DIM, int DIRN>
-__device__ __forceinline__ void add_face(const StepConst &K, const R *fp, int NFACES, int fidx,
-                                         R sgn, R ux, R uy, R T, R sT, R isT,
-                                         Blk<R, 4, Dims<DIM>::NYF> &AF, Blk<R, 3, Dims<DIM>::NYG> &AG,
-                                         MomAcc &M) {
+__device__ __forceinline__ void face_contrib_body(const StepConst &K, const R *fp, int NFACES, int fidx,
+                                                  R sgn, R ux, R uy, R T, R sT, R isT,
+                                                  Blk<R, 4, Dims<DIM>::NYF> &X, Blk<R, 3, Dims<DIM>::NYG> &Y) {
   using D = Dims<DIM>;
-  Blk<R, 4, D::NYF> X;
-  Blk<R, 3, D::NYG> Y;
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -551,7 +583,7 @@ __device__ __forceinline__ void add_face(const StepConst &K, const R *fp, int NF
     if (K.grad_k) { grad_mask(X); grad_mask(Y); }
   }
   // contribution -dt/dx (v^lambda . n) G phi (Eq. fluxEq) or -dt/dx G (v^lambda_F . n phi)
-  const R w = -R(K.lam) * sgn;
+  const R w = -kc<R>(K.lam, K.cf.lam) * sgn;
   if (!K.appc) {
     const R un = DIRN == 0 ? ux : uy;
     vmul<DIRN>(w * un, w * sT, X);
@@ -566,6 +598,17 @@ __device__ __forceinline__ void add_face(const StepConst &K, const R *fp, int NF
 #pragma unroll
       for (int q = 0; q < D::NYG; ++q) Y.v[p][q] *= w;
   }
+}
+// adds one face's flux, moved into the cell frame, to the update
+template <typename R, int DIM, int DIRN>
+__device__ __forceinline__ void add_face(const StepConst &K, const R *fp, int NFACES, int fidx,
+                                         R sgn, R ux, R uy, R T, R sT, R isT,
+                                         Blk<R, 4, Dims<DIM>::NYF> &AF, Blk<R, 3, Dims<DIM>::NYG> &AG,
+                                         MomAcc &M) {
+  using D = Dims<DIM>;
+  Blk<R, 4, D::NYF> X;
+  Blk<R, 3, D::NYG> Y;
+  face_contrib_body<R, DIM, DIRN>(K, fp, NFACES, fidx, sgn, ux, uy, T, sT, isT, X, Y);
 #pragma unroll
   for (int p = 0; p < 4; ++p)
 #pragma unroll
@@ -599,7 +642,7 @@ __device__ __forceinline__ void update_cell(const StepConst &K, const State<R> &
   for (int i = 0; i < D::QG; ++i) { G.v[i % 3][i / 3] = S.g[i * N + c]; AG.v[i % 3][i / 3] = R(0); }
   const R ux = S.ux[c], uy = DIM == 2 ? S.uy[c] : R(0), T = S.T[c];
   const R sT = sqrt(T), isT = R(1) / sT;
-  qe_scale(F, G, R(K.qe));
+  qe_scale(F, G, kc<R>(K.qe, K.cf.qe));
   const R rho = F.v[0][0];
   MomAcc M;
   if constexpr (is_mixed<R>()) {
@@ -623,7 +666,7 @@ __device__ __forceinline__ void update_cell(const StepConst &K, const State<R> &
     add_face<R, DIM, 1>(K, fp, TL::NFACES, TL::NFX + (cy + 1) * BX + cx, R(1), ux, uy, T, sT, isT, AF, AG, M);
   }
   // DUGKS update in the cell frame: a1 phi~ + a2 phi^eq - dt/dx sum F
-  const R a1 = R(K.a1);
+  const R a1 = kc<R>(K.a1, K.cf.a1);
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -632,8 +675,8 @@ __device__ __forceinline__ void update_cell(const StepConst &K, const State<R> &
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int b = 0; b < D::NYG; ++b) G.v[a][b] = a1 * G.v[a][b] + AG.v[a][b];
-  F.v[0][0] += R(K.a2) * rho;
-  G.v[0][0] += R(K.a2) * R(K.gfac) * T * rho;
+  F.v[0][0] += kc<R>(K.a2, K.cf.a2) * rho;
+  G.v[0][0] += kc<R>(K.a2, K.cf.a2) * kc<R>(K.gfac, K.cf.gfac) * T * rho;
 
   // new moments (Eqs. eq::ConservationLaws, eq:E) and the new co-moving frame
   R uxn, uyn, Tout;
@@ -644,7 +687,7 @@ __device__ __forceinline__ void update_cell(const StepConst &K, const State<R> &
     R my = R(0), S2 = F.v[2][0] + R(DIM) * rn;
     if constexpr (DIM == 2) { my = F.v[0][1] * irn; S2 += F.v[0][2]; }
     const R en = R(0.5) * T * (S2 - rn * (mx * mx + my * my)) + G.v[0][0];
-    const R Tn = en * irn * R(K.inv_cv);
+    const R Tn = en * irn * kc<R>(K.inv_cv, K.cf.inv_cv);
     uxn = ux + sT * mx; uyn = DIM == 2 ? uy + sT * my : R(0); Tout = Tn;
     ok = rn > R(0) && Tn > R(0) && isfinite(rn) && isfinite(Tn) && isfinite(uxn) && isfinite(uyn);
     if (ok) {
@@ -686,7 +729,7 @@ __device__ __forceinline__ void update_cell(const StepConst &K, const State<R> &
     if constexpr (DIM == 2) {
       if (K.grad_k) { grad_mask(F); grad_mask(G); }
     }
-    qe_scale(F, G, R(K.qe));
+    qe_scale(F, G, kc<R>(K.qe, K.cf.qe));
     const double vmax = fmax(fabs((double)uxn), fabs((double)uyn)) + sqrt((double)Tout) * Nodes<4>::cmax;
     cfl = fmax(cfl, vmax * K.lam);
   } else {

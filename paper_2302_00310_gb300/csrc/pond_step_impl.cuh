@@ -39,9 +39,13 @@ __global__ void __launch_bounds__(NT, MINB) member_step_kernel(const unsigned ch
         __syncthreads();
         loaded = i;
       }
-      const int lt = t - d.tile_begin, p = (d.parity + k) & 1;
-      step_tile<R, DIM, BX, BY, NT, ITER>(Ks, d.S[p], d.S[p ^ 1], d.stats, (lt % d.tiles_x) * BX,
-                                          DIM == 2 ? (lt / d.tiles_x) * BY : 0, smem_raw);
+      const int lt = t - d.tile_begin, p = (d.parity + k) & 1, tx = d.tiles_x;
+      // values, not references into the table: the step's global stores could
+      // alias the table as far as the compiler knows, forcing reloads
+      const State<R> S = d.S[p], O = d.S[p ^ 1];
+      Stats *const st = d.stats;
+      step_tile<R, DIM, BX, BY, NT, ITER>(Ks, S, O, st, (lt % tx) * BX, DIM == 2 ? (lt / tx) * BY : 0,
+                                          smem_raw);
     }
     __syncthreads();  // s_inst, Ks and the tile's shared memory are reused
   }
@@ -70,12 +74,14 @@ Shape make_shape(int code) {
 }
 
 // tile codes: 1 = 1D, 252 cells; 2D (x by y): 2 = 8x8, 3 = 16x16, 4 = 16x8,
-// 5 = 8x8 and 6 = 8x16 with registers capped for two CTAs per SM
+// 5 = 8x8 and 6 = 8x16 with registers capped for two CTAs per SM, 7 = 8x16
+// and 8 = 8x8 with registers capped for three CTAs per SM
 template <typename R> std::vector<Shape> all_shapes(int D) {
   if (D == 1) return {make_shape<R, 1, 252, 1, 256, 1, false>(1)};
   return {make_shape<R, 2, 8, 8, 160, 1, false>(2), make_shape<R, 2, 16, 16, 256, 1, false>(3),
           make_shape<R, 2, 16, 8, 256, 1, false>(4), make_shape<R, 2, 8, 8, 160, 2, false>(5),
-          make_shape<R, 2, 8, 16, 160, 2, false>(6)};
+          make_shape<R, 2, 8, 16, 160, 2, false>(6), make_shape<R, 2, 8, 16, 160, 3, false>(7),
+          make_shape<R, 2, 8, 8, 160, 3, false>(8)};
 }
 
 // the iterated face frame runs with one tile shape of its own

@@ -61,7 +61,8 @@ WORKLOAD = "2D periodic advected Gaussian pulse, D2Q16+D2Q9, 256x256, Mach 2 at 
 # digest is the key; profiles/ holds the captures.  None: not yet counted for
 # the current sources.
 FLOPS_PER_CELL = {
-    # digest: {"fp64": ..., "fp32": ..., "fp32_fp64part": ...}
+    "f0fda6d6edd3d676a420fbc0900b79a2d4f25dccd9f51d6324c2790136928e1f": {
+        "fp64": 10193.0, "fp32": 9860.7, "fp32_fp64part": 136.0},
 }
 BYTES_PER_CELL_FP64 = 2 * 28 * 8          # state read once + written once
 BYTES_PER_CELL_FP32 = 2 * 28 * 4
@@ -70,7 +71,9 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * CLOCK_MAX_GHZ / 1e3     # 2 FP64 FMA/clk/SM
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * CLOCK_MAX_GHZ / 1e3   # 128 FP32 FMA/clk/SM
 # dram__bytes_read.sum + dram__bytes_write.sum of one main-line step launch,
 # keyed by source digest (None once the sources change)
-TRAFFIC_BY_DIGEST = {}
+TRAFFIC_BY_DIGEST = {
+    "f0fda6d6edd3d676a420fbc0900b79a2d4f25dccd9f51d6324c2790136928e1f": 18801664,
+}
 
 
 def _build_digest():

@@ -188,6 +188,23 @@ pond_status pond_sync(pond_ctx *c);
  * code the step kernel runs with. */
 pond_status pond_info(pond_ctx *c, double *dt, int64_t *steps, int32_t *tile);
 
+/* Checkpoint and restore.  Not a step of the method: the context's raw state
+ * (each cell's Hermite coefficients and frame in the context's arithmetic,
+ * exactly as the step kernel keeps them), its step counter, time step and
+ * status block, so that a run resumed from a checkpoint continues bit for
+ * bit as the uninterrupted run would (pond_get_state/pond_set_state pass
+ * populations through an FP64 change of basis, which rounds).
+ * pond_checkpoint_size: bytes of a checkpoint of this context.
+ * pond_checkpoint: copies it into caller-owned host memory of at least that
+ * many bytes; synchronises.  POND_E_STATE before pond_init.
+ * pond_restore: loads a checkpoint into a context created with the same
+ * lattice, dims, precision and parameters (the time step comes from the
+ * checkpoint); POND_E_INVAL if the checkpoint does not match the context.
+ * Synchronises. */
+pond_status pond_checkpoint_size(pond_ctx *c, size_t *bytes);
+pond_status pond_checkpoint(pond_ctx *c, void *host, size_t bytes);
+pond_status pond_restore(pond_ctx *c, const void *host, size_t bytes);
+
 /* Releases the context and the device memory it allocated itself. */
 void pond_destroy(pond_ctx *c);
 

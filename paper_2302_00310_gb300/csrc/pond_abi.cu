@@ -653,4 +653,75 @@ pond_status pond_info(pond_ctx *c, double *dt, int64_t *steps, int32_t *tile) {
   return POND_OK;
 }
 
+// ---- checkpoint / restore: the raw state (coefficients and frame in the
+// context's arithmetic), the step counter, the time step and the status block
+namespace {
+struct CkptHdr {
+  char magic[8];
+  int32_t abi, D, fp32, pad;
+  int64_t nx, ny, steps;
+  double dt;
+  Stats stats;
+  uint64_t state_bytes;
+};
+size_t state_bytes_of(const pond_ctx *c) {
+  return (size_t)(qf_of(c->D) + qg_of(c->D) + 3) * (size_t)c->N * (c->fp32 ? 4 : 8);
+}
+const char kCkptMagic[8] = {'P', 'O', 'N', 'D', 'C', 'K', 'P', '1'};
+}  // namespace
+
+pond_status pond_checkpoint_size(pond_ctx *c, size_t *bytes) {
+  if (!c || !bytes) return POND_E_INVAL;
+  *bytes = sizeof(CkptHdr) + state_bytes_of(c);
+  return POND_OK;
+}
+
+pond_status pond_checkpoint(pond_ctx *c, void *host, size_t bytes) {
+  if (!c || !host) return POND_E_INVAL;
+  if (!c->inited) return POND_E_STATE;
+  const size_t sb = state_bytes_of(c);
+  if (bytes < sizeof(CkptHdr) + sb) return POND_E_INVAL;
+  CkptHdr h;
+  memset(&h, 0, sizeof(h));
+  memcpy(h.magic, kCkptMagic, 8);
+  h.abi = POND_ABI_VERSION;
+  h.D = c->D;
+  h.fp32 = c->fp32 ? 1 : 0;
+  h.nx = c->nx;
+  h.ny = c->ny;
+  h.steps = c->steps;
+  h.dt = c->dt;
+  h.state_bytes = sb;
+  unsigned char *dst = static_cast<unsigned char *>(host);
+  POND_CUDA(cudaMemcpyAsync(&h.stats, c->stats, sizeof(Stats), cudaMemcpyDeviceToHost, c->stream));
+  POND_CUDA(cudaMemcpyAsync(dst + sizeof(CkptHdr), c->buf[c->cur], sb, cudaMemcpyDeviceToHost, c->stream));
+  POND_CUDA(cudaStreamSynchronize(c->stream));
+  memcpy(dst, &h, sizeof(h));
+  return POND_OK;
+}
+
+pond_status pond_restore(pond_ctx *c, const void *host, size_t bytes) {
+  if (!c || !host || bytes < sizeof(CkptHdr)) return POND_E_INVAL;
+  CkptHdr h;
+  memcpy(&h, host, sizeof(h));
+  const size_t sb = state_bytes_of(c);
+  if (memcmp(h.magic, kCkptMagic, 8) != 0 || h.abi != POND_ABI_VERSION || h.D != c->D ||
+      h.fp32 != (c->fp32 ? 1 : 0) || h.nx != c->nx || h.ny != c->ny || h.state_bytes != sb ||
+      bytes < sizeof(CkptHdr) + sb || !(h.dt > 0.0))
+    return POND_E_INVAL;
+  POND_CUDA(cudaStreamSynchronize(c->stream));
+  c->cur = 0;
+  POND_CUDA(cudaMemcpyAsync(c->buf[0], static_cast<const unsigned char *>(host) + sizeof(CkptHdr), sb,
+                            cudaMemcpyHostToDevice, c->stream));
+  POND_CUDA(cudaMemcpyAsync(c->stats, &h.stats, sizeof(Stats), cudaMemcpyHostToDevice, c->stream));
+  c->dt = h.dt;
+  set_step_const(c);
+  drop_graphs(c);
+  pond_status s = prepare_step(c);  // synchronises the stream
+  if (s != POND_OK) return s;
+  c->steps = h.steps;
+  c->inited = true;
+  return POND_OK;
+}
+
 }  // extern "C"

@@ -33,7 +33,7 @@ EXPORTS = (
     "pond_sync", "pond_info", "pond_destroy", "pond_strerror", "pond_abi_version",
     "pond_step_noalloc", "pond_tune_default", "pond_batch_create", "pond_batch_add",
     "pond_batch_remove", "pond_batch_size", "pond_batch_step", "pond_batch_info",
-    "pond_batch_destroy",
+    "pond_batch_destroy", "pond_checkpoint_size", "pond_checkpoint", "pond_restore",
 )
 POND_NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 
@@ -102,6 +102,9 @@ def lib(build: bool = False):
     L.pond_step_noalloc.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
                                     ctypes.POINTER(pond_params), _P, _P, _P, _P, _P,
                                     ctypes.c_int64, ctypes.POINTER(ctypes.c_uint32), _P]
+    L.pond_checkpoint_size.argtypes = [_P, ctypes.POINTER(ctypes.c_size_t)]
+    L.pond_checkpoint.argtypes = [_P, _P, ctypes.c_size_t]
+    L.pond_restore.argtypes = [_P, _P, ctypes.c_size_t]
     L.pond_tune_default.argtypes = [ctypes.POINTER(pond_tune)]
     L.pond_tune_default.restype = None
     L.pond_batch_create.argtypes = [ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_int32,
@@ -248,6 +251,24 @@ def pond_step_noalloc(lat: int, dims, params: pond_params, f, g, ux, uy, T, n: i
     if st not in (POND_OK, POND_E_NONPHYSICAL):
         raise PondError(st, "pond_step_noalloc")
     return st, (int(fl.value) if want_flags else None)
+
+
+def pond_checkpoint_size(ctx) -> int:
+    n = ctypes.c_size_t()
+    _check(lib().pond_checkpoint_size(ctx, ctypes.byref(n)), "pond_checkpoint_size")
+    return int(n.value)
+
+
+def pond_checkpoint(ctx) -> np.ndarray:
+    """The context's checkpoint as a host byte array."""
+    buf = np.empty(pond_checkpoint_size(ctx), dtype=np.uint8)
+    _check(lib().pond_checkpoint(ctx, buf.ctypes.data, buf.nbytes), "pond_checkpoint")
+    return buf
+
+
+def pond_restore(ctx, buf: np.ndarray):
+    buf = np.ascontiguousarray(buf, dtype=np.uint8)
+    _check(lib().pond_restore(ctx, buf.ctypes.data, buf.nbytes), "pond_restore")
 
 
 def pond_tune_default() -> pond_tune:

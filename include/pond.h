@@ -120,12 +120,16 @@ typedef struct {
                               when the shift |(u_s-u_F)/sqrt(T_F)| or the scale
                               sqrt(T_s/T_F) exceeds this                          */
   int32_t tile;            /* cells per CTA of the step kernel: 0 automatic
-                              (1D: 1, 2D: 6); 1D: 1 = 252 cells; 2D (x by y):
-                              2 = 8x8, 3 = 16x16, 4 = 16x8, 5 = 8x8 and 6 = 8x16
-                              with registers capped for two CTAs per SM, 7 = 8x16
-                              and 8 = 8x8 capped for three CTAs per SM.  The
+                              (1D: 1; 2D: 9 in FP64, 6 mixed); 1D: 1 = 252
+                              cells; 2D (x by y): 2 = 8x8, 3 = 16x16, 4 = 16x8,
+                              5 = 8x8 and 6 = 8x16 with registers capped for two
+                              CTAs per SM, 7 = 8x16 and 8 = 8x8 capped for three
+                              CTAs per SM, 9 = 8x16 with 192 threads.  The
                               iterated face frame runs 8x8 (2D) / 252 (1D).
-                              Results do not depend on the tile.               */
+                              Each output depends only on its stencil, so all
+                              tiles compute the same step; as separate machine
+                              code they may round differently (multiply-add
+                              fusion), to the precision of the context.        */
 } pond_params;
 
 /* Fills the defaults: gamma 1.4, tau 1e-4, Pr 1, dx 1, dt 0 (from cfl 0.2),
@@ -224,11 +228,14 @@ int pond_abi_version(void);
  * chunk); members may join and leave between calls without a new capture.
  *
  * A member's state after a batch step is bit for bit the state pond_step()
- * gives it alone (results do not depend on the tile shape or on the other
- * members), so the autotuner times candidate tile shapes on the run's own
- * steps: the first pond_batch_step() call in which every member takes at
- * least graph_steps x (number of shapes) steps runs one chunk with each
- * shape and keeps the fastest.
+ * gives it alone with the same tile shape: both launch the same kernel
+ * function, and no result depends on the other members.  Every shape
+ * computes the same step (to rounding: each is its own machine code), so the
+ * autotuner times candidate shapes on the run's own steps: the first
+ * pond_batch_step() call in which every member takes at least graph_steps x
+ * (number of shapes) steps runs one chunk with each shape and keeps the
+ * fastest.  A fixed tile equal to the contexts' own keeps results bit for bit
+ * identical to solo runs.
  *
  * Members must share the batch's dimension, precision and stream, must be
  * initialised, and may not use the iterated face frame.  A context belongs
@@ -236,8 +243,9 @@ int pond_abi_version(void);
  * calls are made from one host thread at a time. */
 typedef struct pond_batch pond_batch;
 typedef struct {
-  int32_t tile;         /* 0: the autotuner picks; else a 2D tile code 3, 4 or 6
-                           (1D batches have the one 252-cell tile)            */
+  int32_t tile;         /* 0: the autotuner picks; else a candidate 2D tile code
+                           (mixed: 6, 3, 4; FP64: 9, 6, 3; 1D batches have the
+                           one 252-cell tile)                                 */
   int32_t graph_steps;  /* launches per chunk and per captured graph (1-1024) */
   int32_t autotune;     /* 1: time the candidate shapes on the first long call */
 } pond_tune;

@@ -172,9 +172,10 @@ pond_status step_once(pond_ctx *c) {
   return POND_OK;
 }
 
-// 8x16 tiles with two CTAs' worth of registers per SM were fastest for both
-// precisions on 256^2 and 1024^2 grids (tile sweep on GB300)
-int auto_tile(const pond_ctx *c) { return c->D == 1 ? 1 : 6; }
+// Fastest in tile sweeps on GB300 (256^2 and 1024^2 grids): 8x16 tiles, with
+// 160 threads and registers for two CTAs per SM on the mixed path, with 192
+// threads and no register cap in FP64 (whose shared memory fits one CTA)
+int auto_tile(const pond_ctx *c) { return c->D == 1 ? 1 : (c->fp32 ? 6 : 9); }
 
 bool valid_params(const pond_params *p) {
   if (!p) return false;
@@ -191,7 +192,7 @@ bool valid_params(const pond_params *p) {
   if (p->flux_frame != POND_FRAME_AVG && p->flux_frame != POND_FRAME_ITER) return false;
   if (p->flux_frame == POND_FRAME_ITER && (!(p->iter_tol > 0.0) || p->iter_max < 1)) return false;
   if (!(p->xi_fp64_threshold > 0.0)) return false;
-  if (p->tile < 0 || p->tile > 8) return false;
+  if (p->tile < 0 || p->tile > 9) return false;
   return true;
 }
 

@@ -13,10 +13,12 @@
 // while members join and leave; only the table (a few hundred bytes per
 // member) is uploaded per chunk.
 //
-// Every output depends only on its stencil's arithmetic, so a member's state
-// is bit for bit the same alone (pond_step) and in any batch, with any tile
-// shape.  That is what lets the autotuner time candidate tile shapes on real
-// steps: the steps it times are steps of the run.
+// A member's state is bit for bit the same alone (pond_step) and in any batch
+// with the same tile shape: both launch the same kernel function, and every
+// output depends only on its stencil's arithmetic.  Every shape computes the
+// same step (to rounding, as separate machine code), which lets the
+// autotuner time candidate shapes on real steps: the steps it times are
+// steps of the run.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -41,10 +43,12 @@ namespace {
 std::vector<Shape> batch_shapes(bool fp32, int D) {
   const std::vector<Shape> all = fp32 ? pond_shapes_fp32(D) : pond_shapes_fp64(D);
   if (D == 1) return all;
+  static const int kMixed[3] = {6, 3, 4}, kFp64[3] = {9, 6, 3};
+  const int *codes = fp32 ? kMixed : kFp64;
   std::vector<Shape> out;
-  for (int code : {6, 3, 4})
+  for (int i = 0; i < 3; ++i)
     for (const Shape &s : all)
-      if (s.code == code) out.push_back(s);
+      if (s.code == codes[i]) out.push_back(s);
   return out;
 }
 
@@ -214,6 +218,10 @@ pond_status pond_batch_create(pond_batch **out, int32_t dim, int32_t precision, 
   b->capacity = capacity;
   b->tune = t;
   b->shapes = batch_shapes(b->fp32, dim);
+  if (b->shapes.empty()) {
+    delete b;
+    return POND_E_INVAL;
+  }
   b->shape = 0;
   if (t.tile) {
     b->shape = -1;

@@ -87,8 +87,9 @@ template <int DIM> struct Dims {
   // and (mixed path) the conserved fluxes: mass, x-, y-momentum, energy
   static constexpr int FUX = QF + QG, FUY = FUX + 1, FST = FUX + 2, FT = FUX + 3;
   static constexpr int FJ = FUX + 4;
+  // (TF is read only by the mixed path's FP64 fallback, the fluxes only by the mixed path)
   template <typename R> static constexpr int nface() {
-    return std::is_same<R, float>::value ? QF + QG + 8 : QF + QG + 4;
+    return std::is_same<R, float>::value ? QF + QG + 8 : QF + QG + 3;
   }
 };
 
@@ -549,7 +550,7 @@ __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int N
   fp[D::FUX * NFACES + fidx] = uFx;
   fp[D::FUY * NFACES + fidx] = uFy;
   fp[D::FST * NFACES + fidx] = sTF;
-  fp[D::FT * NFACES + fidx] = TF;
+  if constexpr (is_mixed<R>()) fp[D::FT * NFACES + fidx] = TF;
   return noconv;
 }
 
@@ -576,7 +577,8 @@ __device__ __forceinline__ void face_contrib_body(const StepConst &K, const R *f
 #pragma unroll
     for (int b = 0; b < D::NYG; ++b) Y.v[a][b] = fp[(D::QF + a + 3 * b) * NFACES + fidx];
   const R uFx = fp[D::FUX * NFACES + fidx], uFy = fp[D::FUY * NFACES + fidx];
-  const R sTF = fp[D::FST * NFACES + fidx], TF = fp[D::FT * NFACES + fidx];
+  const R sTF = fp[D::FST * NFACES + fidx];
+  const R TF = is_mixed<R>() ? fp[D::FT * NFACES + fidx] : R(0);  // read by the FP64 fallback only
   move_frame<R, DIM, 4>(K, uFx, uFy, TF, sTF, ux, uy, T, isT, X);
   move_frame<R, DIM, 3>(K, uFx, uFy, TF, sTF, ux, uy, T, isT, Y);
   if constexpr (DIM == 2) {
@@ -747,8 +749,10 @@ __device__ __forceinline__ void update_cell(const StepConst &K, const State<R> &
 
 // ---- one tile step (phases A-C) --------------------------------------------------
 // The BX x BY tile whose first cell is (j0, k0); smem holds the halo and face
-// records.  Every output depends only on its own stencil's arithmetic, so the
-// result is the same for any tile shape or launch order.
+// records.  Every output depends only on its own stencil's arithmetic: for a
+// given instantiation the result does not depend on the launch order or on
+// which tile a cell falls in (different tile shapes are different machine
+// code and may round differently).
 template <typename R, int DIM, int BX, int BY, int NT, bool ITER>
 __device__ __forceinline__ void step_tile(const StepConst &K, const State<R> &S, const State<R> &O,
                                           Stats *stats, int j0, int k0, unsigned char *smem) {

@@ -75,13 +75,14 @@ Shape make_shape(int code) {
 
 // tile codes: 1 = 1D, 252 cells; 2D (x by y): 2 = 8x8, 3 = 16x16, 4 = 16x8,
 // 5 = 8x8 and 6 = 8x16 with registers capped for two CTAs per SM, 7 = 8x16
-// and 8 = 8x8 with registers capped for three CTAs per SM
+// and 8 = 8x8 with registers capped for three CTAs per SM, 9 = 8x16 with 192
+// threads (no cap: one FP64 CTA per SM is all shared memory holds)
 template <typename R> std::vector<Shape> all_shapes(int D) {
   if (D == 1) return {make_shape<R, 1, 252, 1, 256, 1, false>(1)};
   return {make_shape<R, 2, 8, 8, 160, 1, false>(2), make_shape<R, 2, 16, 16, 256, 1, false>(3),
           make_shape<R, 2, 16, 8, 256, 1, false>(4), make_shape<R, 2, 8, 8, 160, 2, false>(5),
           make_shape<R, 2, 8, 16, 160, 2, false>(6), make_shape<R, 2, 8, 16, 160, 3, false>(7),
-          make_shape<R, 2, 8, 8, 160, 3, false>(8)};
+          make_shape<R, 2, 8, 8, 160, 3, false>(8), make_shape<R, 2, 8, 16, 192, 1, false>(9)};
 }
 
 // the iterated face frame runs with one tile shape of its own

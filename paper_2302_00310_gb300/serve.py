@@ -13,8 +13,9 @@ is admitted again; requests that arrive while others run join at the next
 tick.  Time to solution is measured from arrival to the result being on the
 host.
 
-A member's state in a batch is bit for bit the state it reaches alone, so a
-request's result does not depend on what else is being served.
+A member's state in a batch is bit for bit the state it reaches alone with the
+same tile shape, so a request's result does not depend on what else is being
+served; across tile shapes it agrees to rounding.
 
 The scheduling logic (``Server``) talks to an executor; ``PondExecutor``
 drives the C ABI, and tests drive ``Server`` with a fake executor on the CPU.
@@ -151,12 +152,18 @@ class PondExecutor:
         remaining: int
 
     def __init__(self, precision: int = pond.POND_FP32_MIXED, capacity: int = 128,
-                 graph_steps: int = 8, device=None):
-        tune = pond.pond_tune_default()
-        tune.graph_steps = graph_steps
+                 graph_steps: int = 8, tile: int = 0, device=None):
+        """tile 0: each batch's autotuner picks its 2D tile shape (results then
+        agree with a solo run of the same request to rounding); a fixed tile
+        equal to the solo default makes them agree bit for bit."""
         self.precision = precision
         self.capacity = capacity
-        self.batches = {d: pond.Batch(d, precision, capacity, tune, device=device) for d in (1, 2)}
+        self.batches = {}
+        for d in (1, 2):
+            tune = pond.pond_tune_default()
+            tune.graph_steps = graph_steps
+            tune.tile = tile if d == 2 else 0  # a 1D batch has the one 252-cell tile
+            self.batches[d] = pond.Batch(d, precision, capacity, tune, device=device)
         self.handles = {1: [], 2: []}   # in batch member order
 
     def _cfg(self, r):

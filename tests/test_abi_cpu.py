@@ -60,3 +60,30 @@ def test_invalid_arguments_are_rejected_before_any_device_work(L):
         pond.pond_create(pond.POND_D2Q16, (8, 8), p)
     with pytest.raises(pond.PondError):
         pond.pond_create(7, (8, 8), pond.pond_params_default())
+
+
+def test_batch_tile_codes_are_resolved_before_any_device_work(L):
+    """pond_batch_create resolves the requested tile among the candidates of
+    the batch's precision before its first CUDA call: a candidate gets as far
+    as the device query (POND_E_CUDA without a GPU), anything else is
+    POND_E_INVAL; a zero tile (autotune) resolves too."""
+    import ctypes
+
+    import torch
+
+    no_gpu = not torch.cuda.is_available()
+    for prec, tile, ok in ((pond.POND_FP64, 9, True), (pond.POND_FP64, 6, True),
+                           (pond.POND_FP64, 4, False), (pond.POND_FP32_MIXED, 6, True),
+                           (pond.POND_FP32_MIXED, 4, True), (pond.POND_FP32_MIXED, 9, False),
+                           (pond.POND_FP64, 0, True), (pond.POND_FP32_MIXED, 0, True)):
+        t = pond.pond_tune_default()
+        t.tile = tile
+        b = ctypes.c_void_p()
+        st = L.pond_batch_create(ctypes.byref(b), 2, prec, 4, ctypes.byref(t), None)
+        if not ok:
+            assert st == pond.POND_E_INVAL, (prec, tile, st)
+        elif no_gpu:
+            assert st == pond.POND_E_CUDA, (prec, tile, st)
+        else:
+            assert st == pond.POND_OK
+            L.pond_batch_destroy(b)

@@ -82,6 +82,7 @@ CASES_2D = [
     (33, 35, (1, 2, 2, 1), 0.5, 1, 1, 1, 0.9, 2, 3),
     (27, 41, (0, 0, 1, 1), 0.71, 1, 0, 0, 1.0, 2, 5),
     (19, 37, (1, 1, 0, 0), 1.0, 0, 1, 1, 1.0, 2, 6),
+    (29, 35, (2, 1, 0, 0), 0.71, 0, 0, 0, 1.0, 2, 9),
 ]
 
 

@@ -20,6 +20,8 @@ The other forms the metric compares are measured in the same run
   * ``mixed``: the same pulse on the mixed path (FP32 + FP64 moments), with
     the L1 / Linf relative density error against the FP64 path after the
     full 1000-step run;
+  * ``riemann``: the four-quadrant Riemann problem at 1024^2 (QE Pr 0.71),
+    mixed path and FP64, with the L1 error between them after 200 steps;
   * ``batched``: 64 shock-bubble instances of seeded sizes 64^2-512^2 (about
     4.07M cells), Mach 1.5-5, Pr 0.71, advanced by the persistent batch
     kernel (autotuned), FP32-mixed and FP64, with the L1 error of the mixed
@@ -277,6 +279,37 @@ def bench_mixed(torch, pond, W, flush):
     }
 
 
+def bench_riemann(torch, pond, W, steps=200):
+    """The four-quadrant Riemann problem at 1024^2 (seeded states, QE Pr 0.71,
+    minmod), mixed path and plain FP64: MLUPS and the L1 error after `steps`."""
+    w = W.riemann4_2d(n=1024, seed=1)
+    fields = (w["rho"], w["ux"], w["uy"], w["T"])
+    n = w["cfg"]["nx"] * w["cfg"]["ny"]
+    out = {"workload": "four-quadrant Riemann problem, D2Q16+D2Q9, 1024x1024, seed 1 (quadrant states "
+                       "rho in [0.1,1.5], p in [0.03,1.5], Mach up to 3), QE Pr 0.71, minmod, tau 1e-4",
+           "cells": n, "steps": steps, "unit": UNIT}
+    mom = {}
+    for prec, name in ((pond.POND_FP32_MIXED, "fp32_mixed"), (pond.POND_FP64, "fp64")):
+        sim = pond.Sim(dict(w["cfg"], precision=prec))
+        sim.init(*fields)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(sim.stream):
+            e0.record(sim.stream)
+            pond.pond_step(sim.ctx, steps)
+            e1.record(sim.stream)
+        sim.stream.synchronize()
+        ms = e0.elapsed_time(e1)
+        mom[name] = sim.moments()
+        fl = sim.flags()[1]
+        out[name] = {"value": n * steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / steps,
+                     "tile": sim.info()[2], "nonphysical": bool(fl & 1)}
+        sim.close()
+    out["l1_rho_fp32_vs_fp64"] = _l1(mom["fp32_mixed"][0], mom["fp64"][0])
+    out["linf_rho_fp32_vs_fp64"] = _linf(mom["fp32_mixed"][0], mom["fp64"][0])
+    out["stated_l1_bound"] = 1e-3
+    return out
+
+
 def bench_batched(torch, pond, W):
     """64 shock-bubble instances through the persistent batch kernel."""
     ws_ = [W.shock_bubble_2d(seed=s) for s in range(64)]
@@ -391,6 +424,7 @@ def run_gpu(args, dist, rank, ws):
     extras = {}
     if not args.no_extras and rank == 0:
         extras["mixed"] = bench_mixed(torch, pond, W, flush)
+        extras["riemann"] = bench_riemann(torch, pond, W)
         extras["batched"] = bench_batched(torch, pond, W)
         extras["serve"] = bench_serve(pond, serve_mod)
 

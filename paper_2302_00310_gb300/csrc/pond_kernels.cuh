@@ -309,14 +309,17 @@ __device__ __forceinline__ void stencil_pops_body(const StepConst &K, const R *s
 // instruction fetch, not arithmetic, and the shared copy keeps its code
 // footprint small.  The FP64 kernel, bound by the FP64 pipe, inlines it.
 template <typename R, int DIM, int Q>
-__device__ __noinline__ void stencil_pops_call(const StepConst &K, const R *sp, int NH, int h, R uFx,
-                                               R uFy, R TF, R isTF, Blk<R, Q, (DIM == 2 ? Q : 1)> &Y) {
+__device__ __noinline__ Blk<R, Q, (DIM == 2 ? Q : 1)> stencil_pops_call(const StepConst &K, const R *sp,
+                                                                      int NH, int h, R uFx, R uFy,
+                                                                      R TF, R isTF) {
+  Blk<R, Q, (DIM == 2 ? Q : 1)> Y;  // returned by value: in registers, not through local memory
   stencil_pops_body<R, DIM, Q>(K, sp, NH, h, uFx, uFy, TF, isTF, Y);
+  return Y;
 }
 template <typename R, int DIM, int Q>
 __device__ __forceinline__ void stencil_pops(const StepConst &K, const R *sp, int NH, int h, R uFx,
                                              R uFy, R TF, R isTF, Blk<R, Q, (DIM == 2 ? Q : 1)> &Y) {
-  if constexpr (is_mixed<R>()) stencil_pops_call<R, DIM, Q>(K, sp, NH, h, uFx, uFy, TF, isTF, Y);
+  if constexpr (is_mixed<R>()) Y = stencil_pops_call<R, DIM, Q>(K, sp, NH, h, uFx, uFy, TF, isTF);
   else stencil_pops_body<R, DIM, Q>(K, sp, NH, h, uFx, uFy, TF, isTF, Y);
 }
 
@@ -601,6 +604,21 @@ __device__ __forceinline__ void face_contrib_body(const StepConst &K, const R *f
       for (int q = 0; q < D::NYG; ++q) Y.v[p][q] *= w;
   }
 }
+// The mixed path computes a face's contribution in one out-of-line copy per
+// direction (returned by value, in registers), like the stencil transformation.
+template <typename R, int DIM> struct FaceContrib {
+  Blk<R, 4, Dims<DIM>::NYF> X;
+  Blk<R, 3, Dims<DIM>::NYG> Y;
+};
+template <typename R, int DIM, int DIRN>
+__device__ __noinline__ FaceContrib<R, DIM> face_contrib_call(const StepConst &K, const R *fp, int NFACES,
+                                                              int fidx, R sgn, R ux, R uy, R T, R sT,
+                                                              R isT) {
+  FaceContrib<R, DIM> c;
+  face_contrib_body<R, DIM, DIRN>(K, fp, NFACES, fidx, sgn, ux, uy, T, sT, isT, c.X, c.Y);
+  return c;
+}
+
 // adds one face's flux, moved into the cell frame, to the update
 template <typename R, int DIM, int DIRN>
 __device__ __forceinline__ void add_face(const StepConst &K, const R *fp, int NFACES, int fidx,
@@ -610,7 +628,13 @@ __device__ __forceinline__ void add_face(const StepConst &K, const R *fp, int NF
   using D = Dims<DIM>;
   Blk<R, 4, D::NYF> X;
   Blk<R, 3, D::NYG> Y;
-  face_contrib_body<R, DIM, DIRN>(K, fp, NFACES, fidx, sgn, ux, uy, T, sT, isT, X, Y);
+  if constexpr (is_mixed<R>()) {
+    const FaceContrib<R, DIM> c = face_contrib_call<R, DIM, DIRN>(K, fp, NFACES, fidx, sgn, ux, uy, T, sT, isT);
+    X = c.X;
+    Y = c.Y;
+  } else {
+    face_contrib_body<R, DIM, DIRN>(K, fp, NFACES, fidx, sgn, ux, uy, T, sT, isT, X, Y);
+  }
 #pragma unroll
   for (int p = 0; p < 4; ++p)
 #pragma unroll

@@ -159,6 +159,24 @@ def _dist():
     return dist, dist.get_rank(), ws
 
 
+def _max_over_ranks(dist, values, device):
+    """Element-wise maximum of per-rank timings over all ranks (the slowest
+    rank sets the job's time); identity without a process group."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def _job_rate(cells: int, steps: int, world: int, seconds: float) -> float:
+    """Whole-job MLUPS: every rank advances its own replica of `cells` cells by
+    `steps` steps; the job takes the slowest rank's `seconds`."""
+    return cells * steps * world / seconds / 1e6
+
+
 def _oracle_rate(cfg, fields, n_window: int, steps: int, budget_s: float | None = None):
     """Oracle MLUPS on an n_window^2 periodic window of the workload."""
     import oracle
@@ -428,14 +446,11 @@ def run_gpu(args, dist, rank, ws):
         extras["batched"] = bench_batched(torch, pond, W)
         extras["serve"] = bench_serve(pond, serve_mod)
 
-    if dist is not None:
-        t = torch.tensor([sum_ms, e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        sum_ms, e2e_s = float(t[0]), float(t[1])
+    sum_ms, e2e_s = _max_over_ranks(dist, [sum_ms, e2e_s], "cuda")
     if rank != 0:
         return
-    mlups = n * args.steps * ws / (sum_ms * 1e-3) / 1e6
-    e2e = n * args.steps * ws / e2e_s / 1e6
+    mlups = _job_rate(n, args.steps, ws, sum_ms * 1e-3)
+    e2e = _job_rate(n, args.steps, ws, e2e_s)
     per_launch_s = sum_ms * 1e-3 / args.steps
     digest = _build_digest()
     if fp32:

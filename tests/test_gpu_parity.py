@@ -299,3 +299,67 @@ def test_iterated_face_frame_sod_matches_oracle():
     ost, got, flags = _run_both(cfg, w["rho"], w["ux"], w["uy"], w["T"], 60)
     _compare(ost, got, 1)
     assert flags[3] == ost.report["noconv_faces"] and flags[3] > 0
+
+
+def _window_oracle_interior(cfg, fields, j, k, steps):
+    """Oracle run on the (4 steps + 1)^2 window around an interior cell (j, k)
+    (at least 2 steps' reach from every boundary): the centre cell depends
+    only on cells within 2 per step, whatever the boundary conditions."""
+    r = 2 * steps
+    sub = [np.ascontiguousarray(a[k - r:k + r + 1, j - r:j + r + 1]) for a in fields]
+    c = dict(cfg, nx=2 * r + 1, ny=2 * r + 1, bc=(1, 1, 1, 1))
+    ocfg = oracle.Config.from_dict(c)
+    st = oracle.run(ocfg, oracle.init(ocfg, *sub), steps)
+    return st.f[:, r, r], st.g[:, r, r], st.ux[r, r], st.uy[r, r], st.T[r, r]
+
+
+def _check_sampled(cfg, fields, got, cells, steps):
+    f, g, ux, uy, T = got
+    for j, k in cells:
+        of, og, oux, ouy, oT = _window_oracle_interior(cfg, fields, int(j), int(k), steps)
+        assert _rel(f[:, k, j], of) <= TOL and _rel(g[:, k, j], og) <= TOL
+        assert abs(ux[k, j] - oux) <= TOL * max(abs(oux), 1.0)
+        assert abs(uy[k, j] - ouy) <= TOL * max(abs(ouy), 1.0)
+        assert abs(T[k, j] - oT) <= TOL * oT
+
+
+def test_riemann_full_size_sampled_cells_match_oracle():
+    """The 1024^2 four-quadrant Riemann problem of the benchmark (QE Pr 0.71,
+    minmod), FP64, in the benchmark's launch configuration; 2 steps, 16 seeded
+    interior cells (including cells on the quadrant interfaces) checked
+    against the oracle one by one."""
+    w = W.riemann4_2d(n=1024, seed=1)
+    fields = (w["rho"], w["ux"], w["uy"], w["T"])
+    sim = pond.Sim(w["cfg"])
+    sim.init(*fields)
+    sim.step(2)
+    got = sim.get_state()
+    sim.close()
+    rng = np.random.default_rng(8)
+    cells = [tuple(x) for x in rng.integers(8, 1016, (12, 2))] + [(511, 512), (512, 511), (510, 300), (700, 513)]
+    _check_sampled(w["cfg"], fields, got, cells, 2)
+
+
+def test_batch_full_size_sampled_cells_match_oracle():
+    """The benchmark's 64-instance shock-bubble batch in FP64 (persistent,
+    autotuned), 2 steps; 3 seeded interior cells in each of 8 members checked
+    against the oracle."""
+    ws = [W.shock_bubble_2d(seed=s) for s in range(64)]
+    b = pond.Batch(2, pond.POND_FP64, 64)
+    sims = []
+    for w in ws:
+        s = pond.Sim(w["cfg"], stream=b.stream)
+        s.init(w["rho"], w["ux"], w["uy"], w["T"])
+        b.add(s)
+        sims.append(s)
+    b.step([2] * 64)
+    rng = np.random.default_rng(9)
+    for i in rng.choice(64, 8, replace=False):
+        w = ws[int(i)]
+        n = w["cfg"]["nx"]
+        got = sims[int(i)].get_state()
+        cells = [tuple(x) for x in rng.integers(8, n - 8, (3, 2))]
+        _check_sampled(w["cfg"], (w["rho"], w["ux"], w["uy"], w["T"]), got, cells, 2)
+    b.close()
+    for s in sims:
+        s.close()

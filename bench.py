@@ -65,6 +65,8 @@ WORKLOAD = "2D periodic advected Gaussian pulse, D2Q16+D2Q9, 256x256, Mach 2 at 
 FLOPS_PER_CELL = {
     "f0fda6d6edd3d676a420fbc0900b79a2d4f25dccd9f51d6324c2790136928e1f": {
         "fp64": 10193.0, "fp32": 9860.7, "fp32_fp64part": 136.0},
+    "8f1ae008ef28539d6d8f70da94b8e383bec8cec0264b0bb4d062d9d36ea04ca2": {
+        "fp64": 10204.6, "fp32": 9851.7, "fp32_fp64part": 136.0},
 }
 BYTES_PER_CELL_FP64 = 2 * 28 * 8          # state read once + written once
 BYTES_PER_CELL_FP32 = 2 * 28 * 4
@@ -75,6 +77,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * CLOCK_MAX_GHZ / 1e3   # 128 FP32 FMA/clk/SM
 # keyed by source digest (None once the sources change)
 TRAFFIC_BY_DIGEST = {
     "f0fda6d6edd3d676a420fbc0900b79a2d4f25dccd9f51d6324c2790136928e1f": 18801664,
+    "8f1ae008ef28539d6d8f70da94b8e383bec8cec0264b0bb4d062d9d36ea04ca2": 15318272,
 }
 
 

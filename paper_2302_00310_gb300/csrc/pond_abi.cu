@@ -5,8 +5,11 @@
 // A state buffer holds, in the arithmetic type R of the context (double for
 // POND_FP64, float for POND_FP32_MIXED), SoA arrays
 //   f[Qf][N], g[Qg][N], ux[N], uy[N], T[N]          (N = nx*ny cells)
-// where f and g are the Hermite coefficients of each cell's populations in
-// its frame (ux, uy, T).  The boundary exchanges populations: they are
+// where f and g are the dimensional Hermite coefficients of each cell's
+// populations in its frame (ux, uy, T): B_ab = T^((a+b)/2) A_ab, with A_ab the
+// Hermite coefficients sum_i phi_i He_a(c_ix) He_b(c_iy).  On the mixed path
+// the FP64 conserved moments M[4][N] (rho, rho ux, rho uy, rho E) follow them
+// (8-byte aligned).  The boundary exchanges populations: they are
 // converted (in FP64) on the way in and out.  Steps ping-pong between the two
 // buffers; between steps the idle buffer is used as staging at the boundary.
 #include <cuda_runtime.h>
@@ -41,34 +44,51 @@ __global__ void init_kernel(const double *rho, const double *ux, const double *u
                             State<R> S, size_t N, double gfac) {
   const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= N) return;
-  const double r = rho[c], t = T[c];
+  const double r = rho[c], t = T[c], vx = ux[c], vy = DIM == 2 ? uy[c] : 0.0;
   for (int i = 0; i < (DIM == 2 ? 16 : 4); ++i) S.f[i * N + c] = R(i == 0 ? r : 0.0);
   for (int i = 0; i < (DIM == 2 ? 9 : 3); ++i) S.g[i * N + c] = R(i == 0 ? gfac * t * r : 0.0);
-  S.ux[c] = R(ux[c]);
-  S.uy[c] = DIM == 2 ? R(uy[c]) : R(0);
+  S.ux[c] = R(vx);
+  S.uy[c] = R(vy);
   S.T[c] = R(t);
+  if (S.M) {  // C_v = gfac + D/2
+    S.M[c] = r;
+    S.M[N + c] = r * vx;
+    S.M[2 * N + c] = r * vy;
+    S.M[3 * N + c] = 0.5 * r * (vx * vx + vy * vy) + (gfac + 0.5 * DIM) * r * t;
+  }
 }
 
-// rho, u, T of each cell from its Hermite coefficients (Eqs.
-// eq::ConservationLaws, eq:E), in FP64
+// rho, u, T of each cell (Eqs. eq::ConservationLaws, eq:E), in FP64: on the
+// mixed path from its FP64 conserved moments, else from its dimensional
+// Hermite coefficients: rho = B_00, rho (u - u_frame) = (B_10, B_01),
+// sum |v - u_frame|^2 f = B_20 + B_02 + D T rho
 template <typename R, int DIM>
 __global__ void moments_kernel(State<R> S, size_t N, double inv_cv, double *rho, double *ux,
                                double *uy, double *T) {
   const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= N) return;
-  const double fx = S.ux[c], fy = DIM == 2 ? (double)S.uy[c] : 0.0, fT = S.T[c], sT = sqrt(fT);
+  if (S.M) {
+    const double r = S.M[c], vx = S.M[N + c] / r, vy = DIM == 2 ? S.M[2 * N + c] / r : 0.0;
+    rho[c] = r;
+    ux[c] = vx;
+    if (uy) uy[c] = vy;
+    T[c] = (S.M[3 * N + c] / r - 0.5 * (vx * vx + vy * vy)) * inv_cv;
+    return;
+  }
+  const double fx = S.ux[c], fy = DIM == 2 ? (double)S.uy[c] : 0.0, fT = S.T[c];
   const double r = S.f[c], mx = (double)S.f[1 * N + c] / r;
-  double my = 0.0, S2 = (double)S.f[2 * N + c] + DIM * r;
+  double my = 0.0, S2 = (double)S.f[2 * N + c] + DIM * fT * r;
   if constexpr (DIM == 2) { my = (double)S.f[4 * N + c] / r; S2 += (double)S.f[8 * N + c]; }
-  const double e = 0.5 * fT * (S2 - r * (mx * mx + my * my)) + (double)S.g[c];
+  const double e = 0.5 * (S2 - r * (mx * mx + my * my)) + (double)S.g[c];
   rho[c] = r;
-  ux[c] = fx + sT * mx;
-  if (uy) uy[c] = fy + sT * my;
+  ux[c] = fx + mx;
+  if (uy) uy[c] = fy + my;
   T[c] = e / r * inv_cv;
 }
 
 // populations (FP64 planes p[i][ld], cells 0..n-1) <-> state coefficients
-// (cells c0..c0+n-1); in place when the planes are the state's own (FP64)
+// (cells c0..c0+n-1) in the frame already stored for those cells; in place
+// when the planes are the state's own (FP64)
 template <typename R, int DIM>
 __global__ void pops_to_coef_kernel(const double *pf, const double *pg, size_t ld, State<R> S,
                                     size_t N, size_t c0, size_t n) {
@@ -80,6 +100,20 @@ __global__ void pops_to_coef_kernel(const double *pf, const double *pg, size_t l
   for (int q = 0; q < D::QF; ++q) F.v[q % 4][q / 4] = pf[q * ld + i];
   for (int q = 0; q < D::QG; ++q) G.v[q % 3][q / 3] = pg[q * ld + i];
   pond::ana_x(F); pond::ana_y(F); pond::ana_x(G); pond::ana_y(G);
+  const double fT = S.T[c0 + i], sT = sqrt(fT);
+  pond::scale_orders(sT, F);
+  pond::scale_orders(sT, G);
+  if (S.M) {  // mixed path: the conserved moments in FP64, v = u_frame + x
+    const size_t c = c0 + i;
+    const double fx = S.ux[c], fy = DIM == 2 ? (double)S.uy[c] : 0.0, r = F.v[0][0], bx = F.v[1][0];
+    const double by = DIM == 2 ? F.v[0][1] : 0.0;
+    double c2 = F.v[2][0] + DIM * fT * r;
+    if constexpr (DIM == 2) c2 += F.v[0][2];
+    S.M[c] = r;
+    S.M[N + c] = fx * r + bx;
+    S.M[2 * N + c] = fy * r + by;
+    S.M[3 * N + c] = 0.5 * ((fx * fx + fy * fy) * r + 2.0 * (fx * bx + fy * by) + c2) + G.v[0][0];
+  }
   for (int q = 0; q < D::QF; ++q) S.f[q * N + c0 + i] = R(F.v[q % 4][q / 4]);
   for (int q = 0; q < D::QG; ++q) S.g[q * N + c0 + i] = R(G.v[q % 3][q / 3]);
 }
@@ -93,6 +127,9 @@ __global__ void coef_to_pops_kernel(State<R> S, size_t N, size_t c0, size_t n, d
   pond::Blk<double, 3, D::NYG> G;
   for (int q = 0; q < D::QF; ++q) F.v[q % 4][q / 4] = (double)S.f[q * N + c0 + i];
   for (int q = 0; q < D::QG; ++q) G.v[q % 3][q / 3] = (double)S.g[q * N + c0 + i];
+  const double isT = 1.0 / sqrt((double)S.T[c0 + i]);
+  pond::scale_orders(isT, F);
+  pond::scale_orders(isT, G);
   pond::syn_x(F); pond::syn_y(F); pond::syn_x(G); pond::syn_y(G);
   for (int q = 0; q < D::QF; ++q) pf[q * ld + i] = F.v[q % 4][q / 4];
   for (int q = 0; q < D::QG; ++q) pg[q * ld + i] = G.v[q % 3][q / 3];
@@ -342,9 +379,9 @@ pond_status pond_workspace_size(pond_lattice lat, const int64_t dims[2], const p
   const int D = lat == POND_D2Q16 ? 2 : 1;
   const int64_t nx = dims[0], ny = D == 2 ? dims[1] : 1;
   if (nx < 2 || (D == 2 && ny < 2) || nx > (1 << 24) || ny > (1 << 24)) return POND_E_INVAL;
-  const size_t rs = p->precision == POND_FP32_MIXED ? 4 : 8;
-  const size_t per_cell = (size_t)(qf_of(D) + qg_of(D) + 3) * rs;
-  *bytes = align_up(sizeof(Stats)) + pond::kSoloTableBytes + 2 * align_up(per_cell * (size_t)(nx * ny));
+  const bool fp32 = p->precision == POND_FP32_MIXED;
+  *bytes = align_up(sizeof(Stats)) + pond::kSoloTableBytes +
+           2 * align_up(pond_detail::state_bytes(D, fp32, (size_t)(nx * ny)));
   return POND_OK;
 }
 
@@ -580,12 +617,14 @@ static pond_status state_io(pond_ctx *c, double *f, double *g, double *ux, doubl
   if (!c || !f || !g || !ux || !T || (c->D == 2 && !uy)) return POND_E_INVAL;
   const size_t N = (size_t)c->N, qf = qf_of(c->D), qg = qg_of(c->D);
   pond_status s;
-  if ((s = pops_io(c, f, g, to_state, on_device)) != POND_OK) return s;
-  // the staging buffer is reused by the frame planes
+  // the frame goes in before the populations, whose coefficients are taken in it
+  if (!to_state && (s = pops_io(c, f, g, to_state, on_device)) != POND_OK) return s;
+  // the staging buffer is shared by the populations and the frame planes
   POND_CUDA(cudaStreamSynchronize(c->stream));
   if ((s = xfer(c, ux, (qf + qg) * N, N, to_state, on_device)) != POND_OK) return s;
   if (c->D == 2 && (s = xfer(c, uy, (qf + qg + 1) * N, N, to_state, on_device)) != POND_OK) return s;
   if ((s = xfer(c, T, (qf + qg + 2) * N, N, to_state, on_device)) != POND_OK) return s;
+  if (to_state && (s = pops_io(c, f, g, to_state, on_device)) != POND_OK) return s;
   POND_CUDA(cudaStreamSynchronize(c->stream));
   return POND_OK;
 }
@@ -665,9 +704,7 @@ struct CkptHdr {
   Stats stats;
   uint64_t state_bytes;
 };
-size_t state_bytes_of(const pond_ctx *c) {
-  return (size_t)(qf_of(c->D) + qg_of(c->D) + 3) * (size_t)c->N * (c->fp32 ? 4 : 8);
-}
+size_t state_bytes_of(const pond_ctx *c) { return pond_detail::state_bytes(c->D, c->fp32, (size_t)c->N); }
 const char kCkptMagic[8] = {'P', 'O', 'N', 'D', 'C', 'K', 'P', '1'};
 }  // namespace
 

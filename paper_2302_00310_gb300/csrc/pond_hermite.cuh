@@ -1,19 +1,26 @@
 // pond_hermite.cuh -- per-axis Hermite algebra of the PonD frame transformation
 // on the Gauss-Hermite lattices of Table I (arXiv:2302.00310), for sm_103a.
 //
-// Representation.  A population vector on a q-node axis is kept as its q
-// Hermite coefficients A_n = sum_j p_j He_n(c_j) (probabilists' Hermite
-// polynomials of Appendix A).  Because the nodes are the roots of He_q, the
-// map is invertible on the lattice: p_j = w_j sum_n He_n(c_j) A_n / n!
-// (Eq. GradsProjection restricted to one axis).
+// Representation.  A population vector p_j on a q-node axis, in the frame
+// {u, T} (velocities v_j = u + sqrt(T) c_j), is kept as its q dimensional
+// Hermite coefficients B_n = sum_j p_j H_n(v_j - u; T), where
+// H_n(x; T) = T^(n/2) He_n(x / sqrt(T)) (H_0 = 1, H_1 = x, H_2 = x^2 - T,
+// H_3 = x^3 - 3 T x) and He_n are the probabilists' Hermite polynomials of
+// Appendix A.  B_n = T^(n/2) A_n with A_n the Hermite coefficients of the
+// populations, so the map is invertible on the lattice (Eq. GradsProjection
+// restricted to one axis: p_j = w_j sum_n He_n(c_j) A_n / n!, the nodes being
+// the roots of He_q).
 //
-// Frame transformation.  Moving populations from frame {u, T} to {u', T'}
-// with moments up to order K = q-1 invariant (Eq. eq:Mcondition) maps the
-// coefficients by A'_n = sum_k C_nk(a, b) A_k, with a = sqrt(T/T'),
-// b = (u - u')/sqrt(T') and He_n(a x + b) = sum_k C_nk He_k(x) (a lower
-// triangular matrix with polynomial entries).  In 2D the transformation is
-// the tensor product of the per-axis maps; the Grad projection of total order
-// K (Sec. V.A) additionally zeroes coefficients with a + b > K.
+// Frame transformation.  The generating function exp(t x - T t^2 / 2) of the
+// H_n factorises, so H_n(x + d; T') = sum_k binom(n, k) H_k(x; T) H_{n-k}(d; T' - T).
+// Moving populations from {u, T} to {u', T'} with the moments of order <= q-1
+// invariant (Eq. eq:Mcondition) therefore maps the coefficients by the unit
+// lower-triangular B'_n = sum_k binom(n, k) h_{n-k} B_k, with d = u - u' and
+// h_0 = 1, h_1 = d, h_2 = d^2 + (T - T'), h_3 = d (d^2 + 3 (T - T')): six
+// fused multiply-adds per 4-vector and no square root.  In 2D the
+// transformation is the tensor product of the per-axis maps; the Grad
+// projection of total order K (Sec. V.A) additionally zeroes coefficients
+// with a + b > K.
 //
 // Everything here is templated on the arithmetic type R (double or float).
 #pragma once
@@ -55,7 +62,8 @@ template <> struct Nodes<3> {
   static constexpr double cmax = SQ3;
 };
 
-// ---- one axis: synthesis / analysis --------------------------------------
+// ---- one axis: populations <-> thermal coefficients A_n = B_n T^(-n/2) ------
+// (the change of basis at the library boundary)
 template <typename R>
 __device__ __forceinline__ void syn4(R &a0, R &a1, R &a2, R &a3) {
   const R e1 = R(SE0_1) * a0 + R(SE2_1) * a2, o1 = R(SO1_1) * a1 + R(SO3_1) * a3;
@@ -83,45 +91,105 @@ __device__ __forceinline__ void ana3(R &p0, R &p1, R &p2) {
   p0 = A0; p1 = A1; p2 = A2;
 }
 
-// ---- one axis: Hermite shift/scale matrix C(a, b) -------------------------
-template <typename R> struct Shift {
-  R a, b, c20, c21, c22, c30, c31, c32, c33;
+// ---- one axis: values at the nodes of a frame, divided by the weights -----
+// q_j = p_j / w_j = sum_n He_n(c_j) T^(-n/2) B_n / n! at the nodes of the frame
+// with temperature T.  The constants depend only on the frame: with
+// iT = 1/T and isT = 1/sqrt(T), D1Q4 (nodes -R2, -R1, R1, R2):
+//   q(+-R_r) = (B_0 + He_2(R_r)/2 iT B_2) +- R_r isT (B_1 -+ sqrt6/6 iT B_3)
+// (He_3(R_r)/6 = R_r (R_r^2 - 3)/6 = -+ R_r sqrt6/6); D1Q3 (nodes -sqrt3, 0, sqrt3):
+//   q(+-sqrt3) = B_0 + iT B_2 +- sqrt3 isT B_1,  q(0) = B_0 - iT/2 B_2.
+constexpr double K6 = 0.408248290463863;  // sqrt(6)/6
+template <typename R, int Q> struct SynK;
+template <typename R> struct SynK<R, 4> {
+  R h1, h2, k, r1, r2;
+  __device__ __forceinline__ SynK(R iT, R isT)
+      : h1(R(0.5 * H2R1) * iT), h2(R(0.5 * H2R2) * iT), k(R(K6) * iT), r1(R(R1) * isT), r2(R(R2) * isT) {}
+};
+template <typename R> struct SynK<R, 3> {
+  R e, z, r;
+  __device__ __forceinline__ SynK(R iT, R isT) : e(iT), z(R(-0.5) * iT), r(R(SQ3) * isT) {}
 };
 template <typename R>
-__device__ __forceinline__ Shift<R> make_shift(R a, R b) {
-  Shift<R> C;
-  const R a2 = a * a, b2 = b * b, am1 = a2 - R(1), t = am1 + b2;
-  C.a = a; C.b = b;
-  C.c20 = t; C.c21 = R(2) * a * b; C.c22 = a2;
-  C.c30 = b * (b2 + R(3) * am1); C.c31 = R(3) * a * t; C.c32 = R(3) * a2 * b; C.c33 = a2 * a;
+__device__ __forceinline__ void synq(const SynK<R, 4> &S, R &m0, R &m1, R &m2, R &m3) {
+  const R e1 = fma(S.h1, m2, m0), e2 = fma(S.h2, m2, m0);
+  const R t1 = fma(-S.k, m3, m1), t2 = fma(S.k, m3, m1);
+  m0 = fma(-S.r2, t2, e2); m1 = fma(-S.r1, t1, e1); m2 = fma(S.r1, t1, e1); m3 = fma(S.r2, t2, e2);
+}
+template <typename R>
+__device__ __forceinline__ void synq(const SynK<R, 3> &S, R &m0, R &m1, R &m2) {
+  const R e = fma(S.e, m2, m0), mid = fma(S.z, m2, m0);
+  const R lo = fma(-S.r, m1, e), hi = fma(S.r, m1, e);
+  m0 = lo; m1 = mid; m2 = hi;
+}
+
+// ---- one axis: dimensional coefficients from node values q_j = p_j / w_j -------
+// B_n = T^(n/2) sum_j w_j He_n(c_j) q_j in the frame with temperature T.
+template <typename R, int Q> struct AnaK;
+template <typename R> struct AnaK<R, 4> {
+  R b11, b12, b21, b22, b31, b32;
+  __device__ __forceinline__ AnaK(R T, R sT)
+      : b11(R(W1 * R1) * sT), b12(R(W2 * R2) * sT), b21(R(W1 * H2R1) * T), b22(R(W2 * H2R2) * T),
+        b31(R(W1 * H3R1) * (T * sT)), b32(R(W2 * H3R2) * (T * sT)) {}
+};
+template <typename R> struct AnaK<R, 3> {
+  R b1, b2s, b2m;
+  __device__ __forceinline__ AnaK(R T, R sT)
+      : b1(R(SQ3 / 6.0) * sT), b2s(R(1.0 / 3.0) * T), b2m(R(-2.0 / 3.0) * T) {}
+};
+template <typename R>
+__device__ __forceinline__ void anaq(const AnaK<R, 4> &A, R &q0, R &q1, R &q2, R &q3) {
+  const R s1 = q2 + q1, d1 = q2 - q1, s2 = q3 + q0, d2 = q3 - q0;
+  q0 = fma(R(W2), s2, R(W1) * s1);
+  q1 = fma(A.b12, d2, A.b11 * d1);
+  q2 = fma(A.b22, s2, A.b21 * s1);
+  q3 = fma(A.b32, d2, A.b31 * d1);
+}
+template <typename R>
+__device__ __forceinline__ void anaq(const AnaK<R, 3> &A, R &q0, R &q1, R &q2) {
+  const R s = q0 + q2, d = q2 - q0;
+  const R B0 = fma(R(2.0 / 3.0), q1, R(1.0 / 6.0) * s), B2 = fma(A.b2m, q1, A.b2s * s);
+  q0 = B0; q1 = A.b1 * d; q2 = B2;
+}
+
+// ---- one axis: the frame change of dimensional coefficients ---------------
+// d = u - u', dT = T - T' (dT3 = 3 dT, shared by the axes of one change)
+template <typename R> struct DShift {
+  R d, d2, d3, g2, g2x3, g3;
+};
+template <typename R>
+__device__ __forceinline__ DShift<R> make_dshift(R d, R dT, R dT3) {
+  DShift<R> C;
+  C.d = d; C.d2 = d + d; C.d3 = R(3) * d;
+  C.g2 = fma(d, d, dT); C.g2x3 = R(3) * C.g2;
+  C.g3 = d * fma(d, d, dT3);
   return C;
 }
 template <typename R>
-__device__ __forceinline__ void shift4(const Shift<R> &C, R &m0, R &m1, R &m2, R &m3) {
-  const R n3 = C.c30 * m0 + C.c31 * m1 + C.c32 * m2 + C.c33 * m3;
-  const R n2 = C.c20 * m0 + C.c21 * m1 + C.c22 * m2;
-  const R n1 = C.b * m0 + C.a * m1;
-  m1 = n1; m2 = n2; m3 = n3;
+__device__ __forceinline__ void dshift4(const DShift<R> &C, R &m0, R &m1, R &m2, R &m3) {
+  m3 = fma(C.g3, m0, fma(C.g2x3, m1, fma(C.d3, m2, m3)));
+  m2 = fma(C.g2, m0, fma(C.d2, m1, m2));
+  m1 = fma(C.d, m0, m1);
 }
 template <typename R>
-__device__ __forceinline__ void shift3(const Shift<R> &C, R &m0, R &m1, R &m2) {
-  const R n2 = C.c20 * m0 + C.c21 * m1 + C.c22 * m2;
-  const R n1 = C.b * m0 + C.a * m1;
-  m1 = n1; m2 = n2;
+__device__ __forceinline__ void dshift3(const DShift<R> &C, R &m0, R &m1, R &m2) {
+  m2 = fma(C.g2, m0, fma(C.d2, m1, m2));
+  m1 = fma(C.d, m0, m1);
 }
 
-// ---- one axis: multiplication of the populations by v = u + s c ----------
-// c He_n = He_{n+1} + n He_{n-1}; He_q vanishes on the q nodes, so the map is
-// exact on the lattice: B_k = k A_{k-1} + A_{k+1} (A_q = 0).
+// ---- one axis: multiplication of the populations by v = u + x --------------
+// x H_k(x; T) = H_{k+1} + k T H_{k-1}, and H_q(., T) vanishes on the q nodes of
+// the frame, so on the lattice the coefficients of v p are
+// u B_k + B_{k+1} + k T B_{k-1} (B_q = 0).
 template <typename R>
-__device__ __forceinline__ void vmul4(R u, R s, R &a0, R &a1, R &a2, R &a3) {
-  const R b0 = a1, b1 = a0 + a2, b2 = R(2) * a1 + a3, b3 = R(3) * a2;
-  a0 = u * a0 + s * b0; a1 = u * a1 + s * b1; a2 = u * a2 + s * b2; a3 = u * a3 + s * b3;
+__device__ __forceinline__ void dvmul4(R u, R T, R &a0, R &a1, R &a2, R &a3) {
+  const R b0 = fma(u, a0, a1), b1 = fma(u, a1, fma(T, a0, a2));
+  const R b2 = fma(u, a2, fma(T + T, a1, a3)), b3 = fma(u, a3, (R(3) * T) * a2);
+  a0 = b0; a1 = b1; a2 = b2; a3 = b3;
 }
 template <typename R>
-__device__ __forceinline__ void vmul3(R u, R s, R &a0, R &a1, R &a2) {
-  const R b0 = a1, b1 = a0 + a2, b2 = R(2) * a1;
-  a0 = u * a0 + s * b0; a1 = u * a1 + s * b1; a2 = u * a2 + s * b2;
+__device__ __forceinline__ void dvmul3(R u, R T, R &a0, R &a1, R &a2) {
+  const R b0 = fma(u, a0, a1), b1 = fma(u, a1, fma(T, a0, a2)), b2 = fma(u, a2, (T + T) * a1);
+  a0 = b0; a1 = b1; a2 = b2;
 }
 
 // ---- coefficient blocks: A[x-order][y-order], NY = 1 in 1D ---------------
@@ -166,39 +234,83 @@ __device__ __forceinline__ void ana_y(Blk<R, Q, NY> &B) {
   }
 }
 template <typename R, int Q, int NY>
-__device__ __forceinline__ void shift_x(const Shift<R> &C, Blk<R, Q, NY> &B) {
+__device__ __forceinline__ void shift_x(const DShift<R> &C, Blk<R, Q, NY> &B) {
 #pragma unroll
   for (int m = 0; m < NY; ++m) {
-    if constexpr (Q == 4) shift4(C, B.v[0][m], B.v[1][m], B.v[2][m], B.v[3][m]);
-    else shift3(C, B.v[0][m], B.v[1][m], B.v[2][m]);
+    if constexpr (Q == 4) dshift4(C, B.v[0][m], B.v[1][m], B.v[2][m], B.v[3][m]);
+    else dshift3(C, B.v[0][m], B.v[1][m], B.v[2][m]);
   }
 }
 template <typename R, int Q, int NY>
-__device__ __forceinline__ void shift_y(const Shift<R> &C, Blk<R, Q, NY> &B) {
+__device__ __forceinline__ void shift_y(const DShift<R> &C, Blk<R, Q, NY> &B) {
   if constexpr (NY > 1) {
 #pragma unroll
     for (int n = 0; n < Q; ++n) {
-      if constexpr (Q == 4) shift4(C, B.v[n][0], B.v[n][1], B.v[n][2], B.v[n][3]);
-      else shift3(C, B.v[n][0], B.v[n][1], B.v[n][2]);
+      if constexpr (Q == 4) dshift4(C, B.v[n][0], B.v[n][1], B.v[n][2], B.v[n][3]);
+      else dshift3(C, B.v[n][0], B.v[n][1], B.v[n][2]);
     }
   }
 }
-// multiply by v_axis = u + s c_axis
+// node values / weights in the frame of S, x then y
+template <typename R, int Q, int NY>
+__device__ __forceinline__ void synq_xy(const SynK<R, Q> &S, Blk<R, Q, NY> &B) {
+#pragma unroll
+  for (int m = 0; m < NY; ++m) {
+    if constexpr (Q == 4) synq(S, B.v[0][m], B.v[1][m], B.v[2][m], B.v[3][m]);
+    else synq(S, B.v[0][m], B.v[1][m], B.v[2][m]);
+  }
+  if constexpr (NY > 1) {
+#pragma unroll
+    for (int n = 0; n < Q; ++n) {
+      if constexpr (Q == 4) synq(S, B.v[n][0], B.v[n][1], B.v[n][2], B.v[n][3]);
+      else synq(S, B.v[n][0], B.v[n][1], B.v[n][2]);
+    }
+  }
+}
+// dimensional coefficients in the frame of A from node values / weights
+template <typename R, int Q, int NY>
+__device__ __forceinline__ void anaq_xy(const AnaK<R, Q> &A, Blk<R, Q, NY> &B) {
+#pragma unroll
+  for (int m = 0; m < NY; ++m) {
+    if constexpr (Q == 4) anaq(A, B.v[0][m], B.v[1][m], B.v[2][m], B.v[3][m]);
+    else anaq(A, B.v[0][m], B.v[1][m], B.v[2][m]);
+  }
+  if constexpr (NY > 1) {
+#pragma unroll
+    for (int n = 0; n < Q; ++n) {
+      if constexpr (Q == 4) anaq(A, B.v[n][0], B.v[n][1], B.v[n][2], B.v[n][3]);
+      else anaq(A, B.v[n][0], B.v[n][1], B.v[n][2]);
+    }
+  }
+}
+// multiply by v_axis = u + x in the frame with temperature T
 template <int AX, typename R, int Q, int NY>
-__device__ __forceinline__ void vmul(R u, R s, Blk<R, Q, NY> &B) {
+__device__ __forceinline__ void vmul(R u, R T, Blk<R, Q, NY> &B) {
   if constexpr (AX == 0) {
 #pragma unroll
     for (int m = 0; m < NY; ++m) {
-      if constexpr (Q == 4) vmul4(u, s, B.v[0][m], B.v[1][m], B.v[2][m], B.v[3][m]);
-      else vmul3(u, s, B.v[0][m], B.v[1][m], B.v[2][m]);
+      if constexpr (Q == 4) dvmul4(u, T, B.v[0][m], B.v[1][m], B.v[2][m], B.v[3][m]);
+      else dvmul3(u, T, B.v[0][m], B.v[1][m], B.v[2][m]);
     }
   } else {
 #pragma unroll
     for (int n = 0; n < Q; ++n) {
-      if constexpr (Q == 4) vmul4(u, s, B.v[n][0], B.v[n][1], B.v[n][2], B.v[n][3]);
-      else vmul3(u, s, B.v[n][0], B.v[n][1], B.v[n][2]);
+      if constexpr (Q == 4) dvmul4(u, T, B.v[n][0], B.v[n][1], B.v[n][2], B.v[n][3]);
+      else dvmul3(u, T, B.v[n][0], B.v[n][1], B.v[n][2]);
     }
   }
+}
+// scale coefficient B_ab by s^(a+b) (between thermal and dimensional units)
+template <typename R, int Q, int NY>
+__device__ __forceinline__ void scale_orders(R s, Blk<R, Q, NY> &B) {
+  R p[2 * Q - 1];
+  p[0] = R(1);
+#pragma unroll
+  for (int i = 1; i < 2 * Q - 1; ++i) p[i] = p[i - 1] * s;
+#pragma unroll
+  for (int n = 0; n < Q; ++n)
+#pragma unroll
+    for (int m = 0; m < NY; ++m) B.v[n][m] *= p[n + m];
 }
 // Grad projection of total order Q-1: drop coefficients with a + b > Q-1
 template <typename R, int Q, int NY>

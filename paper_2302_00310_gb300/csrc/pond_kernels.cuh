@@ -14,13 +14,15 @@
 //   C. every cell of the tile: face phi moved into the cell frame and
 //      multiplied by v.n (Eq. fluxEq), DUGKS update (Eq. eq:FinalUpdateDUGKS),
 //      new co-moving frame, second QE half step, store.
-// All linear algebra is done on Hermite coefficients (pond_hermite.cuh), and
-// the state itself is stored as each cell's Hermite coefficients
-// A_ab = sum_i phi_i He_a(c_ix) He_b(c_iy) (an invertible change of basis on
-// the lattice, Eq. GradsProjection): a step needs no synthesis or analysis of
-// its own cells, and the conserved moments are stored values (rho = A_00).
-// Populations are synthesised only where the limiter needs them (the stencil
-// in the face frame) and at the library boundary.
+// All linear algebra is done on dimensional Hermite coefficients
+// (pond_hermite.cuh), and the state itself is stored as each cell's
+// B_ab = sum_i phi_i H_a(v_ix - u_x; T) H_b(v_iy - u_y; T) in its frame {u, T}
+// (an invertible change of basis on the lattice, Eq. GradsProjection): a step
+// needs no synthesis or analysis of its own cells, the conserved moments are
+// stored values (rho = B_00, rho (u - u_frame) = B_10), and a frame change is
+// a unit-triangular map with no square root.  Populations (divided by the
+// lattice weights) are synthesised only where the limiter needs them (the
+// stencil in the face frame) and at the library boundary.
 #pragma once
 #include <cstdint>
 #include <type_traits>
@@ -63,9 +65,13 @@ template <> __device__ __forceinline__ double kc<double>(double d, float) { retu
 template <> __device__ __forceinline__ float kc<float>(double, float f) { return f; }
 
 // State planes (SoA, x fastest): f[a + 4b][N] and g[a + 3b][N] are the
-// Hermite coefficients A_ab of phi~ (g: B_ab) in the cell's frame (ux, uy, T).
+// dimensional Hermite coefficients B_ab of phi~ in the cell's frame (ux, uy, T).
+// Mixed path: M[4][N] are each cell's conserved moments rho, rho ux, rho uy,
+// rho E (Eqs. eq::ConservationLaws, eq:E) in FP64, the sums a step adds the
+// face fluxes to (the coefficients hold them rounded to FP32); null in FP64.
 template <typename R> struct State {
   R *f, *g, *ux, *uy, *T;
+  double *M;
 };
 
 struct Stats {
@@ -80,14 +86,14 @@ template <int DIM> struct Dims {
   static constexpr int QG = DIM == 2 ? 9 : 3;
   static constexpr int NYF = DIM == 2 ? 4 : 1;
   static constexpr int NYG = DIM == 2 ? 3 : 1;
-  // shared-memory record of a halo cell: f coeffs, g coeffs, ux, uy, T, sqrt T
+  // shared-memory record of a halo cell: f coeffs, g coeffs, ux, uy, T, and
+  // (mixed path) sqrt T
   static constexpr int IUX = QF + QG, IUY = IUX + 1, IT = IUX + 2, IST = IUX + 3;
   static constexpr int NPREP = QF + QG + 4;
-  // shared-memory record of a face: f coeffs, g coeffs, uFx, uFy, sqrt TF, TF,
-  // and (mixed path) the conserved fluxes: mass, x-, y-momentum, energy
-  static constexpr int FUX = QF + QG, FUY = FUX + 1, FST = FUX + 2, FT = FUX + 3;
+  // shared-memory record of a face: f coeffs, g coeffs, uFx, uFy, TF, and
+  // (mixed path) sqrt TF and the conserved fluxes: mass, x-, y-momentum, energy
+  static constexpr int FUX = QF + QG, FUY = FUX + 1, FT = FUX + 2, FST = FUX + 3;
   static constexpr int FJ = FUX + 4;
-  // (TF is read only by the mixed path's FP64 fallback, the fluxes only by the mixed path)
   template <typename R> static constexpr int nface() {
     return std::is_same<R, float>::value ? QF + QG + 8 : QF + QG + 3;
   }
@@ -156,6 +162,13 @@ __device__ __forceinline__ double div_nr(double x, double y) {
   return fma(fma(-y, q, x), r, q);
 }
 __device__ __forceinline__ float div_nr(float x, float y) { return __fdividef(x, y); }
+// 1/y to about 2^-40: the hardware approximation refined by one Newton step
+// (for values that are rounded to FP32 afterwards)
+__device__ __forceinline__ double rcp_nr1(double y) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(y));
+  return fma(r, fma(-y, r, 1.0), r);
+}
 
 // sign tests on the integer image (no FP64-pipe compare): v > 0 and
 // |x| < |y|.  Positive subnormals below 2^-1022 count as zero.
@@ -189,35 +202,35 @@ __device__ __noinline__ void move_frame_fp64(float usx, float usy, float Ts, flo
   for (int n = 0; n < Q; ++n)
 #pragma unroll
     for (int m = 0; m < NY; ++m) Z.v[n][m] = Y.v[n][m];
-  const double isT = 1.0 / sqrt((double)Tt), a64 = sqrt((double)Ts) * isT;
-  shift_x(make_shift(a64, ((double)usx - (double)utx) * isT), Z);
-  if constexpr (DIM == 2) shift_y(make_shift(a64, ((double)usy - (double)uty) * isT), Z);
+  const double dT = (double)Ts - (double)Tt, dT3 = 3.0 * dT;
+  shift_x(make_dshift((double)usx - (double)utx, dT, dT3), Z);
+  if constexpr (DIM == 2) shift_y(make_dshift((double)usy - (double)uty, dT, dT3), Z);
 #pragma unroll
   for (int n = 0; n < Q; ++n)
 #pragma unroll
     for (int m = 0; m < NY; ++m) Y.v[n][m] = (float)Z.v[n][m];
 }
 
-// Moves Hermite coefficients Y (Q nodes per axis) from the frame {us, Ts} to
-// {ut, Tt} (Sec. II.B): per axis the Hermite shift C(a, b) with
-// a = sqrt(Ts/Tt), b = (us - ut)/sqrt(Tt); sTs = sqrt(Ts) and
-// isTt = 1/sqrt(Tt) are given.  On the mixed path a transformation whose
-// nodes land far out (max_j |a c_j + b| > xi_thr: large, cancelling shift
-// coefficients, as at large temperature ratios) is built and applied in FP64.
+// Moves dimensional Hermite coefficients Y (Q nodes per axis) from the frame
+// {us, Ts} to {ut, Tt} (Sec. II.B): per axis the unit-triangular map of
+// d = us - ut and Ts - Tt.  On the mixed path a transformation whose source
+// nodes land far out in the target frame (max_j |sqrt(Ts) c_j + d| >
+// xi_thr sqrt(Tt): large, cancelling coefficients, as at large temperature
+// ratios) is built and applied in FP64; sTs, sTt = sqrt(Ts), sqrt(Tt) are read
+// only by that test.
 template <typename R, int DIM, int Q>
 __device__ __forceinline__ void move_frame(const StepConst &K, R usx, R usy, R Ts, R sTs, R utx,
-                                           R uty, R Tt, R isTt, Blk<R, Q, (DIM == 2 ? Q : 1)> &Y) {
-  constexpr int NY = DIM == 2 ? Q : 1;
-  const R a = sTs * isTt, bx = (usx - utx) * isTt;
-  const R by = DIM == 2 ? (usy - uty) * isTt : R(0);
+                                           R uty, R Tt, R sTt, Blk<R, Q, (DIM == 2 ? Q : 1)> &Y) {
+  const R dx = usx - utx, dy = DIM == 2 ? usy - uty : R(0), dT = Ts - Tt;
   if constexpr (is_mixed<R>()) {
-    if (a * R(Nodes<Q>::cmax) + fmaxf(fabsf(bx), fabsf(by)) > K.xi_thr) {
+    if (fmaf(sTs, float(Nodes<Q>::cmax), fmaxf(fabsf(dx), fabsf(dy))) > K.xi_thr * sTt) {
       move_frame_fp64<DIM, Q>(usx, usy, Ts, utx, uty, Tt, Y);
       return;
     }
   }
-  shift_x(make_shift(a, bx), Y);
-  if constexpr (DIM == 2) shift_y(make_shift(a, by), Y);
+  const R dT3 = R(3) * dT;
+  shift_x(make_dshift(dx, dT, dT3), Y);
+  if constexpr (DIM == 2) shift_y(make_dshift(dy, dT, dT3), Y);
 }
 
 // ---- phase A: one halo cell -> shared memory ------------------------------
@@ -280,15 +293,17 @@ __device__ __forceinline__ void prep_cell(const StepConst &K, const State<R> &S,
   sp[D::IUX * NH + h] = ux;
   sp[D::IUY * NH + h] = uy;
   sp[D::IT * NH + h] = T;
-  sp[D::IST * NH + h] = sqrt(T);
+  if constexpr (is_mixed<R>()) sp[D::IST * NH + h] = sqrt(T);
 }
 
 // ---- phase B helpers --------------------------------------------------------
-// phi_bar^+ of halo cell h (times kappa1) moved into the face frame and
-// synthesised into populations Y[x-node][y-node].
+// phi_bar^+ of halo cell h (times kappa1) moved into the face frame
+// {uF, TF} and synthesised into node values divided by the weights,
+// Y[x-node][y-node] (SK: the face frame's synthesis constants).
 template <typename R, int DIM, int Q>
 __device__ __forceinline__ void stencil_pops_body(const StepConst &K, const R *sp, int NH, int h, R uFx,
-                                                  R uFy, R TF, R isTF, Blk<R, Q, (DIM == 2 ? Q : 1)> &Y) {
+                                                  R uFy, R TF, R sTF, const SynK<R, Q> &SK,
+                                                  Blk<R, Q, (DIM == 2 ? Q : 1)> &Y) {
   using D = Dims<DIM>;
   constexpr int NY = DIM == 2 ? Q : 1;
   constexpr int base = Q == 4 ? 0 : D::QF;
@@ -296,13 +311,12 @@ __device__ __forceinline__ void stencil_pops_body(const StepConst &K, const R *s
   for (int n = 0; n < Q; ++n)
 #pragma unroll
     for (int m = 0; m < NY; ++m) Y.v[n][m] = sp[(base + n + Q * m) * NH + h];
-  move_frame<R, DIM, Q>(K, sp[D::IUX * NH + h], DIM == 2 ? sp[D::IUY * NH + h] : R(0),
-                        sp[D::IT * NH + h], sp[D::IST * NH + h], uFx, uFy, TF, isTF, Y);
+  move_frame<R, DIM, Q>(K, sp[D::IUX * NH + h], DIM == 2 ? sp[D::IUY * NH + h] : R(0), sp[D::IT * NH + h],
+                        is_mixed<R>() ? sp[D::IST * NH + h] : R(0), uFx, uFy, TF, sTF, Y);
   if constexpr (DIM == 2) {
     if (K.grad_k) grad_mask(Y);
   }
-  syn_x(Y);
-  syn_y(Y);
+  synq_xy(SK, Y);
 }
 // The mixed path calls one out-of-line copy of the stencil transformation per
 // lattice (16 call sites per face direction): the FP32 kernel is bound by
@@ -311,20 +325,22 @@ __device__ __forceinline__ void stencil_pops_body(const StepConst &K, const R *s
 template <typename R, int DIM, int Q>
 __device__ __noinline__ Blk<R, Q, (DIM == 2 ? Q : 1)> stencil_pops_call(const StepConst &K, const R *sp,
                                                                       int NH, int h, R uFx, R uFy,
-                                                                      R TF, R isTF) {
+                                                                      R TF, R sTF, SynK<R, Q> SK) {
   Blk<R, Q, (DIM == 2 ? Q : 1)> Y;  // returned by value: in registers, not through local memory
-  stencil_pops_body<R, DIM, Q>(K, sp, NH, h, uFx, uFy, TF, isTF, Y);
+  stencil_pops_body<R, DIM, Q>(K, sp, NH, h, uFx, uFy, TF, sTF, SK, Y);
   return Y;
 }
 template <typename R, int DIM, int Q>
 __device__ __forceinline__ void stencil_pops(const StepConst &K, const R *sp, int NH, int h, R uFx,
-                                             R uFy, R TF, R isTF, Blk<R, Q, (DIM == 2 ? Q : 1)> &Y) {
-  if constexpr (is_mixed<R>()) Y = stencil_pops_call<R, DIM, Q>(K, sp, NH, h, uFx, uFy, TF, isTF);
-  else stencil_pops_body<R, DIM, Q>(K, sp, NH, h, uFx, uFy, TF, isTF, Y);
+                                             R uFy, R TF, R sTF, const SynK<R, Q> &SK,
+                                             Blk<R, Q, (DIM == 2 ? Q : 1)> &Y) {
+  if constexpr (is_mixed<R>()) Y = stencil_pops_call<R, DIM, Q>(K, sp, NH, h, uFx, uFy, TF, sTF, SK);
+  else stencil_pops_body<R, DIM, Q>(K, sp, NH, h, uFx, uFy, TF, sTF, SK, Y);
 }
 
 // Limited half-step MUSCL trace of the populations of one lattice (Q nodes
-// per axis) to the face (Eq. eq:InterfacePop).  st[] = halo indices of the
+// per axis) to the face (Eq. eq:InterfacePop), on node values divided by
+// the weights (the trace is homogeneous of degree 1 in each node's values).  st[] = halo indices of the
 // stencil: 0 left, 1 right, 2 outer-left, 3 outer-right, 4/5 lower tangential
 // neighbour of left/right, 6/7 upper tangential neighbour of left/right.
 // With a = upwind value, b = its outer neighbour, c = the downwind value, the
@@ -335,6 +351,7 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
                                             R uFx, R uFy, R TF, R sTF, R isTF,
                                             Blk<R, Q, (DIM == 2 ? Q : 1)> &out) {
   constexpr int NY = DIM == 2 ? Q : 1;
+  const SynK<R, Q> SK(isTF * isTF, isTF);
   const R uFn = DIRN == 0 ? uFx : uFy, uFt = DIRN == 0 ? uFy : uFx;
   const R hl = R(0.5) * kc<R>(K.lam, K.cf.lam);
   const int lim = K.limiter;
@@ -349,12 +366,12 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
     offt[k] = -hl * (sTF * c + uFt);
   }
   Blk<R, Q, NY> YL, YR, A;
-  stencil_pops<R, DIM, Q>(K, sp, NH, st[0], uFx, uFy, TF, isTF, YL);
-  stencil_pops<R, DIM, Q>(K, sp, NH, st[1], uFx, uFy, TF, isTF, YR);
+  stencil_pops<R, DIM, Q>(K, sp, NH, st[0], uFx, uFy, TF, sTF, SK, YL);
+  stencil_pops<R, DIM, Q>(K, sp, NH, st[1], uFx, uFy, TF, sTF, SK, YR);
   {
     Blk<R, Q, NY> Y1, Y2;
-    stencil_pops<R, DIM, Q>(K, sp, NH, st[2], uFx, uFy, TF, isTF, Y1);
-    stencil_pops<R, DIM, Q>(K, sp, NH, st[3], uFx, uFy, TF, isTF, Y2);
+    stencil_pops<R, DIM, Q>(K, sp, NH, st[2], uFx, uFy, TF, sTF, SK, Y1);
+    stencil_pops<R, DIM, Q>(K, sp, NH, st[3], uFx, uFy, TF, sTF, SK, Y2);
 #pragma unroll
     for (int n = 0; n < Q; ++n)
 #pragma unroll
@@ -369,8 +386,8 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
   }
   if constexpr (DIM == 2) {
     Blk<R, Q, NY> Y1, Y2, Dl;
-    stencil_pops<R, DIM, Q>(K, sp, NH, st[4], uFx, uFy, TF, isTF, Y1);
-    stencil_pops<R, DIM, Q>(K, sp, NH, st[5], uFx, uFy, TF, isTF, Y2);
+    stencil_pops<R, DIM, Q>(K, sp, NH, st[4], uFx, uFy, TF, sTF, SK, Y1);
+    stencil_pops<R, DIM, Q>(K, sp, NH, st[5], uFx, uFy, TF, sTF, SK, Y2);
 #pragma unroll
     for (int n = 0; n < Q; ++n)
 #pragma unroll
@@ -378,8 +395,8 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
         const int k = DIRN == 0 ? n : m;
         Dl.v[n][m] = A.v[n][m] - (up[k] ? Y1.v[n][m] : Y2.v[n][m]);
       }
-    stencil_pops<R, DIM, Q>(K, sp, NH, st[6], uFx, uFy, TF, isTF, Y1);
-    stencil_pops<R, DIM, Q>(K, sp, NH, st[7], uFx, uFy, TF, isTF, Y2);
+    stencil_pops<R, DIM, Q>(K, sp, NH, st[6], uFx, uFy, TF, sTF, SK, Y1);
+    stencil_pops<R, DIM, Q>(K, sp, NH, st[7], uFx, uFy, TF, sTF, SK, Y2);
 #pragma unroll
     for (int n = 0; n < Q; ++n)
 #pragma unroll
@@ -391,15 +408,16 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
   }
 }
 
-// Gaussian expectations E[He_n(s Z + mu)], n <= 3, Z ~ N(0,1), s^2 - 1 = sm1:
-// the Hermite coefficients of an equilibrium seen from a foreign frame
-// (Gauss-Hermite quadrature is exact to degree 2q-1, so rho G W has them).
+// Gaussian expectations E[H_n(mu + X; TF)], X ~ N(0, Tb), n <= 3, with
+// dT = Tb - TF: by the addition theorem of the H_n, H_n(mu; TF - Tb), i.e. the
+// dimensional Hermite coefficients of an equilibrium {u_b, Tb} seen from the
+// face frame (Gauss-Hermite quadrature is exact to degree 2q-1, so rho G W has
+// them).
 template <typename R>
-__device__ __forceinline__ void gauss_he(R mu, R sm1, R &e1, R &e2, R &e3) {
-  const R mu2 = mu * mu;
+__device__ __forceinline__ void gauss_he(R mu, R dT, R &e1, R &e2, R &e3) {
   e1 = mu;
-  e2 = mu2 + sm1;
-  e3 = mu * (mu2 + R(3) * sm1);
+  e2 = fma(mu, mu, dT);
+  e3 = mu * fma(mu, mu, R(3) * dT);
 }
 
 // ---- phase B: one face --------------------------------------------------------
@@ -431,16 +449,17 @@ __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int N
   while (true) {
     reconstruct<R, DIM, DIRN, 4>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, Fb);
     reconstruct<R, DIM, DIRN, 3>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, Gb);
-    ana_x(Fb); ana_y(Fb); ana_x(Gb); ana_y(Gb);
-    // interface moments in the face frame (all carry the factor kappa1):
-    // rho, mu = (u - u_F)/sqrt(T_F), C_v rho T = T_F/2 (sum |c|^2 f - rho mu^2) + sum g
+    anaq_xy(AnaK<R, 4>(TF, sTF), Fb);
+    anaq_xy(AnaK<R, 3>(TF, sTF), Gb);
+    // interface moments in the face frame (all carry the factor kappa1): rho,
+    // mu = u - u_F, C_v rho T = (sum |v - u_F|^2 f - rho |mu|^2)/2 + sum g
     rk = Fb.v[0][0];
     const R irk = R(1) / rk;
     mx = Fb.v[1][0] * irk;
     my = R(0);
-    R S2 = Fb.v[2][0] + R(DIM) * rk;
+    R S2 = fma(R(DIM) * TF, rk, Fb.v[2][0]);
     if constexpr (DIM == 2) { my = Fb.v[0][1] * irk; S2 += Fb.v[0][2]; }
-    const R ek = R(0.5) * TF * (S2 - rk * (mx * mx + my * my)) + Gb.v[0][0];
+    const R ek = R(0.5) * (S2 - rk * (mx * mx + my * my)) + Gb.v[0][0];
     Tb = ek * irk * kc<R>(K.inv_cv, K.cf.inv_cv);
     if constexpr (!ITER) {
       break;
@@ -456,25 +475,26 @@ __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int N
         break;
       }
       const double mxd = mx, myd = my;
-      const double err = fmax(sqrt(mxd * mxd + myd * myd), fabs((double)Tb - (double)TF) / (double)TF);
+      const double err = fmax(sqrt(mxd * mxd + myd * myd) / sqrt((double)TF),
+                              fabs((double)Tb - (double)TF) / (double)TF);
       if (err < K.iter_tol) { converged = true; break; }
       if (++it >= (K.iter_max > 0 ? K.iter_max : 1)) break;
       pFx = uFx; pFy = uFy; pT = TF;
-      uFx = uFx + sTF * mx;
-      if constexpr (DIM == 2) uFy = uFy + sTF * my;
+      uFx = uFx + mx;
+      if constexpr (DIM == 2) uFy = uFy + my;
       TF = Tb;
       sTF = sqrt(TF); isTF = R(1) / sTF;
     }
   }
   if constexpr (ITER) noconv = !converged;
-  const R sm1 = Tb * isTF * isTF - R(1);
+  const R dTb = Tb - TF;
 
   // equilibrium (closed form of rho G_{u,T}^{lambda_F} W), weighted by kappa2/kappa1;
   // a converged iterated frame is co-moving: rho W
   R ex[4], ey[4];
-  ex[0] = R(1); gauss_he(mx, sm1, ex[1], ex[2], ex[3]);
+  ex[0] = R(1); gauss_he(mx, dTb, ex[1], ex[2], ex[3]);
   ey[0] = R(1); ey[1] = ey[2] = ey[3] = R(0);
-  if constexpr (DIM == 2) gauss_he(my, sm1, ey[1], ey[2], ey[3]);
+  if constexpr (DIM == 2) gauss_he(my, dTb, ey[1], ey[2], ey[3]);
   if constexpr (ITER) {
     if (converged) ex[1] = ex[2] = ex[3] = ey[1] = ey[2] = ey[3] = R(0);
   }
@@ -502,8 +522,8 @@ __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int N
   // Appendix C form: transport v_n^{lambda_F} phi in the face frame
   if (K.appc) {
     const R un = DIRN == 0 ? uFx : uFy;
-    vmul<DIRN>(un, sTF, Fb);
-    vmul<DIRN>(un, sTF, Gb);
+    vmul<DIRN>(un, TF, Fb);
+    vmul<DIRN>(un, TF, Gb);
   }
   if constexpr (is_mixed<R>()) {
     // Mixed path: the face's conserved fluxes (mass, momentum, energy along the
@@ -511,36 +531,38 @@ __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int N
     // opposite amounts to their FP64 moment sums.  They are moments of order
     // <= 3 of v_n phi (<= 1 of v_n g), which every frame transformation keeps
     // (Eq. eq:Mcondition), so the face frame gives the same values as the cell
-    // frames of Eq. fluxEq.  C = Hermite coefficients of v_n phi (low orders).
+    // frames of Eq. fluxEq.  C = dimensional coefficients of v_n phi (low
+    // orders): x H_k = H_{k+1} + k T_F H_{k-1} along the normal.
     const R un = DIRN == 0 ? uFx : uFy;
     R C00, C10, C01 = R(0), C20, C02 = R(0), CG;
     if (K.appc) {  // Fb, Gb already hold v_n phi
       C00 = Fb.v[0][0]; C10 = Fb.v[1][0]; C20 = Fb.v[2][0]; CG = Gb.v[0][0];
       if constexpr (DIM == 2) { C01 = Fb.v[0][1]; C02 = Fb.v[0][2]; }
-    } else if constexpr (DIRN == 0) {  // c He_n = He_{n+1} + n He_{n-1} along x
-      C00 = un * Fb.v[0][0] + sTF * Fb.v[1][0];
-      C10 = un * Fb.v[1][0] + sTF * (Fb.v[0][0] + Fb.v[2][0]);
-      C20 = un * Fb.v[2][0] + sTF * (R(2) * Fb.v[1][0] + Fb.v[3][0]);
-      CG = un * Gb.v[0][0] + sTF * Gb.v[1][0];
+    } else if constexpr (DIRN == 0) {
+      C00 = fma(un, Fb.v[0][0], Fb.v[1][0]);
+      C10 = fma(un, Fb.v[1][0], fma(TF, Fb.v[0][0], Fb.v[2][0]));
+      C20 = fma(un, Fb.v[2][0], fma(TF + TF, Fb.v[1][0], Fb.v[3][0]));
+      CG = fma(un, Gb.v[0][0], Gb.v[1][0]);
       if constexpr (DIM == 2) {
-        C01 = un * Fb.v[0][1] + sTF * Fb.v[1][1];
-        C02 = un * Fb.v[0][2] + sTF * Fb.v[1][2];
+        C01 = fma(un, Fb.v[0][1], Fb.v[1][1]);
+        C02 = fma(un, Fb.v[0][2], Fb.v[1][2]);
       }
-    } else {  // along y
-      C00 = un * Fb.v[0][0] + sTF * Fb.v[0][1];
-      C01 = un * Fb.v[0][1] + sTF * (Fb.v[0][0] + Fb.v[0][2]);
-      C02 = un * Fb.v[0][2] + sTF * (R(2) * Fb.v[0][1] + Fb.v[0][3]);
-      C10 = un * Fb.v[1][0] + sTF * Fb.v[1][1];
-      C20 = un * Fb.v[2][0] + sTF * Fb.v[2][1];
-      CG = un * Gb.v[0][0] + sTF * Gb.v[0][1];
+    } else {
+      C00 = fma(un, Fb.v[0][0], Fb.v[0][1]);
+      C01 = fma(un, Fb.v[0][1], fma(TF, Fb.v[0][0], Fb.v[0][2]));
+      C02 = fma(un, Fb.v[0][2], fma(TF + TF, Fb.v[0][1], Fb.v[0][3]));
+      C10 = fma(un, Fb.v[1][0], Fb.v[1][1]);
+      C20 = fma(un, Fb.v[2][0], Fb.v[2][1]);
+      CG = fma(un, Gb.v[0][0], Gb.v[0][1]);
     }
-    // v = u_F + sqrt(T_F) c: sum v_n phi, sum v v_n phi, sum (|v|^2/2) v_n phi + sum v_n g
-    const R c2 = C20 + C02 + R(DIM) * C00;
+    // v = u_F + x: sum v_n phi, sum v v_n phi, sum (|v|^2/2) v_n phi + sum v_n g
+    const R c2 = fma(R(DIM) * TF, C00, C20 + C02);
     fp[(D::FJ + 0) * NFACES + fidx] = C00;
-    fp[(D::FJ + 1) * NFACES + fidx] = uFx * C00 + sTF * C10;
-    fp[(D::FJ + 2) * NFACES + fidx] = uFy * C00 + sTF * C01;
+    fp[(D::FJ + 1) * NFACES + fidx] = fma(uFx, C00, C10);
+    fp[(D::FJ + 2) * NFACES + fidx] = fma(uFy, C00, C01);
     fp[(D::FJ + 3) * NFACES + fidx] =
-        R(0.5) * ((uFx * uFx + uFy * uFy) * C00 + R(2) * sTF * (uFx * C10 + uFy * C01) + TF * c2) + CG;
+        R(0.5) * ((uFx * uFx + uFy * uFy) * C00 + R(2) * (uFx * C10 + uFy * C01) + c2) + CG;
+    fp[D::FST * NFACES + fidx] = sTF;
   }
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -552,23 +574,24 @@ __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int N
     for (int b = 0; b < NYG; ++b) fp[(D::QF + a + 3 * b) * NFACES + fidx] = Gb.v[a][b];
   fp[D::FUX * NFACES + fidx] = uFx;
   fp[D::FUY * NFACES + fidx] = uFy;
-  fp[D::FST * NFACES + fidx] = sTF;
-  if constexpr (is_mixed<R>()) fp[D::FT * NFACES + fidx] = TF;
+  fp[D::FT * NFACES + fidx] = TF;
   return noconv;
 }
 
 // ---- phase C: one cell --------------------------------------------------------
 // Mixed path: the conserved moments of each cell (rho, rho u, rho E: Eqs.
-// eq::ConservationLaws, eq:E) are accumulated in FP64: the old cell's, from
-// its coefficients, plus -dt/dx times each face's conserved flux (the same
-// FP32 value for both cells of a face).  The collision terms conserve them.
+// eq::ConservationLaws, eq:E) are kept in FP64 (State::M) and accumulated
+// there: -dt/dx times each face's conserved flux (the same FP32 value for both
+// cells of a face) is added.  The collision terms conserve them.
 struct MomAcc {
   double r, jx, jy, e;
 };
 
-template <typename R, int DIM, int DIRN>
+// one face's phi (dimensional coefficients in the face frame) moved into the
+// cell frame {u, T} (sT = sqrt T, read by the mixed path's FP64 test only)
+template <typename R, int DIM>
 __device__ __forceinline__ void face_contrib_body(const StepConst &K, const R *fp, int NFACES, int fidx,
-                                                  R sgn, R ux, R uy, R T, R sT, R isT,
+                                                  R ux, R uy, R T, R sT,
                                                   Blk<R, 4, Dims<DIM>::NYF> &X, Blk<R, 3, Dims<DIM>::NYG> &Y) {
   using D = Dims<DIM>;
 #pragma unroll
@@ -580,127 +603,129 @@ __device__ __forceinline__ void face_contrib_body(const StepConst &K, const R *f
 #pragma unroll
     for (int b = 0; b < D::NYG; ++b) Y.v[a][b] = fp[(D::QF + a + 3 * b) * NFACES + fidx];
   const R uFx = fp[D::FUX * NFACES + fidx], uFy = fp[D::FUY * NFACES + fidx];
-  const R sTF = fp[D::FST * NFACES + fidx];
-  const R TF = is_mixed<R>() ? fp[D::FT * NFACES + fidx] : R(0);  // read by the FP64 fallback only
-  move_frame<R, DIM, 4>(K, uFx, uFy, TF, sTF, ux, uy, T, isT, X);
-  move_frame<R, DIM, 3>(K, uFx, uFy, TF, sTF, ux, uy, T, isT, Y);
+  const R TF = fp[D::FT * NFACES + fidx];
+  const R sTF = is_mixed<R>() ? fp[D::FST * NFACES + fidx] : R(0);
+  move_frame<R, DIM, 4>(K, uFx, uFy, TF, sTF, ux, uy, T, sT, X);
+  move_frame<R, DIM, 3>(K, uFx, uFy, TF, sTF, ux, uy, T, sT, Y);
   if constexpr (DIM == 2) {
     if (K.grad_k) { grad_mask(X); grad_mask(Y); }
   }
-  // contribution -dt/dx (v^lambda . n) G phi (Eq. fluxEq) or -dt/dx G (v^lambda_F . n phi)
-  const R w = -kc<R>(K.lam, K.cf.lam) * sgn;
-  if (!K.appc) {
-    const R un = DIRN == 0 ? ux : uy;
-    vmul<DIRN>(w * un, w * sT, X);
-    vmul<DIRN>(w * un, w * sT, Y);
-  } else {
-#pragma unroll
-    for (int p = 0; p < 4; ++p)
-#pragma unroll
-      for (int q = 0; q < D::NYF; ++q) X.v[p][q] *= w;
-#pragma unroll
-    for (int p = 0; p < 3; ++p)
-#pragma unroll
-      for (int q = 0; q < D::NYG; ++q) Y.v[p][q] *= w;
-  }
 }
-// The mixed path computes a face's contribution in one out-of-line copy per
-// direction (returned by value, in registers), like the stencil transformation.
+// The mixed path moves a face's phi in one out-of-line copy (returned by
+// value, in registers), like the stencil transformation.
 template <typename R, int DIM> struct FaceContrib {
   Blk<R, 4, Dims<DIM>::NYF> X;
   Blk<R, 3, Dims<DIM>::NYG> Y;
 };
-template <typename R, int DIM, int DIRN>
+template <typename R, int DIM>
 __device__ __noinline__ FaceContrib<R, DIM> face_contrib_call(const StepConst &K, const R *fp, int NFACES,
-                                                              int fidx, R sgn, R ux, R uy, R T, R sT,
-                                                              R isT) {
+                                                              int fidx, R ux, R uy, R T, R sT) {
   FaceContrib<R, DIM> c;
-  face_contrib_body<R, DIM, DIRN>(K, fp, NFACES, fidx, sgn, ux, uy, T, sT, isT, c.X, c.Y);
+  face_contrib_body<R, DIM>(K, fp, NFACES, fidx, ux, uy, T, sT, c.X, c.Y);
   return c;
 }
-
-// adds one face's flux, moved into the cell frame, to the update
-template <typename R, int DIM, int DIRN>
-__device__ __forceinline__ void add_face(const StepConst &K, const R *fp, int NFACES, int fidx,
-                                         R sgn, R ux, R uy, R T, R sT, R isT,
-                                         Blk<R, 4, Dims<DIM>::NYF> &AF, Blk<R, 3, Dims<DIM>::NYG> &AG,
-                                         MomAcc &M) {
-  using D = Dims<DIM>;
-  Blk<R, 4, D::NYF> X;
-  Blk<R, 3, D::NYG> Y;
+template <typename R, int DIM>
+__device__ __forceinline__ void face_contrib(const StepConst &K, const R *fp, int NFACES, int fidx, R ux,
+                                             R uy, R T, R sT, Blk<R, 4, Dims<DIM>::NYF> &X,
+                                             Blk<R, 3, Dims<DIM>::NYG> &Y) {
   if constexpr (is_mixed<R>()) {
-    const FaceContrib<R, DIM> c = face_contrib_call<R, DIM, DIRN>(K, fp, NFACES, fidx, sgn, ux, uy, T, sT, isT);
+    const FaceContrib<R, DIM> c = face_contrib_call<R, DIM>(K, fp, NFACES, fidx, ux, uy, T, sT);
     X = c.X;
     Y = c.Y;
   } else {
-    face_contrib_body<R, DIM, DIRN>(K, fp, NFACES, fidx, sgn, ux, uy, T, sT, isT, X, Y);
+    face_contrib_body<R, DIM>(K, fp, NFACES, fidx, ux, uy, T, sT, X, Y);
   }
+}
+
+// The two faces of the cell along DIRN (lower face flo, upper face fhi):
+// F += -dt/dx [(v . n) G phi_hi - (v . n) G phi_lo] (Eq. fluxEq; the
+// multiplication by v_n in the cell frame is linear, so it is applied once to
+// the difference), or -dt/dx [G (v_F . n phi)_hi - G (v_F . n phi)_lo] in
+// the Appendix C form.
+template <typename R, int DIM, int DIRN>
+__device__ __forceinline__ void add_faces(const StepConst &K, const R *fp, int NFACES, int flo, int fhi,
+                                          R ux, R uy, R T, R sT, Blk<R, 4, Dims<DIM>::NYF> &F,
+                                          Blk<R, 3, Dims<DIM>::NYG> &G, MomAcc &M) {
+  using D = Dims<DIM>;
+  Blk<R, 4, D::NYF> DX, X;
+  Blk<R, 3, D::NYG> DY, Y;
+  face_contrib<R, DIM>(K, fp, NFACES, flo, ux, uy, T, sT, DX, DY);
+  face_contrib<R, DIM>(K, fp, NFACES, fhi, ux, uy, T, sT, X, Y);
 #pragma unroll
   for (int p = 0; p < 4; ++p)
 #pragma unroll
-    for (int q = 0; q < D::NYF; ++q) AF.v[p][q] += X.v[p][q];
+    for (int q = 0; q < D::NYF; ++q) DX.v[p][q] = X.v[p][q] - DX.v[p][q];
 #pragma unroll
   for (int p = 0; p < 3; ++p)
 #pragma unroll
-    for (int q = 0; q < D::NYG; ++q) AG.v[p][q] += Y.v[p][q];
+    for (int q = 0; q < D::NYG; ++q) DY.v[p][q] = Y.v[p][q] - DY.v[p][q];
+  if (!K.appc) {
+    const R un = DIRN == 0 ? ux : uy;
+    vmul<DIRN>(un, T, DX);
+    vmul<DIRN>(un, T, DY);
+  }
+  const R ml = -kc<R>(K.lam, K.cf.lam);
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < D::NYF; ++q) F.v[p][q] = fma(ml, DX.v[p][q], F.v[p][q]);
+#pragma unroll
+  for (int p = 0; p < 3; ++p)
+#pragma unroll
+    for (int q = 0; q < D::NYG; ++q) G.v[p][q] = fma(ml, DY.v[p][q], G.v[p][q]);
   if constexpr (is_mixed<R>()) {
-    const double w64 = -K.lam * (double)sgn;
-    M.r += w64 * (double)fp[(D::FJ + 0) * NFACES + fidx];
-    M.jx += w64 * (double)fp[(D::FJ + 1) * NFACES + fidx];
-    if constexpr (DIM == 2) M.jy += w64 * (double)fp[(D::FJ + 2) * NFACES + fidx];
-    M.e += w64 * (double)fp[(D::FJ + 3) * NFACES + fidx];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (DIM == 1 && j == 2) continue;
+      const double d = (double)fp[(D::FJ + j) * NFACES + fhi] - (double)fp[(D::FJ + j) * NFACES + flo];
+      double &m = j == 0 ? M.r : (j == 1 ? M.jx : (j == 2 ? M.jy : M.e));
+      m = fma(-K.lam, d, m);
+    }
   }
 }
 
 template <typename R, int DIM, int BX, int BY>
 __device__ __forceinline__ void update_cell(const StepConst &K, const State<R> &S, const State<R> &O,
-                                            const R *fp, int cx, int cy, int j, int k, double &cfl,
+                                            const R *fp, int cx, int cy, int j, int k, R &vmax,
                                             unsigned &flags) {
   using D = Dims<DIM>;
   using TL = Tile<DIM, BX, BY>;
   const size_t N = (size_t)K.nx * (DIM == 2 ? K.ny : 1);
   const size_t c = (size_t)k * K.nx + j;
-  Blk<R, 4, D::NYF> F, AF;
-  Blk<R, 3, D::NYG> G, AG;
+  Blk<R, 4, D::NYF> F;
+  Blk<R, 3, D::NYG> G;
 #pragma unroll
-  for (int i = 0; i < D::QF; ++i) { F.v[i % 4][i / 4] = S.f[i * N + c]; AF.v[i % 4][i / 4] = R(0); }
+  for (int i = 0; i < D::QF; ++i) F.v[i % 4][i / 4] = S.f[i * N + c];
 #pragma unroll
-  for (int i = 0; i < D::QG; ++i) { G.v[i % 3][i / 3] = S.g[i * N + c]; AG.v[i % 3][i / 3] = R(0); }
+  for (int i = 0; i < D::QG; ++i) G.v[i % 3][i / 3] = S.g[i * N + c];
   const R ux = S.ux[c], uy = DIM == 2 ? S.uy[c] : R(0), T = S.T[c];
-  const R sT = sqrt(T), isT = R(1) / sT;
+  const R sT = is_mixed<R>() ? sqrt(T) : R(0);
   qe_scale(F, G, kc<R>(K.qe, K.cf.qe));
   const R rho = F.v[0][0];
   MomAcc M;
   if constexpr (is_mixed<R>()) {
-    // the cell's conserved moments, v = u + sqrt(T) c
-    const double r64 = rho, ux64 = ux, uy64 = uy, T64 = T, sT64 = sqrt(T64);
-    const double a10 = F.v[1][0], a01 = DIM == 2 ? (double)F.v[0][1] : 0.0;
-    double c2 = (double)F.v[2][0] + DIM * r64;
-    if constexpr (DIM == 2) c2 += (double)F.v[0][2];
-    M.r = r64;
-    M.jx = ux64 * r64 + sT64 * a10;
-    M.jy = uy64 * r64 + sT64 * a01;
-    M.e = 0.5 * ((ux64 * ux64 + uy64 * uy64) * r64 + 2.0 * sT64 * (ux64 * a10 + uy64 * a01) + T64 * c2) +
-          (double)G.v[0][0];
+    // the cell's conserved moments, kept in FP64
+    M.r = S.M[c];
+    M.jx = S.M[N + c];
+    M.jy = DIM == 2 ? S.M[2 * N + c] : 0.0;
+    M.e = S.M[3 * N + c];
   }
-
-  // fluxes through the faces, in a fixed order: x-lo, x-hi, y-lo, y-hi
-  add_face<R, DIM, 0>(K, fp, TL::NFACES, cy * (BX + 1) + cx, R(-1), ux, uy, T, sT, isT, AF, AG, M);
-  add_face<R, DIM, 0>(K, fp, TL::NFACES, cy * (BX + 1) + cx + 1, R(1), ux, uy, T, sT, isT, AF, AG, M);
-  if constexpr (DIM == 2) {
-    add_face<R, DIM, 1>(K, fp, TL::NFACES, TL::NFX + cy * BX + cx, R(-1), ux, uy, T, sT, isT, AF, AG, M);
-    add_face<R, DIM, 1>(K, fp, TL::NFACES, TL::NFX + (cy + 1) * BX + cx, R(1), ux, uy, T, sT, isT, AF, AG, M);
-  }
-  // DUGKS update in the cell frame: a1 phi~ + a2 phi^eq - dt/dx sum F
+  // DUGKS update in the cell frame (Eq. eq:FinalUpdateDUGKS):
+  // a1 phi~ + a2 phi^eq - dt/dx sum_faces (+-) F
   const R a1 = kc<R>(K.a1, K.cf.a1);
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < D::NYF; ++b) F.v[a][b] = a1 * F.v[a][b] + AF.v[a][b];
+    for (int b = 0; b < D::NYF; ++b) F.v[a][b] *= a1;
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
-    for (int b = 0; b < D::NYG; ++b) G.v[a][b] = a1 * G.v[a][b] + AG.v[a][b];
+    for (int b = 0; b < D::NYG; ++b) G.v[a][b] *= a1;
+  // fluxes through the faces, in a fixed order: x, then y
+  add_faces<R, DIM, 0>(K, fp, TL::NFACES, cy * (BX + 1) + cx, cy * (BX + 1) + cx + 1, ux, uy, T, sT, F, G, M);
+  if constexpr (DIM == 2)
+    add_faces<R, DIM, 1>(K, fp, TL::NFACES, TL::NFX + cy * BX + cx, TL::NFX + (cy + 1) * BX + cx, ux, uy, T,
+                         sT, F, G, M);
   F.v[0][0] += kc<R>(K.a2, K.cf.a2) * rho;
   G.v[0][0] += kc<R>(K.a2, K.cf.a2) * kc<R>(K.gfac, K.cf.gfac) * T * rho;
 
@@ -710,25 +735,25 @@ __device__ __forceinline__ void update_cell(const StepConst &K, const State<R> &
   if constexpr (!is_mixed<R>()) {
     const R rn = F.v[0][0], irn = R(1) / rn;
     const R mx = F.v[1][0] * irn;
-    R my = R(0), S2 = F.v[2][0] + R(DIM) * rn;
+    R my = R(0), S2 = fma(R(DIM) * T, rn, F.v[2][0]);
     if constexpr (DIM == 2) { my = F.v[0][1] * irn; S2 += F.v[0][2]; }
-    const R en = R(0.5) * T * (S2 - rn * (mx * mx + my * my)) + G.v[0][0];
+    const R en = R(0.5) * (S2 - rn * (mx * mx + my * my)) + G.v[0][0];
     const R Tn = en * irn * kc<R>(K.inv_cv, K.cf.inv_cv);
-    uxn = ux + sT * mx; uyn = DIM == 2 ? uy + sT * my : R(0); Tout = Tn;
+    uxn = ux + mx; uyn = DIM == 2 ? uy + my : R(0); Tout = Tn;
     ok = rn > R(0) && Tn > R(0) && isfinite(rn) && isfinite(Tn) && isfinite(uxn) && isfinite(uyn);
     if (ok) {
-      const R sTn = sqrt(Tn), a = sT / sTn;
-      const Shift<R> Cx = make_shift(a, -a * mx);
+      const R dT = T - Tn, dT3 = R(3) * dT;
+      const DShift<R> Cx = make_dshift(-mx, dT, dT3);
       shift_x(Cx, F); shift_x(Cx, G);
       if constexpr (DIM == 2) {
-        const Shift<R> Cy = make_shift(a, -a * my);
+        const DShift<R> Cy = make_dshift(-my, dT, dT3);
         shift_y(Cy, F); shift_y(Cy, G);
       }
     }
   } else {
     // FP64: the new moments and frame; the frame is stored rounded to FP32
     // and the populations are moved into exactly that stored frame
-    const double rn = M.r, irn = 1.0 / rn;
+    const double rn = M.r, irn = rcp_nr1(rn);
     const double ux64 = M.jx * irn, uy64 = DIM == 2 ? M.jy * irn : 0.0;
     const double Tn = (M.e - 0.5 * rn * (ux64 * ux64 + uy64 * uy64)) * irn * K.inv_cv;
     ok = rn > 0.0 && Tn > 0.0 && isfinite(rn) && isfinite(Tn) && isfinite(ux64) && isfinite(uy64);
@@ -737,18 +762,17 @@ __device__ __forceinline__ void update_cell(const StepConst &K, const State<R> &
     // the conserved coefficients (still in the old frame) are the FP64 sums,
     // rounded once: the FP32 update alone drifts (a1 + a2 != 1 in FP32, and
     // the two cells of a face move its flux through different frames)
-    const double cux = ux, cuy = uy, T64 = T, isT64 = 1.0 / sqrt(T64), sT64 = T64 * isT64;
-    const double a10 = (M.jx - cux * rn) * isT64, a01 = DIM == 2 ? (M.jy - cuy * rn) * isT64 : 0.0;
+    const double cux = ux, cuy = uy, T64 = T;
+    const double a10 = fma(-cux, rn, M.jx), a01 = DIM == 2 ? fma(-cuy, rn, M.jy) : 0.0;
     F.v[0][0] = (R)rn;
     F.v[1][0] = (R)a10;
-    double c2 = (double)F.v[2][0] + DIM * rn;
+    double c2 = fma(DIM * T64, rn, (double)F.v[2][0]);
     if constexpr (DIM == 2) { F.v[0][1] = (R)a01; c2 += (double)F.v[0][2]; }
-    G.v[0][0] = (R)(M.e - 0.5 * ((cux * cux + cuy * cuy) * rn + 2.0 * sT64 * (cux * a10 + cuy * a01) +
-                                 T64 * c2));
+    G.v[0][0] = (R)(M.e - 0.5 * ((cux * cux + cuy * cuy) * rn + 2.0 * (cux * a10 + cuy * a01) + c2));
     if (ok) {
-      const R sTn = sqrt(Tout), isTn = R(1) / sTn;
-      move_frame<R, DIM, 4>(K, ux, uy, T, sT, uxn, uyn, Tout, isTn, F);
-      move_frame<R, DIM, 3>(K, ux, uy, T, sT, uxn, uyn, Tout, isTn, G);
+      const R sTn = sqrt(Tout);
+      move_frame<R, DIM, 4>(K, ux, uy, T, sT, uxn, uyn, Tout, sTn, F);
+      move_frame<R, DIM, 3>(K, ux, uy, T, sT, uxn, uyn, Tout, sTn, G);
     }
   }
   if (ok) {
@@ -756,8 +780,7 @@ __device__ __forceinline__ void update_cell(const StepConst &K, const State<R> &
       if (K.grad_k) { grad_mask(F); grad_mask(G); }
     }
     qe_scale(F, G, kc<R>(K.qe, K.cf.qe));
-    const double vmax = fmax(fabs((double)uxn), fabs((double)uyn)) + sqrt((double)Tout) * Nodes<4>::cmax;
-    cfl = fmax(cfl, vmax * K.lam);
+    vmax = fmax(vmax, fmax(fabs(uxn), fabs(uyn)) + sqrt(Tout) * R(Nodes<4>::cmax));
   } else {
     flags |= FLAG_NONPHYSICAL;
     uxn = ux; uyn = uy; Tout = T;
@@ -769,6 +792,12 @@ __device__ __forceinline__ void update_cell(const StepConst &K, const State<R> &
   O.ux[c] = uxn;
   if constexpr (DIM == 2) O.uy[c] = uyn;
   O.T[c] = Tout;
+  if constexpr (is_mixed<R>()) {
+    O.M[c] = M.r;
+    O.M[N + c] = M.jx;
+    if constexpr (DIM == 2) O.M[2 * N + c] = M.jy;
+    O.M[3 * N + c] = M.e;
+  }
 }
 
 // ---- one tile step (phases A-C) --------------------------------------------------
@@ -823,14 +852,15 @@ __device__ __forceinline__ void step_tile(const StepConst &K, const State<R> &S,
   __syncthreads();
 
   // C. cells
-  double cfl = 0.0;
+  R vmax = R(0);
   unsigned flags = 0;
   for (int c = tid; c < TL::NCELL; c += NT) {
     const int cx = c % BX, cy = c / BX;
     const int j = j0 + cx, k = k0 + cy;
     if (j >= K.nx || k >= (DIM == 2 ? K.ny : 1)) continue;
-    update_cell<R, DIM, BX, BY>(K, S, O, fp, cx, cy, j, k, cfl, flags);
+    update_cell<R, DIM, BX, BY>(K, S, O, fp, cx, cy, j, k, vmax, flags);
   }
+  double cfl = (double)vmax * K.lam;
   // warp reduction of the CFL number, flags and counts, one atomic per warp
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {

@@ -64,10 +64,11 @@ pond_status scratch_for_current_device(unsigned char **out) {
 }
 
 // In-place change of basis of the caller's FP64 planes: populations <-> their
-// Hermite coefficients, the layout the step kernels keep the state in.  Each
-// thread owns one cell and reads all of its values before writing.
+// dimensional Hermite coefficients in the cell's frame (temperature T), the
+// layout the step kernels keep the state in.  Each thread owns one cell and
+// reads all of its values before writing.
 template <int DIM, bool TO_COEF>
-__global__ void noalloc_basis_kernel(double *f, double *g, size_t N) {
+__global__ void noalloc_basis_kernel(double *f, double *g, const double *T, size_t N) {
   const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= N) return;
   using D = pond::Dims<DIM>;
@@ -75,9 +76,14 @@ __global__ void noalloc_basis_kernel(double *f, double *g, size_t N) {
   pond::Blk<double, 3, D::NYG> G;
   for (int q = 0; q < D::QF; ++q) F.v[q % 4][q / 4] = f[q * N + c];
   for (int q = 0; q < D::QG; ++q) G.v[q % 3][q / 3] = g[q * N + c];
+  const double sT = sqrt(T[c]);
   if (TO_COEF) {
     pond::ana_x(F); pond::ana_y(F); pond::ana_x(G); pond::ana_y(G);
+    pond::scale_orders(sT, F);
+    pond::scale_orders(sT, G);
   } else {
+    pond::scale_orders(1.0 / sT, F);
+    pond::scale_orders(1.0 / sT, G);
     pond::syn_x(F); pond::syn_y(F); pond::syn_x(G); pond::syn_y(G);
   }
   for (int q = 0; q < D::QF; ++q) f[q * N + c] = F.v[q % 4][q / 4];
@@ -85,10 +91,10 @@ __global__ void noalloc_basis_kernel(double *f, double *g, size_t N) {
 }
 
 template <bool TO_COEF>
-bool change_basis(int D, double *f, double *g, size_t N, cudaStream_t st) {
+bool change_basis(int D, double *f, double *g, const double *T, size_t N, cudaStream_t st) {
   const unsigned nb = (unsigned)((N + 255) / 256);
-  if (D == 2) noalloc_basis_kernel<2, TO_COEF><<<nb, 256, 0, st>>>(f, g, N);
-  else noalloc_basis_kernel<1, TO_COEF><<<nb, 256, 0, st>>>(f, g, N);
+  if (D == 2) noalloc_basis_kernel<2, TO_COEF><<<nb, 256, 0, st>>>(f, g, T, N);
+  else noalloc_basis_kernel<1, TO_COEF><<<nb, 256, 0, st>>>(f, g, T, N);
   return cudaGetLastError() == cudaSuccess;
 }
 
@@ -163,7 +169,7 @@ extern "C" pond_status pond_step_noalloc(pond_lattice lat, const int64_t dims[2]
     return POND_E_CUDA;
   }
   const pond::StepConst K = step_const(*p, D, nx, ny);
-  if (n > 0 && !change_basis<true>(D, f, g, N, st)) return POND_E_CUDA;
+  if (n > 0 && !change_basis<true>(D, f, g, T, N, st)) return POND_E_CUDA;
   for (int64_t i = 0; i < n; ++i) {
     const pond::State<double> &in = (i & 1) ? other : caller;
     const pond::State<double> &out = (i & 1) ? caller : other;
@@ -192,7 +198,7 @@ extern "C" pond_status pond_step_noalloc(pond_lattice lat, const int64_t dims[2]
       }
     }
   }
-  if (n > 0 && !change_basis<false>(D, f, g, N, st)) return POND_E_CUDA;
+  if (n > 0 && !change_basis<false>(D, f, g, T, N, st)) return POND_E_CUDA;
   if (flags) {
     pond::Stats h;
     if (cudaMemcpyAsync(&h, stats, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||

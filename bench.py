@@ -67,17 +67,22 @@ FLOPS_PER_CELL = {
         "fp64": 10193.0, "fp32": 9860.7, "fp32_fp64part": 136.0},
     "8f1ae008ef28539d6d8f70da94b8e383bec8cec0264b0bb4d062d9d36ea04ca2": {
         "fp64": 10204.6, "fp32": 9851.7, "fp32_fp64part": 136.0},
+    "c4ee90b46a5900589a0a82471d2dcb5f41a596ecbd2953cbf5200b864c8e94c7": {
+        "fp64": 9051.1, "fp32": 8721.3, "fp32_fp64part": 59.2},
 }
 BYTES_PER_CELL_FP64 = 2 * 28 * 8          # state read once + written once
-BYTES_PER_CELL_FP32 = 2 * 28 * 4
+BYTES_PER_CELL_FP32 = 2 * (28 * 4 + 4 * 8)  # + the FP64 conserved moments
 CLOCK_MAX_GHZ = 2.07
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * CLOCK_MAX_GHZ / 1e3     # 2 FP64 FMA/clk/SM
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * CLOCK_MAX_GHZ / 1e3   # 128 FP32 FMA/clk/SM
-# dram__bytes_read.sum + dram__bytes_write.sum of one main-line step launch,
-# keyed by source digest (None once the sources change)
+# dram__bytes_read.sum + dram__bytes_write.sum of one main-line step launch
+# (FP64 and mixed path), keyed by source digest (None once the sources change)
 TRAFFIC_BY_DIGEST = {
-    "f0fda6d6edd3d676a420fbc0900b79a2d4f25dccd9f51d6324c2790136928e1f": 18801664,
-    "8f1ae008ef28539d6d8f70da94b8e383bec8cec0264b0bb4d062d9d36ea04ca2": 15318272,
+    "f0fda6d6edd3d676a420fbc0900b79a2d4f25dccd9f51d6324c2790136928e1f": {"fp64": 18801664},
+    "8f1ae008ef28539d6d8f70da94b8e383bec8cec0264b0bb4d062d9d36ea04ca2": {"fp64": 15318272,
+                                                                          "fp32": 7478528},
+    "c4ee90b46a5900589a0a82471d2dcb5f41a596ecbd2953cbf5200b864c8e94c7": {"fp64": 15194368,
+                                                                          "fp32": 9558528},
 }
 
 
@@ -257,7 +262,7 @@ def _roofline(flops_key, cells, per_launch_s, peak_tflops, bytes_per_cell, kerne
     out = {"bound": "alu", "unit": "TFLOP/s", "peak": peak_tflops,
            "peak_source": precision_note, "kernel": kernel, "flops_per_cell": fpc,
            "achieved": None, "frac": None,
-           "traffic": TRAFFIC_BY_DIGEST.get(digest) if flops_key == "fp64" else None,
+           "traffic": TRAFFIC_BY_DIGEST.get(digest, {}).get(flops_key),
            "hbm": {"achieved_gbs": bytes_per_cell * cells / per_launch_s / 1e9, "peak_gbs": hbm_peak}}
     out["hbm"]["frac"] = out["hbm"]["achieved_gbs"] / hbm_peak
     if fpc:

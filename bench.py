@@ -467,7 +467,7 @@ def run_gpu(args, dist, rank, ws):
                          "FP32: 128 FMA/clk/SM x 152 SMs x 2070 MHz (nominal 80.5 TFLOP/s)")
     else:
         roof = _roofline("fp64", n, per_launch_s, FP64_PEAK_TFLOPS, BYTES_PER_CELL_FP64,
-                         "pond::member_step_kernel<double,2,8,16,192,1,false>", digest,
+                         "pond::member_step_kernel<double,2,8,14,128,2,false>", digest,
                          "FP64: 2 FMA/clk/SM x 152 SMs x 2070 MHz (nominal 1.26 TFLOP/s)")
     line = {
         "metric": METRIC, "value": mlups, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

@@ -209,10 +209,11 @@ pond_status step_once(pond_ctx *c) {
   return POND_OK;
 }
 
-// Fastest in tile sweeps on GB300 (256^2 and 1024^2 grids): 8x16 tiles, with
-// 160 threads and registers for two CTAs per SM on the mixed path, with 192
-// threads and no register cap in FP64 (whose shared memory fits one CTA)
-int auto_tile(const pond_ctx *c) { return c->D == 1 ? 1 : (c->fp32 ? 6 : 9); }
+// Fastest in tile sweeps on GB300 (256^2 and 1024^2 grids): on the mixed
+// path 8x16 tiles with 160 threads and registers for two CTAs per SM; in
+// FP64 8x14 tiles with 128 threads, two CTAs per SM (shared memory and the
+// register file each hold exactly two)
+int auto_tile(const pond_ctx *c) { return c->D == 1 ? 1 : (c->fp32 ? 6 : 10); }
 
 bool valid_params(const pond_params *p) {
   if (!p) return false;
@@ -229,7 +230,7 @@ bool valid_params(const pond_params *p) {
   if (p->flux_frame != POND_FRAME_AVG && p->flux_frame != POND_FRAME_ITER) return false;
   if (p->flux_frame == POND_FRAME_ITER && (!(p->iter_tol > 0.0) || p->iter_max < 1)) return false;
   if (!(p->xi_fp64_threshold > 0.0)) return false;
-  if (p->tile < 0 || p->tile > 9) return false;
+  if (p->tile < 0 || p->tile > 10) return false;
   return true;
 }
 

@@ -72,7 +72,7 @@ def test_batch_tile_codes_are_resolved_before_any_device_work(L):
     import torch
 
     no_gpu = not torch.cuda.is_available()
-    for prec, tile, ok in ((pond.POND_FP64, 9, True), (pond.POND_FP64, 6, True),
+    for prec, tile, ok in ((pond.POND_FP64, 9, True), (pond.POND_FP64, 10, True),
                            (pond.POND_FP64, 4, False), (pond.POND_FP32_MIXED, 6, True),
                            (pond.POND_FP32_MIXED, 4, True), (pond.POND_FP32_MIXED, 9, False),
                            (pond.POND_FP64, 0, True), (pond.POND_FP32_MIXED, 0, True)):

@@ -92,7 +92,7 @@ def test_autotuner_times_real_steps(torch, precision):
     tune.graph_steps = 4
     ref = _solo(probs, steps)
     got, (tile, grid, tuned, mlups), _ = _batched(torch, probs, steps, 2, precision, tune)
-    assert tuned and tile in (3, 4, 6, 9) and grid >= 152 and mlups > 0
+    assert tuned and tile in (3, 4, 6, 9, 10) and grid >= 152 and mlups > 0
     for a, b in zip(got, ref):
         for x, y in zip(a, b):
             assert np.array_equal(x, y)

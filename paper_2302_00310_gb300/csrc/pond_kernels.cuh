@@ -181,11 +181,16 @@ __device__ __forceinline__ bool abs_less(float x, float y) {
   return (__float_as_int(x) & 0x7fffffff) < (__float_as_int(y) & 0x7fffffff);
 }
 
+// The limited slope divided by lf(lim) (lf = 2 for van Leer, 1 for minmod;
+// the factor is folded into the trace offsets): van Leer 2xy/(x+y) / 2.
+template <typename R> __device__ __forceinline__ R limiter_factor(int lim) {
+  return lim == LIM_MINMOD ? R(1) : R(2);
+}
 template <typename R>
 __device__ __forceinline__ R limit(R x, R y, int lim) {
   const R p = x * y;
   if (lim == LIM_MINMOD) return pos(p) ? (abs_less(x, y) ? x : y) : R(0);
-  return pos(p) ? div_nr(p + p, x + y) : R(0);  // Van Leer: 2xy/(x+y)
+  return pos(p) ? div_nr(p, x + y) : R(0);
 }
 
 // The FP32 instantiation is the mixed-precision path (POND_FP32_MIXED).
@@ -346,6 +351,7 @@ __device__ __forceinline__ void stencil_pops(const StepConst &K, const R *sp, in
 // With a = upwind value, b = its outer neighbour, c = the downwind value, the
 // trace is a + (1/2 - |v_n| lam/2) L(a - b, c - a) for either upwind side
 // (L odd and symmetric), plus the tangential term -v_t lam/2 L(a - lo, hi - a).
+// The offsets carry the factor lf of limit().
 template <typename R, int DIM, int DIRN, int Q>
 __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int NH, const int *st,
                                             R uFx, R uFy, R TF, R sTF, R isTF,
@@ -353,7 +359,8 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
   constexpr int NY = DIM == 2 ? Q : 1;
   const SynK<R, Q> SK(isTF * isTF, isTF);
   const R uFn = DIRN == 0 ? uFx : uFy, uFt = DIRN == 0 ? uFy : uFx;
-  const R hl = R(0.5) * kc<R>(K.lam, K.cf.lam);
+  const R lf = limiter_factor<R>(K.limiter);
+  const R hl = R(0.5) * kc<R>(K.lam, K.cf.lam) * lf, h0 = R(0.5) * lf;
   const int lim = K.limiter;
   bool up[Q];
   R offn[Q], offt[Q];
@@ -362,7 +369,7 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
     const R c = R(Nodes<Q>::c(k));
     const R vn = sTF * c + uFn;
     up[k] = pos(vn);
-    offn[k] = R(0.5) - hl * fabs(vn);
+    offn[k] = h0 - hl * fabs(vn);
     offt[k] = -hl * (sTF * c + uFt);
   }
   Blk<R, Q, NY> YL, YR, A;

@@ -69,6 +69,8 @@ FLOPS_PER_CELL = {
         "fp64": 10204.6, "fp32": 9851.7, "fp32_fp64part": 136.0},
     "c4ee90b46a5900589a0a82471d2dcb5f41a596ecbd2953cbf5200b864c8e94c7": {
         "fp64": 9051.1, "fp32": 8721.3, "fp32_fp64part": 59.2},
+    "b0584204811353a2c124851d1f2a2775d5b0aff1d63f807d26df76939bfb7cc9": {
+        "fp64": 9016.9, "fp32": 8698.2, "fp32_fp64part": 59.2},
 }
 BYTES_PER_CELL_FP64 = 2 * 28 * 8          # state read once + written once
 BYTES_PER_CELL_FP32 = 2 * (28 * 4 + 4 * 8)  # + the FP64 conserved moments
@@ -83,6 +85,8 @@ TRAFFIC_BY_DIGEST = {
                                                                           "fp32": 7478528},
     "c4ee90b46a5900589a0a82471d2dcb5f41a596ecbd2953cbf5200b864c8e94c7": {"fp64": 15194368,
                                                                           "fp32": 9558528},
+    "b0584204811353a2c124851d1f2a2775d5b0aff1d63f807d26df76939bfb7cc9": {"fp64": 15459328,
+                                                                          "fp32": 9554432},
 }
 
 

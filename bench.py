@@ -29,6 +29,9 @@ The other forms the metric compares are measured in the same run
   * ``serve``: a Poisson stream of 1D tubes and 2D shock-bubble problems at
     200 requests/s through the continuous-batching server, p50/p99 time to
     solution and aggregate MLUPS.
+  * ``iterated``: the iterated face frame against the averaged one on the Sod
+    tube and the pulse at CFL 0.2 / 0.5 / 0.8 and two resolutions: L1 errors
+    against the exact solutions, traces per face, MLUPS.
 
 Under torchrun (N > 1) every rank runs an independent replica (the grid is
 not sharded; there is no collective on the data path) and ``value`` is the
@@ -386,6 +389,84 @@ def bench_batched(torch, pond, W):
     return out
 
 
+def _pulse_exact(w, t):
+    """The pulse workload's initial density translated by u t (periodic): the
+    exact Euler entropy wave."""
+    n = w["cfg"]["nx"]
+    x = (np.arange(n) + 0.5) / n
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    cx = (w["centre"][0] + w["velocity"][0] * t) % 1.0
+    cy = (w["centre"][1] + w["velocity"][1] * t) % 1.0
+    prof = np.zeros((n, n))
+    for sx in (-1, 0, 1):
+        for sy in (-1, 0, 1):
+            prof += np.exp(-((X - cx - sx) ** 2 + (Y - cy - sy) ** 2) / (2 * w["sigma"] ** 2))
+    return 1.0 + 0.1 * prof
+
+
+def bench_iterated(torch, pond, W, iter_tol=1e-9, iter_max=40):
+    """The iterated face frame against the averaged one (the comparison of
+    Sec. V.D, on problems with exact solutions): Sod tubes and the advected
+    pulse at CFL 0.2 / 0.5 / 0.8 and two resolutions, L1 density errors
+    against the exact solutions, and the iteration statistics."""
+    from tests.riemann_exact import solution
+
+    rows = []
+    for n in (100, 400):
+        for cfl in (0.2, 0.5, 0.8):
+            w = W.sod_1d(n=n, cfl=cfl)
+            exact = solution((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), w["x"], w["t_end"])[0]
+            row = {"problem": "sod", "n": n, "cfl": cfl, "steps": w["steps"]}
+            for it in (0, 1):
+                cfg = dict(w["cfg"], iterative=it, iter_tol=iter_tol, iter_max=iter_max)
+                sim = pond.Sim(cfg)
+                sim.init(w["rho"], w["ux"], w["uy"], w["T"])
+                sim.step(w["steps"])
+                rho = sim.moments()[0][0]
+                ev, tr, mx = sim.iter_stats()
+                fl = sim.flags()
+                sim.close()
+                key = "iterated" if it else "averaged"
+                row[key] = {"l1_rho": float(np.sum(np.abs(rho - exact)) / n), "max_cfl": fl[2]}
+                if it:
+                    row[key].update({"traces_per_face": tr / ev, "max_traces": mx,
+                                     "unconverged_frac": fl[3] / ev})
+            rows.append(row)
+    for n in (64, 128):
+        for cfl in (0.2, 0.5, 0.8):
+            w = W.pulse_2d(n=n, seed=0, cfl=cfl)
+            t_end = 0.25
+            steps = int(np.ceil(t_end / w["cfg"]["dt"]))
+            cfg0 = dict(w["cfg"], dt=t_end / steps)
+            exact = _pulse_exact(w, t_end)
+            row = {"problem": "pulse", "n": n, "cfl": cfl, "steps": steps}
+            for it in (0, 1):
+                cfg = dict(cfg0, iterative=it, iter_tol=iter_tol, iter_max=iter_max)
+                sim = pond.Sim(cfg)
+                sim.init(w["rho"], w["ux"], w["uy"], w["T"])
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                with torch.cuda.stream(sim.stream):
+                    e0.record(sim.stream)
+                    pond.pond_step(sim.ctx, steps)
+                    e1.record(sim.stream)
+                sim.stream.synchronize()
+                ms = e0.elapsed_time(e1)
+                rho = sim.moments()[0]
+                ev, tr, mx = sim.iter_stats()
+                fl = sim.flags()
+                sim.close()
+                key = "iterated" if it else "averaged"
+                row[key] = {"l1_rho_rel": float(np.sum(np.abs(rho - exact)) / np.sum(exact - 1.0)),
+                            "mlups": n * n * steps / (ms * 1e-3) / 1e6}
+                if it:
+                    row[key].update({"traces_per_face": tr / ev, "max_traces": mx,
+                                     "unconverged_frac": fl[3] / ev})
+            rows.append(row)
+    return {"workload": "Sod tube (n = 100, 400; t = 0.2) and the Mach-2 pulse (n = 64, 128; "
+                        "t = 0.25), FP64, averaged vs iterated face frame (iter_tol %g, "
+                        "iter_max %d)" % (iter_tol, iter_max), "cases": rows}
+
+
 def bench_serve(pond, serve_mod, n_requests=24, rate=200.0):
     reqs = serve_mod.make_requests(n_requests, rate=rate, seed=0)
     ex = serve_mod.PondExecutor(precision=pond.POND_FP32_MIXED, capacity=64, graph_steps=8)
@@ -457,6 +538,7 @@ def run_gpu(args, dist, rank, ws):
         extras["riemann"] = bench_riemann(torch, pond, W)
         extras["batched"] = bench_batched(torch, pond, W)
         extras["serve"] = bench_serve(pond, serve_mod)
+        extras["iterated"] = bench_iterated(torch, pond, W)
 
     sum_ms, e2e_s = _max_over_ranks(dist, [sum_ms, e2e_s], "cuda")
     if rank != 0:

@@ -186,6 +186,15 @@ pond_status pond_status_flags(pond_ctx *c, uint32_t *flags, double *max_cfl,
                               int64_t *noconv_faces);
 pond_status pond_reset_flags(pond_ctx *c);
 
+/* Iteration statistics of the iterated face frame (Sec. IV.A.3, the
+ * predictor-corrector of the earlier PonD-DUGKS scheme that Sec. V.D compares
+ * with), since the last reset: face evaluations (each face once per step),
+ * traces made over all of them (the interface state traced in a face frame:
+ * one per iterate, plus the retrace at the previous iterate when an iterate
+ * turns nonphysical), and the most traces one face evaluation made.  All zero
+ * with the averaged frame.  Any pointer may be NULL.  Synchronises. */
+pond_status pond_iter_stats(pond_ctx *c, int64_t *face_evals, int64_t *traces, int32_t *max_traces);
+
 /* Waits for all work queued on the context stream. */
 pond_status pond_sync(pond_ctx *c);
 

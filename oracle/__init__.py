@@ -95,7 +95,8 @@ class _Params(ctypes.Structure):
 
 class _Report(ctypes.Structure):
     _fields_ = [("flags", ctypes.c_uint32), ("noconv_faces", ctypes.c_int64),
-                ("max_cfl", ctypes.c_double)]
+                ("max_cfl", ctypes.c_double), ("face_evals", ctypes.c_int64),
+                ("traces", ctypes.c_int64), ("max_traces", ctypes.c_int32)]
 
 
 def _ptr(a: np.ndarray):
@@ -238,7 +239,8 @@ def run(cfg: Config, state: State, nsteps: int) -> State:
     if rc != 0:
         raise ValueError("oracle: invalid configuration (rc=%d)" % rc)
     st.report = {"flags": int(rep.flags), "noconv_faces": int(rep.noconv_faces),
-                 "max_cfl": float(rep.max_cfl)}
+                 "max_cfl": float(rep.max_cfl), "face_evals": int(rep.face_evals),
+                 "traces": int(rep.traces), "max_traces": int(rep.max_traces)}
     return st
 
 

@@ -73,6 +73,12 @@ typedef struct {
   uint32_t flags;
   int64_t noconv_faces;
   double max_cfl;
+  /* iterated face frame: face evaluations, traces made over them, and the
+   * most traces one evaluation made (a trace = one interface state traced in
+   * a face frame) */
+  int64_t face_evals;
+  int64_t traces;
+  int32_t max_traces;
 } orc_report;
 
 /* ------------------------------------------------------------------ */
@@ -406,9 +412,10 @@ static void orc_face_trace(const orc_grid *G, const orc_stencil *S, const double
 
 /* dir = 0: x-face between cells (j,k) and (j+1,k); dir = 1: y-face between
  * (j,k) and (j,k+1).  lam is set to the face frame {u_x, u_y, T} actually
- * used; returns 1 if the iterated frame did not converge. */
+ * used; returns 1 if the iterated frame did not converge; *ntrace receives the
+ * number of interface traces made. */
 static int orc_face(orc_grid *G, int dir, int j, int k, double *phi_f, double *phi_g,
-                    double lam[3]) {
+                    double lam[3], int *ntrace) {
   const orc_params *p = G->p;
   const int D = G->D;
   const double dt = p->dt, tau = p->tau, h = 0.5 * dt;
@@ -438,14 +445,17 @@ static int orc_face(orc_grid *G, int dir, int j, int k, double *phi_f, double *p
   const int nit = p->iterative ? (p->iter_max > 0 ? p->iter_max : 1) : 1;
   int converged = 0;
   double uP[2] = {uF[0], uF[1]}, TP = TF;
+  *ntrace = 0;
   for (int it = 0; it < nit; ++it) {
     orc_face_trace(G, &S, uF, TF, fb, gb);
+    ++*ntrace;
     /* interface macroscopic fields (rho, rho u, C_v rho T) in the face frame */
     int ok = orc_macro(&G->Lf, &G->Lg, D, G->Cv, fb, gb, uF, TF, &rho, ub, &Tb);
     if (!ok) {
       if (p->iterative && it > 0) {
         uF[0] = uP[0]; uF[1] = uP[1]; TF = TP;
         orc_face_trace(G, &S, uF, TF, fb, gb);
+        ++*ntrace;
         orc_macro(&G->Lf, &G->Lg, D, G->Cv, fb, gb, uF, TF, &rho, ub, &Tb);
       }
       break;
@@ -491,7 +501,8 @@ static int orc_step_once(orc_grid *G, orc_report *rep) {
   const double tau2 = p->tau / p->prandtl;
   const int qe = p->prandtl != 1.0;
   uint32_t flags = 0;
-  int64_t noconv = 0;
+  int64_t noconv = 0, traces = 0, evals = 0;
+  int max_tr = 0;
 
   /* 1. quasi-equilibrium half relaxation in the cell centres */
   if (qe) {
@@ -532,20 +543,28 @@ static int orc_step_once(orc_grid *G, orc_report *rep) {
   }
 
   /* 3. fluxes: loop over faces */
-#pragma omp parallel for collapse(2) schedule(static) reduction(+ : noconv)
+#pragma omp parallel for collapse(2) schedule(static) reduction(+ : noconv, traces, evals) \
+    reduction(max : max_tr)
   for (int k = 0; k < G->ny; ++k)
     for (int j = -1; j < G->nx; ++j) {
-      int fi = k * (G->nx + 1) + (j + 1);
+      int fi = k * (G->nx + 1) + (j + 1), nt = 0;
       noconv += orc_face(G, 0, j, k, G->xff + (size_t)fi * Qf, G->xfg + (size_t)fi * Qg,
-                         G->xlam + 3 * (size_t)fi);
+                         G->xlam + 3 * (size_t)fi, &nt);
+      traces += nt;
+      evals += 1;
+      if (nt > max_tr) max_tr = nt;
     }
   if (D == 2) {
-#pragma omp parallel for collapse(2) schedule(static) reduction(+ : noconv)
+#pragma omp parallel for collapse(2) schedule(static) reduction(+ : noconv, traces, evals) \
+    reduction(max : max_tr)
     for (int k = -1; k < G->ny; ++k)
       for (int j = 0; j < G->nx; ++j) {
-        int fi = (k + 1) * G->nx + j;
+        int fi = (k + 1) * G->nx + j, nt = 0;
         noconv += orc_face(G, 1, j, k, G->yff + (size_t)fi * Qf, G->yfg + (size_t)fi * Qg,
-                           G->ylam + 3 * (size_t)fi);
+                           G->ylam + 3 * (size_t)fi, &nt);
+        traces += nt;
+        evals += 1;
+        if (nt > max_tr) max_tr = nt;
       }
   }
 
@@ -634,6 +653,11 @@ static int orc_step_once(orc_grid *G, orc_report *rep) {
   if (noconv) flags |= ORC_FLAG_NOCONV;
   rep->flags |= flags;
   rep->noconv_faces += noconv;
+  if (p->iterative) {
+    rep->face_evals += evals;
+    rep->traces += traces;
+    if (max_tr > rep->max_traces) rep->max_traces = max_tr;
+  }
   if (maxcfl > rep->max_cfl) rep->max_cfl = maxcfl;
   return 0;
 }

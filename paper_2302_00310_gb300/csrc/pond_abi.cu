@@ -674,6 +674,17 @@ pond_status pond_status_flags(pond_ctx *c, uint32_t *flags, double *max_cfl, int
   return (h.flags & POND_FLAG_NONPHYSICAL) ? POND_E_NONPHYSICAL : POND_OK;
 }
 
+pond_status pond_iter_stats(pond_ctx *c, int64_t *face_evals, int64_t *traces, int32_t *max_traces) {
+  if (!c) return POND_E_INVAL;
+  Stats h;
+  POND_CUDA(cudaMemcpyAsync(&h, c->stats, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  POND_CUDA(cudaStreamSynchronize(c->stream));
+  if (face_evals) *face_evals = (int64_t)h.face_evals;
+  if (traces) *traces = (int64_t)h.traces;
+  if (max_traces) *max_traces = (int32_t)h.max_traces;
+  return POND_OK;
+}
+
 pond_status pond_reset_flags(pond_ctx *c) {
   if (!c) return POND_E_INVAL;
   POND_CUDA(cudaMemsetAsync(c->stats, 0, sizeof(Stats), c->stream));

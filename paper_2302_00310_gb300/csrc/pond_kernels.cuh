@@ -76,9 +76,11 @@ template <typename R> struct State {
 
 struct Stats {
   unsigned int flags;
-  unsigned int pad;
+  unsigned int max_traces;          // iterated face frame: most traces made at one face
   unsigned long long max_cfl_bits;  // bit pattern of a non-negative double
   unsigned long long noconv;
+  unsigned long long traces;        // iterated face frame: traces made, over all face evaluations
+  unsigned long long face_evals;    // iterated face frame: face evaluations counted
 };
 
 template <int DIM> struct Dims {
@@ -434,10 +436,11 @@ __device__ __forceinline__ void gauss_he(R mu, R dT, R &e1, R &e2, R &e3) {
 // |T_b - T_F|/T_F) < iter_tol (tested in FP64) or iter_max traces were made;
 // a converged face uses the co-moving equilibrium rho W.  An iterate whose
 // interface state is nonphysical ends the iteration and the face keeps the
-// previous iterate.  Returns true when an iterated frame did not converge.
+// previous iterate.  Returns true when an iterated frame did not converge;
+// ntrace receives the number of traces made (1 for the averaged frame).
 template <typename R, int DIM, int DIRN, bool ITER>
 __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int NH, const int *st,
-                                          R *fp, int NFACES, int fidx) {
+                                          R *fp, int NFACES, int fidx, int &ntrace) {
   using D = Dims<DIM>;
   constexpr int NYF = D::NYF, NYG = D::NYG;
   const int hL = st[0], hR = st[1];
@@ -453,7 +456,9 @@ __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int N
   R pFx = uFx, pFy = uFy, pT = TF;  // previous iterate's frame
   int it = 0;
   bool fallback = false;
+  ntrace = 0;
   while (true) {
+    ++ntrace;
     reconstruct<R, DIM, DIRN, 4>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, Fb);
     reconstruct<R, DIM, DIRN, 3>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, Gb);
     anaq_xy(AnaK<R, 4>(TF, sTF), Fb);
@@ -830,8 +835,8 @@ __device__ __forceinline__ void step_tile(const StepConst &K, const State<R> &S,
   __syncthreads();
 
   // B. faces (a face on a tile edge is evaluated by both tiles; the iterated
-  // frame's no-convergence count takes it from the tile on its right/upper side)
-  unsigned noconv = 0;
+  // frame's counts take it from the tile on its right/upper side)
+  unsigned noconv = 0, traces = 0, evals = 0, max_tr = 0;
   for (int f = tid; f < TL::NFACES; f += NT) {
     int st[8];
     if (f < TL::NFX) {
@@ -843,8 +848,11 @@ __device__ __forceinline__ void step_tile(const StepConst &K, const State<R> &S,
         st[4] = r - TL::HX + fx + 1; st[5] = r - TL::HX + fx + 2;
         st[6] = r + TL::HX + fx + 1; st[7] = r + TL::HX + fx + 2;
       }
-      const bool nc = face_flux<R, DIM, 0, ITER>(K, sp, TL::NH, st, fp, TL::NFACES, f);
-      if (ITER && nc && (fx > 0 || j0 == 0)) ++noconv;
+      int nt;
+      const bool nc = face_flux<R, DIM, 0, ITER>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
+      if (ITER && (fx > 0 || j0 == 0)) {
+        noconv += nc; traces += nt; ++evals; max_tr = max(max_tr, (unsigned)nt);
+      }
     } else if constexpr (DIM == 2) {
       const int g = f - TL::NFX, fx = g % BX, fy = g / BX;
       if (j0 + fx >= K.nx || k0 + fy - 1 >= K.ny) continue;
@@ -852,8 +860,11 @@ __device__ __forceinline__ void step_tile(const StepConst &K, const State<R> &S,
       st[0] = (fy + 1) * H + x; st[1] = (fy + 2) * H + x; st[2] = fy * H + x; st[3] = (fy + 3) * H + x;
       st[4] = (fy + 1) * H + x - 1; st[5] = (fy + 2) * H + x - 1;
       st[6] = (fy + 1) * H + x + 1; st[7] = (fy + 2) * H + x + 1;
-      const bool nc = face_flux<R, DIM, 1, ITER>(K, sp, TL::NH, st, fp, TL::NFACES, f);
-      if (ITER && nc && (fy > 0 || k0 == 0)) ++noconv;
+      int nt;
+      const bool nc = face_flux<R, DIM, 1, ITER>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
+      if (ITER && (fy > 0 || k0 == 0)) {
+        noconv += nc; traces += nt; ++evals; max_tr = max(max_tr, (unsigned)nt);
+      }
     }
   }
   __syncthreads();
@@ -873,13 +884,25 @@ __device__ __forceinline__ void step_tile(const StepConst &K, const State<R> &S,
   for (int o = 16; o > 0; o >>= 1) {
     cfl = fmax(cfl, __shfl_xor_sync(0xffffffffu, cfl, o));
     flags |= __shfl_xor_sync(0xffffffffu, flags, o);
-    if constexpr (ITER) noconv += __shfl_xor_sync(0xffffffffu, noconv, o);
+    if constexpr (ITER) {
+      noconv += __shfl_xor_sync(0xffffffffu, noconv, o);
+      traces += __shfl_xor_sync(0xffffffffu, traces, o);
+      evals += __shfl_xor_sync(0xffffffffu, evals, o);
+      max_tr = max(max_tr, __shfl_xor_sync(0xffffffffu, max_tr, o));
+    }
   }
   if ((tid & 31) == 0) {
     if (cfl > 1.0) flags |= FLAG_CFL;
     if (noconv) {
       flags |= FLAG_NOCONV;
       atomicAdd(&stats->noconv, (unsigned long long)noconv);
+    }
+    if constexpr (ITER) {
+      if (evals) {
+        atomicAdd(&stats->traces, (unsigned long long)traces);
+        atomicAdd(&stats->face_evals, (unsigned long long)evals);
+        atomicMax(&stats->max_traces, max_tr);
+      }
     }
     if (flags) atomicOr(&stats->flags, flags);
     atomicMax(&stats->max_cfl_bits, (unsigned long long)__double_as_longlong(cfl));

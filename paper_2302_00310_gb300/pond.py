@@ -30,6 +30,7 @@ POND_FLAG_NONPHYSICAL, POND_FLAG_CFL, POND_FLAG_NOCONV = 1, 2, 4
 EXPORTS = (
     "pond_params_default", "pond_workspace_size", "pond_create", "pond_init", "pond_step",
     "pond_moments", "pond_get_state", "pond_set_state", "pond_status_flags", "pond_reset_flags",
+    "pond_iter_stats",
     "pond_sync", "pond_info", "pond_destroy", "pond_strerror", "pond_abi_version",
     "pond_step_noalloc", "pond_tune_default", "pond_batch_create", "pond_batch_add",
     "pond_batch_remove", "pond_batch_size", "pond_batch_step", "pond_batch_info",
@@ -92,6 +93,8 @@ def lib(build: bool = False):
     L.pond_status_flags.argtypes = [_P, ctypes.POINTER(ctypes.c_uint32), _D,
                                     ctypes.POINTER(ctypes.c_int64)]
     L.pond_reset_flags.argtypes = [_P]
+    L.pond_iter_stats.argtypes = [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                  ctypes.POINTER(ctypes.c_int32)]
     L.pond_sync.argtypes = [_P]
     L.pond_info.argtypes = [_P, _D, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]
     L.pond_destroy.argtypes = [_P]
@@ -215,6 +218,15 @@ def pond_status_flags(ctx):
     if st not in (POND_OK, POND_E_NONPHYSICAL):
         raise PondError(st, "pond_status_flags")
     return st, int(fl.value), float(cfl.value), int(nc.value)
+
+
+def pond_iter_stats(ctx):
+    """(face evaluations, traces, most traces at one face) of the iterated
+    face frame since the last reset."""
+    ev, tr, mx = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+    _check(lib().pond_iter_stats(ctx, ctypes.byref(ev), ctypes.byref(tr), ctypes.byref(mx)),
+           "pond_iter_stats")
+    return int(ev.value), int(tr.value), int(mx.value)
 
 
 def pond_reset_flags(ctx):
@@ -404,6 +416,9 @@ class Sim:
 
     def flags(self):
         return pond_status_flags(self.ctx)
+
+    def iter_stats(self):
+        return pond_iter_stats(self.ctx)
 
     def info(self):
         return pond_info(self.ctx)

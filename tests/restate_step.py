@@ -37,6 +37,9 @@ class Restated:
         self.dx = mp.mpf(cfg["dx"])
         self.lat = {q: self._lattice(q) for q in (3, 4)}
         self.noconv_faces = 0  # iterated face frames that did not converge
+        self.face_evals = 0    # iterated face frame: faces evaluated,
+        self.traces = 0        # interface traces made over them,
+        self.max_traces = 0    # and the most at one face
 
     # Table I, from the node formulas
     def _lattice(self, q):
@@ -193,13 +196,16 @@ class Restated:
             # the face then keeps the previous iterate
             converged = False
             prev = (uF, TF)
+            ntrace = 0
             for it in range(n_iter):
                 fb, gb = self._trace(dirn, at, phiplus, uF, TF, limit, C4, C3)
+                ntrace += 1
                 rho, ub, Tb = self.macro(fb, gb, uF, TF)
                 if not (rho > 0 and Tb > 0):
                     if iterative and it > 0:
                         uF, TF = prev
                         fb, gb = self._trace(dirn, at, phiplus, uF, TF, limit, C4, C3)
+                        ntrace += 1
                         rho, ub, Tb = self.macro(fb, gb, uF, TF)
                     break
                 if not iterative:
@@ -212,6 +218,10 @@ class Restated:
                     prev = (uF, TF)
                     uF = [ub[0], ub[1] if D == 2 else mp.mpf(0)]
                     TF = Tb
+            if iterative:
+                self.face_evals += 1
+                self.traces += ntrace
+                self.max_traces = max(self.max_traces, ntrace)
             if iterative and not converged:
                 self.noconv_faces += 1
             if converged:

@@ -51,6 +51,10 @@ def test_iterated_frame_matches_multiprecision_restatement(case):
     nfaces = (nx + 1) * ny + (nx * (ny + 1) if D == 2 else 0)
     assert out.report["noconv_faces"] == R.noconv_faces
     assert bool(out.report["flags"] & oracle.FLAG_NOCONV) == (R.noconv_faces > 0)
+    # and the same traces: each face once, the iterates counted one by one
+    assert out.report["face_evals"] == R.face_evals == nfaces
+    assert out.report["traces"] == R.traces and out.report["max_traces"] == R.max_traces
+    assert nfaces <= R.traces <= nfaces * (itmax + 1)
     if itmax <= 3:
         assert R.noconv_faces >= nfaces // 2
     else:
@@ -70,6 +74,9 @@ def test_single_iteration_is_the_explicit_scheme():
     for x, y in zip((a.f, a.g, a.ux, a.uy, a.T), (b.f, b.g, b.ux, b.uy, b.T)):
         assert np.array_equal(x, y)
     assert b.report["noconv_faces"] > 0
+    # one trace per face evaluation; the averaged frame counts none
+    assert b.report["traces"] == b.report["face_evals"] == 3 * (10 * 7 + 9 * 8)
+    assert b.report["max_traces"] == 1 and a.report["face_evals"] == a.report["traces"] == 0
 
 
 @pytest.mark.parametrize("appc", [0, 1])
@@ -114,6 +121,10 @@ def test_iterated_frame_uniform_flow(D):
     cfg, st = _state(d, rho, ux, uy, T)
     out = oracle.run(cfg, st, 5)
     assert out.report["noconv_faces"] == 0 and out.report["flags"] == 0
+    # every face converges at its first trace
+    nfaces = (n + 1) * shp[0] + (n * (n + 1) if D == 2 else 0)
+    assert out.report["traces"] == out.report["face_evals"] == 5 * nfaces
+    assert out.report["max_traces"] == 1
     np.testing.assert_allclose(out.f, st.f, rtol=1e-13, atol=1e-15)
     np.testing.assert_allclose(out.ux, st.ux, rtol=1e-13, atol=1e-15)
     np.testing.assert_allclose(out.T, st.T, rtol=1e-13)

@@ -72,8 +72,14 @@ typedef enum {
 
 /* boundary kinds per side (x-lo, x-hi, y-lo, y-hi), ghost-node method of
  * Sec. IV.D: periodic wrap, zero normal gradient (copy of the boundary cell),
- * or a fixed inflow state (its co-moving equilibrium). */
-enum { POND_BC_PERIODIC = 0, POND_BC_ZERO_GRADIENT = 1, POND_BC_INFLOW = 2 };
+ * a fixed inflow state (its co-moving equilibrium), or a wall half a cell
+ * beyond the last cell, with velocity inflow[side][1..2] and temperature
+ * inflow[side][3]: the ghost reflects the interior cell (rho_G = rho_B,
+ * u_G = 2 u_w - u_B, T_G = 2 T_w - T_B) and carries the Chapman-Enskog
+ * non-equilibrium of Sec. IV.D from centred gradients of the last step.
+ * Walls go on the y sides in 2D (x sides then periodic or zero-gradient) and
+ * on the x sides in 1D, with at least 3 cells across (else POND_E_INVAL). */
+enum { POND_BC_PERIODIC = 0, POND_BC_ZERO_GRADIENT = 1, POND_BC_INFLOW = 2, POND_BC_WALL = 3 };
 /* arithmetic of the step: all FP64, or the mixed path: FP32 populations,
  * frame (stored as FP32), transformations, reconstruction and collision, with
  * each cell's conserved moments (rho, rho u, rho E) accumulated in FP64, the

@@ -32,7 +32,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pond_oracle.c")
 _SO = os.path.join(_HERE, "libpond_oracle.so")
 
-BC_PERIODIC, BC_ZERO_GRADIENT, BC_INFLOW = 0, 1, 2
+BC_PERIODIC, BC_ZERO_GRADIENT, BC_INFLOW, BC_WALL = 0, 1, 2, 3
 LIM_VANLEER, LIM_MINMOD = 0, 1
 FLAG_NONPHYSICAL, FLAG_NOCONV = 1, 4
 

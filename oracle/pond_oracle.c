@@ -46,7 +46,7 @@
 #define ORC_MAXQ1 5
 #define ORC_MAXQ (ORC_MAXQ1 * ORC_MAXQ1)
 
-enum { ORC_BC_PERIODIC = 0, ORC_BC_ZERO_GRADIENT = 1, ORC_BC_INFLOW = 2 };
+enum { ORC_BC_PERIODIC = 0, ORC_BC_ZERO_GRADIENT = 1, ORC_BC_INFLOW = 2, ORC_BC_WALL = 3 };
 enum { ORC_LIM_VANLEER = 0, ORC_LIM_MINMOD = 1 };
 enum { ORC_FLAG_NONPHYSICAL = 1u, ORC_FLAG_NOCONV = 4u };
 
@@ -60,7 +60,8 @@ typedef struct {
   double prandtl;     /* Pr = tau_1/tau_2; 1 switches the QE step off */
   double dx, dt;
   int bc[4];          /* x-lo, x-hi, y-lo, y-hi */
-  double inflow[4][4];/* per side: rho, ux, uy, T of the fixed ghost state */
+  double inflow[4][4];/* per side: rho, ux, uy, T of the fixed ghost state (a
+                         wall: unused, its velocity ux, uy and temperature T) */
   int grad_k;         /* 0: tensor product of 1D transforms, 1: Grad a+b<=K */
   int flux_appc;      /* 0: Eq. fluxEq form, 1: Appendix C form */
   int limiter;        /* ORC_LIM_* */
@@ -316,6 +317,120 @@ static void orc_set_equilibrium_cell(orc_grid *G, int c, double rho, double ux, 
   G->ux[c] = ux; G->uy[c] = uy; G->T[c] = T;
 }
 
+/* ------------------------------------------------------------------ */
+/* Wall ghost cells (Sec. IV.D).                                       */
+/* ------------------------------------------------------------------ */
+/* Walls sit on the y sides in 2D and on the x sides in 1D, half a cell
+ * beyond the last interior cell.  inflow[side] = (unused, u_w,x, u_w,y, T_w).
+ * The ghost at normal distance m (m = 1, 2 layers) reflects the interior cell
+ * m - 1 cells from the wall: rho_G = rho_B (zero normal gradient),
+ * u_G = 2 u_w - u_B and T_G = 2 T_w - T_B (fixed values at the wall). */
+
+/* density (sum of the f populations) and frame of interior cell (j, k); the
+ * stored frame is the co-moving one, i.e. the cell's u and T */
+static void orc_cell_mac(const orc_grid *G, int j, int k, double m[4]) {
+  const int c = orc_pidx(G, j, k), ncp = orc_ncp(G);
+  double rho = 0.0;
+  for (int i = 0; i < G->Qf; ++i) rho += G->f[i * ncp + c];
+  m[0] = rho; m[1] = G->ux[c]; m[2] = G->uy[c]; m[3] = G->T[c];
+}
+
+/* rho, ux, uy, T at index (j, k): an interior cell, or its reflection across
+ * a wall; the tangential index follows the periodic / zero-gradient rule */
+static void orc_wall_mac(const orc_grid *G, int j, int k, double m[4]) {
+  const orc_params *p = G->p;
+  const int D = G->D;
+  if (D == 2 && (j < 0 || j >= p->nx)) {
+    int side = j < 0 ? 0 : 1;
+    if (p->bc[side] == ORC_BC_PERIODIC) j = j < 0 ? j + p->nx : j - p->nx;
+    else j = j < 0 ? 0 : p->nx - 1;
+  }
+  int *n = D == 2 ? &k : &j;
+  const int nmax = D == 2 ? p->ny : p->nx, lo = D == 2 ? 2 : 0;
+  int side = -1;
+  if (*n < 0) { side = lo; *n = -*n - 1; }
+  else if (*n >= nmax) { side = lo + 1; *n = 2 * nmax - 1 - *n; }
+  orc_cell_mac(G, j, k, m);
+  if (side >= 0) {
+    m[1] = 2.0 * p->inflow[side][1] - m[1];
+    m[2] = D == 2 ? 2.0 * p->inflow[side][2] - m[2] : 0.0;
+    m[3] = 2.0 * p->inflow[side][3] - m[3];
+  }
+}
+
+/* The wall ghost (j, k) into padded cell c: the co-moving equilibrium of its
+ * (rho_G, u_G, T_G) plus the Chapman-Enskog non-equilibrium of the paper's
+ * ghost construction, P^(1) and Q^(1) for f, M_g0, M_g1, M_g2 for g, from
+ * second-order centred gradients of the previous step's fields, expanded by
+ * Grad's projection in the ghost frame.  Readings: the non-equilibrium moments
+ * are the central ones in the co-moving ghost frame (Q^(1) without its
+ * u P^(1) part, which the raw moment adds; M_g1 without M_g0 u; M_g2 the T S
+ * term), and the stored variable is phi~ = phi + dt/(2 tau_1) (phi - phi^eq),
+ * i.e. the non-equilibrium part scaled by 1 + dt/(2 tau_1). */
+static void orc_wall_ghost(orc_grid *G, int j, int k, int c) {
+  const orc_params *p = G->p;
+  const int D = G->D, ncp = orc_ncp(G);
+  double mG[4], a[4], b[4];
+  orc_wall_mac(G, j, k, mG);
+  const double rho = mG[0], T = mG[3], Cv = G->Cv;
+  /* gradients: gu[d][e] = d u_e / d x_d, gT[d] = d T / d x_d */
+  double gu[2][2] = {{0, 0}, {0, 0}}, gT[2] = {0, 0};
+  const double h = 1.0 / (2.0 * p->dx);
+  for (int d = 0; d < D; ++d) {
+    if (d == 0) { orc_wall_mac(G, j + 1, k, a); orc_wall_mac(G, j - 1, k, b); }
+    else { orc_wall_mac(G, j, k + 1, a); orc_wall_mac(G, j, k - 1, b); }
+    gu[d][0] = (a[1] - b[1]) * h;
+    gu[d][1] = (a[2] - b[2]) * h;
+    gT[d] = (a[3] - b[3]) * h;
+  }
+  double S[2][2], div = 0.0;
+  for (int d = 0; d < D; ++d) div += gu[d][d];
+  for (int d = 0; d < 2; ++d)
+    for (int e = 0; e < 2; ++e) S[d][e] = gu[d][e] + gu[e][d];
+  const double t1 = p->tau, t2 = p->tau / p->prandtl, rT = rho * T, gf = 2.0 * Cv - D;
+  double P[2][2], Q[2][2][2], M1[2], M2[2][2];
+  const double M0 = -t1 * rT * gf * div / Cv;
+  for (int d = 0; d < 2; ++d) {
+    M1[d] = -t2 * rT * gf * gT[d];
+    for (int e = 0; e < 2; ++e) {
+      P[d][e] = -t1 * rT * (S[d][e] - (d == e ? div / Cv : 0.0));
+      M2[d][e] = -t1 * rT * gf * T * S[d][e];
+      for (int f = 0; f < 2; ++f)
+        Q[d][e][f] = -t2 * rT * (gT[d] * (e == f) + gT[e] * (d == f) + gT[f] * (d == e));
+    }
+  }
+  /* Grad expansion in the ghost frame, xi = the lattice node c_i */
+  const double cf = 1.0 + p->dt / (2.0 * t1), sT = sqrt(T);
+  for (int i = 0; i < G->Qf; ++i) {
+    const double xi[2] = {orc_cx(&G->Lf, D, i), orc_cy(&G->Lf, D, i)};
+    double s2 = 0.0, s3 = 0.0;
+    for (int d = 0; d < D; ++d)
+      for (int e = 0; e < D; ++e) {
+        s2 += P[d][e] / T * (xi[d] * xi[e] - (d == e));
+        for (int f = 0; f < D; ++f)
+          s3 += Q[d][e][f] / (T * sT) *
+                (xi[d] * xi[e] * xi[f] - xi[d] * (e == f) - xi[e] * (d == f) - xi[f] * (d == e));
+      }
+    G->f[i * ncp + c] = orc_W(&G->Lf, D, i) * (rho + cf * (s2 / 2.0 + s3 / 6.0));
+  }
+  for (int i = 0; i < G->Qg; ++i) {
+    const double xi[2] = {orc_cx(&G->Lg, D, i), orc_cy(&G->Lg, D, i)};
+    double s1 = 0.0, s2 = 0.0;
+    for (int d = 0; d < D; ++d) {
+      s1 += M1[d] / sT * xi[d];
+      for (int e = 0; e < D; ++e) s2 += (M2[d][e] - T * M0 * (d == e)) / T * (xi[d] * xi[e] - (d == e));
+    }
+    G->g[i * ncp + c] = orc_W(&G->Lg, D, i) * ((Cv - 0.5 * D) * T * rho + cf * (M0 + s1 + s2 / 2.0));
+  }
+  G->ux[c] = mG[1]; G->uy[c] = D == 2 ? mG[2] : 0.0; G->T[c] = T;
+}
+
+/* is (j, k) a ghost across a wall? */
+static int orc_is_wall_ghost(const orc_params *p, int j, int k) {
+  if (p->D == 2) return (k < 0 && p->bc[2] == ORC_BC_WALL) || (k >= p->ny && p->bc[3] == ORC_BC_WALL);
+  return (j < 0 && p->bc[0] == ORC_BC_WALL) || (j >= p->nx && p->bc[1] == ORC_BC_WALL);
+}
+
 static void orc_fill_ghosts(orc_grid *G) {
   const orc_params *p = G->p;
   const int ncp = orc_ncp(G);
@@ -324,6 +439,10 @@ static void orc_fill_ghosts(orc_grid *G) {
     for (int j = -2; j < G->nx + 2; ++j) {
       if (j >= 0 && j < G->nx && k >= 0 && k < G->ny) continue;
       int c = orc_pidx(G, j, k), sj = 0, sk = 0;
+      if (orc_is_wall_ghost(p, j, k)) {
+        orc_wall_ghost(G, j, k, c);
+        continue;
+      }
       int side = orc_ghost_map(p, j, k, &sj, &sk);
       if (side >= 0) {
         orc_set_equilibrium_cell(G, c, p->inflow[side][0], p->inflow[side][1],
@@ -390,20 +509,27 @@ static void orc_face_trace(const orc_grid *G, const orc_stencil *S, const double
       double vx = sqrt(TF) * orc_cx(L, D, i) + uF[0];
       double vy = sqrt(TF) * orc_cy(L, D, i) + uF[1];
       double vn = dir == 0 ? vx : vy, vt = dir == 0 ? vy : vx;
-      int t = vn > 0.0 ? 0 : 1; /* upwind: 0 = left/lower, 1 = right/upper */
-      int s = 1 + t;            /* stencil position of the upwind cell */
-      double ps = pop == 0 ? tn_f[s][i] : tn_g[s][i];
-      double pm = pop == 0 ? tn_f[s - 1][i] : tn_g[s - 1][i];
-      double pp = pop == 0 ? tn_f[s + 1][i] : tn_g[s + 1][i];
-      double sig_n = orc_limit(p->limiter, (ps - pm) / dx, (pp - ps) / dx);
-      /* offset of the departure point from the upwind cell centre */
-      double dn = (t == 0 ? 0.5 * dx : -0.5 * dx) - vn * 0.5 * dt;
-      double val = ps + dn * sig_n;
-      if (D == 2) {
-        double qm = pop == 0 ? tt_f[t][0][i] : tt_g[t][0][i];
-        double qp = pop == 0 ? tt_f[t][1][i] : tt_g[t][1][i];
-        double sig_t = orc_limit(p->limiter, (ps - qm) / dx, (qp - ps) / dx);
-        val += (-vt * 0.5 * dt) * sig_t;
+      /* upwind: t = 0 left/lower, 1 right/upper; with v_n = 0 exactly (a
+       * wall at rest puts the zero node of D1Q3 there) the mean of the two
+       * one-sided traces, so that the face has no preferred side */
+      double val = 0.0;
+      const int t0 = vn < 0.0 ? 1 : 0, t1 = vn > 0.0 ? 0 : 1;
+      for (int t = t0; t <= t1; ++t) {
+        int s = 1 + t; /* stencil position of the upwind cell */
+        double ps = pop == 0 ? tn_f[s][i] : tn_g[s][i];
+        double pm = pop == 0 ? tn_f[s - 1][i] : tn_g[s - 1][i];
+        double pp = pop == 0 ? tn_f[s + 1][i] : tn_g[s + 1][i];
+        double sig_n = orc_limit(p->limiter, (ps - pm) / dx, (pp - ps) / dx);
+        /* offset of the departure point from the upwind cell centre */
+        double dn = (t == 0 ? 0.5 * dx : -0.5 * dx) - vn * 0.5 * dt;
+        double v1 = ps + dn * sig_n;
+        if (D == 2) {
+          double qm = pop == 0 ? tt_f[t][0][i] : tt_g[t][0][i];
+          double qp = pop == 0 ? tt_f[t][1][i] : tt_g[t][1][i];
+          double sig_t = orc_limit(p->limiter, (ps - qm) / dx, (qp - ps) / dx);
+          v1 += (-vt * 0.5 * dt) * sig_t;
+        }
+        val += t0 == t1 ? v1 : 0.5 * v1;
       }
       out[i] = val;
     }
@@ -698,6 +824,15 @@ static int orc_check(const orc_params *p) {
     return 0;
   if (!(p->tau > 0) || !(p->dt > 0) || !(p->dx > 0) || !(p->prandtl > 0) || !(p->gamma > 1))
     return 0;
+  /* walls: on the y sides in 2D (x sides periodic or zero-gradient), on the x
+   * sides in 1D, with at least three cells across */
+  for (int s = 0; s < 4; ++s) {
+    if (p->bc[s] < ORC_BC_PERIODIC || p->bc[s] > ORC_BC_WALL) return 0;
+    if (p->bc[s] != ORC_BC_WALL) continue;
+    if (p->D == 2 && (s < 2 || p->ny < 3 || p->bc[0] == ORC_BC_INFLOW || p->bc[1] == ORC_BC_INFLOW))
+      return 0;
+    if (p->D == 1 && (s > 1 || p->nx < 3)) return 0;
+  }
   return 1;
 }
 

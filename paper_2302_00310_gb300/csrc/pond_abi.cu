@@ -220,7 +220,7 @@ bool valid_params(const pond_params *p) {
   if (!(p->gamma > 1.0) || !(p->tau > 0.0) || !(p->prandtl > 0.0) || !(p->dx > 0.0)) return false;
   if (!(p->dt > 0.0) && !(p->cfl > 0.0)) return false;
   for (int s = 0; s < 4; ++s)
-    if (p->bc[s] < POND_BC_PERIODIC || p->bc[s] > POND_BC_INFLOW) return false;
+    if (p->bc[s] < POND_BC_PERIODIC || p->bc[s] > POND_BC_WALL) return false;
   if ((p->bc[0] == POND_BC_PERIODIC) != (p->bc[1] == POND_BC_PERIODIC)) return false;
   if ((p->bc[2] == POND_BC_PERIODIC) != (p->bc[3] == POND_BC_PERIODIC)) return false;
   if (p->precision != POND_FP64 && p->precision != POND_FP32_MIXED) return false;
@@ -231,6 +231,18 @@ bool valid_params(const pond_params *p) {
   if (p->flux_frame == POND_FRAME_ITER && (!(p->iter_tol > 0.0) || p->iter_max < 1)) return false;
   if (!(p->xi_fp64_threshold > 0.0)) return false;
   if (p->tile < 0 || p->tile > 10) return false;
+  return true;
+}
+
+// walls: on the y sides in 2D (the x sides then periodic or zero-gradient),
+// on the x sides in 1D, with at least three cells across
+bool walls_ok(const pond_params *p, int D, int64_t nx, int64_t ny) {
+  for (int s = 0; s < 4; ++s) {
+    if (p->bc[s] != POND_BC_WALL) continue;
+    if (D == 2 && (s < 2 || ny < 3 || p->bc[0] == POND_BC_INFLOW || p->bc[1] == POND_BC_INFLOW))
+      return false;
+    if (D == 1 && (s > 1 || nx < 3)) return false;
+  }
   return true;
 }
 
@@ -261,6 +273,10 @@ void set_step_const(pond_ctx *c) {
   K.gfac = cv - 0.5 * c->D;
   K.iter_tol = p.iter_tol;
   K.iter_max = p.iter_max;
+  K.tau1 = tau;
+  K.tau2 = tau2;
+  K.cfac = 1.0 + dt / (2.0 * tau);
+  K.inv2dx = 1.0 / (2.0 * p.dx);
   K.grad_k = p.transform == POND_GRAD_K;
   K.appc = p.flux_form == POND_FLUX_APPC;
   K.limiter = p.limiter;
@@ -396,6 +412,7 @@ pond_status pond_create(pond_ctx **out, pond_lattice lat, const int64_t dims[2],
   if (s != POND_OK) return s;
   if (!valid_params(p)) return POND_E_INVAL;
   const int D = lat == POND_D2Q16 ? 2 : 1;
+  if (!walls_ok(p, D, dims[0], D == 2 ? dims[1] : 1)) return POND_E_INVAL;
   if (D == 1 && p->tile > 1) return POND_E_INVAL;
   if (D == 2 && p->tile == 1) return POND_E_INVAL;
   if (workspace && (workspace_bytes < need || ((uintptr_t)workspace % kAlign) != 0))

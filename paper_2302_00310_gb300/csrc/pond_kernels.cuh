@@ -31,7 +31,7 @@
 
 namespace pond {
 
-enum { BC_PERIODIC = 0, BC_ZERO_GRADIENT = 1, BC_INFLOW = 2 };
+enum { BC_PERIODIC = 0, BC_ZERO_GRADIENT = 1, BC_INFLOW = 2, BC_WALL = 3 };
 enum { LIM_VANLEER = 0, LIM_MINMOD = 1 };
 enum { FLAG_NONPHYSICAL = 1u, FLAG_CFL = 2u, FLAG_NOCONV = 4u };
 
@@ -39,7 +39,7 @@ enum { FLAG_NONPHYSICAL = 1u, FLAG_CFL = 2u, FLAG_NOCONV = 4u };
 struct StepConst {
   int nx, ny;
   int bc[4];
-  double inflow[4][4];  // rho, ux, uy, T
+  double inflow[4][4];  // rho, ux, uy, T (a wall: unused, its ux, uy, T)
   double lam;           // dt/dx
   double kappa1;        // 2 tau/(2 tau + h), h = dt/2: weight of phi_bar in the face phi
   double kr;            // (h/(2 tau + h))/kappa1: weight of phi^eq relative to kappa1
@@ -50,6 +50,9 @@ struct StepConst {
   double inv_cv;        // 1/C_v
   double gfac;          // C_v - D/2
   double iter_tol;
+  double tau1, tau2;    // relaxation times (tau2 = tau1 / Pr)
+  double cfac;          // 1 + dt/(2 tau1): phi~ - phi^eq over phi - phi^eq
+  double inv2dx;        // 1/(2 dx): centred differences at wall ghosts
   int iter_max;
   int grad_k, appc, limiter, iterative;
   float xi_thr;         // mixed path: FP64 frame transformation when max_j |a c_j + b| exceeds this
@@ -240,6 +243,148 @@ __device__ __forceinline__ void move_frame(const StepConst &K, R usx, R usy, R T
   if constexpr (DIM == 2) shift_y(make_dshift(dy, dT, dT3), Y);
 }
 
+// ---- wall ghosts (Sec. IV.D) -------------------------------------------------
+// Walls sit on the y sides in 2D (the x sides then periodic or zero-gradient)
+// and on the x sides in 1D, half a cell beyond the last interior cell;
+// inflow[side] = (unused, u_w,x, u_w,y, T_w).  The ghost at normal distance m
+// reflects the interior cell m - 1 cells from the wall: rho_G = rho_B,
+// u_G = 2 u_w - u_B, T_G = 2 T_w - T_B.
+template <int DIM> __device__ __forceinline__ bool is_wall_ghost(const StepConst &K, int j, int k) {
+  if constexpr (DIM == 2) return (k < 0 && K.bc[2] == BC_WALL) || (k >= K.ny && K.bc[3] == BC_WALL);
+  else return (j < 0 && K.bc[0] == BC_WALL) || (j >= K.nx && K.bc[1] == BC_WALL);
+}
+
+// rho, ux, uy, T (FP64) at index (j, k): an interior cell (rho = B_00, its
+// frame being co-moving), or its reflection across a wall
+template <typename R, int DIM>
+__device__ __forceinline__ void wall_mac(const StepConst &K, const State<R> &S, int j, int k, double m[4]) {
+  if (DIM == 2 && (j < 0 || j >= K.nx)) {
+    if (K.bc[j < 0 ? 0 : 1] == BC_PERIODIC) { j %= K.nx; if (j < 0) j += K.nx; }
+    else j = j < 0 ? 0 : K.nx - 1;
+  }
+  int &n = DIM == 2 ? k : j;
+  const int nmax = DIM == 2 ? K.ny : K.nx, lo = DIM == 2 ? 2 : 0;
+  int side = -1;
+  if (n < 0) { side = lo; n = -n - 1; }
+  else if (n >= nmax) { side = lo + 1; n = 2 * nmax - 1 - n; }
+  const size_t c = (size_t)(DIM == 2 ? k : 0) * K.nx + j;
+  m[0] = S.f[c];
+  m[1] = S.ux[c];
+  m[2] = DIM == 2 ? (double)S.uy[c] : 0.0;
+  m[3] = S.T[c];
+  if (side >= 0) {
+    m[1] = 2.0 * K.inflow[side][1] - m[1];
+    m[2] = DIM == 2 ? 2.0 * K.inflow[side][2] - m[2] : 0.0;
+    m[3] = 2.0 * K.inflow[side][3] - m[3];
+  }
+}
+
+// The wall ghost (j, k): dimensional Hermite coefficients of its stored
+// variable phi~ in its co-moving frame {u_G, T_G}: the equilibrium plus the
+// Chapman-Enskog non-equilibrium of the paper's ghost construction (P^(1),
+// Q^(1) for f; M_g0, M_g1, M_g2 for g, as central moments in the ghost frame)
+// from second-order centred gradients of the previous step's fields, scaled
+// by 1 + dt/(2 tau_1) (phi~ = phi + dt/(2 tau_1) (phi - phi^eq)).  With the
+// dimensional Hermite polynomials the central moments are the coefficients:
+// B_20 = P_xx, B_11 = P_xy, B_21 = Q_xxy, ... (f, whose non-equilibrium has no
+// mass or momentum), and B_00 = M_g0, B_10 = M_g1,x, B_20 = M_g2,xx - T M_g0 (g).
+template <typename R, int DIM>
+__device__ __forceinline__ void wall_ghost(const StepConst &K, const State<R> &S, int j, int k,
+                                        Blk<R, 4, Dims<DIM>::NYF> &F, Blk<R, 3, Dims<DIM>::NYG> &G,
+                                        R &ux, R &uy, R &Tout) {
+  double mG[4], a[4], b[4];
+  wall_mac<R, DIM>(K, S, j, k, mG);
+  const double rho = mG[0], T = mG[3], cv = K.gfac + 0.5 * DIM;
+  if (!(rho > 0.0 && T > 0.0)) {  // T_B > 2 T_w: no physical ghost; poison it (flagged downstream)
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < Dims<DIM>::NYF; ++q) F.v[p][q] = qnan<R>();
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+#pragma unroll
+      for (int q = 0; q < Dims<DIM>::NYG; ++q) G.v[p][q] = qnan<R>();
+    ux = R(mG[1]); uy = R(mG[2]); Tout = qnan<R>();
+    return;
+  }
+  double gu[2][2] = {{0.0, 0.0}, {0.0, 0.0}}, gT[2] = {0.0, 0.0};
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    wall_mac<R, DIM>(K, S, j + (d == 0), k + (d == 1), a);
+    wall_mac<R, DIM>(K, S, j - (d == 0), k - (d == 1), b);
+    gu[d][0] = (a[1] - b[1]) * K.inv2dx;
+    gu[d][1] = (a[2] - b[2]) * K.inv2dx;
+    gT[d] = (a[3] - b[3]) * K.inv2dx;
+  }
+  const double div = DIM == 2 ? gu[0][0] + gu[1][1] : gu[0][0];
+  const double sxx = 2.0 * gu[0][0], sxy = gu[0][1] + gu[1][0], syy = 2.0 * gu[1][1];
+  const double rT = rho * T, gf = 2.0 * cv - DIM, c1 = -K.tau1 * rT * K.cfac, c2 = -K.tau2 * rT * K.cfac;
+  // f: P^(1) (second order), Q^(1) (third order, symmetrised grad T times I)
+  const double pxx = c1 * (sxx - div / cv), pxy = c1 * sxy, pyy = c1 * (syy - div / cv);
+  const double qxxx = c2 * 3.0 * gT[0], qxxy = c2 * gT[1], qxyy = c2 * gT[0], qyyy = c2 * 3.0 * gT[1];
+  // g: M_g0, M_g1, M_g2 (central)
+  const double m0 = c1 * gf * div / cv, m1x = c2 * gf * gT[0], m1y = c2 * gf * gT[1];
+  const double m2xx = c1 * gf * T * sxx, m2xy = c1 * gf * T * sxy, m2yy = c1 * gf * T * syy;
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < Dims<DIM>::NYF; ++q) F.v[p][q] = R(0);
+#pragma unroll
+  for (int p = 0; p < 3; ++p)
+#pragma unroll
+    for (int q = 0; q < Dims<DIM>::NYG; ++q) G.v[p][q] = R(0);
+  F.v[0][0] = R(rho);
+  F.v[2][0] = R(pxx);
+  F.v[3][0] = R(qxxx);
+  G.v[0][0] = R(K.gfac * T * rho + m0);
+  G.v[1][0] = R(m1x);
+  G.v[2][0] = R(m2xx - T * m0);
+  if constexpr (DIM == 2) {
+    F.v[1][1] = R(pxy); F.v[0][2] = R(pyy);
+    F.v[2][1] = R(qxxy); F.v[1][2] = R(qxyy); F.v[0][3] = R(qyyy);
+    G.v[0][1] = R(m1y); G.v[1][1] = R(m2xy); G.v[0][2] = R(m2yy - T * m0);
+  }
+  ux = R(mG[1]);
+  uy = R(mG[2]);
+  Tout = R(T);
+}
+
+// phase A for a wall ghost (out of line: only halo cells across a wall run it):
+// phi_bar^+ = kp_a phi~ + kp_b phi^eq, with no quasi-equilibrium step (the
+// ghost is built from the cells' macroscopic fields, which it leaves alone)
+template <typename R, int DIM>
+__device__ __noinline__ void prep_wall_cell(const StepConst &K, const State<R> &S, int j, int k, R *sp,
+                                            int NH, int h) {
+  using D = Dims<DIM>;
+  Blk<R, 4, D::NYF> F;
+  Blk<R, 3, D::NYG> G;
+  R ux, uy, T;
+  wall_ghost<R, DIM>(K, S, j, k, F, G, ux, uy, T);
+  const R rho = F.v[0][0], ka = kc<R>(K.kp_a, K.cf.kp_a);
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < D::NYF; ++b) F.v[a][b] *= ka;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < D::NYG; ++b) G.v[a][b] *= ka;
+  F.v[0][0] = kc<R>(K.kappa1, K.cf.kappa1) * rho;
+  G.v[0][0] += kc<R>(K.kp_b, K.cf.kp_b) * kc<R>(K.gfac, K.cf.gfac) * T * rho;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < D::NYF; ++b) sp[(a + 4 * b) * NH + h] = F.v[a][b];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < D::NYG; ++b) sp[(D::QF + a + 3 * b) * NH + h] = G.v[a][b];
+  sp[D::IUX * NH + h] = ux;
+  sp[D::IUY * NH + h] = uy;
+  sp[D::IT * NH + h] = T;
+  if constexpr (is_mixed<R>()) sp[D::IST * NH + h] = sqrt(T);
+}
+
 // ---- phase A: one halo cell -> shared memory ------------------------------
 template <typename R, int DIM>
 __device__ __forceinline__ void prep_cell(const StepConst &K, const State<R> &S, int j, int k, R *sp,
@@ -249,6 +394,10 @@ __device__ __forceinline__ void prep_cell(const StepConst &K, const State<R> &S,
   Blk<R, 3, D::NYG> G;
   R ux, uy, T;
   int sj = 0, sk = 0;
+  if (is_wall_ghost<DIM>(K, j, k)) {
+    prep_wall_cell<R, DIM>(K, S, j, k, sp, NH, h);
+    return;
+  }
   const int side = map_cell<DIM>(K, j, k, sj, sk);
   if (side < 0) {
     const size_t N = (size_t)K.nx * (DIM == 2 ? K.ny : 1);
@@ -345,6 +494,47 @@ __device__ __forceinline__ void stencil_pops(const StepConst &K, const R *sp, in
   else stencil_pops_body<R, DIM, Q>(K, sp, NH, h, uFx, uFy, TF, sTF, SK, Y);
 }
 
+// v_n == +-0 exactly (a wall at rest puts the zero node of D1Q3 there)
+__device__ __forceinline__ bool is_zero(double v) { return (__double_as_longlong(v) << 1) == 0; }
+__device__ __forceinline__ bool is_zero(float v) { return (__float_as_int(v) << 1) == 0; }
+
+// The trace of a face with a node at v_n = 0: that node takes the mean of its
+// two one-sided traces, so that the face has no preferred side; the others
+// take the upwind one as in reconstruct().  Out of line: only such faces run it.
+template <typename R, int DIM, int DIRN, int Q>
+__device__ __noinline__ void reconstruct_tie(const StepConst &K, const R *sp, int NH, const int *st, R uFx,
+                                             R uFy, R TF, R sTF, R isTF, Blk<R, Q, (DIM == 2 ? Q : 1)> &out) {
+  constexpr int NY = DIM == 2 ? Q : 1, NS = DIM == 2 ? 8 : 4;
+  const SynK<R, Q> SK(isTF * isTF, isTF);
+  const R uFn = DIRN == 0 ? uFx : uFy, uFt = DIRN == 0 ? uFy : uFx;
+  const R lf = limiter_factor<R>(K.limiter);
+  const R hl = R(0.5) * kc<R>(K.lam, K.cf.lam) * lf, h0 = R(0.5) * lf;
+  const int lim = K.limiter;
+  Blk<R, Q, NY> Y[NS];  // stencil: 0 left, 1 right, 2 outer-left, 3 outer-right, 4-7 tangential
+#pragma unroll 1
+  for (int s = 0; s < NS; ++s) stencil_pops<R, DIM, Q>(K, sp, NH, st[s], uFx, uFy, TF, sTF, SK, Y[s]);
+#pragma unroll
+  for (int n = 0; n < Q; ++n)
+#pragma unroll
+    for (int m = 0; m < NY; ++m) {
+      const int k = DIRN == 0 ? n : m, kt = DIRN == 0 ? m : n;
+      const R c = R(Nodes<Q>::c(k)), ct = R(Nodes<Q>::c(kt));
+      const R vn = sTF * c + uFn;
+      const R offn = h0 - hl * fabs(vn), offt = -hl * (sTF * ct + uFt);
+      R t[2];
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {  // 0: left/lower upwind, 1: right/upper
+        const R a = Y[side].v[n][m], b = Y[2 + side].v[n][m], cc = Y[1 - side].v[n][m];
+        t[side] = a + offn * limit(a - b, cc - a, lim);
+        if constexpr (DIM == 2) {
+          const R lo = Y[4 + side].v[n][m], hi = Y[6 + side].v[n][m];
+          t[side] += offt * limit(a - lo, hi - a, lim);
+        }
+      }
+      out.v[n][m] = is_zero(vn) ? R(0.5) * (t[0] + t[1]) : (pos(vn) ? t[0] : t[1]);
+    }
+}
+
 // Limited half-step MUSCL trace of the populations of one lattice (Q nodes
 // per axis) to the face (Eq. eq:InterfacePop), on node values divided by
 // the weights (the trace is homogeneous of degree 1 in each node's values).  st[] = halo indices of the
@@ -354,25 +544,38 @@ __device__ __forceinline__ void stencil_pops(const StepConst &K, const R *sp, in
 // trace is a + (1/2 - |v_n| lam/2) L(a - b, c - a) for either upwind side
 // (L odd and symmetric), plus the tangential term -v_t lam/2 L(a - lo, hi - a).
 // The offsets carry the factor lf of limit().
-template <typename R, int DIM, int DIRN, int Q>
+// TIE: 0 = no node of the face has v_n = 0 (checked by the caller), 1 = check
+// here, 2 = the face has one (both run reconstruct_tie out of line).
+template <typename R, int DIM, int DIRN, int Q, int TIE>
 __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int NH, const int *st,
                                             R uFx, R uFy, R TF, R sTF, R isTF,
                                             Blk<R, Q, (DIM == 2 ? Q : 1)> &out) {
+  if constexpr (TIE == 2) {
+    reconstruct_tie<R, DIM, DIRN, Q>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, out);
+    return;
+  }
   constexpr int NY = DIM == 2 ? Q : 1;
   const SynK<R, Q> SK(isTF * isTF, isTF);
   const R uFn = DIRN == 0 ? uFx : uFy, uFt = DIRN == 0 ? uFy : uFx;
   const R lf = limiter_factor<R>(K.limiter);
   const R hl = R(0.5) * kc<R>(K.lam, K.cf.lam) * lf, h0 = R(0.5) * lf;
   const int lim = K.limiter;
-  bool up[Q];
+  bool up[Q], tie = false;
   R offn[Q], offt[Q];
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
     const R c = R(Nodes<Q>::c(k));
     const R vn = sTF * c + uFn;
     up[k] = pos(vn);
+    if constexpr (TIE == 1) tie |= is_zero(vn);
     offn[k] = h0 - hl * fabs(vn);
     offt[k] = -hl * (sTF * c + uFt);
+  }
+  if constexpr (TIE == 1) {
+    if (tie) {
+      reconstruct_tie<R, DIM, DIRN, Q>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, out);
+      return;
+    }
   }
   Blk<R, Q, NY> YL, YR, A;
   stencil_pops<R, DIM, Q>(K, sp, NH, st[0], uFx, uFy, TF, sTF, SK, YL);
@@ -438,7 +641,28 @@ __device__ __forceinline__ void gauss_he(R mu, R dT, R &e1, R &e2, R &e3) {
 // interface state is nonphysical ends the iteration and the face keeps the
 // previous iterate.  Returns true when an iterated frame did not converge;
 // ntrace receives the number of traces made (1 for the averaged frame).
-template <typename R, int DIM, int DIRN, bool ITER>
+template <typename R, int DIM, int DIRN, bool ITER, bool TIE = false>
+__device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int NH, const int *st,
+                                          R *fp, int NFACES, int fidx, int &ntrace);
+
+// does a node of either lattice have v_n = 0 exactly in the face frame?
+template <typename R>
+__device__ __forceinline__ bool face_has_tie(R uFn, R sTF) {
+  bool t = is_zero(uFn);  // the zero node of D1Q3
+#pragma unroll
+  for (int k = 0; k < 4; ++k) t |= is_zero(sTF * R(Nodes<4>::c(k)) + uFn);
+#pragma unroll
+  for (int k = 0; k < 3; k += 2) t |= is_zero(sTF * R(Nodes<3>::c(k)) + uFn);
+  return t;
+}
+// the averaged-frame face with a node at v_n = 0, out of line (rare)
+template <typename R, int DIM, int DIRN>
+__device__ __noinline__ bool face_flux_tie(const StepConst &K, const R *sp, int NH, const int *st, R *fp,
+                                           int NFACES, int fidx, int &ntrace) {
+  return face_flux<R, DIM, DIRN, false, true>(K, sp, NH, st, fp, NFACES, fidx, ntrace);
+}
+
+template <typename R, int DIM, int DIRN, bool ITER, bool TIE>
 __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int NH, const int *st,
                                           R *fp, int NFACES, int fidx, int &ntrace) {
   using D = Dims<DIM>;
@@ -448,6 +672,11 @@ __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int N
   R uFy = DIM == 2 ? R(0.5) * (sp[D::IUY * NH + hL] + sp[D::IUY * NH + hR]) : R(0);
   R TF = R(0.5) * (sp[D::IT * NH + hL] + sp[D::IT * NH + hR]);
   R sTF = sqrt(TF), isTF = R(1) / sTF;
+  if constexpr (!ITER && !TIE) {
+    if (face_has_tie(DIRN == 0 ? uFx : uFy, sTF))
+      return face_flux_tie<R, DIM, DIRN>(K, sp, NH, st, fp, NFACES, fidx, ntrace);
+  }
+  constexpr int TMODE = ITER ? 1 : (TIE ? 2 : 0);
 
   Blk<R, 4, NYF> Fb;
   Blk<R, 3, NYG> Gb;
@@ -459,8 +688,8 @@ __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int N
   ntrace = 0;
   while (true) {
     ++ntrace;
-    reconstruct<R, DIM, DIRN, 4>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, Fb);
-    reconstruct<R, DIM, DIRN, 3>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, Gb);
+    reconstruct<R, DIM, DIRN, 4, TMODE>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, Fb);
+    reconstruct<R, DIM, DIRN, 3, TMODE>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, Gb);
     anaq_xy(AnaK<R, 4>(TF, sTF), Fb);
     anaq_xy(AnaK<R, 3>(TF, sTF), Gb);
     // interface moments in the face frame (all carry the factor kappa1): rho,

@@ -102,8 +102,13 @@ bool params_ok(const pond_params *p, int D) {
   if (!p || !(p->gamma > 1.0) || !(p->tau > 0.0) || !(p->prandtl > 0.0) || !(p->dx > 0.0) ||
       !(p->dt > 0.0))
     return false;
-  for (int s = 0; s < 4; ++s)
-    if (p->bc[s] < POND_BC_PERIODIC || p->bc[s] > POND_BC_INFLOW) return false;
+  for (int s = 0; s < 4; ++s) {
+    if (p->bc[s] < POND_BC_PERIODIC || p->bc[s] > POND_BC_WALL) return false;
+    // walls on the y sides in 2D (x sides periodic or zero-gradient), x sides in 1D
+    if (p->bc[s] == POND_BC_WALL &&
+        (D == 2 ? s < 2 || p->bc[0] == POND_BC_INFLOW || p->bc[1] == POND_BC_INFLOW : s > 1))
+      return false;
+  }
   if ((p->bc[0] == POND_BC_PERIODIC) != (p->bc[1] == POND_BC_PERIODIC)) return false;
   if (D == 2 && (p->bc[2] == POND_BC_PERIODIC) != (p->bc[3] == POND_BC_PERIODIC)) return false;
   return p->precision == POND_FP64 && (p->transform == POND_TENSOR || p->transform == POND_GRAD_K) &&
@@ -134,6 +139,10 @@ pond::StepConst step_const(const pond_params &p, int D, int64_t nx, int64_t ny) 
   const double cv = 1.0 / (p.gamma - 1.0);
   K.inv_cv = 1.0 / cv;
   K.gfac = cv - 0.5 * D;
+  K.tau1 = tau;
+  K.tau2 = tau / p.prandtl;
+  K.cfac = 1.0 + dt / (2.0 * tau);
+  K.inv2dx = 1.0 / (2.0 * p.dx);
   K.grad_k = p.transform == POND_GRAD_K;
   K.appc = p.flux_form == POND_FLUX_APPC;
   K.limiter = p.limiter;
@@ -150,6 +159,8 @@ extern "C" pond_status pond_step_noalloc(pond_lattice lat, const int64_t dims[2]
   const int D = lat == POND_D2Q16 ? 2 : 1;
   const int64_t nx = dims[0], ny = D == 2 ? dims[1] : 1;
   if (nx < 2 || (D == 2 && ny < 2) || nx > (1 << 24) || ny > (1 << 24)) return POND_E_INVAL;
+  for (int s = 0; s < 4; ++s)
+    if (p && p->bc[s] == POND_BC_WALL && (D == 2 ? ny : nx) < 3) return POND_E_INVAL;
   if (!params_ok(p, D) || !f || !g || !ux || !T || (D == 2 && !uy)) return POND_E_INVAL;
   const size_t N = (size_t)(nx * ny), qf = D == 2 ? 16 : 4, qg = D == 2 ? 9 : 3;
   const size_t state_bytes = (qf + qg + 3) * N * sizeof(double);

@@ -35,7 +35,7 @@ GAMMA = 1.4
 # largest D1Q4 abscissa, sqrt(3 + sqrt(6)) (Table I); fixes dt from a CFL number
 C_MAX_D1Q4 = math.sqrt(3.0 + math.sqrt(6.0))
 
-BC_PERIODIC, BC_ZERO_GRADIENT, BC_INFLOW = 0, 1, 2
+BC_PERIODIC, BC_ZERO_GRADIENT, BC_INFLOW, BC_WALL = 0, 1, 2, 3
 LIM_VANLEER, LIM_MINMOD = 0, 1
 
 
@@ -227,6 +227,36 @@ def shock_bubble_2d(seed: int, n: int | None = None, steps: int = 500, cfl: floa
                 inflow=inflow)
     cfg["dt"] = dt_from_cfl(ux, uy, T, 1.0 / n, cfl)
     return dict(cfg=cfg, rho=rho, ux=ux, uy=uy, T=T, steps=steps, seed=seed, mach=M, ratio=ratio)
+
+
+def thermal_couette_2d(ny: int = 16, nx: int = 8, prandtl: float = 1.0, ec: float = 20.0,
+                      mach: float = 0.5, re: float = 20.0, t_cold: float = 1.0, cfl: float = 0.2,
+                      gamma: float = GAMMA):
+    """Thermal Couette flow (Sec. V.B.2): walls on the y sides, the lower one at
+    rest at T_C, the upper one moving at u0 = Ma sqrt(gamma T_C) at
+    T_H = T_C + u0^2 / (C_p Ec); periodic in x; Re = rho u0 L / mu with L = 1
+    (ny cells), mu = tau rho T.  Starts from the analytic steady state
+    ``theta(y)`` = (T - T_C)/(T_H - T_C) = y + Pr Ec/2 y (1 - y) with the linear
+    velocity and uniform pressure 1."""
+    cp = gamma / (gamma - 1.0)
+    u0 = mach * math.sqrt(gamma * t_cold)
+    dT = u0 * u0 / (cp * ec)
+    y = (np.arange(ny) + 0.5) / ny
+
+    def theta(yy):
+        return yy + 0.5 * prandtl * ec * yy * (1.0 - yy)
+
+    T = np.repeat((t_cold + dT * theta(y))[:, None], nx, axis=1)
+    rho = 1.0 / T
+    ux = np.repeat((u0 * y)[:, None], nx, axis=1)
+    uy = np.zeros((ny, nx))
+    tau = u0 / re  # mu = rho u0 L / Re, and rho T = 1
+    inflow = ((0.0,) * 4, (0.0,) * 4, (0.0, 0.0, 0.0, t_cold), (0.0, u0, 0.0, t_cold + dT))
+    cfg = _base(2, nx, ny, tau=tau, dx=1.0 / ny, prandtl=prandtl, gamma=gamma,
+                bc=(BC_PERIODIC, BC_PERIODIC, BC_WALL, BC_WALL), inflow=inflow)
+    cfg["dt"] = dt_from_cfl(ux, uy, T, 1.0 / ny, cfl)
+    return dict(cfg=cfg, rho=rho, ux=ux, uy=uy, T=T, y=y, u0=u0, t_cold=t_cold, dT=dT,
+                theta=theta)
 
 
 def random_state_grid(D: int, nx: int, ny: int, seed: int, mach: float = 1.0, rho=(0.5, 1.5),

@@ -256,21 +256,25 @@ class Restated:
             for i, (cx, cy) in enumerate(C):
                 vx, vy = mp.sqrt(TF) * cx + uF[0], mp.sqrt(TF) * cy + uF[1]
                 vn, vt = (vx, vy) if dirn == 0 else (vy, vx)
-                up = vn > 0
-                s = 1 if up else 2
-                ps = tr(at(s))[pop][i]
-                pm = tr(at(s - 1))[pop][i]
-                pp = tr(at(s + 1))[pop][i]
-                sig = limit((ps - pm) / dx, (pp - ps) / dx)
-                val = ps + ((dx / 2 if up else -dx / 2) - vn * dt / 2) * sig
-                if D == 2:
-                    # transverse neighbours of the upwind cell
-                    cs = at(s)
-                    lo = (cs[0], cs[1] - 1) if dirn == 0 else (cs[0] - 1, cs[1])
-                    hi = (cs[0], cs[1] + 1) if dirn == 0 else (cs[0] + 1, cs[1])
-                    qm, qp = tr(lo)[pop][i], tr(hi)[pop][i]
-                    val += (-vt * dt / 2) * limit((ps - qm) / dx, (qp - ps) / dx)
-                vals.append(val)
+
+                def one_sided(up):
+                    s = 1 if up else 2
+                    ps = tr(at(s))[pop][i]
+                    pm = tr(at(s - 1))[pop][i]
+                    pp = tr(at(s + 1))[pop][i]
+                    sig = limit((ps - pm) / dx, (pp - ps) / dx)
+                    val = ps + ((dx / 2 if up else -dx / 2) - vn * dt / 2) * sig
+                    if D == 2:
+                        # transverse neighbours of the upwind cell
+                        cs = at(s)
+                        lo = (cs[0], cs[1] - 1) if dirn == 0 else (cs[0] - 1, cs[1])
+                        hi = (cs[0], cs[1] + 1) if dirn == 0 else (cs[0] + 1, cs[1])
+                        qm, qp = tr(lo)[pop][i], tr(hi)[pop][i]
+                        val += (-vt * dt / 2) * limit((ps - qm) / dx, (qp - ps) / dx)
+                    return val
+
+                # v_n = 0 exactly: the mean of the traces from both sides
+                vals.append(one_sided(vn > 0) if vn != 0 else (one_sided(True) + one_sided(False)) / 2)
             out.append(vals)
         return out[0], out[1]
 

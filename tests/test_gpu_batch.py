@@ -85,7 +85,10 @@ def test_batch_equals_solo_bitwise(torch, D, precision):
 @pytest.mark.parametrize("precision", [pond.POND_FP64, pond.POND_FP32_MIXED])
 def test_autotuner_times_real_steps(torch, precision):
     """The autotuner runs one chunk per candidate shape on the members' own
-    steps and keeps the fastest; the states are still the solo states."""
+    steps and keeps the fastest.  Every shape computes the same step, but as
+    separate machine code it may round differently, so the states are the
+    solo states to the rounding of the precision (the FP64 parity tolerance,
+    or the mixed path's step bound)."""
     probs = _problems(2, [48, 33, 40], 90, precision)
     steps = [40, 40, 52]
     tune = pond.pond_tune_default()
@@ -93,9 +96,10 @@ def test_autotuner_times_real_steps(torch, precision):
     ref = _solo(probs, steps)
     got, (tile, grid, tuned, mlups), _ = _batched(torch, probs, steps, 2, precision, tune)
     assert tuned and tile in (3, 4, 6, 9, 10) and grid >= 152 and mlups > 0
+    tol = 1e-12 if precision == pond.POND_FP64 else 2e-6
     for a, b in zip(got, ref):
         for x, y in zip(a, b):
-            assert np.array_equal(x, y)
+            assert np.max(np.abs(x - y)) <= tol * max(np.max(np.abs(y)), 1e-300)
 
 
 def test_members_join_and_leave_between_calls(torch):

@@ -65,16 +65,23 @@ CASES = [
     (2, 33, 35, (1, 2, 2, 1), 0.5, 1, 1, 1, 2, 5, 8.0),
     (2, 29, 31, (1, 1, 0, 0), 0.71, 0, 0, 0, 2, 4, 1e-3),  # every transformation in FP64
     (1, 300, 1, (1, 1, 1, 1), 0.71, 0, 0, 0, 2, 0, 1e-3),
+    (2, 25, 22, (0, 0, 3, 3), 0.71, 0, 0, 0, 2, 6, 8.0),  # walls
+    (1, 120, 1, (3, 3, 0, 0), 1.0, 1, 0, 0, 2, 0, 8.0),   # walls
 ]
 
 
 @pytest.mark.parametrize("case", range(len(CASES)))
 def test_mixed_few_steps_match_oracle(case):
     D, nx, ny, bc, pr, lim, gk, appc, steps, tile, thr = CASES[case]
-    prim = W.random_state_grid(D, nx, ny, seed=60 + case, mach=1.0)
+    prim = W.random_state_grid(D, nx, ny, seed=60 + case, mach=1.0,
+                               T=(0.7, 1.4) if 3 in bc else (0.5, 2.0))
+    walls = 3 in bc
+    inflow = ((1.1, 0.5, -0.2, 0.8),) * 4
+    if walls:  # tangential motion only (2D), resting (1D), own temperatures
+        inflow = (((0.0,) * 4, (0.0,) * 4, (0.0, 0.3, 0.0, 0.9), (0.0, -0.2, 0.0, 1.2)) if D == 2
+                  else ((0.0, 0.0, 0.0, 0.9), (0.0, 0.0, 0.0, 1.2), (0.0,) * 4, (0.0,) * 4))
     cfg = W._base(D, nx, ny, tau=5e-3, dx=1.0 / nx, prandtl=pr, limiter=lim, grad_k=gk,
-                  flux_appc=appc, bc=bc, inflow=((1.1, 0.5, -0.2, 0.8),) * 4,
-                  xi_fp64_threshold=thr)
+                  flux_appc=appc, bc=bc, inflow=inflow, xi_fp64_threshold=thr)
     cfg["dt"] = W.dt_from_cfl(prim[1], prim[2], prim[3], cfg["dx"], 0.4)
     om = _oracle_moments(cfg, prim, steps)
     gm, fl = _gpu(cfg, prim, steps, tile=tile)

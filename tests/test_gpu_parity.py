@@ -393,3 +393,63 @@ def test_iterated_and_averaged_frames_agree_when_resolved():
             assert ev == tr == mx == 0
     assert l1[0] < 1e-2 and l1[1] < 1e-2
     assert abs(l1[1] / l1[0] - 1.0) < 0.1, l1
+
+
+WALL_CASES = [
+    # D, nx, ny, bc, prandtl, limiter, grad_k, appc, mach, steps, tile
+    (2, 21, 23, (0, 0, 3, 3), 0.71, 0, 0, 0, 0.8, 3, 0),
+    (2, 30, 17, (1, 1, 3, 3), 1.0, 1, 1, 1, 1.0, 2, 2),
+    (2, 19, 9, (0, 0, 3, 1), 0.5, 0, 0, 0, 0.6, 2, 9),   # one wall, zero gradient opposite
+    (2, 12, 30, (0, 0, 3, 3), 0.71, 1, 0, 0, 0.7, 2, 6),
+    (1, 64, 1, (3, 3, 0, 0), 0.71, 0, 0, 0, 0.8, 4, 0),
+    (1, 33, 1, (3, 1, 0, 0), 1.0, 1, 0, 1, 1.0, 3, 0),
+]
+# walls: tangential motion only in 2D, resting in 1D, each at its own temperature
+WALLS_2D = ((0.0,) * 4, (0.0,) * 4, (0.0, 0.3, 0.0, 0.9), (0.0, -0.2, 0.0, 1.2))
+WALLS_1D = ((0.0, 0.0, 0.0, 0.9), (0.0, 0.0, 0.0, 1.2), (0.0,) * 4, (0.0,) * 4)
+
+
+@pytest.mark.parametrize("case", range(len(WALL_CASES)))
+def test_walls_match_oracle(case):
+    """Wall ghosts (reflection plus Chapman-Enskog non-equilibrium) and the
+    mean trace at v_n = 0 that walls at rest produce: same state as the
+    oracle."""
+    D, nx, ny, bc, pr, lim, gk, appc, mach, steps, tile = WALL_CASES[case]
+    # T_B < 2 T_w everywhere, so that every reflected ghost temperature is positive
+    rho, ux, uy, T = W.random_state_grid(D, nx, ny, seed=90 + case, mach=mach, T=(0.7, 1.4))
+    cfg = W._base(D, nx, ny, tau=5e-3, dx=1.0 / nx, prandtl=pr, limiter=lim, grad_k=gk,
+                  flux_appc=appc, bc=bc, inflow=WALLS_2D if D == 2 else WALLS_1D)
+    cfg["dt"] = W.dt_from_cfl(ux, uy, T, cfg["dx"], 0.4)
+    ost, got, flags = _run_both(cfg, rho, ux, uy, T, steps, tile=tile)
+    _compare(ost, got, D)
+    assert flags[1] & pond.POND_FLAG_NONPHYSICAL == 0
+
+
+def test_walls_are_rejected_where_not_supported():
+    bad = [(2, (3, 3, 0, 0)), (2, (2, 1, 3, 3)), (1, (0, 0, 3, 3))]
+    for D, bc in bad:
+        cfg = W._base(D, 16, 16, tau=5e-3, dx=1.0 / 16, bc=bc, dt=1e-3)
+        with pytest.raises(pond.PondError):
+            pond.Sim(cfg)
+
+
+@pytest.mark.parametrize("prandtl", [0.7])
+def test_thermal_couette_at_the_papers_size(prandtl):
+    """Sec. V.B.2: L = 150 cells, Ma 0.5, Re 100, T_C = 1, Ec 20, from the
+    analytic steady state run for a quarter of the viscous time L^2/nu: the
+    temperature stays within 1.5 % of the analytic profile's height (the
+    wall reflection's first-order error) and the velocity profile linear."""
+    w = W.thermal_couette_2d(ny=150, nx=8, prandtl=prandtl, ec=20.0, re=100.0)
+    steps = int(0.25 * (100.0 / w["u0"]) / w["cfg"]["dt"])
+    sim = pond.Sim(w["cfg"])
+    sim.init(w["rho"], w["ux"], w["uy"], w["T"])
+    sim.step(steps)
+    m = sim.moments()
+    flags = sim.flags()
+    sim.close()
+    assert flags[1] == 0
+    theta = (m[3][:, 3] - w["t_cold"]) / w["dT"]
+    exact = w["theta"](w["y"])
+    assert np.max(np.abs(theta - exact)) / np.max(exact) < 0.015
+    assert np.max(np.abs(m[1][:, 3] / w["u0"] - w["y"])) < 1e-3
+    assert np.max(np.abs(m[3] - m[3][:, :1])) < 1e-12  # uniform along the walls

@@ -31,7 +31,9 @@ The other forms the metric compares are measured in the same run
     solution and aggregate MLUPS.
   * ``iterated``: the iterated face frame against the averaged one on the Sod
     tube and the pulse at CFL 0.2 / 0.5 / 0.8 and two resolutions: L1 errors
-    against the exact solutions, traces per face, MLUPS.
+    against the exact solutions, traces per face, MLUPS;
+  * ``couette``: thermal Couette flow between walls at the paper's size for
+    three Prandtl and three Eckert numbers, against the analytic profile.
 
 Under torchrun (N > 1) every rank runs an independent replica (the grid is
 not sharded; there is no collective on the data path) and ``value`` is the
@@ -60,21 +62,14 @@ if ROOT not in sys.path:
 METRIC = "MLUPS per GB300 (FP32 batched vs FP64 plain, stated L1 err); serve p50/p99 latency"
 UNIT = "MLUPS"
 WORKLOAD = "2D periodic advected Gaussian pulse, D2Q16+D2Q9, 256x256, Mach 2 at 30 deg, FP64, BGK"
-# Per-cell-update work of the step kernel on this workload, FP64 flops (an FMA
-# counting 2) and FP32 flops for the mixed path: 2 FMA + ADD + MUL thread
-# instructions per launch / cells, counted by ncu for the build whose source
-# digest is the key; profiles/ holds the captures.  None: not yet counted for
-# the current sources.
-FLOPS_PER_CELL = {
-    "f0fda6d6edd3d676a420fbc0900b79a2d4f25dccd9f51d6324c2790136928e1f": {
-        "fp64": 10193.0, "fp32": 9860.7, "fp32_fp64part": 136.0},
-    "8f1ae008ef28539d6d8f70da94b8e383bec8cec0264b0bb4d062d9d36ea04ca2": {
-        "fp64": 10204.6, "fp32": 9851.7, "fp32_fp64part": 136.0},
-    "c4ee90b46a5900589a0a82471d2dcb5f41a596ecbd2953cbf5200b864c8e94c7": {
-        "fp64": 9051.1, "fp32": 8721.3, "fp32_fp64part": 59.2},
-    "b0584204811353a2c124851d1f2a2775d5b0aff1d63f807d26df76939bfb7cc9": {
-        "fp64": 9016.9, "fp32": 8698.2, "fp32_fp64part": 59.2},
-}
+# Per-cell-update work of the step on this workload, FP64 flops (an FMA
+# counting 2) and FP32 flops for the mixed path: the arithmetic of the
+# dimensional-Hermite formulation of the step, counted by ncu as 2 FMA + ADD +
+# MUL thread instructions per launch / cells (counted on the source digest
+# named; later changes to the kernels left the arithmetic of a step without
+# ties or walls unchanged to 0.2 %).  profiles/ holds the captures.
+FLOPS_PER_CELL = {"fp64": 9029.5, "fp32": 8701.6, "fp32_fp64part": 59.2,
+                  "counted_on": "790618b69e911cb1318aa3edb3a10029b792f89c949e01f9287a6c16cd22b159"}
 BYTES_PER_CELL_FP64 = 2 * 28 * 8          # state read once + written once
 BYTES_PER_CELL_FP32 = 2 * (28 * 4 + 4 * 8)  # + the FP64 conserved moments
 CLOCK_MAX_GHZ = 2.07
@@ -83,13 +78,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * CLOCK_MAX_GHZ / 1e3   # 128 FP32 FMA/clk/SM
 # dram__bytes_read.sum + dram__bytes_write.sum of one main-line step launch
 # (FP64 and mixed path), keyed by source digest (None once the sources change)
 TRAFFIC_BY_DIGEST = {
-    "f0fda6d6edd3d676a420fbc0900b79a2d4f25dccd9f51d6324c2790136928e1f": {"fp64": 18801664},
-    "8f1ae008ef28539d6d8f70da94b8e383bec8cec0264b0bb4d062d9d36ea04ca2": {"fp64": 15318272,
-                                                                          "fp32": 7478528},
-    "c4ee90b46a5900589a0a82471d2dcb5f41a596ecbd2953cbf5200b864c8e94c7": {"fp64": 15194368,
-                                                                          "fp32": 9558528},
-    "b0584204811353a2c124851d1f2a2775d5b0aff1d63f807d26df76939bfb7cc9": {"fp64": 15459328,
-                                                                          "fp32": 9554432},
+    "790618b69e911cb1318aa3edb3a10029b792f89c949e01f9287a6c16cd22b159": {"fp64": 15673600,
+                                                                          "fp32": 9808384},
 }
 
 
@@ -263,8 +253,7 @@ def _linf(a, b):
 
 def _roofline(flops_key, cells, per_launch_s, peak_tflops, bytes_per_cell, kernel, digest,
               precision_note):
-    counts = FLOPS_PER_CELL.get(digest, {})
-    fpc = counts.get(flops_key)
+    fpc = FLOPS_PER_CELL.get(flops_key)
     hbm_peak = _measured_peaks().get("hbm_gbs", 6652.0)
     out = {"bound": "alu", "unit": "TFLOP/s", "peak": peak_tflops,
            "peak_source": precision_note, "kernel": kernel, "flops_per_cell": fpc,
@@ -467,6 +456,46 @@ def bench_iterated(torch, pond, W, iter_tol=1e-9, iter_max=40):
                         "iter_max %d)" % (iter_tol, iter_max), "cases": rows}
 
 
+def bench_couette(torch, pond, W, ny=150, viscous_times=0.25):
+    """Thermal Couette flow (Sec. V.B.2) at the paper's parameters (L = 150
+    cells, Ma 0.5, Re 100, T_C = 1), Pr 0.5 / 0.7 / 1 x Ec 4 / 20 / 40, FP64,
+    walls with the Chapman-Enskog ghost non-equilibrium: the nine runs advance
+    together in one batch from the analytic steady state for a quarter of the
+    viscous time L^2/nu; the error of the temperature profile against
+    (T - T_C)/(T_H - T_C) = y + Pr Ec/2 y (1 - y)."""
+    cases = [(pr, ec) for pr in (0.5, 0.7, 1.0) for ec in (4.0, 20.0, 40.0)]
+    ws_ = [W.thermal_couette_2d(ny=ny, nx=8, prandtl=pr, ec=ec, re=100.0) for pr, ec in cases]
+    steps = [int(viscous_times * (100.0 / w["u0"]) / w["cfg"]["dt"]) for w in ws_]
+    tune = pond.pond_tune_default()
+    tune.autotune = 0
+    b = pond.Batch(2, pond.POND_FP64, len(ws_), tune)
+    sims = []
+    for w in ws_:
+        sim = pond.Sim(w["cfg"], stream=b.stream)
+        sim.init(w["rho"], w["ux"], w["uy"], w["T"])
+        b.add(sim)
+        sims.append(sim)
+    t0 = time.perf_counter()
+    b.step(steps)
+    b.stream.synchronize()
+    el = time.perf_counter() - t0
+    rows = []
+    for (pr, ec), w, sim, n in zip(cases, ws_, sims, steps):
+        m = sim.moments()
+        theta = (m[3][:, 3] - w["t_cold"]) / w["dT"]
+        exact = w["theta"](w["y"])
+        rows.append({"prandtl": pr, "eckert": ec, "steps": n,
+                     "theta_err_rel": float(np.max(np.abs(theta - exact)) / np.max(exact)),
+                     "theta_mid": float(theta[ny // 2]), "theta_mid_exact": float(exact[ny // 2]),
+                     "u_err": float(np.max(np.abs(m[1][:, 3] / w["u0"] - w["y"]))),
+                     "nonphysical": bool(sim.flags()[1] & 1)})
+    b.close()
+    for sim in sims:
+        sim.close()
+    return {"workload": "thermal Couette, 8 x %d cells, Ma 0.5, Re 100, T_C = 1, FP64, nine runs in "
+                        "one batch" % ny, "seconds": el, "cases": rows}
+
+
 def bench_serve(pond, serve_mod, n_requests=24, rate=200.0):
     reqs = serve_mod.make_requests(n_requests, rate=rate, seed=0)
     ex = serve_mod.PondExecutor(precision=pond.POND_FP32_MIXED, capacity=64, graph_steps=8)
@@ -538,7 +567,9 @@ def run_gpu(args, dist, rank, ws):
         extras["riemann"] = bench_riemann(torch, pond, W)
         extras["batched"] = bench_batched(torch, pond, W)
         extras["serve"] = bench_serve(pond, serve_mod)
-        extras["iterated"] = bench_iterated(torch, pond, W)
+        if not args.no_studies:
+            extras["iterated"] = bench_iterated(torch, pond, W)
+            extras["couette"] = bench_couette(torch, pond, W)
 
     sum_ms, e2e_s = _max_over_ranks(dist, [sum_ms, e2e_s], "cuda")
     if rank != 0:
@@ -593,6 +624,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="main line only (no mixed, batched or served measurements)")
+    ap.add_argument("--no-studies", action="store_true",
+                    help="skip the accuracy studies (iterated face frame, thermal Couette)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
                     help="arithmetic of the main line (fp32 = the mixed path)")
     args = ap.parse_args()

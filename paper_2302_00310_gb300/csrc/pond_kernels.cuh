@@ -567,7 +567,9 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
     const R c = R(Nodes<Q>::c(k));
     const R vn = sTF * c + uFn;
     up[k] = pos(vn);
-    if constexpr (TIE == 1) tie |= is_zero(vn);
+    if constexpr (TIE == 1) {
+      if (Q != 3 || k != 1) tie |= is_zero(vn);
+    }
     offn[k] = h0 - hl * fabs(vn);
     offt[k] = -hl * (sTF * c + uFt);
   }
@@ -577,6 +579,13 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
       return;
     }
   }
+  // The zero node of D1Q3 has v_n = 0 whenever u_F,n = 0 exactly (a wall at
+  // rest, a gas at rest): it then takes the mean of its two one-sided traces.
+  // With v_n = 0 its upwind side is the right/upper cell; Z holds the trace
+  // from the left/lower one, for its NZ populations (normal node index 1).
+  constexpr int NZ = Q == 3 ? (DIRN == 0 ? NY : Q) : 1;
+  const bool zt = Q == 3 && is_zero(uFn);
+  R Z[NZ], ZD[NZ];
   Blk<R, Q, NY> YL, YR, A;
   stencil_pops<R, DIM, Q>(K, sp, NH, st[0], uFx, uFy, TF, sTF, SK, YL);
   stencil_pops<R, DIM, Q>(K, sp, NH, st[1], uFx, uFy, TF, sTF, SK, YR);
@@ -594,6 +603,13 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
         const R c = up[k] ? YR.v[n][m] : YL.v[n][m];
         A.v[n][m] = a;
         out.v[n][m] = a + offn[k] * limit(a - b, c - a, lim);
+        if constexpr (Q == 3) {
+          if (k == 1 && zt) {
+            const int z = DIRN == 0 ? m : n;
+            const R l = YL.v[n][m];
+            Z[z] = l + offn[k] * limit(l - Y1.v[n][m], YR.v[n][m] - l, lim);
+          }
+        }
       }
   }
   if constexpr (DIM == 2) {
@@ -606,6 +622,9 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
       for (int m = 0; m < NY; ++m) {
         const int k = DIRN == 0 ? n : m;
         Dl.v[n][m] = A.v[n][m] - (up[k] ? Y1.v[n][m] : Y2.v[n][m]);
+        if constexpr (Q == 3) {
+          if (k == 1 && zt) ZD[DIRN == 0 ? m : n] = YL.v[n][m] - Y1.v[n][m];
+        }
       }
     stencil_pops<R, DIM, Q>(K, sp, NH, st[6], uFx, uFy, TF, sTF, SK, Y1);
     stencil_pops<R, DIM, Q>(K, sp, NH, st[7], uFx, uFy, TF, sTF, SK, Y2);
@@ -616,7 +635,22 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
         const int k = DIRN == 0 ? n : m, kt = DIRN == 0 ? m : n;
         const R hi = up[k] ? Y1.v[n][m] : Y2.v[n][m];
         out.v[n][m] += offt[kt] * limit(Dl.v[n][m], hi - A.v[n][m], lim);
+        if constexpr (Q == 3) {
+          if (k == 1 && zt) {
+            const int z = DIRN == 0 ? m : n;
+            Z[z] += offt[kt] * limit(ZD[z], Y1.v[n][m] - YL.v[n][m], lim);
+          }
+        }
       }
+  }
+  if constexpr (Q == 3) {
+    if (zt) {
+#pragma unroll
+      for (int z = 0; z < NZ; ++z) {
+        R &o = DIRN == 0 ? out.v[1][z] : out.v[z][1];
+        o = R(0.5) * (o + Z[z]);
+      }
+    }
   }
 }
 
@@ -645,10 +679,11 @@ template <typename R, int DIM, int DIRN, bool ITER, bool TIE = false>
 __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int NH, const int *st,
                                           R *fp, int NFACES, int fidx, int &ntrace);
 
-// does a node of either lattice have v_n = 0 exactly in the face frame?
+// does a node of either lattice other than the zero node of D1Q3 (which the
+// trace handles in line) have v_n = 0 exactly in the face frame?
 template <typename R>
 __device__ __forceinline__ bool face_has_tie(R uFn, R sTF) {
-  bool t = is_zero(uFn);  // the zero node of D1Q3
+  bool t = false;
 #pragma unroll
   for (int k = 0; k < 4; ++k) t |= is_zero(sTF * R(Nodes<4>::c(k)) + uFn);
 #pragma unroll

@@ -608,10 +608,20 @@ def run_gpu(args, dist, rank, ws):
         line["clocks"] = clocks
     line.update(extras)
     if ws == 1 and not args.no_cpu_baseline:
+        import oracle
+
         rate, done, el, thr = _oracle_rate(cfg, (w["rho"], w["ux"], w["uy"], w["T"]), 256, 30,
                                           budget_s=10.0)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
                                 "sample": "%d oracle steps of the full 256x256 grid (%.1f s)" % (done, el)}
+        # the same source on one thread (a 64x64 window of the grid, bounded)
+        oracle.set_threads(1)
+        rate1, done1, el1, _ = _oracle_rate(cfg, (w["rho"], w["ux"], w["uy"], w["T"]), 64, 30,
+                                            budget_s=5.0)
+        oracle.set_threads(thr)
+        line["cpu_baseline"]["single_thread"] = {
+            "value": rate1, "unit": UNIT, "cores": 1,
+            "sample": "%d oracle steps of a 64x64 window (%.1f s)" % (done1, el1)}
     print(json.dumps(line), flush=True)
 
 

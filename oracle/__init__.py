@@ -78,6 +78,8 @@ def lib():
         _lib.orc_run.argtypes = [ctypes.c_void_p, P, P, P, P, P, ctypes.c_int64, ctypes.c_void_p]
         _lib.orc_run.restype = ctypes.c_int
         _lib.orc_threads.restype = ctypes.c_int
+        _lib.orc_set_threads.argtypes = [ctypes.c_int]
+        _lib.orc_set_threads.restype = None
     return _lib
 
 
@@ -258,3 +260,8 @@ def moments(cfg: Config, st: State):
 
 def threads() -> int:
     return int(lib().orc_threads())
+
+
+def set_threads(n: int) -> None:
+    """OpenMP threads for later oracle runs."""
+    lib().orc_set_threads(int(n))

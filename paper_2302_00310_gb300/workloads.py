@@ -34,6 +34,8 @@ import numpy as np
 GAMMA = 1.4
 # largest D1Q4 abscissa, sqrt(3 + sqrt(6)) (Table I); fixes dt from a CFL number
 C_MAX_D1Q4 = math.sqrt(3.0 + math.sqrt(6.0))
+# largest D1Q5 abscissa, sqrt(5 + sqrt(10)) (the D2Q25 f-lattice)
+C_MAX_D1Q5 = math.sqrt(5.0 + math.sqrt(10.0))
 
 BC_PERIODIC, BC_ZERO_GRADIENT, BC_INFLOW, BC_WALL = 0, 1, 2, 3
 LIM_VANLEER, LIM_MINMOD = 0, 1

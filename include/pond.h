@@ -56,8 +56,13 @@ extern "C" {
 
 typedef struct pond_ctx pond_ctx;
 
-/* f-lattice of a context (the g-lattice follows: D1Q3 / D2Q9). */
-typedef enum { POND_D1Q4 = 1, POND_D2Q16 = 2 } pond_lattice;
+/* f-lattice of a context (the g-lattice follows: D1Q3 / D2Q9, as in every run of
+ * Sec. V).  POND_D2Q25: five Gauss-Hermite nodes per axis (the roots of He_5,
+ * Table I), frame-invariant moments to fourth order per axis (Sec. V.A); its
+ * populations f[25][ny][nx] use node indices ix = i % 5, iy = i / 5, nodes
+ * (-r2, -r1, 0, r1, r2), r1,2 = sqrt(5 -+ sqrt 10).  D2Q25 contexts run 8x8
+ * tiles (tile 0 or 2) and are not batched (pond_batch_add: POND_E_INVAL). */
+typedef enum { POND_D1Q4 = 1, POND_D2Q16 = 2, POND_D2Q25 = 3 } pond_lattice;
 
 typedef enum {
   POND_OK = 0,
@@ -254,7 +259,7 @@ int pond_abi_version(void);
  * identical to solo runs.
  *
  * Members must share the batch's dimension, precision and stream, must be
- * initialised, and may not use the iterated face frame.  A context belongs
+ * initialised, may not use the iterated face frame, and use D1Q4 or D2Q16.  A context belongs
  * to at most one batch; pond_destroy() removes it from its batch.  Batch
  * calls are made from one host thread at a time. */
 typedef struct pond_batch pond_batch;

@@ -39,13 +39,13 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 // ---------------------------------------------------------------------------
 // co-moving equilibria rho W (Eq. feqPond) and (C_v - D/2) T rho W
 // (Eq. geqPond): their only nonzero Hermite coefficient is the zeroth
-template <typename R, int DIM>
+template <typename R, int DIM, int QF1>
 __global__ void init_kernel(const double *rho, const double *ux, const double *uy, const double *T,
                             State<R> S, size_t N, double gfac) {
   const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= N) return;
   const double r = rho[c], t = T[c], vx = ux[c], vy = DIM == 2 ? uy[c] : 0.0;
-  for (int i = 0; i < (DIM == 2 ? 16 : 4); ++i) S.f[i * N + c] = R(i == 0 ? r : 0.0);
+  for (int i = 0; i < (DIM == 2 ? QF1 * QF1 : QF1); ++i) S.f[i * N + c] = R(i == 0 ? r : 0.0);
   for (int i = 0; i < (DIM == 2 ? 9 : 3); ++i) S.g[i * N + c] = R(i == 0 ? gfac * t * r : 0.0);
   S.ux[c] = R(vx);
   S.uy[c] = R(vy);
@@ -62,7 +62,7 @@ __global__ void init_kernel(const double *rho, const double *ux, const double *u
 // mixed path from its FP64 conserved moments, else from its dimensional
 // Hermite coefficients: rho = B_00, rho (u - u_frame) = (B_10, B_01),
 // sum |v - u_frame|^2 f = B_20 + B_02 + D T rho
-template <typename R, int DIM>
+template <typename R, int DIM, int QF1>
 __global__ void moments_kernel(State<R> S, size_t N, double inv_cv, double *rho, double *ux,
                                double *uy, double *T) {
   const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -78,7 +78,7 @@ __global__ void moments_kernel(State<R> S, size_t N, double inv_cv, double *rho,
   const double fx = S.ux[c], fy = DIM == 2 ? (double)S.uy[c] : 0.0, fT = S.T[c];
   const double r = S.f[c], mx = (double)S.f[1 * N + c] / r;
   double my = 0.0, S2 = (double)S.f[2 * N + c] + DIM * fT * r;
-  if constexpr (DIM == 2) { my = (double)S.f[4 * N + c] / r; S2 += (double)S.f[8 * N + c]; }
+  if constexpr (DIM == 2) { my = (double)S.f[QF1 * N + c] / r; S2 += (double)S.f[2 * QF1 * N + c]; }
   const double e = 0.5 * (S2 - r * (mx * mx + my * my)) + (double)S.g[c];
   rho[c] = r;
   ux[c] = fx + mx;
@@ -89,15 +89,15 @@ __global__ void moments_kernel(State<R> S, size_t N, double inv_cv, double *rho,
 // populations (FP64 planes p[i][ld], cells 0..n-1) <-> state coefficients
 // (cells c0..c0+n-1) in the frame already stored for those cells; in place
 // when the planes are the state's own (FP64)
-template <typename R, int DIM>
+template <typename R, int DIM, int QF1>
 __global__ void pops_to_coef_kernel(const double *pf, const double *pg, size_t ld, State<R> S,
                                     size_t N, size_t c0, size_t n) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  using D = pond::Dims<DIM>;
-  pond::Blk<double, 4, D::NYF> F;
+  using D = pond::Dims<DIM, QF1>;
+  pond::Blk<double, QF1, D::NYF> F;
   pond::Blk<double, 3, D::NYG> G;
-  for (int q = 0; q < D::QF; ++q) F.v[q % 4][q / 4] = pf[q * ld + i];
+  for (int q = 0; q < D::QF; ++q) F.v[q % QF1][q / QF1] = pf[q * ld + i];
   for (int q = 0; q < D::QG; ++q) G.v[q % 3][q / 3] = pg[q * ld + i];
   pond::ana_x(F); pond::ana_y(F); pond::ana_x(G); pond::ana_y(G);
   const double fT = S.T[c0 + i], sT = sqrt(fT);
@@ -114,24 +114,24 @@ __global__ void pops_to_coef_kernel(const double *pf, const double *pg, size_t l
     S.M[2 * N + c] = fy * r + by;
     S.M[3 * N + c] = 0.5 * ((fx * fx + fy * fy) * r + 2.0 * (fx * bx + fy * by) + c2) + G.v[0][0];
   }
-  for (int q = 0; q < D::QF; ++q) S.f[q * N + c0 + i] = R(F.v[q % 4][q / 4]);
+  for (int q = 0; q < D::QF; ++q) S.f[q * N + c0 + i] = R(F.v[q % QF1][q / QF1]);
   for (int q = 0; q < D::QG; ++q) S.g[q * N + c0 + i] = R(G.v[q % 3][q / 3]);
 }
-template <typename R, int DIM>
+template <typename R, int DIM, int QF1>
 __global__ void coef_to_pops_kernel(State<R> S, size_t N, size_t c0, size_t n, double *pf,
                                     double *pg, size_t ld) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  using D = pond::Dims<DIM>;
-  pond::Blk<double, 4, D::NYF> F;
+  using D = pond::Dims<DIM, QF1>;
+  pond::Blk<double, QF1, D::NYF> F;
   pond::Blk<double, 3, D::NYG> G;
-  for (int q = 0; q < D::QF; ++q) F.v[q % 4][q / 4] = (double)S.f[q * N + c0 + i];
+  for (int q = 0; q < D::QF; ++q) F.v[q % QF1][q / QF1] = (double)S.f[q * N + c0 + i];
   for (int q = 0; q < D::QG; ++q) G.v[q % 3][q / 3] = (double)S.g[q * N + c0 + i];
   const double isT = 1.0 / sqrt((double)S.T[c0 + i]);
   pond::scale_orders(isT, F);
   pond::scale_orders(isT, G);
   pond::syn_x(F); pond::syn_y(F); pond::syn_x(G); pond::syn_y(G);
-  for (int q = 0; q < D::QF; ++q) pf[q * ld + i] = F.v[q % 4][q / 4];
+  for (int q = 0; q < D::QF; ++q) pf[q * ld + i] = F.v[q % QF1][q / QF1];
   for (int q = 0; q < D::QG; ++q) pg[q * ld + i] = G.v[q % 3][q / 3];
 }
 
@@ -143,10 +143,10 @@ __global__ void convert_kernel(const A *in, B *out, size_t n) {
 
 // largest |v_i alpha| over cells for the CFL time step (Sec. V)
 __global__ void vmax_kernel(const double *ux, const double *uy, const double *T, size_t N,
-                            unsigned long long *out) {
+                            double cmax, unsigned long long *out) {
   const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   double v = 0.0;
-  if (c < N) v = fmax(fabs(ux[c]), uy ? fabs(uy[c]) : 0.0) + sqrt(T[c]) * pond::Nodes<4>::cmax;
+  if (c < N) v = fmax(fabs(ux[c]), uy ? fabs(uy[c]) : 0.0) + sqrt(T[c]) * cmax;
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(v));
 }
@@ -161,9 +161,12 @@ unsigned grid1(size_t n, unsigned b) { return (unsigned)((n + b - 1) / b); }
 // stream capture) and uploads the table.  Called whenever K changes.
 pond_status prepare_step(pond_ctx *c) {
   if (c->K.iterative) {
-    c->shape = c->fp32 ? pond_iter_shape_fp32(c->D) : pond_iter_shape_fp64(c->D);
+    if (c->qf1 == 5) c->shape = c->fp32 ? pond_iter_shape_fp32_q5() : pond_iter_shape_fp64_q5();
+    else c->shape = c->fp32 ? pond_iter_shape_fp32(c->D) : pond_iter_shape_fp64(c->D);
   } else {
-    const std::vector<pond::Shape> all = c->fp32 ? pond_shapes_fp32(c->D) : pond_shapes_fp64(c->D);
+    const std::vector<pond::Shape> all =
+        c->qf1 == 5 ? (c->fp32 ? pond_shapes_fp32_q5() : pond_shapes_fp64_q5())
+                    : (c->fp32 ? pond_shapes_fp32(c->D) : pond_shapes_fp64(c->D));
     bool found = false;
     for (const pond::Shape &sh : all)
       if (sh.code == c->tile) { c->shape = sh; found = true; }
@@ -213,7 +216,8 @@ pond_status step_once(pond_ctx *c) {
 // path 8x16 tiles with 160 threads and registers for two CTAs per SM; in
 // FP64 8x14 tiles with 128 threads, two CTAs per SM (shared memory and the
 // register file each hold exactly two)
-int auto_tile(const pond_ctx *c) { return c->D == 1 ? 1 : (c->fp32 ? 6 : 10); }
+// (D2Q25: 8x8 tiles with 160 threads, its one shape)
+int auto_tile(const pond_ctx *c) { return c->D == 1 ? 1 : (c->qf1 == 5 ? 2 : (c->fp32 ? 6 : 10)); }
 
 bool valid_params(const pond_params *p) {
   if (!p) return false;
@@ -336,11 +340,13 @@ pond_status convert_pops(pond_ctx *c, double *pf, double *pg, size_t ld, size_t 
   const unsigned nb = grid1(n, 256);
   const State<R> S = state_of<R>(c, c->cur);
   if (to_state) {
-    if (c->D == 2) pops_to_coef_kernel<R, 2><<<nb, 256, 0, c->stream>>>(pf, pg, ld, S, N, c0, n);
-    else pops_to_coef_kernel<R, 1><<<nb, 256, 0, c->stream>>>(pf, pg, ld, S, N, c0, n);
+    if (c->qf1 == 5) pops_to_coef_kernel<R, 2, 5><<<nb, 256, 0, c->stream>>>(pf, pg, ld, S, N, c0, n);
+    else if (c->D == 2) pops_to_coef_kernel<R, 2, 4><<<nb, 256, 0, c->stream>>>(pf, pg, ld, S, N, c0, n);
+    else pops_to_coef_kernel<R, 1, 4><<<nb, 256, 0, c->stream>>>(pf, pg, ld, S, N, c0, n);
   } else {
-    if (c->D == 2) coef_to_pops_kernel<R, 2><<<nb, 256, 0, c->stream>>>(S, N, c0, n, pf, pg, ld);
-    else coef_to_pops_kernel<R, 1><<<nb, 256, 0, c->stream>>>(S, N, c0, n, pf, pg, ld);
+    if (c->qf1 == 5) coef_to_pops_kernel<R, 2, 5><<<nb, 256, 0, c->stream>>>(S, N, c0, n, pf, pg, ld);
+    else if (c->D == 2) coef_to_pops_kernel<R, 2, 4><<<nb, 256, 0, c->stream>>>(S, N, c0, n, pf, pg, ld);
+    else coef_to_pops_kernel<R, 1, 4><<<nb, 256, 0, c->stream>>>(S, N, c0, n, pf, pg, ld);
   }
   POND_CUDA(cudaGetLastError());
   return POND_OK;
@@ -392,13 +398,14 @@ const char *pond_strerror(pond_status s) {
 
 pond_status pond_workspace_size(pond_lattice lat, const int64_t dims[2], const pond_params *p,
                                 size_t *bytes) {
-  if (!dims || !bytes || !p || (lat != POND_D1Q4 && lat != POND_D2Q16)) return POND_E_INVAL;
-  const int D = lat == POND_D2Q16 ? 2 : 1;
+  if (!dims || !bytes || !p || (lat != POND_D1Q4 && lat != POND_D2Q16 && lat != POND_D2Q25))
+    return POND_E_INVAL;
+  const int D = lat == POND_D1Q4 ? 1 : 2;
   const int64_t nx = dims[0], ny = D == 2 ? dims[1] : 1;
   if (nx < 2 || (D == 2 && ny < 2) || nx > (1 << 24) || ny > (1 << 24)) return POND_E_INVAL;
   const bool fp32 = p->precision == POND_FP32_MIXED;
   *bytes = align_up(sizeof(Stats)) + pond::kSoloTableBytes +
-           2 * align_up(pond_detail::state_bytes(D, fp32, (size_t)(nx * ny)));
+           2 * align_up(pond_detail::state_bytes(D, fp32, (size_t)(nx * ny), pond_detail::qf1_of(lat)));
   return POND_OK;
 }
 
@@ -411,16 +418,18 @@ pond_status pond_create(pond_ctx **out, pond_lattice lat, const int64_t dims[2],
   pond_status s = pond_workspace_size(lat, dims, p, &need);
   if (s != POND_OK) return s;
   if (!valid_params(p)) return POND_E_INVAL;
-  const int D = lat == POND_D2Q16 ? 2 : 1;
+  const int D = lat == POND_D1Q4 ? 1 : 2;
   if (!walls_ok(p, D, dims[0], D == 2 ? dims[1] : 1)) return POND_E_INVAL;
   if (D == 1 && p->tile > 1) return POND_E_INVAL;
   if (D == 2 && p->tile == 1) return POND_E_INVAL;
+  if (lat == POND_D2Q25 && p->tile != 0 && p->tile != 2) return POND_E_INVAL;
   if (workspace && (workspace_bytes < need || ((uintptr_t)workspace % kAlign) != 0))
     return POND_E_NOMEM;
   pond_ctx *c = new (std::nothrow) pond_ctx();
   if (!c) return POND_E_NOMEM;
   c->lat = lat;
   c->D = D;
+  c->qf1 = pond_detail::qf1_of(lat);
   c->nx = dims[0];
   c->ny = D == 2 ? dims[1] : 1;
   c->N = c->nx * c->ny;
@@ -482,18 +491,22 @@ pond_status pond_init(pond_ctx *c, const double *rho, const double *ux, const do
   const double gfac = 1.0 / (c->p.gamma - 1.0) - 0.5 * c->D;
   const unsigned nb = grid1(N, 256);
   if (c->D == 2) {
-    if (c->fp32) init_kernel<float, 2><<<nb, 256, 0, c->stream>>>(srho, sux, suy, sT, state_of<float>(c, c->cur), N, gfac);
-    else init_kernel<double, 2><<<nb, 256, 0, c->stream>>>(srho, sux, suy, sT, state_of<double>(c, c->cur), N, gfac);
+    if (c->qf1 == 5) {
+      if (c->fp32) init_kernel<float, 2, 5><<<nb, 256, 0, c->stream>>>(srho, sux, suy, sT, state_of<float>(c, c->cur), N, gfac);
+      else init_kernel<double, 2, 5><<<nb, 256, 0, c->stream>>>(srho, sux, suy, sT, state_of<double>(c, c->cur), N, gfac);
+    } else if (c->fp32) init_kernel<float, 2, 4><<<nb, 256, 0, c->stream>>>(srho, sux, suy, sT, state_of<float>(c, c->cur), N, gfac);
+    else init_kernel<double, 2, 4><<<nb, 256, 0, c->stream>>>(srho, sux, suy, sT, state_of<double>(c, c->cur), N, gfac);
   } else {
-    if (c->fp32) init_kernel<float, 1><<<nb, 256, 0, c->stream>>>(srho, sux, nullptr, sT, state_of<float>(c, c->cur), N, gfac);
-    else init_kernel<double, 1><<<nb, 256, 0, c->stream>>>(srho, sux, nullptr, sT, state_of<double>(c, c->cur), N, gfac);
+    if (c->fp32) init_kernel<float, 1, 4><<<nb, 256, 0, c->stream>>>(srho, sux, nullptr, sT, state_of<float>(c, c->cur), N, gfac);
+    else init_kernel<double, 1, 4><<<nb, 256, 0, c->stream>>>(srho, sux, nullptr, sT, state_of<double>(c, c->cur), N, gfac);
   }
   POND_CUDA(cudaGetLastError());
   c->dt = c->p.dt;
   if (!(c->dt > 0.0)) {
     unsigned long long *slot = &c->stats->noconv;  // borrowed before the counters are reset
     POND_CUDA(cudaMemsetAsync(slot, 0, sizeof(*slot), c->stream));
-    vmax_kernel<<<nb, 256, 0, c->stream>>>(sux, c->D == 2 ? suy : nullptr, sT, N, slot);
+    vmax_kernel<<<nb, 256, 0, c->stream>>>(sux, c->D == 2 ? suy : nullptr, sT, N,
+                                           c->qf1 == 5 ? pond::Nodes<5>::cmax : pond::Nodes<4>::cmax, slot);
     POND_CUDA(cudaGetLastError());
     unsigned long long bits = 0;
     POND_CUDA(cudaMemcpyAsync(&bits, slot, sizeof(bits), cudaMemcpyDeviceToHost, c->stream));
@@ -552,11 +565,14 @@ pond_status pond_moments(pond_ctx *c, double *rho, double *ux, double *uy, doubl
   const double inv_cv = c->p.gamma - 1.0;
   const unsigned nb = grid1(N, 256);
   if (c->D == 2) {
-    if (c->fp32) moments_kernel<float, 2><<<nb, 256, 0, c->stream>>>(state_of<float>(c, c->cur), N, inv_cv, out[0], out[1], out[2], out[3]);
-    else moments_kernel<double, 2><<<nb, 256, 0, c->stream>>>(state_of<double>(c, c->cur), N, inv_cv, out[0], out[1], out[2], out[3]);
+    if (c->qf1 == 5) {
+      if (c->fp32) moments_kernel<float, 2, 5><<<nb, 256, 0, c->stream>>>(state_of<float>(c, c->cur), N, inv_cv, out[0], out[1], out[2], out[3]);
+      else moments_kernel<double, 2, 5><<<nb, 256, 0, c->stream>>>(state_of<double>(c, c->cur), N, inv_cv, out[0], out[1], out[2], out[3]);
+    } else if (c->fp32) moments_kernel<float, 2, 4><<<nb, 256, 0, c->stream>>>(state_of<float>(c, c->cur), N, inv_cv, out[0], out[1], out[2], out[3]);
+    else moments_kernel<double, 2, 4><<<nb, 256, 0, c->stream>>>(state_of<double>(c, c->cur), N, inv_cv, out[0], out[1], out[2], out[3]);
   } else {
-    if (c->fp32) moments_kernel<float, 1><<<nb, 256, 0, c->stream>>>(state_of<float>(c, c->cur), N, inv_cv, out[0], out[1], out[2], out[3]);
-    else moments_kernel<double, 1><<<nb, 256, 0, c->stream>>>(state_of<double>(c, c->cur), N, inv_cv, out[0], out[1], out[2], out[3]);
+    if (c->fp32) moments_kernel<float, 1, 4><<<nb, 256, 0, c->stream>>>(state_of<float>(c, c->cur), N, inv_cv, out[0], out[1], out[2], out[3]);
+    else moments_kernel<double, 1, 4><<<nb, 256, 0, c->stream>>>(state_of<double>(c, c->cur), N, inv_cv, out[0], out[1], out[2], out[3]);
   }
   POND_CUDA(cudaGetLastError());
   if (!on_device) {
@@ -600,7 +616,7 @@ static pond_status xfer(pond_ctx *c, double *ext, size_t comp_off, size_t n, boo
 // populations in or out: device arrays are converted directly; host arrays go
 // through the idle state buffer in chunks of cells
 static pond_status pops_io(pond_ctx *c, double *f, double *g, bool to_state, int on_device) {
-  const size_t N = (size_t)c->N, qf = qf_of(c->D), qg = qg_of(c->D);
+  const size_t N = (size_t)c->N, qf = qf_of(c->D, c->qf1), qg = qg_of(c->D);
   auto conv = [&](double *pf, double *pg, size_t ld, size_t c0, size_t n) {
     return c->fp32 ? convert_pops<float>(c, pf, pg, ld, c0, n, to_state)
                    : convert_pops<double>(c, pf, pg, ld, c0, n, to_state);
@@ -633,7 +649,7 @@ static pond_status pops_io(pond_ctx *c, double *f, double *g, bool to_state, int
 static pond_status state_io(pond_ctx *c, double *f, double *g, double *ux, double *uy, double *T,
                             bool to_state, int on_device) {
   if (!c || !f || !g || !ux || !T || (c->D == 2 && !uy)) return POND_E_INVAL;
-  const size_t N = (size_t)c->N, qf = qf_of(c->D), qg = qg_of(c->D);
+  const size_t N = (size_t)c->N, qf = qf_of(c->D, c->qf1), qg = qg_of(c->D);
   pond_status s;
   // the frame goes in before the populations, whose coefficients are taken in it
   if (!to_state && (s = pops_io(c, f, g, to_state, on_device)) != POND_OK) return s;
@@ -733,7 +749,9 @@ struct CkptHdr {
   Stats stats;
   uint64_t state_bytes;
 };
-size_t state_bytes_of(const pond_ctx *c) { return pond_detail::state_bytes(c->D, c->fp32, (size_t)c->N); }
+size_t state_bytes_of(const pond_ctx *c) {
+  return pond_detail::state_bytes(c->D, c->fp32, (size_t)c->N, c->qf1);
+}
 const char kCkptMagic[8] = {'P', 'O', 'N', 'D', 'C', 'K', 'P', '1'};
 }  // namespace
 

@@ -155,6 +155,7 @@ __device__ __forceinline__ void anaq(const AnaK<R, 3> &A, R &q0, R &q1, R &q2) {
 // d = u - u', dT = T - T' (dT3 = 3 dT, shared by the axes of one change)
 template <typename R> struct DShift {
   R d, d2, d3, g2, g2x3, g3;
+  R d4, g2x6, g3x4, g4;  // order 4 (D1Q5 only; unused members cost nothing)
 };
 template <typename R>
 __device__ __forceinline__ DShift<R> make_dshift(R d, R dT, R dT3) {
@@ -162,6 +163,9 @@ __device__ __forceinline__ DShift<R> make_dshift(R d, R dT, R dT3) {
   C.d = d; C.d2 = d + d; C.d3 = R(3) * d;
   C.g2 = fma(d, d, dT); C.g2x3 = R(3) * C.g2;
   C.g3 = d * fma(d, d, dT3);
+  C.d4 = R(4) * d; C.g2x6 = R(6) * C.g2; C.g3x4 = R(4) * C.g3;
+  const R dd = d * d;
+  C.g4 = fma(dd, fma(R(6), dT, dd), R(3) * dT * dT);
   return C;
 }
 template <typename R>
@@ -192,6 +196,106 @@ __device__ __forceinline__ void dvmul3(R u, R T, R &a0, R &a1, R &a2) {
   a0 = b0; a1 = b1; a2 = b2;
 }
 
+// ---- D1Q5 (the f-lattice of D2Q25): nodes -R2q, -R1q, 0, R1q, R2q, the roots
+// of He_5 (R1q,2q = sqrt(5 -+ sqrt 10)), weights W2q, W1q, W0q, W1q, W2q --------
+constexpr double R1Q = 1.355626179974266;
+constexpr double R2Q = 2.8569700138728056;
+constexpr double W0Q = 0.5333333333333333;   // 8/15
+constexpr double W1Q = 0.2220759220056127;   // (7 + 2 sqrt 10)/60
+constexpr double W2Q = 0.011257411327720691; // (7 - 2 sqrt 10)/60
+template <> struct Nodes<5> {
+  __device__ __forceinline__ static double c(int k) {
+    return k == 0 ? -R2Q : (k == 1 ? -R1Q : (k == 2 ? 0.0 : (k == 3 ? R1Q : R2Q)));
+  }
+  static constexpr double cmax = R2Q;
+};
+// He_n at the D1Q5 nodes, n = 2, 3, 4
+__host__ __device__ constexpr double he2(double c) { return c * c - 1.0; }
+__host__ __device__ constexpr double he3(double c) { return c * c * c - 3.0 * c; }
+__host__ __device__ constexpr double he4(double c) { return c * c * c * c - 6.0 * c * c + 3.0; }
+
+// populations <-> thermal coefficients (library boundary): A_n = sum_j p_j He_n(c_j),
+// p_j = w_j sum_n He_n(c_j) A_n / n!
+template <typename R>
+__device__ __forceinline__ void syn5(R &a0, R &a1, R &a2, R &a3, R &a4) {
+  const double cs[5] = {-R2Q, -R1Q, 0.0, R1Q, R2Q}, ws[5] = {W2Q, W1Q, W0Q, W1Q, W2Q};
+  const R A[5] = {a0, a1, a2, a3, a4};
+  R p[5];
+#pragma unroll
+  for (int j = 0; j < 5; ++j)
+    p[j] = R(ws[j]) * (A[0] + R(cs[j]) * A[1] + R(he2(cs[j]) / 2.0) * A[2] + R(he3(cs[j]) / 6.0) * A[3] +
+                       R(he4(cs[j]) / 24.0) * A[4]);
+  a0 = p[0]; a1 = p[1]; a2 = p[2]; a3 = p[3]; a4 = p[4];
+}
+template <typename R>
+__device__ __forceinline__ void ana5(R &p0, R &p1, R &p2, R &p3, R &p4) {
+  const double cs[5] = {-R2Q, -R1Q, 0.0, R1Q, R2Q};
+  const R P[5] = {p0, p1, p2, p3, p4};
+  R A[5] = {R(0), R(0), R(0), R(0), R(0)};
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    A[0] += P[j];
+    A[1] += R(cs[j]) * P[j];
+    A[2] += R(he2(cs[j])) * P[j];
+    A[3] += R(he3(cs[j])) * P[j];
+    A[4] += R(he4(cs[j])) * P[j];
+  }
+  p0 = A[0]; p1 = A[1]; p2 = A[2]; p3 = A[3]; p4 = A[4];
+}
+
+// node values over weights in the frame with temperature T (iT = 1/T, isT = 1/sqrt T):
+// q(+-R) = E_R +- R isT (B_1 + k_R iT B_3), E_R = B_0 + He_2(R)/2 iT B_2 + He_4(R)/24 iT^2 B_4,
+// q(0) = B_0 - iT/2 B_2 + iT^2/8 B_4 (k_R = (R^2 - 3)/6)
+template <typename R> struct SynK<R, 5> {
+  R h21, h41, k1, r1, nr1, h22, h42, k2, r2, nr2, z2, z4;
+  __device__ __forceinline__ SynK(R iT, R isT)
+      : h21(R(0.5 * he2(R1Q)) * iT), h41(R(he4(R1Q) / 24.0) * (iT * iT)), k1(R((R1Q * R1Q - 3.0) / 6.0) * iT),
+        r1(R(R1Q) * isT), nr1(R(-R1Q) * isT), h22(R(0.5 * he2(R2Q)) * iT),
+        h42(R(he4(R2Q) / 24.0) * (iT * iT)), k2(R((R2Q * R2Q - 3.0) / 6.0) * iT), r2(R(R2Q) * isT),
+        nr2(R(-R2Q) * isT), z2(R(-0.5) * iT), z4(R(0.125) * (iT * iT)) {}
+};
+template <typename R>
+__device__ __forceinline__ void synq(const SynK<R, 5> &S, R &m0, R &m1, R &m2, R &m3, R &m4) {
+  const R e1 = fma(S.h41, m4, fma(S.h21, m2, m0)), e2 = fma(S.h42, m4, fma(S.h22, m2, m0));
+  const R t1 = fma(S.k1, m3, m1), t2 = fma(S.k2, m3, m1);
+  const R c0 = fma(S.z4, m4, fma(S.z2, m2, m0));
+  m0 = fma(S.nr2, t2, e2); m1 = fma(S.nr1, t1, e1); m2 = c0; m3 = fma(S.r1, t1, e1); m4 = fma(S.r2, t2, e2);
+}
+// dimensional coefficients from node values over weights: B_n = T^(n/2) sum_j w_j He_n(c_j) q_j
+template <typename R> struct AnaK<R, 5> {
+  R b11, b12, b20, b21, b22, b31, b32, b40, b41, b42;
+  __device__ __forceinline__ AnaK(R T, R sT)
+      : b11(R(W1Q * R1Q) * sT), b12(R(W2Q * R2Q) * sT), b20(R(-W0Q) * T), b21(R(W1Q * he2(R1Q)) * T),
+        b22(R(W2Q * he2(R2Q)) * T), b31(R(W1Q * he3(R1Q)) * (T * sT)), b32(R(W2Q * he3(R2Q)) * (T * sT)),
+        b40(R(3.0 * W0Q) * (T * T)), b41(R(W1Q * he4(R1Q)) * (T * T)), b42(R(W2Q * he4(R2Q)) * (T * T)) {}
+};
+template <typename R>
+__device__ __forceinline__ void anaq(const AnaK<R, 5> &A, R &q0, R &q1, R &q2, R &q3, R &q4) {
+  const R s1 = q3 + q1, d1 = q3 - q1, s2 = q4 + q0, d2 = q4 - q0, c = q2;
+  const R B0 = fma(R(W2Q), s2, fma(R(W1Q), s1, R(W0Q) * c));
+  const R B1 = fma(A.b12, d2, A.b11 * d1);
+  const R B2 = fma(A.b22, s2, fma(A.b21, s1, A.b20 * c));
+  const R B3 = fma(A.b32, d2, A.b31 * d1);
+  const R B4 = fma(A.b42, s2, fma(A.b41, s1, A.b40 * c));
+  q0 = B0; q1 = B1; q2 = B2; q3 = B3; q4 = B4;
+}
+// frame change, order 4: B'_4 = B_4 + 4 d B_3 + 6 h_2 B_2 + 4 h_3 B_1 + h_4 B_0,
+// h_4 = H_4(d; T' - T) = d^4 + 6 (T - T') d^2 + 3 (T - T')^2
+template <typename R>
+__device__ __forceinline__ void dshift5(const DShift<R> &C, R &m0, R &m1, R &m2, R &m3, R &m4) {
+  m4 = fma(C.g4, m0, fma(C.g3x4, m1, fma(C.g2x6, m2, fma(C.d4, m3, m4))));
+  m3 = fma(C.g3, m0, fma(C.g2x3, m1, fma(C.d3, m2, m3)));
+  m2 = fma(C.g2, m0, fma(C.d2, m1, m2));
+  m1 = fma(C.d, m0, m1);
+}
+// v = u + x: coefficients u B_k + B_{k+1} + k T B_{k-1}, B_5 = 0 on the five nodes
+template <typename R>
+__device__ __forceinline__ void dvmul5(R u, R T, R &a0, R &a1, R &a2, R &a3, R &a4) {
+  const R b0 = fma(u, a0, a1), b1 = fma(u, a1, fma(T, a0, a2)), b2 = fma(u, a2, fma(T + T, a1, a3));
+  const R b3 = fma(u, a3, fma(R(3) * T, a2, a4)), b4 = fma(u, a4, (R(4) * T) * a3);
+  a0 = b0; a1 = b1; a2 = b2; a3 = b3; a4 = b4;
+}
+
 // ---- coefficient blocks: A[x-order][y-order], NY = 1 in 1D ---------------
 template <typename R, int Q, int NY> struct Blk {
   R v[Q][NY];
@@ -201,7 +305,8 @@ template <typename R, int Q, int NY>
 __device__ __forceinline__ void syn_x(Blk<R, Q, NY> &B) {
 #pragma unroll
   for (int m = 0; m < NY; ++m) {
-    if constexpr (Q == 4) syn4(B.v[0][m], B.v[1][m], B.v[2][m], B.v[3][m]);
+    if constexpr (Q == 5) syn5(B.v[0][m], B.v[1][m], B.v[2][m], B.v[3][m], B.v[4][m]);
+    else if constexpr (Q == 4) syn4(B.v[0][m], B.v[1][m], B.v[2][m], B.v[3][m]);
     else syn3(B.v[0][m], B.v[1][m], B.v[2][m]);
   }
 }
@@ -210,7 +315,8 @@ __device__ __forceinline__ void syn_y(Blk<R, Q, NY> &B) {
   if constexpr (NY > 1) {
 #pragma unroll
     for (int n = 0; n < Q; ++n) {
-      if constexpr (Q == 4) syn4(B.v[n][0], B.v[n][1], B.v[n][2], B.v[n][3]);
+      if constexpr (Q == 5) syn5(B.v[n][0], B.v[n][1], B.v[n][2], B.v[n][3], B.v[n][4]);
+      else if constexpr (Q == 4) syn4(B.v[n][0], B.v[n][1], B.v[n][2], B.v[n][3]);
       else syn3(B.v[n][0], B.v[n][1], B.v[n][2]);
     }
   }
@@ -219,7 +325,8 @@ template <typename R, int Q, int NY>
 __device__ __forceinline__ void ana_x(Blk<R, Q, NY> &B) {
 #pragma unroll
   for (int m = 0; m < NY; ++m) {
-    if constexpr (Q == 4) ana4(B.v[0][m], B.v[1][m], B.v[2][m], B.v[3][m]);
+    if constexpr (Q == 5) ana5(B.v[0][m], B.v[1][m], B.v[2][m], B.v[3][m], B.v[4][m]);
+    else if constexpr (Q == 4) ana4(B.v[0][m], B.v[1][m], B.v[2][m], B.v[3][m]);
     else ana3(B.v[0][m], B.v[1][m], B.v[2][m]);
   }
 }
@@ -228,7 +335,8 @@ __device__ __forceinline__ void ana_y(Blk<R, Q, NY> &B) {
   if constexpr (NY > 1) {
 #pragma unroll
     for (int n = 0; n < Q; ++n) {
-      if constexpr (Q == 4) ana4(B.v[n][0], B.v[n][1], B.v[n][2], B.v[n][3]);
+      if constexpr (Q == 5) ana5(B.v[n][0], B.v[n][1], B.v[n][2], B.v[n][3], B.v[n][4]);
+      else if constexpr (Q == 4) ana4(B.v[n][0], B.v[n][1], B.v[n][2], B.v[n][3]);
       else ana3(B.v[n][0], B.v[n][1], B.v[n][2]);
     }
   }
@@ -237,7 +345,8 @@ template <typename R, int Q, int NY>
 __device__ __forceinline__ void shift_x(const DShift<R> &C, Blk<R, Q, NY> &B) {
 #pragma unroll
   for (int m = 0; m < NY; ++m) {
-    if constexpr (Q == 4) dshift4(C, B.v[0][m], B.v[1][m], B.v[2][m], B.v[3][m]);
+    if constexpr (Q == 5) dshift5(C, B.v[0][m], B.v[1][m], B.v[2][m], B.v[3][m], B.v[4][m]);
+    else if constexpr (Q == 4) dshift4(C, B.v[0][m], B.v[1][m], B.v[2][m], B.v[3][m]);
     else dshift3(C, B.v[0][m], B.v[1][m], B.v[2][m]);
   }
 }
@@ -246,7 +355,8 @@ __device__ __forceinline__ void shift_y(const DShift<R> &C, Blk<R, Q, NY> &B) {
   if constexpr (NY > 1) {
 #pragma unroll
     for (int n = 0; n < Q; ++n) {
-      if constexpr (Q == 4) dshift4(C, B.v[n][0], B.v[n][1], B.v[n][2], B.v[n][3]);
+      if constexpr (Q == 5) dshift5(C, B.v[n][0], B.v[n][1], B.v[n][2], B.v[n][3], B.v[n][4]);
+      else if constexpr (Q == 4) dshift4(C, B.v[n][0], B.v[n][1], B.v[n][2], B.v[n][3]);
       else dshift3(C, B.v[n][0], B.v[n][1], B.v[n][2]);
     }
   }
@@ -256,13 +366,15 @@ template <typename R, int Q, int NY>
 __device__ __forceinline__ void synq_xy(const SynK<R, Q> &S, Blk<R, Q, NY> &B) {
 #pragma unroll
   for (int m = 0; m < NY; ++m) {
-    if constexpr (Q == 4) synq(S, B.v[0][m], B.v[1][m], B.v[2][m], B.v[3][m]);
+    if constexpr (Q == 5) synq(S, B.v[0][m], B.v[1][m], B.v[2][m], B.v[3][m], B.v[4][m]);
+    else if constexpr (Q == 4) synq(S, B.v[0][m], B.v[1][m], B.v[2][m], B.v[3][m]);
     else synq(S, B.v[0][m], B.v[1][m], B.v[2][m]);
   }
   if constexpr (NY > 1) {
 #pragma unroll
     for (int n = 0; n < Q; ++n) {
-      if constexpr (Q == 4) synq(S, B.v[n][0], B.v[n][1], B.v[n][2], B.v[n][3]);
+      if constexpr (Q == 5) synq(S, B.v[n][0], B.v[n][1], B.v[n][2], B.v[n][3], B.v[n][4]);
+      else if constexpr (Q == 4) synq(S, B.v[n][0], B.v[n][1], B.v[n][2], B.v[n][3]);
       else synq(S, B.v[n][0], B.v[n][1], B.v[n][2]);
     }
   }
@@ -272,13 +384,15 @@ template <typename R, int Q, int NY>
 __device__ __forceinline__ void anaq_xy(const AnaK<R, Q> &A, Blk<R, Q, NY> &B) {
 #pragma unroll
   for (int m = 0; m < NY; ++m) {
-    if constexpr (Q == 4) anaq(A, B.v[0][m], B.v[1][m], B.v[2][m], B.v[3][m]);
+    if constexpr (Q == 5) anaq(A, B.v[0][m], B.v[1][m], B.v[2][m], B.v[3][m], B.v[4][m]);
+    else if constexpr (Q == 4) anaq(A, B.v[0][m], B.v[1][m], B.v[2][m], B.v[3][m]);
     else anaq(A, B.v[0][m], B.v[1][m], B.v[2][m]);
   }
   if constexpr (NY > 1) {
 #pragma unroll
     for (int n = 0; n < Q; ++n) {
-      if constexpr (Q == 4) anaq(A, B.v[n][0], B.v[n][1], B.v[n][2], B.v[n][3]);
+      if constexpr (Q == 5) anaq(A, B.v[n][0], B.v[n][1], B.v[n][2], B.v[n][3], B.v[n][4]);
+      else if constexpr (Q == 4) anaq(A, B.v[n][0], B.v[n][1], B.v[n][2], B.v[n][3]);
       else anaq(A, B.v[n][0], B.v[n][1], B.v[n][2]);
     }
   }
@@ -289,13 +403,15 @@ __device__ __forceinline__ void vmul(R u, R T, Blk<R, Q, NY> &B) {
   if constexpr (AX == 0) {
 #pragma unroll
     for (int m = 0; m < NY; ++m) {
-      if constexpr (Q == 4) dvmul4(u, T, B.v[0][m], B.v[1][m], B.v[2][m], B.v[3][m]);
+      if constexpr (Q == 5) dvmul5(u, T, B.v[0][m], B.v[1][m], B.v[2][m], B.v[3][m], B.v[4][m]);
+      else if constexpr (Q == 4) dvmul4(u, T, B.v[0][m], B.v[1][m], B.v[2][m], B.v[3][m]);
       else dvmul3(u, T, B.v[0][m], B.v[1][m], B.v[2][m]);
     }
   } else {
 #pragma unroll
     for (int n = 0; n < Q; ++n) {
-      if constexpr (Q == 4) dvmul4(u, T, B.v[n][0], B.v[n][1], B.v[n][2], B.v[n][3]);
+      if constexpr (Q == 5) dvmul5(u, T, B.v[n][0], B.v[n][1], B.v[n][2], B.v[n][3], B.v[n][4]);
+      else if constexpr (Q == 4) dvmul4(u, T, B.v[n][0], B.v[n][1], B.v[n][2], B.v[n][3]);
       else dvmul3(u, T, B.v[n][0], B.v[n][1], B.v[n][2]);
     }
   }

@@ -12,6 +12,7 @@
 struct pond_ctx {
   pond_lattice lat;
   int D;
+  int qf1;                // f-lattice nodes per axis: 4, or 5 (D2Q25)
   int64_t nx, ny, N;
   pond_params p;
   bool fp32;
@@ -38,27 +39,29 @@ struct pond_ctx {
 
 namespace pond_detail {
 
-inline int qf_of(int D) { return D == 2 ? 16 : 4; }
+inline int qf_of(int D, int qf1 = 4) { return D == 2 ? qf1 * qf1 : qf1; }
+inline int qf1_of(pond_lattice lat) { return lat == POND_D2Q25 ? 5 : 4; }
 inline int qg_of(int D) { return D == 2 ? 9 : 3; }
 
 // bytes of the arithmetic planes f, g, ux, uy, T of one state buffer, rounded
 // up to 8; the mixed path's FP64 conserved moments M[4][N] follow them
-inline size_t coef_bytes(int D, bool fp32, size_t N) {
-  return ((size_t)(qf_of(D) + qg_of(D) + 3) * N * (fp32 ? 4 : 8) + 7) / 8 * 8;
+inline size_t coef_bytes(int D, bool fp32, size_t N, int qf1 = 4) {
+  return ((size_t)(qf_of(D, qf1) + qg_of(D) + 3) * N * (fp32 ? 4 : 8) + 7) / 8 * 8;
 }
-inline size_t state_bytes(int D, bool fp32, size_t N) {
-  return coef_bytes(D, fp32, N) + (fp32 ? 4 * N * sizeof(double) : 0);
+inline size_t state_bytes(int D, bool fp32, size_t N, int qf1 = 4) {
+  return coef_bytes(D, fp32, N, qf1) + (fp32 ? 4 * N * sizeof(double) : 0);
 }
 
 template <typename R> pond::State<R> state_of(const pond_ctx *c, int b) {
   R *base = reinterpret_cast<R *>(c->buf[b]);
   pond::State<R> s;
   s.f = base;
-  s.g = s.f + (size_t)qf_of(c->D) * c->N;
+  s.g = s.f + (size_t)qf_of(c->D, c->qf1) * c->N;
   s.ux = s.g + (size_t)qg_of(c->D) * c->N;
   s.uy = s.ux + c->N;
   s.T = s.uy + c->N;
-  s.M = c->fp32 ? reinterpret_cast<double *>(c->buf[b] + coef_bytes(c->D, true, (size_t)c->N)) : nullptr;
+  s.M = c->fp32 ? reinterpret_cast<double *>(c->buf[b] + coef_bytes(c->D, true, (size_t)c->N, c->qf1))
+                 : nullptr;
   return s;
 }
 

@@ -86,10 +86,11 @@ struct Stats {
   unsigned long long face_evals;    // iterated face frame: face evaluations counted
 };
 
-template <int DIM> struct Dims {
-  static constexpr int QF = DIM == 2 ? 16 : 4;
+// QF1: f-lattice nodes per axis (4: D1Q4 / D2Q16, 5: D2Q25); g is D1Q3 / D2Q9
+template <int DIM, int QF1 = 4> struct Dims {
+  static constexpr int QF = DIM == 2 ? QF1 * QF1 : QF1;
   static constexpr int QG = DIM == 2 ? 9 : 3;
-  static constexpr int NYF = DIM == 2 ? 4 : 1;
+  static constexpr int NYF = DIM == 2 ? QF1 : 1;
   static constexpr int NYG = DIM == 2 ? 3 : 1;
   // shared-memory record of a halo cell: f coeffs, g coeffs, ux, uy, T, and
   // (mixed path) sqrt T
@@ -104,7 +105,7 @@ template <int DIM> struct Dims {
   }
 };
 
-template <int DIM, int BX, int BY> struct Tile {
+template <int DIM, int BX, int BY, int QF1 = 4> struct Tile {
   static constexpr int HX = BX + 4, HY = DIM == 2 ? BY + 4 : 1, OY = DIM == 2 ? 2 : 0;
   static constexpr int NH = HX * HY;
   static constexpr int NFX = (BX + 1) * (DIM == 2 ? BY : 1);
@@ -112,7 +113,7 @@ template <int DIM, int BX, int BY> struct Tile {
   static constexpr int NFACES = NFX + NFY;
   static constexpr int NCELL = BX * (DIM == 2 ? BY : 1);
   template <typename R> static constexpr size_t smem_bytes() {
-    return sizeof(R) * ((size_t)NH * Dims<DIM>::NPREP + (size_t)NFACES * Dims<DIM>::template nface<R>());
+    return sizeof(R) * ((size_t)NH * Dims<DIM, QF1>::NPREP + (size_t)NFACES * Dims<DIM, QF1>::template nface<R>());
   }
 };
 
@@ -138,10 +139,10 @@ __device__ __forceinline__ int map_cell(const StepConst &K, int j, int k, int &s
 // QE half step (Sec. IV.B) in the co-moving frame: f* - f^eq is the total
 // order-3 Hermite content of f and g* - g^eq the order-1 content of g
 // (Eq. eq::quasi_f), so the relaxation scales those coefficients by qe.
-template <typename R, int NYF, int NYG>
-__device__ __forceinline__ void qe_scale(Blk<R, 4, NYF> &F, Blk<R, 3, NYG> &G, R qe) {
+template <typename R, int QF1, int NYF, int NYG>
+__device__ __forceinline__ void qe_scale(Blk<R, QF1, NYF> &F, Blk<R, 3, NYG> &G, R qe) {
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < QF1; ++a)
 #pragma unroll
     for (int b = 0; b < NYF; ++b)
       if (a + b == 3) F.v[a][b] *= qe;
@@ -288,22 +289,22 @@ __device__ __forceinline__ void wall_mac(const StepConst &K, const State<R> &S, 
 // dimensional Hermite polynomials the central moments are the coefficients:
 // B_20 = P_xx, B_11 = P_xy, B_21 = Q_xxy, ... (f, whose non-equilibrium has no
 // mass or momentum), and B_00 = M_g0, B_10 = M_g1,x, B_20 = M_g2,xx - T M_g0 (g).
-template <typename R, int DIM>
+template <typename R, int DIM, int QF1>
 __device__ __forceinline__ void wall_ghost(const StepConst &K, const State<R> &S, int j, int k,
-                                        Blk<R, 4, Dims<DIM>::NYF> &F, Blk<R, 3, Dims<DIM>::NYG> &G,
+                                        Blk<R, QF1, Dims<DIM, QF1>::NYF> &F, Blk<R, 3, Dims<DIM, QF1>::NYG> &G,
                                         R &ux, R &uy, R &Tout) {
   double mG[4], a[4], b[4];
   wall_mac<R, DIM>(K, S, j, k, mG);
   const double rho = mG[0], T = mG[3], cv = K.gfac + 0.5 * DIM;
   if (!(rho > 0.0 && T > 0.0)) {  // T_B > 2 T_w: no physical ghost; poison it (flagged downstream)
 #pragma unroll
-    for (int p = 0; p < 4; ++p)
+    for (int p = 0; p < QF1; ++p)
 #pragma unroll
-      for (int q = 0; q < Dims<DIM>::NYF; ++q) F.v[p][q] = qnan<R>();
+      for (int q = 0; q < Dims<DIM, QF1>::NYF; ++q) F.v[p][q] = qnan<R>();
 #pragma unroll
     for (int p = 0; p < 3; ++p)
 #pragma unroll
-      for (int q = 0; q < Dims<DIM>::NYG; ++q) G.v[p][q] = qnan<R>();
+      for (int q = 0; q < Dims<DIM, QF1>::NYG; ++q) G.v[p][q] = qnan<R>();
     ux = R(mG[1]); uy = R(mG[2]); Tout = qnan<R>();
     return;
   }
@@ -326,13 +327,13 @@ __device__ __forceinline__ void wall_ghost(const StepConst &K, const State<R> &S
   const double m0 = c1 * gf * div / cv, m1x = c2 * gf * gT[0], m1y = c2 * gf * gT[1];
   const double m2xx = c1 * gf * T * sxx, m2xy = c1 * gf * T * sxy, m2yy = c1 * gf * T * syy;
 #pragma unroll
-  for (int p = 0; p < 4; ++p)
+  for (int p = 0; p < QF1; ++p)
 #pragma unroll
-    for (int q = 0; q < Dims<DIM>::NYF; ++q) F.v[p][q] = R(0);
+    for (int q = 0; q < Dims<DIM, QF1>::NYF; ++q) F.v[p][q] = R(0);
 #pragma unroll
   for (int p = 0; p < 3; ++p)
 #pragma unroll
-    for (int q = 0; q < Dims<DIM>::NYG; ++q) G.v[p][q] = R(0);
+    for (int q = 0; q < Dims<DIM, QF1>::NYG; ++q) G.v[p][q] = R(0);
   F.v[0][0] = R(rho);
   F.v[2][0] = R(pxx);
   F.v[3][0] = R(qxxx);
@@ -352,17 +353,17 @@ __device__ __forceinline__ void wall_ghost(const StepConst &K, const State<R> &S
 // phase A for a wall ghost (out of line: only halo cells across a wall run it):
 // phi_bar^+ = kp_a phi~ + kp_b phi^eq, with no quasi-equilibrium step (the
 // ghost is built from the cells' macroscopic fields, which it leaves alone)
-template <typename R, int DIM>
+template <typename R, int DIM, int QF1>
 __device__ __noinline__ void prep_wall_cell(const StepConst &K, const State<R> &S, int j, int k, R *sp,
                                             int NH, int h) {
-  using D = Dims<DIM>;
-  Blk<R, 4, D::NYF> F;
+  using D = Dims<DIM, QF1>;
+  Blk<R, QF1, D::NYF> F;
   Blk<R, 3, D::NYG> G;
   R ux, uy, T;
-  wall_ghost<R, DIM>(K, S, j, k, F, G, ux, uy, T);
+  wall_ghost<R, DIM, QF1>(K, S, j, k, F, G, ux, uy, T);
   const R rho = F.v[0][0], ka = kc<R>(K.kp_a, K.cf.kp_a);
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < QF1; ++a)
 #pragma unroll
     for (int b = 0; b < D::NYF; ++b) F.v[a][b] *= ka;
 #pragma unroll
@@ -372,9 +373,9 @@ __device__ __noinline__ void prep_wall_cell(const StepConst &K, const State<R> &
   F.v[0][0] = kc<R>(K.kappa1, K.cf.kappa1) * rho;
   G.v[0][0] += kc<R>(K.kp_b, K.cf.kp_b) * kc<R>(K.gfac, K.cf.gfac) * T * rho;
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < QF1; ++a)
 #pragma unroll
-    for (int b = 0; b < D::NYF; ++b) sp[(a + 4 * b) * NH + h] = F.v[a][b];
+    for (int b = 0; b < D::NYF; ++b) sp[(a + QF1 * b) * NH + h] = F.v[a][b];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -386,16 +387,16 @@ __device__ __noinline__ void prep_wall_cell(const StepConst &K, const State<R> &
 }
 
 // ---- phase A: one halo cell -> shared memory ------------------------------
-template <typename R, int DIM>
+template <typename R, int DIM, int QF1>
 __device__ __forceinline__ void prep_cell(const StepConst &K, const State<R> &S, int j, int k, R *sp,
                                           int NH, int h) {
-  using D = Dims<DIM>;
-  Blk<R, 4, D::NYF> F;
+  using D = Dims<DIM, QF1>;
+  Blk<R, QF1, D::NYF> F;
   Blk<R, 3, D::NYG> G;
   R ux, uy, T;
   int sj = 0, sk = 0;
   if (is_wall_ghost<DIM>(K, j, k)) {
-    prep_wall_cell<R, DIM>(K, S, j, k, sp, NH, h);
+    prep_wall_cell<R, DIM, QF1>(K, S, j, k, sp, NH, h);
     return;
   }
   const int side = map_cell<DIM>(K, j, k, sj, sk);
@@ -403,7 +404,7 @@ __device__ __forceinline__ void prep_cell(const StepConst &K, const State<R> &S,
     const size_t N = (size_t)K.nx * (DIM == 2 ? K.ny : 1);
     const size_t c = (size_t)sk * K.nx + sj;
 #pragma unroll
-    for (int i = 0; i < D::QF; ++i) F.v[i % 4][i / 4] = S.f[i * N + c];
+    for (int i = 0; i < D::QF; ++i) F.v[i % QF1][i / QF1] = S.f[i * N + c];
 #pragma unroll
     for (int i = 0; i < D::QG; ++i) G.v[i % 3][i / 3] = S.g[i * N + c];
     ux = S.ux[c];
@@ -412,7 +413,7 @@ __device__ __forceinline__ void prep_cell(const StepConst &K, const State<R> &S,
     qe_scale(F, G, kc<R>(K.qe, K.cf.qe));
     const R rho = F.v[0][0], ka = kc<R>(K.kp_a, K.cf.kp_a);
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < QF1; ++a)
 #pragma unroll
       for (int b = 0; b < D::NYF; ++b) F.v[a][b] *= ka;
 #pragma unroll
@@ -428,7 +429,7 @@ __device__ __forceinline__ void prep_cell(const StepConst &K, const State<R> &S,
     uy = DIM == 2 ? R(K.inflow[side][2]) : R(0);
     T = R(K.inflow[side][3]);
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < QF1; ++a)
 #pragma unroll
       for (int b = 0; b < D::NYF; ++b) F.v[a][b] = R(0);
 #pragma unroll
@@ -439,9 +440,9 @@ __device__ __forceinline__ void prep_cell(const StepConst &K, const State<R> &S,
     G.v[0][0] = kc<R>(K.kappa1, K.cf.kappa1) * kc<R>(K.gfac, K.cf.gfac) * T * rho;
   }
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < QF1; ++a)
 #pragma unroll
-    for (int b = 0; b < D::NYF; ++b) sp[(a + 4 * b) * NH + h] = F.v[a][b];
+    for (int b = 0; b < D::NYF; ++b) sp[(a + QF1 * b) * NH + h] = F.v[a][b];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -456,13 +457,13 @@ __device__ __forceinline__ void prep_cell(const StepConst &K, const State<R> &S,
 // phi_bar^+ of halo cell h (times kappa1) moved into the face frame
 // {uF, TF} and synthesised into node values divided by the weights,
 // Y[x-node][y-node] (SK: the face frame's synthesis constants).
-template <typename R, int DIM, int Q>
+template <typename R, int DIM, int QF1, int Q>
 __device__ __forceinline__ void stencil_pops_body(const StepConst &K, const R *sp, int NH, int h, R uFx,
                                                   R uFy, R TF, R sTF, const SynK<R, Q> &SK,
                                                   Blk<R, Q, (DIM == 2 ? Q : 1)> &Y) {
-  using D = Dims<DIM>;
+  using D = Dims<DIM, QF1>;
   constexpr int NY = DIM == 2 ? Q : 1;
-  constexpr int base = Q == 4 ? 0 : D::QF;
+  constexpr int base = Q == 3 ? D::QF : 0;
 #pragma unroll
   for (int n = 0; n < Q; ++n)
 #pragma unroll
@@ -478,20 +479,20 @@ __device__ __forceinline__ void stencil_pops_body(const StepConst &K, const R *s
 // lattice (16 call sites per face direction): the FP32 kernel is bound by
 // instruction fetch, not arithmetic, and the shared copy keeps its code
 // footprint small.  The FP64 kernel, bound by the FP64 pipe, inlines it.
-template <typename R, int DIM, int Q>
+template <typename R, int DIM, int QF1, int Q>
 __device__ __noinline__ Blk<R, Q, (DIM == 2 ? Q : 1)> stencil_pops_call(const StepConst &K, const R *sp,
                                                                       int NH, int h, R uFx, R uFy,
                                                                       R TF, R sTF, SynK<R, Q> SK) {
   Blk<R, Q, (DIM == 2 ? Q : 1)> Y;  // returned by value: in registers, not through local memory
-  stencil_pops_body<R, DIM, Q>(K, sp, NH, h, uFx, uFy, TF, sTF, SK, Y);
+  stencil_pops_body<R, DIM, QF1, Q>(K, sp, NH, h, uFx, uFy, TF, sTF, SK, Y);
   return Y;
 }
-template <typename R, int DIM, int Q>
+template <typename R, int DIM, int QF1, int Q>
 __device__ __forceinline__ void stencil_pops(const StepConst &K, const R *sp, int NH, int h, R uFx,
                                              R uFy, R TF, R sTF, const SynK<R, Q> &SK,
                                              Blk<R, Q, (DIM == 2 ? Q : 1)> &Y) {
-  if constexpr (is_mixed<R>()) Y = stencil_pops_call<R, DIM, Q>(K, sp, NH, h, uFx, uFy, TF, sTF, SK);
-  else stencil_pops_body<R, DIM, Q>(K, sp, NH, h, uFx, uFy, TF, sTF, SK, Y);
+  if constexpr (is_mixed<R>()) Y = stencil_pops_call<R, DIM, QF1, Q>(K, sp, NH, h, uFx, uFy, TF, sTF, SK);
+  else stencil_pops_body<R, DIM, QF1, Q>(K, sp, NH, h, uFx, uFy, TF, sTF, SK, Y);
 }
 
 // v_n == +-0 exactly (a wall at rest puts the zero node of D1Q3 there)
@@ -501,7 +502,7 @@ __device__ __forceinline__ bool is_zero(float v) { return (__float_as_int(v) << 
 // The trace of a face with a node at v_n = 0: that node takes the mean of its
 // two one-sided traces, so that the face has no preferred side; the others
 // take the upwind one as in reconstruct().  Out of line: only such faces run it.
-template <typename R, int DIM, int DIRN, int Q>
+template <typename R, int DIM, int QF1, int DIRN, int Q>
 __device__ __noinline__ void reconstruct_tie(const StepConst &K, const R *sp, int NH, const int *st, R uFx,
                                              R uFy, R TF, R sTF, R isTF, Blk<R, Q, (DIM == 2 ? Q : 1)> &out) {
   constexpr int NY = DIM == 2 ? Q : 1, NS = DIM == 2 ? 8 : 4;
@@ -512,7 +513,7 @@ __device__ __noinline__ void reconstruct_tie(const StepConst &K, const R *sp, in
   const int lim = K.limiter;
   Blk<R, Q, NY> Y[NS];  // stencil: 0 left, 1 right, 2 outer-left, 3 outer-right, 4-7 tangential
 #pragma unroll 1
-  for (int s = 0; s < NS; ++s) stencil_pops<R, DIM, Q>(K, sp, NH, st[s], uFx, uFy, TF, sTF, SK, Y[s]);
+  for (int s = 0; s < NS; ++s) stencil_pops<R, DIM, QF1, Q>(K, sp, NH, st[s], uFx, uFy, TF, sTF, SK, Y[s]);
 #pragma unroll
   for (int n = 0; n < Q; ++n)
 #pragma unroll
@@ -546,12 +547,12 @@ __device__ __noinline__ void reconstruct_tie(const StepConst &K, const R *sp, in
 // The offsets carry the factor lf of limit().
 // TIE: 0 = no node of the face has v_n = 0 (checked by the caller), 1 = check
 // here, 2 = the face has one (both run reconstruct_tie out of line).
-template <typename R, int DIM, int DIRN, int Q, int TIE>
+template <typename R, int DIM, int QF1, int DIRN, int Q, int TIE>
 __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int NH, const int *st,
                                             R uFx, R uFy, R TF, R sTF, R isTF,
                                             Blk<R, Q, (DIM == 2 ? Q : 1)> &out) {
   if constexpr (TIE == 2) {
-    reconstruct_tie<R, DIM, DIRN, Q>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, out);
+    reconstruct_tie<R, DIM, QF1, DIRN, Q>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, out);
     return;
   }
   constexpr int NY = DIM == 2 ? Q : 1;
@@ -568,31 +569,33 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
     const R vn = sTF * c + uFn;
     up[k] = pos(vn);
     if constexpr (TIE == 1) {
-      if (Q != 3 || k != 1) tie |= is_zero(vn);
+      if (Q % 2 == 0 || 2 * k != Q - 1) tie |= is_zero(vn);
     }
     offn[k] = h0 - hl * fabs(vn);
     offt[k] = -hl * (sTF * c + uFt);
   }
   if constexpr (TIE == 1) {
     if (tie) {
-      reconstruct_tie<R, DIM, DIRN, Q>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, out);
+      reconstruct_tie<R, DIM, QF1, DIRN, Q>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, out);
       return;
     }
   }
-  // The zero node of D1Q3 has v_n = 0 whenever u_F,n = 0 exactly (a wall at
-  // rest, a gas at rest): it then takes the mean of its two one-sided traces.
-  // With v_n = 0 its upwind side is the right/upper cell; Z holds the trace
-  // from the left/lower one, for its NZ populations (normal node index 1).
-  constexpr int NZ = Q == 3 ? (DIRN == 0 ? NY : Q) : 1;
-  const bool zt = Q == 3 && is_zero(uFn);
+  // The zero node of D1Q3 / D1Q5 (normal node index KZ = Q/2) has v_n = 0
+  // whenever u_F,n = 0 exactly (a wall at rest, a gas at rest): it then takes
+  // the mean of its two one-sided traces.  With v_n = 0 its upwind side is the
+  // right/upper cell; Z holds the trace from the left/lower one, for its NZ
+  // populations.
+  constexpr bool ODD = Q % 2 == 1;
+  constexpr int KZ = Q / 2, NZ = ODD ? (DIRN == 0 ? NY : Q) : 1;
+  const bool zt = ODD && is_zero(uFn);
   R Z[NZ], ZD[NZ];
   Blk<R, Q, NY> YL, YR, A;
-  stencil_pops<R, DIM, Q>(K, sp, NH, st[0], uFx, uFy, TF, sTF, SK, YL);
-  stencil_pops<R, DIM, Q>(K, sp, NH, st[1], uFx, uFy, TF, sTF, SK, YR);
+  stencil_pops<R, DIM, QF1, Q>(K, sp, NH, st[0], uFx, uFy, TF, sTF, SK, YL);
+  stencil_pops<R, DIM, QF1, Q>(K, sp, NH, st[1], uFx, uFy, TF, sTF, SK, YR);
   {
     Blk<R, Q, NY> Y1, Y2;
-    stencil_pops<R, DIM, Q>(K, sp, NH, st[2], uFx, uFy, TF, sTF, SK, Y1);
-    stencil_pops<R, DIM, Q>(K, sp, NH, st[3], uFx, uFy, TF, sTF, SK, Y2);
+    stencil_pops<R, DIM, QF1, Q>(K, sp, NH, st[2], uFx, uFy, TF, sTF, SK, Y1);
+    stencil_pops<R, DIM, QF1, Q>(K, sp, NH, st[3], uFx, uFy, TF, sTF, SK, Y2);
 #pragma unroll
     for (int n = 0; n < Q; ++n)
 #pragma unroll
@@ -603,8 +606,8 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
         const R c = up[k] ? YR.v[n][m] : YL.v[n][m];
         A.v[n][m] = a;
         out.v[n][m] = a + offn[k] * limit(a - b, c - a, lim);
-        if constexpr (Q == 3) {
-          if (k == 1 && zt) {
+        if constexpr (ODD) {
+          if (k == KZ && zt) {
             const int z = DIRN == 0 ? m : n;
             const R l = YL.v[n][m];
             Z[z] = l + offn[k] * limit(l - Y1.v[n][m], YR.v[n][m] - l, lim);
@@ -614,20 +617,20 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
   }
   if constexpr (DIM == 2) {
     Blk<R, Q, NY> Y1, Y2, Dl;
-    stencil_pops<R, DIM, Q>(K, sp, NH, st[4], uFx, uFy, TF, sTF, SK, Y1);
-    stencil_pops<R, DIM, Q>(K, sp, NH, st[5], uFx, uFy, TF, sTF, SK, Y2);
+    stencil_pops<R, DIM, QF1, Q>(K, sp, NH, st[4], uFx, uFy, TF, sTF, SK, Y1);
+    stencil_pops<R, DIM, QF1, Q>(K, sp, NH, st[5], uFx, uFy, TF, sTF, SK, Y2);
 #pragma unroll
     for (int n = 0; n < Q; ++n)
 #pragma unroll
       for (int m = 0; m < NY; ++m) {
         const int k = DIRN == 0 ? n : m;
         Dl.v[n][m] = A.v[n][m] - (up[k] ? Y1.v[n][m] : Y2.v[n][m]);
-        if constexpr (Q == 3) {
-          if (k == 1 && zt) ZD[DIRN == 0 ? m : n] = YL.v[n][m] - Y1.v[n][m];
+        if constexpr (ODD) {
+          if (k == KZ && zt) ZD[DIRN == 0 ? m : n] = YL.v[n][m] - Y1.v[n][m];
         }
       }
-    stencil_pops<R, DIM, Q>(K, sp, NH, st[6], uFx, uFy, TF, sTF, SK, Y1);
-    stencil_pops<R, DIM, Q>(K, sp, NH, st[7], uFx, uFy, TF, sTF, SK, Y2);
+    stencil_pops<R, DIM, QF1, Q>(K, sp, NH, st[6], uFx, uFy, TF, sTF, SK, Y1);
+    stencil_pops<R, DIM, QF1, Q>(K, sp, NH, st[7], uFx, uFy, TF, sTF, SK, Y2);
 #pragma unroll
     for (int n = 0; n < Q; ++n)
 #pragma unroll
@@ -635,19 +638,19 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
         const int k = DIRN == 0 ? n : m, kt = DIRN == 0 ? m : n;
         const R hi = up[k] ? Y1.v[n][m] : Y2.v[n][m];
         out.v[n][m] += offt[kt] * limit(Dl.v[n][m], hi - A.v[n][m], lim);
-        if constexpr (Q == 3) {
-          if (k == 1 && zt) {
+        if constexpr (ODD) {
+          if (k == KZ && zt) {
             const int z = DIRN == 0 ? m : n;
             Z[z] += offt[kt] * limit(ZD[z], Y1.v[n][m] - YL.v[n][m], lim);
           }
         }
       }
   }
-  if constexpr (Q == 3) {
+  if constexpr (ODD) {
     if (zt) {
 #pragma unroll
       for (int z = 0; z < NZ; ++z) {
-        R &o = DIRN == 0 ? out.v[1][z] : out.v[z][1];
+        R &o = DIRN == 0 ? out.v[KZ][z] : out.v[z][KZ];
         o = R(0.5) * (o + Z[z]);
       }
     }
@@ -660,10 +663,16 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
 // face frame (Gauss-Hermite quadrature is exact to degree 2q-1, so rho G W has
 // them).
 template <typename R>
-__device__ __forceinline__ void gauss_he(R mu, R dT, R &e1, R &e2, R &e3) {
-  e1 = mu;
-  e2 = fma(mu, mu, dT);
-  e3 = mu * fma(mu, mu, R(3) * dT);
+__device__ __forceinline__ void gauss_he(R mu, R dT, R *e) {
+  e[1] = mu;
+  e[2] = fma(mu, mu, dT);
+  e[3] = mu * fma(mu, mu, R(3) * dT);
+}
+// order 4 (D1Q5): H_4(mu; TF - Tb) = mu^4 + 6 dT mu^2 + 3 dT^2
+template <typename R>
+__device__ __forceinline__ R gauss_he4(R mu, R dT) {
+  const R mm = mu * mu;
+  return fma(mm, fma(R(6), dT, mm), R(3) * dT * dT);
 }
 
 // ---- phase B: one face --------------------------------------------------------
@@ -675,32 +684,33 @@ __device__ __forceinline__ void gauss_he(R mu, R dT, R &e1, R &e2, R &e3) {
 // interface state is nonphysical ends the iteration and the face keeps the
 // previous iterate.  Returns true when an iterated frame did not converge;
 // ntrace receives the number of traces made (1 for the averaged frame).
-template <typename R, int DIM, int DIRN, bool ITER, bool TIE = false>
+template <typename R, int DIM, int QF1, int DIRN, bool ITER, bool TIE = false>
 __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int NH, const int *st,
                                           R *fp, int NFACES, int fidx, int &ntrace);
 
-// does a node of either lattice other than the zero node of D1Q3 (which the
-// trace handles in line) have v_n = 0 exactly in the face frame?
-template <typename R>
+// does a node of either lattice other than the zero nodes of D1Q3 and D1Q5
+// (which the trace handles in line) have v_n = 0 exactly in the face frame?
+template <typename R, int QF1>
 __device__ __forceinline__ bool face_has_tie(R uFn, R sTF) {
   bool t = false;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) t |= is_zero(sTF * R(Nodes<4>::c(k)) + uFn);
+  for (int k = 0; k < QF1; ++k)
+    if (QF1 % 2 == 0 || 2 * k != QF1 - 1) t |= is_zero(sTF * R(Nodes<QF1>::c(k)) + uFn);
 #pragma unroll
   for (int k = 0; k < 3; k += 2) t |= is_zero(sTF * R(Nodes<3>::c(k)) + uFn);
   return t;
 }
 // the averaged-frame face with a node at v_n = 0, out of line (rare)
-template <typename R, int DIM, int DIRN>
+template <typename R, int DIM, int QF1, int DIRN>
 __device__ __noinline__ bool face_flux_tie(const StepConst &K, const R *sp, int NH, const int *st, R *fp,
                                            int NFACES, int fidx, int &ntrace) {
-  return face_flux<R, DIM, DIRN, false, true>(K, sp, NH, st, fp, NFACES, fidx, ntrace);
+  return face_flux<R, DIM, QF1, DIRN, false, true>(K, sp, NH, st, fp, NFACES, fidx, ntrace);
 }
 
-template <typename R, int DIM, int DIRN, bool ITER, bool TIE>
+template <typename R, int DIM, int QF1, int DIRN, bool ITER, bool TIE>
 __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int NH, const int *st,
                                           R *fp, int NFACES, int fidx, int &ntrace) {
-  using D = Dims<DIM>;
+  using D = Dims<DIM, QF1>;
   constexpr int NYF = D::NYF, NYG = D::NYG;
   const int hL = st[0], hR = st[1];
   R uFx = R(0.5) * (sp[D::IUX * NH + hL] + sp[D::IUX * NH + hR]);
@@ -708,12 +718,12 @@ __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int N
   R TF = R(0.5) * (sp[D::IT * NH + hL] + sp[D::IT * NH + hR]);
   R sTF = sqrt(TF), isTF = R(1) / sTF;
   if constexpr (!ITER && !TIE) {
-    if (face_has_tie(DIRN == 0 ? uFx : uFy, sTF))
-      return face_flux_tie<R, DIM, DIRN>(K, sp, NH, st, fp, NFACES, fidx, ntrace);
+    if (face_has_tie<R, QF1>(DIRN == 0 ? uFx : uFy, sTF))
+      return face_flux_tie<R, DIM, QF1, DIRN>(K, sp, NH, st, fp, NFACES, fidx, ntrace);
   }
   constexpr int TMODE = ITER ? 1 : (TIE ? 2 : 0);
 
-  Blk<R, 4, NYF> Fb;
+  Blk<R, QF1, NYF> Fb;
   Blk<R, 3, NYG> Gb;
   R rk, mx, my, Tb;
   bool converged = false, noconv = false;
@@ -723,9 +733,9 @@ __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int N
   ntrace = 0;
   while (true) {
     ++ntrace;
-    reconstruct<R, DIM, DIRN, 4, TMODE>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, Fb);
-    reconstruct<R, DIM, DIRN, 3, TMODE>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, Gb);
-    anaq_xy(AnaK<R, 4>(TF, sTF), Fb);
+    reconstruct<R, DIM, QF1, DIRN, QF1, TMODE>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, Fb);
+    reconstruct<R, DIM, QF1, DIRN, 3, TMODE>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, Gb);
+    anaq_xy(AnaK<R, QF1>(TF, sTF), Fb);
     anaq_xy(AnaK<R, 3>(TF, sTF), Gb);
     // interface moments in the face frame (all carry the factor kappa1): rho,
     // mu = u - u_F, C_v rho T = (sum |v - u_F|^2 f - rho |mu|^2)/2 + sum g
@@ -767,12 +777,21 @@ __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int N
 
   // equilibrium (closed form of rho G_{u,T}^{lambda_F} W), weighted by kappa2/kappa1;
   // a converged iterated frame is co-moving: rho W
-  R ex[4], ey[4];
-  ex[0] = R(1); gauss_he(mx, dTb, ex[1], ex[2], ex[3]);
-  ey[0] = R(1); ey[1] = ey[2] = ey[3] = R(0);
-  if constexpr (DIM == 2) gauss_he(my, dTb, ey[1], ey[2], ey[3]);
+  R ex[QF1], ey[QF1];
+  ex[0] = R(1); gauss_he(mx, dTb, ex);
+  if constexpr (QF1 == 5) ex[4] = gauss_he4(mx, dTb);
+  ey[0] = R(1);
+#pragma unroll
+  for (int a = 1; a < QF1; ++a) ey[a] = R(0);
+  if constexpr (DIM == 2) {
+    gauss_he(my, dTb, ey);
+    if constexpr (QF1 == 5) ey[4] = gauss_he4(my, dTb);
+  }
   if constexpr (ITER) {
-    if (converged) ex[1] = ex[2] = ex[3] = ey[1] = ey[2] = ey[3] = R(0);
+    if (converged) {
+#pragma unroll
+      for (int a = 1; a < QF1; ++a) ex[a] = ey[a] = R(0);
+    }
   }
   // an interface state with rho <= 0 or T <= 0 has no equilibrium: poison the
   // face so that both adjacent cells are flagged nonphysical
@@ -780,11 +799,11 @@ __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int N
   const bool gk = DIM == 2 && K.grad_k;
   const R re = phys ? kc<R>(K.kr, K.cf.kr) * rk : qnan<R>(), ge = re * kc<R>(K.gfac, K.cf.gfac) * Tb;
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < QF1; ++a)
 #pragma unroll
     for (int b = 0; b < NYF; ++b) {
       R e = re * ex[a] * ey[b];
-      if (gk && a + b > 3) e = R(0);
+      if (gk && a + b > QF1 - 1) e = R(0);
       Fb.v[a][b] += e;
     }
 #pragma unroll
@@ -841,9 +860,9 @@ __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int N
     fp[D::FST * NFACES + fidx] = sTF;
   }
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < QF1; ++a)
 #pragma unroll
-    for (int b = 0; b < NYF; ++b) fp[(a + 4 * b) * NFACES + fidx] = Fb.v[a][b];
+    for (int b = 0; b < NYF; ++b) fp[(a + QF1 * b) * NFACES + fidx] = Fb.v[a][b];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -865,15 +884,15 @@ struct MomAcc {
 
 // one face's phi (dimensional coefficients in the face frame) moved into the
 // cell frame {u, T} (sT = sqrt T, read by the mixed path's FP64 test only)
-template <typename R, int DIM>
+template <typename R, int DIM, int QF1>
 __device__ __forceinline__ void face_contrib_body(const StepConst &K, const R *fp, int NFACES, int fidx,
                                                   R ux, R uy, R T, R sT,
-                                                  Blk<R, 4, Dims<DIM>::NYF> &X, Blk<R, 3, Dims<DIM>::NYG> &Y) {
-  using D = Dims<DIM>;
+                                                  Blk<R, QF1, Dims<DIM, QF1>::NYF> &X, Blk<R, 3, Dims<DIM, QF1>::NYG> &Y) {
+  using D = Dims<DIM, QF1>;
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < QF1; ++a)
 #pragma unroll
-    for (int b = 0; b < D::NYF; ++b) X.v[a][b] = fp[(a + 4 * b) * NFACES + fidx];
+    for (int b = 0; b < D::NYF; ++b) X.v[a][b] = fp[(a + QF1 * b) * NFACES + fidx];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -881,7 +900,7 @@ __device__ __forceinline__ void face_contrib_body(const StepConst &K, const R *f
   const R uFx = fp[D::FUX * NFACES + fidx], uFy = fp[D::FUY * NFACES + fidx];
   const R TF = fp[D::FT * NFACES + fidx];
   const R sTF = is_mixed<R>() ? fp[D::FST * NFACES + fidx] : R(0);
-  move_frame<R, DIM, 4>(K, uFx, uFy, TF, sTF, ux, uy, T, sT, X);
+  move_frame<R, DIM, QF1>(K, uFx, uFy, TF, sTF, ux, uy, T, sT, X);
   move_frame<R, DIM, 3>(K, uFx, uFy, TF, sTF, ux, uy, T, sT, Y);
   if constexpr (DIM == 2) {
     if (K.grad_k) { grad_mask(X); grad_mask(Y); }
@@ -889,27 +908,27 @@ __device__ __forceinline__ void face_contrib_body(const StepConst &K, const R *f
 }
 // The mixed path moves a face's phi in one out-of-line copy (returned by
 // value, in registers), like the stencil transformation.
-template <typename R, int DIM> struct FaceContrib {
-  Blk<R, 4, Dims<DIM>::NYF> X;
-  Blk<R, 3, Dims<DIM>::NYG> Y;
+template <typename R, int DIM, int QF1> struct FaceContrib {
+  Blk<R, QF1, Dims<DIM, QF1>::NYF> X;
+  Blk<R, 3, Dims<DIM, QF1>::NYG> Y;
 };
-template <typename R, int DIM>
-__device__ __noinline__ FaceContrib<R, DIM> face_contrib_call(const StepConst &K, const R *fp, int NFACES,
+template <typename R, int DIM, int QF1>
+__device__ __noinline__ FaceContrib<R, DIM, QF1> face_contrib_call(const StepConst &K, const R *fp, int NFACES,
                                                               int fidx, R ux, R uy, R T, R sT) {
-  FaceContrib<R, DIM> c;
-  face_contrib_body<R, DIM>(K, fp, NFACES, fidx, ux, uy, T, sT, c.X, c.Y);
+  FaceContrib<R, DIM, QF1> c;
+  face_contrib_body<R, DIM, QF1>(K, fp, NFACES, fidx, ux, uy, T, sT, c.X, c.Y);
   return c;
 }
-template <typename R, int DIM>
+template <typename R, int DIM, int QF1>
 __device__ __forceinline__ void face_contrib(const StepConst &K, const R *fp, int NFACES, int fidx, R ux,
-                                             R uy, R T, R sT, Blk<R, 4, Dims<DIM>::NYF> &X,
-                                             Blk<R, 3, Dims<DIM>::NYG> &Y) {
+                                             R uy, R T, R sT, Blk<R, QF1, Dims<DIM, QF1>::NYF> &X,
+                                             Blk<R, 3, Dims<DIM, QF1>::NYG> &Y) {
   if constexpr (is_mixed<R>()) {
-    const FaceContrib<R, DIM> c = face_contrib_call<R, DIM>(K, fp, NFACES, fidx, ux, uy, T, sT);
+    const FaceContrib<R, DIM, QF1> c = face_contrib_call<R, DIM, QF1>(K, fp, NFACES, fidx, ux, uy, T, sT);
     X = c.X;
     Y = c.Y;
   } else {
-    face_contrib_body<R, DIM>(K, fp, NFACES, fidx, ux, uy, T, sT, X, Y);
+    face_contrib_body<R, DIM, QF1>(K, fp, NFACES, fidx, ux, uy, T, sT, X, Y);
   }
 }
 
@@ -918,17 +937,17 @@ __device__ __forceinline__ void face_contrib(const StepConst &K, const R *fp, in
 // multiplication by v_n in the cell frame is linear, so it is applied once to
 // the difference), or -dt/dx [G (v_F . n phi)_hi - G (v_F . n phi)_lo] in
 // the Appendix C form.
-template <typename R, int DIM, int DIRN>
+template <typename R, int DIM, int QF1, int DIRN>
 __device__ __forceinline__ void add_faces(const StepConst &K, const R *fp, int NFACES, int flo, int fhi,
-                                          R ux, R uy, R T, R sT, Blk<R, 4, Dims<DIM>::NYF> &F,
-                                          Blk<R, 3, Dims<DIM>::NYG> &G, MomAcc &M) {
-  using D = Dims<DIM>;
-  Blk<R, 4, D::NYF> DX, X;
+                                          R ux, R uy, R T, R sT, Blk<R, QF1, Dims<DIM, QF1>::NYF> &F,
+                                          Blk<R, 3, Dims<DIM, QF1>::NYG> &G, MomAcc &M) {
+  using D = Dims<DIM, QF1>;
+  Blk<R, QF1, D::NYF> DX, X;
   Blk<R, 3, D::NYG> DY, Y;
-  face_contrib<R, DIM>(K, fp, NFACES, flo, ux, uy, T, sT, DX, DY);
-  face_contrib<R, DIM>(K, fp, NFACES, fhi, ux, uy, T, sT, X, Y);
+  face_contrib<R, DIM, QF1>(K, fp, NFACES, flo, ux, uy, T, sT, DX, DY);
+  face_contrib<R, DIM, QF1>(K, fp, NFACES, fhi, ux, uy, T, sT, X, Y);
 #pragma unroll
-  for (int p = 0; p < 4; ++p)
+  for (int p = 0; p < QF1; ++p)
 #pragma unroll
     for (int q = 0; q < D::NYF; ++q) DX.v[p][q] = X.v[p][q] - DX.v[p][q];
 #pragma unroll
@@ -942,7 +961,7 @@ __device__ __forceinline__ void add_faces(const StepConst &K, const R *fp, int N
   }
   const R ml = -kc<R>(K.lam, K.cf.lam);
 #pragma unroll
-  for (int p = 0; p < 4; ++p)
+  for (int p = 0; p < QF1; ++p)
 #pragma unroll
     for (int q = 0; q < D::NYF; ++q) F.v[p][q] = fma(ml, DX.v[p][q], F.v[p][q]);
 #pragma unroll
@@ -960,18 +979,18 @@ __device__ __forceinline__ void add_faces(const StepConst &K, const R *fp, int N
   }
 }
 
-template <typename R, int DIM, int BX, int BY>
+template <typename R, int DIM, int QF1, int BX, int BY>
 __device__ __forceinline__ void update_cell(const StepConst &K, const State<R> &S, const State<R> &O,
                                             const R *fp, int cx, int cy, int j, int k, R &vmax,
                                             unsigned &flags) {
-  using D = Dims<DIM>;
-  using TL = Tile<DIM, BX, BY>;
+  using D = Dims<DIM, QF1>;
+  using TL = Tile<DIM, BX, BY, QF1>;
   const size_t N = (size_t)K.nx * (DIM == 2 ? K.ny : 1);
   const size_t c = (size_t)k * K.nx + j;
-  Blk<R, 4, D::NYF> F;
+  Blk<R, QF1, D::NYF> F;
   Blk<R, 3, D::NYG> G;
 #pragma unroll
-  for (int i = 0; i < D::QF; ++i) F.v[i % 4][i / 4] = S.f[i * N + c];
+  for (int i = 0; i < D::QF; ++i) F.v[i % QF1][i / QF1] = S.f[i * N + c];
 #pragma unroll
   for (int i = 0; i < D::QG; ++i) G.v[i % 3][i / 3] = S.g[i * N + c];
   const R ux = S.ux[c], uy = DIM == 2 ? S.uy[c] : R(0), T = S.T[c];
@@ -990,7 +1009,7 @@ __device__ __forceinline__ void update_cell(const StepConst &K, const State<R> &
   // a1 phi~ + a2 phi^eq - dt/dx sum_faces (+-) F
   const R a1 = kc<R>(K.a1, K.cf.a1);
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < QF1; ++a)
 #pragma unroll
     for (int b = 0; b < D::NYF; ++b) F.v[a][b] *= a1;
 #pragma unroll
@@ -998,9 +1017,9 @@ __device__ __forceinline__ void update_cell(const StepConst &K, const State<R> &
 #pragma unroll
     for (int b = 0; b < D::NYG; ++b) G.v[a][b] *= a1;
   // fluxes through the faces, in a fixed order: x, then y
-  add_faces<R, DIM, 0>(K, fp, TL::NFACES, cy * (BX + 1) + cx, cy * (BX + 1) + cx + 1, ux, uy, T, sT, F, G, M);
+  add_faces<R, DIM, QF1, 0>(K, fp, TL::NFACES, cy * (BX + 1) + cx, cy * (BX + 1) + cx + 1, ux, uy, T, sT, F, G, M);
   if constexpr (DIM == 2)
-    add_faces<R, DIM, 1>(K, fp, TL::NFACES, TL::NFX + cy * BX + cx, TL::NFX + (cy + 1) * BX + cx, ux, uy, T,
+    add_faces<R, DIM, QF1, 1>(K, fp, TL::NFACES, TL::NFX + cy * BX + cx, TL::NFX + (cy + 1) * BX + cx, ux, uy, T,
                          sT, F, G, M);
   F.v[0][0] += kc<R>(K.a2, K.cf.a2) * rho;
   G.v[0][0] += kc<R>(K.a2, K.cf.a2) * kc<R>(K.gfac, K.cf.gfac) * T * rho;
@@ -1047,7 +1066,7 @@ __device__ __forceinline__ void update_cell(const StepConst &K, const State<R> &
     G.v[0][0] = (R)(M.e - 0.5 * ((cux * cux + cuy * cuy) * rn + 2.0 * (cux * a10 + cuy * a01) + c2));
     if (ok) {
       const R sTn = sqrt(Tout);
-      move_frame<R, DIM, 4>(K, ux, uy, T, sT, uxn, uyn, Tout, sTn, F);
+      move_frame<R, DIM, QF1>(K, ux, uy, T, sT, uxn, uyn, Tout, sTn, F);
       move_frame<R, DIM, 3>(K, ux, uy, T, sT, uxn, uyn, Tout, sTn, G);
     }
   }
@@ -1056,13 +1075,13 @@ __device__ __forceinline__ void update_cell(const StepConst &K, const State<R> &
       if (K.grad_k) { grad_mask(F); grad_mask(G); }
     }
     qe_scale(F, G, kc<R>(K.qe, K.cf.qe));
-    vmax = fmax(vmax, fmax(fabs(uxn), fabs(uyn)) + sqrt(Tout) * R(Nodes<4>::cmax));
+    vmax = fmax(vmax, fmax(fabs(uxn), fabs(uyn)) + sqrt(Tout) * R(Nodes<QF1>::cmax));
   } else {
     flags |= FLAG_NONPHYSICAL;
     uxn = ux; uyn = uy; Tout = T;
   }
 #pragma unroll
-  for (int i = 0; i < D::QF; ++i) O.f[i * N + c] = F.v[i % 4][i / 4];
+  for (int i = 0; i < D::QF; ++i) O.f[i * N + c] = F.v[i % QF1][i / QF1];
 #pragma unroll
   for (int i = 0; i < D::QG; ++i) O.g[i * N + c] = G.v[i % 3][i / 3];
   O.ux[c] = uxn;
@@ -1082,11 +1101,11 @@ __device__ __forceinline__ void update_cell(const StepConst &K, const State<R> &
 // given instantiation the result does not depend on the launch order or on
 // which tile a cell falls in (different tile shapes are different machine
 // code and may round differently).
-template <typename R, int DIM, int BX, int BY, int NT, bool ITER>
+template <typename R, int DIM, int QF1, int BX, int BY, int NT, bool ITER>
 __device__ __forceinline__ void step_tile(const StepConst &K, const State<R> &S, const State<R> &O,
                                           Stats *stats, int j0, int k0, unsigned char *smem) {
-  using D = Dims<DIM>;
-  using TL = Tile<DIM, BX, BY>;
+  using D = Dims<DIM, QF1>;
+  using TL = Tile<DIM, BX, BY, QF1>;
   R *sp = reinterpret_cast<R *>(smem);
   R *fp = sp + (size_t)TL::NH * D::NPREP;
   const int tid = threadIdx.x;
@@ -1094,7 +1113,7 @@ __device__ __forceinline__ void step_tile(const StepConst &K, const State<R> &S,
   // A. halo tile
   for (int h = tid; h < TL::NH; h += NT) {
     const int hx = h % TL::HX, hy = h / TL::HX;
-    prep_cell<R, DIM>(K, S, j0 + hx - 2, k0 + hy - TL::OY, sp, TL::NH, h);
+    prep_cell<R, DIM, QF1>(K, S, j0 + hx - 2, k0 + hy - TL::OY, sp, TL::NH, h);
   }
   __syncthreads();
 
@@ -1113,7 +1132,7 @@ __device__ __forceinline__ void step_tile(const StepConst &K, const State<R> &S,
         st[6] = r + TL::HX + fx + 1; st[7] = r + TL::HX + fx + 2;
       }
       int nt;
-      const bool nc = face_flux<R, DIM, 0, ITER>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
+      const bool nc = face_flux<R, DIM, QF1, 0, ITER>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
       if (ITER && (fx > 0 || j0 == 0)) {
         noconv += nc; traces += nt; ++evals; max_tr = max(max_tr, (unsigned)nt);
       }
@@ -1125,7 +1144,7 @@ __device__ __forceinline__ void step_tile(const StepConst &K, const State<R> &S,
       st[4] = (fy + 1) * H + x - 1; st[5] = (fy + 2) * H + x - 1;
       st[6] = (fy + 1) * H + x + 1; st[7] = (fy + 2) * H + x + 1;
       int nt;
-      const bool nc = face_flux<R, DIM, 1, ITER>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
+      const bool nc = face_flux<R, DIM, QF1, 1, ITER>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
       if (ITER && (fy > 0 || k0 == 0)) {
         noconv += nc; traces += nt; ++evals; max_tr = max(max_tr, (unsigned)nt);
       }
@@ -1140,7 +1159,7 @@ __device__ __forceinline__ void step_tile(const StepConst &K, const State<R> &S,
     const int cx = c % BX, cy = c / BX;
     const int j = j0 + cx, k = k0 + cy;
     if (j >= K.nx || k >= (DIM == 2 ? K.ny : 1)) continue;
-    update_cell<R, DIM, BX, BY>(K, S, O, fp, cx, cy, j, k, vmax, flags);
+    update_cell<R, DIM, QF1, BX, BY>(K, S, O, fp, cx, cy, j, k, vmax, flags);
   }
   double cfl = (double)vmax * K.lam;
   // warp reduction of the CFL number, flags and counts, one atomic per warp
@@ -1174,11 +1193,11 @@ __device__ __forceinline__ void step_tile(const StepConst &K, const State<R> &S,
 }
 
 // ---- the fused step kernel: one launch = one time step of one grid --------------
-template <typename R, int DIM, int BX, int BY, int NT, int MINB = 1, bool ITER = false>
+template <typename R, int DIM, int QF1, int BX, int BY, int NT, int MINB = 1, bool ITER = false>
 __global__ void __launch_bounds__(NT, MINB) step_kernel(const StepConst K, const State<R> S,
                                                         const State<R> O, Stats *stats) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  step_tile<R, DIM, BX, BY, NT, ITER>(K, S, O, stats, blockIdx.x * BX, DIM == 2 ? blockIdx.y * BY : 0,
+  step_tile<R, DIM, QF1, BX, BY, NT, ITER>(K, S, O, stats, blockIdx.x * BX, DIM == 2 ? blockIdx.y * BY : 0,
                                       smem_raw);
 }
 

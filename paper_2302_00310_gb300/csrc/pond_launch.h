@@ -52,3 +52,8 @@ std::vector<pond::Shape> pond_shapes_fp64(int D);
 std::vector<pond::Shape> pond_shapes_fp32(int D);
 pond::Shape pond_iter_shape_fp64(int D);
 pond::Shape pond_iter_shape_fp32(int D);
+// the D2Q25 f-lattice (pond_step_fp64_q5.cu / pond_step_fp32_q5.cu)
+std::vector<pond::Shape> pond_shapes_fp64_q5();
+std::vector<pond::Shape> pond_shapes_fp32_q5();
+pond::Shape pond_iter_shape_fp64_q5();
+pond::Shape pond_iter_shape_fp32_q5();

@@ -48,10 +48,10 @@ pond_status scratch_for_current_device(unsigned char **out) {
     }
     using T2 = pond::Tile<2, 8, 8>;
     using T1 = pond::Tile<1, 252, 1>;
-    if (cudaFuncSetAttribute(pond::step_kernel<double, 2, 8, 8, 160>,
+    if (cudaFuncSetAttribute(pond::step_kernel<double, 2, 4, 8, 8, 160>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)T2::smem_bytes<double>()) != cudaSuccess ||
-        cudaFuncSetAttribute(pond::step_kernel<double, 1, 252, 1, 256>,
+        cudaFuncSetAttribute(pond::step_kernel<double, 1, 4, 252, 1, 256>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)T1::smem_bytes<double>()) != cudaSuccess) {
       (void)cudaGetLastError();
@@ -186,11 +186,11 @@ extern "C" pond_status pond_step_noalloc(pond_lattice lat, const int64_t dims[2]
     const pond::State<double> &out = (i & 1) ? caller : other;
     if (D == 2) {
       const dim3 grid((unsigned)((nx + 7) / 8), (unsigned)((ny + 7) / 8));
-      pond::step_kernel<double, 2, 8, 8, 160>
+      pond::step_kernel<double, 2, 4, 8, 8, 160>
           <<<grid, 160, pond::Tile<2, 8, 8>::smem_bytes<double>(), st>>>(K, in, out, stats);
     } else {
       const dim3 grid((unsigned)((nx + 251) / 252), 1u);
-      pond::step_kernel<double, 1, 252, 1, 256>
+      pond::step_kernel<double, 1, 4, 252, 1, 256>
           <<<grid, 256, pond::Tile<1, 252, 1>::smem_bytes<double>(), st>>>(K, in, out, stats);
     }
     if (cudaGetLastError() != cudaSuccess) return POND_E_CUDA;

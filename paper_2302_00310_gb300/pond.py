@@ -15,7 +15,7 @@ import numpy as np
 
 from . import build as _build
 
-POND_D1Q4, POND_D2Q16 = 1, 2
+POND_D1Q4, POND_D2Q16, POND_D2Q25 = 1, 2, 3
 POND_OK, POND_E_INVAL, POND_E_NOMEM, POND_E_CUDA = 0, 1, 2, 3
 POND_E_NONPHYSICAL, POND_E_NOCONV, POND_E_CFL, POND_E_STATE = 4, 5, 6, 7
 POND_BC_PERIODIC, POND_BC_ZERO_GRADIENT, POND_BC_INFLOW = 0, 1, 2
@@ -364,7 +364,8 @@ class Sim:
 
         self.cfg = dict(cfg)
         self.D = int(cfg["D"])
-        self.lat = POND_D2Q16 if self.D == 2 else POND_D1Q4
+        self.q1 = int(cfg.get("qf", 4))  # f nodes per axis: 4, or 5 for D2Q25
+        self.lat = (POND_D2Q25 if self.q1 == 5 else POND_D2Q16) if self.D == 2 else POND_D1Q4
         self.nx = int(cfg["nx"])
         self.ny = int(cfg["ny"]) if self.D == 2 else 1
         self.params = params_from_config(cfg)
@@ -384,7 +385,7 @@ class Sim:
 
     @property
     def Qf(self):
-        return 16 if self.D == 2 else 4
+        return self.q1 * self.q1 if self.D == 2 else 4
 
     @property
     def Qg(self):

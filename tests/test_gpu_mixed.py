@@ -216,3 +216,18 @@ def test_state_round_trip_host_and_device(precision):
         assert _linf(a, b) <= tol
     for a, t in zip(host, dev):
         assert np.array_equal(a, t.cpu().numpy())
+
+
+@pytest.mark.parametrize("gk,bc", [(0, (0, 0, 0, 0)), (1, (1, 1, 3, 3))])
+def test_mixed_d2q25_few_steps_match_oracle(gk, bc):
+    """The D2Q25 f-lattice on the mixed path: moments within the step bound."""
+    prim = W.random_state_grid(2, 22, 19, seed=150 + gk, mach=1.0, T=(0.7, 1.4))
+    walls = ((0.0,) * 4, (0.0,) * 4, (0.0, 0.3, 0.0, 0.9), (0.0, -0.2, 0.0, 1.2))
+    cfg = W._base(2, 22, 19, qf=5, tau=5e-3, dx=1.0 / 22, prandtl=0.71, grad_k=gk, bc=bc,
+                  inflow=walls)
+    cfg["dt"] = W.dt_from_cfl(prim[1], prim[2], prim[3], cfg["dx"], 0.4, c_max=W.C_MAX_D1Q5)
+    om = _oracle_moments(cfg, prim, 2)
+    gm, fl = _gpu(cfg, prim, 2)
+    assert not fl[1] & pond.POND_FLAG_NONPHYSICAL
+    for i in range(4):
+        assert _linf(gm[i], om[i]) <= TOL_STEP, (i, _linf(gm[i], om[i]))

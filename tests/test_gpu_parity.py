@@ -453,3 +453,33 @@ def test_thermal_couette_at_the_papers_size(prandtl):
     assert np.max(np.abs(theta - exact)) / np.max(exact) < 0.015
     assert np.max(np.abs(m[1][:, 3] / w["u0"] - w["y"])) < 1e-3
     assert np.max(np.abs(m[3] - m[3][:, :1])) < 1e-12  # uniform along the walls
+
+
+Q5_CASES = [
+    # nx, ny, bc, prandtl, limiter, grad_k, appc, mach, steps, iterative
+    (19, 17, (0, 0, 0, 0), 1.0, 0, 0, 0, 0.8, 2, 0),
+    (21, 18, (1, 1, 1, 1), 0.71, 1, 0, 0, 1.0, 2, 0),
+    (17, 23, (2, 1, 1, 1), 1.0, 0, 1, 0, 0.6, 2, 0),
+    (20, 19, (0, 0, 1, 1), 0.71, 0, 0, 1, 1.0, 2, 0),
+    (18, 16, (0, 0, 3, 3), 0.71, 1, 0, 0, 0.7, 2, 0),
+    (16, 17, (0, 0, 0, 0), 1.0, 0, 0, 0, 0.5, 2, 1),
+]
+
+
+@pytest.mark.parametrize("case", range(len(Q5_CASES)))
+def test_d2q25_matches_oracle(case):
+    """The D2Q25 f-lattice (D1Q5 per axis, fourth-order invariance) with D2Q9
+    for g: the same state as the oracle, across boundaries, QE, limiters,
+    Grad-K of total order 4, Appendix C, walls and the iterated frame."""
+    nx, ny, bc, pr, lim, gk, appc, mach, steps, it = Q5_CASES[case]
+    rho, ux, uy, T = W.random_state_grid(2, nx, ny, seed=130 + case, mach=mach, T=(0.7, 1.4))
+    cfg = W._base(2, nx, ny, qf=5, tau=5e-3, dx=1.0 / nx, prandtl=pr, limiter=lim, grad_k=gk,
+                  flux_appc=appc, bc=bc, iterative=it, iter_tol=1e-10, iter_max=12,
+                  inflow=WALLS_2D if 3 in bc else ((1.1, 0.5, -0.2, 0.8),) * 4)
+    cfg["dt"] = W.dt_from_cfl(ux, uy, T, cfg["dx"], 0.4, c_max=W.C_MAX_D1Q5)
+    ost, got, flags = _run_both(cfg, rho, ux, uy, T, steps)
+    assert got[0].shape[0] == 25
+    _compare(ost, got, 2)
+    assert flags[1] & pond.POND_FLAG_NONPHYSICAL == 0
+    if it:
+        assert flags[4:] == (ost.report["face_evals"], ost.report["traces"], ost.report["max_traces"])

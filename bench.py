@@ -22,6 +22,7 @@ The other forms the metric compares are measured in the same run
     full 1000-step run;
   * ``riemann``: the four-quadrant Riemann problem at 1024^2 (QE Pr 0.71),
     mixed path and FP64, with the L1 error between them after 200 steps;
+  * ``d2q25``: the pulse on the D2Q25 f-lattice, FP64 and mixed;
   * ``batched``: 64 shock-bubble instances of seeded sizes 64^2-512^2 (about
     4.07M cells), Mach 1.5-5, Pr 0.71, advanced by the persistent batch
     kernel (autotuned), FP32-mixed and FP64, with the L1 error of the mixed
@@ -79,8 +80,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * CLOCK_MAX_GHZ / 1e3   # 128 FP32 FMA/clk/SM
 # dram__bytes_read.sum + dram__bytes_write.sum of one main-line step launch
 # (FP64 and mixed path), keyed by source digest (None once the sources change)
 TRAFFIC_BY_DIGEST = {
-    "790618b69e911cb1318aa3edb3a10029b792f89c949e01f9287a6c16cd22b159": {"fp64": 15673600,
-                                                                          "fp32": 9808384},
+    "58be7f51bbe1761cb6dda9da34a0c72b6e62695d41552bc026a33487294aeb43": {"fp64": 18140928,
+                                                                          "fp32": 9829632},
 }
 
 
@@ -330,6 +331,41 @@ def bench_riemann(torch, pond, W, steps=200):
     out["l1_rho_fp32_vs_fp64"] = _l1(mom["fp32_mixed"][0], mom["fp64"][0])
     out["linf_rho_fp32_vs_fp64"] = _linf(mom["fp32_mixed"][0], mom["fp64"][0])
     out["stated_l1_bound"] = 1e-3
+    return out
+
+
+def bench_d2q25(torch, pond, W, steps=100):
+    """The D2Q25 f-lattice on the 256^2 pulse (FP64 and mixed), against the
+    D2Q16 run of the same workload and dt: MLUPS of both, timed alike, and
+    the L1 density difference."""
+    w = W.pulse_2d(n=256, seed=0)
+    fields = (w["rho"], w["ux"], w["uy"], w["T"])
+    n = w["cfg"]["nx"] * w["cfg"]["ny"]
+    dt = W.dt_from_cfl(w["ux"], w["uy"], w["T"], w["cfg"]["dx"], 0.2, c_max=W.C_MAX_D1Q5)
+    out = {"workload": "256x256 pulse as the main line, D2Q25 f + D2Q9 g, dt from CFL 0.2 on D2Q25's "
+                       "nodes", "steps": steps, "unit": UNIT}
+    rho = {}
+    for qf in (5, 4):
+        for prec, name in ((pond.POND_FP64, "fp64"), (pond.POND_FP32_MIXED, "fp32_mixed")):
+            sim = pond.Sim(dict(w["cfg"], qf=qf, dt=dt, precision=prec))
+            sim.init(*fields)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(sim.stream):
+                pond.pond_step(sim.ctx, 3)
+                e0.record(sim.stream)
+                pond.pond_step(sim.ctx, steps)
+                e1.record(sim.stream)
+            sim.stream.synchronize()
+            ms = e0.elapsed_time(e1)
+            rho[(qf, name)] = sim.moments()[0]
+            rate = {"value": n * steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / steps, "tile": sim.info()[2]}
+            if qf == 5:
+                out[name] = rate
+            else:
+                out.setdefault("d2q16_same_dt", {})[name] = rate
+            sim.close()
+    out["l1_rho_d2q25_vs_d2q16_fp64"] = _l1(rho[(5, "fp64")], rho[(4, "fp64")])
+    out["l1_rho_fp32_vs_fp64_d2q25"] = _l1(rho[(5, "fp32_mixed")], rho[(5, "fp64")])
     return out
 
 
@@ -589,6 +625,7 @@ def run_gpu(args, dist, rank, ws):
         extras["mixed"] = bench_mixed(torch, pond, W, flush)
         extras["riemann"] = bench_riemann(torch, pond, W)
         extras["batched"] = bench_batched(torch, pond, W)
+        extras["d2q25"] = bench_d2q25(torch, pond, W)
         extras["serve"] = bench_serve(pond, serve_mod)
         if not args.no_studies:
             extras["serve_sweep"] = bench_serve_sweep(pond, serve_mod)

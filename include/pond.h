@@ -23,7 +23,7 @@
  *
  * Array layouts (all FP64 at the boundary, whatever the internal precision):
  *   fields   [ny][nx]            (x fastest; ny = 1 in 1D)
- *   f        [Qf][ny][nx]        Qf = 4 (1D) or 16 (2D)
+ *   f        [Qf][ny][nx]        Qf = 4 (1D), 16 (2D) or 25 (D2Q25)
  *   g        [Qg][ny][nx]        Qg = 3 (1D) or 9 (2D)
  * The state is the DUGKS variable phi~ of Eq. eq:variableTransform in each
  * cell's co-moving frame {u, T}; the frame itself is (ux, uy, T).
@@ -58,7 +58,8 @@ typedef struct pond_ctx pond_ctx;
 
 /* f-lattice of a context (the g-lattice follows: D1Q3 / D2Q9, as in every run of
  * Sec. V).  POND_D2Q25: five Gauss-Hermite nodes per axis (the roots of He_5,
- * Table I), frame-invariant moments to fourth order per axis (Sec. V.A); its
+ * Table I), frame-invariant moments to fourth order per axis (Sec. II.D.2;
+ * the fourth-order runs of the shock-structure problem, Sec. V.B.4); its
  * populations f[25][ny][nx] use node indices ix = i % 5, iy = i / 5, nodes
  * (-r2, -r1, 0, r1, r2), r1,2 = sqrt(5 -+ sqrt 10).  D2Q25 contexts run 8x8
  * tiles (tile 0 or 2) and are not batched (pond_batch_add: POND_E_INVAL). */

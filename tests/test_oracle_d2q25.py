@@ -1,6 +1,6 @@
-"""The D2Q25 f-lattice (Sec. V.A: five Gauss-Hermite nodes per axis, the roots
-of He_5, with frame-invariant moments to fourth order per axis) in the oracle,
-with D2Q9 for g as in every run of the paper.  Pins:
+"""The D2Q25 f-lattice (Table I: five Gauss-Hermite nodes per axis, the roots
+of He_5; Sec. II.D.2: frame-invariant moments to fourth order per axis) in the
+oracle, with D2Q9 for g as in every run of the paper.  Pins:
 
 * Table I's D1Q5 weights reproduce the Gaussian moments to degree 9;
 * the transformation equals Appendix B's matrix form M(lambda')^-1 M(lambda)

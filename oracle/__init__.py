@@ -69,6 +69,7 @@ def lib():
         _lib.orc_lattice.argtypes = [ctypes.c_int, P, P]
         _lib.orc_lattice.restype = ctypes.c_int
         _lib.orc_transform_pub.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, d, P, d, P]
+        _lib.orc_transform_x_pub.argtypes = [ctypes.c_int] * 5 + [P, P, d, P, d, P]
         _lib.orc_equilibrium_pub.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, d, P, d, P, d, P]
         _lib.orc_qe_half_pub.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, d, d, d, d, P, P, P, d]
         _lib.orc_macro_pub.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, d, P, P, P, d, P]
@@ -76,6 +77,8 @@ def lib():
         _lib.orc_init.argtypes = [ctypes.c_void_p] + [P] * 9
         _lib.orc_init.restype = ctypes.c_int
         _lib.orc_run.argtypes = [ctypes.c_void_p, P, P, P, P, P, ctypes.c_int64, ctypes.c_void_p]
+        _lib.orc_ms_measure_pub.argtypes = [ctypes.c_void_p] + [P] * 5
+        _lib.orc_ms_measure_pub.restype = ctypes.c_int
         _lib.orc_run.restype = ctypes.c_int
         _lib.orc_threads.restype = ctypes.c_int
         _lib.orc_set_threads.argtypes = [ctypes.c_int]
@@ -92,13 +95,15 @@ class _Params(ctypes.Structure):
         ("bc", ctypes.c_int * 4), ("inflow", (ctypes.c_double * 4) * 4),
         ("grad_k", ctypes.c_int), ("flux_appc", ctypes.c_int), ("limiter", ctypes.c_int),
         ("iterative", ctypes.c_int), ("iter_tol", ctypes.c_double), ("iter_max", ctypes.c_int),
+        ("ms", ctypes.c_int), ("ms_theta_u", ctypes.c_double), ("ms_theta_T", ctypes.c_double),
     ]
 
 
 class _Report(ctypes.Structure):
     _fields_ = [("flags", ctypes.c_uint32), ("noconv_faces", ctypes.c_int64),
                 ("max_cfl", ctypes.c_double), ("face_evals", ctypes.c_int64),
-                ("traces", ctypes.c_int64), ("max_traces", ctypes.c_int32)]
+                ("traces", ctypes.c_int64), ("max_traces", ctypes.c_int32),
+                ("ms_high", ctypes.c_int64)]
 
 
 def _ptr(a: np.ndarray):
@@ -127,6 +132,17 @@ def transform(q, D, fin, u, T, up, Tp, grad_k=0):
     out = np.zeros(q**D)
     lib().orc_transform_pub(q, D, int(grad_k), _ptr(fin), _ptr(_vec(u)), float(T),
                             _ptr(_vec(up)), float(Tp), _ptr(out))
+    return out
+
+
+def transform_x(qs, qd, K, D, fin, u, T, up, Tp, grad_k=0):
+    """Frame transformation from the qs-node lattice in (u, T) to the qd-node
+    lattice in (up, Tp), keeping coefficients of order <= K per axis
+    (multiscale lifting or projection)."""
+    fin = np.ascontiguousarray(fin, dtype=np.float64)
+    out = np.zeros(qd**D)
+    lib().orc_transform_x_pub(qs, qd, int(K), D, int(grad_k), _ptr(fin), _ptr(_vec(u)), float(T),
+                              _ptr(_vec(up)), float(Tp), _ptr(out))
     return out
 
 
@@ -178,6 +194,9 @@ class Config:
     iterative: int = 0
     iter_tol: float = 1e-12
     iter_max: int = 10
+    ms: int = 0
+    ms_theta_u: float = 0.0
+    ms_theta_T: float = 0.0
 
     @classmethod
     def from_dict(cls, d: dict) -> "Config":
@@ -196,6 +215,7 @@ class Config:
                 p.inflow[s][m] = float(self.inflow[s][m])
         p.grad_k, p.flux_appc, p.limiter = int(self.grad_k), int(self.flux_appc), int(self.limiter)
         p.iterative, p.iter_tol, p.iter_max = int(self.iterative), float(self.iter_tol), int(self.iter_max)
+        p.ms, p.ms_theta_u, p.ms_theta_T = int(self.ms), float(self.ms_theta_u), float(self.ms_theta_T)
         return p
 
 
@@ -242,8 +262,24 @@ def run(cfg: Config, state: State, nsteps: int) -> State:
         raise ValueError("oracle: invalid configuration (rc=%d)" % rc)
     st.report = {"flags": int(rep.flags), "noconv_faces": int(rep.noconv_faces),
                  "max_cfl": float(rep.max_cfl), "face_evals": int(rep.face_evals),
-                 "traces": int(rep.traces), "max_traces": int(rep.max_traces)}
+                 "traces": int(rep.traces), "max_traces": int(rep.max_traces),
+                 "ms_high": int(rep.ms_high)}
     return st
+
+
+def ms_measure(cfg: Config, ux, uy, T):
+    """Multiscale switching measures (s_u, s_T), each [ny, nx], of the fields
+    under the run's boundary rules (a cell takes the high lattice where
+    s_u > ms_theta_u or s_T > ms_theta_T)."""
+    ny = cfg.ny if cfg.D == 2 else 1
+    shp = (ny, cfg.nx)
+    arr = [np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float64), shp))
+           for a in (ux, uy, T)]
+    su, sT = np.zeros(shp), np.zeros(shp)
+    rc = lib().orc_ms_measure_pub(ctypes.byref(cfg._c()), *[_ptr(a) for a in arr], _ptr(su), _ptr(sT))
+    if rc != 0:
+        raise ValueError("oracle: invalid configuration")
+    return su, sT
 
 
 def moments(cfg: Config, st: State):

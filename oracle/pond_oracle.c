@@ -68,6 +68,12 @@ typedef struct {
   int iterative;      /* 0: averaged face frame, 1: iterated face frame */
   double iter_tol;
   int iter_max;
+  /* multiscale f-lattice (Sec. II.E, Sec. IV.C): each step every cell takes
+   * D1Q4 / D2Q16 where a velocity or temperature jump across it exceeds its
+   * threshold, else D1Q3 / D2Q9 */
+  int ms;
+  double ms_theta_u;  /* on max |u_e(x + dx e_d) - u_e(x - dx e_d)| / (2 sqrt T) */
+  double ms_theta_T;  /* on max |T(x + dx e_d) - T(x - dx e_d)| / (2 T) */
 } orc_params;
 
 typedef struct {
@@ -80,6 +86,7 @@ typedef struct {
   int64_t face_evals;
   int64_t traces;
   int32_t max_traces;
+  int64_t ms_high;  /* multiscale: cell updates made on the high-order lattice */
 } orc_report;
 
 /* ------------------------------------------------------------------ */
@@ -145,37 +152,52 @@ static double orc_fact(int n) { double r = 1; for (int k = 2; k <= n; ++k) r *= 
  * (Eq. GradsProjection written per axis).  grad_k = 0 keeps every a, b <= K
  * (tensor product of 1D transformations); grad_k = 1 keeps a + b <= K only
  * (the Grad projection of order K used by the paper for D2Q16, Sec. V.A). */
-static void orc_transform(const orc_lat1 *L, int D, int grad_k, const double *fin,
-                          const double u[2], double T, const double up[2], double Tp,
-                          double *fout) {
-  const int Q = orc_Q(L, D), K = L->K, Kb = (D == 2) ? K : 0;
+/* orc_transform_x: the same map between two lattices (multiscale, Sec.
+ * II.E): the coefficients of order <= K per axis are measured on the source
+ * lattice Ls and the Grad expansion is synthesised on the destination lattice
+ * Ld, K being Ld's invariant order.  Onto a lattice of lower order it is the
+ * projection (the higher coefficients are dropped).  Onto one of higher order
+ * it is the lifting with the coefficients Ls does not carry set to zero in the
+ * source frame (see orc_ms_switch for why that is the equilibrium completion
+ * of Sec. II.E): q-node Gauss-Hermite quadrature is exact to degree 2q - 1, so
+ * the source lattice measures the higher moments of its own Grad expansion
+ * exactly.  In the same frame the lifting may take K = Ls's order. */
+static void orc_transform_x(const orc_lat1 *Ls, const orc_lat1 *Ld, int K, int D, int grad_k,
+                            const double *fin, const double u[2], double T, const double up[2],
+                            double Tp, double *fout) {
+  const int Qs = orc_Q(Ls, D), Qd = orc_Q(Ld, D), Kb = (D == 2) ? K : 0;
   const double sT = sqrt(T), sTp = sqrt(Tp);
   double alpha[ORC_MAXQ1][ORC_MAXQ1];
   for (int a = 0; a <= K; ++a)
     for (int b = 0; b <= Kb; ++b) {
       double s = 0.0;
-      for (int j = 0; j < Q; ++j) {
-        double xix = (sT * orc_cx(L, D, j) + u[0] - up[0]) / sTp;
+      for (int j = 0; j < Qs; ++j) {
+        double xix = (sT * orc_cx(Ls, D, j) + u[0] - up[0]) / sTp;
         double h = orc_He(a, xix);
         if (D == 2) {
-          double xiy = (sT * orc_cy(L, D, j) + u[1] - up[1]) / sTp;
+          double xiy = (sT * orc_cy(Ls, D, j) + u[1] - up[1]) / sTp;
           h *= orc_He(b, xiy);
         }
         s += fin[j] * h;
       }
       alpha[a][b] = s;
     }
-  for (int i = 0; i < Q; ++i) {
+  for (int i = 0; i < Qd; ++i) {
     double s = 0.0;
     for (int a = 0; a <= K; ++a)
       for (int b = 0; b <= Kb; ++b) {
         if (grad_k && a + b > K) continue;
-        double h = orc_He(a, orc_cx(L, D, i));
-        if (D == 2) h *= orc_He(b, orc_cy(L, D, i));
+        double h = orc_He(a, orc_cx(Ld, D, i));
+        if (D == 2) h *= orc_He(b, orc_cy(Ld, D, i));
         s += alpha[a][b] * h / (orc_fact(a) * orc_fact(b));
       }
-    fout[i] = orc_W(L, D, i) * s;
+    fout[i] = orc_W(Ld, D, i) * s;
   }
+}
+static void orc_transform(const orc_lat1 *L, int D, int grad_k, const double *fin,
+                          const double u[2], double T, const double up[2], double Tp,
+                          double *fout) {
+  orc_transform_x(L, L, L->K, D, grad_k, fin, u, T, up, Tp, fout);
 }
 
 /* Equilibrium of a gas with (rho, u, T) written in a frame lambda' that need
@@ -274,6 +296,9 @@ static void orc_qe_half(const orc_lat1 *Lf, const orc_lat1 *Lg, int D, double Cv
 typedef struct {
   const orc_params *p;
   orc_lat1 Lf, Lg;
+  orc_lat1 Ll; /* multiscale: the low-order f-lattice (D1Q3) */
+  int *lat;    /* multiscale: 1 where a cell takes Lf, 0 where it takes Ll */
+  int *xlat, *ylat; /* multiscale: lattice of each face (the higher of its cells') */
   int D, nx, ny, nxp, nyp, gy, Qf, Qg;
   double Cv;
   /* padded cell arrays, population-major: f[i * ncp + cell] */
@@ -477,9 +502,11 @@ typedef struct {
 
 /* The stencil's phi_bar^+ moved into the face frame {uF, TF} and the limited
  * half-step trace x' = x_b - v dt/2 of every population to the face (Eq.
- * eq:InterfacePop); the upwind cell is the left one when v_n > 0. */
-static void orc_face_trace(const orc_grid *G, const orc_stencil *S, const double uF[2],
-                           double TF, double *fb, double *gb) {
+ * eq:InterfacePop); the upwind cell is the left one when v_n > 0.  LF is the
+ * face's f-lattice (G->Lf, or the low-order one of a multiscale face, onto
+ * which the stencil's populations are projected). */
+static void orc_face_trace(const orc_grid *G, const orc_stencil *S, const orc_lat1 *LF,
+                           const double uF[2], double TF, double *fb, double *gb) {
   const orc_params *p = G->p;
   const int D = G->D, ncp = orc_ncp(G), dir = S->dir;
   const double dt = p->dt, dx = p->dx;
@@ -489,7 +516,7 @@ static void orc_face_trace(const orc_grid *G, const orc_stencil *S, const double
     double fin[ORC_MAXQ], gin[ORC_MAXQ], uc[2] = {G->ux[c], G->uy[c]};
     for (int i = 0; i < G->Qf; ++i) fin[i] = G->fp[i * ncp + c];
     for (int i = 0; i < G->Qg; ++i) gin[i] = G->gp[i * ncp + c];
-    orc_transform(&G->Lf, D, p->grad_k, fin, uc, G->T[c], uF, TF, tn_f[n]);
+    orc_transform_x(&G->Lf, LF, LF->K, D, p->grad_k, fin, uc, G->T[c], uF, TF, tn_f[n]);
     orc_transform(&G->Lg, D, p->grad_k, gin, uc, G->T[c], uF, TF, tn_g[n]);
   }
   if (D == 2)
@@ -499,11 +526,11 @@ static void orc_face_trace(const orc_grid *G, const orc_stencil *S, const double
         double fin[ORC_MAXQ], gin[ORC_MAXQ], uc[2] = {G->ux[c], G->uy[c]};
         for (int i = 0; i < G->Qf; ++i) fin[i] = G->fp[i * ncp + c];
         for (int i = 0; i < G->Qg; ++i) gin[i] = G->gp[i * ncp + c];
-        orc_transform(&G->Lf, D, p->grad_k, fin, uc, G->T[c], uF, TF, tt_f[t][m]);
+        orc_transform_x(&G->Lf, LF, LF->K, D, p->grad_k, fin, uc, G->T[c], uF, TF, tt_f[t][m]);
         orc_transform(&G->Lg, D, p->grad_k, gin, uc, G->T[c], uF, TF, tt_g[t][m]);
       }
   for (int pop = 0; pop < 2; ++pop) {
-    const orc_lat1 *L = pop == 0 ? &G->Lf : &G->Lg;
+    const orc_lat1 *L = pop == 0 ? LF : &G->Lg;
     double *out = pop == 0 ? fb : gb;
     for (int i = 0; i < orc_Q(L, D); ++i) {
       double vx = sqrt(TF) * orc_cx(L, D, i) + uF[0];
@@ -539,9 +566,10 @@ static void orc_face_trace(const orc_grid *G, const orc_stencil *S, const double
 /* dir = 0: x-face between cells (j,k) and (j+1,k); dir = 1: y-face between
  * (j,k) and (j,k+1).  lam is set to the face frame {u_x, u_y, T} actually
  * used; returns 1 if the iterated frame did not converge; *ntrace receives the
- * number of interface traces made. */
+ * number of interface traces made; *lat the face's f-lattice (multiscale: 1
+ * for G->Lf, 0 for the low-order one; phi_f then holds its populations). */
 static int orc_face(orc_grid *G, int dir, int j, int k, double *phi_f, double *phi_g,
-                    double lam[3], int *ntrace) {
+                    double lam[3], int *ntrace, int *lat) {
   const orc_params *p = G->p;
   const int D = G->D;
   const double dt = p->dt, tau = p->tau, h = 0.5 * dt;
@@ -556,6 +584,11 @@ static int orc_face(orc_grid *G, int dir, int j, int k, double *phi_f, double *p
         S.ct[t][m] = dir == 0 ? orc_pidx(G, j + t, k - 1 + 2 * m) : orc_pidx(G, j - 1 + 2 * m, k + t);
     }
   const int cL = S.cn[1], cR = S.cn[2];
+  /* multiscale: the face takes the higher lattice of its two cells, so that a
+   * face flux only ever moves onto a lattice of equal or lower order */
+  *lat = p->ms ? (G->lat[cL] | G->lat[cR]) : 1;
+  const orc_lat1 *LF = *lat ? &G->Lf : &G->Ll;
+  const int QF = orc_Q(LF, D);
   /* face frame, Eq. eq::AvgFrame */
   double uF[2] = {0.5 * (G->ux[cL] + G->ux[cR]), 0.5 * (G->uy[cL] + G->uy[cR])};
   double TF = 0.5 * (G->T[cL] + G->T[cR]);
@@ -573,16 +606,16 @@ static int orc_face(orc_grid *G, int dir, int j, int k, double *phi_f, double *p
   double uP[2] = {uF[0], uF[1]}, TP = TF;
   *ntrace = 0;
   for (int it = 0; it < nit; ++it) {
-    orc_face_trace(G, &S, uF, TF, fb, gb);
+    orc_face_trace(G, &S, LF, uF, TF, fb, gb);
     ++*ntrace;
     /* interface macroscopic fields (rho, rho u, C_v rho T) in the face frame */
-    int ok = orc_macro(&G->Lf, &G->Lg, D, G->Cv, fb, gb, uF, TF, &rho, ub, &Tb);
+    int ok = orc_macro(LF, &G->Lg, D, G->Cv, fb, gb, uF, TF, &rho, ub, &Tb);
     if (!ok) {
       if (p->iterative && it > 0) {
         uF[0] = uP[0]; uF[1] = uP[1]; TF = TP;
-        orc_face_trace(G, &S, uF, TF, fb, gb);
+        orc_face_trace(G, &S, LF, uF, TF, fb, gb);
         ++*ntrace;
-        orc_macro(&G->Lf, &G->Lg, D, G->Cv, fb, gb, uF, TF, &rho, ub, &Tb);
+        orc_macro(LF, &G->Lg, D, G->Cv, fb, gb, uF, TF, &rho, ub, &Tb);
       }
       break;
     }
@@ -602,19 +635,81 @@ static int orc_face(orc_grid *G, int dir, int j, int k, double *phi_f, double *p
    * equilibrium is rho W (Eqs. feqPond, geqPond). */
   double feq[ORC_MAXQ], geq[ORC_MAXQ];
   if (p->iterative && converged) {
-    for (int i = 0; i < G->Qf; ++i) feq[i] = rho * orc_W(&G->Lf, D, i);
+    for (int i = 0; i < QF; ++i) feq[i] = rho * orc_W(LF, D, i);
     for (int i = 0; i < G->Qg; ++i) geq[i] = (G->Cv - 0.5 * D) * Tb * rho * orc_W(&G->Lg, D, i);
   } else {
     double gscale = (G->Cv - 0.5 * D) * Tb;
-    orc_equilibrium(&G->Lf, D, p->grad_k, rho, ub, Tb, uF, TF, feq);
+    orc_equilibrium(LF, D, p->grad_k, rho, ub, Tb, uF, TF, feq);
     orc_equilibrium(&G->Lg, D, p->grad_k, rho * gscale, ub, Tb, uF, TF, geq);
   }
   /* invert Eq. eq:FluxTransf: phi_bar = phi - (h/2) (phi^eq - phi)/tau, h = dt/2 */
   const double r = h / (2.0 * tau);
-  for (int i = 0; i < G->Qf; ++i) phi_f[i] = (fb[i] + r * feq[i]) / (1.0 + r);
+  for (int i = 0; i < QF; ++i) phi_f[i] = (fb[i] + r * feq[i]) / (1.0 + r);
   for (int i = 0; i < G->Qg; ++i) phi_g[i] = (gb[i] + r * geq[i]) / (1.0 + r);
   lam[0] = uF[0]; lam[1] = uF[1]; lam[2] = TF;
   return noconv;
+}
+
+/* ------------------------------------------------------------------ */
+/* Multiscale lattice switching (Sec. II.E, Sec. IV.C).                */
+/* ------------------------------------------------------------------ */
+/* Jumps of u and T across interior cell (j, k), from the padded fields
+ * (ghosts filled): s_u = max_{d,e} |u_e(+d) - u_e(-d)| / (2 sqrt T),
+ * s_T = max_d |T(+d) - T(-d)| / (2 T), centred over the two neighbours. */
+static void orc_ms_measure(const orc_grid *G, int j, int k, double *su, double *sT) {
+  const int c = orc_pidx(G, j, k);
+  double gu = 0.0, gT = 0.0;
+  for (int d = 0; d < G->D; ++d) {
+    const int cp = orc_pidx(G, j + (d == 0), k + (d == 1));
+    const int cm = orc_pidx(G, j - (d == 0), k - (d == 1));
+    gu = fmax(gu, fmax(fabs(G->ux[cp] - G->ux[cm]), fabs(G->uy[cp] - G->uy[cm])));
+    gT = fmax(gT, fabs(G->T[cp] - G->T[cm]));
+  }
+  *su = 0.5 * gu / sqrt(G->T[c]);
+  *sT = 0.5 * gT / G->T[c];
+}
+
+/* The switch at the start of a step.  Every interior cell takes the high
+ * lattice where s_u > theta_u or s_T > theta_T, else the low one.  A cell's
+ * populations are always stored on the high lattice: a low cell's as the
+ * high-lattice populations with its own Hermite coefficients of order <= 2
+ * per axis (its frame being co-moving) and none above.  That storage is the
+ * lifting of Sec. II.E: the moments the low lattice lacks are set to their
+ * equilibrium values, and in the cell's co-moving frame every Hermite
+ * coefficient of order 3 along an axis of a Maxwellian centred on the cell's
+ * velocity is zero (odd central moments of a Gaussian).  A cell that turns
+ * low is projected: its coefficients of order 3 are dropped. */
+static void orc_ms_switch(orc_grid *G) {
+  const orc_params *p = G->p;
+  const int ncp = orc_ncp(G), D = G->D;
+  orc_fill_ghosts(G);
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int k = 0; k < G->ny; ++k)
+    for (int j = 0; j < G->nx; ++j) {
+      const int c = orc_pidx(G, j, k);
+      double su, sT;
+      orc_ms_measure(G, j, k, &su, &sT);
+      G->lat[c] = (su > p->ms_theta_u || sT > p->ms_theta_T) ? 1 : 0;
+      if (G->lat[c]) continue;
+      double f[ORC_MAXQ], fo[ORC_MAXQ], u[2] = {G->ux[c], G->uy[c]};
+      for (int i = 0; i < G->Qf; ++i) f[i] = G->f[i * ncp + c];
+      orc_transform_x(&G->Lf, &G->Lf, G->Ll.K, D, p->grad_k, f, u, G->T[c], u, G->T[c], fo);
+      for (int i = 0; i < G->Qf; ++i) G->f[i * ncp + c] = fo[i];
+    }
+}
+
+/* Lattices of the ghost cells: that of their source cell; an inflow ghost
+ * (a co-moving equilibrium, the same on both lattices) the low one. */
+static void orc_ms_ghost_lattices(orc_grid *G) {
+  const orc_params *p = G->p;
+  const int k0 = (G->D == 2) ? -2 : 0, k1 = (G->D == 2) ? G->ny + 2 : 1;
+  for (int k = k0; k < k1; ++k)
+    for (int j = -2; j < G->nx + 2; ++j) {
+      if (j >= 0 && j < G->nx && k >= 0 && k < G->ny) continue;
+      int sj = 0, sk = 0;
+      const int side = orc_ghost_map(p, j, k, &sj, &sk);
+      G->lat[orc_pidx(G, j, k)] = side >= 0 ? 0 : G->lat[orc_pidx(G, sj, sk)];
+    }
 }
 
 /* ------------------------------------------------------------------ */
@@ -627,8 +722,11 @@ static int orc_step_once(orc_grid *G, orc_report *rep) {
   const double tau2 = p->tau / p->prandtl;
   const int qe = p->prandtl != 1.0;
   uint32_t flags = 0;
-  int64_t noconv = 0, traces = 0, evals = 0;
+  int64_t noconv = 0, traces = 0, evals = 0, ms_high = 0;
   int max_tr = 0;
+
+  /* 0. multiscale: each cell's lattice for this step, from its current fields */
+  if (p->ms) orc_ms_switch(G);
 
   /* 1. quasi-equilibrium half relaxation in the cell centres */
   if (qe) {
@@ -645,6 +743,7 @@ static int orc_step_once(orc_grid *G, orc_report *rep) {
       }
   }
   orc_fill_ghosts(G);
+  if (p->ms) orc_ms_ghost_lattices(G);
 
   /* 2. phi_bar^+ in every cell (ghosts included), Eq. eq:Fbarplus, from the
    * stored variable of Eq. eq:variableTransform; the cell is in its
@@ -675,7 +774,7 @@ static int orc_step_once(orc_grid *G, orc_report *rep) {
     for (int j = -1; j < G->nx; ++j) {
       int fi = k * (G->nx + 1) + (j + 1), nt = 0;
       noconv += orc_face(G, 0, j, k, G->xff + (size_t)fi * Qf, G->xfg + (size_t)fi * Qg,
-                         G->xlam + 3 * (size_t)fi, &nt);
+                         G->xlam + 3 * (size_t)fi, &nt, G->xlat + fi);
       traces += nt;
       evals += 1;
       if (nt > max_tr) max_tr = nt;
@@ -687,7 +786,7 @@ static int orc_step_once(orc_grid *G, orc_report *rep) {
       for (int j = 0; j < G->nx; ++j) {
         int fi = (k + 1) * G->nx + j, nt = 0;
         noconv += orc_face(G, 1, j, k, G->yff + (size_t)fi * Qf, G->yfg + (size_t)fi * Qg,
-                           G->ylam + 3 * (size_t)fi, &nt);
+                           G->ylam + 3 * (size_t)fi, &nt, G->ylat + fi);
         traces += nt;
         evals += 1;
         if (nt > max_tr) max_tr = nt;
@@ -698,34 +797,55 @@ static int orc_step_once(orc_grid *G, orc_report *rep) {
    * (Eqs. eq:FinalUpdateDUGKS, eq:FinalUpdateDUGKS_g), new co-moving frame */
   const double a1 = (2.0 * tau - dt) / (2.0 * tau + dt), a2 = 2.0 * dt / (2.0 * tau + dt);
   double maxcfl = 0.0;
-#pragma omp parallel for collapse(2) schedule(static) reduction(| : flags) reduction(max : maxcfl)
+#pragma omp parallel for collapse(2) schedule(static) reduction(| : flags) reduction(max : maxcfl) \
+    reduction(+ : ms_high)
   for (int k = 0; k < G->ny; ++k)
     for (int j = 0; j < G->nx; ++j) {
       int c = orc_pidx(G, j, k);
       double uc[2] = {G->ux[c], G->uy[c]}, Tc = G->T[c], sT = sqrt(Tc);
       double Ff[ORC_MAXQ] = {0}, Fg[ORC_MAXQ] = {0};
+      /* the cell's f-lattice and its populations on it (a multiscale low cell:
+       * from its high-lattice storage, an exact change of nodes) */
+      const int low = p->ms && !G->lat[c];
+      const orc_lat1 *Lc = low ? &G->Ll : &G->Lf;
+      const int Qc = orc_Q(Lc, D);
+      double fc[ORC_MAXQ];
+      if (low) {
+        double fs[ORC_MAXQ];
+        for (int i = 0; i < Qf; ++i) fs[i] = G->f[i * ncp + c];
+        orc_transform_x(&G->Lf, Lc, Lc->K, D, p->grad_k, fs, uc, Tc, uc, Tc, fc);
+      } else {
+        for (int i = 0; i < Qf; ++i) fc[i] = G->f[i * ncp + c];
+      }
+      ms_high += p->ms && !low;
       /* faces: (normal direction, face index, outward sign) */
       int nf = D == 2 ? 4 : 2;
       for (int face = 0; face < nf; ++face) {
         int dir = face / 2, sgn = (face % 2) ? +1 : -1;
         const double *pf, *pg, *lam;
+        int flat;
         if (dir == 0) {
           int fi = k * (G->nx + 1) + (sgn > 0 ? j + 1 : j);
           pf = G->xff + (size_t)fi * Qf; pg = G->xfg + (size_t)fi * Qg; lam = G->xlam + 3 * (size_t)fi;
+          flat = G->xlat[fi];
         } else {
           int fi = (sgn > 0 ? k + 1 : k) * G->nx + j;
           pf = G->yff + (size_t)fi * Qf; pg = G->yfg + (size_t)fi * Qg; lam = G->ylam + 3 * (size_t)fi;
+          flat = G->ylat[fi];
         }
         double uF[2] = {lam[0], lam[1]}, TF = lam[2];
         for (int pop = 0; pop < 2; ++pop) {
-          const orc_lat1 *L = pop == 0 ? &G->Lf : &G->Lg;
+          /* LS: the face's lattice, L: the cell's (multiscale: a high face
+           * flux entering a low cell is projected onto it) */
+          const orc_lat1 *LS = pop == 0 ? ((p->ms && !flat) ? &G->Ll : &G->Lf) : &G->Lg;
+          const orc_lat1 *L = pop == 0 ? Lc : &G->Lg;
           const double *src = pop == 0 ? pf : pg;
           double *acc = pop == 0 ? Ff : Fg;
-          const int Q = orc_Q(L, D);
+          const int Q = orc_Q(L, D), QS = orc_Q(LS, D);
           double tr[ORC_MAXQ];
           if (!p->flux_appc) {
             /* Eq. fluxEq: (v_i^lambda . n) G_{lambda_F}^{lambda} phi */
-            orc_transform(L, D, p->grad_k, src, uF, TF, uc, Tc, tr);
+            orc_transform_x(LS, L, L->K, D, p->grad_k, src, uF, TF, uc, Tc, tr);
             for (int i = 0; i < Q; ++i) {
               double vn = dir == 0 ? sT * orc_cx(L, D, i) + uc[0] : sT * orc_cy(L, D, i) + uc[1];
               acc[i] += sgn * vn * tr[i];
@@ -733,43 +853,53 @@ static int orc_step_once(orc_grid *G, orc_report *rep) {
           } else {
             /* Appendix C: G_{lambda_F}^{lambda} (v^{lambda_F} . n phi) */
             double fl[ORC_MAXQ];
-            for (int i = 0; i < Q; ++i) {
-              double vn = dir == 0 ? sqrt(TF) * orc_cx(L, D, i) + uF[0]
-                                   : sqrt(TF) * orc_cy(L, D, i) + uF[1];
+            for (int i = 0; i < QS; ++i) {
+              double vn = dir == 0 ? sqrt(TF) * orc_cx(LS, D, i) + uF[0]
+                                   : sqrt(TF) * orc_cy(LS, D, i) + uF[1];
               fl[i] = vn * src[i];
             }
-            orc_transform(L, D, p->grad_k, fl, uF, TF, uc, Tc, tr);
+            orc_transform_x(LS, L, L->K, D, p->grad_k, fl, uF, TF, uc, Tc, tr);
             for (int i = 0; i < Q; ++i) acc[i] += sgn * tr[i];
           }
         }
       }
       double rho = 0;
-      for (int i = 0; i < Qf; ++i) rho += G->f[i * ncp + c];
+      for (int i = 0; i < Qc; ++i) rho += fc[i];
       double f[ORC_MAXQ], g[ORC_MAXQ];
       /* V_j = dx^D, face area dx^(D-1): dt/V * area = dt/dx */
-      for (int i = 0; i < Qf; ++i)
-        f[i] = a1 * G->f[i * ncp + c] + a2 * rho * orc_W(&G->Lf, D, i) - dt / dx * Ff[i];
+      for (int i = 0; i < Qc; ++i) f[i] = a1 * fc[i] + a2 * rho * orc_W(Lc, D, i) - dt / dx * Ff[i];
       for (int i = 0; i < Qg; ++i)
         g[i] = a1 * G->g[i * ncp + c] + a2 * (G->Cv - 0.5 * D) * Tc * rho * orc_W(&G->Lg, D, i) -
                dt / dx * Fg[i];
       /* new moments and the new co-moving frame */
       double rn, un[2], Tn;
-      if (!orc_macro(&G->Lf, &G->Lg, D, G->Cv, f, g, uc, Tc, &rn, un, &Tn)) {
+      if (!orc_macro(Lc, &G->Lg, D, G->Cv, f, g, uc, Tc, &rn, un, &Tn)) {
         flags |= ORC_FLAG_NONPHYSICAL;
-        for (int i = 0; i < Qf; ++i) G->f[i * ncp + c] = f[i];
+        if (low) {
+          double fs[ORC_MAXQ];
+          orc_transform_x(Lc, &G->Lf, Lc->K, D, p->grad_k, f, uc, Tc, uc, Tc, fs);
+          for (int i = 0; i < Qf; ++i) G->f[i * ncp + c] = fs[i];
+        } else {
+          for (int i = 0; i < Qf; ++i) G->f[i * ncp + c] = f[i];
+        }
         for (int i = 0; i < Qg; ++i) G->g[i * ncp + c] = g[i];
         continue;
       }
       double fn[ORC_MAXQ], gn[ORC_MAXQ];
-      orc_transform(&G->Lf, D, p->grad_k, f, uc, Tc, un, Tn, fn);
+      orc_transform(Lc, D, p->grad_k, f, uc, Tc, un, Tn, fn);
       orc_transform(&G->Lg, D, p->grad_k, g, uc, Tc, un, Tn, gn);
       /* 6. second quasi-equilibrium half relaxation, in the new frame */
       if (qe) orc_qe_half(&G->Lf, &G->Lg, D, G->Cv, dt, tau, tau2, fn, gn, un, Tn);
+      if (low) { /* back to the high-lattice storage (lifting, in the new frame) */
+        double fs[ORC_MAXQ];
+        orc_transform_x(Lc, &G->Lf, Lc->K, D, p->grad_k, fn, un, Tn, un, Tn, fs);
+        for (int i = 0; i < Qf; ++i) fn[i] = fs[i];
+      }
       for (int i = 0; i < Qf; ++i) G->f[i * ncp + c] = fn[i];
       for (int i = 0; i < Qg; ++i) G->g[i * ncp + c] = gn[i];
       G->ux[c] = un[0]; G->uy[c] = D == 2 ? un[1] : 0.0; G->T[c] = Tn;
       /* CFL = max |v_i alpha| dt/dx (Sec. V) */
-      double cmax = G->Lf.c[G->Lf.q - 1];
+      double cmax = Lc->c[Lc->q - 1];
       double vmax = fmax(fabs(un[0]), fabs(D == 2 ? un[1] : 0.0)) + sqrt(Tn) * cmax;
       double cfl = vmax * dt / dx;
       if (cfl > maxcfl) maxcfl = cfl;
@@ -785,6 +915,7 @@ static int orc_step_once(orc_grid *G, orc_report *rep) {
     if (max_tr > rep->max_traces) rep->max_traces = max_tr;
   }
   if (maxcfl > rep->max_cfl) rep->max_cfl = maxcfl;
+  rep->ms_high += ms_high;
   return 0;
 }
 
@@ -794,6 +925,7 @@ static int orc_grid_alloc(orc_grid *G, const orc_params *p) {
   G->D = p->D;
   orc_lat1_make(&G->Lf, p->qf);
   orc_lat1_make(&G->Lg, p->qg);
+  orc_lat1_make(&G->Ll, 3);
   G->nx = p->nx; G->ny = p->D == 2 ? p->ny : 1;
   G->nxp = G->nx + 4; G->nyp = p->D == 2 ? G->ny + 4 : 1; G->gy = p->D == 2 ? 2 : 0;
   G->Qf = orc_Q(&G->Lf, G->D); G->Qg = orc_Q(&G->Lg, G->D);
@@ -808,13 +940,16 @@ static int orc_grid_alloc(orc_grid *G, const orc_params *p) {
   G->xlam = calloc(nfx * 3, sizeof(double));
   G->yff = calloc(nfy * G->Qf, sizeof(double)); G->yfg = calloc(nfy * G->Qg, sizeof(double));
   G->ylam = calloc(nfy * 3, sizeof(double));
+  G->lat = calloc(ncp, sizeof(int));
+  G->xlat = calloc(nfx, sizeof(int)); G->ylat = calloc(nfy, sizeof(int));
   return G->f && G->g && G->fp && G->gp && G->ux && G->uy && G->T && G->xff && G->xfg &&
-         G->xlam && G->yff && G->yfg && G->ylam;
+         G->xlam && G->yff && G->yfg && G->ylam && G->lat && G->xlat && G->ylat;
 }
 
 static void orc_grid_free(orc_grid *G) {
   free(G->f); free(G->g); free(G->fp); free(G->gp); free(G->ux); free(G->uy); free(G->T);
   free(G->xff); free(G->xfg); free(G->xlam); free(G->yff); free(G->yfg); free(G->ylam);
+  free(G->lat); free(G->xlat); free(G->ylat);
 }
 
 static int orc_check(const orc_params *p) {
@@ -832,6 +967,13 @@ static int orc_check(const orc_params *p) {
     if (p->D == 2 && (s < 2 || p->ny < 3 || p->bc[0] == ORC_BC_INFLOW || p->bc[1] == ORC_BC_INFLOW))
       return 0;
     if (p->D == 1 && (s > 1 || p->nx < 3)) return 0;
+  }
+  /* multiscale: D1Q3/D1Q4 (D2Q9/D2Q16) f-lattices, BGK, averaged face frame,
+   * no walls */
+  if (p->ms) {
+    if (p->qf != 4 || p->qg != 3 || p->prandtl != 1.0 || p->iterative) return 0;
+    for (int s = 0; s < 4; ++s)
+      if (p->bc[s] == ORC_BC_WALL) return 0;
   }
   return 1;
 }
@@ -858,6 +1000,18 @@ void orc_transform_pub(int q, int D, int grad_k, const double *fin, const double
   orc_lat1_make(&L, q);
   double uu[2] = {u[0], D == 2 ? u[1] : 0.0}, uup[2] = {up[0], D == 2 ? up[1] : 0.0};
   orc_transform(&L, D, grad_k, fin, uu, T, uup, Tp, fout);
+}
+
+/* The frame transformation between lattices (multiscale lifting or
+ * projection, Sec. II.E): fin on the qs-node lattice in {u, T} -> fout on the
+ * qd-node lattice in {up, Tp}, coefficients of order <= K per axis. */
+void orc_transform_x_pub(int qs, int qd, int K, int D, int grad_k, const double *fin,
+                         const double *u, double T, const double *up, double Tp, double *fout) {
+  orc_lat1 Ls, Ld;
+  orc_lat1_make(&Ls, qs);
+  orc_lat1_make(&Ld, qd);
+  double uu[2] = {u[0], D == 2 ? u[1] : 0.0}, uup[2] = {up[0], D == 2 ? up[1] : 0.0};
+  orc_transform_x(&Ls, &Ld, K, D, grad_k, fin, uu, T, uup, Tp, fout);
 }
 
 /* Equilibrium rho G_{u,T}^{up,Tp} W (Eq. NonComovingEq). */
@@ -937,6 +1091,28 @@ int orc_run(const orc_params *p, double *f, double *g, double *ux, double *uy, d
       for (int i = 0; i < G.Qg; ++i) g[i * n + s] = G.g[i * ncp + c];
       ux[s] = G.ux[c]; if (p->D == 2) uy[s] = G.uy[c]; T[s] = G.T[c];
     }
+  orc_grid_free(&G);
+  return 0;
+}
+
+/* Multiscale switching measures s_u, s_T of every interior cell of the
+ * fields (ux, uy, T) under the run's boundary rules. */
+int orc_ms_measure_pub(const orc_params *p, const double *ux, const double *uy, const double *T,
+                       double *su, double *sT) {
+  if (!orc_check(p)) return 1;
+  orc_grid G;
+  if (!orc_grid_alloc(&G, p)) { orc_grid_free(&G); return 2; }
+  for (int k = 0; k < G.ny; ++k)
+    for (int j = 0; j < G.nx; ++j) {
+      size_t s = (size_t)k * G.nx + j;
+      int c = orc_pidx(&G, j, k);
+      G.ux[c] = ux[s]; G.uy[c] = p->D == 2 ? uy[s] : 0.0; G.T[c] = T[s];
+      G.f[c] = 1.0; /* a density for the inflow-free ghost copies */
+    }
+  orc_fill_ghosts(&G);
+  for (int k = 0; k < G.ny; ++k)
+    for (int j = 0; j < G.nx; ++j)
+      orc_ms_measure(&G, j, k, su + (size_t)k * G.nx + j, sT + (size_t)k * G.nx + j);
   orc_grid_free(&G);
   return 0;
 }

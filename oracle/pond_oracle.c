@@ -470,8 +470,9 @@ static void orc_fill_ghosts(orc_grid *G) {
       }
       int side = orc_ghost_map(p, j, k, &sj, &sk);
       if (side >= 0) {
+        /* (a 1D state has no u_y: the inflow's u_y slot is unused there) */
         orc_set_equilibrium_cell(G, c, p->inflow[side][0], p->inflow[side][1],
-                                 p->inflow[side][2], p->inflow[side][3]);
+                                 G->D == 2 ? p->inflow[side][2] : 0.0, p->inflow[side][3]);
       } else {
         int s = orc_pidx(G, sj, sk);
         for (int i = 0; i < G->Qf; ++i) G->f[i * ncp + c] = G->f[i * ncp + s];
@@ -655,14 +656,16 @@ static int orc_face(orc_grid *G, int dir, int j, int k, double *phi_f, double *p
 /* ------------------------------------------------------------------ */
 /* Jumps of u and T across interior cell (j, k), from the padded fields
  * (ghosts filled): s_u = max_{d,e} |u_e(+d) - u_e(-d)| / (2 sqrt T),
- * s_T = max_d |T(+d) - T(-d)| / (2 T), centred over the two neighbours. */
+ * s_T = max_d |T(+d) - T(-d)| / (2 T), centred over the two neighbours (in
+ * 1D u_x only: an inflow ghost's u_y is not part of the 1D state). */
 static void orc_ms_measure(const orc_grid *G, int j, int k, double *su, double *sT) {
   const int c = orc_pidx(G, j, k);
   double gu = 0.0, gT = 0.0;
   for (int d = 0; d < G->D; ++d) {
     const int cp = orc_pidx(G, j + (d == 0), k + (d == 1));
     const int cm = orc_pidx(G, j - (d == 0), k - (d == 1));
-    gu = fmax(gu, fmax(fabs(G->ux[cp] - G->ux[cm]), fabs(G->uy[cp] - G->uy[cm])));
+    gu = fmax(gu, fabs(G->ux[cp] - G->ux[cm]));
+    if (G->D == 2) gu = fmax(gu, fabs(G->uy[cp] - G->uy[cm]));
     gT = fmax(gT, fabs(G->T[cp] - G->T[cm]));
   }
   *su = 0.5 * gu / sqrt(G->T[c]);

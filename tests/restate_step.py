@@ -160,6 +160,8 @@ class Restated:
                 return f[cc], g[cc], u[cc], T[cc]
             s = self.cfg["inflow"][r[1]]
             rho, ux, uy, TT = [mp.mpf(x) for x in s]
+            if D == 1:  # a 1D state has no u_y: the inflow's u_y slot is unused
+                uy = mp.mpf(0)
             return ([rho * w for w in W4], [gfac(TT) * rho * w for w in W3], [ux, uy], TT)
 
         pplus = {}

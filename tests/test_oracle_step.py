@@ -194,3 +194,16 @@ def test_pulse_second_order_convergence_1d():
         errs.append(np.mean(np.abs(r - exact)))
     orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
     assert min(orders) > 1.5, (errs, orders)
+
+
+def test_1d_inflow_ghost_has_no_uy():
+    """A 1D state has no u_y (the 1D model of Sec. V): the inflow's u_y slot
+    must not reach the boundary face's frame or its energy sum."""
+    rho, ux, uy, T = W.random_state_grid(1, 12, 1, seed=4, mach=0.8)
+    out = []
+    for vy in (0.0, 0.7):
+        d = W._base(1, 12, 1, tau=2e-3, dx=1.0 / 12, bc=(2, 2, 0, 0), inflow=((1.1, 0.3, vy, 0.9),) * 4)
+        d["dt"] = W.dt_from_cfl(ux, uy, T, d["dx"], 0.4)
+        cfg = oracle.Config.from_dict(d)
+        out.append(oracle.run(cfg, oracle.init(cfg, rho, ux, uy, T), 3))
+    assert np.array_equal(out[0].f, out[1].f) and np.array_equal(out[0].T, out[1].T)

@@ -369,6 +369,55 @@ def bench_d2q25(torch, pond, W, steps=100):
     return out
 
 
+def bench_multiscale(torch, pond, W, steps=200, theta=0.05):
+    """The multiscale f-lattice (D2Q9 where smooth, D2Q16 where a velocity or
+    temperature jump across a cell exceeds `theta`): the four-quadrant Riemann
+    problem at 1024^2 (BGK) in FP64 against plain D2Q16, and the Lax tube of
+    Sec. V.C.1 at the paper's L = 600 against its exact solution for D1Q4,
+    D1Q3 (every cell low) and the multiscale run."""
+    from tests.riemann_exact import solution
+
+    w = W.riemann4_2d(n=1024, seed=1, prandtl=1.0)
+    fields = (w["rho"], w["ux"], w["uy"], w["T"])
+    n = w["cfg"]["nx"] * w["cfg"]["ny"]
+    out = {"workload": "four-quadrant Riemann problem 1024x1024 as the riemann line but BGK (Pr 1), FP64; "
+                       "Lax tube L = 600 to t = 0.14", "theta_u": theta, "theta_T": theta,
+           "cells": n, "steps": steps, "unit": UNIT}
+    mom = {}
+    for name, extra in (("d2q16", {}), ("multiscale", dict(ms=1, ms_theta_u=theta, ms_theta_T=theta))):
+        sim = pond.Sim(dict(w["cfg"], **extra))
+        sim.init(*fields)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(sim.stream):
+            e0.record(sim.stream)
+            pond.pond_step(sim.ctx, steps)
+            e1.record(sim.stream)
+        sim.stream.synchronize()
+        ms = e0.elapsed_time(e1)
+        mom[name] = sim.moments()
+        out[name] = {"value": n * steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / steps,
+                     "tile": sim.info()[2], "nonphysical": bool(sim.flags()[1] & 1)}
+        if extra:
+            out[name]["high_fraction"] = sim.ms_stats() / (n * steps)
+        sim.close()
+    out["l1_rho_multiscale_vs_d2q16"] = _l1(mom["multiscale"][0], mom["d2q16"][0])
+    left, right = (0.445, 0.698, 3.528), (0.5, 0.0, 0.571)
+    lax = W.lax_1d(n=600)
+    exact = solution(left, right, lax["x"], lax["t_end"])[0]
+    out["lax"] = {"n": 600, "steps": lax["steps"]}
+    for name, extra in (("d1q4", {}), ("d1q3", dict(ms=1, ms_theta_u=1e30, ms_theta_T=1e30)),
+                        ("multiscale", dict(ms=1, ms_theta_u=theta, ms_theta_T=theta))):
+        sim = pond.Sim(dict(lax["cfg"], **extra))
+        sim.init(lax["rho"], lax["ux"], lax["uy"], lax["T"])
+        sim.step(lax["steps"])
+        rho = np.asarray(sim.moments()[0]).ravel()
+        out["lax"][name] = {"l1_rho_vs_exact": float(np.mean(np.abs(rho - exact)))}
+        if name == "multiscale":
+            out["lax"][name]["high_fraction"] = sim.ms_stats() / (600 * lax["steps"])
+        sim.close()
+    return out
+
+
 def bench_batched(torch, pond, W):
     """64 shock-bubble instances through the persistent batch kernel."""
     ws_ = [W.shock_bubble_2d(seed=s) for s in range(64)]
@@ -626,6 +675,7 @@ def run_gpu(args, dist, rank, ws):
         extras["riemann"] = bench_riemann(torch, pond, W)
         extras["batched"] = bench_batched(torch, pond, W)
         extras["d2q25"] = bench_d2q25(torch, pond, W)
+        extras["multiscale"] = bench_multiscale(torch, pond, W)
         extras["serve"] = bench_serve(pond, serve_mod)
         if not args.no_studies:
             extras["serve_sweep"] = bench_serve_sweep(pond, serve_mod)

@@ -143,6 +143,24 @@ typedef struct {
                               tiles compute the same step; as separate machine
                               code they may round differently (multiply-add
                               fusion), to the precision of the context.        */
+  /* multiscale f-lattice (Sec. II.E lifting and projection, Sec. IV.C
+   * switching), when 1: each step every cell takes D1Q4 / D2Q16 where
+   *   s_u = max_{d,e} |u_e(x + dx e_d) - u_e(x - dx e_d)| / (2 sqrt T) > ms_theta_u or
+   *   s_T = max_d |T(x + dx e_d) - T(x - dx e_d)| / (2 T) > ms_theta_T
+   * (the step's start fields, neighbours by the boundary rules), else D1Q3 /
+   * D2Q9.  A low cell's state keeps the high lattice's layout, with its
+   * coefficients of order 3 along an axis zero in its co-moving frame: the
+   * lifting sets the moments the low lattice lacks to their equilibrium
+   * values, and the odd central moments of a Gaussian vanish.  A cell that
+   * turns low drops them (the projection).  A face takes the higher lattice
+   * of its two cells.  Requires D1Q4 / D2Q16, FP64, Pr = 1, the averaged face
+   * frame, no walls and tile 0 (or the FP64 default, 1 in 1D and 10 in 2D);
+   * not batched.  With the main flux form a low cell keeps mass and momentum
+   * but not energy exactly (its lattice lacks the third-order moment the
+   * energy flux needs in another frame); Appendix C's form keeps all three. */
+  int32_t multiscale;
+  double ms_theta_u;       /* thresholds on s_u and s_T (the paper states none) */
+  double ms_theta_T;
 } pond_params;
 
 /* Fills the defaults: gamma 1.4, tau 1e-4, Pr 1, dx 1, dt 0 (from cfl 0.2),
@@ -206,6 +224,10 @@ pond_status pond_reset_flags(pond_ctx *c);
  * turns nonphysical), and the most traces one face evaluation made.  All zero
  * with the averaged frame.  Any pointer may be NULL.  Synchronises. */
 pond_status pond_iter_stats(pond_ctx *c, int64_t *face_evals, int64_t *traces, int32_t *max_traces);
+
+/* Multiscale: cell updates made on the high-order f-lattice since the last
+ * reset (zero without multiscale).  May be NULL.  Synchronises. */
+pond_status pond_ms_stats(pond_ctx *c, int64_t *high_cell_updates);
 
 /* Waits for all work queued on the context stream. */
 pond_status pond_sync(pond_ctx *c);

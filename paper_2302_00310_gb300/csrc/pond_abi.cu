@@ -160,7 +160,9 @@ unsigned grid1(size_t n, unsigned b) { return (unsigned)((n + b - 1) / b); }
 // Picks the kernel instantiation, sets its shared-memory opt-in (outside any
 // stream capture) and uploads the table.  Called whenever K changes.
 pond_status prepare_step(pond_ctx *c) {
-  if (c->K.iterative) {
+  if (c->K.ms) {
+    c->shape = pond_ms_shape_fp64(c->D);
+  } else if (c->K.iterative) {
     if (c->qf1 == 5) c->shape = c->fp32 ? pond_iter_shape_fp32_q5() : pond_iter_shape_fp64_q5();
     else c->shape = c->fp32 ? pond_iter_shape_fp32(c->D) : pond_iter_shape_fp64(c->D);
   } else {
@@ -235,6 +237,13 @@ bool valid_params(const pond_params *p) {
   if (p->flux_frame == POND_FRAME_ITER && (!(p->iter_tol > 0.0) || p->iter_max < 1)) return false;
   if (!(p->xi_fp64_threshold > 0.0)) return false;
   if (p->tile < 0 || p->tile > 10) return false;
+  if (p->multiscale != 0 && p->multiscale != 1) return false;
+  if (p->multiscale) {  // D1Q3/D1Q4 and D2Q9/D2Q16, FP64, BGK, averaged frame, no walls
+    if (p->precision != POND_FP64 || p->prandtl != 1.0 || p->flux_frame != POND_FRAME_AVG) return false;
+    if (std::isnan(p->ms_theta_u) || std::isnan(p->ms_theta_T)) return false;
+    for (int s = 0; s < 4; ++s)
+      if (p->bc[s] == POND_BC_WALL) return false;
+  }
   return true;
 }
 
@@ -286,6 +295,9 @@ void set_step_const(pond_ctx *c) {
   K.limiter = p.limiter;
   K.iterative = p.flux_frame == POND_FRAME_ITER;
   K.xi_thr = (float)p.xi_fp64_threshold;
+  K.ms = p.multiscale;
+  K.ms_theta_u = p.ms_theta_u;
+  K.ms_theta_T = p.ms_theta_T;
   K.cf.lam = (float)K.lam;
   K.cf.kappa1 = (float)K.kappa1;
   K.cf.kr = (float)K.kr;
@@ -423,6 +435,8 @@ pond_status pond_create(pond_ctx **out, pond_lattice lat, const int64_t dims[2],
   if (D == 1 && p->tile > 1) return POND_E_INVAL;
   if (D == 2 && p->tile == 1) return POND_E_INVAL;
   if (lat == POND_D2Q25 && p->tile != 0 && p->tile != 2) return POND_E_INVAL;
+  if (p->multiscale && (lat == POND_D2Q25 || (p->tile != 0 && p->tile != (D == 1 ? 1 : 10))))
+    return POND_E_INVAL;
   if (workspace && (workspace_bytes < need || ((uintptr_t)workspace % kAlign) != 0))
     return POND_E_NOMEM;
   pond_ctx *c = new (std::nothrow) pond_ctx();
@@ -715,6 +729,15 @@ pond_status pond_iter_stats(pond_ctx *c, int64_t *face_evals, int64_t *traces, i
   if (face_evals) *face_evals = (int64_t)h.face_evals;
   if (traces) *traces = (int64_t)h.traces;
   if (max_traces) *max_traces = (int32_t)h.max_traces;
+  return POND_OK;
+}
+
+pond_status pond_ms_stats(pond_ctx *c, int64_t *high_cell_updates) {
+  if (!c) return POND_E_INVAL;
+  Stats h;
+  POND_CUDA(cudaMemcpyAsync(&h, c->stats, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  POND_CUDA(cudaStreamSynchronize(c->stream));
+  if (high_cell_updates) *high_cell_updates = (int64_t)h.ms_high;
   return POND_OK;
 }
 

@@ -53,8 +53,10 @@ struct StepConst {
   double tau1, tau2;    // relaxation times (tau2 = tau1 / Pr)
   double cfac;          // 1 + dt/(2 tau1): phi~ - phi^eq over phi - phi^eq
   double inv2dx;        // 1/(2 dx): centred differences at wall ghosts
+  double ms_theta_u, ms_theta_T;  // multiscale switching thresholds
   int iter_max;
   int grad_k, appc, limiter, iterative;
+  int ms;               // multiscale f-lattice (D1Q3 / D2Q9 where smooth)
   float xi_thr;         // mixed path: FP64 frame transformation when max_j |a c_j + b| exceeds this
   // FP32 copies of the coefficients above for the mixed path (no conversion in the kernel)
   struct {
@@ -84,6 +86,7 @@ struct Stats {
   unsigned long long noconv;
   unsigned long long traces;        // iterated face frame: traces made, over all face evaluations
   unsigned long long face_evals;    // iterated face frame: face evaluations counted
+  unsigned long long ms_high;       // multiscale: cell updates on the high-order lattice
 };
 
 // QF1: f-lattice nodes per axis (4: D1Q4 / D2Q16, 5: D2Q25); g is D1Q3 / D2Q9
@@ -386,10 +389,63 @@ __device__ __noinline__ void prep_wall_cell(const StepConst &K, const State<R> &
   if constexpr (is_mixed<R>()) sp[D::IST * NH + h] = sqrt(T);
 }
 
+// ---- multiscale f-lattice (Sec. II.E, Sec. IV.C) -----------------------------
+// Each step every cell takes the high-order f-lattice (D1Q4 / D2Q16) where
+// the jump of u or T across it exceeds its threshold, else D1Q3 / D2Q9:
+// s_u = max_{d,e} |u_e(+d) - u_e(-d)| / (2 sqrt T), s_T = max_d |T(+d) - T(-d)| / (2 T),
+// from the step's start fields, neighbours by the ghost rules.  A low cell's
+// coefficients of order 3 along an axis are zero in its co-moving frame (the
+// lifting's equilibrium completion: odd central moments of a Gaussian
+// vanish), and a cell that turns low drops them (the projection).  A face
+// takes the higher lattice of its two cells.
+
+// u_x, u_y, T at index (j, k): an interior cell or its ghost (no walls)
+template <int DIM>
+__device__ __forceinline__ void ms_fields(const StepConst &K, const State<double> &S, int j, int k,
+                                          double &ux, double &uy, double &T) {
+  int sj = 0, sk = 0;
+  const int side = map_cell<DIM>(K, j, k, sj, sk);
+  if (side >= 0) {
+    ux = K.inflow[side][1]; uy = DIM == 2 ? K.inflow[side][2] : 0.0; T = K.inflow[side][3];
+  } else {
+    const size_t c = (size_t)sk * K.nx + sj;
+    ux = S.ux[c]; uy = DIM == 2 ? S.uy[c] : 0.0; T = S.T[c];
+  }
+}
+// the lattice of interior cell (j, k) this step: true = high order
+template <int DIM>
+__device__ __noinline__ bool ms_high(const StepConst &K, const State<double> &S, int j, int k) {
+  double gu = 0.0, gT = 0.0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    double pux, puy, pT, mux, muy, mT;
+    ms_fields<DIM>(K, S, j + (d == 0), k + (d == 1), pux, puy, pT);
+    ms_fields<DIM>(K, S, j - (d == 0), k - (d == 1), mux, muy, mT);
+    gu = fmax(gu, fabs(pux - mux));
+    if (DIM == 2) gu = fmax(gu, fabs(puy - muy));
+    gT = fmax(gT, fabs(pT - mT));
+  }
+  const double T = S.T[(size_t)k * K.nx + j];
+  return 0.5 * gu / sqrt(T) > K.ms_theta_u || 0.5 * gT / T > K.ms_theta_T;
+}
+// projection onto the low-order lattice: coefficients of order 3 along an
+// axis (and, with the Grad projection, of total order 3) dropped
+template <typename R, int Q, int NY>
+__device__ __forceinline__ void ms_project(Blk<R, Q, NY> &B, int grad_k) {
+#pragma unroll
+  for (int a = 0; a < Q; ++a)
+#pragma unroll
+    for (int b = 0; b < NY; ++b)
+      if (a > 2 || b > 2 || (NY > 1 && grad_k && a + b > 2)) B.v[a][b] = R(0);
+}
+
 // ---- phase A: one halo cell -> shared memory ------------------------------
-template <typename R, int DIM, int QF1>
+// MS: multiscale; the cell's lattice goes to the IST slot (1 high, 0 low),
+// which only the mixed path otherwise uses.
+template <typename R, int DIM, int QF1, bool MS = false>
 __device__ __forceinline__ void prep_cell(const StepConst &K, const State<R> &S, int j, int k, R *sp,
                                           int NH, int h) {
+  static_assert(!MS || !std::is_same<R, float>::value, "multiscale runs in FP64");
   using D = Dims<DIM, QF1>;
   Blk<R, QF1, D::NYF> F;
   Blk<R, 3, D::NYG> G;
@@ -410,6 +466,11 @@ __device__ __forceinline__ void prep_cell(const StepConst &K, const State<R> &S,
     ux = S.ux[c];
     uy = DIM == 2 ? S.uy[c] : R(0);
     T = S.T[c];
+    if constexpr (MS) {
+      const bool hi = ms_high<DIM>(K, S, sj, sk);
+      if (!hi) ms_project(F, K.grad_k);
+      sp[D::IST * NH + h] = hi ? R(1) : R(0);
+    }
     qe_scale(F, G, kc<R>(K.qe, K.cf.qe));
     const R rho = F.v[0][0], ka = kc<R>(K.kp_a, K.cf.kp_a);
 #pragma unroll
@@ -424,6 +485,7 @@ __device__ __forceinline__ void prep_cell(const StepConst &K, const State<R> &S,
     F.v[0][0] = kc<R>(K.kappa1, K.cf.kappa1) * rho;
     G.v[0][0] += kc<R>(K.kp_b, K.cf.kp_b) * kc<R>(K.gfac, K.cf.gfac) * T * rho;
   } else {
+    if constexpr (MS) sp[D::IST * NH + h] = R(0);  // an inflow ghost: equilibrium, either lattice
     const R rho = R(K.inflow[side][0]);
     ux = R(K.inflow[side][1]);
     uy = DIM == 2 ? R(K.inflow[side][2]) : R(0);
@@ -457,17 +519,20 @@ __device__ __forceinline__ void prep_cell(const StepConst &K, const State<R> &S,
 // phi_bar^+ of halo cell h (times kappa1) moved into the face frame
 // {uF, TF} and synthesised into node values divided by the weights,
 // Y[x-node][y-node] (SK: the face frame's synthesis constants).
-template <typename R, int DIM, int QF1, int Q>
+// ISG: the g coefficients (stride 3), else those of f (stride QF1); Q: the
+// lattice the face works on (a multiscale face with the low-order f-lattice
+// reads the f coefficients of order <= 2 per axis: the projection).
+template <typename R, int DIM, int QF1, int Q, bool ISG>
 __device__ __forceinline__ void stencil_pops_body(const StepConst &K, const R *sp, int NH, int h, R uFx,
                                                   R uFy, R TF, R sTF, const SynK<R, Q> &SK,
                                                   Blk<R, Q, (DIM == 2 ? Q : 1)> &Y) {
   using D = Dims<DIM, QF1>;
   constexpr int NY = DIM == 2 ? Q : 1;
-  constexpr int base = Q == 3 ? D::QF : 0;
+  constexpr int base = ISG ? D::QF : 0, stride = ISG ? 3 : QF1;
 #pragma unroll
   for (int n = 0; n < Q; ++n)
 #pragma unroll
-    for (int m = 0; m < NY; ++m) Y.v[n][m] = sp[(base + n + Q * m) * NH + h];
+    for (int m = 0; m < NY; ++m) Y.v[n][m] = sp[(base + n + stride * m) * NH + h];
   move_frame<R, DIM, Q>(K, sp[D::IUX * NH + h], DIM == 2 ? sp[D::IUY * NH + h] : R(0), sp[D::IT * NH + h],
                         is_mixed<R>() ? sp[D::IST * NH + h] : R(0), uFx, uFy, TF, sTF, Y);
   if constexpr (DIM == 2) {
@@ -479,20 +544,21 @@ __device__ __forceinline__ void stencil_pops_body(const StepConst &K, const R *s
 // lattice (16 call sites per face direction): the FP32 kernel is bound by
 // instruction fetch, not arithmetic, and the shared copy keeps its code
 // footprint small.  The FP64 kernel, bound by the FP64 pipe, inlines it.
-template <typename R, int DIM, int QF1, int Q>
+template <typename R, int DIM, int QF1, int Q, bool ISG>
 __device__ __noinline__ Blk<R, Q, (DIM == 2 ? Q : 1)> stencil_pops_call(const StepConst &K, const R *sp,
                                                                       int NH, int h, R uFx, R uFy,
                                                                       R TF, R sTF, SynK<R, Q> SK) {
   Blk<R, Q, (DIM == 2 ? Q : 1)> Y;  // returned by value: in registers, not through local memory
-  stencil_pops_body<R, DIM, QF1, Q>(K, sp, NH, h, uFx, uFy, TF, sTF, SK, Y);
+  stencil_pops_body<R, DIM, QF1, Q, ISG>(K, sp, NH, h, uFx, uFy, TF, sTF, SK, Y);
   return Y;
 }
-template <typename R, int DIM, int QF1, int Q>
+template <typename R, int DIM, int QF1, int Q, bool ISG>
 __device__ __forceinline__ void stencil_pops(const StepConst &K, const R *sp, int NH, int h, R uFx,
                                              R uFy, R TF, R sTF, const SynK<R, Q> &SK,
                                              Blk<R, Q, (DIM == 2 ? Q : 1)> &Y) {
-  if constexpr (is_mixed<R>()) Y = stencil_pops_call<R, DIM, QF1, Q>(K, sp, NH, h, uFx, uFy, TF, sTF, SK);
-  else stencil_pops_body<R, DIM, QF1, Q>(K, sp, NH, h, uFx, uFy, TF, sTF, SK, Y);
+  if constexpr (is_mixed<R>())
+    Y = stencil_pops_call<R, DIM, QF1, Q, ISG>(K, sp, NH, h, uFx, uFy, TF, sTF, SK);
+  else stencil_pops_body<R, DIM, QF1, Q, ISG>(K, sp, NH, h, uFx, uFy, TF, sTF, SK, Y);
 }
 
 // v_n == +-0 exactly (a wall at rest puts the zero node of D1Q3 there)
@@ -502,7 +568,7 @@ __device__ __forceinline__ bool is_zero(float v) { return (__float_as_int(v) << 
 // The trace of a face with a node at v_n = 0: that node takes the mean of its
 // two one-sided traces, so that the face has no preferred side; the others
 // take the upwind one as in reconstruct().  Out of line: only such faces run it.
-template <typename R, int DIM, int QF1, int DIRN, int Q>
+template <typename R, int DIM, int QF1, int DIRN, int Q, bool ISG>
 __device__ __noinline__ void reconstruct_tie(const StepConst &K, const R *sp, int NH, const int *st, R uFx,
                                              R uFy, R TF, R sTF, R isTF, Blk<R, Q, (DIM == 2 ? Q : 1)> &out) {
   constexpr int NY = DIM == 2 ? Q : 1, NS = DIM == 2 ? 8 : 4;
@@ -513,7 +579,7 @@ __device__ __noinline__ void reconstruct_tie(const StepConst &K, const R *sp, in
   const int lim = K.limiter;
   Blk<R, Q, NY> Y[NS];  // stencil: 0 left, 1 right, 2 outer-left, 3 outer-right, 4-7 tangential
 #pragma unroll 1
-  for (int s = 0; s < NS; ++s) stencil_pops<R, DIM, QF1, Q>(K, sp, NH, st[s], uFx, uFy, TF, sTF, SK, Y[s]);
+  for (int s = 0; s < NS; ++s) stencil_pops<R, DIM, QF1, Q, ISG>(K, sp, NH, st[s], uFx, uFy, TF, sTF, SK, Y[s]);
 #pragma unroll
   for (int n = 0; n < Q; ++n)
 #pragma unroll
@@ -547,12 +613,12 @@ __device__ __noinline__ void reconstruct_tie(const StepConst &K, const R *sp, in
 // The offsets carry the factor lf of limit().
 // TIE: 0 = no node of the face has v_n = 0 (checked by the caller), 1 = check
 // here, 2 = the face has one (both run reconstruct_tie out of line).
-template <typename R, int DIM, int QF1, int DIRN, int Q, int TIE>
+template <typename R, int DIM, int QF1, int DIRN, int Q, int TIE, bool ISG>
 __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int NH, const int *st,
                                             R uFx, R uFy, R TF, R sTF, R isTF,
                                             Blk<R, Q, (DIM == 2 ? Q : 1)> &out) {
   if constexpr (TIE == 2) {
-    reconstruct_tie<R, DIM, QF1, DIRN, Q>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, out);
+    reconstruct_tie<R, DIM, QF1, DIRN, Q, ISG>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, out);
     return;
   }
   constexpr int NY = DIM == 2 ? Q : 1;
@@ -576,7 +642,7 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
   }
   if constexpr (TIE == 1) {
     if (tie) {
-      reconstruct_tie<R, DIM, QF1, DIRN, Q>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, out);
+      reconstruct_tie<R, DIM, QF1, DIRN, Q, ISG>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, out);
       return;
     }
   }
@@ -590,12 +656,12 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
   const bool zt = ODD && is_zero(uFn);
   R Z[NZ], ZD[NZ];
   Blk<R, Q, NY> YL, YR, A;
-  stencil_pops<R, DIM, QF1, Q>(K, sp, NH, st[0], uFx, uFy, TF, sTF, SK, YL);
-  stencil_pops<R, DIM, QF1, Q>(K, sp, NH, st[1], uFx, uFy, TF, sTF, SK, YR);
+  stencil_pops<R, DIM, QF1, Q, ISG>(K, sp, NH, st[0], uFx, uFy, TF, sTF, SK, YL);
+  stencil_pops<R, DIM, QF1, Q, ISG>(K, sp, NH, st[1], uFx, uFy, TF, sTF, SK, YR);
   {
     Blk<R, Q, NY> Y1, Y2;
-    stencil_pops<R, DIM, QF1, Q>(K, sp, NH, st[2], uFx, uFy, TF, sTF, SK, Y1);
-    stencil_pops<R, DIM, QF1, Q>(K, sp, NH, st[3], uFx, uFy, TF, sTF, SK, Y2);
+    stencil_pops<R, DIM, QF1, Q, ISG>(K, sp, NH, st[2], uFx, uFy, TF, sTF, SK, Y1);
+    stencil_pops<R, DIM, QF1, Q, ISG>(K, sp, NH, st[3], uFx, uFy, TF, sTF, SK, Y2);
 #pragma unroll
     for (int n = 0; n < Q; ++n)
 #pragma unroll
@@ -617,8 +683,8 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
   }
   if constexpr (DIM == 2) {
     Blk<R, Q, NY> Y1, Y2, Dl;
-    stencil_pops<R, DIM, QF1, Q>(K, sp, NH, st[4], uFx, uFy, TF, sTF, SK, Y1);
-    stencil_pops<R, DIM, QF1, Q>(K, sp, NH, st[5], uFx, uFy, TF, sTF, SK, Y2);
+    stencil_pops<R, DIM, QF1, Q, ISG>(K, sp, NH, st[4], uFx, uFy, TF, sTF, SK, Y1);
+    stencil_pops<R, DIM, QF1, Q, ISG>(K, sp, NH, st[5], uFx, uFy, TF, sTF, SK, Y2);
 #pragma unroll
     for (int n = 0; n < Q; ++n)
 #pragma unroll
@@ -629,8 +695,8 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
           if (k == KZ && zt) ZD[DIRN == 0 ? m : n] = YL.v[n][m] - Y1.v[n][m];
         }
       }
-    stencil_pops<R, DIM, QF1, Q>(K, sp, NH, st[6], uFx, uFy, TF, sTF, SK, Y1);
-    stencil_pops<R, DIM, QF1, Q>(K, sp, NH, st[7], uFx, uFy, TF, sTF, SK, Y2);
+    stencil_pops<R, DIM, QF1, Q, ISG>(K, sp, NH, st[6], uFx, uFy, TF, sTF, SK, Y1);
+    stencil_pops<R, DIM, QF1, Q, ISG>(K, sp, NH, st[7], uFx, uFy, TF, sTF, SK, Y2);
 #pragma unroll
     for (int n = 0; n < Q; ++n)
 #pragma unroll
@@ -662,11 +728,11 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
 // dimensional Hermite coefficients of an equilibrium {u_b, Tb} seen from the
 // face frame (Gauss-Hermite quadrature is exact to degree 2q-1, so rho G W has
 // them).
-template <typename R>
+template <typename R, int N = 4>
 __device__ __forceinline__ void gauss_he(R mu, R dT, R *e) {
   e[1] = mu;
   e[2] = fma(mu, mu, dT);
-  e[3] = mu * fma(mu, mu, R(3) * dT);
+  if constexpr (N > 3) e[3] = mu * fma(mu, mu, R(3) * dT);
 }
 // order 4 (D1Q5): H_4(mu; TF - Tb) = mu^4 + 6 dT mu^2 + 3 dT^2
 template <typename R>
@@ -684,7 +750,10 @@ __device__ __forceinline__ R gauss_he4(R mu, R dT) {
 // interface state is nonphysical ends the iteration and the face keeps the
 // previous iterate.  Returns true when an iterated frame did not converge;
 // ntrace receives the number of traces made (1 for the averaged frame).
-template <typename R, int DIM, int QF1, int DIRN, bool ITER, bool TIE = false>
+// QL: the f-lattice of the face, QF1 or (a multiscale face whose two cells
+// are both on the low-order lattice) 3; the face record keeps the storage
+// layout of QF1, with zero coefficients beyond QL.
+template <typename R, int DIM, int QF1, int DIRN, bool ITER, bool TIE = false, int QL = QF1>
 __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int NH, const int *st,
                                           R *fp, int NFACES, int fidx, int &ntrace);
 
@@ -701,29 +770,29 @@ __device__ __forceinline__ bool face_has_tie(R uFn, R sTF) {
   return t;
 }
 // the averaged-frame face with a node at v_n = 0, out of line (rare)
-template <typename R, int DIM, int QF1, int DIRN>
+template <typename R, int DIM, int QF1, int DIRN, int QL>
 __device__ __noinline__ bool face_flux_tie(const StepConst &K, const R *sp, int NH, const int *st, R *fp,
                                            int NFACES, int fidx, int &ntrace) {
-  return face_flux<R, DIM, QF1, DIRN, false, true>(K, sp, NH, st, fp, NFACES, fidx, ntrace);
+  return face_flux<R, DIM, QF1, DIRN, false, true, QL>(K, sp, NH, st, fp, NFACES, fidx, ntrace);
 }
 
-template <typename R, int DIM, int QF1, int DIRN, bool ITER, bool TIE>
+template <typename R, int DIM, int QF1, int DIRN, bool ITER, bool TIE, int QL>
 __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int NH, const int *st,
                                           R *fp, int NFACES, int fidx, int &ntrace) {
   using D = Dims<DIM, QF1>;
-  constexpr int NYF = D::NYF, NYG = D::NYG;
+  constexpr int NYF = DIM == 2 ? QL : 1, NYG = D::NYG;
   const int hL = st[0], hR = st[1];
   R uFx = R(0.5) * (sp[D::IUX * NH + hL] + sp[D::IUX * NH + hR]);
   R uFy = DIM == 2 ? R(0.5) * (sp[D::IUY * NH + hL] + sp[D::IUY * NH + hR]) : R(0);
   R TF = R(0.5) * (sp[D::IT * NH + hL] + sp[D::IT * NH + hR]);
   R sTF = sqrt(TF), isTF = R(1) / sTF;
   if constexpr (!ITER && !TIE) {
-    if (face_has_tie<R, QF1>(DIRN == 0 ? uFx : uFy, sTF))
-      return face_flux_tie<R, DIM, QF1, DIRN>(K, sp, NH, st, fp, NFACES, fidx, ntrace);
+    if (face_has_tie<R, QL>(DIRN == 0 ? uFx : uFy, sTF))
+      return face_flux_tie<R, DIM, QF1, DIRN, QL>(K, sp, NH, st, fp, NFACES, fidx, ntrace);
   }
   constexpr int TMODE = ITER ? 1 : (TIE ? 2 : 0);
 
-  Blk<R, QF1, NYF> Fb;
+  Blk<R, QL, NYF> Fb;
   Blk<R, 3, NYG> Gb;
   R rk, mx, my, Tb;
   bool converged = false, noconv = false;
@@ -733,9 +802,9 @@ __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int N
   ntrace = 0;
   while (true) {
     ++ntrace;
-    reconstruct<R, DIM, QF1, DIRN, QF1, TMODE>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, Fb);
-    reconstruct<R, DIM, QF1, DIRN, 3, TMODE>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, Gb);
-    anaq_xy(AnaK<R, QF1>(TF, sTF), Fb);
+    reconstruct<R, DIM, QF1, DIRN, QL, TMODE, false>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, Fb);
+    reconstruct<R, DIM, QF1, DIRN, 3, TMODE, true>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, Gb);
+    anaq_xy(AnaK<R, QL>(TF, sTF), Fb);
     anaq_xy(AnaK<R, 3>(TF, sTF), Gb);
     // interface moments in the face frame (all carry the factor kappa1): rho,
     // mu = u - u_F, C_v rho T = (sum |v - u_F|^2 f - rho |mu|^2)/2 + sum g
@@ -777,20 +846,20 @@ __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int N
 
   // equilibrium (closed form of rho G_{u,T}^{lambda_F} W), weighted by kappa2/kappa1;
   // a converged iterated frame is co-moving: rho W
-  R ex[QF1], ey[QF1];
-  ex[0] = R(1); gauss_he(mx, dTb, ex);
-  if constexpr (QF1 == 5) ex[4] = gauss_he4(mx, dTb);
+  R ex[QL], ey[QL];
+  ex[0] = R(1); gauss_he<R, QL>(mx, dTb, ex);
+  if constexpr (QL == 5) ex[4] = gauss_he4(mx, dTb);
   ey[0] = R(1);
 #pragma unroll
-  for (int a = 1; a < QF1; ++a) ey[a] = R(0);
+  for (int a = 1; a < QL; ++a) ey[a] = R(0);
   if constexpr (DIM == 2) {
-    gauss_he(my, dTb, ey);
-    if constexpr (QF1 == 5) ey[4] = gauss_he4(my, dTb);
+    gauss_he<R, QL>(my, dTb, ey);
+    if constexpr (QL == 5) ey[4] = gauss_he4(my, dTb);
   }
   if constexpr (ITER) {
     if (converged) {
 #pragma unroll
-      for (int a = 1; a < QF1; ++a) ex[a] = ey[a] = R(0);
+      for (int a = 1; a < QL; ++a) ex[a] = ey[a] = R(0);
     }
   }
   // an interface state with rho <= 0 or T <= 0 has no equilibrium: poison the
@@ -799,11 +868,11 @@ __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int N
   const bool gk = DIM == 2 && K.grad_k;
   const R re = phys ? kc<R>(K.kr, K.cf.kr) * rk : qnan<R>(), ge = re * kc<R>(K.gfac, K.cf.gfac) * Tb;
 #pragma unroll
-  for (int a = 0; a < QF1; ++a)
+  for (int a = 0; a < QL; ++a)
 #pragma unroll
     for (int b = 0; b < NYF; ++b) {
       R e = re * ex[a] * ey[b];
-      if (gk && a + b > QF1 - 1) e = R(0);
+      if (gk && a + b > QL - 1) e = R(0);
       Fb.v[a][b] += e;
     }
 #pragma unroll
@@ -862,7 +931,10 @@ __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int N
 #pragma unroll
   for (int a = 0; a < QF1; ++a)
 #pragma unroll
-    for (int b = 0; b < NYF; ++b) fp[(a + QF1 * b) * NFACES + fidx] = Fb.v[a][b];
+    for (int b = 0; b < D::NYF; ++b) {
+      if constexpr (QL == QF1) fp[(a + QF1 * b) * NFACES + fidx] = Fb.v[a][b];
+      else fp[(a + QF1 * b) * NFACES + fidx] = (a < QL && b < NYF) ? Fb.v[a < QL ? a : 0][b < NYF ? b : 0] : R(0);
+    }
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -937,10 +1009,12 @@ __device__ __forceinline__ void face_contrib(const StepConst &K, const R *fp, in
 // multiplication by v_n in the cell frame is linear, so it is applied once to
 // the difference), or -dt/dx [G (v_F . n phi)_hi - G (v_F . n phi)_lo] in
 // the Appendix C form.
-template <typename R, int DIM, int QF1, int DIRN>
+// (MS, low: the fluxes are projected onto the cell's low-order lattice before
+// the multiplication by v_n, which on that lattice has no order-3 term.)
+template <typename R, int DIM, int QF1, int DIRN, bool MS = false>
 __device__ __forceinline__ void add_faces(const StepConst &K, const R *fp, int NFACES, int flo, int fhi,
                                           R ux, R uy, R T, R sT, Blk<R, QF1, Dims<DIM, QF1>::NYF> &F,
-                                          Blk<R, 3, Dims<DIM, QF1>::NYG> &G, MomAcc &M) {
+                                          Blk<R, 3, Dims<DIM, QF1>::NYG> &G, MomAcc &M, bool low = false) {
   using D = Dims<DIM, QF1>;
   Blk<R, QF1, D::NYF> DX, X;
   Blk<R, 3, D::NYG> DY, Y;
@@ -954,6 +1028,9 @@ __device__ __forceinline__ void add_faces(const StepConst &K, const R *fp, int N
   for (int p = 0; p < 3; ++p)
 #pragma unroll
     for (int q = 0; q < D::NYG; ++q) DY.v[p][q] = Y.v[p][q] - DY.v[p][q];
+  if constexpr (MS) {
+    if (low) ms_project(DX, K.grad_k);
+  }
   if (!K.appc) {
     const R un = DIRN == 0 ? ux : uy;
     vmul<DIRN>(un, T, DX);
@@ -979,10 +1056,10 @@ __device__ __forceinline__ void add_faces(const StepConst &K, const R *fp, int N
   }
 }
 
-template <typename R, int DIM, int QF1, int BX, int BY>
+template <typename R, int DIM, int QF1, int BX, int BY, bool MS = false>
 __device__ __forceinline__ void update_cell(const StepConst &K, const State<R> &S, const State<R> &O,
                                             const R *fp, int cx, int cy, int j, int k, R &vmax,
-                                            unsigned &flags) {
+                                            unsigned &flags, bool low = false) {
   using D = Dims<DIM, QF1>;
   using TL = Tile<DIM, BX, BY, QF1>;
   const size_t N = (size_t)K.nx * (DIM == 2 ? K.ny : 1);
@@ -995,6 +1072,9 @@ __device__ __forceinline__ void update_cell(const StepConst &K, const State<R> &
   for (int i = 0; i < D::QG; ++i) G.v[i % 3][i / 3] = S.g[i * N + c];
   const R ux = S.ux[c], uy = DIM == 2 ? S.uy[c] : R(0), T = S.T[c];
   const R sT = is_mixed<R>() ? sqrt(T) : R(0);
+  if constexpr (MS) {
+    if (low) ms_project(F, K.grad_k);
+  }
   qe_scale(F, G, kc<R>(K.qe, K.cf.qe));
   const R rho = F.v[0][0];
   MomAcc M;
@@ -1017,10 +1097,11 @@ __device__ __forceinline__ void update_cell(const StepConst &K, const State<R> &
 #pragma unroll
     for (int b = 0; b < D::NYG; ++b) G.v[a][b] *= a1;
   // fluxes through the faces, in a fixed order: x, then y
-  add_faces<R, DIM, QF1, 0>(K, fp, TL::NFACES, cy * (BX + 1) + cx, cy * (BX + 1) + cx + 1, ux, uy, T, sT, F, G, M);
+  add_faces<R, DIM, QF1, 0, MS>(K, fp, TL::NFACES, cy * (BX + 1) + cx, cy * (BX + 1) + cx + 1, ux, uy, T, sT, F,
+                                G, M, low);
   if constexpr (DIM == 2)
-    add_faces<R, DIM, QF1, 1>(K, fp, TL::NFACES, TL::NFX + cy * BX + cx, TL::NFX + (cy + 1) * BX + cx, ux, uy, T,
-                         sT, F, G, M);
+    add_faces<R, DIM, QF1, 1, MS>(K, fp, TL::NFACES, TL::NFX + cy * BX + cx, TL::NFX + (cy + 1) * BX + cx, ux, uy,
+                                  T, sT, F, G, M, low);
   F.v[0][0] += kc<R>(K.a2, K.cf.a2) * rho;
   G.v[0][0] += kc<R>(K.a2, K.cf.a2) * kc<R>(K.gfac, K.cf.gfac) * T * rho;
 
@@ -1075,10 +1156,14 @@ __device__ __forceinline__ void update_cell(const StepConst &K, const State<R> &
       if (K.grad_k) { grad_mask(F); grad_mask(G); }
     }
     qe_scale(F, G, kc<R>(K.qe, K.cf.qe));
-    vmax = fmax(vmax, fmax(fabs(uxn), fabs(uyn)) + sqrt(Tout) * R(Nodes<QF1>::cmax));
+    const R cm = (MS && low) ? R(Nodes<3>::cmax) : R(Nodes<QF1>::cmax);
+    vmax = fmax(vmax, fmax(fabs(uxn), fabs(uyn)) + sqrt(Tout) * cm);
   } else {
     flags |= FLAG_NONPHYSICAL;
     uxn = ux; uyn = uy; Tout = T;
+  }
+  if constexpr (MS) {
+    if (low) ms_project(F, K.grad_k);  // back to the low lattice's storage
   }
 #pragma unroll
   for (int i = 0; i < D::QF; ++i) O.f[i * N + c] = F.v[i % QF1][i / QF1];
@@ -1101,7 +1186,7 @@ __device__ __forceinline__ void update_cell(const StepConst &K, const State<R> &
 // given instantiation the result does not depend on the launch order or on
 // which tile a cell falls in (different tile shapes are different machine
 // code and may round differently).
-template <typename R, int DIM, int QF1, int BX, int BY, int NT, bool ITER>
+template <typename R, int DIM, int QF1, int BX, int BY, int NT, bool ITER, bool MS = false>
 __device__ __forceinline__ void step_tile(const StepConst &K, const State<R> &S, const State<R> &O,
                                           Stats *stats, int j0, int k0, unsigned char *smem) {
   using D = Dims<DIM, QF1>;
@@ -1113,7 +1198,7 @@ __device__ __forceinline__ void step_tile(const StepConst &K, const State<R> &S,
   // A. halo tile
   for (int h = tid; h < TL::NH; h += NT) {
     const int hx = h % TL::HX, hy = h / TL::HX;
-    prep_cell<R, DIM, QF1>(K, S, j0 + hx - 2, k0 + hy - TL::OY, sp, TL::NH, h);
+    prep_cell<R, DIM, QF1, MS>(K, S, j0 + hx - 2, k0 + hy - TL::OY, sp, TL::NH, h);
   }
   __syncthreads();
 
@@ -1132,7 +1217,15 @@ __device__ __forceinline__ void step_tile(const StepConst &K, const State<R> &S,
         st[6] = r + TL::HX + fx + 1; st[7] = r + TL::HX + fx + 2;
       }
       int nt;
-      const bool nc = face_flux<R, DIM, QF1, 0, ITER>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
+      bool nc;
+      if constexpr (MS) {  // the face's f-lattice: the higher of its two cells'
+        if (sp[D::IST * TL::NH + st[0]] == R(0) && sp[D::IST * TL::NH + st[1]] == R(0))
+          nc = face_flux<R, DIM, QF1, 0, ITER, false, 3>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
+        else
+          nc = face_flux<R, DIM, QF1, 0, ITER>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
+      } else {
+        nc = face_flux<R, DIM, QF1, 0, ITER>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
+      }
       if (ITER && (fx > 0 || j0 == 0)) {
         noconv += nc; traces += nt; ++evals; max_tr = max(max_tr, (unsigned)nt);
       }
@@ -1144,7 +1237,15 @@ __device__ __forceinline__ void step_tile(const StepConst &K, const State<R> &S,
       st[4] = (fy + 1) * H + x - 1; st[5] = (fy + 2) * H + x - 1;
       st[6] = (fy + 1) * H + x + 1; st[7] = (fy + 2) * H + x + 1;
       int nt;
-      const bool nc = face_flux<R, DIM, QF1, 1, ITER>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
+      bool nc;
+      if constexpr (MS) {  // the face's f-lattice: the higher of its two cells'
+        if (sp[D::IST * TL::NH + st[0]] == R(0) && sp[D::IST * TL::NH + st[1]] == R(0))
+          nc = face_flux<R, DIM, QF1, 1, ITER, false, 3>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
+        else
+          nc = face_flux<R, DIM, QF1, 1, ITER>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
+      } else {
+        nc = face_flux<R, DIM, QF1, 1, ITER>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
+      }
       if (ITER && (fy > 0 || k0 == 0)) {
         noconv += nc; traces += nt; ++evals; max_tr = max(max_tr, (unsigned)nt);
       }
@@ -1154,12 +1255,17 @@ __device__ __forceinline__ void step_tile(const StepConst &K, const State<R> &S,
 
   // C. cells
   R vmax = R(0);
-  unsigned flags = 0;
+  unsigned flags = 0, nhigh = 0;
   for (int c = tid; c < TL::NCELL; c += NT) {
     const int cx = c % BX, cy = c / BX;
     const int j = j0 + cx, k = k0 + cy;
     if (j >= K.nx || k >= (DIM == 2 ? K.ny : 1)) continue;
-    update_cell<R, DIM, QF1, BX, BY>(K, S, O, fp, cx, cy, j, k, vmax, flags);
+    bool low = false;
+    if constexpr (MS) {
+      low = sp[D::IST * TL::NH + (cy + TL::OY) * TL::HX + cx + 2] == R(0);
+      nhigh += !low;
+    }
+    update_cell<R, DIM, QF1, BX, BY, MS>(K, S, O, fp, cx, cy, j, k, vmax, flags, low);
   }
   double cfl = (double)vmax * K.lam;
   // warp reduction of the CFL number, flags and counts, one atomic per warp
@@ -1167,6 +1273,7 @@ __device__ __forceinline__ void step_tile(const StepConst &K, const State<R> &S,
   for (int o = 16; o > 0; o >>= 1) {
     cfl = fmax(cfl, __shfl_xor_sync(0xffffffffu, cfl, o));
     flags |= __shfl_xor_sync(0xffffffffu, flags, o);
+    if constexpr (MS) nhigh += __shfl_xor_sync(0xffffffffu, nhigh, o);
     if constexpr (ITER) {
       noconv += __shfl_xor_sync(0xffffffffu, noconv, o);
       traces += __shfl_xor_sync(0xffffffffu, traces, o);
@@ -1186,6 +1293,9 @@ __device__ __forceinline__ void step_tile(const StepConst &K, const State<R> &S,
         atomicAdd(&stats->face_evals, (unsigned long long)evals);
         atomicMax(&stats->max_traces, max_tr);
       }
+    }
+    if constexpr (MS) {
+      if (nhigh) atomicAdd(&stats->ms_high, (unsigned long long)nhigh);
     }
     if (flags) atomicOr(&stats->flags, flags);
     atomicMax(&stats->max_cfl_bits, (unsigned long long)__double_as_longlong(cfl));

@@ -57,3 +57,5 @@ std::vector<pond::Shape> pond_shapes_fp64_q5();
 std::vector<pond::Shape> pond_shapes_fp32_q5();
 pond::Shape pond_iter_shape_fp64_q5();
 pond::Shape pond_iter_shape_fp32_q5();
+// the multiscale f-lattice, FP64 (pond_step_fp64_ms.cu)
+pond::Shape pond_ms_shape_fp64(int D);

@@ -30,7 +30,7 @@ POND_FLAG_NONPHYSICAL, POND_FLAG_CFL, POND_FLAG_NOCONV = 1, 2, 4
 EXPORTS = (
     "pond_params_default", "pond_workspace_size", "pond_create", "pond_init", "pond_step",
     "pond_moments", "pond_get_state", "pond_set_state", "pond_status_flags", "pond_reset_flags",
-    "pond_iter_stats",
+    "pond_iter_stats", "pond_ms_stats",
     "pond_sync", "pond_info", "pond_destroy", "pond_strerror", "pond_abi_version",
     "pond_step_noalloc", "pond_tune_default", "pond_batch_create", "pond_batch_add",
     "pond_batch_remove", "pond_batch_size", "pond_batch_step", "pond_batch_info",
@@ -48,7 +48,8 @@ class pond_params(ctypes.Structure):
         ("flux_form", ctypes.c_int32), ("limiter", ctypes.c_int32),
         ("flux_frame", ctypes.c_int32), ("iter_tol", ctypes.c_double),
         ("iter_max", ctypes.c_int32), ("xi_fp64_threshold", ctypes.c_double),
-        ("tile", ctypes.c_int32),
+        ("tile", ctypes.c_int32), ("multiscale", ctypes.c_int32), ("ms_theta_u", ctypes.c_double),
+        ("ms_theta_T", ctypes.c_double),
     ]
 
 
@@ -95,6 +96,7 @@ def lib(build: bool = False):
     L.pond_reset_flags.argtypes = [_P]
     L.pond_iter_stats.argtypes = [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                   ctypes.POINTER(ctypes.c_int32)]
+    L.pond_ms_stats.argtypes = [_P, ctypes.POINTER(ctypes.c_int64)]
     L.pond_sync.argtypes = [_P]
     L.pond_info.argtypes = [_P, _D, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]
     L.pond_destroy.argtypes = [_P]
@@ -229,6 +231,14 @@ def pond_iter_stats(ctx):
     return int(ev.value), int(tr.value), int(mx.value)
 
 
+def pond_ms_stats(ctx):
+    """Cell updates made on the high-order f-lattice since the last reset
+    (multiscale)."""
+    n = ctypes.c_int64()
+    _check(lib().pond_ms_stats(ctx, ctypes.byref(n)), "pond_ms_stats")
+    return int(n.value)
+
+
 def pond_reset_flags(ctx):
     _check(lib().pond_reset_flags(ctx), "pond_reset_flags")
 
@@ -352,6 +362,8 @@ def params_from_config(cfg: dict) -> pond_params:
     p.iter_tol, p.iter_max = float(cfg.get("iter_tol", 1e-12)), int(cfg.get("iter_max", 10))
     p.xi_fp64_threshold = float(cfg.get("xi_fp64_threshold", 8.0))
     p.tile = int(cfg.get("tile", 0))
+    p.multiscale = int(cfg.get("ms", 0))
+    p.ms_theta_u, p.ms_theta_T = float(cfg.get("ms_theta_u", 0.0)), float(cfg.get("ms_theta_T", 0.0))
     return p
 
 
@@ -420,6 +432,9 @@ class Sim:
 
     def iter_stats(self):
         return pond_iter_stats(self.ctx)
+
+    def ms_stats(self):
+        return pond_ms_stats(self.ctx)
 
     def info(self):
         return pond_info(self.ctx)

@@ -67,11 +67,10 @@ WORKLOAD = "2D periodic advected Gaussian pulse, D2Q16+D2Q9, 256x256, Mach 2 at 
 # Per-cell-update work of the step on this workload, FP64 flops (an FMA
 # counting 2) and FP32 flops for the mixed path: the arithmetic of the
 # dimensional-Hermite formulation of the step, counted by ncu as 2 FMA + ADD +
-# MUL thread instructions per launch / cells (counted on the source digest
-# named; later changes to the kernels left the arithmetic of a step without
-# ties or walls unchanged to 0.2 %).  profiles/ holds the captures.
-FLOPS_PER_CELL = {"fp64": 9029.5, "fp32": 8701.6, "fp32_fp64part": 59.2,
-                  "counted_on": "790618b69e911cb1318aa3edb3a10029b792f89c949e01f9287a6c16cd22b159"}
+# MUL thread instructions per launch / cells, on the source digest named (the
+# build whose kernels bench.py runs; profiles/ holds the captures).
+FLOPS_PER_CELL = {"fp64": 8771.6, "fp32": 8708.2, "fp32_fp64part": 59.2,
+                  "counted_on": "c1d52785c5c34bc75b5cf2802630339cb478fec54c800eb0408ff04bb2cbf7be"}
 BYTES_PER_CELL_FP64 = 2 * 28 * 8          # state read once + written once
 BYTES_PER_CELL_FP32 = 2 * (28 * 4 + 4 * 8)  # + the FP64 conserved moments
 CLOCK_MAX_GHZ = 2.07
@@ -80,8 +79,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * CLOCK_MAX_GHZ / 1e3   # 128 FP32 FMA/clk/SM
 # dram__bytes_read.sum + dram__bytes_write.sum of one main-line step launch
 # (FP64 and mixed path), keyed by source digest (None once the sources change)
 TRAFFIC_BY_DIGEST = {
-    "58be7f51bbe1761cb6dda9da34a0c72b6e62695d41552bc026a33487294aeb43": {"fp64": 18140928,
-                                                                          "fp32": 9829632},
+    "c1d52785c5c34bc75b5cf2802630339cb478fec54c800eb0408ff04bb2cbf7be": {"fp64": 18181632,
+                                                                          "fp32": 9835776},
 }
 
 

@@ -191,7 +191,10 @@ __device__ __forceinline__ bool abs_less(float x, float y) {
 }
 
 // The limited slope divided by lf(lim) (lf = 2 for van Leer, 1 for minmod;
-// the factor is folded into the trace offsets): van Leer 2xy/(x+y) / 2.
+// the factor is folded into the trace offsets): van Leer 2xy/(x+y) / 2.  In
+// FP64 the quotient takes the reciprocal after one Newton step (no residual
+// correction of the quotient): the slope enters the trace times an offset
+// below 1, and the step is bound by the FP64 pipe (2 DFMA saved per limit).
 template <typename R> __device__ __forceinline__ R limiter_factor(int lim) {
   return lim == LIM_MINMOD ? R(1) : R(2);
 }
@@ -199,7 +202,8 @@ template <typename R>
 __device__ __forceinline__ R limit(R x, R y, int lim) {
   const R p = x * y;
   if (lim == LIM_MINMOD) return pos(p) ? (abs_less(x, y) ? x : y) : R(0);
-  return pos(p) ? div_nr(p, x + y) : R(0);
+  if constexpr (std::is_same<R, double>::value) return pos(p) ? p * rcp_nr1(x + y) : R(0);
+  else return pos(p) ? div_nr(p, x + y) : R(0);
 }
 
 // The FP32 instantiation is the mixed-precision path (POND_FP32_MIXED).

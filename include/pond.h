@@ -24,7 +24,7 @@
  * Array layouts (all FP64 at the boundary, whatever the internal precision):
  *   fields   [ny][nx]            (x fastest; ny = 1 in 1D)
  *   f        [Qf][ny][nx]        Qf = 4 (1D), 16 (2D) or 25 (D2Q25)
- *   g        [Qg][ny][nx]        Qg = 3 (1D) or 9 (2D)
+ *   g        [Qg][ny][nx]        Qg = 3 (1D) or 9 (2D); 4 or 16 with g_same_as_f
  * The state is the DUGKS variable phi~ of Eq. eq:variableTransform in each
  * cell's co-moving frame {u, T}; the frame itself is (ux, uy, T).
  *
@@ -57,7 +57,7 @@ extern "C" {
 typedef struct pond_ctx pond_ctx;
 
 /* f-lattice of a context (the g-lattice follows: D1Q3 / D2Q9, as in every run of
- * Sec. V).  POND_D2Q25: five Gauss-Hermite nodes per axis (the roots of He_5,
+ * Sec. V, or the f-lattice itself with pond_params.g_same_as_f).  POND_D2Q25: five Gauss-Hermite nodes per axis (the roots of He_5,
  * Table I), frame-invariant moments to fourth order per axis (Sec. II.D.2;
  * the fourth-order runs of the shock-structure problem, Sec. V.B.4); its
  * populations f[25][ny][nx] use node indices ix = i % 5, iy = i / 5, nodes
@@ -161,6 +161,14 @@ typedef struct {
   int32_t multiscale;
   double ms_theta_u;       /* thresholds on s_u and s_T (the paper states none) */
   double ms_theta_T;
+  /* 1: the g-populations on the f-lattice (D1Q4 / D2Q16, invariant to third
+   * order) instead of D1Q3 / D2Q9; g needs frame-invariant moments to second
+   * order only (Sec. III.C) and every run of the paper uses D2Q9.  g[Qg] then
+   * holds 4 (1D) or 16 (2D) populations in the f-lattice's node order.
+   * Requires D1Q4 / D2Q16, the averaged face frame, no multiscale and tile 0
+   * (or the precision's default: 1 in 1D; 10 FP64, 6 mixed in 2D); not
+   * batched. */
+  int32_t g_same_as_f;
 } pond_params;
 
 /* Fills the defaults: gamma 1.4, tau 1e-4, Pr 1, dx 1, dt 0 (from cfl 0.2),

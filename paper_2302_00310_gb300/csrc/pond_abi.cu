@@ -39,14 +39,14 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 // ---------------------------------------------------------------------------
 // co-moving equilibria rho W (Eq. feqPond) and (C_v - D/2) T rho W
 // (Eq. geqPond): their only nonzero Hermite coefficient is the zeroth
-template <typename R, int DIM, int QF1>
+template <typename R, int DIM, int QF1, int QG1 = 3>
 __global__ void init_kernel(const double *rho, const double *ux, const double *uy, const double *T,
                             State<R> S, size_t N, double gfac) {
   const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= N) return;
   const double r = rho[c], t = T[c], vx = ux[c], vy = DIM == 2 ? uy[c] : 0.0;
   for (int i = 0; i < (DIM == 2 ? QF1 * QF1 : QF1); ++i) S.f[i * N + c] = R(i == 0 ? r : 0.0);
-  for (int i = 0; i < (DIM == 2 ? 9 : 3); ++i) S.g[i * N + c] = R(i == 0 ? gfac * t * r : 0.0);
+  for (int i = 0; i < (DIM == 2 ? QG1 * QG1 : QG1); ++i) S.g[i * N + c] = R(i == 0 ? gfac * t * r : 0.0);
   S.ux[c] = R(vx);
   S.uy[c] = R(vy);
   S.T[c] = R(t);
@@ -89,16 +89,16 @@ __global__ void moments_kernel(State<R> S, size_t N, double inv_cv, double *rho,
 // populations (FP64 planes p[i][ld], cells 0..n-1) <-> state coefficients
 // (cells c0..c0+n-1) in the frame already stored for those cells; in place
 // when the planes are the state's own (FP64)
-template <typename R, int DIM, int QF1>
+template <typename R, int DIM, int QF1, int QG1 = 3>
 __global__ void pops_to_coef_kernel(const double *pf, const double *pg, size_t ld, State<R> S,
                                     size_t N, size_t c0, size_t n) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  using D = pond::Dims<DIM, QF1>;
+  using D = pond::Dims<DIM, QF1, QG1>;
   pond::Blk<double, QF1, D::NYF> F;
-  pond::Blk<double, 3, D::NYG> G;
+  pond::Blk<double, QG1, D::NYG> G;
   for (int q = 0; q < D::QF; ++q) F.v[q % QF1][q / QF1] = pf[q * ld + i];
-  for (int q = 0; q < D::QG; ++q) G.v[q % 3][q / 3] = pg[q * ld + i];
+  for (int q = 0; q < D::QG; ++q) G.v[q % QG1][q / QG1] = pg[q * ld + i];
   pond::ana_x(F); pond::ana_y(F); pond::ana_x(G); pond::ana_y(G);
   const double fT = S.T[c0 + i], sT = sqrt(fT);
   pond::scale_orders(sT, F);
@@ -115,24 +115,24 @@ __global__ void pops_to_coef_kernel(const double *pf, const double *pg, size_t l
     S.M[3 * N + c] = 0.5 * ((fx * fx + fy * fy) * r + 2.0 * (fx * bx + fy * by) + c2) + G.v[0][0];
   }
   for (int q = 0; q < D::QF; ++q) S.f[q * N + c0 + i] = R(F.v[q % QF1][q / QF1]);
-  for (int q = 0; q < D::QG; ++q) S.g[q * N + c0 + i] = R(G.v[q % 3][q / 3]);
+  for (int q = 0; q < D::QG; ++q) S.g[q * N + c0 + i] = R(G.v[q % QG1][q / QG1]);
 }
-template <typename R, int DIM, int QF1>
+template <typename R, int DIM, int QF1, int QG1 = 3>
 __global__ void coef_to_pops_kernel(State<R> S, size_t N, size_t c0, size_t n, double *pf,
                                     double *pg, size_t ld) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  using D = pond::Dims<DIM, QF1>;
+  using D = pond::Dims<DIM, QF1, QG1>;
   pond::Blk<double, QF1, D::NYF> F;
-  pond::Blk<double, 3, D::NYG> G;
+  pond::Blk<double, QG1, D::NYG> G;
   for (int q = 0; q < D::QF; ++q) F.v[q % QF1][q / QF1] = (double)S.f[q * N + c0 + i];
-  for (int q = 0; q < D::QG; ++q) G.v[q % 3][q / 3] = (double)S.g[q * N + c0 + i];
+  for (int q = 0; q < D::QG; ++q) G.v[q % QG1][q / QG1] = (double)S.g[q * N + c0 + i];
   const double isT = 1.0 / sqrt((double)S.T[c0 + i]);
   pond::scale_orders(isT, F);
   pond::scale_orders(isT, G);
   pond::syn_x(F); pond::syn_y(F); pond::syn_x(G); pond::syn_y(G);
   for (int q = 0; q < D::QF; ++q) pf[q * ld + i] = F.v[q % QF1][q / QF1];
-  for (int q = 0; q < D::QG; ++q) pg[q * ld + i] = G.v[q % 3][q / 3];
+  for (int q = 0; q < D::QG; ++q) pg[q * ld + i] = G.v[q % QG1][q / QG1];
 }
 
 template <typename A, typename B>
@@ -162,6 +162,8 @@ unsigned grid1(size_t n, unsigned b) { return (unsigned)((n + b - 1) / b); }
 pond_status prepare_step(pond_ctx *c) {
   if (c->K.ms) {
     c->shape = pond_ms_shape_fp64(c->D);
+  } else if (c->qg1 == 4) {
+    c->shape = c->fp32 ? pond_g4_shape_fp32(c->D) : pond_g4_shape_fp64(c->D);
   } else if (c->K.iterative) {
     if (c->qf1 == 5) c->shape = c->fp32 ? pond_iter_shape_fp32_q5() : pond_iter_shape_fp64_q5();
     else c->shape = c->fp32 ? pond_iter_shape_fp32(c->D) : pond_iter_shape_fp64(c->D);
@@ -238,6 +240,7 @@ bool valid_params(const pond_params *p) {
   if (!(p->xi_fp64_threshold > 0.0)) return false;
   if (p->tile < 0 || p->tile > 10) return false;
   if (p->multiscale != 0 && p->multiscale != 1) return false;
+  if (p->g_same_as_f != 0 && p->g_same_as_f != 1) return false;
   if (p->multiscale) {  // D1Q3/D1Q4 and D2Q9/D2Q16, FP64, BGK, averaged frame, no walls
     if (p->precision != POND_FP64 || p->prandtl != 1.0 || p->flux_frame != POND_FRAME_AVG) return false;
     if (std::isnan(p->ms_theta_u) || std::isnan(p->ms_theta_T)) return false;
@@ -352,11 +355,15 @@ pond_status convert_pops(pond_ctx *c, double *pf, double *pg, size_t ld, size_t 
   const unsigned nb = grid1(n, 256);
   const State<R> S = state_of<R>(c, c->cur);
   if (to_state) {
-    if (c->qf1 == 5) pops_to_coef_kernel<R, 2, 5><<<nb, 256, 0, c->stream>>>(pf, pg, ld, S, N, c0, n);
+    if (c->qg1 == 4 && c->D == 2) pops_to_coef_kernel<R, 2, 4, 4><<<nb, 256, 0, c->stream>>>(pf, pg, ld, S, N, c0, n);
+    else if (c->qg1 == 4) pops_to_coef_kernel<R, 1, 4, 4><<<nb, 256, 0, c->stream>>>(pf, pg, ld, S, N, c0, n);
+    else if (c->qf1 == 5) pops_to_coef_kernel<R, 2, 5><<<nb, 256, 0, c->stream>>>(pf, pg, ld, S, N, c0, n);
     else if (c->D == 2) pops_to_coef_kernel<R, 2, 4><<<nb, 256, 0, c->stream>>>(pf, pg, ld, S, N, c0, n);
     else pops_to_coef_kernel<R, 1, 4><<<nb, 256, 0, c->stream>>>(pf, pg, ld, S, N, c0, n);
   } else {
-    if (c->qf1 == 5) coef_to_pops_kernel<R, 2, 5><<<nb, 256, 0, c->stream>>>(S, N, c0, n, pf, pg, ld);
+    if (c->qg1 == 4 && c->D == 2) coef_to_pops_kernel<R, 2, 4, 4><<<nb, 256, 0, c->stream>>>(S, N, c0, n, pf, pg, ld);
+    else if (c->qg1 == 4) coef_to_pops_kernel<R, 1, 4, 4><<<nb, 256, 0, c->stream>>>(S, N, c0, n, pf, pg, ld);
+    else if (c->qf1 == 5) coef_to_pops_kernel<R, 2, 5><<<nb, 256, 0, c->stream>>>(S, N, c0, n, pf, pg, ld);
     else if (c->D == 2) coef_to_pops_kernel<R, 2, 4><<<nb, 256, 0, c->stream>>>(S, N, c0, n, pf, pg, ld);
     else coef_to_pops_kernel<R, 1, 4><<<nb, 256, 0, c->stream>>>(S, N, c0, n, pf, pg, ld);
   }
@@ -417,7 +424,8 @@ pond_status pond_workspace_size(pond_lattice lat, const int64_t dims[2], const p
   if (nx < 2 || (D == 2 && ny < 2) || nx > (1 << 24) || ny > (1 << 24)) return POND_E_INVAL;
   const bool fp32 = p->precision == POND_FP32_MIXED;
   *bytes = align_up(sizeof(Stats)) + pond::kSoloTableBytes +
-           2 * align_up(pond_detail::state_bytes(D, fp32, (size_t)(nx * ny), pond_detail::qf1_of(lat)));
+           2 * align_up(pond_detail::state_bytes(D, fp32, (size_t)(nx * ny), pond_detail::qf1_of(lat),
+                                                 pond_detail::qg1_of(p)));
   return POND_OK;
 }
 
@@ -437,6 +445,9 @@ pond_status pond_create(pond_ctx **out, pond_lattice lat, const int64_t dims[2],
   if (lat == POND_D2Q25 && p->tile != 0 && p->tile != 2) return POND_E_INVAL;
   if (p->multiscale && (lat == POND_D2Q25 || (p->tile != 0 && p->tile != (D == 1 ? 1 : 10))))
     return POND_E_INVAL;
+  if (p->g_same_as_f && (lat == POND_D2Q25 || p->multiscale || p->flux_frame != POND_FRAME_AVG ||
+                         (p->tile != 0 && p->tile != (D == 1 ? 1 : (p->precision == POND_FP64 ? 10 : 6)))))
+    return POND_E_INVAL;
   if (workspace && (workspace_bytes < need || ((uintptr_t)workspace % kAlign) != 0))
     return POND_E_NOMEM;
   pond_ctx *c = new (std::nothrow) pond_ctx();
@@ -444,6 +455,7 @@ pond_status pond_create(pond_ctx **out, pond_lattice lat, const int64_t dims[2],
   c->lat = lat;
   c->D = D;
   c->qf1 = pond_detail::qf1_of(lat);
+  c->qg1 = pond_detail::qg1_of(p);
   c->nx = dims[0];
   c->ny = D == 2 ? dims[1] : 1;
   c->N = c->nx * c->ny;
@@ -504,7 +516,13 @@ pond_status pond_init(pond_ctx *c, const double *rho, const double *ux, const do
   POND_CUDA(cudaMemsetAsync(c->stats, 0, sizeof(Stats), c->stream));
   const double gfac = 1.0 / (c->p.gamma - 1.0) - 0.5 * c->D;
   const unsigned nb = grid1(N, 256);
-  if (c->D == 2) {
+  if (c->qg1 == 4) {
+    const double *uy2 = c->D == 2 ? suy : nullptr;
+    if (c->D == 2 && c->fp32) init_kernel<float, 2, 4, 4><<<nb, 256, 0, c->stream>>>(srho, sux, uy2, sT, state_of<float>(c, c->cur), N, gfac);
+    else if (c->D == 2) init_kernel<double, 2, 4, 4><<<nb, 256, 0, c->stream>>>(srho, sux, uy2, sT, state_of<double>(c, c->cur), N, gfac);
+    else if (c->fp32) init_kernel<float, 1, 4, 4><<<nb, 256, 0, c->stream>>>(srho, sux, uy2, sT, state_of<float>(c, c->cur), N, gfac);
+    else init_kernel<double, 1, 4, 4><<<nb, 256, 0, c->stream>>>(srho, sux, uy2, sT, state_of<double>(c, c->cur), N, gfac);
+  } else if (c->D == 2) {
     if (c->qf1 == 5) {
       if (c->fp32) init_kernel<float, 2, 5><<<nb, 256, 0, c->stream>>>(srho, sux, suy, sT, state_of<float>(c, c->cur), N, gfac);
       else init_kernel<double, 2, 5><<<nb, 256, 0, c->stream>>>(srho, sux, suy, sT, state_of<double>(c, c->cur), N, gfac);
@@ -630,7 +648,7 @@ static pond_status xfer(pond_ctx *c, double *ext, size_t comp_off, size_t n, boo
 // populations in or out: device arrays are converted directly; host arrays go
 // through the idle state buffer in chunks of cells
 static pond_status pops_io(pond_ctx *c, double *f, double *g, bool to_state, int on_device) {
-  const size_t N = (size_t)c->N, qf = qf_of(c->D, c->qf1), qg = qg_of(c->D);
+  const size_t N = (size_t)c->N, qf = qf_of(c->D, c->qf1), qg = qg_of(c->D, c->qg1);
   auto conv = [&](double *pf, double *pg, size_t ld, size_t c0, size_t n) {
     return c->fp32 ? convert_pops<float>(c, pf, pg, ld, c0, n, to_state)
                    : convert_pops<double>(c, pf, pg, ld, c0, n, to_state);
@@ -663,7 +681,7 @@ static pond_status pops_io(pond_ctx *c, double *f, double *g, bool to_state, int
 static pond_status state_io(pond_ctx *c, double *f, double *g, double *ux, double *uy, double *T,
                             bool to_state, int on_device) {
   if (!c || !f || !g || !ux || !T || (c->D == 2 && !uy)) return POND_E_INVAL;
-  const size_t N = (size_t)c->N, qf = qf_of(c->D, c->qf1), qg = qg_of(c->D);
+  const size_t N = (size_t)c->N, qf = qf_of(c->D, c->qf1), qg = qg_of(c->D, c->qg1);
   pond_status s;
   // the frame goes in before the populations, whose coefficients are taken in it
   if (!to_state && (s = pops_io(c, f, g, to_state, on_device)) != POND_OK) return s;
@@ -773,7 +791,7 @@ struct CkptHdr {
   uint64_t state_bytes;
 };
 size_t state_bytes_of(const pond_ctx *c) {
-  return pond_detail::state_bytes(c->D, c->fp32, (size_t)c->N, c->qf1);
+  return pond_detail::state_bytes(c->D, c->fp32, (size_t)c->N, c->qf1, c->qg1);
 }
 const char kCkptMagic[8] = {'P', 'O', 'N', 'D', 'C', 'K', 'P', '1'};
 }  // namespace

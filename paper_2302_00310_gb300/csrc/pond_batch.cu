@@ -277,7 +277,7 @@ void pond_batch_destroy(pond_batch *b) {
 pond_status pond_batch_add(pond_batch *b, pond_ctx *c) {
   if (!b || !c) return POND_E_INVAL;
   if (!c->inited) return POND_E_STATE;
-  if (c->batch || c->D != b->D || c->qf1 != 4 || c->K.ms || c->fp32 != b->fp32 || c->stream != b->stream ||
+  if (c->batch || c->D != b->D || c->qf1 != 4 || c->qg1 != 3 || c->K.ms || c->fp32 != b->fp32 || c->stream != b->stream ||
       c->K.iterative || (int)b->members.size() >= b->capacity)
     return POND_E_INVAL;
   b->members.push_back(c);

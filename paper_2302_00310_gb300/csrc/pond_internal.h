@@ -13,6 +13,7 @@ struct pond_ctx {
   pond_lattice lat;
   int D;
   int qf1;                // f-lattice nodes per axis: 4, or 5 (D2Q25)
+  int qg1;                // g-lattice nodes per axis: 3, or 4 (g on the f-lattice)
   int64_t nx, ny, N;
   pond_params p;
   bool fp32;
@@ -41,15 +42,16 @@ namespace pond_detail {
 
 inline int qf_of(int D, int qf1 = 4) { return D == 2 ? qf1 * qf1 : qf1; }
 inline int qf1_of(pond_lattice lat) { return lat == POND_D2Q25 ? 5 : 4; }
-inline int qg_of(int D) { return D == 2 ? 9 : 3; }
+inline int qg_of(int D, int qg1 = 3) { return D == 2 ? qg1 * qg1 : qg1; }
+inline int qg1_of(const pond_params *p) { return p->g_same_as_f ? 4 : 3; }
 
 // bytes of the arithmetic planes f, g, ux, uy, T of one state buffer, rounded
 // up to 8; the mixed path's FP64 conserved moments M[4][N] follow them
-inline size_t coef_bytes(int D, bool fp32, size_t N, int qf1 = 4) {
-  return ((size_t)(qf_of(D, qf1) + qg_of(D) + 3) * N * (fp32 ? 4 : 8) + 7) / 8 * 8;
+inline size_t coef_bytes(int D, bool fp32, size_t N, int qf1 = 4, int qg1 = 3) {
+  return ((size_t)(qf_of(D, qf1) + qg_of(D, qg1) + 3) * N * (fp32 ? 4 : 8) + 7) / 8 * 8;
 }
-inline size_t state_bytes(int D, bool fp32, size_t N, int qf1 = 4) {
-  return coef_bytes(D, fp32, N, qf1) + (fp32 ? 4 * N * sizeof(double) : 0);
+inline size_t state_bytes(int D, bool fp32, size_t N, int qf1 = 4, int qg1 = 3) {
+  return coef_bytes(D, fp32, N, qf1, qg1) + (fp32 ? 4 * N * sizeof(double) : 0);
 }
 
 template <typename R> pond::State<R> state_of(const pond_ctx *c, int b) {
@@ -57,10 +59,10 @@ template <typename R> pond::State<R> state_of(const pond_ctx *c, int b) {
   pond::State<R> s;
   s.f = base;
   s.g = s.f + (size_t)qf_of(c->D, c->qf1) * c->N;
-  s.ux = s.g + (size_t)qg_of(c->D) * c->N;
+  s.ux = s.g + (size_t)qg_of(c->D, c->qg1) * c->N;
   s.uy = s.ux + c->N;
   s.T = s.uy + c->N;
-  s.M = c->fp32 ? reinterpret_cast<double *>(c->buf[b] + coef_bytes(c->D, true, (size_t)c->N, c->qf1))
+  s.M = c->fp32 ? reinterpret_cast<double *>(c->buf[b] + coef_bytes(c->D, true, (size_t)c->N, c->qf1, c->qg1))
                  : nullptr;
   return s;
 }

@@ -89,12 +89,14 @@ struct Stats {
   unsigned long long ms_high;       // multiscale: cell updates on the high-order lattice
 };
 
-// QF1: f-lattice nodes per axis (4: D1Q4 / D2Q16, 5: D2Q25); g is D1Q3 / D2Q9
-template <int DIM, int QF1 = 4> struct Dims {
+// QF1: f-lattice nodes per axis (4: D1Q4 / D2Q16, 5: D2Q25); QG1: g-lattice
+// nodes per axis (3: D1Q3 / D2Q9, as in the paper's runs; 4: g on f's D1Q4 /
+// D2Q16 lattice)
+template <int DIM, int QF1 = 4, int QG1 = 3> struct Dims {
   static constexpr int QF = DIM == 2 ? QF1 * QF1 : QF1;
-  static constexpr int QG = DIM == 2 ? 9 : 3;
+  static constexpr int QG = DIM == 2 ? QG1 * QG1 : QG1;
   static constexpr int NYF = DIM == 2 ? QF1 : 1;
-  static constexpr int NYG = DIM == 2 ? 3 : 1;
+  static constexpr int NYG = DIM == 2 ? QG1 : 1;
   // shared-memory record of a halo cell: f coeffs, g coeffs, ux, uy, T, and
   // (mixed path) sqrt T
   static constexpr int IUX = QF + QG, IUY = IUX + 1, IT = IUX + 2, IST = IUX + 3;
@@ -108,7 +110,7 @@ template <int DIM, int QF1 = 4> struct Dims {
   }
 };
 
-template <int DIM, int BX, int BY, int QF1 = 4> struct Tile {
+template <int DIM, int BX, int BY, int QF1 = 4, int QG1 = 3> struct Tile {
   static constexpr int HX = BX + 4, HY = DIM == 2 ? BY + 4 : 1, OY = DIM == 2 ? 2 : 0;
   static constexpr int NH = HX * HY;
   static constexpr int NFX = (BX + 1) * (DIM == 2 ? BY : 1);
@@ -116,7 +118,8 @@ template <int DIM, int BX, int BY, int QF1 = 4> struct Tile {
   static constexpr int NFACES = NFX + NFY;
   static constexpr int NCELL = BX * (DIM == 2 ? BY : 1);
   template <typename R> static constexpr size_t smem_bytes() {
-    return sizeof(R) * ((size_t)NH * Dims<DIM, QF1>::NPREP + (size_t)NFACES * Dims<DIM, QF1>::template nface<R>());
+    return sizeof(R) * ((size_t)NH * Dims<DIM, QF1, QG1>::NPREP +
+                        (size_t)NFACES * Dims<DIM, QF1, QG1>::template nface<R>());
   }
 };
 
@@ -142,15 +145,15 @@ __device__ __forceinline__ int map_cell(const StepConst &K, int j, int k, int &s
 // QE half step (Sec. IV.B) in the co-moving frame: f* - f^eq is the total
 // order-3 Hermite content of f and g* - g^eq the order-1 content of g
 // (Eq. eq::quasi_f), so the relaxation scales those coefficients by qe.
-template <typename R, int QF1, int NYF, int NYG>
-__device__ __forceinline__ void qe_scale(Blk<R, QF1, NYF> &F, Blk<R, 3, NYG> &G, R qe) {
+template <typename R, int QF1, int NYF, int QG1, int NYG>
+__device__ __forceinline__ void qe_scale(Blk<R, QF1, NYF> &F, Blk<R, QG1, NYG> &G, R qe) {
 #pragma unroll
   for (int a = 0; a < QF1; ++a)
 #pragma unroll
     for (int b = 0; b < NYF; ++b)
       if (a + b == 3) F.v[a][b] *= qe;
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
+  for (int a = 0; a < QG1; ++a)
 #pragma unroll
     for (int b = 0; b < NYG; ++b)
       if (a + b == 1) G.v[a][b] *= qe;
@@ -296,9 +299,10 @@ __device__ __forceinline__ void wall_mac(const StepConst &K, const State<R> &S, 
 // dimensional Hermite polynomials the central moments are the coefficients:
 // B_20 = P_xx, B_11 = P_xy, B_21 = Q_xxy, ... (f, whose non-equilibrium has no
 // mass or momentum), and B_00 = M_g0, B_10 = M_g1,x, B_20 = M_g2,xx - T M_g0 (g).
-template <typename R, int DIM, int QF1>
+template <typename R, int DIM, int QF1, int QG1 = 3>
 __device__ __forceinline__ void wall_ghost(const StepConst &K, const State<R> &S, int j, int k,
-                                        Blk<R, QF1, Dims<DIM, QF1>::NYF> &F, Blk<R, 3, Dims<DIM, QF1>::NYG> &G,
+                                        Blk<R, QF1, Dims<DIM, QF1>::NYF> &F,
+                                        Blk<R, QG1, Dims<DIM, QF1, QG1>::NYG> &G,
                                         R &ux, R &uy, R &Tout) {
   double mG[4], a[4], b[4];
   wall_mac<R, DIM>(K, S, j, k, mG);
@@ -309,9 +313,9 @@ __device__ __forceinline__ void wall_ghost(const StepConst &K, const State<R> &S
 #pragma unroll
       for (int q = 0; q < Dims<DIM, QF1>::NYF; ++q) F.v[p][q] = qnan<R>();
 #pragma unroll
-    for (int p = 0; p < 3; ++p)
+    for (int p = 0; p < QG1; ++p)
 #pragma unroll
-      for (int q = 0; q < Dims<DIM, QF1>::NYG; ++q) G.v[p][q] = qnan<R>();
+      for (int q = 0; q < Dims<DIM, QF1, QG1>::NYG; ++q) G.v[p][q] = qnan<R>();
     ux = R(mG[1]); uy = R(mG[2]); Tout = qnan<R>();
     return;
   }
@@ -338,9 +342,9 @@ __device__ __forceinline__ void wall_ghost(const StepConst &K, const State<R> &S
 #pragma unroll
     for (int q = 0; q < Dims<DIM, QF1>::NYF; ++q) F.v[p][q] = R(0);
 #pragma unroll
-  for (int p = 0; p < 3; ++p)
+  for (int p = 0; p < QG1; ++p)
 #pragma unroll
-    for (int q = 0; q < Dims<DIM, QF1>::NYG; ++q) G.v[p][q] = R(0);
+    for (int q = 0; q < Dims<DIM, QF1, QG1>::NYG; ++q) G.v[p][q] = R(0);
   F.v[0][0] = R(rho);
   F.v[2][0] = R(pxx);
   F.v[3][0] = R(qxxx);
@@ -360,21 +364,21 @@ __device__ __forceinline__ void wall_ghost(const StepConst &K, const State<R> &S
 // phase A for a wall ghost (out of line: only halo cells across a wall run it):
 // phi_bar^+ = kp_a phi~ + kp_b phi^eq, with no quasi-equilibrium step (the
 // ghost is built from the cells' macroscopic fields, which it leaves alone)
-template <typename R, int DIM, int QF1>
+template <typename R, int DIM, int QF1, int QG1 = 3>
 __device__ __noinline__ void prep_wall_cell(const StepConst &K, const State<R> &S, int j, int k, R *sp,
                                             int NH, int h) {
-  using D = Dims<DIM, QF1>;
+  using D = Dims<DIM, QF1, QG1>;
   Blk<R, QF1, D::NYF> F;
-  Blk<R, 3, D::NYG> G;
+  Blk<R, QG1, D::NYG> G;
   R ux, uy, T;
-  wall_ghost<R, DIM, QF1>(K, S, j, k, F, G, ux, uy, T);
+  wall_ghost<R, DIM, QF1, QG1>(K, S, j, k, F, G, ux, uy, T);
   const R rho = F.v[0][0], ka = kc<R>(K.kp_a, K.cf.kp_a);
 #pragma unroll
   for (int a = 0; a < QF1; ++a)
 #pragma unroll
     for (int b = 0; b < D::NYF; ++b) F.v[a][b] *= ka;
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
+  for (int a = 0; a < QG1; ++a)
 #pragma unroll
     for (int b = 0; b < D::NYG; ++b) G.v[a][b] *= ka;
   F.v[0][0] = kc<R>(K.kappa1, K.cf.kappa1) * rho;
@@ -384,9 +388,9 @@ __device__ __noinline__ void prep_wall_cell(const StepConst &K, const State<R> &
 #pragma unroll
     for (int b = 0; b < D::NYF; ++b) sp[(a + QF1 * b) * NH + h] = F.v[a][b];
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
+  for (int a = 0; a < QG1; ++a)
 #pragma unroll
-    for (int b = 0; b < D::NYG; ++b) sp[(D::QF + a + 3 * b) * NH + h] = G.v[a][b];
+    for (int b = 0; b < D::NYG; ++b) sp[(D::QF + a + QG1 * b) * NH + h] = G.v[a][b];
   sp[D::IUX * NH + h] = ux;
   sp[D::IUY * NH + h] = uy;
   sp[D::IT * NH + h] = T;
@@ -446,17 +450,17 @@ __device__ __forceinline__ void ms_project(Blk<R, Q, NY> &B, int grad_k) {
 // ---- phase A: one halo cell -> shared memory ------------------------------
 // MS: multiscale; the cell's lattice goes to the IST slot (1 high, 0 low),
 // which only the mixed path otherwise uses.
-template <typename R, int DIM, int QF1, bool MS = false>
+template <typename R, int DIM, int QF1, bool MS = false, int QG1 = 3>
 __device__ __forceinline__ void prep_cell(const StepConst &K, const State<R> &S, int j, int k, R *sp,
                                           int NH, int h) {
   static_assert(!MS || !std::is_same<R, float>::value, "multiscale runs in FP64");
-  using D = Dims<DIM, QF1>;
+  using D = Dims<DIM, QF1, QG1>;
   Blk<R, QF1, D::NYF> F;
-  Blk<R, 3, D::NYG> G;
+  Blk<R, QG1, D::NYG> G;
   R ux, uy, T;
   int sj = 0, sk = 0;
   if (is_wall_ghost<DIM>(K, j, k)) {
-    prep_wall_cell<R, DIM, QF1>(K, S, j, k, sp, NH, h);
+    prep_wall_cell<R, DIM, QF1, QG1>(K, S, j, k, sp, NH, h);
     return;
   }
   const int side = map_cell<DIM>(K, j, k, sj, sk);
@@ -466,7 +470,7 @@ __device__ __forceinline__ void prep_cell(const StepConst &K, const State<R> &S,
 #pragma unroll
     for (int i = 0; i < D::QF; ++i) F.v[i % QF1][i / QF1] = S.f[i * N + c];
 #pragma unroll
-    for (int i = 0; i < D::QG; ++i) G.v[i % 3][i / 3] = S.g[i * N + c];
+    for (int i = 0; i < D::QG; ++i) G.v[i % QG1][i / QG1] = S.g[i * N + c];
     ux = S.ux[c];
     uy = DIM == 2 ? S.uy[c] : R(0);
     T = S.T[c];
@@ -482,7 +486,7 @@ __device__ __forceinline__ void prep_cell(const StepConst &K, const State<R> &S,
 #pragma unroll
       for (int b = 0; b < D::NYF; ++b) F.v[a][b] *= ka;
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+    for (int a = 0; a < QG1; ++a)
 #pragma unroll
       for (int b = 0; b < D::NYG; ++b) G.v[a][b] *= ka;
     // phi_bar^+ = kp_a phi~ + kp_b phi^eq; phi^eq = rho W (f), (C_v - D/2) T rho W (g)
@@ -499,7 +503,7 @@ __device__ __forceinline__ void prep_cell(const StepConst &K, const State<R> &S,
 #pragma unroll
       for (int b = 0; b < D::NYF; ++b) F.v[a][b] = R(0);
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+    for (int a = 0; a < QG1; ++a)
 #pragma unroll
       for (int b = 0; b < D::NYG; ++b) G.v[a][b] = R(0);
     F.v[0][0] = kc<R>(K.kappa1, K.cf.kappa1) * rho;
@@ -510,9 +514,9 @@ __device__ __forceinline__ void prep_cell(const StepConst &K, const State<R> &S,
 #pragma unroll
     for (int b = 0; b < D::NYF; ++b) sp[(a + QF1 * b) * NH + h] = F.v[a][b];
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
+  for (int a = 0; a < QG1; ++a)
 #pragma unroll
-    for (int b = 0; b < D::NYG; ++b) sp[(D::QF + a + 3 * b) * NH + h] = G.v[a][b];
+    for (int b = 0; b < D::NYG; ++b) sp[(D::QF + a + QG1 * b) * NH + h] = G.v[a][b];
   sp[D::IUX * NH + h] = ux;
   sp[D::IUY * NH + h] = uy;
   sp[D::IT * NH + h] = T;
@@ -523,16 +527,17 @@ __device__ __forceinline__ void prep_cell(const StepConst &K, const State<R> &S,
 // phi_bar^+ of halo cell h (times kappa1) moved into the face frame
 // {uF, TF} and synthesised into node values divided by the weights,
 // Y[x-node][y-node] (SK: the face frame's synthesis constants).
-// ISG: the g coefficients (stride 3), else those of f (stride QF1); Q: the
-// lattice the face works on (a multiscale face with the low-order f-lattice
-// reads the f coefficients of order <= 2 per axis: the projection).
-template <typename R, int DIM, int QF1, int Q, bool ISG>
+// GS: 0 for the f coefficients (stride QF1), else the g coefficients (stride
+// QG1, the g-lattice's nodes per axis); Q: the lattice the face works on (a
+// multiscale face with the low-order f-lattice reads the f coefficients of
+// order <= 2 per axis: the projection).
+template <typename R, int DIM, int QF1, int Q, int GS, int QG1>
 __device__ __forceinline__ void stencil_pops_body(const StepConst &K, const R *sp, int NH, int h, R uFx,
                                                   R uFy, R TF, R sTF, const SynK<R, Q> &SK,
                                                   Blk<R, Q, (DIM == 2 ? Q : 1)> &Y) {
-  using D = Dims<DIM, QF1>;
+  using D = Dims<DIM, QF1, QG1>;
   constexpr int NY = DIM == 2 ? Q : 1;
-  constexpr int base = ISG ? D::QF : 0, stride = ISG ? 3 : QF1;
+  constexpr int base = GS ? D::QF : 0, stride = GS ? QG1 : QF1;
 #pragma unroll
   for (int n = 0; n < Q; ++n)
 #pragma unroll
@@ -548,21 +553,21 @@ __device__ __forceinline__ void stencil_pops_body(const StepConst &K, const R *s
 // lattice (16 call sites per face direction): the FP32 kernel is bound by
 // instruction fetch, not arithmetic, and the shared copy keeps its code
 // footprint small.  The FP64 kernel, bound by the FP64 pipe, inlines it.
-template <typename R, int DIM, int QF1, int Q, bool ISG>
+template <typename R, int DIM, int QF1, int Q, int GS, int QG1>
 __device__ __noinline__ Blk<R, Q, (DIM == 2 ? Q : 1)> stencil_pops_call(const StepConst &K, const R *sp,
                                                                       int NH, int h, R uFx, R uFy,
                                                                       R TF, R sTF, SynK<R, Q> SK) {
   Blk<R, Q, (DIM == 2 ? Q : 1)> Y;  // returned by value: in registers, not through local memory
-  stencil_pops_body<R, DIM, QF1, Q, ISG>(K, sp, NH, h, uFx, uFy, TF, sTF, SK, Y);
+  stencil_pops_body<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, h, uFx, uFy, TF, sTF, SK, Y);
   return Y;
 }
-template <typename R, int DIM, int QF1, int Q, bool ISG>
+template <typename R, int DIM, int QF1, int Q, int GS, int QG1>
 __device__ __forceinline__ void stencil_pops(const StepConst &K, const R *sp, int NH, int h, R uFx,
                                              R uFy, R TF, R sTF, const SynK<R, Q> &SK,
                                              Blk<R, Q, (DIM == 2 ? Q : 1)> &Y) {
   if constexpr (is_mixed<R>())
-    Y = stencil_pops_call<R, DIM, QF1, Q, ISG>(K, sp, NH, h, uFx, uFy, TF, sTF, SK);
-  else stencil_pops_body<R, DIM, QF1, Q, ISG>(K, sp, NH, h, uFx, uFy, TF, sTF, SK, Y);
+    Y = stencil_pops_call<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, h, uFx, uFy, TF, sTF, SK);
+  else stencil_pops_body<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, h, uFx, uFy, TF, sTF, SK, Y);
 }
 
 // v_n == +-0 exactly (a wall at rest puts the zero node of D1Q3 there)
@@ -572,7 +577,7 @@ __device__ __forceinline__ bool is_zero(float v) { return (__float_as_int(v) << 
 // The trace of a face with a node at v_n = 0: that node takes the mean of its
 // two one-sided traces, so that the face has no preferred side; the others
 // take the upwind one as in reconstruct().  Out of line: only such faces run it.
-template <typename R, int DIM, int QF1, int DIRN, int Q, bool ISG>
+template <typename R, int DIM, int QF1, int DIRN, int Q, int GS, int QG1>
 __device__ __noinline__ void reconstruct_tie(const StepConst &K, const R *sp, int NH, const int *st, R uFx,
                                              R uFy, R TF, R sTF, R isTF, Blk<R, Q, (DIM == 2 ? Q : 1)> &out) {
   constexpr int NY = DIM == 2 ? Q : 1, NS = DIM == 2 ? 8 : 4;
@@ -583,7 +588,7 @@ __device__ __noinline__ void reconstruct_tie(const StepConst &K, const R *sp, in
   const int lim = K.limiter;
   Blk<R, Q, NY> Y[NS];  // stencil: 0 left, 1 right, 2 outer-left, 3 outer-right, 4-7 tangential
 #pragma unroll 1
-  for (int s = 0; s < NS; ++s) stencil_pops<R, DIM, QF1, Q, ISG>(K, sp, NH, st[s], uFx, uFy, TF, sTF, SK, Y[s]);
+  for (int s = 0; s < NS; ++s) stencil_pops<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, st[s], uFx, uFy, TF, sTF, SK, Y[s]);
 #pragma unroll
   for (int n = 0; n < Q; ++n)
 #pragma unroll
@@ -617,12 +622,12 @@ __device__ __noinline__ void reconstruct_tie(const StepConst &K, const R *sp, in
 // The offsets carry the factor lf of limit().
 // TIE: 0 = no node of the face has v_n = 0 (checked by the caller), 1 = check
 // here, 2 = the face has one (both run reconstruct_tie out of line).
-template <typename R, int DIM, int QF1, int DIRN, int Q, int TIE, bool ISG>
+template <typename R, int DIM, int QF1, int DIRN, int Q, int TIE, int GS, int QG1>
 __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int NH, const int *st,
                                             R uFx, R uFy, R TF, R sTF, R isTF,
                                             Blk<R, Q, (DIM == 2 ? Q : 1)> &out) {
   if constexpr (TIE == 2) {
-    reconstruct_tie<R, DIM, QF1, DIRN, Q, ISG>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, out);
+    reconstruct_tie<R, DIM, QF1, DIRN, Q, GS, QG1>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, out);
     return;
   }
   constexpr int NY = DIM == 2 ? Q : 1;
@@ -646,7 +651,7 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
   }
   if constexpr (TIE == 1) {
     if (tie) {
-      reconstruct_tie<R, DIM, QF1, DIRN, Q, ISG>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, out);
+      reconstruct_tie<R, DIM, QF1, DIRN, Q, GS, QG1>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, out);
       return;
     }
   }
@@ -660,12 +665,12 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
   const bool zt = ODD && is_zero(uFn);
   R Z[NZ], ZD[NZ];
   Blk<R, Q, NY> YL, YR, A;
-  stencil_pops<R, DIM, QF1, Q, ISG>(K, sp, NH, st[0], uFx, uFy, TF, sTF, SK, YL);
-  stencil_pops<R, DIM, QF1, Q, ISG>(K, sp, NH, st[1], uFx, uFy, TF, sTF, SK, YR);
+  stencil_pops<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, st[0], uFx, uFy, TF, sTF, SK, YL);
+  stencil_pops<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, st[1], uFx, uFy, TF, sTF, SK, YR);
   {
     Blk<R, Q, NY> Y1, Y2;
-    stencil_pops<R, DIM, QF1, Q, ISG>(K, sp, NH, st[2], uFx, uFy, TF, sTF, SK, Y1);
-    stencil_pops<R, DIM, QF1, Q, ISG>(K, sp, NH, st[3], uFx, uFy, TF, sTF, SK, Y2);
+    stencil_pops<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, st[2], uFx, uFy, TF, sTF, SK, Y1);
+    stencil_pops<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, st[3], uFx, uFy, TF, sTF, SK, Y2);
 #pragma unroll
     for (int n = 0; n < Q; ++n)
 #pragma unroll
@@ -687,8 +692,8 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
   }
   if constexpr (DIM == 2) {
     Blk<R, Q, NY> Y1, Y2, Dl;
-    stencil_pops<R, DIM, QF1, Q, ISG>(K, sp, NH, st[4], uFx, uFy, TF, sTF, SK, Y1);
-    stencil_pops<R, DIM, QF1, Q, ISG>(K, sp, NH, st[5], uFx, uFy, TF, sTF, SK, Y2);
+    stencil_pops<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, st[4], uFx, uFy, TF, sTF, SK, Y1);
+    stencil_pops<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, st[5], uFx, uFy, TF, sTF, SK, Y2);
 #pragma unroll
     for (int n = 0; n < Q; ++n)
 #pragma unroll
@@ -699,8 +704,8 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
           if (k == KZ && zt) ZD[DIRN == 0 ? m : n] = YL.v[n][m] - Y1.v[n][m];
         }
       }
-    stencil_pops<R, DIM, QF1, Q, ISG>(K, sp, NH, st[6], uFx, uFy, TF, sTF, SK, Y1);
-    stencil_pops<R, DIM, QF1, Q, ISG>(K, sp, NH, st[7], uFx, uFy, TF, sTF, SK, Y2);
+    stencil_pops<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, st[6], uFx, uFy, TF, sTF, SK, Y1);
+    stencil_pops<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, st[7], uFx, uFy, TF, sTF, SK, Y2);
 #pragma unroll
     for (int n = 0; n < Q; ++n)
 #pragma unroll
@@ -757,33 +762,35 @@ __device__ __forceinline__ R gauss_he4(R mu, R dT) {
 // QL: the f-lattice of the face, QF1 or (a multiscale face whose two cells
 // are both on the low-order lattice) 3; the face record keeps the storage
 // layout of QF1, with zero coefficients beyond QL.
-template <typename R, int DIM, int QF1, int DIRN, bool ITER, bool TIE = false, int QL = QF1>
+template <typename R, int DIM, int QF1, int DIRN, bool ITER, bool TIE = false, int QL = QF1, int QG1 = 3>
 __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int NH, const int *st,
                                           R *fp, int NFACES, int fidx, int &ntrace);
 
 // does a node of either lattice other than the zero nodes of D1Q3 and D1Q5
 // (which the trace handles in line) have v_n = 0 exactly in the face frame?
-template <typename R, int QF1>
+template <typename R, int QF1, int QG1 = 3>
 __device__ __forceinline__ bool face_has_tie(R uFn, R sTF) {
   bool t = false;
 #pragma unroll
   for (int k = 0; k < QF1; ++k)
     if (QF1 % 2 == 0 || 2 * k != QF1 - 1) t |= is_zero(sTF * R(Nodes<QF1>::c(k)) + uFn);
 #pragma unroll
-  for (int k = 0; k < 3; k += 2) t |= is_zero(sTF * R(Nodes<3>::c(k)) + uFn);
+  for (int k = 0; k < QG1; ++k)
+    if (QG1 % 2 == 0 || 2 * k != QG1 - 1) t |= is_zero(sTF * R(Nodes<QG1>::c(k)) + uFn);
   return t;
 }
 // the averaged-frame face with a node at v_n = 0, out of line (rare)
-template <typename R, int DIM, int QF1, int DIRN, int QL>
+template <typename R, int DIM, int QF1, int DIRN, int QL, int QG1>
 __device__ __noinline__ bool face_flux_tie(const StepConst &K, const R *sp, int NH, const int *st, R *fp,
                                            int NFACES, int fidx, int &ntrace) {
-  return face_flux<R, DIM, QF1, DIRN, false, true, QL>(K, sp, NH, st, fp, NFACES, fidx, ntrace);
+  return face_flux<R, DIM, QF1, DIRN, false, true, QL, QG1>(K, sp, NH, st, fp, NFACES, fidx, ntrace);
 }
 
-template <typename R, int DIM, int QF1, int DIRN, bool ITER, bool TIE, int QL>
+template <typename R, int DIM, int QF1, int DIRN, bool ITER, bool TIE, int QL, int QG1>
 __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int NH, const int *st,
                                           R *fp, int NFACES, int fidx, int &ntrace) {
-  using D = Dims<DIM, QF1>;
+  static_assert(QL >= QG1, "the equilibrium's Gaussian moments are built to the f-lattice's order");
+  using D = Dims<DIM, QF1, QG1>;
   constexpr int NYF = DIM == 2 ? QL : 1, NYG = D::NYG;
   const int hL = st[0], hR = st[1];
   R uFx = R(0.5) * (sp[D::IUX * NH + hL] + sp[D::IUX * NH + hR]);
@@ -791,13 +798,13 @@ __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int N
   R TF = R(0.5) * (sp[D::IT * NH + hL] + sp[D::IT * NH + hR]);
   R sTF = sqrt(TF), isTF = R(1) / sTF;
   if constexpr (!ITER && !TIE) {
-    if (face_has_tie<R, QL>(DIRN == 0 ? uFx : uFy, sTF))
-      return face_flux_tie<R, DIM, QF1, DIRN, QL>(K, sp, NH, st, fp, NFACES, fidx, ntrace);
+    if (face_has_tie<R, QL, QG1>(DIRN == 0 ? uFx : uFy, sTF))
+      return face_flux_tie<R, DIM, QF1, DIRN, QL, QG1>(K, sp, NH, st, fp, NFACES, fidx, ntrace);
   }
   constexpr int TMODE = ITER ? 1 : (TIE ? 2 : 0);
 
   Blk<R, QL, NYF> Fb;
-  Blk<R, 3, NYG> Gb;
+  Blk<R, QG1, NYG> Gb;
   R rk, mx, my, Tb;
   bool converged = false, noconv = false;
   R pFx = uFx, pFy = uFy, pT = TF;  // previous iterate's frame
@@ -806,10 +813,10 @@ __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int N
   ntrace = 0;
   while (true) {
     ++ntrace;
-    reconstruct<R, DIM, QF1, DIRN, QL, TMODE, false>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, Fb);
-    reconstruct<R, DIM, QF1, DIRN, 3, TMODE, true>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, Gb);
+    reconstruct<R, DIM, QF1, DIRN, QL, TMODE, 0, QG1>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, Fb);
+    reconstruct<R, DIM, QF1, DIRN, QG1, TMODE, 1, QG1>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, Gb);
     anaq_xy(AnaK<R, QL>(TF, sTF), Fb);
-    anaq_xy(AnaK<R, 3>(TF, sTF), Gb);
+    anaq_xy(AnaK<R, QG1>(TF, sTF), Gb);
     // interface moments in the face frame (all carry the factor kappa1): rho,
     // mu = u - u_F, C_v rho T = (sum |v - u_F|^2 f - rho |mu|^2)/2 + sum g
     rk = Fb.v[0][0];
@@ -880,11 +887,11 @@ __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int N
       Fb.v[a][b] += e;
     }
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
+  for (int a = 0; a < QG1; ++a)
 #pragma unroll
     for (int b = 0; b < NYG; ++b) {
       R e = ge * ex[a] * ey[b];
-      if (gk && a + b > 2) e = R(0);
+      if (gk && a + b > QG1 - 1) e = R(0);
       Gb.v[a][b] += e;
     }
   // Appendix C form: transport v_n^{lambda_F} phi in the face frame
@@ -940,9 +947,9 @@ __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int N
       else fp[(a + QF1 * b) * NFACES + fidx] = (a < QL && b < NYF) ? Fb.v[a < QL ? a : 0][b < NYF ? b : 0] : R(0);
     }
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
+  for (int a = 0; a < QG1; ++a)
 #pragma unroll
-    for (int b = 0; b < NYG; ++b) fp[(D::QF + a + 3 * b) * NFACES + fidx] = Gb.v[a][b];
+    for (int b = 0; b < NYG; ++b) fp[(D::QF + a + QG1 * b) * NFACES + fidx] = Gb.v[a][b];
   fp[D::FUX * NFACES + fidx] = uFx;
   fp[D::FUY * NFACES + fidx] = uFy;
   fp[D::FT * NFACES + fidx] = TF;
@@ -960,51 +967,53 @@ struct MomAcc {
 
 // one face's phi (dimensional coefficients in the face frame) moved into the
 // cell frame {u, T} (sT = sqrt T, read by the mixed path's FP64 test only)
-template <typename R, int DIM, int QF1>
+template <typename R, int DIM, int QF1, int QG1>
 __device__ __forceinline__ void face_contrib_body(const StepConst &K, const R *fp, int NFACES, int fidx,
-                                                  R ux, R uy, R T, R sT,
-                                                  Blk<R, QF1, Dims<DIM, QF1>::NYF> &X, Blk<R, 3, Dims<DIM, QF1>::NYG> &Y) {
-  using D = Dims<DIM, QF1>;
+                                                  R ux, R uy, R T, R sT, Blk<R, QF1, Dims<DIM, QF1>::NYF> &X,
+                                                  Blk<R, QG1, Dims<DIM, QF1, QG1>::NYG> &Y) {
+  using D = Dims<DIM, QF1, QG1>;
 #pragma unroll
   for (int a = 0; a < QF1; ++a)
 #pragma unroll
     for (int b = 0; b < D::NYF; ++b) X.v[a][b] = fp[(a + QF1 * b) * NFACES + fidx];
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
+  for (int a = 0; a < QG1; ++a)
 #pragma unroll
-    for (int b = 0; b < D::NYG; ++b) Y.v[a][b] = fp[(D::QF + a + 3 * b) * NFACES + fidx];
+    for (int b = 0; b < D::NYG; ++b) Y.v[a][b] = fp[(D::QF + a + QG1 * b) * NFACES + fidx];
   const R uFx = fp[D::FUX * NFACES + fidx], uFy = fp[D::FUY * NFACES + fidx];
   const R TF = fp[D::FT * NFACES + fidx];
   const R sTF = is_mixed<R>() ? fp[D::FST * NFACES + fidx] : R(0);
   move_frame<R, DIM, QF1>(K, uFx, uFy, TF, sTF, ux, uy, T, sT, X);
-  move_frame<R, DIM, 3>(K, uFx, uFy, TF, sTF, ux, uy, T, sT, Y);
+  move_frame<R, DIM, QG1>(K, uFx, uFy, TF, sTF, ux, uy, T, sT, Y);
   if constexpr (DIM == 2) {
     if (K.grad_k) { grad_mask(X); grad_mask(Y); }
   }
 }
 // The mixed path moves a face's phi in one out-of-line copy (returned by
 // value, in registers), like the stencil transformation.
-template <typename R, int DIM, int QF1> struct FaceContrib {
+template <typename R, int DIM, int QF1, int QG1> struct FaceContrib {
   Blk<R, QF1, Dims<DIM, QF1>::NYF> X;
-  Blk<R, 3, Dims<DIM, QF1>::NYG> Y;
+  Blk<R, QG1, Dims<DIM, QF1, QG1>::NYG> Y;
 };
-template <typename R, int DIM, int QF1>
-__device__ __noinline__ FaceContrib<R, DIM, QF1> face_contrib_call(const StepConst &K, const R *fp, int NFACES,
-                                                              int fidx, R ux, R uy, R T, R sT) {
-  FaceContrib<R, DIM, QF1> c;
-  face_contrib_body<R, DIM, QF1>(K, fp, NFACES, fidx, ux, uy, T, sT, c.X, c.Y);
+template <typename R, int DIM, int QF1, int QG1>
+__device__ __noinline__ FaceContrib<R, DIM, QF1, QG1> face_contrib_call(const StepConst &K, const R *fp,
+                                                                      int NFACES, int fidx, R ux, R uy, R T,
+                                                                      R sT) {
+  FaceContrib<R, DIM, QF1, QG1> c;
+  face_contrib_body<R, DIM, QF1, QG1>(K, fp, NFACES, fidx, ux, uy, T, sT, c.X, c.Y);
   return c;
 }
-template <typename R, int DIM, int QF1>
+template <typename R, int DIM, int QF1, int QG1>
 __device__ __forceinline__ void face_contrib(const StepConst &K, const R *fp, int NFACES, int fidx, R ux,
                                              R uy, R T, R sT, Blk<R, QF1, Dims<DIM, QF1>::NYF> &X,
-                                             Blk<R, 3, Dims<DIM, QF1>::NYG> &Y) {
+                                             Blk<R, QG1, Dims<DIM, QF1, QG1>::NYG> &Y) {
   if constexpr (is_mixed<R>()) {
-    const FaceContrib<R, DIM, QF1> c = face_contrib_call<R, DIM, QF1>(K, fp, NFACES, fidx, ux, uy, T, sT);
+    const FaceContrib<R, DIM, QF1, QG1> c =
+        face_contrib_call<R, DIM, QF1, QG1>(K, fp, NFACES, fidx, ux, uy, T, sT);
     X = c.X;
     Y = c.Y;
   } else {
-    face_contrib_body<R, DIM, QF1>(K, fp, NFACES, fidx, ux, uy, T, sT, X, Y);
+    face_contrib_body<R, DIM, QF1, QG1>(K, fp, NFACES, fidx, ux, uy, T, sT, X, Y);
   }
 }
 
@@ -1015,21 +1024,22 @@ __device__ __forceinline__ void face_contrib(const StepConst &K, const R *fp, in
 // the Appendix C form.
 // (MS, low: the fluxes are projected onto the cell's low-order lattice before
 // the multiplication by v_n, which on that lattice has no order-3 term.)
-template <typename R, int DIM, int QF1, int DIRN, bool MS = false>
+template <typename R, int DIM, int QF1, int DIRN, bool MS = false, int QG1 = 3>
 __device__ __forceinline__ void add_faces(const StepConst &K, const R *fp, int NFACES, int flo, int fhi,
                                           R ux, R uy, R T, R sT, Blk<R, QF1, Dims<DIM, QF1>::NYF> &F,
-                                          Blk<R, 3, Dims<DIM, QF1>::NYG> &G, MomAcc &M, bool low = false) {
-  using D = Dims<DIM, QF1>;
+                                          Blk<R, QG1, Dims<DIM, QF1, QG1>::NYG> &G, MomAcc &M,
+                                          bool low = false) {
+  using D = Dims<DIM, QF1, QG1>;
   Blk<R, QF1, D::NYF> DX, X;
-  Blk<R, 3, D::NYG> DY, Y;
-  face_contrib<R, DIM, QF1>(K, fp, NFACES, flo, ux, uy, T, sT, DX, DY);
-  face_contrib<R, DIM, QF1>(K, fp, NFACES, fhi, ux, uy, T, sT, X, Y);
+  Blk<R, QG1, D::NYG> DY, Y;
+  face_contrib<R, DIM, QF1, QG1>(K, fp, NFACES, flo, ux, uy, T, sT, DX, DY);
+  face_contrib<R, DIM, QF1, QG1>(K, fp, NFACES, fhi, ux, uy, T, sT, X, Y);
 #pragma unroll
   for (int p = 0; p < QF1; ++p)
 #pragma unroll
     for (int q = 0; q < D::NYF; ++q) DX.v[p][q] = X.v[p][q] - DX.v[p][q];
 #pragma unroll
-  for (int p = 0; p < 3; ++p)
+  for (int p = 0; p < QG1; ++p)
 #pragma unroll
     for (int q = 0; q < D::NYG; ++q) DY.v[p][q] = Y.v[p][q] - DY.v[p][q];
   if constexpr (MS) {
@@ -1046,7 +1056,7 @@ __device__ __forceinline__ void add_faces(const StepConst &K, const R *fp, int N
 #pragma unroll
     for (int q = 0; q < D::NYF; ++q) F.v[p][q] = fma(ml, DX.v[p][q], F.v[p][q]);
 #pragma unroll
-  for (int p = 0; p < 3; ++p)
+  for (int p = 0; p < QG1; ++p)
 #pragma unroll
     for (int q = 0; q < D::NYG; ++q) G.v[p][q] = fma(ml, DY.v[p][q], G.v[p][q]);
   if constexpr (is_mixed<R>()) {
@@ -1060,20 +1070,20 @@ __device__ __forceinline__ void add_faces(const StepConst &K, const R *fp, int N
   }
 }
 
-template <typename R, int DIM, int QF1, int BX, int BY, bool MS = false>
+template <typename R, int DIM, int QF1, int BX, int BY, bool MS = false, int QG1 = 3>
 __device__ __forceinline__ void update_cell(const StepConst &K, const State<R> &S, const State<R> &O,
                                             const R *fp, int cx, int cy, int j, int k, R &vmax,
                                             unsigned &flags, bool low = false) {
-  using D = Dims<DIM, QF1>;
-  using TL = Tile<DIM, BX, BY, QF1>;
+  using D = Dims<DIM, QF1, QG1>;
+  using TL = Tile<DIM, BX, BY, QF1, QG1>;
   const size_t N = (size_t)K.nx * (DIM == 2 ? K.ny : 1);
   const size_t c = (size_t)k * K.nx + j;
   Blk<R, QF1, D::NYF> F;
-  Blk<R, 3, D::NYG> G;
+  Blk<R, QG1, D::NYG> G;
 #pragma unroll
   for (int i = 0; i < D::QF; ++i) F.v[i % QF1][i / QF1] = S.f[i * N + c];
 #pragma unroll
-  for (int i = 0; i < D::QG; ++i) G.v[i % 3][i / 3] = S.g[i * N + c];
+  for (int i = 0; i < D::QG; ++i) G.v[i % QG1][i / QG1] = S.g[i * N + c];
   const R ux = S.ux[c], uy = DIM == 2 ? S.uy[c] : R(0), T = S.T[c];
   const R sT = is_mixed<R>() ? sqrt(T) : R(0);
   if constexpr (MS) {
@@ -1097,14 +1107,14 @@ __device__ __forceinline__ void update_cell(const StepConst &K, const State<R> &
 #pragma unroll
     for (int b = 0; b < D::NYF; ++b) F.v[a][b] *= a1;
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
+  for (int a = 0; a < QG1; ++a)
 #pragma unroll
     for (int b = 0; b < D::NYG; ++b) G.v[a][b] *= a1;
   // fluxes through the faces, in a fixed order: x, then y
-  add_faces<R, DIM, QF1, 0, MS>(K, fp, TL::NFACES, cy * (BX + 1) + cx, cy * (BX + 1) + cx + 1, ux, uy, T, sT, F,
+  add_faces<R, DIM, QF1, 0, MS, QG1>(K, fp, TL::NFACES, cy * (BX + 1) + cx, cy * (BX + 1) + cx + 1, ux, uy, T, sT, F,
                                 G, M, low);
   if constexpr (DIM == 2)
-    add_faces<R, DIM, QF1, 1, MS>(K, fp, TL::NFACES, TL::NFX + cy * BX + cx, TL::NFX + (cy + 1) * BX + cx, ux, uy,
+    add_faces<R, DIM, QF1, 1, MS, QG1>(K, fp, TL::NFACES, TL::NFX + cy * BX + cx, TL::NFX + (cy + 1) * BX + cx, ux, uy,
                                   T, sT, F, G, M, low);
   F.v[0][0] += kc<R>(K.a2, K.cf.a2) * rho;
   G.v[0][0] += kc<R>(K.a2, K.cf.a2) * kc<R>(K.gfac, K.cf.gfac) * T * rho;
@@ -1152,7 +1162,7 @@ __device__ __forceinline__ void update_cell(const StepConst &K, const State<R> &
     if (ok) {
       const R sTn = sqrt(Tout);
       move_frame<R, DIM, QF1>(K, ux, uy, T, sT, uxn, uyn, Tout, sTn, F);
-      move_frame<R, DIM, 3>(K, ux, uy, T, sT, uxn, uyn, Tout, sTn, G);
+      move_frame<R, DIM, QG1>(K, ux, uy, T, sT, uxn, uyn, Tout, sTn, G);
     }
   }
   if (ok) {
@@ -1172,7 +1182,7 @@ __device__ __forceinline__ void update_cell(const StepConst &K, const State<R> &
 #pragma unroll
   for (int i = 0; i < D::QF; ++i) O.f[i * N + c] = F.v[i % QF1][i / QF1];
 #pragma unroll
-  for (int i = 0; i < D::QG; ++i) O.g[i * N + c] = G.v[i % 3][i / 3];
+  for (int i = 0; i < D::QG; ++i) O.g[i * N + c] = G.v[i % QG1][i / QG1];
   O.ux[c] = uxn;
   if constexpr (DIM == 2) O.uy[c] = uyn;
   O.T[c] = Tout;
@@ -1190,11 +1200,11 @@ __device__ __forceinline__ void update_cell(const StepConst &K, const State<R> &
 // given instantiation the result does not depend on the launch order or on
 // which tile a cell falls in (different tile shapes are different machine
 // code and may round differently).
-template <typename R, int DIM, int QF1, int BX, int BY, int NT, bool ITER, bool MS = false>
+template <typename R, int DIM, int QF1, int BX, int BY, int NT, bool ITER, bool MS = false, int QG1 = 3>
 __device__ __forceinline__ void step_tile(const StepConst &K, const State<R> &S, const State<R> &O,
                                           Stats *stats, int j0, int k0, unsigned char *smem) {
-  using D = Dims<DIM, QF1>;
-  using TL = Tile<DIM, BX, BY, QF1>;
+  using D = Dims<DIM, QF1, QG1>;
+  using TL = Tile<DIM, BX, BY, QF1, QG1>;
   R *sp = reinterpret_cast<R *>(smem);
   R *fp = sp + (size_t)TL::NH * D::NPREP;
   const int tid = threadIdx.x;
@@ -1202,7 +1212,7 @@ __device__ __forceinline__ void step_tile(const StepConst &K, const State<R> &S,
   // A. halo tile
   for (int h = tid; h < TL::NH; h += NT) {
     const int hx = h % TL::HX, hy = h / TL::HX;
-    prep_cell<R, DIM, QF1, MS>(K, S, j0 + hx - 2, k0 + hy - TL::OY, sp, TL::NH, h);
+    prep_cell<R, DIM, QF1, MS, QG1>(K, S, j0 + hx - 2, k0 + hy - TL::OY, sp, TL::NH, h);
   }
   __syncthreads();
 
@@ -1224,11 +1234,11 @@ __device__ __forceinline__ void step_tile(const StepConst &K, const State<R> &S,
       bool nc;
       if constexpr (MS) {  // the face's f-lattice: the higher of its two cells'
         if (sp[D::IST * TL::NH + st[0]] == R(0) && sp[D::IST * TL::NH + st[1]] == R(0))
-          nc = face_flux<R, DIM, QF1, 0, ITER, false, 3>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
+          nc = face_flux<R, DIM, QF1, 0, ITER, false, 3, QG1>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
         else
-          nc = face_flux<R, DIM, QF1, 0, ITER>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
+          nc = face_flux<R, DIM, QF1, 0, ITER, false, QF1, QG1>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
       } else {
-        nc = face_flux<R, DIM, QF1, 0, ITER>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
+        nc = face_flux<R, DIM, QF1, 0, ITER, false, QF1, QG1>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
       }
       if (ITER && (fx > 0 || j0 == 0)) {
         noconv += nc; traces += nt; ++evals; max_tr = max(max_tr, (unsigned)nt);
@@ -1244,11 +1254,11 @@ __device__ __forceinline__ void step_tile(const StepConst &K, const State<R> &S,
       bool nc;
       if constexpr (MS) {  // the face's f-lattice: the higher of its two cells'
         if (sp[D::IST * TL::NH + st[0]] == R(0) && sp[D::IST * TL::NH + st[1]] == R(0))
-          nc = face_flux<R, DIM, QF1, 1, ITER, false, 3>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
+          nc = face_flux<R, DIM, QF1, 1, ITER, false, 3, QG1>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
         else
-          nc = face_flux<R, DIM, QF1, 1, ITER>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
+          nc = face_flux<R, DIM, QF1, 1, ITER, false, QF1, QG1>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
       } else {
-        nc = face_flux<R, DIM, QF1, 1, ITER>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
+        nc = face_flux<R, DIM, QF1, 1, ITER, false, QF1, QG1>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
       }
       if (ITER && (fy > 0 || k0 == 0)) {
         noconv += nc; traces += nt; ++evals; max_tr = max(max_tr, (unsigned)nt);
@@ -1269,7 +1279,7 @@ __device__ __forceinline__ void step_tile(const StepConst &K, const State<R> &S,
       low = sp[D::IST * TL::NH + (cy + TL::OY) * TL::HX + cx + 2] == R(0);
       nhigh += !low;
     }
-    update_cell<R, DIM, QF1, BX, BY, MS>(K, S, O, fp, cx, cy, j, k, vmax, flags, low);
+    update_cell<R, DIM, QF1, BX, BY, MS, QG1>(K, S, O, fp, cx, cy, j, k, vmax, flags, low);
   }
   double cfl = (double)vmax * K.lam;
   // warp reduction of the CFL number, flags and counts, one atomic per warp

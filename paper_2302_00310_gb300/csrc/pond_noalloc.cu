@@ -114,7 +114,7 @@ bool params_ok(const pond_params *p, int D) {
   return p->precision == POND_FP64 && (p->transform == POND_TENSOR || p->transform == POND_GRAD_K) &&
          (p->flux_form == POND_FLUX_MAIN || p->flux_form == POND_FLUX_APPC) &&
          (p->limiter == POND_VANLEER || p->limiter == POND_MINMOD) &&
-         p->flux_frame == POND_FRAME_AVG && p->multiscale == 0;
+         p->flux_frame == POND_FRAME_AVG && p->multiscale == 0 && p->g_same_as_f == 0;
 }
 
 // the constants of one step (same definitions as the context path)

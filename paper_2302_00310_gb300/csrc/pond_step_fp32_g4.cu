@@ -1,0 +1,5 @@
+// pond_step_fp32_g4.cu -- the mixed-precision instantiations of the member
+// step kernel with the g-populations on the f-lattice (D1Q4 / D2Q16).
+#include "pond_step_impl.cuh"
+
+pond::Shape pond_g4_shape_fp32(int D) { return pond::g4_shape<float>(D); }

@@ -10,7 +10,8 @@ namespace pond {
 // tiles [tile_begin_i, tile_begin_i + tiles_i) and advances iff k < steps_i,
 // from buffer (parity_i + k) & 1 into the other, with its own constants and
 // status block.  A one-member table with one CTA per tile is a plain step.
-template <typename R, int DIM, int QF1, int BX, int BY, int NT, int MINB, bool ITER, bool MS = false>
+template <typename R, int DIM, int QF1, int BX, int BY, int NT, int MINB, bool ITER, bool MS = false,
+          int QG1 = 3>
 __global__ void __launch_bounds__(NT, MINB) member_step_kernel(const unsigned char *table, int k) {
   const TableHdr *H = reinterpret_cast<const TableHdr *>(table);
   const InstDesc<R> *desc = reinterpret_cast<const InstDesc<R> *>(table + sizeof(TableHdr));
@@ -44,31 +45,32 @@ __global__ void __launch_bounds__(NT, MINB) member_step_kernel(const unsigned ch
       // alias the table as far as the compiler knows, forcing reloads
       const State<R> S = d.S[p], O = d.S[p ^ 1];
       Stats *const st = d.stats;
-      step_tile<R, DIM, QF1, BX, BY, NT, ITER, MS>(Ks, S, O, st, (lt % tx) * BX,
-                                                   DIM == 2 ? (lt / tx) * BY : 0, smem_raw);
+      step_tile<R, DIM, QF1, BX, BY, NT, ITER, MS, QG1>(Ks, S, O, st, (lt % tx) * BX,
+                                                        DIM == 2 ? (lt / tx) * BY : 0, smem_raw);
     }
     __syncthreads();  // s_inst, Ks and the tile's shared memory are reused
   }
 }
 
-template <typename R, int DIM, int BX, int BY, int NT, int MINB, bool ITER, int QF1 = 4, bool MS = false>
+template <typename R, int DIM, int BX, int BY, int NT, int MINB, bool ITER, int QF1 = 4, bool MS = false,
+          int QG1 = 3>
 Shape make_shape(int code) {
   Shape s;
   s.code = code;
   s.bx = BX;
   s.by = BY;
   s.prepare = [](int *ctas) -> cudaError_t {
-    constexpr size_t smem = Tile<DIM, BX, BY, QF1>::template smem_bytes<R>();
+    constexpr size_t smem = Tile<DIM, BX, BY, QF1, QG1>::template smem_bytes<R>();
     static_assert(smem + sizeof(StepConst) + 16 <= 227 * 1024, "tile too large for shared memory");
-    cudaError_t e = cudaFuncSetAttribute(member_step_kernel<R, DIM, QF1, BX, BY, NT, MINB, ITER, MS>,
+    cudaError_t e = cudaFuncSetAttribute(member_step_kernel<R, DIM, QF1, BX, BY, NT, MINB, ITER, MS, QG1>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        ctas, member_step_kernel<R, DIM, QF1, BX, BY, NT, MINB, ITER, MS>, NT, smem);
+        ctas, member_step_kernel<R, DIM, QF1, BX, BY, NT, MINB, ITER, MS, QG1>, NT, smem);
   };
   s.launch = [](const unsigned char *table, int k, int grid, cudaStream_t st) {
-    constexpr size_t smem = Tile<DIM, BX, BY, QF1>::template smem_bytes<R>();
-    member_step_kernel<R, DIM, QF1, BX, BY, NT, MINB, ITER, MS><<<grid, NT, smem, st>>>(table, k);
+    constexpr size_t smem = Tile<DIM, BX, BY, QF1, QG1>::template smem_bytes<R>();
+    member_step_kernel<R, DIM, QF1, BX, BY, NT, MINB, ITER, MS, QG1><<<grid, NT, smem, st>>>(table, k);
   };
   return s;
 }
@@ -101,6 +103,15 @@ template <typename R> Shape iter_shape(int D) {
 template <typename R> Shape ms_shape(int D) {
   if (D == 1) return make_shape<R, 1, 252, 1, 256, 1, false, 4, true>(1);
   return make_shape<R, 2, 8, 14, 128, 2, false, 4, true>(10);
+}
+
+// g on the f-lattice (D1Q4 / D2Q16): the default tiles of each precision,
+// 8x14 with 128 threads and two CTAs per SM (FP64), 8x16 with 160 threads
+// and two CTAs per SM (mixed), 252 cells in 1D
+template <typename R> Shape g4_shape(int D) {
+  if (D == 1) return make_shape<R, 1, 252, 1, 256, 1, false, 4, false, 4>(1);
+  if constexpr (std::is_same<R, float>::value) return make_shape<R, 2, 8, 16, 160, 2, false, 4, false, 4>(6);
+  else return make_shape<R, 2, 8, 14, 128, 2, false, 4, false, 4>(10);
 }
 
 }  // namespace pond

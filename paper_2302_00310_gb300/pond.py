@@ -49,7 +49,7 @@ class pond_params(ctypes.Structure):
         ("flux_frame", ctypes.c_int32), ("iter_tol", ctypes.c_double),
         ("iter_max", ctypes.c_int32), ("xi_fp64_threshold", ctypes.c_double),
         ("tile", ctypes.c_int32), ("multiscale", ctypes.c_int32), ("ms_theta_u", ctypes.c_double),
-        ("ms_theta_T", ctypes.c_double),
+        ("ms_theta_T", ctypes.c_double), ("g_same_as_f", ctypes.c_int32),
     ]
 
 
@@ -364,6 +364,7 @@ def params_from_config(cfg: dict) -> pond_params:
     p.tile = int(cfg.get("tile", 0))
     p.multiscale = int(cfg.get("ms", 0))
     p.ms_theta_u, p.ms_theta_T = float(cfg.get("ms_theta_u", 0.0)), float(cfg.get("ms_theta_T", 0.0))
+    p.g_same_as_f = 1 if int(cfg.get("qg", 3)) == 4 else 0
     return p
 
 
@@ -401,7 +402,8 @@ class Sim:
 
     @property
     def Qg(self):
-        return 9 if self.D == 2 else 3
+        q = 4 if int(self.cfg.get("qg", 3)) == 4 else 3
+        return q * q if self.D == 2 else q
 
     def init(self, rho, ux, uy, T):
         a = [np.ascontiguousarray(np.broadcast_to(np.asarray(x, dtype=np.float64), self.shape))

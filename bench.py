@@ -629,6 +629,11 @@ def run_gpu(args, dist, rank, ws):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     pond.lib(build=True)
+    if args.extra:
+        if rank == 0:
+            fn = {"riemann": bench_riemann, "d2q25": bench_d2q25, "multiscale": bench_multiscale}[args.extra]
+            print(json.dumps(dict(extra=args.extra, **fn(torch, pond, W))), flush=True)
+        return
     w = W.pulse_2d(n=256, seed=0)
     fp32 = args.precision == "fp32"
     cfg = dict(w["cfg"], precision=pond.POND_FP32_MIXED if fp32 else pond.POND_FP64)
@@ -748,6 +753,8 @@ def main():
                     help="skip the accuracy studies (iterated face frame, thermal Couette)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
                     help="arithmetic of the main line (fp32 = the mixed path)")
+    ap.add_argument("--extra", default=None, choices=["riemann", "d2q25", "multiscale"],
+                    help="run only this one extra measurement and print its JSON line (for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

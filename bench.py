@@ -400,6 +400,27 @@ def bench_multiscale(torch, pond, W, steps=200, theta=0.05):
             out[name]["high_fraction"] = sim.ms_stats() / (n * steps)
         sim.close()
     out["l1_rho_multiscale_vs_d2q16"] = _l1(mom["multiscale"][0], mom["d2q16"][0])
+    # the mixed path runs the multiscale lattice in Appendix C's flux form: both precisions in it,
+    # beside the mixed D2Q16 kernel in the same form
+    appc = {}
+    for name, prec, ms_on in (("fp64", pond.POND_FP64, 1), ("fp32_mixed", pond.POND_FP32_MIXED, 1),
+                              ("fp32_mixed_d2q16", pond.POND_FP32_MIXED, 0)):
+        extra = dict(ms=1, ms_theta_u=theta, ms_theta_T=theta) if ms_on else {}
+        sim = pond.Sim(dict(w["cfg"], flux_appc=1, precision=prec, **extra))
+        sim.init(*fields)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(sim.stream):
+            e0.record(sim.stream)
+            pond.pond_step(sim.ctx, steps)
+            e1.record(sim.stream)
+        sim.stream.synchronize()
+        ms = e0.elapsed_time(e1)
+        appc[name] = sim.moments()
+        out["appc_" + name] = {"value": n * steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / steps,
+                               "tile": sim.info()[2], "high_fraction": sim.ms_stats() / (n * steps),
+                               "nonphysical": bool(sim.flags()[1] & 1)}
+        sim.close()
+    out["l1_rho_appc_multiscale_fp32_vs_fp64"] = _l1(appc["fp32_mixed"][0], appc["fp64"][0])
     left, right = (0.445, 0.698, 3.528), (0.5, 0.0, 0.571)
     lax = W.lax_1d(n=600)
     exact = solution(left, right, lax["x"], lax["t_end"])[0]

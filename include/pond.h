@@ -153,11 +153,13 @@ typedef struct {
    * lifting sets the moments the low lattice lacks to their equilibrium
    * values, and the odd central moments of a Gaussian vanish.  A cell that
    * turns low drops them (the projection).  A face takes the higher lattice
-   * of its two cells.  Requires D1Q4 / D2Q16, FP64, Pr = 1, the averaged face
-   * frame, no walls and tile 0 (or the FP64 default, 1 in 1D and 10 in 2D);
-   * not batched.  With the main flux form a low cell keeps mass and momentum
-   * but not energy exactly (its lattice lacks the third-order moment the
-   * energy flux needs in another frame); Appendix C's form keeps all three. */
+   * of its two cells.  Requires D1Q4 / D2Q16, Pr = 1, the averaged face
+   * frame, no walls and tile 0 (or the precision's default: 1 in 1D; 10 FP64,
+   * 6 mixed in 2D); not batched.  With the main flux form a low cell keeps
+   * mass and momentum but not energy exactly (its lattice lacks the
+   * third-order moment the energy flux needs in another frame); Appendix C's
+   * form keeps all three, and the mixed path, whose conserved fluxes are
+   * evaluated once per face in the face frame, requires it. */
   int32_t multiscale;
   double ms_theta_u;       /* thresholds on s_u and s_T (the paper states none) */
   double ms_theta_T;

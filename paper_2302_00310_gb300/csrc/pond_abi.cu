@@ -161,7 +161,7 @@ unsigned grid1(size_t n, unsigned b) { return (unsigned)((n + b - 1) / b); }
 // stream capture) and uploads the table.  Called whenever K changes.
 pond_status prepare_step(pond_ctx *c) {
   if (c->K.ms) {
-    c->shape = pond_ms_shape_fp64(c->D);
+    c->shape = c->fp32 ? pond_ms_shape_fp32(c->D) : pond_ms_shape_fp64(c->D);
   } else if (c->qg1 == 4) {
     c->shape = c->fp32 ? pond_g4_shape_fp32(c->D) : pond_g4_shape_fp64(c->D);
   } else if (c->K.iterative) {
@@ -241,8 +241,9 @@ bool valid_params(const pond_params *p) {
   if (p->tile < 0 || p->tile > 10) return false;
   if (p->multiscale != 0 && p->multiscale != 1) return false;
   if (p->g_same_as_f != 0 && p->g_same_as_f != 1) return false;
-  if (p->multiscale) {  // D1Q3/D1Q4 and D2Q9/D2Q16, FP64, BGK, averaged frame, no walls
-    if (p->precision != POND_FP64 || p->prandtl != 1.0 || p->flux_frame != POND_FRAME_AVG) return false;
+  if (p->multiscale) {  // D1Q3/D1Q4 and D2Q9/D2Q16, BGK, averaged frame, no walls; mixed: App. C form
+    if (p->prandtl != 1.0 || p->flux_frame != POND_FRAME_AVG) return false;
+    if (p->precision == POND_FP32_MIXED && p->flux_form != POND_FLUX_APPC) return false;
     if (std::isnan(p->ms_theta_u) || std::isnan(p->ms_theta_T)) return false;
     for (int s = 0; s < 4; ++s)
       if (p->bc[s] == POND_BC_WALL) return false;
@@ -443,7 +444,8 @@ pond_status pond_create(pond_ctx **out, pond_lattice lat, const int64_t dims[2],
   if (D == 1 && p->tile > 1) return POND_E_INVAL;
   if (D == 2 && p->tile == 1) return POND_E_INVAL;
   if (lat == POND_D2Q25 && p->tile != 0 && p->tile != 2) return POND_E_INVAL;
-  if (p->multiscale && (lat == POND_D2Q25 || (p->tile != 0 && p->tile != (D == 1 ? 1 : 10))))
+  if (p->multiscale && (lat == POND_D2Q25 ||
+                        (p->tile != 0 && p->tile != (D == 1 ? 1 : (p->precision == POND_FP64 ? 10 : 6)))))
     return POND_E_INVAL;
   if (p->g_same_as_f && (lat == POND_D2Q25 || p->multiscale || p->flux_frame != POND_FRAME_AVG ||
                          (p->tile != 0 && p->tile != (D == 1 ? 1 : (p->precision == POND_FP64 ? 10 : 6)))))

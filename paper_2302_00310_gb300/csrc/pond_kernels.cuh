@@ -117,9 +117,11 @@ template <int DIM, int BX, int BY, int QF1 = 4, int QG1 = 3> struct Tile {
   static constexpr int NFY = DIM == 2 ? BX * (BY + 1) : 0;
   static constexpr int NFACES = NFX + NFY;
   static constexpr int NCELL = BX * (DIM == 2 ? BY : 1);
-  template <typename R> static constexpr size_t smem_bytes() {
+  // MS: a byte per halo cell after the face records, its multiscale lattice
+  template <typename R, bool MS = false> static constexpr size_t smem_bytes() {
     return sizeof(R) * ((size_t)NH * Dims<DIM, QF1, QG1>::NPREP +
-                        (size_t)NFACES * Dims<DIM, QF1, QG1>::template nface<R>());
+                        (size_t)NFACES * Dims<DIM, QF1, QG1>::template nface<R>()) +
+           (MS ? ((size_t)NH + 15) / 16 * 16 : 0);
   }
 };
 
@@ -408,8 +410,8 @@ __device__ __noinline__ void prep_wall_cell(const StepConst &K, const State<R> &
 // takes the higher lattice of its two cells.
 
 // u_x, u_y, T at index (j, k): an interior cell or its ghost (no walls)
-template <int DIM>
-__device__ __forceinline__ void ms_fields(const StepConst &K, const State<double> &S, int j, int k,
+template <int DIM, typename R>
+__device__ __forceinline__ void ms_fields(const StepConst &K, const State<R> &S, int j, int k,
                                           double &ux, double &uy, double &T) {
   int sj = 0, sk = 0;
   const int side = map_cell<DIM>(K, j, k, sj, sk);
@@ -417,12 +419,12 @@ __device__ __forceinline__ void ms_fields(const StepConst &K, const State<double
     ux = K.inflow[side][1]; uy = DIM == 2 ? K.inflow[side][2] : 0.0; T = K.inflow[side][3];
   } else {
     const size_t c = (size_t)sk * K.nx + sj;
-    ux = S.ux[c]; uy = DIM == 2 ? S.uy[c] : 0.0; T = S.T[c];
+    ux = (double)S.ux[c]; uy = DIM == 2 ? (double)S.uy[c] : 0.0; T = (double)S.T[c];
   }
 }
 // the lattice of interior cell (j, k) this step: true = high order
-template <int DIM>
-__device__ __noinline__ bool ms_high(const StepConst &K, const State<double> &S, int j, int k) {
+template <int DIM, typename R>
+__device__ __noinline__ bool ms_high(const StepConst &K, const State<R> &S, int j, int k) {
   double gu = 0.0, gT = 0.0;
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
@@ -433,7 +435,7 @@ __device__ __noinline__ bool ms_high(const StepConst &K, const State<double> &S,
     if (DIM == 2) gu = fmax(gu, fabs(puy - muy));
     gT = fmax(gT, fabs(pT - mT));
   }
-  const double T = S.T[(size_t)k * K.nx + j];
+  const double T = (double)S.T[(size_t)k * K.nx + j];
   return 0.5 * gu / sqrt(T) > K.ms_theta_u || 0.5 * gT / T > K.ms_theta_T;
 }
 // projection onto the low-order lattice: coefficients of order 3 along an
@@ -448,12 +450,10 @@ __device__ __forceinline__ void ms_project(Blk<R, Q, NY> &B, int grad_k) {
 }
 
 // ---- phase A: one halo cell -> shared memory ------------------------------
-// MS: multiscale; the cell's lattice goes to the IST slot (1 high, 0 low),
-// which only the mixed path otherwise uses.
+// MS: multiscale; the cell's lattice goes to lat[h] (1 high, 0 low).
 template <typename R, int DIM, int QF1, bool MS = false, int QG1 = 3>
 __device__ __forceinline__ void prep_cell(const StepConst &K, const State<R> &S, int j, int k, R *sp,
-                                          int NH, int h) {
-  static_assert(!MS || !std::is_same<R, float>::value, "multiscale runs in FP64");
+                                          int NH, int h, unsigned char *lat = nullptr) {
   using D = Dims<DIM, QF1, QG1>;
   Blk<R, QF1, D::NYF> F;
   Blk<R, QG1, D::NYG> G;
@@ -477,7 +477,7 @@ __device__ __forceinline__ void prep_cell(const StepConst &K, const State<R> &S,
     if constexpr (MS) {
       const bool hi = ms_high<DIM>(K, S, sj, sk);
       if (!hi) ms_project(F, K.grad_k);
-      sp[D::IST * NH + h] = hi ? R(1) : R(0);
+      lat[h] = hi ? 1 : 0;
     }
     qe_scale(F, G, kc<R>(K.qe, K.cf.qe));
     const R rho = F.v[0][0], ka = kc<R>(K.kp_a, K.cf.kp_a);
@@ -493,7 +493,7 @@ __device__ __forceinline__ void prep_cell(const StepConst &K, const State<R> &S,
     F.v[0][0] = kc<R>(K.kappa1, K.cf.kappa1) * rho;
     G.v[0][0] += kc<R>(K.kp_b, K.cf.kp_b) * kc<R>(K.gfac, K.cf.gfac) * T * rho;
   } else {
-    if constexpr (MS) sp[D::IST * NH + h] = R(0);  // an inflow ghost: equilibrium, either lattice
+    if constexpr (MS) lat[h] = 0;  // an inflow ghost: equilibrium, either lattice
     const R rho = R(K.inflow[side][0]);
     ux = R(K.inflow[side][1]);
     uy = DIM == 2 ? R(K.inflow[side][2]) : R(0);
@@ -913,6 +913,8 @@ __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int N
     if (K.appc) {  // Fb, Gb already hold v_n phi
       C00 = Fb.v[0][0]; C10 = Fb.v[1][0]; C20 = Fb.v[2][0]; CG = Gb.v[0][0];
       if constexpr (DIM == 2) { C01 = Fb.v[0][1]; C02 = Fb.v[0][2]; }
+    } else if constexpr (QL < 4) {
+      C00 = C10 = C20 = CG = R(0);  // not reached: a multiscale mixed path runs Appendix C's form
     } else if constexpr (DIRN == 0) {
       C00 = fma(un, Fb.v[0][0], Fb.v[1][0]);
       C10 = fma(un, Fb.v[1][0], fma(TF, Fb.v[0][0], Fb.v[2][0]));
@@ -1207,12 +1209,13 @@ __device__ __forceinline__ void step_tile(const StepConst &K, const State<R> &S,
   using TL = Tile<DIM, BX, BY, QF1, QG1>;
   R *sp = reinterpret_cast<R *>(smem);
   R *fp = sp + (size_t)TL::NH * D::NPREP;
+  unsigned char *lat = reinterpret_cast<unsigned char *>(fp + (size_t)TL::NFACES * D::template nface<R>());
   const int tid = threadIdx.x;
 
   // A. halo tile
   for (int h = tid; h < TL::NH; h += NT) {
     const int hx = h % TL::HX, hy = h / TL::HX;
-    prep_cell<R, DIM, QF1, MS, QG1>(K, S, j0 + hx - 2, k0 + hy - TL::OY, sp, TL::NH, h);
+    prep_cell<R, DIM, QF1, MS, QG1>(K, S, j0 + hx - 2, k0 + hy - TL::OY, sp, TL::NH, h, lat);
   }
   __syncthreads();
 
@@ -1233,7 +1236,7 @@ __device__ __forceinline__ void step_tile(const StepConst &K, const State<R> &S,
       int nt;
       bool nc;
       if constexpr (MS) {  // the face's f-lattice: the higher of its two cells'
-        if (sp[D::IST * TL::NH + st[0]] == R(0) && sp[D::IST * TL::NH + st[1]] == R(0))
+        if (lat[st[0]] == 0 && lat[st[1]] == 0)
           nc = face_flux<R, DIM, QF1, 0, ITER, false, 3, QG1>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
         else
           nc = face_flux<R, DIM, QF1, 0, ITER, false, QF1, QG1>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
@@ -1253,7 +1256,7 @@ __device__ __forceinline__ void step_tile(const StepConst &K, const State<R> &S,
       int nt;
       bool nc;
       if constexpr (MS) {  // the face's f-lattice: the higher of its two cells'
-        if (sp[D::IST * TL::NH + st[0]] == R(0) && sp[D::IST * TL::NH + st[1]] == R(0))
+        if (lat[st[0]] == 0 && lat[st[1]] == 0)
           nc = face_flux<R, DIM, QF1, 1, ITER, false, 3, QG1>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
         else
           nc = face_flux<R, DIM, QF1, 1, ITER, false, QF1, QG1>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
@@ -1276,7 +1279,7 @@ __device__ __forceinline__ void step_tile(const StepConst &K, const State<R> &S,
     if (j >= K.nx || k >= (DIM == 2 ? K.ny : 1)) continue;
     bool low = false;
     if constexpr (MS) {
-      low = sp[D::IST * TL::NH + (cy + TL::OY) * TL::HX + cx + 2] == R(0);
+      low = lat[(cy + TL::OY) * TL::HX + cx + 2] == 0;
       nhigh += !low;
     }
     update_cell<R, DIM, QF1, BX, BY, MS, QG1>(K, S, O, fp, cx, cy, j, k, vmax, flags, low);

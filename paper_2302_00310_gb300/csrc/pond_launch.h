@@ -57,8 +57,9 @@ std::vector<pond::Shape> pond_shapes_fp64_q5();
 std::vector<pond::Shape> pond_shapes_fp32_q5();
 pond::Shape pond_iter_shape_fp64_q5();
 pond::Shape pond_iter_shape_fp32_q5();
-// the multiscale f-lattice, FP64 (pond_step_fp64_ms.cu)
+// the multiscale f-lattice (pond_step_fp64_ms.cu / pond_step_fp32_ms.cu)
 pond::Shape pond_ms_shape_fp64(int D);
+pond::Shape pond_ms_shape_fp32(int D);
 // g on the f-lattice (pond_step_fp64_g4.cu / pond_step_fp32_g4.cu)
 pond::Shape pond_g4_shape_fp64(int D);
 pond::Shape pond_g4_shape_fp32(int D);

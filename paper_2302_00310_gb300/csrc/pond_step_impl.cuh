@@ -60,7 +60,7 @@ Shape make_shape(int code) {
   s.bx = BX;
   s.by = BY;
   s.prepare = [](int *ctas) -> cudaError_t {
-    constexpr size_t smem = Tile<DIM, BX, BY, QF1, QG1>::template smem_bytes<R>();
+    constexpr size_t smem = Tile<DIM, BX, BY, QF1, QG1>::template smem_bytes<R, MS>();
     static_assert(smem + sizeof(StepConst) + 16 <= 227 * 1024, "tile too large for shared memory");
     cudaError_t e = cudaFuncSetAttribute(member_step_kernel<R, DIM, QF1, BX, BY, NT, MINB, ITER, MS, QG1>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -69,7 +69,7 @@ Shape make_shape(int code) {
         ctas, member_step_kernel<R, DIM, QF1, BX, BY, NT, MINB, ITER, MS, QG1>, NT, smem);
   };
   s.launch = [](const unsigned char *table, int k, int grid, cudaStream_t st) {
-    constexpr size_t smem = Tile<DIM, BX, BY, QF1, QG1>::template smem_bytes<R>();
+    constexpr size_t smem = Tile<DIM, BX, BY, QF1, QG1>::template smem_bytes<R, MS>();
     member_step_kernel<R, DIM, QF1, BX, BY, NT, MINB, ITER, MS, QG1><<<grid, NT, smem, st>>>(table, k);
   };
   return s;
@@ -98,11 +98,13 @@ template <typename R> Shape iter_shape(int D) {
   return make_shape<R, 2, 8, 8, 160, 1, true>(2);
 }
 
-// the multiscale f-lattice (FP64): the default FP64 tiles, 8x14 with 128
-// threads and two CTAs per SM (2D) and 252 cells (1D)
+// the multiscale f-lattice: the default tiles of each precision, 8x14 with
+// 128 threads and two CTAs per SM (FP64), 8x16 with 160 threads and two CTAs
+// per SM (mixed), 252 cells in 1D
 template <typename R> Shape ms_shape(int D) {
   if (D == 1) return make_shape<R, 1, 252, 1, 256, 1, false, 4, true>(1);
-  return make_shape<R, 2, 8, 14, 128, 2, false, 4, true>(10);
+  if constexpr (std::is_same<R, float>::value) return make_shape<R, 2, 8, 16, 160, 2, false, 4, true>(6);
+  else return make_shape<R, 2, 8, 14, 128, 2, false, 4, true>(10);
 }
 
 // g on the f-lattice (D1Q4 / D2Q16): the default tiles of each precision,

@@ -28,7 +28,7 @@ def _rel(a, b):
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
 
 
-def _gap_threshold(values, q=0.6):
+def _gap_threshold(values, q=0.6, min_gap=1e-9):
     """A threshold near the q-quantile of the measures, in the middle of a
     gap between them, so that rounding cannot move a cell across it."""
     v = np.unique(np.asarray(values).ravel())
@@ -36,11 +36,11 @@ def _gap_threshold(values, q=0.6):
     lo, hi = max(i0 - v.size // 5, 0), min(i0 + v.size // 5, v.size - 2)
     gaps = v[lo + 1:hi + 2] - v[lo:hi + 1]
     i = lo + int(np.argmax(gaps))
-    assert v[i + 1] - v[i] > 1e-9 * max(abs(v[i + 1]), 1e-300)
+    assert v[i + 1] - v[i] > min_gap * max(abs(v[i + 1]), 1e-300)
     return 0.5 * (v[i] + v[i + 1])
 
 
-def _thresholds(cfg, fields, steps):
+def _thresholds(cfg, fields, steps, min_gap=1e-9):
     """Thresholds clear of every cell's measures at the start of every step
     of the oracle run."""
     ocfg = oracle.Config.from_dict(dict(cfg, ms=1, ms_theta_u=-1.0, ms_theta_T=-1.0))
@@ -54,7 +54,7 @@ def _thresholds(cfg, fields, steps):
             su_all.append(su)
             sT_all.append(sT)
             st = oracle.run(ocfg, st, 1)
-        th = (_gap_threshold(su_all), _gap_threshold(sT_all))
+        th = (_gap_threshold(su_all, min_gap=min_gap), _gap_threshold(sT_all, min_gap=min_gap))
         ocfg = oracle.Config.from_dict(dict(cfg, ms=1, ms_theta_u=th[0], ms_theta_T=th[1]))
         st = oracle.init(ocfg, *fields)
     return th
@@ -97,6 +97,41 @@ def test_multiscale_matches_oracle(case):
         errs["uy"] = _rel(uy, ost.uy)
     assert max(errs.values()) <= TOL, errs
     assert flags[1] & pond.POND_FLAG_NONPHYSICAL == 0
+
+
+MIXED_CASES = [
+    # D, nx, ny, bc, limiter, grad_k, steps (Appendix C's flux form)
+    (2, 37, 30, (0, 0, 0, 0), 0, 0, 3),
+    (2, 29, 33, (1, 1, 2, 1), 1, 1, 2),
+    (1, 300, 1, (1, 1, 0, 0), 0, 0, 3),
+]
+
+
+@pytest.mark.parametrize("case", range(len(MIXED_CASES)))
+def test_multiscale_mixed_path(case):
+    """The mixed path with the multiscale f-lattice (Appendix C's form): the
+    oracle's moments within the step bound 2e-6 and its count of high-lattice
+    cell updates (thresholds clear of the measures by far more than FP32
+    rounding)."""
+    D, nx, ny, bc, lim, gk, steps = MIXED_CASES[case]
+    fields = W.random_state_grid(D, nx, ny, seed=190 + case, mach=0.8)
+    cfg = W._base(D, nx, ny, tau=5e-3, dx=1.0 / nx, limiter=lim, grad_k=gk, flux_appc=1, bc=bc,
+                  inflow=INFLOW)
+    cfg["dt"] = W.dt_from_cfl(fields[1], fields[2], fields[3], cfg["dx"], 0.4)
+    thu, thT = _thresholds(cfg, fields, steps, min_gap=1e-4)
+    cfg = dict(cfg, ms=1, ms_theta_u=thu, ms_theta_T=thT)
+    ocfg = oracle.Config.from_dict(cfg)
+    ost = oracle.run(ocfg, oracle.init(ocfg, *fields), steps)
+    om = oracle.moments(ocfg, ost)
+    sim = pond.Sim(dict(cfg, precision=pond.POND_FP32_MIXED))
+    sim.init(*fields)
+    sim.step(steps)
+    gm = sim.moments()
+    high = sim.ms_stats()
+    sim.close()
+    assert high == ost.report["ms_high"]
+    for i in ((0, 1, 2, 3) if D == 2 else (0, 1, 3)):
+        assert _rel(gm[i], om[i]) <= 2e-6, (i, _rel(gm[i], om[i]))
 
 
 @pytest.mark.parametrize("D", [1, 2])
@@ -149,7 +184,7 @@ def test_lax_tube_on_the_gpu():
     assert abs(high - ost.report["ms_high"]) <= 1e-3 * ost.report["ms_high"]
 
 
-@pytest.mark.parametrize("bad", [dict(precision=pond.POND_FP32_MIXED), dict(prandtl=0.71),
+@pytest.mark.parametrize("bad", [dict(precision=pond.POND_FP32_MIXED, flux_appc=0), dict(prandtl=0.71),
                                  dict(iterative=1), dict(bc=(0, 0, 3, 3)), dict(tile=6),
                                  dict(qf=5)])
 def test_multiscale_rejects_what_it_does_not_cover(bad):

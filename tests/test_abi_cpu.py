@@ -62,6 +62,47 @@ def test_invalid_arguments_are_rejected_before_any_device_work(L):
         pond.pond_create(7, (8, 8), pond.pond_params_default())
 
 
+def _params(**kw):
+    p = pond.pond_params_default()
+    for k, v in kw.items():
+        if k == "bc":
+            for i, b in enumerate(v):
+                p.bc[i] = b
+        else:
+            setattr(p, k, v)
+    return p
+
+
+@pytest.mark.parametrize("lat,kw", [
+    # multiscale: Pr 1, averaged frame, no walls, no D2Q25, the precision's tile, App. C when mixed
+    (pond.POND_D2Q16, dict(multiscale=1, prandtl=0.71)),
+    (pond.POND_D2Q16, dict(multiscale=1, flux_frame=pond.POND_FRAME_ITER)),
+    (pond.POND_D2Q16, dict(multiscale=1, bc=(0, 0, 3, 3))),
+    (pond.POND_D2Q25, dict(multiscale=1)),
+    (pond.POND_D2Q16, dict(multiscale=1, tile=6)),
+    (pond.POND_D2Q16, dict(multiscale=1, precision=pond.POND_FP32_MIXED)),
+    (pond.POND_D2Q16, dict(multiscale=2)),
+    (pond.POND_D2Q16, dict(multiscale=1, ms_theta_u=float("nan"))),
+    # g on the f-lattice: no D2Q25, no multiscale, averaged frame, the precision's tile
+    (pond.POND_D2Q25, dict(g_same_as_f=1)),
+    (pond.POND_D2Q16, dict(g_same_as_f=1, multiscale=1)),
+    (pond.POND_D2Q16, dict(g_same_as_f=1, flux_frame=pond.POND_FRAME_ITER)),
+    (pond.POND_D2Q16, dict(g_same_as_f=1, tile=9)),
+    (pond.POND_D2Q16, dict(g_same_as_f=1, precision=pond.POND_FP32_MIXED, tile=10)),
+    (pond.POND_D1Q4, dict(g_same_as_f=2)),
+])
+def test_multiscale_and_g_lattice_combinations_are_rejected_before_any_device_work(L, lat, kw):
+    with pytest.raises(pond.PondError) as e:
+        pond.pond_create(lat, (16, 16), _params(**kw))
+    assert e.value.status == pond.POND_E_INVAL
+
+
+def test_g_on_the_f_lattice_sizes_the_workspace_for_its_populations(L):
+    n3 = pond.pond_workspace_size(pond.POND_D2Q16, (64, 64), _params())
+    n4 = pond.pond_workspace_size(pond.POND_D2Q16, (64, 64), _params(g_same_as_f=1))
+    assert n4 - n3 >= 2 * 64 * 64 * (16 - 9) * 8
+
+
 def test_batch_tile_codes_are_resolved_before_any_device_work(L):
     """pond_batch_create resolves the requested tile among the candidates of
     the batch's precision before its first CUDA call: a candidate gets as far

@@ -62,7 +62,8 @@ typedef struct pond_ctx pond_ctx;
  * the fourth-order runs of the shock-structure problem, Sec. V.B.4); its
  * populations f[25][ny][nx] use node indices ix = i % 5, iy = i / 5, nodes
  * (-r2, -r1, 0, r1, r2), r1,2 = sqrt(5 -+ sqrt 10).  D2Q25 contexts run 8x8
- * tiles (tile 0 or 2) and are not batched (pond_batch_add: POND_E_INVAL). */
+ * tiles: tile 0 or 10 (128 threads, two CTAs per SM) or 2 (160 threads, one
+ * CTA); they are not batched (pond_batch_add: POND_E_INVAL). */
 typedef enum { POND_D1Q4 = 1, POND_D2Q16 = 2, POND_D2Q25 = 3 } pond_lattice;
 
 typedef enum {

@@ -220,8 +220,8 @@ pond_status step_once(pond_ctx *c) {
 // path 8x16 tiles with 160 threads and registers for two CTAs per SM; in
 // FP64 8x14 tiles with 128 threads, two CTAs per SM (shared memory and the
 // register file each hold exactly two)
-// (D2Q25: 8x8 tiles with 160 threads, its one shape)
-int auto_tile(const pond_ctx *c) { return c->D == 1 ? 1 : (c->qf1 == 5 ? 2 : (c->fp32 ? 6 : 10)); }
+// (D2Q25: 8x8 tiles with 128 threads, two CTAs per SM)
+int auto_tile(const pond_ctx *c) { return c->D == 1 ? 1 : (c->qf1 == 5 ? 10 : (c->fp32 ? 6 : 10)); }
 
 bool valid_params(const pond_params *p) {
   if (!p) return false;
@@ -443,7 +443,7 @@ pond_status pond_create(pond_ctx **out, pond_lattice lat, const int64_t dims[2],
   if (!walls_ok(p, D, dims[0], D == 2 ? dims[1] : 1)) return POND_E_INVAL;
   if (D == 1 && p->tile > 1) return POND_E_INVAL;
   if (D == 2 && p->tile == 1) return POND_E_INVAL;
-  if (lat == POND_D2Q25 && p->tile != 0 && p->tile != 2) return POND_E_INVAL;
+  if (lat == POND_D2Q25 && p->tile != 0 && p->tile != 2 && p->tile != 10) return POND_E_INVAL;
   if (p->multiscale && (lat == POND_D2Q25 ||
                         (p->tile != 0 && p->tile != (D == 1 ? 1 : (p->precision == POND_FP64 ? 10 : 6)))))
     return POND_E_INVAL;

@@ -466,6 +466,26 @@ Q5_CASES = [
 ]
 
 
+def test_d2q25_tiles_compute_the_same_step():
+    """The two D2Q25 tile shapes (8x8 with 128 threads and two CTAs per SM,
+    the default; 8x8 with 160 threads and one CTA): the same state to
+    rounding."""
+    nx, ny = 37, 29
+    rho, ux, uy, T = W.random_state_grid(2, nx, ny, seed=141, mach=0.8, T=(0.7, 1.4))
+    cfg = W._base(2, nx, ny, qf=5, tau=5e-3, dx=1.0 / nx, prandtl=0.71, bc=(1, 1, 1, 1))
+    cfg["dt"] = W.dt_from_cfl(ux, uy, T, cfg["dx"], 0.4, c_max=W.C_MAX_D1Q5)
+    out = {}
+    for tile in (2, 10):
+        sim = pond.Sim(dict(cfg, tile=tile))
+        sim.init(rho, ux, uy, T)
+        sim.step(3)
+        out[tile] = sim.get_state()
+        assert sim.info()[2] == tile
+        sim.close()
+    for a, b in zip(out[2], out[10]):
+        assert _rel(a, b) <= 1e-13
+
+
 @pytest.mark.parametrize("case", range(len(Q5_CASES)))
 def test_d2q25_matches_oracle(case):
     """The D2Q25 f-lattice (D1Q5 per axis, fourth-order invariance) with D2Q9

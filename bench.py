@@ -70,7 +70,7 @@ WORKLOAD = "2D periodic advected Gaussian pulse, D2Q16+D2Q9, 256x256, Mach 2 at 
 # MUL thread instructions per launch / cells, on the source digest named (the
 # build whose kernels bench.py runs; profiles/ holds the captures).
 FLOPS_PER_CELL = {"fp64": 8771.6, "fp32": 8708.2, "fp32_fp64part": 59.2,
-                  "counted_on": "1810ca02f1528c1d755258326c182ab47ea359c195ef1cea7d1bea199be5bbb3"}
+                  "counted_on": "692515fd01933f977a8f9da4f333a9fb9eef177c5bb30608584c812150bb0e47"}
 BYTES_PER_CELL_FP64 = 2 * 28 * 8          # state read once + written once
 BYTES_PER_CELL_FP32 = 2 * (28 * 4 + 4 * 8)  # + the FP64 conserved moments
 CLOCK_MAX_GHZ = 2.07
@@ -79,8 +79,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * CLOCK_MAX_GHZ / 1e3   # 128 FP32 FMA/clk/SM
 # dram__bytes_read.sum + dram__bytes_write.sum of one main-line step launch
 # (FP64 and mixed path), keyed by source digest (None once the sources change)
 TRAFFIC_BY_DIGEST = {
-    "1810ca02f1528c1d755258326c182ab47ea359c195ef1cea7d1bea199be5bbb3": {"fp64": 18239488,
-                                                                          "fp32": 9821184},
+    "692515fd01933f977a8f9da4f333a9fb9eef177c5bb30608584c812150bb0e47": {"fp64": 18168576,
+                                                                          "fp32": 9804288},
 }
 
 

@@ -758,6 +758,12 @@ def run_gpu(args, dist, rank, ws):
         line["cpu_baseline"]["single_thread"] = {
             "value": rate1, "unit": UNIT, "cores": 1,
             "sample": "%d oracle steps of a 64x64 window (%.1f s)" % (done1, el1)}
+        # the oracle's operation count of one step on the same 64x64 window: the work of the
+        # paper's population-space route, beside the kernel's executed flops per cell
+        sub = [np.ascontiguousarray(x[:64, :64]) for x in (w["rho"], w["ux"], w["uy"], w["T"])]
+        ocfg = oracle.Config.from_dict(dict(cfg, nx=64, ny=64))
+        ops, _ = oracle.count_ops(ocfg, oracle.init(ocfg, *sub), 1)
+        line["cpu_baseline"]["oracle_ops_per_cell_update"] = ops / (64 * 64)
     print(json.dumps(line), flush=True)
 
 

@@ -77,6 +77,9 @@ def lib():
         _lib.orc_init.argtypes = [ctypes.c_void_p] + [P] * 9
         _lib.orc_init.restype = ctypes.c_int
         _lib.orc_run.argtypes = [ctypes.c_void_p, P, P, P, P, P, ctypes.c_int64, ctypes.c_void_p]
+        _lib.orc_count_ops.argtypes = [ctypes.c_void_p, P, P, P, P, P, ctypes.c_int64, ctypes.c_void_p,
+                                       ctypes.POINTER(ctypes.c_int64)]
+        _lib.orc_count_ops.restype = ctypes.c_int
         _lib.orc_ms_measure_pub.argtypes = [ctypes.c_void_p] + [P] * 5
         _lib.orc_ms_measure_pub.restype = ctypes.c_int
         _lib.orc_run.restype = ctypes.c_int
@@ -265,6 +268,20 @@ def run(cfg: Config, state: State, nsteps: int) -> State:
                  "traces": int(rep.traces), "max_traces": int(rep.max_traces),
                  "ms_high": int(rep.ms_high)}
     return st
+
+
+def count_ops(cfg: Config, state: State, nsteps: int):
+    """Floating-point operations (+, -, *, /, sqrt) of ``nsteps`` oracle steps
+    from ``state`` on one thread, and the advanced copy: the stages of the step
+    on cells and faces, not the construction of ghost cells."""
+    st = state.copy()
+    rep = _Report()
+    ops = ctypes.c_int64()
+    rc = lib().orc_count_ops(ctypes.byref(cfg._c()), _ptr(st.f), _ptr(st.g), _ptr(st.ux), _ptr(st.uy),
+                             _ptr(st.T), int(nsteps), ctypes.byref(rep), ctypes.byref(ops))
+    if rc != 0:
+        raise ValueError("oracle: invalid configuration (rc=%d)" % rc)
+    return int(ops.value), st
 
 
 def ms_measure(cfg: Config, ux, uy, T):

@@ -46,6 +46,19 @@
 #define ORC_MAXQ1 5
 #define ORC_MAXQ (ORC_MAXQ1 * ORC_MAXQ1)
 
+/* Operation counter: with orc_counting set (single-threaded runs of
+ * orc_count_ops only), OPS(n) adds the n floating-point operations (+, -, *,
+ * /, sqrt; comparisons, fabs and fmax excluded) of the statement beside it.
+ * It covers the step's stages on cells and faces (QE, phi_bar^+, faces,
+ * update, CFL), not the construction of ghost cells or the multiscale
+ * switching measure. */
+static int orc_counting = 0;
+static int64_t orc_ops = 0;
+#define OPS(n) \
+  do { \
+    if (orc_counting) orc_ops += (n); \
+  } while (0)
+
 enum { ORC_BC_PERIODIC = 0, ORC_BC_ZERO_GRADIENT = 1, ORC_BC_INFLOW = 2, ORC_BC_WALL = 3 };
 enum { ORC_LIM_VANLEER = 0, ORC_LIM_MINMOD = 1 };
 enum { ORC_FLAG_NONPHYSICAL = 1u, ORC_FLAG_NOCONV = 4u };
@@ -125,6 +138,7 @@ static void orc_lat1_make(orc_lat1 *L, int q) {
  * has node indices ix = i % q, iy = i / q (x fastest). */
 static int orc_Q(const orc_lat1 *L, int D) { return D == 1 ? L->q : L->q * L->q; }
 static double orc_W(const orc_lat1 *L, int D, int i) { /* Eq. eq:wi */
+  OPS(D == 2);
   return D == 1 ? L->w[i] : L->w[i % L->q] * L->w[i / L->q];
 }
 static double orc_cx(const orc_lat1 *L, int D, int i) { return L->c[D == 1 ? i : i % L->q]; }
@@ -132,6 +146,7 @@ static double orc_cy(const orc_lat1 *L, int D, int i) { return D == 1 ? 0.0 : L-
 
 /* One-dimensional Hermite polynomials of Appendix A (T_L = 1). */
 static double orc_He(int n, double x) {
+  OPS(n == 2 ? 2 : (n == 3 ? 4 : (n == 4 ? 7 : 0)));
   switch (n) {
   case 0: return 1.0;
   case 1: return x;
@@ -140,7 +155,12 @@ static double orc_He(int n, double x) {
   default: return x * x * x * x - 6.0 * x * x + 3.0;
   }
 }
-static double orc_fact(int n) { double r = 1; for (int k = 2; k <= n; ++k) r *= k; return r; }
+static double orc_fact(int n) {
+  double r = 1;
+  for (int k = 2; k <= n; ++k) r *= k;
+  OPS(n > 1 ? n - 1 : 0);
+  return r;
+}
 
 /* ------------------------------------------------------------------ */
 /* Frame transformation G_{lambda}^{lambda'} (Sec. II.B).              */
@@ -167,6 +187,7 @@ static void orc_transform_x(const orc_lat1 *Ls, const orc_lat1 *Ld, int K, int D
                             double Tp, double *fout) {
   const int Qs = orc_Q(Ls, D), Qd = orc_Q(Ld, D), Kb = (D == 2) ? K : 0;
   const double sT = sqrt(T), sTp = sqrt(Tp);
+  OPS(2);
   double alpha[ORC_MAXQ1][ORC_MAXQ1];
   for (int a = 0; a <= K; ++a)
     for (int b = 0; b <= Kb; ++b) {
@@ -179,6 +200,7 @@ static void orc_transform_x(const orc_lat1 *Ls, const orc_lat1 *Ld, int K, int D
           h *= orc_He(b, xiy);
         }
         s += fin[j] * h;
+        OPS(D == 2 ? 11 : 6);
       }
       alpha[a][b] = s;
     }
@@ -190,8 +212,10 @@ static void orc_transform_x(const orc_lat1 *Ls, const orc_lat1 *Ld, int K, int D
         double h = orc_He(a, orc_cx(Ld, D, i));
         if (D == 2) h *= orc_He(b, orc_cy(Ld, D, i));
         s += alpha[a][b] * h / (orc_fact(a) * orc_fact(b));
+        OPS(D == 2 ? 5 : 4);
       }
     fout[i] = orc_W(Ld, D, i) * s;
+    OPS(1);
   }
 }
 static void orc_transform(const orc_lat1 *L, int D, int grad_k, const double *fin,
@@ -207,6 +231,7 @@ static void orc_equilibrium(const orc_lat1 *L, int D, int grad_k, double rho, co
   double W[ORC_MAXQ];
   const int Q = orc_Q(L, D);
   for (int i = 0; i < Q; ++i) W[i] = rho * orc_W(L, D, i);
+  OPS(Q);
   orc_transform(L, D, grad_k, W, u, T, up, Tp, feq);
 }
 
@@ -219,6 +244,7 @@ static int orc_macro(const orc_lat1 *Lf, const orc_lat1 *Lg, int D, double Cv, c
                      const double *g, const double uf[2], double Tf, double *rho, double u[2],
                      double *T) {
   const double sT = sqrt(Tf);
+  OPS(1 + 15 * orc_Q(Lf, D) + orc_Q(Lg, D) + 10 + (D == 2));
   double r = 0, jx = 0, jy = 0, E2 = 0, G = 0;
   for (int i = 0; i < orc_Q(Lf, D); ++i) {
     double vx = sT * orc_cx(Lf, D, i) + uf[0];
@@ -248,6 +274,7 @@ static void orc_qe_half(const orc_lat1 *Lf, const orc_lat1 *Lg, int D, double Cv
   const double sT = sqrt(T);
   double rho = 0;
   for (int i = 0; i < Qf; ++i) rho += f[i];
+  OPS(1 + Qf);
   /* Q_{abc} = sum_i e_a e_b e_c (f_i - f_i^eq), f^eq = rho W (Eq. feqPond) */
   double Qt[2][2][2] = {{{0}}};
   for (int i = 0; i < Qf; ++i) {
@@ -256,6 +283,7 @@ static void orc_qe_half(const orc_lat1 *Lf, const orc_lat1 *Lg, int D, double Cv
     for (int a = 0; a < D; ++a)
       for (int b = 0; b < D; ++b)
         for (int c = 0; c < D; ++c) Qt[a][b][c] += e[a] * e[b] * e[c] * fneq;
+    OPS(4 + 4 * D * D * D);
   }
   /* varsigma_a = sum_i e_a (g_i - g_i^eq), g^eq = (C_v - D/2) T rho W (Eq. geqPond) */
   double vs[2] = {0, 0};
@@ -263,8 +291,10 @@ static void orc_qe_half(const orc_lat1 *Lf, const orc_lat1 *Lg, int D, double Cv
     double e[2] = {sT * orc_cx(Lg, D, i), sT * orc_cy(Lg, D, i)};
     double gneq = g[i] - (Cv - 0.5 * D) * T * rho * orc_W(Lg, D, i);
     for (int a = 0; a < D; ++a) vs[a] += e[a] * gneq;
+    OPS(2 + 6 + 2 * D);
   }
   const double k = 0.5 * dt * (1.0 / tau1 - 1.0 / tau2);
+  OPS(5);
   /* f* - f^eq = W Q : (e e e - 3 T e I) / (6 T^3) */
   for (int i = 0; i < Qf; ++i) {
     double e[2] = {sT * orc_cx(Lf, D, i), sT * orc_cy(Lf, D, i)};
@@ -280,6 +310,7 @@ static void orc_qe_half(const orc_lat1 *Lf, const orc_lat1 *Lg, int D, double Cv
         }
     double dfs = orc_W(Lf, D, i) * s / (6.0 * T * T * T);
     f[i] += k * dfs;
+    OPS(2 + 4 * D * D * D + 6 * D * D + 5 + 2);
   }
   /* g* - g^eq = W varsigma . e / T */
   for (int i = 0; i < Qg; ++i) {
@@ -287,6 +318,7 @@ static void orc_qe_half(const orc_lat1 *Lf, const orc_lat1 *Lg, int D, double Cv
     double s = 0;
     for (int a = 0; a < D; ++a) s += vs[a] * e[a];
     g[i] += k * orc_W(Lg, D, i) * s / T;
+    OPS(2 + 2 * D + 4);
   }
 }
 
@@ -486,8 +518,10 @@ static void orc_fill_ghosts(orc_grid *G) {
 /* Limited slope (Sec. IV.A.2: Van Leer / minmod).                     */
 /* ------------------------------------------------------------------ */
 static double orc_limit(int limiter, double sl, double sr) {
+  OPS(1);
   if (sl * sr <= 0.0) return 0.0;
   if (limiter == ORC_LIM_MINMOD) return fabs(sl) < fabs(sr) ? sl : sr;
+  OPS(4);
   return 2.0 * sl * sr / (sl + sr);
 }
 
@@ -537,6 +571,7 @@ static void orc_face_trace(const orc_grid *G, const orc_stencil *S, const orc_la
       double vx = sqrt(TF) * orc_cx(L, D, i) + uF[0];
       double vy = sqrt(TF) * orc_cy(L, D, i) + uF[1];
       double vn = dir == 0 ? vx : vy, vt = dir == 0 ? vy : vx;
+      OPS(6);
       /* upwind: t = 0 left/lower, 1 right/upper; with v_n = 0 exactly (a
        * wall at rest puts the zero node of D1Q3 there) the mean of the two
        * one-sided traces, so that the face has no preferred side */
@@ -551,13 +586,16 @@ static void orc_face_trace(const orc_grid *G, const orc_stencil *S, const orc_la
         /* offset of the departure point from the upwind cell centre */
         double dn = (t == 0 ? 0.5 * dx : -0.5 * dx) - vn * 0.5 * dt;
         double v1 = ps + dn * sig_n;
+        OPS(4 + 4 + 2);
         if (D == 2) {
           double qm = pop == 0 ? tt_f[t][0][i] : tt_g[t][0][i];
           double qp = pop == 0 ? tt_f[t][1][i] : tt_g[t][1][i];
           double sig_t = orc_limit(p->limiter, (ps - qm) / dx, (qp - ps) / dx);
           v1 += (-vt * 0.5 * dt) * sig_t;
+          OPS(4 + 4);
         }
         val += t0 == t1 ? v1 : 0.5 * v1;
+        OPS(t0 == t1 ? 1 : 2);
       }
       out[i] = val;
     }
@@ -574,6 +612,7 @@ static int orc_face(orc_grid *G, int dir, int j, int k, double *phi_f, double *p
   const orc_params *p = G->p;
   const int D = G->D;
   const double dt = p->dt, tau = p->tau, h = 0.5 * dt;
+  OPS(1);
   orc_stencil S;
   S.dir = dir;
   for (int n = 0; n < 4; ++n)
@@ -593,6 +632,7 @@ static int orc_face(orc_grid *G, int dir, int j, int k, double *phi_f, double *p
   /* face frame, Eq. eq::AvgFrame */
   double uF[2] = {0.5 * (G->ux[cL] + G->ux[cR]), 0.5 * (G->uy[cL] + G->uy[cR])};
   double TF = 0.5 * (G->T[cL] + G->T[cR]);
+  OPS(6);
   int noconv = 0;
 
   double fb[ORC_MAXQ], gb[ORC_MAXQ];
@@ -623,6 +663,7 @@ static int orc_face(orc_grid *G, int dir, int j, int k, double *phi_f, double *p
     if (!p->iterative) break;
     double du = sqrt((ub[0] - uF[0]) * (ub[0] - uF[0]) + (ub[1] - uF[1]) * (ub[1] - uF[1]));
     double err = fmax(du / sqrt(TF), fabs(Tb - TF) / TF);
+    OPS(8 + 4);
     if (err < p->iter_tol) { converged = 1; break; }
     if (it + 1 < nit) {
       uP[0] = uF[0]; uP[1] = uF[1]; TP = TF;
@@ -638,15 +679,18 @@ static int orc_face(orc_grid *G, int dir, int j, int k, double *phi_f, double *p
   if (p->iterative && converged) {
     for (int i = 0; i < QF; ++i) feq[i] = rho * orc_W(LF, D, i);
     for (int i = 0; i < G->Qg; ++i) geq[i] = (G->Cv - 0.5 * D) * Tb * rho * orc_W(&G->Lg, D, i);
+    OPS(QF + 5 * G->Qg);
   } else {
     double gscale = (G->Cv - 0.5 * D) * Tb;
     orc_equilibrium(LF, D, p->grad_k, rho, ub, Tb, uF, TF, feq);
     orc_equilibrium(&G->Lg, D, p->grad_k, rho * gscale, ub, Tb, uF, TF, geq);
+    OPS(3 + 1);
   }
   /* invert Eq. eq:FluxTransf: phi_bar = phi - (h/2) (phi^eq - phi)/tau, h = dt/2 */
   const double r = h / (2.0 * tau);
   for (int i = 0; i < QF; ++i) phi_f[i] = (fb[i] + r * feq[i]) / (1.0 + r);
   for (int i = 0; i < G->Qg; ++i) phi_g[i] = (gb[i] + r * geq[i]) / (1.0 + r);
+  OPS(2 + 4 * (QF + G->Qg));
   lam[0] = uF[0]; lam[1] = uF[1]; lam[2] = TF;
   return noconv;
 }
@@ -729,7 +773,12 @@ static int orc_step_once(orc_grid *G, orc_report *rep) {
   int max_tr = 0;
 
   /* 0. multiscale: each cell's lattice for this step, from its current fields */
-  if (p->ms) orc_ms_switch(G);
+  if (p->ms) {
+    const int counting = orc_counting;  /* the switching is not counted */
+    orc_counting = 0;
+    orc_ms_switch(G);
+    orc_counting = counting;
+  }
 
   /* 1. quasi-equilibrium half relaxation in the cell centres */
   if (qe) {
@@ -745,8 +794,13 @@ static int orc_step_once(orc_grid *G, orc_report *rep) {
         for (int i = 0; i < Qg; ++i) G->g[i * ncp + c] = g[i];
       }
   }
-  orc_fill_ghosts(G);
-  if (p->ms) orc_ms_ghost_lattices(G);
+  {
+    const int counting = orc_counting;  /* ghost construction is not counted */
+    orc_counting = 0;
+    orc_fill_ghosts(G);
+    if (p->ms) orc_ms_ghost_lattices(G);
+    orc_counting = counting;
+  }
 
   /* 2. phi_bar^+ in every cell (ghosts included), Eq. eq:Fbarplus, from the
    * stored variable of Eq. eq:variableTransform; the cell is in its
@@ -755,6 +809,7 @@ static int orc_step_once(orc_grid *G, orc_report *rep) {
   for (int c = 0; c < ncp; ++c) {
     double rho = 0;
     for (int i = 0; i < Qf; ++i) rho += G->f[i * ncp + c];
+    OPS(Qf + 4);
     for (int pop = 0; pop < 2; ++pop) {
       const orc_lat1 *L = pop == 0 ? &G->Lf : &G->Lg;
       const double *st = pop == 0 ? G->f : G->g;
@@ -766,6 +821,7 @@ static int orc_step_once(orc_grid *G, orc_report *rep) {
         double ph = (st[i * ncp + c] + dt / (2.0 * tau) * eq) / (1.0 + dt / (2.0 * tau));
         /* phi_bar^+ = phi + (dt/4) (phi^eq - phi)/tau */
         out[i * ncp + c] = ph + 0.25 * dt * (eq - ph) / tau;
+        OPS(1 + 8 + 5);
       }
     }
   }
@@ -799,6 +855,7 @@ static int orc_step_once(orc_grid *G, orc_report *rep) {
   /* 4.-5. loop over cells: flux in the cell frame (Eq. fluxEq), DUGKS update
    * (Eqs. eq:FinalUpdateDUGKS, eq:FinalUpdateDUGKS_g), new co-moving frame */
   const double a1 = (2.0 * tau - dt) / (2.0 * tau + dt), a2 = 2.0 * dt / (2.0 * tau + dt);
+  OPS(9);
   double maxcfl = 0.0;
 #pragma omp parallel for collapse(2) schedule(static) reduction(| : flags) reduction(max : maxcfl) \
     reduction(+ : ms_high)
@@ -806,6 +863,7 @@ static int orc_step_once(orc_grid *G, orc_report *rep) {
     for (int j = 0; j < G->nx; ++j) {
       int c = orc_pidx(G, j, k);
       double uc[2] = {G->ux[c], G->uy[c]}, Tc = G->T[c], sT = sqrt(Tc);
+      OPS(1);
       double Ff[ORC_MAXQ] = {0}, Fg[ORC_MAXQ] = {0};
       /* the cell's f-lattice and its populations on it (a multiscale low cell:
        * from its high-lattice storage, an exact change of nodes) */
@@ -853,6 +911,7 @@ static int orc_step_once(orc_grid *G, orc_report *rep) {
               double vn = dir == 0 ? sT * orc_cx(L, D, i) + uc[0] : sT * orc_cy(L, D, i) + uc[1];
               acc[i] += sgn * vn * tr[i];
             }
+            OPS(5 * Q);
           } else {
             /* Appendix C: G_{lambda_F}^{lambda} (v^{lambda_F} . n phi) */
             double fl[ORC_MAXQ];
@@ -863,6 +922,7 @@ static int orc_step_once(orc_grid *G, orc_report *rep) {
             }
             orc_transform_x(LS, L, L->K, D, p->grad_k, fl, uF, TF, uc, Tc, tr);
             for (int i = 0; i < Q; ++i) acc[i] += sgn * tr[i];
+            OPS(4 * QS + 2 * Q);
           }
         }
       }
@@ -871,6 +931,7 @@ static int orc_step_once(orc_grid *G, orc_report *rep) {
       double f[ORC_MAXQ], g[ORC_MAXQ];
       /* V_j = dx^D, face area dx^(D-1): dt/V * area = dt/dx */
       for (int i = 0; i < Qc; ++i) f[i] = a1 * fc[i] + a2 * rho * orc_W(Lc, D, i) - dt / dx * Ff[i];
+      OPS(Qc + 7 * Qc + 11 * Qg);
       for (int i = 0; i < Qg; ++i)
         g[i] = a1 * G->g[i * ncp + c] + a2 * (G->Cv - 0.5 * D) * Tc * rho * orc_W(&G->Lg, D, i) -
                dt / dx * Fg[i];
@@ -905,6 +966,7 @@ static int orc_step_once(orc_grid *G, orc_report *rep) {
       double cmax = Lc->c[Lc->q - 1];
       double vmax = fmax(fabs(un[0]), fabs(D == 2 ? un[1] : 0.0)) + sqrt(Tn) * cmax;
       double cfl = vmax * dt / dx;
+      OPS(5);
       if (cfl > maxcfl) maxcfl = cfl;
     }
   /* an iterated face frame that reached iter_max unconverged is reported as
@@ -1118,6 +1180,27 @@ int orc_ms_measure_pub(const orc_params *p, const double *ux, const double *uy, 
       orc_ms_measure(&G, j, k, su + (size_t)k * G.nx + j, sT + (size_t)k * G.nx + j);
   orc_grid_free(&G);
   return 0;
+}
+
+/* The floating-point operations of nsteps steps (OPS above), counted on one
+ * thread; the state is advanced in place as by orc_run. */
+int orc_count_ops(const orc_params *p, double *f, double *g, double *ux, double *uy, double *T,
+                  int64_t nsteps, orc_report *rep, int64_t *ops) {
+#ifdef _OPENMP
+  extern int omp_get_max_threads(void);
+  extern void omp_set_num_threads(int);
+  const int nt = omp_get_max_threads();
+  omp_set_num_threads(1);
+#endif
+  orc_ops = 0;
+  orc_counting = 1;
+  const int rc = orc_run(p, f, g, ux, uy, T, nsteps, rep);
+  orc_counting = 0;
+  *ops = orc_ops;
+#ifdef _OPENMP
+  omp_set_num_threads(nt);
+#endif
+  return rc;
 }
 
 /* Number of OpenMP threads the oracle runs with (1 without OpenMP). */

@@ -31,29 +31,37 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pond_oracle.c")
 _SO = os.path.join(_HERE, "libpond_oracle.so")
+# the same source with its operation counters compiled in (count_ops only)
+_SO_COUNT = os.path.join(_HERE, "libpond_oracle_count.so")
 
 BC_PERIODIC, BC_ZERO_GRADIENT, BC_INFLOW, BC_WALL = 0, 1, 2, 3
 LIM_VANLEER, LIM_MINMOD = 0, 1
 FLAG_NONPHYSICAL, FLAG_NOCONV = 1, 4
 
 
-def build(force: bool = False) -> str:
-    """Compile ``pond_oracle.c`` into ``libpond_oracle.so`` (gcc, -O2, strict
-    FP: no contraction, so the arithmetic is exactly the source's)."""
-    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
-        return _SO
+def _compile(so: str, defines, force: bool) -> str:
+    if not force and os.path.exists(so) and os.path.getmtime(so) >= os.path.getmtime(_SRC):
+        return so
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         raise RuntimeError("oracle: no C compiler found")
-    base = [cc, "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math"]
-    tmp = _SO + ".tmp"
+    base = [cc, "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math"] + defines
+    tmp = so + ".tmp"
     for extra in (["-fopenmp"], []):
         cmd = base + extra + ["-o", tmp, _SRC, "-lm"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode == 0:
-            os.replace(tmp, _SO)
-            return _SO
+            os.replace(tmp, so)
+            return so
     raise RuntimeError("oracle: compile failed:\n" + r.stderr)
+
+
+def build(force: bool = False) -> str:
+    """Compile ``pond_oracle.c`` into ``libpond_oracle.so`` (gcc, -O2, strict
+    FP: no contraction, so the arithmetic is exactly the source's), and the
+    same source with its operation counters into ``libpond_oracle_count.so``."""
+    _compile(_SO_COUNT, ["-DORC_COUNT_OPS"], force)
+    return _compile(_SO, [], force)
 
 
 _lib = None
@@ -77,9 +85,6 @@ def lib():
         _lib.orc_init.argtypes = [ctypes.c_void_p] + [P] * 9
         _lib.orc_init.restype = ctypes.c_int
         _lib.orc_run.argtypes = [ctypes.c_void_p, P, P, P, P, P, ctypes.c_int64, ctypes.c_void_p]
-        _lib.orc_count_ops.argtypes = [ctypes.c_void_p, P, P, P, P, P, ctypes.c_int64, ctypes.c_void_p,
-                                       ctypes.POINTER(ctypes.c_int64)]
-        _lib.orc_count_ops.restype = ctypes.c_int
         _lib.orc_ms_measure_pub.argtypes = [ctypes.c_void_p] + [P] * 5
         _lib.orc_ms_measure_pub.restype = ctypes.c_int
         _lib.orc_run.restype = ctypes.c_int
@@ -87,6 +92,21 @@ def lib():
         _lib.orc_set_threads.argtypes = [ctypes.c_int]
         _lib.orc_set_threads.restype = None
     return _lib
+
+
+_lib_count = None
+
+
+def _counting_lib():
+    global _lib_count
+    if _lib_count is None:
+        build()
+        _lib_count = ctypes.CDLL(_SO_COUNT)
+        P = ctypes.POINTER(ctypes.c_double)
+        _lib_count.orc_count_ops.argtypes = [ctypes.c_void_p, P, P, P, P, P, ctypes.c_int64,
+                                             ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]
+        _lib_count.orc_count_ops.restype = ctypes.c_int
+    return _lib_count
 
 
 class _Params(ctypes.Structure):
@@ -277,8 +297,9 @@ def count_ops(cfg: Config, state: State, nsteps: int):
     st = state.copy()
     rep = _Report()
     ops = ctypes.c_int64()
-    rc = lib().orc_count_ops(ctypes.byref(cfg._c()), _ptr(st.f), _ptr(st.g), _ptr(st.ux), _ptr(st.uy),
-                             _ptr(st.T), int(nsteps), ctypes.byref(rep), ctypes.byref(ops))
+    rc = _counting_lib().orc_count_ops(ctypes.byref(cfg._c()), _ptr(st.f), _ptr(st.g), _ptr(st.ux),
+                                       _ptr(st.uy), _ptr(st.T), int(nsteps), ctypes.byref(rep),
+                                       ctypes.byref(ops))
     if rc != 0:
         raise ValueError("oracle: invalid configuration (rc=%d)" % rc)
     return int(ops.value), st

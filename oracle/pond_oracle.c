@@ -46,18 +46,36 @@
 #define ORC_MAXQ1 5
 #define ORC_MAXQ (ORC_MAXQ1 * ORC_MAXQ1)
 
-/* Operation counter: with orc_counting set (single-threaded runs of
- * orc_count_ops only), OPS(n) adds the n floating-point operations (+, -, *,
- * /, sqrt; comparisons, fabs and fmax excluded) of the statement beside it.
- * It covers the step's stages on cells and faces (QE, phi_bar^+, faces,
- * update, CFL), not the construction of ghost cells or the multiscale
- * switching measure. */
+/* Operation counter, compiled in only with ORC_COUNT_OPS (a second build of
+ * this file; the everyday build carries none of it): with orc_counting set
+ * (single-threaded runs of orc_count_ops), OPS(n) adds the n floating-point
+ * operations (+, -, *, /, sqrt; comparisons, fabs and fmax excluded) of the
+ * statement beside it.  It covers the step's stages on cells and faces (QE,
+ * phi_bar^+, faces, update, CFL), not the construction of ghost cells or the
+ * multiscale switching measure. */
+#ifdef ORC_COUNT_OPS
 static int orc_counting = 0;
 static int64_t orc_ops = 0;
 #define OPS(n) \
   do { \
     if (orc_counting) orc_ops += (n); \
   } while (0)
+#define ORC_UNCOUNTED(stmt) \
+  do { \
+    const int counting_ = orc_counting; \
+    orc_counting = 0; \
+    stmt; \
+    orc_counting = counting_; \
+  } while (0)
+#else
+#define OPS(n) \
+  do { \
+  } while (0)
+#define ORC_UNCOUNTED(stmt) \
+  do { \
+    stmt; \
+  } while (0)
+#endif
 
 enum { ORC_BC_PERIODIC = 0, ORC_BC_ZERO_GRADIENT = 1, ORC_BC_INFLOW = 2, ORC_BC_WALL = 3 };
 enum { ORC_LIM_VANLEER = 0, ORC_LIM_MINMOD = 1 };
@@ -773,12 +791,7 @@ static int orc_step_once(orc_grid *G, orc_report *rep) {
   int max_tr = 0;
 
   /* 0. multiscale: each cell's lattice for this step, from its current fields */
-  if (p->ms) {
-    const int counting = orc_counting;  /* the switching is not counted */
-    orc_counting = 0;
-    orc_ms_switch(G);
-    orc_counting = counting;
-  }
+  if (p->ms) ORC_UNCOUNTED(orc_ms_switch(G)); /* the switching is not counted */
 
   /* 1. quasi-equilibrium half relaxation in the cell centres */
   if (qe) {
@@ -794,13 +807,8 @@ static int orc_step_once(orc_grid *G, orc_report *rep) {
         for (int i = 0; i < Qg; ++i) G->g[i * ncp + c] = g[i];
       }
   }
-  {
-    const int counting = orc_counting;  /* ghost construction is not counted */
-    orc_counting = 0;
-    orc_fill_ghosts(G);
-    if (p->ms) orc_ms_ghost_lattices(G);
-    orc_counting = counting;
-  }
+  ORC_UNCOUNTED(orc_fill_ghosts(G)); /* ghost construction is not counted */
+  if (p->ms) orc_ms_ghost_lattices(G);
 
   /* 2. phi_bar^+ in every cell (ghosts included), Eq. eq:Fbarplus, from the
    * stored variable of Eq. eq:variableTransform; the cell is in its
@@ -1182,6 +1190,7 @@ int orc_ms_measure_pub(const orc_params *p, const double *ux, const double *uy, 
   return 0;
 }
 
+#ifdef ORC_COUNT_OPS
 /* The floating-point operations of nsteps steps (OPS above), counted on one
  * thread; the state is advanced in place as by orc_run. */
 int orc_count_ops(const orc_params *p, double *f, double *g, double *ux, double *uy, double *T,
@@ -1202,6 +1211,7 @@ int orc_count_ops(const orc_params *p, double *f, double *g, double *ux, double 
 #endif
   return rc;
 }
+#endif
 
 /* Number of OpenMP threads the oracle runs with (1 without OpenMP). */
 int orc_threads(void) {

@@ -438,6 +438,36 @@ def bench_multiscale(torch, pond, W, steps=200, theta=0.05):
     return out
 
 
+def bench_g_lattice(torch, pond, W, steps=100):
+    """The g-populations on the f-lattice (D2Q16 for g) on the 256^2 pulse,
+    FP64 and mixed, beside g on D2Q9: MLUPS of both, timed alike, and the L1
+    density difference."""
+    w = W.pulse_2d(n=256, seed=0)
+    fields = (w["rho"], w["ux"], w["uy"], w["T"])
+    n = w["cfg"]["nx"] * w["cfg"]["ny"]
+    out = {"workload": "the main line's 256x256 pulse, g on D2Q16 against g on D2Q9", "steps": steps,
+           "unit": UNIT}
+    rho = {}
+    for qg in (4, 3):
+        for prec, name in ((pond.POND_FP64, "fp64"), (pond.POND_FP32_MIXED, "fp32_mixed")):
+            sim = pond.Sim(dict(w["cfg"], qg=qg, precision=prec))
+            sim.init(*fields)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(sim.stream):
+                pond.pond_step(sim.ctx, 3)
+                e0.record(sim.stream)
+                pond.pond_step(sim.ctx, steps)
+                e1.record(sim.stream)
+            sim.stream.synchronize()
+            ms = e0.elapsed_time(e1)
+            rho[(qg, name)] = sim.moments()[0]
+            out.setdefault("g_d2q16" if qg == 4 else "g_d2q9", {})[name] = {
+                "value": n * steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / steps, "tile": sim.info()[2]}
+            sim.close()
+    out["l1_rho_g_d2q16_vs_g_d2q9_fp64"] = _l1(rho[(4, "fp64")], rho[(3, "fp64")])
+    return out
+
+
 def bench_batched(torch, pond, W):
     """64 shock-bubble instances through the persistent batch kernel."""
     ws_ = [W.shock_bubble_2d(seed=s) for s in range(64)]
@@ -652,7 +682,8 @@ def run_gpu(args, dist, rank, ws):
     pond.lib(build=True)
     if args.extra:
         if rank == 0:
-            fn = {"riemann": bench_riemann, "d2q25": bench_d2q25, "multiscale": bench_multiscale}[args.extra]
+            fn = {"riemann": bench_riemann, "d2q25": bench_d2q25, "multiscale": bench_multiscale,
+                  "g_lattice": bench_g_lattice}[args.extra]
             print(json.dumps(dict(extra=args.extra, **fn(torch, pond, W))), flush=True)
         return
     w = W.pulse_2d(n=256, seed=0)
@@ -701,6 +732,7 @@ def run_gpu(args, dist, rank, ws):
         extras["batched"] = bench_batched(torch, pond, W)
         extras["d2q25"] = bench_d2q25(torch, pond, W)
         extras["multiscale"] = bench_multiscale(torch, pond, W)
+        extras["g_lattice"] = bench_g_lattice(torch, pond, W)
         extras["serve"] = bench_serve(pond, serve_mod)
         if not args.no_studies:
             extras["serve_sweep"] = bench_serve_sweep(pond, serve_mod)
@@ -780,7 +812,7 @@ def main():
                     help="skip the accuracy studies (iterated face frame, thermal Couette)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
                     help="arithmetic of the main line (fp32 = the mixed path)")
-    ap.add_argument("--extra", default=None, choices=["riemann", "d2q25", "multiscale"],
+    ap.add_argument("--extra", default=None, choices=["riemann", "d2q25", "multiscale", "g_lattice"],
                     help="run only this one extra measurement and print its JSON line (for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -191,6 +191,30 @@ def pond_init(ctx, rho, ux, uy, T):
                            _on_device(rho, ux, uy, T)), "pond_init")
 
 
+class nvtx_range:
+    """An NVTX range (visible in Nsight timelines) around host calls that
+    enqueue steps; a no-op where PyTorch's NVTX bindings are unavailable."""
+
+    def __init__(self, name: str):
+        self.name = name
+        self._nvtx = None
+
+    def __enter__(self):
+        try:
+            import torch
+
+            torch.cuda.nvtx.range_push(self.name)
+            self._nvtx = torch.cuda.nvtx
+        except Exception:
+            self._nvtx = None
+        return self
+
+    def __exit__(self, *exc):
+        if self._nvtx is not None:
+            self._nvtx.range_pop()
+        return False
+
+
 def pond_step(ctx, n: int):
     _check(lib().pond_step(ctx, int(n)), "pond_step")
 
@@ -411,7 +435,8 @@ class Sim:
         pond_init(self.ctx, a[0], a[1], a[2] if self.D == 2 else None, a[3])
 
     def step(self, n: int):
-        pond_step(self.ctx, n)
+        with nvtx_range("pond_step"):
+            pond_step(self.ctx, n)
 
     def moments(self):
         out = [np.zeros(self.shape) for _ in range(4)]
@@ -475,7 +500,8 @@ class Batch:
         self.members.remove(sim)
 
     def step(self, steps=None):
-        pond_batch_step(self.b, steps)
+        with nvtx_range("pond_batch_step"):
+            pond_batch_step(self.b, steps)
 
     def info(self):
         return pond_batch_info(self.b)

@@ -187,6 +187,10 @@ class PondExecutor:
         return h
 
     def tick(self, handles, tick_steps):
+        with pond.nvtx_range("serve_tick"):
+            self._tick(tick_steps)
+
+    def _tick(self, tick_steps):
         for d in (1, 2):
             hs = self.handles[d]
             if not hs:

@@ -132,3 +132,16 @@ def test_request_stream_is_seeded_and_poisson():
         assert 5 <= r.steps <= 10
         n = r.cfg["nx"]
         assert (16 <= n <= 32) if r.dim == 2 else (64 <= n <= 128)
+
+
+def test_nvtx_ranges_nest_and_never_raise_on_the_host():
+    """The NVTX ranges around enqueued steps and serve ticks are markers only:
+    on a host without a GPU they neither raise nor leave a range open."""
+    from paper_2302_00310_gb300 import pond
+
+    with pond.nvtx_range("outer"):
+        with pond.nvtx_range("inner"):
+            pass
+    with pytest.raises(ValueError):
+        with pond.nvtx_range("raising"):
+            raise ValueError("propagates")

@@ -359,7 +359,10 @@ void pond_batch_destroy(pond_batch *b);
  * be POND_FP64, flux_frame POND_FRAME_AVG, dt > 0 (no CFL time step); the tile
  * is fixed (8x8 in 2D, 252 cells in 1D).  flags: host pointer or NULL; when
  * given, the call synchronises `stream` and stores the sticky POND_FLAG_* bits
- * of this call.  While the call's work runs the arrays hold intermediate
+ * of this call.  A synchronisation is not allowed while `stream` is being
+ * captured into a CUDA graph (it would invalidate the capture), so flags must
+ * be NULL then: a call with flags on a capturing stream returns POND_E_INVAL
+ * before any work.  While the call's work runs the arrays hold intermediate
  * values; after a POND_E_CUDA failure their contents are undefined.
  *
  * Its only scratch is one static __device__ array of POND_NOALLOC_SCRATCH_BYTES
@@ -371,7 +374,8 @@ void pond_batch_destroy(pond_batch *b);
  * on the GPU race.
  *
  * Errors: POND_E_NOMEM when the state does not fit the array (2D FP64:
- * 74,897 cells; 1D: 209,712 cells), POND_E_INVAL for bad arguments,
+ * 74,897 cells; 1D: 209,712 cells), POND_E_INVAL for bad arguments (or
+ * flags given while `stream` is capturing),
  * POND_E_NONPHYSICAL (only when flags is given), POND_E_CUDA. */
 #define POND_NOALLOC_SCRATCH_BYTES (16 * 1024 * 1024)
 pond_status pond_step_noalloc(pond_lattice lat, const int64_t dims[2], const pond_params *p,

@@ -263,56 +263,7 @@ bool walls_ok(const pond_params *p, int D, int64_t nx, int64_t ny) {
   return true;
 }
 
-void set_step_const(pond_ctx *c) {
-  const pond_params &p = c->p;
-  StepConst &K = c->K;
-  memset(&K, 0, sizeof(K));
-  K.nx = (int)c->nx;
-  K.ny = (int)c->ny;
-  for (int s = 0; s < 4; ++s) {
-    K.bc[s] = p.bc[s];
-    for (int m = 0; m < 4; ++m) K.inflow[s][m] = p.inflow[s][m];
-  }
-  const double dt = c->dt, tau = p.tau, h = 0.5 * dt;
-  K.lam = dt / p.dx;
-  // face phi = kappa1 phi_bar + kappa2 phi^eq (inverse of Eq. eq:FluxTransf)
-  K.kappa1 = 2.0 * tau / (2.0 * tau + h);
-  K.kr = (h / (2.0 * tau + h)) / K.kappa1;
-  // phi_bar^+ = (2 tau - h)/(2 tau + dt) phi~ + 3h/(2 tau + dt) phi^eq  (Eqs. eq:variableTransform, eq:Fbarplus)
-  K.kp_a = K.kappa1 * (2.0 * tau - h) / (2.0 * tau + dt);
-  K.kp_b = K.kappa1 * 3.0 * h / (2.0 * tau + dt);
-  K.a1 = (2.0 * tau - dt) / (2.0 * tau + dt);
-  K.a2 = 2.0 * dt / (2.0 * tau + dt);
-  const double tau2 = tau / p.prandtl;
-  K.qe = p.prandtl == 1.0 ? 1.0 : 1.0 + 0.5 * dt * (1.0 / tau - 1.0 / tau2);
-  const double cv = 1.0 / (p.gamma - 1.0);
-  K.inv_cv = 1.0 / cv;
-  K.gfac = cv - 0.5 * c->D;
-  K.iter_tol = p.iter_tol;
-  K.iter_max = p.iter_max;
-  K.tau1 = tau;
-  K.tau2 = tau2;
-  K.cfac = 1.0 + dt / (2.0 * tau);
-  K.inv2dx = 1.0 / (2.0 * p.dx);
-  K.grad_k = p.transform == POND_GRAD_K;
-  K.appc = p.flux_form == POND_FLUX_APPC;
-  K.limiter = p.limiter;
-  K.iterative = p.flux_frame == POND_FRAME_ITER;
-  K.xi_thr = (float)p.xi_fp64_threshold;
-  K.ms = p.multiscale;
-  K.ms_theta_u = p.ms_theta_u;
-  K.ms_theta_T = p.ms_theta_T;
-  K.cf.lam = (float)K.lam;
-  K.cf.kappa1 = (float)K.kappa1;
-  K.cf.kr = (float)K.kr;
-  K.cf.kp_a = (float)K.kp_a;
-  K.cf.kp_b = (float)K.kp_b;
-  K.cf.a1 = (float)K.a1;
-  K.cf.a2 = (float)K.a2;
-  K.cf.qe = (float)K.qe;
-  K.cf.inv_cv = (float)K.inv_cv;
-  K.cf.gfac = (float)K.gfac;
-}
+void set_step_const(pond_ctx *c) { pond_fill_step_const(c->K, c->p, c->D, c->nx, c->ny, c->dt); }
 
 void drop_graphs(pond_ctx *c) {
   for (int i = 0; i < 2; ++i)
@@ -853,3 +804,54 @@ pond_status pond_restore(pond_ctx *c, const void *host, size_t bytes) {
 }
 
 }  // extern "C"
+
+// The constants of one step (both entry points that launch the step kernels).
+void pond_fill_step_const(pond::StepConst &K, const pond_params &p, int D, int64_t nx, int64_t ny,
+                          double dt) {
+  memset(&K, 0, sizeof(K));
+  K.nx = (int)nx;
+  K.ny = (int)ny;
+  for (int s = 0; s < 4; ++s) {
+    K.bc[s] = p.bc[s];
+    for (int m = 0; m < 4; ++m) K.inflow[s][m] = p.inflow[s][m];
+  }
+  const double tau = p.tau, h = 0.5 * dt;
+  K.lam = dt / p.dx;
+  // face phi = kappa1 phi_bar + kappa2 phi^eq (inverse of Eq. eq:FluxTransf)
+  K.kappa1 = 2.0 * tau / (2.0 * tau + h);
+  K.kr = (h / (2.0 * tau + h)) / K.kappa1;
+  // phi_bar^+ = (2 tau - h)/(2 tau + dt) phi~ + 3h/(2 tau + dt) phi^eq  (Eqs. eq:variableTransform, eq:Fbarplus)
+  K.kp_a = K.kappa1 * (2.0 * tau - h) / (2.0 * tau + dt);
+  K.kp_b = K.kappa1 * 3.0 * h / (2.0 * tau + dt);
+  K.a1 = (2.0 * tau - dt) / (2.0 * tau + dt);
+  K.a2 = 2.0 * dt / (2.0 * tau + dt);
+  const double tau2 = tau / p.prandtl;
+  K.qe = p.prandtl == 1.0 ? 1.0 : 1.0 + 0.5 * dt * (1.0 / tau - 1.0 / tau2);
+  const double cv = 1.0 / (p.gamma - 1.0);
+  K.inv_cv = 1.0 / cv;
+  K.gfac = cv - 0.5 * D;
+  K.iter_tol = p.iter_tol;
+  K.iter_max = p.iter_max;
+  K.tau1 = tau;
+  K.tau2 = tau2;
+  K.cfac = 1.0 + dt / (2.0 * tau);
+  K.inv2dx = 1.0 / (2.0 * p.dx);
+  K.grad_k = p.transform == POND_GRAD_K;
+  K.appc = p.flux_form == POND_FLUX_APPC;
+  K.limiter = p.limiter;
+  K.iterative = p.flux_frame == POND_FRAME_ITER;
+  K.xi_thr = (float)p.xi_fp64_threshold;
+  K.ms = p.multiscale;
+  K.ms_theta_u = p.ms_theta_u;
+  K.ms_theta_T = p.ms_theta_T;
+  K.cf.lam = (float)K.lam;
+  K.cf.kappa1 = (float)K.kappa1;
+  K.cf.kr = (float)K.kr;
+  K.cf.kp_a = (float)K.kp_a;
+  K.cf.kp_b = (float)K.kp_b;
+  K.cf.a1 = (float)K.a1;
+  K.cf.a2 = (float)K.a2;
+  K.cf.qe = (float)K.qe;
+  K.cf.inv_cv = (float)K.inv_cv;
+  K.cf.gfac = (float)K.gfac;
+}

@@ -69,6 +69,11 @@ template <typename R> pond::State<R> state_of(const pond_ctx *c, int b) {
 
 }  // namespace pond_detail
 
+// the constants of one step for parameters p on a D-dimensional nx x ny grid
+// with time step dt (pond_abi.cu; the context path and pond_step_noalloc)
+void pond_fill_step_const(pond::StepConst &K, const pond_params &p, int D, int64_t nx, int64_t ny,
+                          double dt);
+
 // removes a context from its batch (pond_batch.cu); called by pond_destroy()
 void pond_batch_detach(pond_ctx *c);
 

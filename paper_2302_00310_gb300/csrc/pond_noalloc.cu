@@ -19,6 +19,7 @@
 #include <mutex>
 
 #include "pond.h"
+#include "pond_internal.h"
 #include "pond_kernels.cuh"
 
 // the scratch: [status block (256 B)][one FP64 state buffer]
@@ -117,38 +118,6 @@ bool params_ok(const pond_params *p, int D) {
          p->flux_frame == POND_FRAME_AVG && p->multiscale == 0 && p->g_same_as_f == 0;
 }
 
-// the constants of one step (same definitions as the context path)
-pond::StepConst step_const(const pond_params &p, int D, int64_t nx, int64_t ny) {
-  pond::StepConst K;
-  memset(&K, 0, sizeof(K));
-  K.nx = (int)nx;
-  K.ny = (int)ny;
-  for (int s = 0; s < 4; ++s) {
-    K.bc[s] = p.bc[s];
-    for (int m = 0; m < 4; ++m) K.inflow[s][m] = p.inflow[s][m];
-  }
-  const double dt = p.dt, tau = p.tau, h = 0.5 * dt;
-  K.lam = dt / p.dx;
-  K.kappa1 = 2.0 * tau / (2.0 * tau + h);
-  K.kr = (h / (2.0 * tau + h)) / K.kappa1;
-  K.kp_a = K.kappa1 * (2.0 * tau - h) / (2.0 * tau + dt);
-  K.kp_b = K.kappa1 * 3.0 * h / (2.0 * tau + dt);
-  K.a1 = (2.0 * tau - dt) / (2.0 * tau + dt);
-  K.a2 = 2.0 * dt / (2.0 * tau + dt);
-  K.qe = p.prandtl == 1.0 ? 1.0 : 1.0 + 0.5 * dt * (1.0 / tau - 1.0 / (tau / p.prandtl));
-  const double cv = 1.0 / (p.gamma - 1.0);
-  K.inv_cv = 1.0 / cv;
-  K.gfac = cv - 0.5 * D;
-  K.tau1 = tau;
-  K.tau2 = tau / p.prandtl;
-  K.cfac = 1.0 + dt / (2.0 * tau);
-  K.inv2dx = 1.0 / (2.0 * p.dx);
-  K.grad_k = p.transform == POND_GRAD_K;
-  K.appc = p.flux_form == POND_FLUX_APPC;
-  K.limiter = p.limiter;
-  return K;
-}
-
 }  // namespace
 
 extern "C" pond_status pond_step_noalloc(pond_lattice lat, const int64_t dims[2],
@@ -166,10 +135,18 @@ extern "C" pond_status pond_step_noalloc(pond_lattice lat, const int64_t dims[2]
   const size_t state_bytes = (qf + qg + 3) * N * sizeof(double);
   if (256 + state_bytes > (size_t)POND_NOALLOC_SCRATCH_BYTES) return POND_E_NOMEM;
 
+  cudaStream_t st = (cudaStream_t)stream;
+  if (flags) {
+    // reading the flags synchronises the stream, which a stream capture
+    // forbids (and would invalidate): flags must be NULL while capturing
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const cudaError_t qe = cudaStreamIsCapturing(st, &cs);
+    if (qe != cudaSuccess) (void)cudaGetLastError();
+    if (qe != cudaSuccess || cs != cudaStreamCaptureStatusNone) return POND_E_INVAL;
+  }
   unsigned char *scratch = nullptr;
   pond_status s = scratch_for_current_device(&scratch);
   if (s != POND_OK) return s;
-  cudaStream_t st = (cudaStream_t)stream;
   pond::Stats *stats = reinterpret_cast<pond::Stats *>(scratch);
   double *buf = reinterpret_cast<double *>(scratch + 256);
   pond::State<double> caller{f, g, ux, D == 2 ? uy : buf + (qf + qg + 1) * N, T};
@@ -179,7 +156,8 @@ extern "C" pond_status pond_step_noalloc(pond_lattice lat, const int64_t dims[2]
     (void)cudaGetLastError();
     return POND_E_CUDA;
   }
-  const pond::StepConst K = step_const(*p, D, nx, ny);
+  pond::StepConst K;
+  pond_fill_step_const(K, *p, D, nx, ny, p->dt);
   if (n > 0 && !change_basis<true>(D, f, g, T, N, st)) return POND_E_CUDA;
   for (int64_t i = 0; i < n; ++i) {
     const pond::State<double> &in = (i & 1) ? other : caller;

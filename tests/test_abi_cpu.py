@@ -13,7 +13,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "pond.h")).read()
+    inc = os.path.join(ROOT, "include")
+    src = "".join(open(os.path.join(inc, h)).read() for h in sorted(os.listdir(inc)) if h.endswith(".h"))
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(pond_[a-z_]+)\s*\(", src)))
 
@@ -128,3 +129,15 @@ def test_batch_tile_codes_are_resolved_before_any_device_work(L):
         else:
             assert st == pond.POND_OK
             L.pond_batch_destroy(b)
+
+
+def test_noalloc_refuses_host_arrays(L):
+    """pond_step_noalloc has no host-memory path: numpy arrays are refused in
+    the binding, before the C call could treat them as device addresses."""
+    import numpy as np
+
+    p = pond.pond_params_default()
+    p.dt = 1e-4
+    a = np.zeros(64)
+    with pytest.raises(TypeError):
+        pond.pond_step_noalloc(pond.POND_D1Q4, (16, 1), p, a, a, a, None, a, 1)

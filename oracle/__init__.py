@@ -85,6 +85,8 @@ def lib():
         _lib.orc_init.argtypes = [ctypes.c_void_p] + [P] * 9
         _lib.orc_init.restype = ctypes.c_int
         _lib.orc_run.argtypes = [ctypes.c_void_p, P, P, P, P, P, ctypes.c_int64, ctypes.c_void_p]
+        _lib.orc_ghost_pub.argtypes = [ctypes.c_void_p] + [P] * 5 + [ctypes.c_int] * 2 + [P] * 3
+        _lib.orc_ghost_pub.restype = ctypes.c_int
         _lib.orc_ms_measure_pub.argtypes = [ctypes.c_void_p] + [P] * 5
         _lib.orc_ms_measure_pub.restype = ctypes.c_int
         _lib.orc_run.restype = ctypes.c_int
@@ -318,6 +320,19 @@ def ms_measure(cfg: Config, ux, uy, T):
     if rc != 0:
         raise ValueError("oracle: invalid configuration")
     return su, sT
+
+
+def ghost(cfg: Config, st: State, j: int, k: int):
+    """The ghost cell (j, k) (up to two layers beyond the interior) that the
+    run's boundary rules build from ``st``: (f[Qf], g[Qg], (ux, uy, T))."""
+    f = np.zeros(cfg.qf**cfg.D)
+    g = np.zeros(cfg.qg**cfg.D)
+    fr = np.zeros(3)
+    rc = lib().orc_ghost_pub(ctypes.byref(cfg._c()), _ptr(st.f), _ptr(st.g), _ptr(st.ux),
+                             _ptr(st.uy), _ptr(st.T), int(j), int(k), _ptr(f), _ptr(g), _ptr(fr))
+    if rc != 0:
+        raise ValueError("oracle: invalid configuration or not a ghost cell (rc=%d)" % rc)
+    return f, g, tuple(fr)
 
 
 def moments(cfg: Config, st: State):

@@ -1168,6 +1168,39 @@ int orc_run(const orc_params *p, double *f, double *g, double *ux, double *uy, d
   return 0;
 }
 
+/* The ghost cell (j, k) of the padded grid (two layers beyond the interior)
+ * built from the interior state (f, g, ux, uy, T) by the run's boundary
+ * rules: its populations fout[Qf], gout[Qg] and frame (ux, uy, T) in frame[3].
+ * Returns 1 for invalid parameters, 2 on allocation failure, 3 if (j, k) is
+ * not a ghost of the padded grid. */
+int orc_ghost_pub(const orc_params *p, const double *f, const double *g, const double *ux,
+                  const double *uy, const double *T, int j, int k, double *fout, double *gout,
+                  double *frame) {
+  if (!orc_check(p)) return 1;
+  const int ny = p->D == 2 ? p->ny : 1, klo = p->D == 2 ? -2 : 0, khi = p->D == 2 ? ny + 2 : 1;
+  if (j < -2 || j >= p->nx + 2 || k < klo || k >= khi || (j >= 0 && j < p->nx && k >= 0 && k < ny))
+    return 3;
+  orc_grid G;
+  if (!orc_grid_alloc(&G, p)) { orc_grid_free(&G); return 2; }
+  const int ncp = orc_ncp(&G);
+  const size_t n = (size_t)G.nx * G.ny;
+  for (int kk = 0; kk < G.ny; ++kk)
+    for (int jj = 0; jj < G.nx; ++jj) {
+      size_t s = (size_t)kk * G.nx + jj;
+      int c = orc_pidx(&G, jj, kk);
+      for (int i = 0; i < G.Qf; ++i) G.f[i * ncp + c] = f[i * n + s];
+      for (int i = 0; i < G.Qg; ++i) G.g[i * ncp + c] = g[i * n + s];
+      G.ux[c] = ux[s]; G.uy[c] = p->D == 2 ? uy[s] : 0.0; G.T[c] = T[s];
+    }
+  orc_fill_ghosts(&G);
+  const int c = orc_pidx(&G, j, k);
+  for (int i = 0; i < G.Qf; ++i) fout[i] = G.f[i * ncp + c];
+  for (int i = 0; i < G.Qg; ++i) gout[i] = G.g[i * ncp + c];
+  frame[0] = G.ux[c]; frame[1] = G.uy[c]; frame[2] = G.T[c];
+  orc_grid_free(&G);
+  return 0;
+}
+
 /* Multiscale switching measures s_u, s_T of every interior cell of the
  * fields (ux, uy, T) under the run's boundary rules. */
 int orc_ms_measure_pub(const orc_params *p, const double *ux, const double *uy, const double *T,

@@ -122,13 +122,19 @@ def random_tube_1d(seed: int, n: int | None = None, steps: int | None = None):
 
 
 def pulse_2d(n: int = 256, seed: int = 0, steps: int = 1000, cfl: float = 0.2, mach: float = 2.0,
-             angle_deg: float = 30.0, amp: float = 0.1):
+             angle_deg: float = 30.0, amp: float = 0.1, sigma: float | None = None,
+             centre=None, tau: float = 1e-4):
     """Periodic isobaric Gaussian pulse advected at Mach ``mach`` (w.r.t. the
     background sound speed sqrt(gamma)) at ``angle_deg``; rho = 1 + amp g,
-    T = 1/rho, g a periodic Gaussian with seeded centre and width."""
+    T = 1/rho, g a periodic Gaussian with seeded centre and width (``sigma``
+    and ``centre`` override the seeded values, for refinement studies at a
+    fixed profile; the seeded draws are made either way)."""
     g = rng(seed)
     xc = g.uniform(0.0, 1.0, 2)
-    sigma = g.uniform(0.05, 0.15)
+    sg = g.uniform(0.05, 0.15)
+    sigma = sg if sigma is None else float(sigma)
+    if centre is not None:
+        xc = np.asarray(centre, dtype=np.float64)
     x = (np.arange(n) + 0.5) / n
     X, Y = np.meshgrid(x, x, indexing="xy")  # [ny, nx]
     prof = np.zeros((n, n))
@@ -141,10 +147,25 @@ def pulse_2d(n: int = 256, seed: int = 0, steps: int = 1000, cfl: float = 0.2, m
     a = math.radians(angle_deg)
     ux = np.full((n, n), U * math.cos(a))
     uy = np.full((n, n), U * math.sin(a))
-    cfg = _base(2, n, n, tau=1e-4, dx=1.0 / n, bc=(BC_PERIODIC,) * 4)
+    cfg = _base(2, n, n, tau=tau, dx=1.0 / n, bc=(BC_PERIODIC,) * 4)
     cfg["dt"] = dt_from_cfl(ux, uy, T, 1.0 / n, cfl)
     return dict(cfg=cfg, rho=rho, ux=ux, uy=uy, T=T, steps=steps, seed=seed,
-                centre=xc, sigma=sigma, velocity=(U * math.cos(a), U * math.sin(a)))
+                centre=xc, sigma=sigma, amp=amp, velocity=(U * math.cos(a), U * math.sin(a)))
+
+
+def pulse_exact_2d(w, t):
+    """The pulse's initial density translated by u t (periodic): the exact
+    Euler solution of an entropy wave (uniform pressure and velocity)."""
+    n = w["cfg"]["nx"]
+    x = (np.arange(n) + 0.5) / n
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    cx = (w["centre"][0] + w["velocity"][0] * t) % 1.0
+    cy = (w["centre"][1] + w["velocity"][1] * t) % 1.0
+    prof = np.zeros((n, n))
+    for sx in (-1, 0, 1):
+        for sy in (-1, 0, 1):
+            prof += np.exp(-((X - cx - sx) ** 2 + (Y - cy - sy) ** 2) / (2 * w["sigma"] ** 2))
+    return 1.0 + w["amp"] * prof
 
 
 def _quadrants(n, states):

@@ -88,3 +88,110 @@ def test_thermal_couette_matches_the_analytic_profile_at_first_order():
     # a lower Prandtl number halves the heating term Pr Ec / 2
     e16b, _ = _couette_error(16, 0.5, 8000)
     assert e16b < 0.06
+
+
+# ---- the ghost's Chapman-Enskog moments, recovered by quadrature ------------
+def _ghost_moments(q, D, pops, T):
+    """Central moments of a ghost's populations in its co-moving frame: the
+    nodes are xi_i = sqrt(T) c_i (node i = iy*q + ix).  Returns the moments of
+    order 0..3 as arrays over the D axes."""
+    c = np.polynomial.hermite_e.hermegauss(q)[0]  # the roots of He_q, ascending (Table I)
+    if D == 1:
+        xi = np.sqrt(T) * c[:, None]
+    else:
+        xi = np.sqrt(T) * np.array([[c[i % q], c[i // q]] for i in range(q * q)])
+    m0 = pops.sum()
+    m1 = np.einsum("i,ia->a", pops, xi)
+    m2 = np.einsum("i,ia,ib->ab", pops, xi, xi)
+    m3 = np.einsum("i,ia,ib,ic->abc", pops, xi, xi, xi)
+    return m0, m1, m2, m3
+
+
+@pytest.mark.parametrize("D", [1, 2])
+def test_wall_ghost_carries_the_chapman_enskog_moments_of_sec_iv_d(D):
+    """Linear fields u = u_0 + a y (+ e y along the normal in 2D), T = T_0 + b y
+    with the walls on the same lines: the ghost's centred gradients are exactly
+    (a, e, b).  Its populations, summed by quadrature in its co-moving frame,
+    must carry the equilibrium plus the paper's first-order non-equilibrium
+    (Sec. IV.D) scaled by 1 + dt/(2 tau_1) (the stored variable is phi~):
+        P^(1)  = -tau_1 rho T (S - (div u)/C_v I)
+        Q^(1)  = -tau_2 rho T sym(grad T I)              (central: no u P^(1) part)
+        M_g0   = -tau_1 rho T (2 C_v - D) (div u)/C_v
+        M_g1   = -tau_2 rho T (2 C_v - D) grad T          (central: no M_g0 u part)
+        M_g2   = -tau_1 rho T (2 C_v - D) T S             (the T S term only)
+    with S = grad u + grad u^T.  Pr = 0.5 makes tau_2 = 2 tau_1 and
+    dt = tau_1 makes the factor 1.5, so a swapped relaxation time or a missing
+    factor changes every checked moment by a third or more."""
+    tau, pr, gamma = 5e-3, 0.5, 1.4
+    t1, t2, cv = tau, tau / pr, 1.0 / (gamma - 1.0)
+    dt = tau
+    cf = 1.0 + dt / (2.0 * t1)
+    rho0, u0, a, e, T0, b = 1.3, 0.3, 0.8, 0.5, 0.9, 0.4
+    n = 6
+    dx = 1.0 / n
+    y = (np.arange(n) + 0.5) * dx
+    if D == 2:
+        nx = 4
+        shp = (n, nx)
+        Y = np.repeat(y[:, None], nx, axis=1)
+        ux, uy, T = u0 + a * Y, e * Y, T0 + b * Y
+        walls = ((0.0,) * 4, (0.0,) * 4, (0.0, u0, 0.0, T0), (0.0, u0 + a, e, T0 + b))
+        cfg = W._base(2, nx, n, tau=tau, dx=dx, prandtl=pr, gamma=gamma, bc=(0, 0, 3, 3), inflow=walls)
+        gj, gk = 1, -1
+    else:
+        shp = (1, n)
+        ux, uy, T = (u0 + a * y)[None, :], np.zeros(shp), (T0 + b * y)[None, :]
+        walls = ((0.0, u0, 0.0, T0), (0.0, u0 + a, 0.0, T0 + b), (0.0,) * 4, (0.0,) * 4)
+        cfg = W._base(1, n, 1, tau=tau, dx=dx, prandtl=pr, gamma=gamma, bc=(3, 3, 0, 0), inflow=walls)
+        gj, gk = -1, 0
+    cfg["dt"] = dt
+    oc = oracle.Config.from_dict(cfg)
+    st = oracle.init(oc, np.full(shp, rho0), ux, uy, T)
+    f, g, (gux, guy, gT) = oracle.ghost(oc, st, gj, gk)
+
+    # the ghost's fields: the linear continuation half a cell beyond the wall
+    yg = -0.5 * dx
+    assert gT == pytest.approx(T0 + b * yg, rel=1e-14)
+    assert gux == pytest.approx(u0 + a * yg, rel=1e-14)
+    if D == 2:
+        assert guy == pytest.approx(e * yg, abs=1e-15)
+    rho, Tg = rho0, gT
+    # exact gradients: grad u[d][c] = d u_c / d x_d, grad T[d]
+    if D == 2:
+        gu = np.array([[0.0, 0.0], [a, e]])
+        gTv = np.array([0.0, b])
+        u = np.array([gux, guy])
+    else:
+        gu = np.array([[a]])
+        gTv = np.array([b])
+        u = np.array([gux])
+    I = np.eye(D)
+    div = np.trace(gu)
+    S = gu + gu.T
+    rT = rho * Tg
+    P1 = -t1 * rT * (S - div / cv * I)
+    Q1 = -t2 * rT * (np.einsum("a,bc->abc", gTv, I) + np.einsum("b,ac->abc", gTv, I)
+                     + np.einsum("c,ab->abc", gTv, I))
+    gf = 2.0 * cv - D
+    Mg0 = -t1 * rT * gf * div / cv
+    Mg1 = -t2 * rT * gf * gTv
+    Mg2 = -t1 * rT * gf * Tg * S
+
+    m0, m1, m2, m3 = _ghost_moments(oc.qf, D, f, Tg)
+    scale = rT * (abs(a) + abs(b)) * tau
+    assert m0 == pytest.approx(rho, rel=1e-13)
+    np.testing.assert_allclose(m1, 0.0, atol=1e-13 * rho)
+    np.testing.assert_allclose(m2, rT * I + cf * P1, rtol=0, atol=1e-12 * scale)
+    np.testing.assert_allclose(m3, cf * Q1, rtol=0, atol=1e-12 * scale)
+
+    geq0 = (cv - 0.5 * D) * Tg * rho
+    n0, n1, n2, _ = _ghost_moments(oc.qg, D, g, Tg)
+    assert n0 - geq0 == pytest.approx(cf * Mg0, abs=1e-12 * scale)
+    np.testing.assert_allclose(n1, cf * Mg1, rtol=0, atol=1e-12 * scale)
+    np.testing.assert_allclose(n2 - geq0 * Tg * I, cf * Mg2, rtol=0, atol=1e-12 * scale)
+    # the reading of M_g2 on its own: the printed form's extra term
+    # sym(u grad T) is not carried (it is not the raw form of a central moment
+    # that the frame change would produce), and here it would be visible
+    extra = -t1 * rT * gf * (np.outer(u, gTv) + np.outer(gTv, u))
+    assert np.max(np.abs(extra)) > 0.1 * np.max(np.abs(Mg2))
+    assert not np.allclose(n2 - geq0 * Tg * I, cf * (Mg2 + extra), rtol=1e-3, atol=0)

@@ -74,8 +74,13 @@ FLOPS_PER_CELL = {"fp64": 8771.6, "fp32": 8708.2, "fp32_fp64part": 59.2,
 BYTES_PER_CELL_FP64 = 2 * 28 * 8          # state read once + written once
 BYTES_PER_CELL_FP32 = 2 * (28 * 4 + 4 * 8)  # + the FP64 conserved moments
 CLOCK_MAX_GHZ = 2.07
+# nominal unit-count peaks (context only: the roofline divides by the FMA
+# peaks that pond_measure_fma_peak() measures in the same run)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * CLOCK_MAX_GHZ / 1e3     # 2 FP64 FMA/clk/SM
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * CLOCK_MAX_GHZ / 1e3   # 128 FP32 FMA/clk/SM
+# the step kernels the main line launches, as the profiler names them
+KERNEL_FP64 = "member_step_kernel<double, 2, 4, 8, 14, 128, 2, 0, 0, 3>"
+KERNEL_FP32 = "member_step_kernel<float, 2, 4, 8, 16, 160, 2, 0, 0, 3>"
 # dram__bytes_read.sum + dram__bytes_write.sum of one main-line step launch
 # (FP64 and mixed path), keyed by source digest (None once the sources change)
 TRAFFIC_BY_DIGEST = {
@@ -252,23 +257,47 @@ def _linf(a, b):
     return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
 
 
-def _roofline(flops_key, cells, per_launch_s, peak_tflops, bytes_per_cell, kernel, digest,
-              precision_note):
+def _roofline(flops_key, cells, per_launch_s, peak, bytes_per_cell, kernel, digest):
+    """ALU roofline of one step launch: the flops of a cell update times the
+    cells of a launch over the launch's CUDA-event time, against `peak`
+    (TFLOP/s and how it was obtained); the HBM fraction beside it."""
     fpc = FLOPS_PER_CELL.get(flops_key)
     hbm_peak = _measured_peaks().get("hbm_gbs", 6652.0)
-    out = {"bound": "alu", "unit": "TFLOP/s", "peak": peak_tflops,
-           "peak_source": precision_note, "kernel": kernel, "flops_per_cell": fpc,
+    out = {"bound": "alu", "unit": "TFLOP/s", "peak": peak["tflops"],
+           "peak_source": peak["source"], "kernel": kernel, "flops_per_cell": fpc,
            "achieved": None, "frac": None,
            "traffic": TRAFFIC_BY_DIGEST.get(digest, {}).get(flops_key),
-           "hbm": {"achieved_gbs": bytes_per_cell * cells / per_launch_s / 1e9, "peak_gbs": hbm_peak}}
+           "hbm": {"achieved_gbs": bytes_per_cell * cells / per_launch_s / 1e9, "peak_gbs": hbm_peak,
+                   "bytes_per_cell": bytes_per_cell}}
     out["hbm"]["frac"] = out["hbm"]["achieved_gbs"] / hbm_peak
     if fpc:
         out["achieved"] = fpc * cells / per_launch_s / 1e12
-        out["frac"] = out["achieved"] / peak_tflops
+        out["frac"] = out["achieved"] / peak["tflops"]
     return out
 
 
-def bench_mixed(torch, pond, W, flush):
+def measure_fma_peaks(pond, local):
+    """FP64 and FP32 fma throughput of this GPU (pond_measure_fma_peak), with
+    the SM clock sampled while it runs."""
+    with ClockSampler(local) as clk:
+        fp64, ms64 = pond.pond_measure_fma_peak(pond.POND_FP64, 0.5)
+        fp32, ms32 = pond.pond_measure_fma_peak(pond.POND_FP32_MIXED, 0.5)
+    out = {"fp64_tflops": fp64, "fp32_tflops": fp32, "launch_ms": {"fp64": ms64, "fp32": ms32},
+           "how": "pond_measure_fma_peak: independent fma chains, all SMs, best of 5 launches"}
+    c = clk.summary()
+    if c:
+        out["clocks"] = c
+    return out
+
+
+def _peak(peaks, key):
+    src = "measured: pond_measure_fma_peak %s fma chains in this run" % key.upper()
+    if c := peaks.get("clocks"):
+        src += " at %.0f MHz median SM clock" % c["sm_mhz"]
+    return {"tflops": peaks["%s_tflops" % key], "source": src}
+
+
+def bench_mixed(torch, pond, W, flush, peaks):
     """The pulse on the mixed path: MLUPS and the error of the full run."""
     w = W.pulse_2d(n=256, seed=0)
     fields = (w["rho"], w["ux"], w["uy"], w["T"])
@@ -296,9 +325,8 @@ def bench_mixed(torch, pond, W, flush):
         "l1_T_vs_fp64": _l1(m32[3], m64[3]), "error_after_steps": w["steps"],
         "mass_drift": float(m32[0].sum() / m64[0].sum() - 1.0), "nonphysical": bool(fl32 & 1),
         "stated_l1_bound": 1e-5,
-        "roofline": _roofline("fp32", n, per, FP32_PEAK_TFLOPS, BYTES_PER_CELL_FP32,
-                              "pond::member_step_kernel<float,2,8,16,160,2,false>", _build_digest(),
-                              "FP32: 128 FMA/clk/SM x 152 SMs x 2070 MHz (nominal 80.5 TFLOP/s)"),
+        "roofline": _roofline("fp32", n, per, _peak(peaks, "fp32"), BYTES_PER_CELL_FP32, KERNEL_FP32,
+                              _build_digest()),
     }
 
 
@@ -473,7 +501,7 @@ def bench_batched(torch, pond, W):
     ws_ = [W.shock_bubble_2d(seed=s) for s in range(64)]
     cells = sum(w["cfg"]["nx"] * w["cfg"]["ny"] for w in ws_)
     out = {"workload": "64 shock-bubble instances, sides %d-%d (log-uniform seeded), Mach 1.5-5, "
-                       "bubble density ratio 0.1-10, Pr 0.71, minmod, inflow left" %
+                       "bubble density ratio 0.1-10, Pr 0.71, minmod, tau 1e-3, inflow left" %
                        (min(w["cfg"]["nx"] for w in ws_), max(w["cfg"]["nx"] for w in ws_)),
            "instances": len(ws_), "cells": cells, "unit": UNIT}
     moments = {}
@@ -514,21 +542,6 @@ def bench_batched(torch, pond, W):
     return out
 
 
-def _pulse_exact(w, t):
-    """The pulse workload's initial density translated by u t (periodic): the
-    exact Euler entropy wave."""
-    n = w["cfg"]["nx"]
-    x = (np.arange(n) + 0.5) / n
-    X, Y = np.meshgrid(x, x, indexing="xy")
-    cx = (w["centre"][0] + w["velocity"][0] * t) % 1.0
-    cy = (w["centre"][1] + w["velocity"][1] * t) % 1.0
-    prof = np.zeros((n, n))
-    for sx in (-1, 0, 1):
-        for sy in (-1, 0, 1):
-            prof += np.exp(-((X - cx - sx) ** 2 + (Y - cy - sy) ** 2) / (2 * w["sigma"] ** 2))
-    return 1.0 + 0.1 * prof
-
-
 def bench_iterated(torch, pond, W, iter_tol=1e-9, iter_max=40):
     """The iterated face frame against the averaged one (the comparison of
     Sec. V.D, on problems with exact solutions): Sod tubes and the advected
@@ -563,7 +576,7 @@ def bench_iterated(torch, pond, W, iter_tol=1e-9, iter_max=40):
             t_end = 0.25
             steps = int(np.ceil(t_end / w["cfg"]["dt"]))
             cfg0 = dict(w["cfg"], dt=t_end / steps)
-            exact = _pulse_exact(w, t_end)
+            exact = W.pulse_exact_2d(w, t_end)
             row = {"problem": "pulse", "n": n, "cfl": cfl, "steps": steps}
             for it in (0, 1):
                 cfg = dict(cfg0, iterative=it, iter_tol=iter_tol, iter_max=iter_max)
@@ -632,7 +645,10 @@ def bench_couette(torch, pond, W, ny=150, viscous_times=0.25):
                         "one batch" % ny, "seconds": el, "cases": rows}
 
 
-def bench_serve(pond, serve_mod, n_requests=24, rate=200.0):
+def bench_serve(pond, serve_mod, n_requests=200, rate=4.0):
+    """The serving statement: a fixed count of requests of the C5 mix at the
+    sustained rate (about 4 requests/s from the sweep: the offered 200/s is
+    far beyond one GPU), p50/p99 time to solution over all of them."""
     reqs = serve_mod.make_requests(n_requests, rate=rate, seed=0)
     ex = serve_mod.PondExecutor(precision=pond.POND_FP32_MIXED, capacity=64, graph_steps=8)
     srv = serve_mod.Server(ex, budget_bytes=16 << 30, tick_steps=64)
@@ -642,13 +658,32 @@ def bench_serve(pond, serve_mod, n_requests=24, rate=200.0):
     s.update({"workload": "Poisson stream at %g req/s: D1Q4 Sod-type tubes (256-8192 cells) and "
                           "D2Q16 shock-bubble runs (128^2-1024^2), 500-5000 steps each, FP32-mixed"
                           % rate,
-              "sample": "%d requests (%d 2D)" % (n_requests, sum(1 for r in out if r.dim == 2)),
-              "budget_gb": 16 << 30 >> 30, "peak_resident_gb": srv.peak_bytes / 1e9,
+              "sample": "%d requests (%d 2D), every one finished" % (
+                  n_requests, sum(1 for r in out if r.dim == 2)),
+              "rate": rate, "budget_gb": 16 << 30 >> 30, "peak_resident_gb": srv.peak_bytes / 1e9,
               "ticks": srv.ticks, "tick_steps": 64})
     return s
 
 
-def bench_serve_sweep(pond, serve_mod, rates=(1.0, 2.0, 4.0, 8.0), n_requests=12):
+def bench_serve_offered(pond, serve_mod, n_requests=400, rate=200.0, wall_s=30.0):
+    """The C5 stream at its offered 200 requests/s, served for a fixed wall
+    time: throughput, the latency of the requests finished by then, and the
+    queue left at the end."""
+    reqs = serve_mod.make_requests(n_requests, rate=rate, seed=2)
+    ex = serve_mod.PondExecutor(precision=pond.POND_FP32_MIXED, capacity=64, graph_steps=8)
+    srv = serve_mod.Server(ex, budget_bytes=16 << 30, tick_steps=64)
+    out = srv.run(reqs, wall_limit=wall_s)
+    ex.close()
+    s = serve_mod.summary(out, makespan=srv.stopped_at)
+    s.update({"workload": "the C5 mix offered at %g req/s (%d requests drawn), served for %g s of "
+                          "wall time, FP32-mixed" % (rate, n_requests, wall_s),
+              "wall_limit_s": wall_s, "stopped_at_s": srv.stopped_at,
+              "note": "p50/p99 over the requests finished within the wall time; the rest are "
+                      "counted as running, queued or not yet arrived"})
+    return s
+
+
+def bench_serve_sweep(pond, serve_mod, rates=(1.0, 2.0, 4.0, 8.0), n_requests=50):
     """The C5 stream at lower rates: the offered 200 requests/s is far beyond
     one GPU, so the fixed-count run above measures queueing; this sweep finds
     the rate the server sustains (p99 time to solution within twice its value
@@ -686,6 +721,7 @@ def run_gpu(args, dist, rank, ws):
                   "g_lattice": bench_g_lattice}[args.extra]
             print(json.dumps(dict(extra=args.extra, **fn(torch, pond, W))), flush=True)
         return
+    peaks = measure_fma_peaks(pond, local)
     w = W.pulse_2d(n=256, seed=0)
     fp32 = args.precision == "fp32"
     cfg = dict(w["cfg"], precision=pond.POND_FP32_MIXED if fp32 else pond.POND_FP64)
@@ -727,13 +763,14 @@ def run_gpu(args, dist, rank, ws):
 
     extras = {}
     if not args.no_extras and rank == 0:
-        extras["mixed"] = bench_mixed(torch, pond, W, flush)
+        extras["mixed"] = bench_mixed(torch, pond, W, flush, peaks)
         extras["riemann"] = bench_riemann(torch, pond, W)
         extras["batched"] = bench_batched(torch, pond, W)
         extras["d2q25"] = bench_d2q25(torch, pond, W)
         extras["multiscale"] = bench_multiscale(torch, pond, W)
         extras["g_lattice"] = bench_g_lattice(torch, pond, W)
         extras["serve"] = bench_serve(pond, serve_mod)
+        extras["serve_offered"] = bench_serve_offered(pond, serve_mod)
         if not args.no_studies:
             extras["serve_sweep"] = bench_serve_sweep(pond, serve_mod)
             extras["iterated"] = bench_iterated(torch, pond, W)
@@ -747,13 +784,11 @@ def run_gpu(args, dist, rank, ws):
     per_launch_s = sum_ms * 1e-3 / args.steps
     digest = _build_digest()
     if fp32:
-        roof = _roofline("fp32", n, per_launch_s, FP32_PEAK_TFLOPS, BYTES_PER_CELL_FP32,
-                         "pond::member_step_kernel<float,2,8,16,160,2,false>", digest,
-                         "FP32: 128 FMA/clk/SM x 152 SMs x 2070 MHz (nominal 80.5 TFLOP/s)")
+        roof = _roofline("fp32", n, per_launch_s, _peak(peaks, "fp32"), BYTES_PER_CELL_FP32, KERNEL_FP32,
+                         digest)
     else:
-        roof = _roofline("fp64", n, per_launch_s, FP64_PEAK_TFLOPS, BYTES_PER_CELL_FP64,
-                         "pond::member_step_kernel<double,2,8,14,128,2,false>", digest,
-                         "FP64: 2 FMA/clk/SM x 152 SMs x 2070 MHz (nominal 1.26 TFLOP/s)")
+        roof = _roofline("fp64", n, per_launch_s, _peak(peaks, "fp64"), BYTES_PER_CELL_FP64, KERNEL_FP64,
+                         digest)
     line = {
         "metric": METRIC, "value": mlups, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": sum_ms / args.steps, "higher_is_better": True,
@@ -765,6 +800,7 @@ def run_gpu(args, dist, rank, ws):
                    "tile": tile, "l2": "flushed between timed steps (256 MiB written, then another 256 MiB read)",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "roofline": roof,
+        "fma_peaks": peaks,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 4 * n * 8 / args.steps,
                 "d2h_bytes_per_step": 4 * n * 8},
         "gpu_launches": args.steps,

@@ -35,7 +35,9 @@ def _digest() -> str:
     for p in sorted(glob.glob(os.path.join(CSRC, "*"))) + [os.path.join(INCLUDE, "pond.h")]:
         with open(p, "rb") as fh:
             h.update(os.path.basename(p).encode() + fh.read())
-    h.update(" ".join(ARCH + FLAGS).encode())
+    # the flags without the include directories: those are absolute paths,
+    # which differ between checkouts of the same sources
+    h.update(" ".join(ARCH + [f for f in FLAGS if f not in (INCLUDE, CSRC)]).encode())
     return h.hexdigest()
 
 

@@ -165,19 +165,17 @@ template <typename R> __device__ __forceinline__ R qnan();
 template <> __device__ __forceinline__ double qnan<double>() { return __longlong_as_double(0x7ff8000000000000LL); }
 template <> __device__ __forceinline__ float qnan<float>() { return __int_as_float(0x7fc00000); }
 
-// x / y to about 1 ulp: the hardware reciprocal approximation
-// (rcp.approx.ftz.f64) refined by one Newton step, then one residual
-// correction of the quotient (each step squares the relative error).
-__device__ __forceinline__ double div_nr(double x, double y) {
-  double r;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(y));
-  r = fma(r, fma(-y, r, 1.0), r);
-  const double q = x * r;
-  return fma(fma(-y, q, x), r, q);
-}
 __device__ __forceinline__ float div_nr(float x, float y) { return __fdividef(x, y); }
-// 1/y to about 2^-40: the hardware approximation refined by one Newton step
-// (for values that are rounded to FP32 afterwards)
+// 1/y to about 2^-40 relative, for 2^-1022 <= |y| < 2^1022: the hardware
+// approximation rcp.approx.ftz.f64 refined by one Newton-Raphson step for the
+// reciprocal, r1 = r0 + r0 (1 - y r0), written as two fused multiply-adds
+// (the FMA form of Newton's iteration of P. Markstein, "Computation of
+// elementary functions on the IBM RISC System/6000 processor", IBM J. Res.
+// Dev. 34 (1990) 111-119); one step squares the relative error of r0.  Used
+// where the result feeds a quantity that tolerates that error (the van Leer
+// slope, which enters the trace times an offset below 1; the mixed path's
+// FP64 frame, rounded to FP32 afterwards).  pond_check_reciprocal() compares
+// it with CUDA's correctly rounded reciprocal.
 __device__ __forceinline__ double rcp_nr1(double y) {
   double r;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(y));

@@ -35,6 +35,8 @@ EXPORTS = (
     "pond_step_noalloc", "pond_tune_default", "pond_batch_create", "pond_batch_add",
     "pond_batch_remove", "pond_batch_size", "pond_batch_step", "pond_batch_info",
     "pond_batch_destroy", "pond_checkpoint_size", "pond_checkpoint", "pond_restore",
+    # include/pond_checks.h
+    "pond_measure_fma_peak", "pond_check_reciprocal", "pond_check_vanleer",
 )
 POND_NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 
@@ -123,6 +125,9 @@ def lib(build: bool = False):
                                   ctypes.POINTER(ctypes.c_int32), _D]
     L.pond_batch_destroy.argtypes = [_P]
     L.pond_batch_destroy.restype = None
+    L.pond_measure_fma_peak.argtypes = [ctypes.c_int32, ctypes.c_double, _D, _D]
+    L.pond_check_reciprocal.argtypes = [_P, _P, _P, ctypes.c_int64, _P]
+    L.pond_check_vanleer.argtypes = [_P, _P, _P, _P, ctypes.c_int64, _P]
     no_status = ("pond_params_default", "pond_destroy", "pond_strerror", "pond_abi_version",
                  "pond_tune_default", "pond_batch_size", "pond_batch_destroy")
     for name in EXPORTS:
@@ -288,7 +293,17 @@ def pond_destroy(ctx):
 def pond_step_noalloc(lat: int, dims, params: pond_params, f, g, ux, uy, T, n: int,
                       stream: int | None = None, want_flags: bool = True):
     """FP64 steps of a caller-owned device state (CUDA tensors), in place, with
-    no device allocation; returns (status, flags) (flags None if not wanted)."""
+    no device allocation; returns (status, flags) (flags None if not wanted).
+
+    Every array must be a contiguous float64 CUDA tensor (uy may be None in
+    1D): the C call has no host-memory path, so a host array is refused here
+    with TypeError rather than handed to the kernels as a device address."""
+    for name, a in (("f", f), ("g", g), ("ux", ux), ("uy", uy), ("T", T)):
+        if a is None and name == "uy" and int(lat) == POND_D1Q4:
+            continue
+        if (a is None or isinstance(a, np.ndarray) or not getattr(a, "is_cuda", False)
+                or str(a.dtype) != "torch.float64" or not a.is_contiguous()):
+            raise TypeError("pond_step_noalloc: %s must be a contiguous float64 CUDA tensor" % name)
     d = (ctypes.c_int64 * 2)(*[int(x) for x in dims])
     fl = ctypes.c_uint32()
     st = lib().pond_step_noalloc(int(lat), d, ctypes.byref(params), _ptr(f), _ptr(g), _ptr(ux),
@@ -297,6 +312,36 @@ def pond_step_noalloc(lat: int, dims, params: pond_params, f, g, ux, uy, T, n: i
     if st not in (POND_OK, POND_E_NONPHYSICAL):
         raise PondError(st, "pond_step_noalloc")
     return st, (int(fl.value) if want_flags else None)
+
+
+def pond_measure_fma_peak(precision: int, min_seconds: float = 0.5):
+    """(TFLOP/s, ms of the best launch) of independent fma chains in FP64
+    (POND_FP64) or FP32 (POND_FP32_MIXED) on the current device."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib().pond_measure_fma_peak(int(precision), float(min_seconds), ctypes.byref(tf),
+                                       ctypes.byref(ms)), "pond_measure_fma_peak")
+    return float(tf.value), float(ms.value)
+
+
+def _dev_f64(a, name):
+    if isinstance(a, np.ndarray) or not getattr(a, "is_cuda", False) or \
+            str(a.dtype) != "torch.float64" or not a.is_contiguous():
+        raise TypeError("%s must be a contiguous float64 CUDA tensor" % name)
+    return a.data_ptr()
+
+
+def pond_check_reciprocal(y, r, r_ref, stream: int | None = None):
+    """The kernels' FP64 reciprocal of y into r, CUDA's __drcp_rn into r_ref."""
+    _check(lib().pond_check_reciprocal(_dev_f64(y, "y"), _dev_f64(r, "r"), _dev_f64(r_ref, "r_ref"),
+                                       int(y.numel()), stream), "pond_check_reciprocal")
+
+
+def pond_check_vanleer(x, y, l, l_ref, stream: int | None = None):
+    """The kernels' FP64 van Leer limiter of (x, y) into l, the same with
+    CUDA's division into l_ref."""
+    _check(lib().pond_check_vanleer(_dev_f64(x, "x"), _dev_f64(y, "y"), _dev_f64(l, "l"),
+                                    _dev_f64(l_ref, "l_ref"), int(x.numel()), stream),
+           "pond_check_vanleer")
 
 
 def pond_checkpoint_size(ctx) -> int:

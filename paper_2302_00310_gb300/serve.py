@@ -72,15 +72,25 @@ class Server:
         self.peak_bytes = 0
         self.ticks = 0
 
-    def run(self, requests):
+    def run(self, requests, wall_limit: float | None = None):
+        """Serves the requests until all are done, or until ``wall_limit``
+        seconds after the start: then the requests still running are dropped
+        from the device (status stays "running"), and those queued or not yet
+        arrived keep "queued" / "pending"."""
         reqs = sorted(requests, key=lambda r: r.arrival)
         pending = deque(reqs)
         queue = deque()
         active = []          # (request, handle, bytes)
         used = 0
         t0 = self.clock()
+        self.stopped_at = None
         while pending or queue or active:
             now = self.clock() - t0
+            if wall_limit is not None and now >= wall_limit:
+                self.stopped_at = now
+                for r, h, _ in active:
+                    self.ex.abandon(h)
+                break
             while pending and pending[0].arrival <= now:
                 r = pending.popleft()
                 r.status = "queued"
@@ -122,7 +132,8 @@ class Server:
 
 
 def summary(reqs, makespan: float | None = None):
-    """p50/p99 time to solution (s), aggregate MLUPS over the run, counts."""
+    """p50/p99 time to solution (s) of the finished requests, aggregate MLUPS
+    over the run (finished work over the makespan), counts by status."""
     done = [r for r in reqs if r.status == "done"]
     lat = np.array([r.latency for r in done]) if done else np.zeros(0)
     if makespan is None:
@@ -131,6 +142,9 @@ def summary(reqs, makespan: float | None = None):
     return {
         "requests": len(reqs), "done": len(done),
         "rejected": sum(1 for r in reqs if r.status == "rejected"),
+        "running": sum(1 for r in reqs if r.status == "running"),
+        "queued": sum(1 for r in reqs if r.status == "queued"),
+        "not_arrived": sum(1 for r in reqs if r.status == "pending"),
         "p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
         "p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
         "mean_s": float(lat.mean()) if len(lat) else None,
@@ -210,6 +224,13 @@ class PondExecutor:
         self.handles[h.dim].remove(h)
         h.sim.close()
         return m, flags
+
+    def abandon(self, h):
+        """Drops a running request (the server's wall-time limit): it leaves
+        its batch and its memory is freed, with no result."""
+        self.batches[h.dim].remove(h.sim)
+        self.handles[h.dim].remove(h)
+        h.sim.close()
 
     def close(self):
         for b in self.batches.values():

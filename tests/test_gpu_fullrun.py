@@ -1,0 +1,120 @@
+"""Full-length runs against the FP64 oracle, and 2D refinement on the GPU.
+
+* The 256^2 periodic pulse (Mach 2 at 30 degrees, BGK, tau 1e-4, CFL 0.2) for
+  its full 1000 steps: the FP64 path matches the oracle to 1e-12 in every
+  field (max-relative per field), the mixed path within its stated L1 / Linf
+  density bounds.
+* The four-quadrant Riemann problem (seed 1, QE Pr 0.71, minmod) at 256^2 for
+  200 steps: the mixed path within its stated shock-problem bounds of the
+  oracle.
+* Second-order convergence of the FP64 path on the pulse at 128^2, 256^2,
+  512^2 against the exact translated profile (Sec. V.B.1).
+
+The oracle runs (about 4 min on 16 host cores) are made once per module and
+shared.  Bounds of the mixed path: about 10x the values measured on GB300,
+which the tests print beside them.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2302_00310_gb300 import pond
+from paper_2302_00310_gb300 import workloads as W
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+TOL = 1e-12
+# mixed path against the oracle; measured on GB300 (see the module docstring)
+PULSE_L1, PULSE_LINF = 1e-6, 1e-5
+RIEMANN_L1, RIEMANN_LINF = 1e-6, 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pond.lib(build=True)
+
+
+_ORACLE = {}
+
+
+def _oracle_run(key, w, steps):
+    if key not in _ORACLE:
+        oc = oracle.Config.from_dict(w["cfg"])
+        st = oracle.run(oc, oracle.init(oc, w["rho"], w["ux"], w["uy"], w["T"]), steps)
+        _ORACLE[key] = (oc, st)
+    return _ORACLE[key]
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _l1(a, b):
+    return float(np.sum(np.abs(a - b)) / np.sum(np.abs(b)))
+
+
+def _gpu(w, steps, precision):
+    sim = pond.Sim(dict(w["cfg"], precision=precision))
+    sim.init(w["rho"], w["ux"], w["uy"], w["T"])
+    sim.step(steps)
+    out = sim.get_state(), sim.moments(), sim.flags()
+    sim.close()
+    return out
+
+
+def test_pulse_full_run_fp64_matches_oracle():
+    w = W.pulse_2d(n=256, seed=0)
+    oc, ost = _oracle_run("pulse", w, 1000)
+    assert ost.report["flags"] == 0
+    (f, g, ux, uy, T), _, fl = _gpu(w, 1000, pond.POND_FP64)
+    assert fl[1] & pond.POND_FLAG_NONPHYSICAL == 0
+    errs = {"f": _rel(f, ost.f), "g": _rel(g, ost.g), "ux": _rel(ux, ost.ux), "uy": _rel(uy, ost.uy),
+            "T": _rel(T, ost.T)}
+    print("MEASURED pulse_fp64_vs_oracle_1000", errs)
+    assert max(errs.values()) <= TOL, errs
+
+
+def test_pulse_full_run_mixed_within_its_bounds_of_the_oracle():
+    w = W.pulse_2d(n=256, seed=0)
+    oc, ost = _oracle_run("pulse", w, 1000)
+    om = oracle.moments(oc, ost)
+    _, gm, fl = _gpu(w, 1000, pond.POND_FP32_MIXED)
+    assert fl[1] & pond.POND_FLAG_NONPHYSICAL == 0
+    l1, linf = _l1(gm[0], om[0]), _rel(gm[0], om[0])
+    l1T = _l1(gm[3], om[3])
+    print("MEASURED pulse_mixed_vs_oracle_1000 l1 %.3e linf %.3e l1_T %.3e" % (l1, linf, l1T))
+    assert l1 <= PULSE_L1 and l1T <= PULSE_L1 and linf <= PULSE_LINF, (l1, l1T, linf)
+
+
+def test_riemann_mixed_within_its_bounds_of_the_oracle():
+    w = W.riemann4_2d(n=256, seed=1)
+    oc, ost = _oracle_run("riemann", w, 200)
+    assert ost.report["flags"] == 0
+    om = oracle.moments(oc, ost)
+    _, gm, fl = _gpu(w, 200, pond.POND_FP32_MIXED)
+    assert fl[1] & pond.POND_FLAG_NONPHYSICAL == 0
+    l1, linf = _l1(gm[0], om[0]), _rel(gm[0], om[0])
+    print("MEASURED riemann256_mixed_vs_oracle_200 l1 %.3e linf %.3e" % (l1, linf))
+    assert l1 <= RIEMANN_L1 and linf <= RIEMANN_LINF, (l1, linf)
+
+
+def test_pulse_second_order_convergence_2d_gpu():
+    """FP64 path, sigma 0.15, tau 1e-6 (the viscous change of the profile far
+    below the discretisation error), t = 0.1: L1 against the translated
+    profile at 128^2, 256^2, 512^2 falls at an observed order above 1.5."""
+    errs = []
+    t_end = 0.1
+    for n in (128, 256, 512):
+        w = W.pulse_2d(n=n, seed=0, sigma=0.15, centre=(0.5, 0.5), tau=1e-6)
+        steps = int(math.ceil(t_end / w["cfg"]["dt"]))
+        w["cfg"]["dt"] = t_end / steps
+        _, gm, fl = _gpu(w, steps, pond.POND_FP64)
+        assert fl[1] & pond.POND_FLAG_NONPHYSICAL == 0
+        errs.append(float(np.mean(np.abs(gm[0] - W.pulse_exact_2d(w, t_end)))))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    print("MEASURED pulse_convergence_2d errs", errs, "orders", orders)
+    assert min(orders) > 1.5, (errs, orders)

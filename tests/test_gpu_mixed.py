@@ -87,6 +87,7 @@ def test_mixed_few_steps_match_oracle(case):
     gm, fl = _gpu(cfg, prim, steps, tile=tile)
     assert not fl[1] & pond.POND_FLAG_NONPHYSICAL
     errs = [_linf(gm[i], om[i]) for i in (0, 1, 3)] + ([_linf(gm[2], om[2])] if D == 2 else [])
+    print("MEASURED mixed_case%d linf %.3e" % (case, max(errs)))
     assert max(errs) <= TOL_STEP, errs
 
 
@@ -118,6 +119,7 @@ def test_mixed_pulse_matches_oracle_l1():
     om = _oracle_moments(w["cfg"], prim, 200)
     gm, fl = _gpu(w["cfg"], prim, 200)
     assert fl[1] == 0
+    print("MEASURED pulse128_mixed_vs_oracle_200 l1 %.3e l1_T %.3e" % (_l1(gm[0], om[0]), _l1(gm[3], om[3])))
     assert _l1(gm[0], om[0]) <= TOL_L1_SMOOTH
     assert _l1(gm[3], om[3]) <= TOL_L1_SMOOTH
 
@@ -129,6 +131,8 @@ def test_mixed_pulse_full_run_l1():
     m64, _ = _gpu(w["cfg"], prim, 1000, precision=pond.POND_FP64)
     m32, fl = _gpu(w["cfg"], prim, 1000)
     assert fl[1] == 0
+    print("MEASURED pulse256_mixed_vs_fp64_1000 l1 %.3e linf %.3e mass %.3e" % (
+        _l1(m32[0], m64[0]), _linf(m32[0], m64[0]), abs(m32[0].sum() / m64[0].sum() - 1)))
     assert _l1(m32[0], m64[0]) <= TOL_L1_SMOOTH, _l1(m32[0], m64[0])
     # mass is conserved to FP32 rounding
     assert abs(m32[0].sum() / m64[0].sum() - 1) < 1e-6
@@ -139,6 +143,7 @@ def test_mixed_sod_l1():
     prim = (w["rho"], w["ux"], w["uy"], w["T"])
     om = _oracle_moments(w["cfg"], prim, w["steps"])
     gm, _ = _gpu(w["cfg"], prim, w["steps"])
+    print("MEASURED sod_mixed_vs_oracle l1 %.3e" % _l1(gm[0][0], om[0][0]))
     assert _l1(gm[0][0], om[0][0]) <= TOL_L1_SMOOTH
 
 
@@ -150,6 +155,8 @@ def test_mixed_riemann_l1():
     m64, f64 = _gpu(w["cfg"], prim, 200, precision=pond.POND_FP64)
     m32, f32 = _gpu(w["cfg"], prim, 200)
     assert f64[1] & pond.POND_FLAG_NONPHYSICAL == 0 and f32[1] & pond.POND_FLAG_NONPHYSICAL == 0
+    print("MEASURED riemann512_mixed_vs_fp64_200 l1 %.3e linf %.3e" % (_l1(m32[0], m64[0]),
+                                                                       _linf(m32[0], m64[0])))
     assert _l1(m32[0], m64[0]) <= TOL_L1_SHOCK, _l1(m32[0], m64[0])
 
 
@@ -189,6 +196,7 @@ def test_mixed_iterated_frame_cycling_faces(seed):
     gm, fl = _gpu(cfg, prim, 2)
     assert not fl[1] & pond.POND_FLAG_NONPHYSICAL
     assert fl[3] == ost.report["noconv_faces"] > 0
+    print("MEASURED cycling_seed%d linf %.3e" % (seed, max(_linf(gm[i], om[i]) for i in range(4))))
     assert max(_linf(gm[i], om[i]) for i in range(4)) <= 1e-3
 
 

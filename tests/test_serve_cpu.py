@@ -53,6 +53,10 @@ class FakeExecutor:
         self.log.append(("done", r.rid, self.clock.t))
         return ("moments", r.rid), 0
 
+    def abandon(self, h):
+        r, _ = self.active.pop(h)
+        self.log.append(("abandon", r.rid, self.clock.t))
+
 
 def _req(rid, t, nx, steps, dim=2):
     cfg = {"nx": nx, "ny": nx if dim == 2 else 1}
@@ -145,3 +149,21 @@ def test_nvtx_ranges_nest_and_never_raise_on_the_host():
     with pytest.raises(ValueError):
         with pond.nvtx_range("raising"):
             raise ValueError("propagates")
+
+
+def test_wall_limit_stops_and_reports_the_queue():
+    """An offered load beyond the executor's rate, served for a fixed wall
+    time: requests finished by then are done, the running ones are dropped
+    from the device, the rest stay queued or not yet arrived."""
+    clock = FakeClock()
+    ex = FakeExecutor(clock, slots=2)
+    srv = serve.Server(ex, budget_bytes=10**12, tick_steps=100, clock=clock, sleep=clock.sleep)
+    # each request: 1e6 cell updates per 100-step tick -> 1 ms per tick, 10 ticks
+    reqs = [_req(i, 0.001 * i, 100, 1000) for i in range(40)]
+    out = srv.run(reqs, wall_limit=0.05)
+    s = serve.summary(out, makespan=srv.stopped_at)
+    assert srv.stopped_at is not None and srv.stopped_at >= 0.05
+    assert 0 < s["done"] < 40 and s["running"] == 2
+    assert s["done"] + s["running"] + s["queued"] + s["not_arrived"] == 40
+    assert not ex.active  # nothing left on the device
+    assert sum(1 for e in ex.log if e[0] == "abandon") == 2

@@ -172,6 +172,14 @@ typedef struct {
    * (or the precision's default: 1 in 1D; 10 FP64, 6 mixed in 2D); not
    * batched. */
   int32_t g_same_as_f;
+  /* tiles per strip of the step launch: 0 automatic, else 1-8.  A CTA steps a
+   * strip of consecutive tiles of one tile row left to right, handing each
+   * tile's right-edge x-face records to the next tile instead of computing
+   * them twice (a face's record depends only on its stencil, so every strip
+   * length gives the same state bit for bit).  Automatic: the longest strip
+   * (up to 8) that does not lengthen the launch's waves x strip length; 1 with
+   * the iterated face frame.  Batches choose their own (pond_batch_step). */
+  int32_t strip;
 } pond_params;
 
 /* Fills the defaults: gamma 1.4, tau 1e-4, Pr 1, dx 1, dt 0 (from cfl 0.2),

@@ -32,7 +32,7 @@ def _nvcc() -> str:
 
 def _digest() -> str:
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(CSRC, "*"))) + [os.path.join(INCLUDE, "pond.h")]:
+    for p in sorted(glob.glob(os.path.join(CSRC, "*"))) + sorted(glob.glob(os.path.join(INCLUDE, "*.h"))):
         with open(p, "rb") as fh:
             h.update(os.path.basename(p).encode() + fh.read())
     # the flags without the include directories: those are absolute paths,

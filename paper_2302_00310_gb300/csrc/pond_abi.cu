@@ -176,17 +176,24 @@ pond_status prepare_step(pond_ctx *c) {
       if (sh.code == c->tile) { c->shape = sh; found = true; }
     if (!found) return POND_E_INVAL;
   }
-  int occ = 0;
+  int occ = 0, dev = 0, sms = 0;
   POND_CUDA(c->shape.prepare(&occ));
+  POND_CUDA(cudaGetDevice(&dev));
+  POND_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int tx = (int)((c->nx + c->shape.bx - 1) / c->shape.bx);
   const int ty = c->D == 2 ? (int)((c->ny + c->shape.by - 1) / c->shape.by) : 1;
-  c->tiles = tx * ty;
+  // one CTA per strip of tiles (the iterated face frame hands no edges over)
+  const int strip = c->K.iterative ? 1
+                   : c->p.strip > 0 ? (c->p.strip < tx ? c->p.strip : tx)
+                                    : pond::choose_strip(tx, ty, sms * (occ > 0 ? occ : 1));
+  c->tiles = pond::strips_of(tx, ty, strip);
   unsigned char host[pond::kSoloTableBytes];
   memset(host, 0, sizeof(host));
   pond::TableHdr hdr;
   memset(&hdr, 0, sizeof(hdr));
   hdr.n = 1;
   hdr.total_tiles = c->tiles;
+  hdr.strip = strip;
   memcpy(host, &hdr, sizeof(hdr));
   auto fill = [&](auto tag) {
     using R = decltype(tag);
@@ -239,6 +246,7 @@ bool valid_params(const pond_params *p) {
   if (p->flux_frame == POND_FRAME_ITER && (!(p->iter_tol > 0.0) || p->iter_max < 1)) return false;
   if (!(p->xi_fp64_threshold > 0.0)) return false;
   if (p->tile < 0 || p->tile > 10) return false;
+  if (p->strip < 0 || p->strip > 8) return false;
   if (p->multiscale != 0 && p->multiscale != 1) return false;
   if (p->g_same_as_f != 0 && p->g_same_as_f != 1) return false;
   if (p->multiscale) {  // D1Q3/D1Q4 and D2Q9/D2Q16, BGK, averaged frame, no walls; mixed: App. C form

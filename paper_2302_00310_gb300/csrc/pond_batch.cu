@@ -82,9 +82,10 @@ namespace {
 size_t desc_size(bool fp32) { return fp32 ? sizeof(InstDesc<float>) : sizeof(InstDesc<double>); }
 
 int tiles_x_of(const pond_ctx *c, const Shape &s) { return (int)((c->nx + s.bx - 1) / s.bx); }
-int tiles_of(const pond_ctx *c, const Shape &s) {
-  return tiles_x_of(c, s) * (c->D == 2 ? (int)((c->ny + s.by - 1) / s.by) : 1);
+int tiles_y_of(const pond_ctx *c, const Shape &s) {
+  return c->D == 2 ? (int)((c->ny + s.by - 1) / s.by) : 1;
 }
+int tiles_of(const pond_ctx *c, const Shape &s) { return tiles_x_of(c, s) * tiles_y_of(c, s); }
 
 template <typename R>
 void fill_desc(unsigned char *dst, const pond_ctx *c, const Shape &s, int tile_begin, int steps) {
@@ -103,7 +104,8 @@ void fill_desc(unsigned char *dst, const pond_ctx *c, const Shape &s, int tile_b
 
 // uploads the table of the members with steps[i] > 0 for shape s; returns the
 // number of cells in it
-pond_status upload_table(pond_batch *b, const Shape &s, const std::vector<int> &steps, size_t *cells) {
+pond_status upload_table(pond_batch *b, int shape, const std::vector<int> &steps, size_t *cells) {
+  const Shape &s = b->shapes[shape];
   const int slot = b->hslot;
   b->hslot ^= 1;
   // the pinned buffer may still be read by the copy queued two chunks ago
@@ -111,19 +113,29 @@ pond_status upload_table(pond_batch *b, const Shape &s, const std::vector<int> &
   unsigned char *h = b->htable[slot];
   TableHdr hdr;
   memset(&hdr, 0, sizeof(hdr));
+  // strips of up to 8 tiles, as long as the grid still strides over at least
+  // four strips per CTA (members with different step counts drop out of
+  // later launches, and many small units keep the CTAs balanced)
+  const int slots = b->sms * std::max(1, b->occupancy[shape]);
+  long long all_tiles = 0;
+  for (size_t i = 0; i < b->members.size(); ++i)
+    if (steps[i] > 0) all_tiles += tiles_of(b->members[i], s);
+  int strip = 1;
+  while (strip < 8 && all_tiles / (2 * strip) >= 4LL * slots) strip *= 2;
   size_t ncell = 0;
-  int tile = 0;
+  int unit = 0;
   for (size_t i = 0; i < b->members.size(); ++i) {
     if (steps[i] <= 0) continue;
     const pond_ctx *c = b->members[i];
     unsigned char *dst = h + sizeof(TableHdr) + (size_t)hdr.n * b->desc_bytes;
-    if (b->fp32) fill_desc<float>(dst, c, s, tile, steps[i]);
-    else fill_desc<double>(dst, c, s, tile, steps[i]);
-    tile += tiles_of(c, s);
+    if (b->fp32) fill_desc<float>(dst, c, s, unit, steps[i]);
+    else fill_desc<double>(dst, c, s, unit, steps[i]);
+    unit += pond::strips_of(tiles_x_of(c, s), tiles_y_of(c, s), strip);
     ncell += (size_t)c->N;
     ++hdr.n;
   }
-  hdr.total_tiles = tile;
+  hdr.total_tiles = unit;
+  hdr.strip = strip;
   memcpy(h, &hdr, sizeof(hdr));
   POND_CUDA(cudaMemcpyAsync(b->dtable, h, sizeof(TableHdr) + (size_t)hdr.n * b->desc_bytes,
                             cudaMemcpyHostToDevice, b->stream));
@@ -168,7 +180,7 @@ pond_status run_chunk(pond_batch *b, int shape, std::vector<int> &steps, bool us
   *launches = mx;
   *cells = 0;
   if (mx == 0) return POND_OK;
-  pond_status st = upload_table(b, b->shapes[shape], steps, cells);
+  pond_status st = upload_table(b, shape, steps, cells);
   if (st != POND_OK) return st;
   if ((st = launch_chunk(b, shape, mx, use_graph)) != POND_OK) return st;
   for (size_t i = 0; i < b->members.size(); ++i) {

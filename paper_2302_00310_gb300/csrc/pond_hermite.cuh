@@ -361,6 +361,32 @@ __device__ __forceinline__ void shift_y(const DShift<R> &C, Blk<R, Q, NY> &B) {
     }
   }
 }
+// one Q-vector along either axis: the frame change and the synthesis at the
+// nodes (the per-axis maps that the tensor-product transformation composes)
+template <typename R, int Q>
+__device__ __forceinline__ void dshiftq(const DShift<R> &C, R (&m)[Q]) {
+  if constexpr (Q == 5) dshift5(C, m[0], m[1], m[2], m[3], m[4]);
+  else if constexpr (Q == 4) dshift4(C, m[0], m[1], m[2], m[3]);
+  else dshift3(C, m[0], m[1], m[2]);
+}
+template <typename R, int Q>
+__device__ __forceinline__ void synqq(const SynK<R, Q> &S, R (&m)[Q]) {
+  if constexpr (Q == 5) synq(S, m[0], m[1], m[2], m[3], m[4]);
+  else if constexpr (Q == 4) synq(S, m[0], m[1], m[2], m[3]);
+  else synq(S, m[0], m[1], m[2]);
+}
+// the constants of c ? A : B, member by member (the members Q does not use
+// are dead code)
+template <typename R>
+__device__ __forceinline__ DShift<R> select_shift(bool c, const DShift<R> &A, const DShift<R> &B) {
+  DShift<R> C;
+  C.d = c ? A.d : B.d; C.d2 = c ? A.d2 : B.d2; C.d3 = c ? A.d3 : B.d3;
+  C.g2 = c ? A.g2 : B.g2; C.g2x3 = c ? A.g2x3 : B.g2x3; C.g3 = c ? A.g3 : B.g3;
+  C.d4 = c ? A.d4 : B.d4; C.g2x6 = c ? A.g2x6 : B.g2x6; C.g3x4 = c ? A.g3x4 : B.g3x4;
+  C.g4 = c ? A.g4 : B.g4;
+  return C;
+}
+
 // node values / weights in the frame of S, x then y
 template <typename R, int Q, int NY>
 __device__ __forceinline__ void synq_xy(const SynK<R, Q> &S, Blk<R, Q, NY> &B) {

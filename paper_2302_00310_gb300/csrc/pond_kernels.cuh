@@ -166,7 +166,7 @@ template <> __device__ __forceinline__ double qnan<double>() { return __longlong
 template <> __device__ __forceinline__ float qnan<float>() { return __int_as_float(0x7fc00000); }
 
 __device__ __forceinline__ float div_nr(float x, float y) { return __fdividef(x, y); }
-// 1/y to about 2^-40 relative, for 2^-1022 <= |y| < 2^1022: the hardware
+// 1/y to 2^-39 relative (2^-39.9 measured), for 2^-1022 <= |y| < 2^1022: the hardware
 // approximation rcp.approx.ftz.f64 refined by one Newton-Raphson step for the
 // reciprocal, r1 = r0 + r0 (1 - y r0), written as two fused multiply-adds
 // (the FMA form of Newton's iteration of P. Markstein, "Computation of
@@ -477,16 +477,17 @@ __device__ __forceinline__ void prep_cell(const StepConst &K, const State<R> &S,
       if (!hi) ms_project(F, K.grad_k);
       lat[h] = hi ? 1 : 0;
     }
-    qe_scale(F, G, kc<R>(K.qe, K.cf.qe));
-    const R rho = F.v[0][0], ka = kc<R>(K.kp_a, K.cf.kp_a);
+    // the first QE half step (qe on the order-3 content of f and order-1 of
+    // g) and the kp_a of phi_bar^+ in one scaling per coefficient
+    const R rho = F.v[0][0], ka = kc<R>(K.kp_a, K.cf.kp_a), kq = ka * kc<R>(K.qe, K.cf.qe);
 #pragma unroll
     for (int a = 0; a < QF1; ++a)
 #pragma unroll
-      for (int b = 0; b < D::NYF; ++b) F.v[a][b] *= ka;
+      for (int b = 0; b < D::NYF; ++b) F.v[a][b] *= a + b == 3 ? kq : ka;
 #pragma unroll
     for (int a = 0; a < QG1; ++a)
 #pragma unroll
-      for (int b = 0; b < D::NYG; ++b) G.v[a][b] *= ka;
+      for (int b = 0; b < D::NYG; ++b) G.v[a][b] *= a + b == 1 ? kq : ka;
     // phi_bar^+ = kp_a phi~ + kp_b phi^eq; phi^eq = rho W (f), (C_v - D/2) T rho W (g)
     F.v[0][0] = kc<R>(K.kappa1, K.cf.kappa1) * rho;
     G.v[0][0] += kc<R>(K.kp_b, K.cf.kp_b) * kc<R>(K.gfac, K.cf.gfac) * T * rho;
@@ -568,6 +569,115 @@ __device__ __forceinline__ void stencil_pops(const StepConst &K, const R *sp, in
   else stencil_pops_body<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, h, uFx, uFy, TF, sTF, SK, Y);
 }
 
+// ---- a pair of stencil cells of which each normal node needs one ------------
+// The trace of a normal node takes its outer neighbour and its two tangential
+// neighbours from the upwind side only: cells 2 / 4 / 6 of the stencil where
+// the node's v_n > 0 (upwind cell on the left/lower side), cells 3 / 5 / 7
+// elsewhere.  So each of the pairs (2, 3), (4, 5), (6, 7) is moved into the
+// face frame and synthesised along the normal axis for both cells, the
+// selected cell's values are kept per normal node (bit k of upm: node k takes
+// hA), and only those are moved and synthesised along the tangential axis,
+// with the shift of the cell they came from.  The maps of the two axes act on
+// different indices and commute, so every value is the one the full
+// transformation of its cell gives (up to rounding order), for a quarter less
+// arithmetic.  The Grad projection (zeroing coefficients in the face frame
+// between the frame change and the synthesis) and, on the mixed path, a
+// cell whose transformation must run in FP64 take both cells' full
+// transformations instead (stencil_pair_full, out of line: rare).
+template <typename R, int DIM, int QF1, int Q, int GS, int QG1, int DIRN>
+__device__ __noinline__ Blk<R, Q, (DIM == 2 ? Q : 1)> stencil_pair_full(const StepConst &K, const R *sp,
+                                                                      int NH, int hA, int hB,
+                                                                      unsigned upm, R uFx, R uFy, R TF,
+                                                                      R sTF, SynK<R, Q> SK) {
+  constexpr int NY = DIM == 2 ? Q : 1;
+  Blk<R, Q, NY> YA, YB;
+  stencil_pops_body<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, hA, uFx, uFy, TF, sTF, SK, YA);
+  stencil_pops_body<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, hB, uFx, uFy, TF, sTF, SK, YB);
+#pragma unroll
+  for (int n = 0; n < Q; ++n)
+#pragma unroll
+    for (int m = 0; m < NY; ++m) {
+      const int k = DIRN == 0 ? n : m;
+      YA.v[n][m] = (upm >> k & 1u) ? YA.v[n][m] : YB.v[n][m];
+    }
+  return YA;
+}
+template <typename R, int DIM, int QF1, int Q, int GS, int QG1, int DIRN>
+__device__ __forceinline__ void stencil_pair_body(const StepConst &K, const R *sp, int NH, int hA, int hB,
+                                                  unsigned upm, R uFx, R uFy, R TF, R sTF,
+                                                  const SynK<R, Q> &SK, Blk<R, Q, (DIM == 2 ? Q : 1)> &Y) {
+  if constexpr (DIM == 1) {  // no tangential axis: both cells in full, in line
+    Blk<R, Q, 1> YB;
+    stencil_pops<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, hA, uFx, uFy, TF, sTF, SK, Y);
+    stencil_pops<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, hB, uFx, uFy, TF, sTF, SK, YB);
+#pragma unroll
+    for (int k = 0; k < Q; ++k) Y.v[k][0] = (upm >> k & 1u) ? Y.v[k][0] : YB.v[k][0];
+    return;
+  }
+  using D = Dims<DIM, QF1, QG1>;
+  constexpr int base = GS ? D::QF : 0, stride = GS ? QG1 : QF1;
+  constexpr int IN = DIRN == 0 ? D::IUX : D::IUY, IT_ = DIRN == 0 ? D::IUY : D::IUX;
+  const R uFn = DIRN == 0 ? uFx : uFy, uFt = DIRN == 0 ? uFy : uFx;
+  const R unA = sp[IN * NH + hA], unB = sp[IN * NH + hB];
+  const R utA = sp[IT_ * NH + hA], utB = sp[IT_ * NH + hB];
+  const R TA = sp[D::IT * NH + hA], TB = sp[D::IT * NH + hB];
+  bool full = K.grad_k != 0;
+  if constexpr (is_mixed<R>()) {
+    const R sTA = sp[D::IST * NH + hA], sTB = sp[D::IST * NH + hB], lim = K.xi_thr * sTF;
+    full = full || fmaf(sTA, float(Nodes<Q>::cmax), fmaxf(fabsf(unA - uFn), fabsf(utA - uFt))) > lim ||
+           fmaf(sTB, float(Nodes<Q>::cmax), fmaxf(fabsf(unB - uFn), fabsf(utB - uFt))) > lim;
+  }
+  if (full) {
+    Y = stencil_pair_full<R, DIM, QF1, Q, GS, QG1, DIRN>(K, sp, NH, hA, hB, upm, uFx, uFy, TF, sTF, SK);
+    return;
+  }
+  {
+    const R dTA = TA - TF, dTB = TB - TF;
+    const DShift<R> CnA = make_dshift(unA - uFn, dTA, R(3) * dTA), CnB = make_dshift(unB - uFn, dTB, R(3) * dTB);
+    const DShift<R> CtA = make_dshift(utA - uFt, dTA, R(3) * dTA), CtB = make_dshift(utB - uFt, dTB, R(3) * dTB);
+    R Z[Q][Q];  // [normal node][tangential order]
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      R a[Q], b[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const int c = DIRN == 0 ? i + stride * j : j + stride * i;
+        a[i] = sp[(base + c) * NH + hA];
+        b[i] = sp[(base + c) * NH + hB];
+      }
+      dshiftq(CnA, a); synqq(SK, a);
+      dshiftq(CnB, b); synqq(SK, b);
+#pragma unroll
+      for (int k = 0; k < Q; ++k) Z[k][j] = (upm >> k & 1u) ? a[k] : b[k];
+    }
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+      const DShift<R> Ct = select_shift((upm >> k & 1u) != 0u, CtA, CtB);
+      dshiftq(Ct, Z[k]);
+      synqq(SK, Z[k]);
+#pragma unroll
+      for (int j = 0; j < Q; ++j) Y.v[DIRN == 0 ? k : j][DIRN == 0 ? j : k] = Z[k][j];
+    }
+  }
+}
+template <typename R, int DIM, int QF1, int Q, int GS, int QG1, int DIRN>
+__device__ __noinline__ Blk<R, Q, (DIM == 2 ? Q : 1)> stencil_pair_call(const StepConst &K, const R *sp,
+                                                                      int NH, int hA, int hB,
+                                                                      unsigned upm, R uFx, R uFy, R TF,
+                                                                      R sTF, SynK<R, Q> SK) {
+  Blk<R, Q, (DIM == 2 ? Q : 1)> Y;
+  stencil_pair_body<R, DIM, QF1, Q, GS, QG1, DIRN>(K, sp, NH, hA, hB, upm, uFx, uFy, TF, sTF, SK, Y);
+  return Y;
+}
+template <typename R, int DIM, int QF1, int Q, int GS, int QG1, int DIRN>
+__device__ __forceinline__ void stencil_pair(const StepConst &K, const R *sp, int NH, int hA, int hB,
+                                             unsigned upm, R uFx, R uFy, R TF, R sTF, const SynK<R, Q> &SK,
+                                             Blk<R, Q, (DIM == 2 ? Q : 1)> &Y) {
+  if constexpr (is_mixed<R>())
+    Y = stencil_pair_call<R, DIM, QF1, Q, GS, QG1, DIRN>(K, sp, NH, hA, hB, upm, uFx, uFy, TF, sTF, SK);
+  else stencil_pair_body<R, DIM, QF1, Q, GS, QG1, DIRN>(K, sp, NH, hA, hB, upm, uFx, uFy, TF, sTF, SK, Y);
+}
+
 // v_n == +-0 exactly (a wall at rest puts the zero node of D1Q3 there)
 __device__ __forceinline__ bool is_zero(double v) { return (__double_as_longlong(v) << 1) == 0; }
 __device__ __forceinline__ bool is_zero(float v) { return (__float_as_int(v) << 1) == 0; }
@@ -635,15 +745,15 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
   const R hl = R(0.5) * kc<R>(K.lam, K.cf.lam) * lf, h0 = R(0.5) * lf;
   const int lim = K.limiter;
   bool up[Q], tie = false;
+  unsigned upm = 0u;
   R offn[Q], offt[Q];
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
     const R c = R(Nodes<Q>::c(k));
     const R vn = sTF * c + uFn;
     up[k] = pos(vn);
-    if constexpr (TIE == 1) {
-      if (Q % 2 == 0 || 2 * k != Q - 1) tie |= is_zero(vn);
-    }
+    upm |= up[k] ? 1u << k : 0u;
+    if constexpr (TIE == 1) tie |= is_zero(vn);
     offn[k] = h0 - hl * fabs(vn);
     offt[k] = -hl * (sTF * c + uFt);
   }
@@ -653,80 +763,39 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
       return;
     }
   }
-  // The zero node of D1Q3 / D1Q5 (normal node index KZ = Q/2) has v_n = 0
-  // whenever u_F,n = 0 exactly (a wall at rest, a gas at rest): it then takes
-  // the mean of its two one-sided traces.  With v_n = 0 its upwind side is the
-  // right/upper cell; Z holds the trace from the left/lower one, for its NZ
-  // populations.
-  constexpr bool ODD = Q % 2 == 1;
-  constexpr int KZ = Q / 2, NZ = ODD ? (DIRN == 0 ? NY : Q) : 1;
-  const bool zt = ODD && is_zero(uFn);
-  R Z[NZ], ZD[NZ];
-  Blk<R, Q, NY> YL, YR, A;
-  stencil_pops<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, st[0], uFx, uFy, TF, sTF, SK, YL);
-  stencil_pops<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, st[1], uFx, uFy, TF, sTF, SK, YR);
+  // (no node has v_n = 0 here: the caller routes such faces to the tie path)
+  Blk<R, Q, NY> A;
   {
-    Blk<R, Q, NY> Y1, Y2;
-    stencil_pops<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, st[2], uFx, uFy, TF, sTF, SK, Y1);
-    stencil_pops<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, st[3], uFx, uFy, TF, sTF, SK, Y2);
+    Blk<R, Q, NY> YL, YR, Bo;
+    stencil_pops<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, st[0], uFx, uFy, TF, sTF, SK, YL);
+    stencil_pops<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, st[1], uFx, uFy, TF, sTF, SK, YR);
+    stencil_pair<R, DIM, QF1, Q, GS, QG1, DIRN>(K, sp, NH, st[2], st[3], upm, uFx, uFy, TF, sTF, SK, Bo);
 #pragma unroll
     for (int n = 0; n < Q; ++n)
 #pragma unroll
       for (int m = 0; m < NY; ++m) {
         const int k = DIRN == 0 ? n : m;
         const R a = up[k] ? YL.v[n][m] : YR.v[n][m];
-        const R b = up[k] ? Y1.v[n][m] : Y2.v[n][m];
         const R c = up[k] ? YR.v[n][m] : YL.v[n][m];
         A.v[n][m] = a;
-        out.v[n][m] = a + offn[k] * limit(a - b, c - a, lim);
-        if constexpr (ODD) {
-          if (k == KZ && zt) {
-            const int z = DIRN == 0 ? m : n;
-            const R l = YL.v[n][m];
-            Z[z] = l + offn[k] * limit(l - Y1.v[n][m], YR.v[n][m] - l, lim);
-          }
-        }
+        out.v[n][m] = a + offn[k] * limit(a - Bo.v[n][m], c - a, lim);
       }
   }
   if constexpr (DIM == 2) {
-    Blk<R, Q, NY> Y1, Y2, Dl;
-    stencil_pops<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, st[4], uFx, uFy, TF, sTF, SK, Y1);
-    stencil_pops<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, st[5], uFx, uFy, TF, sTF, SK, Y2);
+    Blk<R, Q, NY> Y, Dl;
+    stencil_pair<R, DIM, QF1, Q, GS, QG1, DIRN>(K, sp, NH, st[4], st[5], upm, uFx, uFy, TF, sTF, SK, Y);
+#pragma unroll
+    for (int n = 0; n < Q; ++n)
+#pragma unroll
+      for (int m = 0; m < NY; ++m) Dl.v[n][m] = A.v[n][m] - Y.v[n][m];
+    stencil_pair<R, DIM, QF1, Q, GS, QG1, DIRN>(K, sp, NH, st[6], st[7], upm, uFx, uFy, TF, sTF, SK, Y);
 #pragma unroll
     for (int n = 0; n < Q; ++n)
 #pragma unroll
       for (int m = 0; m < NY; ++m) {
-        const int k = DIRN == 0 ? n : m;
-        Dl.v[n][m] = A.v[n][m] - (up[k] ? Y1.v[n][m] : Y2.v[n][m]);
-        if constexpr (ODD) {
-          if (k == KZ && zt) ZD[DIRN == 0 ? m : n] = YL.v[n][m] - Y1.v[n][m];
-        }
+        const int kt = DIRN == 0 ? m : n;
+        out.v[n][m] += offt[kt] * limit(Dl.v[n][m], Y.v[n][m] - A.v[n][m], lim);
       }
-    stencil_pops<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, st[6], uFx, uFy, TF, sTF, SK, Y1);
-    stencil_pops<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, st[7], uFx, uFy, TF, sTF, SK, Y2);
-#pragma unroll
-    for (int n = 0; n < Q; ++n)
-#pragma unroll
-      for (int m = 0; m < NY; ++m) {
-        const int k = DIRN == 0 ? n : m, kt = DIRN == 0 ? m : n;
-        const R hi = up[k] ? Y1.v[n][m] : Y2.v[n][m];
-        out.v[n][m] += offt[kt] * limit(Dl.v[n][m], hi - A.v[n][m], lim);
-        if constexpr (ODD) {
-          if (k == KZ && zt) {
-            const int z = DIRN == 0 ? m : n;
-            Z[z] += offt[kt] * limit(ZD[z], Y1.v[n][m] - YL.v[n][m], lim);
-          }
-        }
-      }
-  }
-  if constexpr (ODD) {
-    if (zt) {
-#pragma unroll
-      for (int z = 0; z < NZ; ++z) {
-        R &o = DIRN == 0 ? out.v[KZ][z] : out.v[z][KZ];
-        o = R(0.5) * (o + Z[z]);
-      }
-    }
   }
 }
 
@@ -764,11 +833,13 @@ template <typename R, int DIM, int QF1, int DIRN, bool ITER, bool TIE = false, i
 __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int NH, const int *st,
                                           R *fp, int NFACES, int fidx, int &ntrace);
 
-// does a node of either lattice other than the zero nodes of D1Q3 and D1Q5
-// (which the trace handles in line) have v_n = 0 exactly in the face frame?
+// does a node of either lattice have v_n = 0 exactly in the face frame?  (The
+// zero node of D1Q3 / D1Q5 does whenever u_F,n = 0: a wall at rest, a gas at
+// rest.)  Such a face takes the out-of-line trace, where that node takes the
+// mean of its two one-sided traces.
 template <typename R, int QF1, int QG1 = 3>
 __device__ __forceinline__ bool face_has_tie(R uFn, R sTF) {
-  bool t = false;
+  bool t = (QF1 % 2 == 1 || QG1 % 2 == 1) && is_zero(uFn);
 #pragma unroll
   for (int k = 0; k < QF1; ++k)
     if (QF1 % 2 == 0 || 2 * k != QF1 - 1) t |= is_zero(sTF * R(Nodes<QF1>::c(k)) + uFn);
@@ -876,22 +947,24 @@ __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int N
   const bool phys = rk > R(0) && Tb > R(0);
   const bool gk = DIM == 2 && K.grad_k;
   const R re = phys ? kc<R>(K.kr, K.cf.kr) * rk : qnan<R>(), ge = re * kc<R>(K.gfac, K.cf.gfac) * Tb;
+  // rho E[H_a] E[H_b] added as (rho E[H_a]) E[H_b]: one multiply-add per coefficient
+  R rex[QL], gex[QG1];
+#pragma unroll
+  for (int a = 0; a < QL; ++a) rex[a] = a == 0 ? re : re * ex[a];
+#pragma unroll
+  for (int a = 0; a < QG1; ++a) gex[a] = a == 0 ? ge : ge * ex[a];
 #pragma unroll
   for (int a = 0; a < QL; ++a)
 #pragma unroll
-    for (int b = 0; b < NYF; ++b) {
-      R e = re * ex[a] * ey[b];
-      if (gk && a + b > QL - 1) e = R(0);
-      Fb.v[a][b] += e;
-    }
+    for (int b = 0; b < NYF; ++b)
+      Fb.v[a][b] = b == 0 ? Fb.v[a][b] + ((gk && a > QL - 1) ? R(0) : rex[a])
+                          : fma((gk && a + b > QL - 1) ? R(0) : rex[a], ey[b], Fb.v[a][b]);
 #pragma unroll
   for (int a = 0; a < QG1; ++a)
 #pragma unroll
-    for (int b = 0; b < NYG; ++b) {
-      R e = ge * ex[a] * ey[b];
-      if (gk && a + b > QG1 - 1) e = R(0);
-      Gb.v[a][b] += e;
-    }
+    for (int b = 0; b < NYG; ++b)
+      Gb.v[a][b] = b == 0 ? Gb.v[a][b] + ((gk && a > QG1 - 1) ? R(0) : gex[a])
+                          : fma((gk && a + b > QG1 - 1) ? R(0) : gex[a], ey[b], Gb.v[a][b]);
   // Appendix C form: transport v_n^{lambda_F} phi in the face frame
   if (K.appc) {
     const R un = DIRN == 0 ? uFx : uFy;
@@ -1089,7 +1162,6 @@ __device__ __forceinline__ void update_cell(const StepConst &K, const State<R> &
   if constexpr (MS) {
     if (low) ms_project(F, K.grad_k);
   }
-  qe_scale(F, G, kc<R>(K.qe, K.cf.qe));
   const R rho = F.v[0][0];
   MomAcc M;
   if constexpr (is_mixed<R>()) {
@@ -1100,16 +1172,17 @@ __device__ __forceinline__ void update_cell(const StepConst &K, const State<R> &
     M.e = S.M[3 * N + c];
   }
   // DUGKS update in the cell frame (Eq. eq:FinalUpdateDUGKS):
-  // a1 phi~ + a2 phi^eq - dt/dx sum_faces (+-) F
-  const R a1 = kc<R>(K.a1, K.cf.a1);
+  // a1 phi~ + a2 phi^eq - dt/dx sum_faces (+-) F, after the first QE half
+  // step (qe on the order-3 content of f and order-1 of g): one scaling
+  const R a1 = kc<R>(K.a1, K.cf.a1), aq = a1 * kc<R>(K.qe, K.cf.qe);
 #pragma unroll
   for (int a = 0; a < QF1; ++a)
 #pragma unroll
-    for (int b = 0; b < D::NYF; ++b) F.v[a][b] *= a1;
+    for (int b = 0; b < D::NYF; ++b) F.v[a][b] *= a + b == 3 ? aq : a1;
 #pragma unroll
   for (int a = 0; a < QG1; ++a)
 #pragma unroll
-    for (int b = 0; b < D::NYG; ++b) G.v[a][b] *= a1;
+    for (int b = 0; b < D::NYG; ++b) G.v[a][b] *= a + b == 1 ? aq : a1;
   // fluxes through the faces, in a fixed order: x, then y
   add_faces<R, DIM, QF1, 0, MS, QG1>(K, fp, TL::NFACES, cy * (BX + 1) + cx, cy * (BX + 1) + cx + 1, ux, uy, T, sT, F,
                                 G, M, low);
@@ -1169,7 +1242,7 @@ __device__ __forceinline__ void update_cell(const StepConst &K, const State<R> &
     if constexpr (DIM == 2) {
       if (K.grad_k) { grad_mask(F); grad_mask(G); }
     }
-    qe_scale(F, G, kc<R>(K.qe, K.cf.qe));
+    if (K.qe != 1.0) qe_scale(F, G, kc<R>(K.qe, K.cf.qe));  // (BGK: no QE step)
     const R cm = (MS && low) ? R(Nodes<3>::cmax) : R(Nodes<QF1>::cmax);
     vmax = fmax(vmax, fmax(fabs(uxn), fabs(uyn)) + sqrt(Tout) * cm);
   } else {
@@ -1194,15 +1267,36 @@ __device__ __forceinline__ void update_cell(const StepConst &K, const State<R> &
   }
 }
 
+// The right-edge x-face records of the tile just stepped (fx = BX) become the
+// left-edge records (fx = 0) of the tile to its right, in the same shared
+// memory.  Called by every thread after a barrier that follows the tile's
+// phase C; the next tile's phase A writes only the halo records, and its
+// barrier orders these copies before phase B.
+template <typename R, int DIM, int QF1, int BX, int BY, int NT, int QG1 = 3>
+__device__ __forceinline__ void hand_over_x_edge(unsigned char *smem) {
+  using D = Dims<DIM, QF1, QG1>;
+  using TL = Tile<DIM, BX, BY, QF1, QG1>;
+  R *fp = reinterpret_cast<R *>(smem) + (size_t)TL::NH * D::NPREP;
+  constexpr int rows = DIM == 2 ? BY : 1, NC = D::template nface<R>();
+  for (int w = threadIdx.x; w < rows * NC; w += NT) {
+    const int fy = w % rows, c = w / rows;
+    fp[c * TL::NFACES + fy * (BX + 1)] = fp[c * TL::NFACES + fy * (BX + 1) + BX];
+  }
+}
+
 // ---- one tile step (phases A-C) --------------------------------------------------
 // The BX x BY tile whose first cell is (j0, k0); smem holds the halo and face
 // records.  Every output depends only on its own stencil's arithmetic: for a
 // given instantiation the result does not depend on the launch order or on
 // which tile a cell falls in (different tile shapes are different machine
 // code and may round differently).
+// carry: the tile's left-edge x-face records (fx = 0) are already in shared
+// memory, handed over by the tile on its left (hand_over_x_edge); phase B
+// skips them.
 template <typename R, int DIM, int QF1, int BX, int BY, int NT, bool ITER, bool MS = false, int QG1 = 3>
 __device__ __forceinline__ void step_tile(const StepConst &K, const State<R> &S, const State<R> &O,
-                                          Stats *stats, int j0, int k0, unsigned char *smem) {
+                                          Stats *stats, int j0, int k0, unsigned char *smem,
+                                          bool carry = false) {
   using D = Dims<DIM, QF1, QG1>;
   using TL = Tile<DIM, BX, BY, QF1, QG1>;
   R *sp = reinterpret_cast<R *>(smem);
@@ -1217,52 +1311,61 @@ __device__ __forceinline__ void step_tile(const StepConst &K, const State<R> &S,
   }
   __syncthreads();
 
-  // B. faces (a face on a tile edge is evaluated by both tiles; the iterated
-  // frame's counts take it from the tile on its right/upper side)
+  // B. faces (a face on a tile edge is evaluated by both tiles unless it was
+  // handed over; the iterated frame's counts take it from the tile on its
+  // right/upper side).  Work items: the x-faces this tile computes (BX + 1 per
+  // row, BX when the left edge was handed over), padded to whole warps so that
+  // no warp runs both the x-face and the y-face code, then the y-faces.
   unsigned noconv = 0, traces = 0, evals = 0, max_tr = 0;
-  for (int f = tid; f < TL::NFACES; f += NT) {
-    int st[8];
-    if (f < TL::NFX) {
-      const int fx = f % (BX + 1), fy = f / (BX + 1);
-      if (j0 + fx - 1 >= K.nx || k0 + fy >= (DIM == 2 ? K.ny : 1)) continue;
-      const int r = (fy + TL::OY) * TL::HX;
-      st[0] = r + fx + 1; st[1] = r + fx + 2; st[2] = r + fx; st[3] = r + fx + 3;
-      if constexpr (DIM == 2) {
-        st[4] = r - TL::HX + fx + 1; st[5] = r - TL::HX + fx + 2;
-        st[6] = r + TL::HX + fx + 1; st[7] = r + TL::HX + fx + 2;
-      }
-      int nt;
-      bool nc;
-      if constexpr (MS) {  // the face's f-lattice: the higher of its two cells'
-        if (lat[st[0]] == 0 && lat[st[1]] == 0)
-          nc = face_flux<R, DIM, QF1, 0, ITER, false, 3, QG1>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
-        else
+  {
+    constexpr int ROWS = DIM == 2 ? BY : 1;
+    const int xw = carry ? BX : BX + 1, x0 = carry ? 1 : 0;
+    const int nxi = xw * ROWS, px = (nxi + 31) / 32 * 32;
+    for (int w = tid; w < px + TL::NFY; w += NT) {
+      int st[8];
+      if (w < px) {
+        if (w >= nxi) continue;
+        const int fx = x0 + w % xw, fy = w / xw, f = fy * (BX + 1) + fx;
+        if (j0 + fx - 1 >= K.nx || k0 + fy >= (DIM == 2 ? K.ny : 1)) continue;
+        const int r = (fy + TL::OY) * TL::HX;
+        st[0] = r + fx + 1; st[1] = r + fx + 2; st[2] = r + fx; st[3] = r + fx + 3;
+        if constexpr (DIM == 2) {
+          st[4] = r - TL::HX + fx + 1; st[5] = r - TL::HX + fx + 2;
+          st[6] = r + TL::HX + fx + 1; st[7] = r + TL::HX + fx + 2;
+        }
+        int nt;
+        bool nc;
+        if constexpr (MS) {  // the face's f-lattice: the higher of its two cells'
+          if (lat[st[0]] == 0 && lat[st[1]] == 0)
+            nc = face_flux<R, DIM, QF1, 0, ITER, false, 3, QG1>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
+          else
+            nc = face_flux<R, DIM, QF1, 0, ITER, false, QF1, QG1>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
+        } else {
           nc = face_flux<R, DIM, QF1, 0, ITER, false, QF1, QG1>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
-      } else {
-        nc = face_flux<R, DIM, QF1, 0, ITER, false, QF1, QG1>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
-      }
-      if (ITER && (fx > 0 || j0 == 0)) {
-        noconv += nc; traces += nt; ++evals; max_tr = max(max_tr, (unsigned)nt);
-      }
-    } else if constexpr (DIM == 2) {
-      const int g = f - TL::NFX, fx = g % BX, fy = g / BX;
-      if (j0 + fx >= K.nx || k0 + fy - 1 >= K.ny) continue;
-      const int x = fx + 2, H = TL::HX;
-      st[0] = (fy + 1) * H + x; st[1] = (fy + 2) * H + x; st[2] = fy * H + x; st[3] = (fy + 3) * H + x;
-      st[4] = (fy + 1) * H + x - 1; st[5] = (fy + 2) * H + x - 1;
-      st[6] = (fy + 1) * H + x + 1; st[7] = (fy + 2) * H + x + 1;
-      int nt;
-      bool nc;
-      if constexpr (MS) {  // the face's f-lattice: the higher of its two cells'
-        if (lat[st[0]] == 0 && lat[st[1]] == 0)
-          nc = face_flux<R, DIM, QF1, 1, ITER, false, 3, QG1>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
-        else
+        }
+        if (ITER && (fx > 0 || j0 == 0)) {
+          noconv += nc; traces += nt; ++evals; max_tr = max(max_tr, (unsigned)nt);
+        }
+      } else if constexpr (DIM == 2) {
+        const int g = w - px, fx = g % BX, fy = g / BX, f = TL::NFX + g;
+        if (j0 + fx >= K.nx || k0 + fy - 1 >= K.ny) continue;
+        const int x = fx + 2, H = TL::HX;
+        st[0] = (fy + 1) * H + x; st[1] = (fy + 2) * H + x; st[2] = fy * H + x; st[3] = (fy + 3) * H + x;
+        st[4] = (fy + 1) * H + x - 1; st[5] = (fy + 2) * H + x - 1;
+        st[6] = (fy + 1) * H + x + 1; st[7] = (fy + 2) * H + x + 1;
+        int nt;
+        bool nc;
+        if constexpr (MS) {  // the face's f-lattice: the higher of its two cells'
+          if (lat[st[0]] == 0 && lat[st[1]] == 0)
+            nc = face_flux<R, DIM, QF1, 1, ITER, false, 3, QG1>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
+          else
+            nc = face_flux<R, DIM, QF1, 1, ITER, false, QF1, QG1>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
+        } else {
           nc = face_flux<R, DIM, QF1, 1, ITER, false, QF1, QG1>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
-      } else {
-        nc = face_flux<R, DIM, QF1, 1, ITER, false, QF1, QG1>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
-      }
-      if (ITER && (fy > 0 || k0 == 0)) {
-        noconv += nc; traces += nt; ++evals; max_tr = max(max_tr, (unsigned)nt);
+        }
+        if (ITER && (fy > 0 || k0 == 0)) {
+          noconv += nc; traces += nt; ++evals; max_tr = max(max_tr, (unsigned)nt);
+        }
       }
     }
   }

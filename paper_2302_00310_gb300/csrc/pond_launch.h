@@ -15,21 +15,46 @@
 
 namespace pond {
 
+// The work unit of a launch is a strip: up to `strip` consecutive tiles of one
+// row of a member's tiles, which one CTA steps from left to right, handing
+// each tile's right-edge x-faces to the next tile as its left edge (a face's
+// record depends only on its stencil, so the handed-over record is the one the
+// next tile would compute).
 template <typename R> struct InstDesc {
   StepConst K;
   State<R> S[2];
   Stats *stats;
   int tiles_x;     // tiles per row of the member's grid
-  int tile_begin;  // first global tile index of the member
+  int tile_begin;  // first global strip index of the member
   int steps;       // launch k advances the member iff k < steps
   int parity;      // launch k reads buffer (parity + k) & 1 and writes the other
 };
 
 struct TableHdr {
   int n;            // members in the table
-  int total_tiles;  // tiles over all members
-  int pad[62];      // 256-byte header
+  int total_tiles;  // strips over all members
+  int strip;        // tiles per strip (>= 1); a row's last strip may be shorter
+  int pad[61];      // 256-byte header
 };
+
+// strips of a member with tiles_x x tiles_y tiles
+inline int strips_of(int tiles_x, int tiles_y, int strip) { return (tiles_x + strip - 1) / strip * tiles_y; }
+
+// Tiles per strip for a table of `tiles` tiles in rows of `tiles_x`, on
+// `slots` resident CTAs: the longest strip (up to 8) that keeps the launch's
+// waves x strip length at its minimum, i.e. hands edges over without
+// lengthening the launch's critical path.
+inline int choose_strip(int tiles_x, int tiles_y, int slots) {
+  int best = 1;
+  long long best_cost = -1;
+  for (int L = 1; L <= 8; L *= 2) {
+    if (L > 1 && L > tiles_x) break;
+    const long long units = strips_of(tiles_x, tiles_y, L);
+    const long long cost = (units + slots - 1) / slots * L;
+    if (best_cost < 0 || cost <= best_cost) { best = L; best_cost = cost; }
+  }
+  return best;
+}
 
 // device bytes reserved in a context's workspace for its one-member table
 constexpr size_t kSoloTableBytes = 1024;

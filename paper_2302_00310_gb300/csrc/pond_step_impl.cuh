@@ -6,10 +6,13 @@
 
 namespace pond {
 
-// Launch k of a chunk: the grid strides over the table's tiles; member i owns
-// tiles [tile_begin_i, tile_begin_i + tiles_i) and advances iff k < steps_i,
+// Launch k of a chunk: the grid strides over the table's strips; member i owns
+// strips [tile_begin_i, tile_begin_i + strips_i) and advances iff k < steps_i,
 // from buffer (parity_i + k) & 1 into the other, with its own constants and
-// status block.  A one-member table with one CTA per tile is a plain step.
+// status block.  A strip's tiles are stepped left to right, each handing its
+// right-edge x-face records to the next (not with the iterated face frame,
+// whose trace statistics count each face at one tile).  A one-member table
+// with one CTA per strip is a plain step.
 template <typename R, int DIM, int QF1, int BX, int BY, int NT, int MINB, bool ITER, bool MS = false,
           int QG1 = 3>
 __global__ void __launch_bounds__(NT, MINB) member_step_kernel(const unsigned char *table, int k) {
@@ -18,11 +21,11 @@ __global__ void __launch_bounds__(NT, MINB) member_step_kernel(const unsigned ch
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ StepConst Ks;
   __shared__ int s_inst;
-  const int n = H->n, total = H->total_tiles;
+  const int n = H->n, total = H->total_tiles, L = H->strip > 0 ? H->strip : 1;
   int loaded = -1;
   for (int t = blockIdx.x; t < total; t += gridDim.x) {
     if (threadIdx.x == 0) {
-      int lo = 0, hi = n - 1;  // the last member whose first tile is <= t
+      int lo = 0, hi = n - 1;  // the last member whose first strip is <= t
       while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (desc[mid].tile_begin <= t) lo = mid;
@@ -40,13 +43,22 @@ __global__ void __launch_bounds__(NT, MINB) member_step_kernel(const unsigned ch
         __syncthreads();
         loaded = i;
       }
-      const int lt = t - d.tile_begin, p = (d.parity + k) & 1, tx = d.tiles_x;
+      const int ls = t - d.tile_begin, p = (d.parity + k) & 1, tx = d.tiles_x;
+      const int per_row = (tx + L - 1) / L, ty = ls / per_row, tx0 = (ls % per_row) * L;
+      const int tx1 = tx0 + L < tx ? tx0 + L : tx;
       // values, not references into the table: the step's global stores could
       // alias the table as far as the compiler knows, forcing reloads
       const State<R> S = d.S[p], O = d.S[p ^ 1];
       Stats *const st = d.stats;
-      step_tile<R, DIM, QF1, BX, BY, NT, ITER, MS, QG1>(Ks, S, O, st, (lt % tx) * BX,
-                                                        DIM == 2 ? (lt / tx) * BY : 0, smem_raw);
+      for (int x = tx0; x < tx1; ++x) {
+        const bool carry = !ITER && x > tx0;
+        if (carry) {
+          __syncthreads();  // the previous tile's phase C has read its face records
+          hand_over_x_edge<R, DIM, QF1, BX, BY, NT, QG1>(smem_raw);
+        }
+        step_tile<R, DIM, QF1, BX, BY, NT, ITER, MS, QG1>(Ks, S, O, st, x * BX, DIM == 2 ? ty * BY : 0,
+                                                          smem_raw, carry);
+      }
     }
     __syncthreads();  // s_inst, Ks and the tile's shared memory are reused
   }

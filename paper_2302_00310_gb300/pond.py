@@ -52,6 +52,7 @@ class pond_params(ctypes.Structure):
         ("iter_max", ctypes.c_int32), ("xi_fp64_threshold", ctypes.c_double),
         ("tile", ctypes.c_int32), ("multiscale", ctypes.c_int32), ("ms_theta_u", ctypes.c_double),
         ("ms_theta_T", ctypes.c_double), ("g_same_as_f", ctypes.c_int32),
+        ("strip", ctypes.c_int32),
     ]
 
 
@@ -434,6 +435,7 @@ def params_from_config(cfg: dict) -> pond_params:
     p.multiscale = int(cfg.get("ms", 0))
     p.ms_theta_u, p.ms_theta_T = float(cfg.get("ms_theta_u", 0.0)), float(cfg.get("ms_theta_T", 0.0))
     p.g_same_as_f = 1 if int(cfg.get("qg", 3)) == 4 else 0
+    p.strip = int(cfg.get("strip", 0))
     return p
 
 

@@ -25,9 +25,10 @@ from paper_2302_00310_gb300 import workloads as W
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 TOL = 1e-12
-# mixed path against the oracle; measured on GB300 (see the module docstring)
+# mixed path against the oracle, about ten times the values measured on GB300:
+# pulse L1 1.04e-7, Linf 8.5e-7 (rho; T's L1 8.2e-8); Riemann L1 1.2e-8, Linf 1.1e-7
 PULSE_L1, PULSE_LINF = 1e-6, 1e-5
-RIEMANN_L1, RIEMANN_LINF = 1e-6, 1e-4
+RIEMANN_L1, RIEMANN_LINF = 1e-7, 1e-6
 
 
 @pytest.fixture(scope="module", autouse=True)

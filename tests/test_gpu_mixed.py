@@ -4,12 +4,17 @@ cell's conserved moments and of its new frame; FP64 frame transformations
 where the shifted nodes land beyond xi_fp64_threshold.
 
 Its results are compared with the FP64 oracle (small grids) and with the FP64
-CUDA path, which matches the oracle to 1e-12 (full-size runs).  Stated error
-bounds, from FP32 rounding (unit roundoff 6e-8) carried through a step's
-~10^4 operations and then accumulated over the run:
-  * moments after <= 3 steps: max-relative error <= 2e-6 per field;
-  * L1 relative density error: <= 1e-5 for the smooth pulse (1000 steps at
-    256^2) and the Sod tube; <= 1e-3 for the four-quadrant Riemann problem.
+CUDA path, which matches the oracle to 1e-12 (full-size runs; the full-length
+runs against the oracle itself are in test_gpu_fullrun.py).  Stated error
+bounds, about ten times the values measured on GB300 (given beside each):
+  * moments after <= 3 steps: max-relative error <= 2e-6 per field
+    (measured at most 2.2e-7 over the cases below);
+  * L1 relative density error: 5e-7 for the 128^2 pulse after 200 steps
+    against the oracle (4.2e-8), 3e-7 for the Sod tube against the oracle
+    (2.8e-8), 1e-6 for the 256^2 pulse after 1000 steps against the FP64 path
+    (1.0e-7), 1e-7 for the 512^2 four-quadrant Riemann problem after 200 steps
+    against the FP64 path (6.5e-9);
+  * the iterated frame's cycling faces: 1e-3 (1.9e-5 and 1.8e-4).
 """
 import numpy as np
 import pytest
@@ -19,9 +24,12 @@ from paper_2302_00310_gb300 import pond
 from paper_2302_00310_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
-TOL_STEP = 2e-6
-TOL_L1_SMOOTH = 1e-5
-TOL_L1_SHOCK = 1e-3
+TOL_STEP = 2e-6            # measured <= 2.2e-7
+TOL_L1_PULSE128 = 5e-7     # measured 4.2e-8 (L1 rho and T, 200 steps, against the oracle)
+TOL_L1_SOD = 3e-7          # measured 2.8e-8 (250 steps, against the oracle)
+TOL_L1_PULSE256 = 1e-6     # measured 1.0e-7 (1000 steps, against the FP64 path)
+TOL_L1_RIEMANN = 1e-7      # measured 6.5e-9 (512^2, 200 steps, against the FP64 path)
+TOL_CYCLING = 1e-3         # measured 1.9e-5 and 1.8e-4 (seeds 70, 72)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -120,8 +128,8 @@ def test_mixed_pulse_matches_oracle_l1():
     gm, fl = _gpu(w["cfg"], prim, 200)
     assert fl[1] == 0
     print("MEASURED pulse128_mixed_vs_oracle_200 l1 %.3e l1_T %.3e" % (_l1(gm[0], om[0]), _l1(gm[3], om[3])))
-    assert _l1(gm[0], om[0]) <= TOL_L1_SMOOTH
-    assert _l1(gm[3], om[3]) <= TOL_L1_SMOOTH
+    assert _l1(gm[0], om[0]) <= TOL_L1_PULSE128
+    assert _l1(gm[3], om[3]) <= TOL_L1_PULSE128
 
 
 def test_mixed_pulse_full_run_l1():
@@ -133,7 +141,7 @@ def test_mixed_pulse_full_run_l1():
     assert fl[1] == 0
     print("MEASURED pulse256_mixed_vs_fp64_1000 l1 %.3e linf %.3e mass %.3e" % (
         _l1(m32[0], m64[0]), _linf(m32[0], m64[0]), abs(m32[0].sum() / m64[0].sum() - 1)))
-    assert _l1(m32[0], m64[0]) <= TOL_L1_SMOOTH, _l1(m32[0], m64[0])
+    assert _l1(m32[0], m64[0]) <= TOL_L1_PULSE256, _l1(m32[0], m64[0])
     # mass is conserved to FP32 rounding
     assert abs(m32[0].sum() / m64[0].sum() - 1) < 1e-6
 
@@ -144,7 +152,7 @@ def test_mixed_sod_l1():
     om = _oracle_moments(w["cfg"], prim, w["steps"])
     gm, _ = _gpu(w["cfg"], prim, w["steps"])
     print("MEASURED sod_mixed_vs_oracle l1 %.3e" % _l1(gm[0][0], om[0][0]))
-    assert _l1(gm[0][0], om[0][0]) <= TOL_L1_SMOOTH
+    assert _l1(gm[0][0], om[0][0]) <= TOL_L1_SOD
 
 
 def test_mixed_riemann_l1():
@@ -157,7 +165,7 @@ def test_mixed_riemann_l1():
     assert f64[1] & pond.POND_FLAG_NONPHYSICAL == 0 and f32[1] & pond.POND_FLAG_NONPHYSICAL == 0
     print("MEASURED riemann512_mixed_vs_fp64_200 l1 %.3e linf %.3e" % (_l1(m32[0], m64[0]),
                                                                        _linf(m32[0], m64[0])))
-    assert _l1(m32[0], m64[0]) <= TOL_L1_SHOCK, _l1(m32[0], m64[0])
+    assert _l1(m32[0], m64[0]) <= TOL_L1_RIEMANN, _l1(m32[0], m64[0])
 
 
 def test_mixed_iterated_frame_converges_in_fp32():
@@ -197,7 +205,7 @@ def test_mixed_iterated_frame_cycling_faces(seed):
     assert not fl[1] & pond.POND_FLAG_NONPHYSICAL
     assert fl[3] == ost.report["noconv_faces"] > 0
     print("MEASURED cycling_seed%d linf %.3e" % (seed, max(_linf(gm[i], om[i]) for i in range(4))))
-    assert max(_linf(gm[i], om[i]) for i in range(4)) <= 1e-3
+    assert max(_linf(gm[i], om[i]) for i in range(4)) <= TOL_CYCLING
 
 
 @pytest.mark.parametrize("precision", [pond.POND_FP64, pond.POND_FP32_MIXED])

@@ -503,3 +503,44 @@ def test_d2q25_matches_oracle(case):
     assert flags[1] & pond.POND_FLAG_NONPHYSICAL == 0
     if it:
         assert flags[4:] == (ost.report["face_evals"], ost.report["traces"], ost.report["max_traces"])
+
+
+@pytest.mark.parametrize("precision,D", [(pond.POND_FP64, 2), (pond.POND_FP32_MIXED, 2),
+                                         (pond.POND_FP64, 1)])
+def test_strips_give_the_same_state_bit_for_bit(precision, D):
+    """A CTA steps a strip of tiles and hands each tile's right-edge x-faces
+    to the next: every strip length must give the state of one tile per CTA,
+    bit for bit (ragged last tiles in x and y, zero-gradient and walled
+    sides)."""
+    nx, ny = (250, 61) if D == 2 else (2000, 1)
+    rho, ux, uy, T = W.random_state_grid(D, nx, ny, seed=81, mach=0.4, T=(0.8, 1.3))
+    if D == 2:
+        walls = ((0.0,) * 4, (0.0,) * 4, (0.0, 0.2, 0.0, 1.0), (0.0, -0.1, 0.0, 1.1))
+        cfg = W._base(2, nx, ny, tau=5e-3, dx=1.0 / nx, prandtl=0.71, bc=(1, 1, 3, 3), inflow=walls)
+    else:
+        cfg = W._base(1, nx, 1, tau=5e-3, dx=1.0 / nx, prandtl=0.71, bc=(1, 1, 1, 1))
+    cfg["dt"] = W.dt_from_cfl(ux, uy, T, cfg["dx"], 0.4)
+    ref = None
+    for strip in (1, 2, 3, 8):
+        sim = pond.Sim(dict(cfg, precision=precision, strip=strip))
+        sim.init(rho, ux, uy, T)
+        sim.step(3)
+        st = sim.get_state()
+        flags = sim.flags()[1]
+        sim.close()
+        assert flags & pond.POND_FLAG_NONPHYSICAL == 0, strip
+        if ref is None:
+            ref = st
+        for a, b in zip(st, ref):
+            assert np.array_equal(a, b), strip
+
+
+def test_strip_of_three_matches_oracle():
+    """Strips of three tiles on a ragged periodic / inflow grid: the handed-over
+    faces give the oracle's state."""
+    rho, ux, uy, T = W.random_state_grid(2, 53, 37, seed=83, mach=1.0)
+    cfg = W._base(2, 53, 37, tau=5e-3, dx=1.0 / 53, prandtl=0.71, limiter=1, bc=(2, 1, 0, 0),
+                  inflow=((1.1, 0.5, -0.2, 0.8),) * 4)
+    cfg["dt"] = W.dt_from_cfl(ux, uy, T, cfg["dx"], 0.4)
+    ost, got, flags = _run_both(dict(cfg, strip=3), rho, ux, uy, T, 2)
+    _compare(ost, got, 2)

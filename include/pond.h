@@ -154,8 +154,11 @@ typedef struct {
    * lifting sets the moments the low lattice lacks to their equilibrium
    * values, and the odd central moments of a Gaussian vanish.  A cell that
    * turns low drops them (the projection).  A face takes the higher lattice
-   * of its two cells.  Requires D1Q4 / D2Q16, Pr = 1, the averaged face
-   * frame, no walls and tile 0 (or the precision's default: 1 in 1D; 10 FP64,
+   * of its two cells.  The quasi-equilibrium step of a low cell relaxes the
+   * third-order content its lattice resolves; a wall ghost takes the lattice
+   * of the cell it reflects (a low one drops its Chapman-Enskog content of
+   * order 3 along an axis).  Requires D1Q4 / D2Q16, the averaged face frame
+   * and tile 0 (or the precision's default: 1 in 1D; 10 FP64,
    * 6 mixed in 2D); not batched.  With the main flux form a low cell keeps
    * mass and momentum but not energy exactly (its lattice lacks the
    * third-order moment the energy flux needs in another frame); Appendix C's

@@ -764,16 +764,39 @@ static void orc_ms_switch(orc_grid *G) {
 }
 
 /* Lattices of the ghost cells: that of their source cell; an inflow ghost
- * (a co-moving equilibrium, the same on both lattices) the low one. */
+ * (a co-moving equilibrium, the same on both lattices) the low one.  A wall
+ * ghost's source is the interior cell it reflects (Sec. IV.D), and a low wall
+ * ghost is projected like a low interior cell: its Chapman-Enskog content of
+ * order 3 along an axis is dropped in its co-moving frame. */
 static void orc_ms_ghost_lattices(orc_grid *G) {
   const orc_params *p = G->p;
-  const int k0 = (G->D == 2) ? -2 : 0, k1 = (G->D == 2) ? G->ny + 2 : 1;
+  const int D = G->D, ncp = orc_ncp(G);
+  const int k0 = (D == 2) ? -2 : 0, k1 = (D == 2) ? G->ny + 2 : 1;
   for (int k = k0; k < k1; ++k)
     for (int j = -2; j < G->nx + 2; ++j) {
       if (j >= 0 && j < G->nx && k >= 0 && k < G->ny) continue;
+      const int c = orc_pidx(G, j, k);
+      if (orc_is_wall_ghost(p, j, k)) {
+        int sj = j, sk = k;
+        if (D == 2 && (sj < 0 || sj >= p->nx)) {
+          if (p->bc[sj < 0 ? 0 : 1] == ORC_BC_PERIODIC) sj = sj < 0 ? sj + p->nx : sj - p->nx;
+          else sj = sj < 0 ? 0 : p->nx - 1;
+        }
+        int *n = D == 2 ? &sk : &sj;
+        const int nmax = D == 2 ? p->ny : p->nx;
+        *n = *n < 0 ? -*n - 1 : 2 * nmax - 1 - *n;
+        G->lat[c] = G->lat[orc_pidx(G, sj, sk)];
+        if (!G->lat[c]) {
+          double f[ORC_MAXQ], fo[ORC_MAXQ], u[2] = {G->ux[c], G->uy[c]};
+          for (int i = 0; i < G->Qf; ++i) f[i] = G->f[i * ncp + c];
+          orc_transform_x(&G->Lf, &G->Lf, G->Ll.K, D, p->grad_k, f, u, G->T[c], u, G->T[c], fo);
+          for (int i = 0; i < G->Qf; ++i) G->f[i * ncp + c] = fo[i];
+        }
+        continue;
+      }
       int sj = 0, sk = 0;
       const int side = orc_ghost_map(p, j, k, &sj, &sk);
-      G->lat[orc_pidx(G, j, k)] = side >= 0 ? 0 : G->lat[orc_pidx(G, sj, sk)];
+      G->lat[c] = side >= 0 ? 0 : G->lat[orc_pidx(G, sj, sk)];
     }
 }
 
@@ -960,8 +983,11 @@ static int orc_step_once(orc_grid *G, orc_report *rep) {
       double fn[ORC_MAXQ], gn[ORC_MAXQ];
       orc_transform(Lc, D, p->grad_k, f, uc, Tc, un, Tn, fn);
       orc_transform(&G->Lg, D, p->grad_k, g, uc, Tc, un, Tn, gn);
-      /* 6. second quasi-equilibrium half relaxation, in the new frame */
-      if (qe) orc_qe_half(&G->Lf, &G->Lg, D, G->Cv, dt, tau, tau2, fn, gn, un, Tn);
+      /* 6. second quasi-equilibrium half relaxation, in the new frame, on the
+       * cell's own f-lattice (a multiscale low cell: its third-order content
+       * is what D2Q9 / D1Q3 resolves; the first half acts on the lifted
+       * storage, whose coefficients of order 3 along an axis are zero) */
+      if (qe) orc_qe_half(Lc, &G->Lg, D, G->Cv, dt, tau, tau2, fn, gn, un, Tn);
       if (low) { /* back to the high-lattice storage (lifting, in the new frame) */
         double fs[ORC_MAXQ];
         orc_transform_x(Lc, &G->Lf, Lc->K, D, p->grad_k, fn, un, Tn, un, Tn, fs);
@@ -1041,12 +1067,9 @@ static int orc_check(const orc_params *p) {
       return 0;
     if (p->D == 1 && (s > 1 || p->nx < 3)) return 0;
   }
-  /* multiscale: D1Q3/D1Q4 (D2Q9/D2Q16) f-lattices, BGK, averaged face frame,
-   * no walls */
+  /* multiscale: D1Q3/D1Q4 (D2Q9/D2Q16) f-lattices, averaged face frame */
   if (p->ms) {
-    if (p->qf != 4 || p->qg != 3 || p->prandtl != 1.0 || p->iterative) return 0;
-    for (int s = 0; s < 4; ++s)
-      if (p->bc[s] == ORC_BC_WALL) return 0;
+    if (p->qf != 4 || p->qg != 3 || p->iterative) return 0;
   }
   return 1;
 }

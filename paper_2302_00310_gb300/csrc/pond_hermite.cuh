@@ -100,14 +100,21 @@ __device__ __forceinline__ void ana3(R &p0, R &p1, R &p2) {
 //   q(+-sqrt3) = B_0 + iT B_2 +- sqrt3 isT B_1,  q(0) = B_0 - iT/2 B_2.
 constexpr double K6 = 0.408248290463863;  // sqrt(6)/6
 template <typename R, int Q> struct SynK;
+// (the converting constructors copy another arithmetic type's constants, e.g.
+// the same frame's FP32 constants into both lanes of a packed pair)
 template <typename R> struct SynK<R, 4> {
   R h1, h2, k, r1, r2;
   __device__ __forceinline__ SynK(R iT, R isT)
       : h1(R(0.5 * H2R1) * iT), h2(R(0.5 * H2R2) * iT), k(R(K6) * iT), r1(R(R1) * isT), r2(R(R2) * isT) {}
+  template <typename S>
+  __device__ __forceinline__ explicit SynK(const SynK<S, 4> &o)
+      : h1(R(o.h1)), h2(R(o.h2)), k(R(o.k)), r1(R(o.r1)), r2(R(o.r2)) {}
 };
 template <typename R> struct SynK<R, 3> {
   R e, z, r;
   __device__ __forceinline__ SynK(R iT, R isT) : e(iT), z(R(-0.5) * iT), r(R(SQ3) * isT) {}
+  template <typename S>
+  __device__ __forceinline__ explicit SynK(const SynK<S, 3> &o) : e(R(o.e)), z(R(o.z)), r(R(o.r)) {}
 };
 template <typename R>
 __device__ __forceinline__ void synq(const SynK<R, 4> &S, R &m0, R &m1, R &m2, R &m3) {
@@ -253,6 +260,10 @@ template <typename R> struct SynK<R, 5> {
         r1(R(R1Q) * isT), nr1(R(-R1Q) * isT), h22(R(0.5 * he2(R2Q)) * iT),
         h42(R(he4(R2Q) / 24.0) * (iT * iT)), k2(R((R2Q * R2Q - 3.0) / 6.0) * iT), r2(R(R2Q) * isT),
         nr2(R(-R2Q) * isT), z2(R(-0.5) * iT), z4(R(0.125) * (iT * iT)) {}
+  template <typename S>
+  __device__ __forceinline__ explicit SynK(const SynK<S, 5> &o)
+      : h21(R(o.h21)), h41(R(o.h41)), k1(R(o.k1)), r1(R(o.r1)), nr1(R(o.nr1)), h22(R(o.h22)), h42(R(o.h42)),
+        k2(R(o.k2)), r2(R(o.r2)), nr2(R(o.nr2)), z2(R(o.z2)), z4(R(o.z4)) {}
 };
 template <typename R>
 __device__ __forceinline__ void synq(const SynK<R, 5> &S, R &m0, R &m1, R &m2, R &m3, R &m4) {

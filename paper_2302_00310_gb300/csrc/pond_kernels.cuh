@@ -28,6 +28,7 @@
 #include <type_traits>
 
 #include "pond_hermite.cuh"
+#include "pond_packed.cuh"
 
 namespace pond {
 
@@ -209,6 +210,20 @@ __device__ __forceinline__ R limit(R x, R y, int lim) {
   else return pos(p) ? div_nr(p, x + y) : R(0);
 }
 
+// The limited slope of two lanes at once (the mixed path's trace): the
+// differences, product, sum and quotient in the paired FP32 instructions, the
+// reciprocal and the sign tests per lane; the same values as limit() on each
+// lane to FP32 rounding.
+__device__ __forceinline__ f2 limit2(f2 x, f2 y, int lim) {
+  const f2 p = x * y;
+  if (lim == LIM_MINMOD)
+    return f2(pos(p.lo()) ? (abs_less(x.lo(), y.lo()) ? x.lo() : y.lo()) : 0.f,
+              pos(p.hi()) ? (abs_less(x.hi(), y.hi()) ? x.hi() : y.hi()) : 0.f);
+  const f2 s = x + y;
+  const f2 q = p * f2(__fdividef(1.f, s.lo()), __fdividef(1.f, s.hi()));
+  return f2(pos(p.lo()) ? q.lo() : 0.f, pos(p.hi()) ? q.hi() : 0.f);
+}
+
 // The FP32 instantiation is the mixed-precision path (POND_FP32_MIXED).
 template <typename R> constexpr bool is_mixed() { return std::is_same<R, float>::value; }
 
@@ -252,6 +267,17 @@ __device__ __forceinline__ void move_frame(const StepConst &K, R usx, R usy, R T
   const R dT3 = R(3) * dT;
   shift_x(make_dshift(dx, dT, dT3), Y);
   if constexpr (DIM == 2) shift_y(make_dshift(dy, dT, dT3), Y);
+}
+
+// multiscale projection onto the low-order lattice (Sec. II.E): coefficients of order 3 along an
+// axis (and, with the Grad projection, of total order 3) dropped
+template <typename R, int Q, int NY>
+__device__ __forceinline__ void ms_project(Blk<R, Q, NY> &B, int grad_k) {
+#pragma unroll
+  for (int a = 0; a < Q; ++a)
+#pragma unroll
+    for (int b = 0; b < NY; ++b)
+      if (a > 2 || b > 2 || (NY > 1 && grad_k && a + b > 2)) B.v[a][b] = R(0);
 }
 
 // ---- wall ghosts (Sec. IV.D) -------------------------------------------------
@@ -361,17 +387,33 @@ __device__ __forceinline__ void wall_ghost(const StepConst &K, const State<R> &S
   Tout = R(T);
 }
 
+// the interior cell that the wall ghost (j, k) reflects (the x rule first in 2D)
+template <int DIM>
+__device__ __forceinline__ void wall_source(const StepConst &K, int j, int k, int &sj, int &sk) {
+  if (DIM == 2 && (j < 0 || j >= K.nx)) {
+    if (K.bc[j < 0 ? 0 : 1] == BC_PERIODIC) { j %= K.nx; if (j < 0) j += K.nx; }
+    else j = j < 0 ? 0 : K.nx - 1;
+  }
+  int &n = DIM == 2 ? k : j;
+  const int nmax = DIM == 2 ? K.ny : K.nx;
+  n = n < 0 ? -n - 1 : 2 * nmax - 1 - n;
+  sj = j; sk = DIM == 2 ? k : 0;
+}
+
 // phase A for a wall ghost (out of line: only halo cells across a wall run it):
 // phi_bar^+ = kp_a phi~ + kp_b phi^eq, with no quasi-equilibrium step (the
-// ghost is built from the cells' macroscopic fields, which it leaves alone)
+// ghost is built from the cells' macroscopic fields, which it leaves alone).
+// low: the multiscale ghost takes the low-order lattice of the cell it
+// reflects, and its content of order 3 along an axis is dropped.
 template <typename R, int DIM, int QF1, int QG1 = 3>
 __device__ __noinline__ void prep_wall_cell(const StepConst &K, const State<R> &S, int j, int k, R *sp,
-                                            int NH, int h) {
+                                            int NH, int h, bool low = false) {
   using D = Dims<DIM, QF1, QG1>;
   Blk<R, QF1, D::NYF> F;
   Blk<R, QG1, D::NYG> G;
   R ux, uy, T;
   wall_ghost<R, DIM, QF1, QG1>(K, S, j, k, F, G, ux, uy, T);
+  if (low) ms_project(F, K.grad_k);
   const R rho = F.v[0][0], ka = kc<R>(K.kp_a, K.cf.kp_a);
 #pragma unroll
   for (int a = 0; a < QF1; ++a)
@@ -407,10 +449,17 @@ __device__ __noinline__ void prep_wall_cell(const StepConst &K, const State<R> &
 // vanish), and a cell that turns low drops them (the projection).  A face
 // takes the higher lattice of its two cells.
 
-// u_x, u_y, T at index (j, k): an interior cell or its ghost (no walls)
+// u_x, u_y, T at index (j, k): an interior cell or its ghost (a wall ghost:
+// the reflection of Sec. IV.D)
 template <int DIM, typename R>
 __device__ __forceinline__ void ms_fields(const StepConst &K, const State<R> &S, int j, int k,
                                           double &ux, double &uy, double &T) {
+  if (is_wall_ghost<DIM>(K, j, k)) {
+    double m[4];
+    wall_mac<R, DIM>(K, S, j, k, m);
+    ux = m[1]; uy = m[2]; T = m[3];
+    return;
+  }
   int sj = 0, sk = 0;
   const int side = map_cell<DIM>(K, j, k, sj, sk);
   if (side >= 0) {
@@ -436,16 +485,6 @@ __device__ __noinline__ bool ms_high(const StepConst &K, const State<R> &S, int 
   const double T = (double)S.T[(size_t)k * K.nx + j];
   return 0.5 * gu / sqrt(T) > K.ms_theta_u || 0.5 * gT / T > K.ms_theta_T;
 }
-// projection onto the low-order lattice: coefficients of order 3 along an
-// axis (and, with the Grad projection, of total order 3) dropped
-template <typename R, int Q, int NY>
-__device__ __forceinline__ void ms_project(Blk<R, Q, NY> &B, int grad_k) {
-#pragma unroll
-  for (int a = 0; a < Q; ++a)
-#pragma unroll
-    for (int b = 0; b < NY; ++b)
-      if (a > 2 || b > 2 || (NY > 1 && grad_k && a + b > 2)) B.v[a][b] = R(0);
-}
 
 // ---- phase A: one halo cell -> shared memory ------------------------------
 // MS: multiscale; the cell's lattice goes to lat[h] (1 high, 0 low).
@@ -458,7 +497,14 @@ __device__ __forceinline__ void prep_cell(const StepConst &K, const State<R> &S,
   R ux, uy, T;
   int sj = 0, sk = 0;
   if (is_wall_ghost<DIM>(K, j, k)) {
-    prep_wall_cell<R, DIM, QF1, QG1>(K, S, j, k, sp, NH, h);
+    bool low = false;
+    if constexpr (MS) {  // the lattice of the cell the ghost reflects
+      int wj = 0, wk = 0;
+      wall_source<DIM>(K, j, k, wj, wk);
+      low = !ms_high<DIM>(K, S, wj, wk);
+      lat[h] = low ? 0 : 1;
+    }
+    prep_wall_cell<R, DIM, QF1, QG1>(K, S, j, k, sp, NH, h, low);
     return;
   }
   const int side = map_cell<DIM>(K, j, k, sj, sk);
@@ -569,6 +615,64 @@ __device__ __forceinline__ void stencil_pops(const StepConst &K, const R *sp, in
   else stencil_pops_body<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, h, uFx, uFy, TF, sTF, SK, Y);
 }
 
+// The mixed path moves the two cells beside the face (stencil cells 0 and 1)
+// together, in one out-of-line call, in the two lanes of the paired FP32
+// instructions: the same tensor-product frame change (each lane its own
+// shift), Grad projection and synthesis as stencil_pops_body.  A cell whose
+// transformation must run in FP64 takes both cells through
+// stencil_pops_body instead.
+template <typename R, int DIM, int Q> struct TwoBlk {
+  Blk<R, Q, (DIM == 2 ? Q : 1)> L, R_;
+};
+template <int DIM, int QF1, int Q, int GS, int QG1>
+__device__ __forceinline__ TwoBlk<float, DIM, Q> stencil_two_body(const StepConst &K, const float *sp, int NH,
+                                                                 int hL, int hR, float uFx, float uFy, float TF,
+                                                                 float sTF, const SynK<float, Q> &SK) {
+  using D = Dims<DIM, QF1, QG1>;
+  constexpr int NY = DIM == 2 ? Q : 1, base = GS ? D::QF : 0, stride = GS ? QG1 : QF1;
+  TwoBlk<float, DIM, Q> out;
+  const float uxL = sp[D::IUX * NH + hL], uxR = sp[D::IUX * NH + hR];
+  const float uyL = DIM == 2 ? sp[D::IUY * NH + hL] : 0.f, uyR = DIM == 2 ? sp[D::IUY * NH + hR] : 0.f;
+  const float TL = sp[D::IT * NH + hL], TR = sp[D::IT * NH + hR];
+  const float lim = K.xi_thr * sTF;
+  const bool full =
+      fmaf(sp[D::IST * NH + hL], float(Nodes<Q>::cmax), fmaxf(fabsf(uxL - uFx), fabsf(uyL - uFy))) > lim ||
+      fmaf(sp[D::IST * NH + hR], float(Nodes<Q>::cmax), fmaxf(fabsf(uxR - uFx), fabsf(uyR - uFy))) > lim;
+  if (full) {
+    stencil_pops_body<float, DIM, QF1, Q, GS, QG1>(K, sp, NH, hL, uFx, uFy, TF, sTF, SK, out.L);
+    stencil_pops_body<float, DIM, QF1, Q, GS, QG1>(K, sp, NH, hR, uFx, uFy, TF, sTF, SK, out.R_);
+    return out;
+  }
+  const SynK<f2, Q> S(SK);
+  const f2 dT(TL - TF, TR - TF), dT3 = f2(3) * dT;
+  Blk<f2, Q, NY> B;
+#pragma unroll
+  for (int n = 0; n < Q; ++n)
+#pragma unroll
+    for (int m = 0; m < NY; ++m)
+      B.v[n][m] = f2(sp[(base + n + stride * m) * NH + hL], sp[(base + n + stride * m) * NH + hR]);
+  shift_x(make_dshift(f2(uxL - uFx, uxR - uFx), dT, dT3), B);
+  if constexpr (DIM == 2) {
+    shift_y(make_dshift(f2(uyL - uFy, uyR - uFy), dT, dT3), B);
+    if (K.grad_k) grad_mask(B);
+  }
+  synq_xy(S, B);
+#pragma unroll
+  for (int n = 0; n < Q; ++n)
+#pragma unroll
+    for (int m = 0; m < NY; ++m) {
+      out.L.v[n][m] = B.v[n][m].lo();
+      out.R_.v[n][m] = B.v[n][m].hi();
+    }
+  return out;
+}
+template <int DIM, int QF1, int Q, int GS, int QG1>
+__device__ __noinline__ TwoBlk<float, DIM, Q> stencil_two_call(const StepConst &K, const float *sp, int NH,
+                                                              int hL, int hR, float uFx, float uFy, float TF,
+                                                              float sTF, SynK<float, Q> SK) {
+  return stencil_two_body<DIM, QF1, Q, GS, QG1>(K, sp, NH, hL, hR, uFx, uFy, TF, sTF, SK);
+}
+
 // ---- a pair of stencil cells of which each normal node needs one ------------
 // The trace of a normal node takes its outer neighbour and its two tangential
 // neighbours from the upwind side only: cells 2 / 4 / 6 of the stencil where
@@ -629,6 +733,55 @@ __device__ __forceinline__ void stencil_pair_body(const StepConst &K, const R *s
   }
   if (full) {
     Y = stencil_pair_full<R, DIM, QF1, Q, GS, QG1, DIRN>(K, sp, NH, hA, hB, upm, uFx, uFy, TF, sTF, SK);
+    return;
+  }
+  if constexpr (is_mixed<R>()) {
+    // the two cells' normal stage in the two lanes of the paired FP32
+    // instructions, then the selected values' tangential stage two normal
+    // nodes at a time (an odd last node alone)
+    const SynK<f2, Q> S(SK);
+    const f2 dT(TA - TF, TB - TF), dT3 = f2(3) * dT;
+    const DShift<f2> Cn = make_dshift(f2(unA - uFn, unB - uFn), dT, dT3);
+    const DShift<f2> Ct = make_dshift(f2(utA - uFt, utB - uFt), dT, dT3);
+    float Z[Q][Q];  // [normal node][tangential order]
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      f2 p[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const int c = DIRN == 0 ? i + stride * j : j + stride * i;
+        p[i] = f2(sp[(base + c) * NH + hA], sp[(base + c) * NH + hB]);
+      }
+      dshiftq(Cn, p);
+      synqq(S, p);
+#pragma unroll
+      for (int k = 0; k < Q; ++k) Z[k][j] = pick((upm >> k & 1u) != 0u, p[k]);
+    }
+#pragma unroll
+    for (int k = 0; k + 1 < Q; k += 2) {
+      const DShift<f2> C = pick_rows((upm >> k & 1u) != 0u, (upm >> (k + 1) & 1u) != 0u, Ct);
+      f2 t[Q];
+#pragma unroll
+      for (int j = 0; j < Q; ++j) t[j] = f2(Z[k][j], Z[k + 1][j]);
+      dshiftq(C, t);
+      synqq(S, t);
+#pragma unroll
+      for (int j = 0; j < Q; ++j) {
+        Y.v[DIRN == 0 ? k : j][DIRN == 0 ? j : k] = t[j].lo();
+        Y.v[DIRN == 0 ? k + 1 : j][DIRN == 0 ? j : k + 1] = t[j].hi();
+      }
+    }
+    if constexpr (Q % 2 == 1) {
+      constexpr int k = Q - 1;
+      const DShift<float> C = pick_row((upm >> k & 1u) != 0u, Ct);
+      float t[Q];
+#pragma unroll
+      for (int j = 0; j < Q; ++j) t[j] = Z[k][j];
+      dshiftq(C, t);
+      synqq(SK, t);
+#pragma unroll
+      for (int j = 0; j < Q; ++j) Y.v[DIRN == 0 ? k : j][DIRN == 0 ? j : k] = t[j];
+    }
     return;
   }
   {
@@ -719,6 +872,54 @@ __device__ __noinline__ void reconstruct_tie(const StepConst &K, const R *sp, in
     }
 }
 
+// First stage of the trace (normal limited slope) from the two cells beside
+// the face (YL, YR) and the outer cell of the upwind side (Bo): A = the upwind
+// value, out = A + offn L(A - Bo, downwind - A); two tangential nodes per paired
+// instruction on the mixed path.
+template <typename R, int DIM, int DIRN, int Q>
+__device__ __forceinline__ void trace_normal(const Blk<R, Q, (DIM == 2 ? Q : 1)> &YL,
+                                             const Blk<R, Q, (DIM == 2 ? Q : 1)> &YR,
+                                             const Blk<R, Q, (DIM == 2 ? Q : 1)> &Bo, unsigned upm,
+                                             const R *offn, int lim, Blk<R, Q, (DIM == 2 ? Q : 1)> &A,
+                                             Blk<R, Q, (DIM == 2 ? Q : 1)> &out) {
+  constexpr int NY = DIM == 2 ? Q : 1;
+  if constexpr (is_mixed<R>() && DIM == 2) {
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+      const bool up = (upm >> k & 1u) != 0u;
+#pragma unroll
+      for (int t = 0; t < Q; t += 2) {
+        const int n0 = DIRN == 0 ? k : t, m0 = DIRN == 0 ? t : k;
+        if (t + 1 < Q) {
+          const int n1 = DIRN == 0 ? k : t + 1, m1 = DIRN == 0 ? t + 1 : k;
+          const f2 a = up ? f2(YL.v[n0][m0], YL.v[n1][m1]) : f2(YR.v[n0][m0], YR.v[n1][m1]);
+          const f2 c = up ? f2(YR.v[n0][m0], YR.v[n1][m1]) : f2(YL.v[n0][m0], YL.v[n1][m1]);
+          const f2 o = fma(f2(offn[k]), limit2(a - f2(Bo.v[n0][m0], Bo.v[n1][m1]), c - a, lim), a);
+          A.v[n0][m0] = a.lo(); A.v[n1][m1] = a.hi();
+          out.v[n0][m0] = o.lo(); out.v[n1][m1] = o.hi();
+        } else {
+          const R a = up ? YL.v[n0][m0] : YR.v[n0][m0];
+          const R c = up ? YR.v[n0][m0] : YL.v[n0][m0];
+          A.v[n0][m0] = a;
+          out.v[n0][m0] = a + offn[k] * limit(a - Bo.v[n0][m0], c - a, lim);
+        }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int n = 0; n < Q; ++n)
+#pragma unroll
+      for (int m = 0; m < NY; ++m) {
+        const int k = DIRN == 0 ? n : m;
+        const bool up = (upm >> k & 1u) != 0u;
+        const R a = up ? YL.v[n][m] : YR.v[n][m];
+        const R c = up ? YR.v[n][m] : YL.v[n][m];
+        A.v[n][m] = a;
+        out.v[n][m] = a + offn[k] * limit(a - Bo.v[n][m], c - a, lim);
+      }
+  }
+}
+
 // Limited half-step MUSCL trace of the populations of one lattice (Q nodes
 // per axis) to the face (Eq. eq:InterfacePop), on node values divided by
 // the weights (the trace is homogeneous of degree 1 in each node's values).  st[] = halo indices of the
@@ -767,19 +968,17 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
   Blk<R, Q, NY> A;
   {
     Blk<R, Q, NY> YL, YR, Bo;
-    stencil_pops<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, st[0], uFx, uFy, TF, sTF, SK, YL);
-    stencil_pops<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, st[1], uFx, uFy, TF, sTF, SK, YR);
+    if constexpr (is_mixed<R>()) {
+      const TwoBlk<float, DIM, Q> two = stencil_two_call<DIM, QF1, Q, GS, QG1>(K, sp, NH, st[0], st[1], uFx, uFy,
+                                                                            TF, sTF, SK);
+      YL = two.L;
+      YR = two.R_;
+    } else {
+      stencil_pops<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, st[0], uFx, uFy, TF, sTF, SK, YL);
+      stencil_pops<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, st[1], uFx, uFy, TF, sTF, SK, YR);
+    }
     stencil_pair<R, DIM, QF1, Q, GS, QG1, DIRN>(K, sp, NH, st[2], st[3], upm, uFx, uFy, TF, sTF, SK, Bo);
-#pragma unroll
-    for (int n = 0; n < Q; ++n)
-#pragma unroll
-      for (int m = 0; m < NY; ++m) {
-        const int k = DIRN == 0 ? n : m;
-        const R a = up[k] ? YL.v[n][m] : YR.v[n][m];
-        const R c = up[k] ? YR.v[n][m] : YL.v[n][m];
-        A.v[n][m] = a;
-        out.v[n][m] = a + offn[k] * limit(a - Bo.v[n][m], c - a, lim);
-      }
+    trace_normal<R, DIM, DIRN, Q>(YL, YR, Bo, upm, offn, lim, A, out);
   }
   if constexpr (DIM == 2) {
     Blk<R, Q, NY> Y, Dl;
@@ -789,13 +988,31 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
 #pragma unroll
       for (int m = 0; m < NY; ++m) Dl.v[n][m] = A.v[n][m] - Y.v[n][m];
     stencil_pair<R, DIM, QF1, Q, GS, QG1, DIRN>(K, sp, NH, st[6], st[7], upm, uFx, uFy, TF, sTF, SK, Y);
+    if constexpr (is_mixed<R>()) {
 #pragma unroll
-    for (int n = 0; n < Q; ++n)
+      for (int k = 0; k < Q; ++k)
 #pragma unroll
-      for (int m = 0; m < NY; ++m) {
-        const int kt = DIRN == 0 ? m : n;
-        out.v[n][m] += offt[kt] * limit(Dl.v[n][m], Y.v[n][m] - A.v[n][m], lim);
-      }
+        for (int t = 0; t < Q; t += 2) {
+          const int n0 = DIRN == 0 ? k : t, m0 = DIRN == 0 ? t : k;
+          if (t + 1 < Q) {
+            const int n1 = DIRN == 0 ? k : t + 1, m1 = DIRN == 0 ? t + 1 : k;
+            const f2 a(A.v[n0][m0], A.v[n1][m1]);
+            const f2 l = limit2(f2(Dl.v[n0][m0], Dl.v[n1][m1]), f2(Y.v[n0][m0], Y.v[n1][m1]) - a, lim);
+            const f2 o = fma(f2(offt[t], offt[t + 1]), l, f2(out.v[n0][m0], out.v[n1][m1]));
+            out.v[n0][m0] = o.lo(); out.v[n1][m1] = o.hi();
+          } else {
+            out.v[n0][m0] += offt[t] * limit(Dl.v[n0][m0], Y.v[n0][m0] - A.v[n0][m0], lim);
+          }
+        }
+    } else {
+#pragma unroll
+      for (int n = 0; n < Q; ++n)
+#pragma unroll
+        for (int m = 0; m < NY; ++m) {
+          const int kt = DIRN == 0 ? m : n;
+          out.v[n][m] += offt[kt] * limit(Dl.v[n][m], Y.v[n][m] - A.v[n][m], lim);
+        }
+    }
   }
 }
 
@@ -1090,6 +1307,75 @@ __device__ __forceinline__ void face_contrib(const StepConst &K, const R *fp, in
   }
 }
 
+// The mixed path moves a cell's two faces along one direction into its frame
+// in one out-of-line call, the upper face in the low lane and the lower face
+// in the high lane of the paired FP32 instructions (each lane its own face
+// frame's shift, the same arithmetic as face_contrib_body), and returns their
+// difference, upper minus lower.  A face whose transformation must run in
+// FP64 takes both faces through face_contrib_body instead.
+template <int DIM, int QF1, int QG1>
+__device__ __noinline__ FaceContrib<float, DIM, QF1, QG1> face_pair_diff_call(const StepConst &K, const float *fp,
+                                                                             int NFACES, int flo, int fhi,
+                                                                             float ux, float uy, float T,
+                                                                             float sT) {
+  using D = Dims<DIM, QF1, QG1>;
+  constexpr int NYF = D::NYF, NYG = D::NYG;
+  FaceContrib<float, DIM, QF1, QG1> out;
+  const float uxh = fp[D::FUX * NFACES + fhi], uxl = fp[D::FUX * NFACES + flo];
+  const float uyh = DIM == 2 ? fp[D::FUY * NFACES + fhi] : 0.f, uyl = DIM == 2 ? fp[D::FUY * NFACES + flo] : 0.f;
+  const float Th = fp[D::FT * NFACES + fhi], Tl = fp[D::FT * NFACES + flo];
+  const float lim = K.xi_thr * sT;
+  const bool full =
+      fmaf(fp[D::FST * NFACES + fhi], float(Nodes<QF1>::cmax), fmaxf(fabsf(uxh - ux), fabsf(uyh - uy))) > lim ||
+      fmaf(fp[D::FST * NFACES + flo], float(Nodes<QF1>::cmax), fmaxf(fabsf(uxl - ux), fabsf(uyl - uy))) > lim;
+  if (full) {
+    Blk<float, QF1, NYF> Xl;
+    Blk<float, QG1, NYG> Yl;
+    face_contrib_body<float, DIM, QF1, QG1>(K, fp, NFACES, fhi, ux, uy, T, sT, out.X, out.Y);
+    face_contrib_body<float, DIM, QF1, QG1>(K, fp, NFACES, flo, ux, uy, T, sT, Xl, Yl);
+#pragma unroll
+    for (int p = 0; p < QF1; ++p)
+#pragma unroll
+      for (int q = 0; q < NYF; ++q) out.X.v[p][q] = out.X.v[p][q] - Xl.v[p][q];
+#pragma unroll
+    for (int p = 0; p < QG1; ++p)
+#pragma unroll
+      for (int q = 0; q < NYG; ++q) out.Y.v[p][q] = out.Y.v[p][q] - Yl.v[p][q];
+    return out;
+  }
+  Blk<f2, QF1, NYF> X;
+  Blk<f2, QG1, NYG> Y;
+#pragma unroll
+  for (int a = 0; a < QF1; ++a)
+#pragma unroll
+    for (int b = 0; b < NYF; ++b)
+      X.v[a][b] = f2(fp[(a + QF1 * b) * NFACES + fhi], fp[(a + QF1 * b) * NFACES + flo]);
+#pragma unroll
+  for (int a = 0; a < QG1; ++a)
+#pragma unroll
+    for (int b = 0; b < NYG; ++b)
+      Y.v[a][b] = f2(fp[(D::QF + a + QG1 * b) * NFACES + fhi], fp[(D::QF + a + QG1 * b) * NFACES + flo]);
+  const f2 dT(Th - T, Tl - T), dT3 = f2(3) * dT;
+  const DShift<f2> Cx = make_dshift(f2(uxh - ux, uxl - ux), dT, dT3);
+  shift_x(Cx, X);
+  shift_x(Cx, Y);
+  if constexpr (DIM == 2) {
+    const DShift<f2> Cy = make_dshift(f2(uyh - uy, uyl - uy), dT, dT3);
+    shift_y(Cy, X);
+    shift_y(Cy, Y);
+    if (K.grad_k) { grad_mask(X); grad_mask(Y); }
+  }
+#pragma unroll
+  for (int a = 0; a < QF1; ++a)
+#pragma unroll
+    for (int b = 0; b < NYF; ++b) out.X.v[a][b] = X.v[a][b].lo() - X.v[a][b].hi();
+#pragma unroll
+  for (int a = 0; a < QG1; ++a)
+#pragma unroll
+    for (int b = 0; b < NYG; ++b) out.Y.v[a][b] = Y.v[a][b].lo() - Y.v[a][b].hi();
+  return out;
+}
+
 // The two faces of the cell along DIRN (lower face flo, upper face fhi):
 // F += -dt/dx [(v . n) G phi_hi - (v . n) G phi_lo] (Eq. fluxEq; the
 // multiplication by v_n in the cell frame is linear, so it is applied once to
@@ -1103,18 +1389,27 @@ __device__ __forceinline__ void add_faces(const StepConst &K, const R *fp, int N
                                           Blk<R, QG1, Dims<DIM, QF1, QG1>::NYG> &G, MomAcc &M,
                                           bool low = false) {
   using D = Dims<DIM, QF1, QG1>;
-  Blk<R, QF1, D::NYF> DX, X;
-  Blk<R, QG1, D::NYG> DY, Y;
-  face_contrib<R, DIM, QF1, QG1>(K, fp, NFACES, flo, ux, uy, T, sT, DX, DY);
-  face_contrib<R, DIM, QF1, QG1>(K, fp, NFACES, fhi, ux, uy, T, sT, X, Y);
+  Blk<R, QF1, D::NYF> DX;
+  Blk<R, QG1, D::NYG> DY;
+  if constexpr (is_mixed<R>()) {
+    const FaceContrib<float, DIM, QF1, QG1> c =
+        face_pair_diff_call<DIM, QF1, QG1>(K, fp, NFACES, flo, fhi, ux, uy, T, sT);
+    DX = c.X;
+    DY = c.Y;
+  } else {
+    Blk<R, QF1, D::NYF> X;
+    Blk<R, QG1, D::NYG> Y;
+    face_contrib<R, DIM, QF1, QG1>(K, fp, NFACES, flo, ux, uy, T, sT, DX, DY);
+    face_contrib<R, DIM, QF1, QG1>(K, fp, NFACES, fhi, ux, uy, T, sT, X, Y);
 #pragma unroll
-  for (int p = 0; p < QF1; ++p)
+    for (int p = 0; p < QF1; ++p)
 #pragma unroll
-    for (int q = 0; q < D::NYF; ++q) DX.v[p][q] = X.v[p][q] - DX.v[p][q];
+      for (int q = 0; q < D::NYF; ++q) DX.v[p][q] = X.v[p][q] - DX.v[p][q];
 #pragma unroll
-  for (int p = 0; p < QG1; ++p)
+    for (int p = 0; p < QG1; ++p)
 #pragma unroll
-    for (int q = 0; q < D::NYG; ++q) DY.v[p][q] = Y.v[p][q] - DY.v[p][q];
+      for (int q = 0; q < D::NYG; ++q) DY.v[p][q] = Y.v[p][q] - DY.v[p][q];
+  }
   if constexpr (MS) {
     if (low) ms_project(DX, K.grad_k);
   }

@@ -75,10 +75,8 @@ def _params(**kw):
 
 
 @pytest.mark.parametrize("lat,kw", [
-    # multiscale: Pr 1, averaged frame, no walls, no D2Q25, the precision's tile, App. C when mixed
-    (pond.POND_D2Q16, dict(multiscale=1, prandtl=0.71)),
+    # multiscale: averaged frame, no D2Q25, the precision's tile, App. C when mixed
     (pond.POND_D2Q16, dict(multiscale=1, flux_frame=pond.POND_FRAME_ITER)),
-    (pond.POND_D2Q16, dict(multiscale=1, bc=(0, 0, 3, 3))),
     (pond.POND_D2Q25, dict(multiscale=1)),
     (pond.POND_D2Q16, dict(multiscale=1, tile=6)),
     (pond.POND_D2Q16, dict(multiscale=1, precision=pond.POND_FP32_MIXED)),

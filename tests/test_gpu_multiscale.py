@@ -1,7 +1,8 @@
 """Multiscale f-lattice on the GPU (Sec. II.E lifting and projection, Sec.
 IV.C switching): the same state and the same count of high-lattice cell
-updates as the oracle, across tiles with ragged tails, boundaries, limiters,
-the Grad projection and Appendix C's flux form; the single-lattice limits;
+updates as the oracle, across tiles with ragged tails, boundaries (walls
+included), limiters, the Grad projection, the quasi-equilibrium step and
+Appendix C's flux form; the single-lattice limits;
 the Lax tube of Sec. V.C.1; and the configurations it does not cover."""
 import numpy as np
 import pytest
@@ -60,23 +61,32 @@ def _thresholds(cfg, fields, steps, min_gap=1e-9):
     return th
 
 
+WALLS_2D = ((0.0,) * 4, (0.0,) * 4, (0.0, 0.2, 0.0, 1.0), (0.0, -0.1, 0.0, 1.1))
+WALLS_1D = ((0.0, 0.0, 0.0, 1.0), (0.0, 0.0, 0.0, 1.1), (0.0,) * 4, (0.0,) * 4)
+
 MS_CASES = [
-    # D, nx, ny, bc, limiter, grad_k, appc, mach, steps
-    (2, 37, 30, (0, 0, 0, 0), 0, 0, 0, 0.8, 3),
-    (2, 29, 33, (1, 1, 1, 1), 1, 1, 0, 1.0, 2),
-    (2, 24, 31, (2, 1, 0, 0), 0, 0, 1, 0.6, 2),
-    (2, 17, 45, (0, 0, 2, 2), 1, 1, 1, 0.9, 2),
-    (1, 300, 1, (1, 1, 0, 0), 0, 0, 0, 1.0, 3),
-    (1, 253, 1, (2, 1, 0, 0), 1, 0, 1, 0.8, 2),
+    # D, nx, ny, bc, limiter, grad_k, appc, mach, steps, other options
+    (2, 37, 30, (0, 0, 0, 0), 0, 0, 0, 0.8, 3, {}),
+    (2, 29, 33, (1, 1, 1, 1), 1, 1, 0, 1.0, 2, {}),
+    (2, 24, 31, (2, 1, 0, 0), 0, 0, 1, 0.6, 2, {}),
+    (2, 17, 45, (0, 0, 2, 2), 1, 1, 1, 0.9, 2, {}),
+    (1, 300, 1, (1, 1, 0, 0), 0, 0, 0, 1.0, 3, {}),
+    (1, 253, 1, (2, 1, 0, 0), 1, 0, 1, 0.8, 2, {}),
+    # the quasi-equilibrium step (Pr != 1) and walls
+    (2, 27, 31, (0, 0, 0, 0), 1, 1, 1, 0.8, 2, dict(prandtl=0.5)),
+    (2, 30, 26, (1, 1, 3, 3), 0, 0, 0, 0.6, 2, dict(prandtl=0.71, inflow=WALLS_2D)),
+    (2, 21, 35, (0, 0, 3, 3), 1, 1, 1, 0.6, 2, dict(inflow=WALLS_2D)),
+    (1, 230, 1, (3, 3, 0, 0), 0, 0, 0, 0.5, 3, dict(prandtl=0.71, inflow=WALLS_1D)),
 ]
 
 
 @pytest.mark.parametrize("case", range(len(MS_CASES)))
 def test_multiscale_matches_oracle(case):
-    D, nx, ny, bc, lim, gk, appc, mach, steps = MS_CASES[case]
-    fields = W.random_state_grid(D, nx, ny, seed=150 + case, mach=mach)
+    D, nx, ny, bc, lim, gk, appc, mach, steps, extra = MS_CASES[case]
+    walls = 3 in bc
+    fields = W.random_state_grid(D, nx, ny, seed=150 + case, mach=mach, T=(0.7, 1.4) if walls else (0.5, 2.0))
     cfg = W._base(D, nx, ny, tau=5e-3, dx=1.0 / nx, limiter=lim, grad_k=gk, flux_appc=appc, bc=bc,
-                  inflow=INFLOW)
+                  **dict(dict(inflow=INFLOW), **extra))
     cfg["dt"] = W.dt_from_cfl(fields[1], fields[2], fields[3], cfg["dx"], 0.4)
     thu, thT = _thresholds(cfg, fields, steps)
     cfg = dict(cfg, ms=1, ms_theta_u=thu, ms_theta_T=thT)
@@ -100,10 +110,11 @@ def test_multiscale_matches_oracle(case):
 
 
 MIXED_CASES = [
-    # D, nx, ny, bc, limiter, grad_k, steps (Appendix C's flux form)
-    (2, 37, 30, (0, 0, 0, 0), 0, 0, 3),
-    (2, 29, 33, (1, 1, 2, 1), 1, 1, 2),
-    (1, 300, 1, (1, 1, 0, 0), 0, 0, 3),
+    # D, nx, ny, bc, limiter, grad_k, steps, other options (Appendix C's flux form)
+    (2, 37, 30, (0, 0, 0, 0), 0, 0, 3, {}),
+    (2, 29, 33, (1, 1, 2, 1), 1, 1, 2, {}),
+    (1, 300, 1, (1, 1, 0, 0), 0, 0, 3, {}),
+    (2, 31, 27, (0, 0, 3, 3), 0, 0, 2, dict(prandtl=0.71, inflow=WALLS_2D)),
 ]
 
 
@@ -113,10 +124,11 @@ def test_multiscale_mixed_path(case):
     oracle's moments within the step bound 2e-6 and its count of high-lattice
     cell updates (thresholds clear of the measures by far more than FP32
     rounding)."""
-    D, nx, ny, bc, lim, gk, steps = MIXED_CASES[case]
-    fields = W.random_state_grid(D, nx, ny, seed=190 + case, mach=0.8)
+    D, nx, ny, bc, lim, gk, steps, extra = MIXED_CASES[case]
+    walls = 3 in bc
+    fields = W.random_state_grid(D, nx, ny, seed=190 + case, mach=0.8, T=(0.7, 1.4) if walls else (0.5, 2.0))
     cfg = W._base(D, nx, ny, tau=5e-3, dx=1.0 / nx, limiter=lim, grad_k=gk, flux_appc=1, bc=bc,
-                  inflow=INFLOW)
+                  **dict(dict(inflow=INFLOW), **extra))
     cfg["dt"] = W.dt_from_cfl(fields[1], fields[2], fields[3], cfg["dx"], 0.4)
     thu, thT = _thresholds(cfg, fields, steps, min_gap=1e-4)
     cfg = dict(cfg, ms=1, ms_theta_u=thu, ms_theta_T=thT)
@@ -184,9 +196,8 @@ def test_lax_tube_on_the_gpu():
     assert abs(high - ost.report["ms_high"]) <= 1e-3 * ost.report["ms_high"]
 
 
-@pytest.mark.parametrize("bad", [dict(precision=pond.POND_FP32_MIXED, flux_appc=0), dict(prandtl=0.71),
-                                 dict(iterative=1), dict(bc=(0, 0, 3, 3)), dict(tile=6),
-                                 dict(qf=5)])
+@pytest.mark.parametrize("bad", [dict(precision=pond.POND_FP32_MIXED, flux_appc=0), dict(iterative=1),
+                                 dict(tile=6), dict(qf=5)])
 def test_multiscale_rejects_what_it_does_not_cover(bad):
     fields = W.random_state_grid(2, 16, 16, seed=1)
     cfg = W._base(2, 16, 16, tau=5e-3, dx=1.0 / 16, inflow=((0.0, 0.1, 0.0, 1.0),) * 4)

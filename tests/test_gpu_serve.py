@@ -42,11 +42,16 @@ def test_each_result_is_the_same_alone_and_in_the_mix(torch, precision, autotune
         sim.step(r.steps)
         alone = sim.moments()
         sim.close()
-        for a, b in zip(r.result, alone):
-            if r.dim == 1 and a is r.result[2]:
+        # velocity components are measured against the flow's velocity scale
+        # (the larger component's maximum): a component that is nearly zero
+        # everywhere carries rounding of the size of the other one's
+        vscale = max(np.max(np.abs(alone[1])), np.max(np.abs(alone[2])) if r.dim == 2 else 0.0)
+        for i, (a, b) in enumerate(zip(r.result, alone)):
+            if r.dim == 1 and i == 2:
                 continue
             if autotune:
-                assert np.max(np.abs(a - b)) <= 2e-6 * max(np.max(np.abs(b)), 1e-30), r.rid
+                scale = vscale if i in (1, 2) else np.max(np.abs(b))
+                assert np.max(np.abs(a - b)) <= 2e-6 * max(scale, 1e-30), (r.rid, i)
             else:
                 assert np.array_equal(a, b), r.rid
 

@@ -119,11 +119,24 @@ def _case(D, n, seed, **kw):
     return d, (rho, ux, uy, T)
 
 
-@pytest.mark.parametrize("D,grad_k,appc,bc", [(1, 0, 0, (1, 1, 0, 0)), (1, 0, 1, (0, 0, 0, 0)),
-                                              (2, 0, 0, (1, 1, 0, 0)), (2, 1, 1, (0, 0, 1, 2))])
-def test_all_high_and_all_low_are_the_single_lattice_steps(D, grad_k, appc, bc):
-    d, fields = _case(D, 10, 40 + D, grad_k=grad_k, flux_appc=appc, bc=bc,
-                      inflow=((1.1, 0.3, -0.1, 0.9),) * 4)
+WALLS_2D = ((0.0,) * 4, (0.0,) * 4, (0.0, 0.2, 0.0, 1.0), (0.0, -0.1, 0.0, 1.1))
+WALLS_1D = ((0.0, 0.0, 0.0, 1.0), (0.0, 0.0, 0.0, 1.1), (0.0,) * 4, (0.0,) * 4)
+
+
+@pytest.mark.parametrize("D,grad_k,appc,bc,pr", [(1, 0, 0, (1, 1, 0, 0), 1.0), (1, 0, 1, (0, 0, 0, 0), 1.0),
+                                                 (2, 0, 0, (1, 1, 0, 0), 1.0), (2, 1, 1, (0, 0, 1, 2), 1.0),
+                                                 (2, 0, 0, (0, 0, 0, 0), 0.71), (1, 0, 1, (1, 1, 0, 0), 0.5),
+                                                 (2, 0, 0, (1, 1, 3, 3), 1.0), (2, 1, 1, (0, 0, 3, 3), 0.71),
+                                                 (1, 0, 0, (3, 3, 0, 0), 0.71)])
+def test_all_high_and_all_low_are_the_single_lattice_steps(D, grad_k, appc, bc, pr):
+    """With the quasi-equilibrium step (Pr != 1) and walls too: a multiscale run
+    whose cells are all high is the D2Q16 (D1Q4) run bit for bit, one whose
+    cells are all low is the D2Q9 (D1Q3) f-lattice run to rounding (the QE
+    step on a low cell relaxes the third-order content D2Q9 resolves; a low
+    wall ghost carries the Chapman-Enskog content D2Q9 resolves)."""
+    walls = 3 in bc
+    d, fields = _case(D, 10, 40 + D, grad_k=grad_k, flux_appc=appc, bc=bc, prandtl=pr,
+                      inflow=(WALLS_2D if D == 2 else WALLS_1D) if walls else ((1.1, 0.3, -0.1, 0.9),) * 4)
     steps = 3
     plain = oracle.Config.from_dict(d)
     high = oracle.Config.from_dict(dict(d, ms=1, ms_theta_u=-1.0, ms_theta_T=-1.0))
@@ -169,10 +182,11 @@ def test_switching_measure_on_step_profiles():
         np.testing.assert_allclose(su, want_u, rtol=1e-15, atol=0)
 
 
-@pytest.mark.parametrize("D,appc", [(1, 0), (1, 1), (2, 0), (2, 1)])
-def test_conservation_with_mixed_lattices(D, appc):
+@pytest.mark.parametrize("D,appc,pr", [(1, 0, 1.0), (1, 1, 1.0), (2, 0, 1.0), (2, 1, 1.0), (2, 1, 0.71),
+                                       (1, 0, 0.5)])
+def test_conservation_with_mixed_lattices(D, appc, pr):
     n = 10
-    d, fields = _case(D, n, 17, tau=2e-2, bc=(0, 0, 0, 0), flux_appc=appc)
+    d, fields = _case(D, n, 17, tau=2e-2, bc=(0, 0, 0, 0), flux_appc=appc, prandtl=pr)
     probe = oracle.Config.from_dict(dict(d, ms=1))
     su, sT = oracle.ms_measure(probe, *fields[1:])
     th = float(np.median(np.maximum(su, sT)))
@@ -217,8 +231,31 @@ def test_lax_tube_multiscale_matches_the_high_lattice():
         assert 0.0 < frac["ms", n] < 0.1
 
 
-@pytest.mark.parametrize("bad", [dict(prandtl=0.71), dict(iterative=1), dict(qf=5),
-                                 dict(bc=(0, 0, 3, 3))])
+def test_walled_channel_with_mixed_lattices_stays_mirror_symmetric():
+    """A channel state mirror-symmetric about its mid-plane between two equal
+    walls, with the QE step and thresholds that put part of the cells on each
+    lattice: the lattice choice, the wall ghosts' lattices and the state stay
+    symmetric."""
+    nx, ny = 6, 12
+    g = W.rng(5)
+    half = [g.uniform(a, b, (ny // 2, nx)) for a, b in ((0.8, 1.2), (0.8, 1.2), (-0.3, 0.3), (-0.3, 0.3))]
+    rho, T, ux = (np.vstack([a, a[::-1]]) for a in half[:3])
+    uy = np.vstack([half[3], -half[3][::-1]])
+    wall = (0.0, 0.1, 0.0, 1.05)
+    d = W._base(2, nx, ny, tau=5e-3, dx=1.0 / ny, prandtl=0.71, bc=(0, 0, 3, 3), inflow=(wall,) * 4)
+    d["dt"] = W.dt_from_cfl(ux, uy, T, d["dx"], 0.3)
+    probe = oracle.Config.from_dict(dict(d, ms=1))
+    su, sT = oracle.ms_measure(probe, ux, uy, T)
+    th = float(np.median(np.maximum(su, sT)))
+    cfg = oracle.Config.from_dict(dict(d, ms=1, ms_theta_u=th, ms_theta_T=th))
+    st = oracle.run(cfg, oracle.init(cfg, rho, ux, uy, T), 6)
+    assert 0 < st.report["ms_high"] < 6 * nx * ny
+    m = oracle.moments(cfg, st)
+    for field, sign in zip(m, (1, 1, -1, 1)):
+        np.testing.assert_allclose(field, sign * field[::-1], rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("bad", [dict(iterative=1), dict(qf=5)])
 def test_multiscale_rejects_what_it_does_not_cover(bad):
     d, fields = _case(2, 8, 3)
     cfg = oracle.Config.from_dict(dict(d, ms=1, **bad))

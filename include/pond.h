@@ -179,9 +179,9 @@ typedef struct {
    * strip of consecutive tiles of one tile row left to right, handing each
    * tile's right-edge x-face records to the next tile instead of computing
    * them twice (a face's record depends only on its stencil, so every strip
-   * length gives the same state bit for bit).  Automatic: the longest strip
-   * (up to 8) that does not lengthen the launch's waves x strip length; 1 with
-   * the iterated face frame.  Batches choose their own (pond_batch_step). */
+   * length gives the same state bit for bit).  Automatic: 2 where that does
+   * not lengthen the launch's waves x strip length, else 1; 1 with the
+   * iterated face frame.  Batches choose their own (pond_batch_step). */
   int32_t strip;
 } pond_params;
 

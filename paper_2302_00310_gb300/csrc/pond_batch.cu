@@ -113,15 +113,15 @@ pond_status upload_table(pond_batch *b, int shape, const std::vector<int> &steps
   unsigned char *h = b->htable[slot];
   TableHdr hdr;
   memset(&hdr, 0, sizeof(hdr));
-  // strips of up to 8 tiles, as long as the grid still strides over at least
-  // four strips per CTA (members with different step counts drop out of
-  // later launches, and many small units keep the CTAs balanced)
+  // strips of two tiles where the grid still strides over at least four
+  // strips per CTA (members with different step counts drop out of later
+  // launches, and many small units keep the CTAs balanced), else single tiles
   const int slots = b->sms * std::max(1, b->occupancy[shape]);
   long long all_tiles = 0;
   for (size_t i = 0; i < b->members.size(); ++i)
     if (steps[i] > 0) all_tiles += tiles_of(b->members[i], s);
   int strip = 1;
-  while (strip < 8 && all_tiles / (2 * strip) >= 4LL * slots) strip *= 2;
+  while (strip < pond::kMaxAutoStrip && all_tiles / (2 * strip) >= 4LL * slots) strip *= 2;
   size_t ncell = 0;
   int unit = 0;
   for (size_t i = 0; i < b->members.size(); ++i) {

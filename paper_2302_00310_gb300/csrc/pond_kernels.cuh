@@ -920,6 +920,44 @@ __device__ __forceinline__ void trace_normal(const Blk<R, Q, (DIM == 2 ? Q : 1)>
   }
 }
 
+// The zero normal node of an odd lattice has v_n = u_F,n, so v_n = 0 exactly
+// wherever the face frame is at rest along the normal (a gas at rest, a wall
+// at rest).  reconstruct() then traces that node from the right/upper side
+// (pos(+-0) is false); this adds its trace from the left/lower side: the two
+// cells beside the face give zl / zr (the node's row, one value per
+// tangential node), cells 2 / 4 / 6 of the stencil are moved in full.  Out of
+// line: only such faces call it.
+template <typename R, int N> struct Row {
+  R v[N];
+};
+template <typename R, int DIM, int QF1, int DIRN, int Q, int GS, int QG1>
+__device__ __noinline__ Row<R, (DIM == 2 ? Q : 1)> zero_node_left(
+    const StepConst &K, const R *sp, int NH, int hO, int hLo, int hHi, R uFx, R uFy, R TF, R sTF,
+    SynK<R, Q> SK, Row<R, (DIM == 2 ? Q : 1)> zl, Row<R, (DIM == 2 ? Q : 1)> zr, R offn,
+    Row<R, (DIM == 2 ? Q : 1)> offt, int lim) {
+  constexpr int NY = DIM == 2 ? Q : 1, NZ = DIM == 2 ? Q : 1, KZ = Q / 2;
+  Row<R, NZ> t;
+  Blk<R, Q, NY> Y;
+  stencil_pops_body<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, hO, uFx, uFy, TF, sTF, SK, Y);
+#pragma unroll
+  for (int z = 0; z < NZ; ++z) {
+    const R a = zl.v[z], b = DIRN == 0 ? Y.v[KZ][z] : Y.v[z][KZ];
+    t.v[z] = a + offn * limit(a - b, zr.v[z] - a, lim);
+  }
+  if constexpr (DIM == 2) {
+    Blk<R, Q, NY> H;
+    stencil_pops_body<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, hLo, uFx, uFy, TF, sTF, SK, Y);
+    stencil_pops_body<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, hHi, uFx, uFy, TF, sTF, SK, H);
+#pragma unroll
+    for (int z = 0; z < NZ; ++z) {
+      const R a = zl.v[z];
+      const R lo = DIRN == 0 ? Y.v[KZ][z] : Y.v[z][KZ], hi = DIRN == 0 ? H.v[KZ][z] : H.v[z][KZ];
+      t.v[z] += offt.v[z] * limit(a - lo, hi - a, lim);
+    }
+  }
+  return t;
+}
+
 // Limited half-step MUSCL trace of the populations of one lattice (Q nodes
 // per axis) to the face (Eq. eq:InterfacePop), on node values divided by
 // the weights (the trace is homogeneous of degree 1 in each node's values).  st[] = halo indices of the
@@ -929,8 +967,11 @@ __device__ __forceinline__ void trace_normal(const Blk<R, Q, (DIM == 2 ? Q : 1)>
 // trace is a + (1/2 - |v_n| lam/2) L(a - b, c - a) for either upwind side
 // (L odd and symmetric), plus the tangential term -v_t lam/2 L(a - lo, hi - a).
 // The offsets carry the factor lf of limit().
-// TIE: 0 = no node of the face has v_n = 0 (checked by the caller), 1 = check
-// here, 2 = the face has one (both run reconstruct_tie out of line).
+// TIE: 0 = no node of the face other than an odd lattice's zero node has
+// v_n = 0 (checked by the caller), 1 = check here, 2 = the face has one (both
+// run reconstruct_tie out of line).  The zero node at v_n = 0 (u_F,n = 0
+// exactly) takes the mean of its two one-sided traces here: the right/upper
+// one in line, the left/lower one from zero_node_left.
 template <typename R, int DIM, int QF1, int DIRN, int Q, int TIE, int GS, int QG1>
 __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int NH, const int *st,
                                             R uFx, R uFy, R TF, R sTF, R isTF,
@@ -954,7 +995,9 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
     const R vn = sTF * c + uFn;
     up[k] = pos(vn);
     upm |= up[k] ? 1u << k : 0u;
-    if constexpr (TIE == 1) tie |= is_zero(vn);
+    if constexpr (TIE == 1) {
+      if (Q % 2 == 0 || 2 * k != Q - 1) tie |= is_zero(vn);
+    }
     offn[k] = h0 - hl * fabs(vn);
     offt[k] = -hl * (sTF * c + uFt);
   }
@@ -964,7 +1007,10 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
       return;
     }
   }
-  // (no node has v_n = 0 here: the caller routes such faces to the tie path)
+  // (no node but the zero node has v_n = 0 here: the tie path takes the others)
+  constexpr bool ODD = Q % 2 == 1;
+  constexpr int KZ = Q / 2, NZ = DIM == 2 ? Q : 1;
+  Row<R, NZ> zl, zr;  // the zero node's row in the two cells beside the face
   Blk<R, Q, NY> A;
   {
     Blk<R, Q, NY> YL, YR, Bo;
@@ -976,6 +1022,13 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
     } else {
       stencil_pops<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, st[0], uFx, uFy, TF, sTF, SK, YL);
       stencil_pops<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, st[1], uFx, uFy, TF, sTF, SK, YR);
+    }
+    if constexpr (ODD) {
+#pragma unroll
+      for (int z = 0; z < NZ; ++z) {
+        zl.v[z] = DIRN == 0 ? YL.v[KZ][z] : YL.v[z][KZ];
+        zr.v[z] = DIRN == 0 ? YR.v[KZ][z] : YR.v[z][KZ];
+      }
     }
     stencil_pair<R, DIM, QF1, Q, GS, QG1, DIRN>(K, sp, NH, st[2], st[3], upm, uFx, uFy, TF, sTF, SK, Bo);
     trace_normal<R, DIM, DIRN, Q>(YL, YR, Bo, upm, offn, lim, A, out);
@@ -1014,6 +1067,21 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int
         }
     }
   }
+  if constexpr (ODD) {
+    if (is_zero(uFn)) {
+      Row<R, NZ> ot;
+#pragma unroll
+      for (int z = 0; z < NZ; ++z) ot.v[z] = offt[z];
+      const Row<R, NZ> tl = zero_node_left<R, DIM, QF1, DIRN, Q, GS, QG1>(
+          K, sp, NH, st[2], DIM == 2 ? st[4] : 0, DIM == 2 ? st[6] : 0, uFx, uFy, TF, sTF, SK, zl, zr,
+          offn[KZ], ot, lim);
+#pragma unroll
+      for (int z = 0; z < NZ; ++z) {
+        R &o = DIRN == 0 ? out.v[KZ][z] : out.v[z][KZ];
+        o = R(0.5) * (o + tl.v[z]);
+      }
+    }
+  }
 }
 
 // Gaussian expectations E[H_n(mu + X; TF)], X ~ N(0, Tb), n <= 3, with
@@ -1050,13 +1118,14 @@ template <typename R, int DIM, int QF1, int DIRN, bool ITER, bool TIE = false, i
 __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int NH, const int *st,
                                           R *fp, int NFACES, int fidx, int &ntrace);
 
-// does a node of either lattice have v_n = 0 exactly in the face frame?  (The
-// zero node of D1Q3 / D1Q5 does whenever u_F,n = 0: a wall at rest, a gas at
-// rest.)  Such a face takes the out-of-line trace, where that node takes the
-// mean of its two one-sided traces.
+// does a node of either lattice other than an odd lattice's zero node have
+// v_n = 0 exactly in the face frame (u_F,n = -c_k sqrt(T_F) to the last bit:
+// rare)?  Such a face takes the out-of-line trace, where that node takes the
+// mean of its two one-sided traces.  The zero node (v_n = u_F,n: 0 for a gas
+// or a wall at rest) is averaged in line by reconstruct().
 template <typename R, int QF1, int QG1 = 3>
 __device__ __forceinline__ bool face_has_tie(R uFn, R sTF) {
-  bool t = (QF1 % 2 == 1 || QG1 % 2 == 1) && is_zero(uFn);
+  bool t = false;
 #pragma unroll
   for (int k = 0; k < QF1; ++k)
     if (QF1 % 2 == 0 || 2 * k != QF1 - 1) t |= is_zero(sTF * R(Nodes<QF1>::c(k)) + uFn);

@@ -82,6 +82,27 @@ def test_batch_equals_solo_bitwise(torch, D, precision):
             assert np.array_equal(x, y)
 
 
+@pytest.mark.parametrize("D,precision", [(2, pond.POND_FP64), (2, pond.POND_FP32_MIXED), (1, pond.POND_FP64)])
+def test_batch_with_strips_equals_solo_bitwise(torch, D, precision):
+    """Enough members that the batch steps strips of two tiles (each CTA
+    hands a tile's right-edge faces to the next; 16 grids of about 160^2, or 8
+    tubes of 80,000 cells, are over 2,400 tiles): the members' states are still
+    the solo states bit for bit."""
+    if D == 2:
+        sizes, steps = [152 + 2 * i for i in range(16)], [4 + i % 5 for i in range(16)]
+    else:
+        sizes, steps = [80000 + 37 * i for i in range(8)], [3 + i % 4 for i in range(8)]
+    probs = _problems(D, sizes, 120, precision)
+    tune = pond.pond_tune_default()
+    tune.graph_steps = 4
+    tune.autotune = 0
+    ref = _solo(probs, steps)
+    got, info, _ = _batched(torch, probs, steps, D, precision, tune)
+    for a, b in zip(got, ref):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+
+
 @pytest.mark.parametrize("precision", [pond.POND_FP64, pond.POND_FP32_MIXED])
 def test_autotuner_times_real_steps(torch, precision):
     """The autotuner runs one chunk per candidate shape on the members' own
@@ -185,7 +206,9 @@ def test_members_that_do_not_fit_are_rejected(torch):
 
 def test_shock_bubble_batch_mixed_vs_fp64(torch):
     """Shock-bubble instances (Mach 1.5-5, density ratio 0.1-10, inflow):
-    the FP32 batch against FP64 solo runs, L1 relative density <= 1e-3."""
+    the FP32 batch against FP64 solo runs after 100 steps: L1 relative
+    density within 3e-7, the bound stated for the benchmark's 64-instance
+    batch (measured 2.7e-8 there at 200 steps)."""
     ws = [W.shock_bubble_2d(seed=s, n=n) for s, n in ((0, 64), (1, 96), (2, 80), (3, 72))]
     b = pond.Batch(2, pond.POND_FP32_MIXED, len(ws))
     sims = []
@@ -207,4 +230,6 @@ def test_shock_bubble_batch_mixed_vs_fp64(torch):
         ref.step(100)
         r64 = ref.moments()[0]
         ref.close()
-        assert np.sum(np.abs(m[0] - r64)) / np.sum(r64) <= 1e-3
+        l1 = float(np.sum(np.abs(m[0] - r64)) / np.sum(r64))
+        print("MEASURED shock_bubble_%d_mixed_vs_fp64_100 l1 %.3e" % (w["cfg"]["nx"], l1))
+        assert l1 <= 3e-7, l1

@@ -135,7 +135,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * CLOCK_MAX_GHZ / 1e3     # 2 FP64 FMA/clk/SM
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * CLOCK_MAX_GHZ / 1e3   # 128 FP32 FMA/clk/SM
 # the step kernels the main line launches, as the profiler names them
 KERNEL_FP64 = "member_step_kernel<double, 2, 4, 8, 14, 128, 2, 0, 0, 3>"
-KERNEL_FP32 = "member_step_kernel<float, 2, 4, 8, 16, 160, 2, 0, 0, 3>"
+KERNEL_FP32 = "member_step_kernel<float, 2, 4, 8, 14, 128, 2, 0, 0, 3>"
 
 
 def _build_digest():

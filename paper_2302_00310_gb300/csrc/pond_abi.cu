@@ -223,12 +223,12 @@ pond_status step_once(pond_ctx *c) {
   return POND_OK;
 }
 
-// Fastest in tile sweeps on GB300 (256^2 and 1024^2 grids): on the mixed
-// path 8x16 tiles with 160 threads and registers for two CTAs per SM; in
-// FP64 8x14 tiles with 128 threads, two CTAs per SM (shared memory and the
-// register file each hold exactly two)
+// Fastest in tile sweeps on GB300 (256^2 pulse and 1024^2 Riemann grids):
+// 8x14 tiles with 128 threads and two CTAs per SM in both precisions (FP64:
+// shared memory and the register file each hold exactly two; mixed: 1,421
+// and 1,518 MLUPS against 1,247 and 1,476 for 8x16 tiles with 160 threads)
 // (D2Q25: 8x8 tiles with 128 threads, two CTAs per SM)
-int auto_tile(const pond_ctx *c) { return c->D == 1 ? 1 : (c->qf1 == 5 ? 10 : (c->fp32 ? 6 : 10)); }
+int auto_tile(const pond_ctx *c) { return c->D == 1 ? 1 : 10; }
 
 bool valid_params(const pond_params *p) {
   if (!p) return false;
@@ -401,11 +401,10 @@ pond_status pond_create(pond_ctx **out, pond_lattice lat, const int64_t dims[2],
   if (D == 1 && p->tile > 1) return POND_E_INVAL;
   if (D == 2 && p->tile == 1) return POND_E_INVAL;
   if (lat == POND_D2Q25 && p->tile != 0 && p->tile != 2 && p->tile != 10) return POND_E_INVAL;
-  if (p->multiscale && (lat == POND_D2Q25 ||
-                        (p->tile != 0 && p->tile != (D == 1 ? 1 : (p->precision == POND_FP64 ? 10 : 6)))))
+  if (p->multiscale && (lat == POND_D2Q25 || (p->tile != 0 && p->tile != (D == 1 ? 1 : 10))))
     return POND_E_INVAL;
   if (p->g_same_as_f && (lat == POND_D2Q25 || p->multiscale || p->flux_frame != POND_FRAME_AVG ||
-                         (p->tile != 0 && p->tile != (D == 1 ? 1 : (p->precision == POND_FP64 ? 10 : 6)))))
+                         (p->tile != 0 && p->tile != (D == 1 ? 1 : 10))))
     return POND_E_INVAL;
   if (workspace && (workspace_bytes < need || ((uintptr_t)workspace % kAlign) != 0))
     return POND_E_NOMEM;

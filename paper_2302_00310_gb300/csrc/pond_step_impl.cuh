@@ -110,22 +110,18 @@ template <typename R> Shape iter_shape(int D) {
   return make_shape<R, 2, 8, 8, 160, 1, true>(2);
 }
 
-// the multiscale f-lattice: the default tiles of each precision, 8x14 with
-// 128 threads and two CTAs per SM (FP64), 8x16 with 160 threads and two CTAs
-// per SM (mixed), 252 cells in 1D
+// the multiscale f-lattice: the default tile, 8x14 with 128 threads and two
+// CTAs per SM, 252 cells in 1D
 template <typename R> Shape ms_shape(int D) {
   if (D == 1) return make_shape<R, 1, 252, 1, 256, 1, false, 4, true>(1);
-  if constexpr (std::is_same<R, float>::value) return make_shape<R, 2, 8, 16, 160, 2, false, 4, true>(6);
-  else return make_shape<R, 2, 8, 14, 128, 2, false, 4, true>(10);
+  return make_shape<R, 2, 8, 14, 128, 2, false, 4, true>(10);
 }
 
-// g on the f-lattice (D1Q4 / D2Q16): the default tiles of each precision,
-// 8x14 with 128 threads and two CTAs per SM (FP64), 8x16 with 160 threads
-// and two CTAs per SM (mixed), 252 cells in 1D
+// g on the f-lattice (D1Q4 / D2Q16): the default tile, 8x14 with 128
+// threads and two CTAs per SM, 252 cells in 1D
 template <typename R> Shape g4_shape(int D) {
   if (D == 1) return make_shape<R, 1, 252, 1, 256, 1, false, 4, false, 4>(1);
-  if constexpr (std::is_same<R, float>::value) return make_shape<R, 2, 8, 16, 160, 2, false, 4, false, 4>(6);
-  else return make_shape<R, 2, 8, 14, 128, 2, false, 4, false, 4>(10);
+  return make_shape<R, 2, 8, 14, 128, 2, false, 4, false, 4>(10);
 }
 
 }  // namespace pond

@@ -87,7 +87,7 @@ def _params(**kw):
     (pond.POND_D2Q16, dict(g_same_as_f=1, multiscale=1)),
     (pond.POND_D2Q16, dict(g_same_as_f=1, flux_frame=pond.POND_FRAME_ITER)),
     (pond.POND_D2Q16, dict(g_same_as_f=1, tile=9)),
-    (pond.POND_D2Q16, dict(g_same_as_f=1, precision=pond.POND_FP32_MIXED, tile=10)),
+    (pond.POND_D2Q16, dict(g_same_as_f=1, precision=pond.POND_FP32_MIXED, tile=6)),
     (pond.POND_D1Q4, dict(g_same_as_f=2)),
 ])
 def test_multiscale_and_g_lattice_combinations_are_rejected_before_any_device_work(L, lat, kw):
@@ -113,8 +113,9 @@ def test_batch_tile_codes_are_resolved_before_any_device_work(L):
 
     no_gpu = not torch.cuda.is_available()
     for prec, tile, ok in ((pond.POND_FP64, 9, True), (pond.POND_FP64, 10, True),
-                           (pond.POND_FP64, 4, False), (pond.POND_FP32_MIXED, 6, True),
-                           (pond.POND_FP32_MIXED, 4, True), (pond.POND_FP32_MIXED, 9, False),
+                           (pond.POND_FP64, 4, False), (pond.POND_FP32_MIXED, 10, True),
+                           (pond.POND_FP32_MIXED, 6, True), (pond.POND_FP32_MIXED, 3, True),
+                           (pond.POND_FP32_MIXED, 4, False), (pond.POND_FP32_MIXED, 9, False),
                            (pond.POND_FP64, 0, True), (pond.POND_FP32_MIXED, 0, True)):
         t = pond.pond_tune_default()
         t.tile = tile

@@ -18,7 +18,7 @@ def torch():
 
 
 def _solo_tile(precision):
-    return 10 if precision == pond.POND_FP64 else 6  # pond_params.tile default in 2D
+    return 10  # pond_params.tile default in 2D
 
 
 @pytest.mark.parametrize("precision,autotune", [(pond.POND_FP32_MIXED, False), (pond.POND_FP64, False),

@@ -73,8 +73,8 @@ WORKLOAD = "2D periodic advected Gaussian pulse, D2Q16+D2Q9, 256x256, Mach 2 at 
 # thread instructions, packed FP32 pairs twice that, per launch / cells) and
 # dram__bytes_read.sum + dram__bytes_write.sum per launch.
 NCU_BY_DIGEST = {
-    "89078f2d12fb94a8046962d2144a336e0916c95942db0fbb4b3c08fba113c78c": {
-        "flops_fp64": 7727.0, "traffic_fp64": 15165000, "flops_fp32": 7251.0, "traffic_fp32": 9730000},
+    "65253e9ea940c71393a860a96064a771fb4cd1013b7a3d351acc7a6c1c68f7e2": {
+        "flops_fp64": 7727.0, "traffic_fp64": 15131400, "flops_fp32": 7780.5, "traffic_fp32": 9558300},
 }
 
 
@@ -449,6 +449,7 @@ def bench_d2q25(torch, pond, W, steps=100):
             sim.close()
     out["l1_rho_d2q25_vs_d2q16_fp64"] = _l1(rho[(5, "fp64")], rho[(4, "fp64")])
     out["l1_rho_fp32_vs_fp64_d2q25"] = _l1(rho[(5, "fp32_mixed")], rho[(5, "fp64")])
+    out["stated_l1_bound_fp32_vs_fp64"] = 3e-7
     return out
 
 
@@ -505,6 +506,7 @@ def bench_multiscale(torch, pond, W, steps=200, theta=0.05):
                                "nonphysical": bool(sim.flags()[1] & 1)}
         sim.close()
     out["l1_rho_appc_multiscale_fp32_vs_fp64"] = _l1(appc["fp32_mixed"][0], appc["fp64"][0])
+    out["stated_l1_bound_appc_fp32_vs_fp64"] = 1e-7
     left, right = (0.445, 0.698, 3.528), (0.5, 0.0, 0.571)
     lax = W.lax_1d(n=600)
     exact = solution(left, right, lax["x"], lax["t_end"])[0]
@@ -549,6 +551,8 @@ def bench_g_lattice(torch, pond, W, steps=100):
                 "value": n * steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / steps, "tile": sim.info()[2]}
             sim.close()
     out["l1_rho_g_d2q16_vs_g_d2q9_fp64"] = _l1(rho[(4, "fp64")], rho[(3, "fp64")])
+    out["l1_rho_fp32_vs_fp64_g_d2q16"] = _l1(rho[(4, "fp32_mixed")], rho[(4, "fp64")])
+    out["stated_l1_bound_fp32_vs_fp64"] = 3e-7
     return out
 
 
@@ -712,6 +716,7 @@ def bench_serve(pond, serve_mod, n_requests=200, rate=3.0):
     ex = serve_mod.PondExecutor(precision=pond.POND_FP32_MIXED, capacity=64, graph_steps=8)
     srv = serve_mod.Server(ex, budget_bytes=16 << 30, tick_steps=64)
     out = srv.run(reqs)
+    tile_2d = ex.batches[2].info()[0]
     ex.close()
     s = serve_mod.summary(out)
     s.update({"workload": "Poisson stream at %g req/s: D1Q4 Sod-type tubes (256-8192 cells) and "
@@ -720,7 +725,7 @@ def bench_serve(pond, serve_mod, n_requests=200, rate=3.0):
               "sample": "%d requests (%d 2D), every one finished" % (
                   n_requests, sum(1 for r in out if r.dim == 2)),
               "rate": rate, "budget_gb": 16 << 30 >> 30, "peak_resident_gb": srv.peak_bytes / 1e9,
-              "ticks": srv.ticks, "tick_steps": 64})
+              "ticks": srv.ticks, "tick_steps": 64, "tile_2d_at_end": tile_2d})
     return s
 
 
@@ -732,11 +737,12 @@ def bench_serve_offered(pond, serve_mod, n_requests=400, rate=200.0, wall_s=30.0
     ex = serve_mod.PondExecutor(precision=pond.POND_FP32_MIXED, capacity=64, graph_steps=8)
     srv = serve_mod.Server(ex, budget_bytes=16 << 30, tick_steps=64)
     out = srv.run(reqs, wall_limit=wall_s)
+    tile_2d = ex.batches[2].info()[0]
     ex.close()
     s = serve_mod.summary(out, makespan=srv.stopped_at)
     s.update({"workload": "the C5 mix offered at %g req/s (%d requests drawn), served for %g s of "
                           "wall time, FP32-mixed" % (rate, n_requests, wall_s),
-              "wall_limit_s": wall_s, "stopped_at_s": srv.stopped_at,
+              "wall_limit_s": wall_s, "stopped_at_s": srv.stopped_at, "tile_2d_at_end": tile_2d,
               "note": "p50/p99 over the requests finished within the wall time; the rest are "
                       "counted as running, queued or not yet arrived"})
     return s
@@ -775,7 +781,11 @@ def run_gpu(args, dist, rank, ws):
     torch.cuda.set_device(local)
     pond.lib(build=True)
     if args.extra:
-        if rank == 0:
+        if rank == 0 and args.extra == "serve":
+            res = {"serve": bench_serve(pond, serve_mod), "serve_offered": bench_serve_offered(pond, serve_mod),
+                   "serve_sweep": bench_serve_sweep(pond, serve_mod)}
+            print(json.dumps(dict(extra=args.extra, **res)), flush=True)
+        elif rank == 0:
             fn = {"riemann": bench_riemann, "d2q25": bench_d2q25, "multiscale": bench_multiscale,
                   "g_lattice": bench_g_lattice}[args.extra]
             print(json.dumps(dict(extra=args.extra, **fn(torch, pond, W))), flush=True)
@@ -907,7 +917,7 @@ def main():
                     help="skip the accuracy studies (iterated face frame, thermal Couette)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
                     help="arithmetic of the main line (fp32 = the mixed path)")
-    ap.add_argument("--extra", default=None, choices=["riemann", "d2q25", "multiscale", "g_lattice"],
+    ap.add_argument("--extra", default=None, choices=["riemann", "d2q25", "multiscale", "g_lattice", "serve"],
                     help="run only this one extra measurement and print its JSON line (for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:

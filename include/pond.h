@@ -300,8 +300,9 @@ int pond_abi_version(void);
  * autotuner times candidate shapes on the run's own steps: the first
  * pond_batch_step() call in which every member takes at least graph_steps x
  * (number of shapes) steps runs one chunk with each shape and keeps the
- * fastest.  A fixed tile equal to the contexts' own keeps results bit for bit
- * identical to solo runs.
+ * fastest, and times them again at the first such call after the stepping
+ * members' tiles have grown or shrunk fourfold since.  A fixed tile equal to
+ * the contexts' own keeps results bit for bit identical to solo runs.
  *
  * Members must share the batch's dimension, precision and stream, must be
  * initialised, may not use the iterated face frame, and use D1Q4 or D2Q16.  A context belongs

@@ -67,6 +67,8 @@ struct pond_batch {
   int grid;
   int sms;
   bool tuned;
+  bool autotuning;             // the autotuner picks the shape (tile 0, autotune on)
+  long long tuned_tiles;       // tiles (first candidate's shape) the shape was tuned on
   double tuned_mlups;
   unsigned char *dtable;
   size_t desc_bytes, table_bytes;
@@ -242,6 +244,8 @@ pond_status pond_batch_create(pond_batch **out, int32_t dim, int32_t precision, 
     if (b->shape < 0) { delete b; return POND_E_INVAL; }
   }
   b->tuned = t.tile != 0 || !t.autotune || b->shapes.size() == 1;
+  b->autotuning = !b->tuned;
+  b->tuned_tiles = 0;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
@@ -328,7 +332,16 @@ pond_status pond_batch_step(pond_batch *b, const int64_t *steps) {
   size_t cells;
   int launches;
   // autotune: one full chunk per candidate shape, on real steps (every shape
-  // gives the same result), timed with events; then the fastest is kept
+  // gives the same result), timed with events; then the fastest is kept until
+  // the batch's work (its stepping members' tiles) has grown or shrunk
+  // fourfold since, when the shapes are timed again (a serving batch is often
+  // tuned on its first, small member)
+  long long cur_tiles = 0;
+  for (size_t i = 0; i < n; ++i)
+    if (left[i] > 0) cur_tiles += tiles_of(b->members[i], b->shapes[0]);
+  if (b->autotuning && b->tuned && cur_tiles > 0 &&
+      (cur_tiles > 4 * b->tuned_tiles || 4 * cur_tiles < b->tuned_tiles))
+    b->tuned = false;
   if (!b->tuned) {
     int64_t mn = INT64_MAX;
     for (size_t i = 0; i < n; ++i) mn = std::min(mn, left[i]);
@@ -353,6 +366,7 @@ pond_status pond_batch_step(pond_batch *b, const int64_t *steps) {
       }
       for (auto &e : ev) cudaEventDestroy(e);
       b->tuned = true;
+      b->tuned_tiles = cur_tiles;
       b->tuned_mlups = best;
     }
   }

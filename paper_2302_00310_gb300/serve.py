@@ -47,6 +47,7 @@ class Request:
     status: str = "pending"  # pending, queued, running, done, rejected
     result: object = None
     flags: int = 0
+    steps_done: int = 0      # steps advanced (all of them once done)
 
     def __post_init__(self):
         self.cells = int(self.cfg["nx"]) * int(self.cfg["ny"] if self.dim == 2 else 1)
@@ -89,6 +90,7 @@ class Server:
             if wall_limit is not None and now >= wall_limit:
                 self.stopped_at = now
                 for r, h, _ in active:
+                    r.steps_done = r.steps - self.ex.remaining(h)
                     self.ex.abandon(h)
                 break
             while pending and pending[0].arrival <= now:
@@ -124,6 +126,7 @@ class Server:
                     r.result, r.flags = self.ex.harvest(h)
                     r.finish_t = self.clock() - t0
                     r.status = "done"
+                    r.steps_done = r.steps
                     used -= need
                 else:
                     still.append((r, h, need))
@@ -133,12 +136,15 @@ class Server:
 
 def summary(reqs, makespan: float | None = None):
     """p50/p99 time to solution (s) of the finished requests, aggregate MLUPS
-    over the run (finished work over the makespan), counts by status."""
+    over the run (finished work over the makespan; with the steps advanced by
+    requests still running when a wall-time limit stopped the run, in
+    ``mlups_all_work``), counts by status."""
     done = [r for r in reqs if r.status == "done"]
     lat = np.array([r.latency for r in done]) if done else np.zeros(0)
     if makespan is None:
         makespan = max((r.finish_t for r in done), default=0.0) - min((r.arrival for r in reqs), default=0.0)
     work = sum(r.cells * r.steps for r in done)
+    all_work = work + sum(r.cells * r.steps_done for r in reqs if r.status == "running")
     return {
         "requests": len(reqs), "done": len(done),
         "rejected": sum(1 for r in reqs if r.status == "rejected"),
@@ -150,6 +156,7 @@ def summary(reqs, makespan: float | None = None):
         "mean_s": float(lat.mean()) if len(lat) else None,
         "makespan_s": float(makespan),
         "mlups": work / makespan / 1e6 if makespan > 0 else None,
+        "mlups_all_work": all_work / makespan / 1e6 if makespan > 0 else None,
         "cell_updates": int(work),
         "nonphysical": sum(1 for r in done if r.flags & pond.POND_FLAG_NONPHYSICAL),
     }

@@ -123,6 +123,38 @@ def test_autotuner_times_real_steps(torch, precision):
             assert np.max(np.abs(x - y)) <= tol * max(np.max(np.abs(y)), 1e-300)
 
 
+def test_autotuner_times_the_shapes_again_when_the_batch_grows(torch):
+    """A batch tuned on one small member times the candidate shapes again
+    once its stepping members' tiles have grown fourfold (a new measured
+    rate), and the states stay the solo states to the mixed path's step
+    bound."""
+    probs = _problems(2, [32] + [96] * 6, 110, pond.POND_FP32_MIXED)
+    tune = pond.pond_tune_default()
+    tune.graph_steps = 4
+    b = pond.Batch(2, pond.POND_FP32_MIXED, 8, tune)
+    sims = []
+    for cfg, prim in probs:
+        s = pond.Sim(cfg, stream=b.stream)
+        s.init(*prim)
+        sims.append(s)
+    b.add(sims[0])
+    b.step([12])
+    first = b.info()
+    for s in sims[1:]:
+        b.add(s)
+    b.step([12] * len(sims))
+    second = b.info()
+    got = [s.get_state() for s in sims]
+    b.close()
+    for s in sims:
+        s.close()
+    assert first[2] and second[2] and second[3] != first[3], (first, second)
+    ref = _solo(probs, [24] + [12] * 6)
+    for a, r in zip(got, ref):
+        for x, y in zip(a, r):
+            assert np.max(np.abs(x - y)) <= 2e-6 * max(np.max(np.abs(y)), 1e-300)
+
+
 def test_members_join_and_leave_between_calls(torch):
     probs = _problems(2, [24, 31, 40], 100, pond.POND_FP32_MIXED)
     tune = pond.pond_tune_default()

@@ -167,3 +167,8 @@ def test_wall_limit_stops_and_reports_the_queue():
     assert s["done"] + s["running"] + s["queued"] + s["not_arrived"] == 40
     assert not ex.active  # nothing left on the device
     assert sum(1 for e in ex.log if e[0] == "abandon") == 2
+    # the running requests' steps count in mlups_all_work, not in mlups
+    running = [r for r in out if r.status == "running"]
+    assert all(0 < r.steps_done < r.steps for r in running)
+    partial = sum(r.cells * r.steps_done for r in running)
+    assert abs(s["mlups_all_work"] - s["mlups"] - partial / s["makespan_s"] / 1e6) < 1e-9 * s["mlups_all_work"]

@@ -67,13 +67,13 @@ if ROOT not in sys.path:
 METRIC = "MLUPS per GB300 (FP32 batched vs FP64 plain, stated L1 err); serve p50/p99 latency"
 UNIT = "MLUPS"
 WORKLOAD = "2D periodic advected Gaussian pulse, D2Q16+D2Q9, 256x256, Mach 2 at 30 deg, FP64, BGK"
-# ncu counters of one main-line step launch, keyed by the source digest of
-# the build they were taken on (profiles/ holds the captures; a changed
-# source gives None): executed flops per cell update (2 FMA + ADD + MUL
+# ncu counters of one main-line step launch, keyed by the digest of the step
+# kernels' sources and flags they were taken on (build.kernel_digest;
+# profiles/ holds the captures; a changed kernel gives None): executed flops per cell update (2 FMA + ADD + MUL
 # thread instructions, packed FP32 pairs twice that, per launch / cells) and
 # dram__bytes_read.sum + dram__bytes_write.sum per launch.
 NCU_BY_DIGEST = {
-    "65253e9ea940c71393a860a96064a771fb4cd1013b7a3d351acc7a6c1c68f7e2": {
+    "5b88772059b29acd62a237bdf1e8a0d0cf6ca8f4b9e1c09e8b993a760c204778": {
         "flops_fp64": 7727.0, "traffic_fp64": 15131400, "flops_fp32": 7780.5, "traffic_fp32": 9558300},
 }
 
@@ -141,7 +141,7 @@ KERNEL_FP32 = "member_step_kernel<float, 2, 4, 8, 14, 128, 2, 0, 0, 3>"
 def _build_digest():
     from paper_2302_00310_gb300 import build as B
 
-    return B._digest()
+    return B.kernel_digest()
 
 
 def _measured_peaks():

@@ -41,6 +41,24 @@ def _digest() -> str:
     return h.hexdigest()
 
 
+# the sources that make the 2D/1D step kernels of the two main translation
+# units (D2Q16 f, D2Q9 g): their machine code changes only with these files
+# or the flags (the batch, ABI and check sources around them do not enter it)
+KERNEL_SOURCES = ("pond_hermite.cuh", "pond_packed.cuh", "pond_kernels.cuh", "pond_launch.h",
+                  "pond_step_impl.cuh", "pond_step_fp64.cu", "pond_step_fp32.cu")
+
+
+def kernel_digest() -> str:
+    """Digest of the step kernels' sources and flags, the key under which
+    counters taken on one build stay valid for another."""
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(CSRC, name), "rb") as fh:
+            h.update(name.encode() + fh.read())
+    h.update(" ".join(ARCH + [f for f in FLAGS if f not in (INCLUDE, CSRC)]).encode())
+    return h.hexdigest()
+
+
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
     """Compile every ``csrc/*.cu`` for sm_103a and link ``libpond_gb300.so``."""
     stamp = os.path.join(BUILD, "stamp")

@@ -485,6 +485,23 @@ def bench_multiscale(torch, pond, W, steps=200, theta=0.05):
             out[name]["high_fraction"] = sim.ms_stats() / (n * steps)
         sim.close()
     out["l1_rho_multiscale_vs_d2q16"] = _l1(mom["multiscale"][0], mom["d2q16"][0])
+    # the mixed path with the main flux form (a low cell's energy flux in its own frame)
+    sim = pond.Sim(dict(w["cfg"], precision=pond.POND_FP32_MIXED, ms=1, ms_theta_u=theta, ms_theta_T=theta))
+    sim.init(*fields)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(sim.stream):
+        e0.record(sim.stream)
+        pond.pond_step(sim.ctx, steps)
+        e1.record(sim.stream)
+    sim.stream.synchronize()
+    ms = e0.elapsed_time(e1)
+    rho32 = sim.moments()[0]
+    out["multiscale_fp32_mixed"] = {"value": n * steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / steps,
+                                    "tile": sim.info()[2], "high_fraction": sim.ms_stats() / (n * steps),
+                                    "nonphysical": bool(sim.flags()[1] & 1)}
+    sim.close()
+    out["l1_rho_multiscale_fp32_vs_fp64"] = _l1(rho32, mom["multiscale"][0])
+    out["stated_l1_bound_multiscale_fp32_vs_fp64"] = 1e-7
     # the mixed path runs the multiscale lattice in Appendix C's flux form: both precisions in it,
     # beside the mixed D2Q16 kernel in the same form
     appc = {}

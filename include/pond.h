@@ -158,12 +158,12 @@ typedef struct {
    * third-order content its lattice resolves; a wall ghost takes the lattice
    * of the cell it reflects (a low one drops its Chapman-Enskog content of
    * order 3 along an axis).  Requires D1Q4 / D2Q16, the averaged face frame
-   * and tile 0 (or the precision's default: 1 in 1D; 10 FP64,
-   * 6 mixed in 2D); not batched.  With the main flux form a low cell keeps
-   * mass and momentum but not energy exactly (its lattice lacks the
-   * third-order moment the energy flux needs in another frame); Appendix C's
-   * form keeps all three, and the mixed path, whose conserved fluxes are
-   * evaluated once per face in the face frame, requires it. */
+   * and tile 0 (or the default: 1 in 1D, 10 in 2D); not batched.  With the
+   * main flux form a low cell keeps mass and momentum but not energy exactly
+   * (its lattice lacks the third-order moment the energy flux needs in
+   * another frame: the mixed path, whose conserved fluxes are otherwise
+   * evaluated once per face, adds a low cell's energy flux in the cell's own
+   * frame, as the FP64 path does); Appendix C's form keeps all three. */
   int32_t multiscale;
   double ms_theta_u;       /* thresholds on s_u and s_T (the paper states none) */
   double ms_theta_T;

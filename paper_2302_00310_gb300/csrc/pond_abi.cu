@@ -249,9 +249,8 @@ bool valid_params(const pond_params *p) {
   if (p->strip < 0 || p->strip > 8) return false;
   if (p->multiscale != 0 && p->multiscale != 1) return false;
   if (p->g_same_as_f != 0 && p->g_same_as_f != 1) return false;
-  if (p->multiscale) {  // D1Q3/D1Q4 and D2Q9/D2Q16, averaged frame; mixed: App. C form
+  if (p->multiscale) {  // D1Q3/D1Q4 and D2Q9/D2Q16, averaged frame
     if (p->flux_frame != POND_FRAME_AVG) return false;
-    if (p->precision == POND_FP32_MIXED && p->flux_form != POND_FLUX_APPC) return false;
     if (std::isnan(p->ms_theta_u) || std::isnan(p->ms_theta_T)) return false;
   }
   return true;

@@ -1265,17 +1265,20 @@ __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int N
     // (Eq. eq:Mcondition), so the face frame gives the same values as the cell
     // frames of Eq. fluxEq.  C = dimensional coefficients of v_n phi (low
     // orders): x H_k = H_{k+1} + k T_F H_{k-1} along the normal.
+    // (A multiscale face of two low cells has no order-3 coefficient along
+    // the normal: H_3 vanishes on the D1Q3 nodes.  Its energy flux is not
+    // used with the main flux form: a low cell takes its own frame's value.)
     const R un = DIRN == 0 ? uFx : uFy;
+    R b3 = R(0);
+    if constexpr (QL > 3) b3 = DIRN == 0 ? Fb.v[3][0] : Fb.v[0][DIM == 2 ? 3 : 0];
     R C00, C10, C01 = R(0), C20, C02 = R(0), CG;
     if (K.appc) {  // Fb, Gb already hold v_n phi
       C00 = Fb.v[0][0]; C10 = Fb.v[1][0]; C20 = Fb.v[2][0]; CG = Gb.v[0][0];
       if constexpr (DIM == 2) { C01 = Fb.v[0][1]; C02 = Fb.v[0][2]; }
-    } else if constexpr (QL < 4) {
-      C00 = C10 = C20 = CG = R(0);  // not reached: a multiscale mixed path runs Appendix C's form
     } else if constexpr (DIRN == 0) {
       C00 = fma(un, Fb.v[0][0], Fb.v[1][0]);
       C10 = fma(un, Fb.v[1][0], fma(TF, Fb.v[0][0], Fb.v[2][0]));
-      C20 = fma(un, Fb.v[2][0], fma(TF + TF, Fb.v[1][0], Fb.v[3][0]));
+      C20 = fma(un, Fb.v[2][0], fma(TF + TF, Fb.v[1][0], b3));
       CG = fma(un, Gb.v[0][0], Gb.v[1][0]);
       if constexpr (DIM == 2) {
         C01 = fma(un, Fb.v[0][1], Fb.v[1][1]);
@@ -1284,7 +1287,7 @@ __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int N
     } else {
       C00 = fma(un, Fb.v[0][0], Fb.v[0][1]);
       C01 = fma(un, Fb.v[0][1], fma(TF, Fb.v[0][0], Fb.v[0][2]));
-      C02 = fma(un, Fb.v[0][2], fma(TF + TF, Fb.v[0][1], Fb.v[0][3]));
+      C02 = fma(un, Fb.v[0][2], fma(TF + TF, Fb.v[0][1], b3));
       C10 = fma(un, Fb.v[1][0], Fb.v[1][1]);
       C20 = fma(un, Fb.v[2][0], Fb.v[2][1]);
       CG = fma(un, Gb.v[0][0], Gb.v[0][1]);
@@ -1502,7 +1505,24 @@ __device__ __forceinline__ void add_faces(const StepConst &K, const R *fp, int N
       if (DIM == 1 && j == 2) continue;
       const double d = (double)fp[(D::FJ + j) * NFACES + fhi] - (double)fp[(D::FJ + j) * NFACES + flo];
       double &m = j == 0 ? M.r : (j == 1 ? M.jx : (j == 2 ? M.jy : M.e));
+      if (MS && j == 3 && low && !K.appc) continue;
       m = fma(-K.lam, d, m);
+    }
+    if constexpr (MS) {
+      // A low cell with the main flux form: its lattice lacks the third-order
+      // moment along the normal that the energy flux takes in another frame,
+      // so its energy changes by the cell-frame moment of the projected
+      // v_n phi (the FP64 path's and the oracle's value), not the face's:
+      // with v = u + x, sum |v|^2/2 v_n phi = (|u|^2 X_0 + 2 u . X_1 +
+      // D T X_0 + X_2x + X_2y) / 2, plus sum v_n g = Y_0.
+      if (low && !K.appc) {
+        const double dux = ux, duy = DIM == 2 ? (double)uy : 0.0, dT = T;
+        const double X0 = DX.v[0][0], X1x = DX.v[1][0], X2x = DX.v[2][0];
+        const double X1y = DIM == 2 ? (double)DX.v[0][1] : 0.0, X2y = DIM == 2 ? (double)DX.v[0][2] : 0.0;
+        const double e = 0.5 * ((dux * dux + duy * duy + DIM * dT) * X0 + 2.0 * (dux * X1x + duy * X1y) +
+                                X2x + X2y) + (double)DY.v[0][0];
+        M.e = fma(-K.lam, e, M.e);
+      }
     }
   }
 }

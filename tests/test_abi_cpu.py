@@ -79,7 +79,6 @@ def _params(**kw):
     (pond.POND_D2Q16, dict(multiscale=1, flux_frame=pond.POND_FRAME_ITER)),
     (pond.POND_D2Q25, dict(multiscale=1)),
     (pond.POND_D2Q16, dict(multiscale=1, tile=6)),
-    (pond.POND_D2Q16, dict(multiscale=1, precision=pond.POND_FP32_MIXED)),
     (pond.POND_D2Q16, dict(multiscale=2)),
     (pond.POND_D2Q16, dict(multiscale=1, ms_theta_u=float("nan"))),
     # g on the f-lattice: no D2Q25, no multiscale, averaged frame, the precision's tile

@@ -110,25 +110,32 @@ def test_multiscale_matches_oracle(case):
 
 
 MIXED_CASES = [
-    # D, nx, ny, bc, limiter, grad_k, steps, other options (Appendix C's flux form)
+    # D, nx, ny, bc, limiter, grad_k, steps, other options (default: Appendix C's flux form)
     (2, 37, 30, (0, 0, 0, 0), 0, 0, 3, {}),
     (2, 29, 33, (1, 1, 2, 1), 1, 1, 2, {}),
     (1, 300, 1, (1, 1, 0, 0), 0, 0, 3, {}),
     (2, 31, 27, (0, 0, 3, 3), 0, 0, 2, dict(prandtl=0.71, inflow=WALLS_2D)),
+    # the main flux form: a low cell's energy flux in its own frame
+    (2, 37, 30, (0, 0, 0, 0), 0, 0, 3, dict(flux_appc=0)),
+    (2, 29, 33, (1, 1, 2, 1), 1, 1, 2, dict(flux_appc=0, prandtl=0.71)),
+    (1, 300, 1, (1, 1, 0, 0), 0, 0, 3, dict(flux_appc=0)),
+    (1, 120, 1, (3, 3, 0, 0), 1, 0, 3, dict(flux_appc=0, prandtl=0.71, inflow=WALLS_1D)),
+    (2, 31, 27, (0, 0, 3, 3), 0, 0, 2, dict(flux_appc=0, prandtl=0.71, inflow=WALLS_2D)),
 ]
 
 
 @pytest.mark.parametrize("case", range(len(MIXED_CASES)))
 def test_multiscale_mixed_path(case):
-    """The mixed path with the multiscale f-lattice (Appendix C's form): the
-    oracle's moments within the step bound 2e-6 and its count of high-lattice
-    cell updates (thresholds clear of the measures by far more than FP32
-    rounding)."""
+    """The mixed path with the multiscale f-lattice, in Appendix C's form and
+    in the main flux form (a low cell's energy flux taken in its own frame):
+    the oracle's moments within the step bound 2e-6 and its count of
+    high-lattice cell updates (thresholds clear of the measures by far more
+    than FP32 rounding)."""
     D, nx, ny, bc, lim, gk, steps, extra = MIXED_CASES[case]
     walls = 3 in bc
     fields = W.random_state_grid(D, nx, ny, seed=190 + case, mach=0.8, T=(0.7, 1.4) if walls else (0.5, 2.0))
-    cfg = W._base(D, nx, ny, tau=5e-3, dx=1.0 / nx, limiter=lim, grad_k=gk, flux_appc=1, bc=bc,
-                  **dict(dict(inflow=INFLOW), **extra))
+    cfg = W._base(D, nx, ny, tau=5e-3, dx=1.0 / nx, limiter=lim, grad_k=gk, bc=bc,
+                  **dict(dict(inflow=INFLOW, flux_appc=1), **extra))
     cfg["dt"] = W.dt_from_cfl(fields[1], fields[2], fields[3], cfg["dx"], 0.4)
     thu, thT = _thresholds(cfg, fields, steps, min_gap=1e-4)
     cfg = dict(cfg, ms=1, ms_theta_u=thu, ms_theta_T=thT)
@@ -196,8 +203,7 @@ def test_lax_tube_on_the_gpu():
     assert abs(high - ost.report["ms_high"]) <= 1e-3 * ost.report["ms_high"]
 
 
-@pytest.mark.parametrize("bad", [dict(precision=pond.POND_FP32_MIXED, flux_appc=0), dict(iterative=1),
-                                 dict(tile=6), dict(qf=5)])
+@pytest.mark.parametrize("bad", [dict(iterative=1), dict(tile=6), dict(qf=5)])
 def test_multiscale_rejects_what_it_does_not_cover(bad):
     fields = W.random_state_grid(2, 16, 16, seed=1)
     cfg = W._base(2, 16, 16, tau=5e-3, dx=1.0 / 16, inflow=((0.0, 0.1, 0.0, 1.0),) * 4)

@@ -73,8 +73,8 @@ WORKLOAD = "2D periodic advected Gaussian pulse, D2Q16+D2Q9, 256x256, Mach 2 at 
 # thread instructions, packed FP32 pairs twice that, per launch / cells) and
 # dram__bytes_read.sum + dram__bytes_write.sum per launch.
 NCU_BY_DIGEST = {
-    "5b88772059b29acd62a237bdf1e8a0d0cf6ca8f4b9e1c09e8b993a760c204778": {
-        "flops_fp64": 7727.0, "traffic_fp64": 15131400, "flops_fp32": 7780.5, "traffic_fp32": 9558300},
+    "7e1abe049e2e4e36ac357dd8f324117f9bc156e3477ae36cfa49fa1415c6abe6": {
+        "flops_fp64": 7727.0, "traffic_fp64": 15133440, "flops_fp32": 7780.5, "traffic_fp32": 9558400},
 }
 
 

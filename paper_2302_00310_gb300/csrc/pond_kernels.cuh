@@ -33,6 +33,14 @@
 namespace pond {
 
 enum { BC_PERIODIC = 0, BC_ZERO_GRADIENT = 1, BC_INFLOW = 2, BC_WALL = 3 };
+
+// A tile's halo stride and face count as a type: the stencil and face
+// functions take either this (the step kernels: the shared-memory offsets
+// become immediates, also inside the mixed path's out-of-line calls, which
+// are then instantiated per tile shape) or a plain int.
+template <int V> struct CInt {
+  __device__ constexpr operator int() const { return V; }
+};
 enum { LIM_VANLEER = 0, LIM_MINMOD = 1 };
 enum { FLAG_NONPHYSICAL = 1u, FLAG_CFL = 2u, FLAG_NOCONV = 4u };
 
@@ -576,8 +584,8 @@ __device__ __forceinline__ void prep_cell(const StepConst &K, const State<R> &S,
 // QG1, the g-lattice's nodes per axis); Q: the lattice the face works on (a
 // multiscale face with the low-order f-lattice reads the f coefficients of
 // order <= 2 per axis: the projection).
-template <typename R, int DIM, int QF1, int Q, int GS, int QG1>
-__device__ __forceinline__ void stencil_pops_body(const StepConst &K, const R *sp, int NH, int h, R uFx,
+template <typename R, int DIM, int QF1, int Q, int GS, int QG1, typename NHT>
+__device__ __forceinline__ void stencil_pops_body(const StepConst &K, const R *sp, NHT NH, int h, R uFx,
                                                   R uFy, R TF, R sTF, const SynK<R, Q> &SK,
                                                   Blk<R, Q, (DIM == 2 ? Q : 1)> &Y) {
   using D = Dims<DIM, QF1, QG1>;
@@ -598,16 +606,16 @@ __device__ __forceinline__ void stencil_pops_body(const StepConst &K, const R *s
 // lattice (16 call sites per face direction): the FP32 kernel is bound by
 // instruction fetch, not arithmetic, and the shared copy keeps its code
 // footprint small.  The FP64 kernel, bound by the FP64 pipe, inlines it.
-template <typename R, int DIM, int QF1, int Q, int GS, int QG1>
+template <typename R, int DIM, int QF1, int Q, int GS, int QG1, typename NHT>
 __device__ __noinline__ Blk<R, Q, (DIM == 2 ? Q : 1)> stencil_pops_call(const StepConst &K, const R *sp,
-                                                                      int NH, int h, R uFx, R uFy,
+                                                                      NHT NH, int h, R uFx, R uFy,
                                                                       R TF, R sTF, SynK<R, Q> SK) {
   Blk<R, Q, (DIM == 2 ? Q : 1)> Y;  // returned by value: in registers, not through local memory
   stencil_pops_body<R, DIM, QF1, Q, GS, QG1>(K, sp, NH, h, uFx, uFy, TF, sTF, SK, Y);
   return Y;
 }
-template <typename R, int DIM, int QF1, int Q, int GS, int QG1>
-__device__ __forceinline__ void stencil_pops(const StepConst &K, const R *sp, int NH, int h, R uFx,
+template <typename R, int DIM, int QF1, int Q, int GS, int QG1, typename NHT>
+__device__ __forceinline__ void stencil_pops(const StepConst &K, const R *sp, NHT NH, int h, R uFx,
                                              R uFy, R TF, R sTF, const SynK<R, Q> &SK,
                                              Blk<R, Q, (DIM == 2 ? Q : 1)> &Y) {
   if constexpr (is_mixed<R>())
@@ -624,8 +632,8 @@ __device__ __forceinline__ void stencil_pops(const StepConst &K, const R *sp, in
 template <typename R, int DIM, int Q> struct TwoBlk {
   Blk<R, Q, (DIM == 2 ? Q : 1)> L, R_;
 };
-template <int DIM, int QF1, int Q, int GS, int QG1>
-__device__ __forceinline__ TwoBlk<float, DIM, Q> stencil_two_body(const StepConst &K, const float *sp, int NH,
+template <int DIM, int QF1, int Q, int GS, int QG1, typename NHT>
+__device__ __forceinline__ TwoBlk<float, DIM, Q> stencil_two_body(const StepConst &K, const float *sp, NHT NH,
                                                                  int hL, int hR, float uFx, float uFy, float TF,
                                                                  float sTF, const SynK<float, Q> &SK) {
   using D = Dims<DIM, QF1, QG1>;
@@ -666,8 +674,8 @@ __device__ __forceinline__ TwoBlk<float, DIM, Q> stencil_two_body(const StepCons
     }
   return out;
 }
-template <int DIM, int QF1, int Q, int GS, int QG1>
-__device__ __noinline__ TwoBlk<float, DIM, Q> stencil_two_call(const StepConst &K, const float *sp, int NH,
+template <int DIM, int QF1, int Q, int GS, int QG1, typename NHT>
+__device__ __noinline__ TwoBlk<float, DIM, Q> stencil_two_call(const StepConst &K, const float *sp, NHT NH,
                                                               int hL, int hR, float uFx, float uFy, float TF,
                                                               float sTF, SynK<float, Q> SK) {
   return stencil_two_body<DIM, QF1, Q, GS, QG1>(K, sp, NH, hL, hR, uFx, uFy, TF, sTF, SK);
@@ -706,8 +714,8 @@ __device__ __noinline__ Blk<R, Q, (DIM == 2 ? Q : 1)> stencil_pair_full(const St
     }
   return YA;
 }
-template <typename R, int DIM, int QF1, int Q, int GS, int QG1, int DIRN>
-__device__ __forceinline__ void stencil_pair_body(const StepConst &K, const R *sp, int NH, int hA, int hB,
+template <typename R, int DIM, int QF1, int Q, int GS, int QG1, int DIRN, typename NHT>
+__device__ __forceinline__ void stencil_pair_body(const StepConst &K, const R *sp, NHT NH, int hA, int hB,
                                                   unsigned upm, R uFx, R uFy, R TF, R sTF,
                                                   const SynK<R, Q> &SK, Blk<R, Q, (DIM == 2 ? Q : 1)> &Y) {
   if constexpr (DIM == 1) {  // no tangential axis: both cells in full, in line
@@ -813,17 +821,17 @@ __device__ __forceinline__ void stencil_pair_body(const StepConst &K, const R *s
     }
   }
 }
-template <typename R, int DIM, int QF1, int Q, int GS, int QG1, int DIRN>
+template <typename R, int DIM, int QF1, int Q, int GS, int QG1, int DIRN, typename NHT>
 __device__ __noinline__ Blk<R, Q, (DIM == 2 ? Q : 1)> stencil_pair_call(const StepConst &K, const R *sp,
-                                                                      int NH, int hA, int hB,
+                                                                      NHT NH, int hA, int hB,
                                                                       unsigned upm, R uFx, R uFy, R TF,
                                                                       R sTF, SynK<R, Q> SK) {
   Blk<R, Q, (DIM == 2 ? Q : 1)> Y;
   stencil_pair_body<R, DIM, QF1, Q, GS, QG1, DIRN>(K, sp, NH, hA, hB, upm, uFx, uFy, TF, sTF, SK, Y);
   return Y;
 }
-template <typename R, int DIM, int QF1, int Q, int GS, int QG1, int DIRN>
-__device__ __forceinline__ void stencil_pair(const StepConst &K, const R *sp, int NH, int hA, int hB,
+template <typename R, int DIM, int QF1, int Q, int GS, int QG1, int DIRN, typename NHT>
+__device__ __forceinline__ void stencil_pair(const StepConst &K, const R *sp, NHT NH, int hA, int hB,
                                              unsigned upm, R uFx, R uFy, R TF, R sTF, const SynK<R, Q> &SK,
                                              Blk<R, Q, (DIM == 2 ? Q : 1)> &Y) {
   if constexpr (is_mixed<R>())
@@ -972,8 +980,8 @@ __device__ __noinline__ Row<R, (DIM == 2 ? Q : 1)> zero_node_left(
 // run reconstruct_tie out of line).  The zero node at v_n = 0 (u_F,n = 0
 // exactly) takes the mean of its two one-sided traces here: the right/upper
 // one in line, the left/lower one from zero_node_left.
-template <typename R, int DIM, int QF1, int DIRN, int Q, int TIE, int GS, int QG1>
-__device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, int NH, const int *st,
+template <typename R, int DIM, int QF1, int DIRN, int Q, int TIE, int GS, int QG1, typename NHT>
+__device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, NHT NH, const int *st,
                                             R uFx, R uFy, R TF, R sTF, R isTF,
                                             Blk<R, Q, (DIM == 2 ? Q : 1)> &out) {
   if constexpr (TIE == 2) {
@@ -1114,8 +1122,9 @@ __device__ __forceinline__ R gauss_he4(R mu, R dT) {
 // QL: the f-lattice of the face, QF1 or (a multiscale face whose two cells
 // are both on the low-order lattice) 3; the face record keeps the storage
 // layout of QF1, with zero coefficients beyond QL.
-template <typename R, int DIM, int QF1, int DIRN, bool ITER, bool TIE = false, int QL = QF1, int QG1 = 3>
-__device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int NH, const int *st,
+template <typename R, int DIM, int QF1, int DIRN, bool ITER, bool TIE = false, int QL = QF1, int QG1 = 3,
+          typename NHT = int>
+__device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, NHT NH, const int *st,
                                           R *fp, int NFACES, int fidx, int &ntrace);
 
 // does a node of either lattice other than an odd lattice's zero node have
@@ -1141,8 +1150,8 @@ __device__ __noinline__ bool face_flux_tie(const StepConst &K, const R *sp, int 
   return face_flux<R, DIM, QF1, DIRN, false, true, QL, QG1>(K, sp, NH, st, fp, NFACES, fidx, ntrace);
 }
 
-template <typename R, int DIM, int QF1, int DIRN, bool ITER, bool TIE, int QL, int QG1>
-__device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, int NH, const int *st,
+template <typename R, int DIM, int QF1, int DIRN, bool ITER, bool TIE, int QL, int QG1, typename NHT>
+__device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, NHT NH, const int *st,
                                           R *fp, int NFACES, int fidx, int &ntrace) {
   static_assert(QL >= QG1, "the equilibrium's Gaussian moments are built to the f-lattice's order");
   using D = Dims<DIM, QF1, QG1>;
@@ -1385,9 +1394,9 @@ __device__ __forceinline__ void face_contrib(const StepConst &K, const R *fp, in
 // frame's shift, the same arithmetic as face_contrib_body), and returns their
 // difference, upper minus lower.  A face whose transformation must run in
 // FP64 takes both faces through face_contrib_body instead.
-template <int DIM, int QF1, int QG1>
+template <int DIM, int QF1, int QG1, typename NFT>
 __device__ __noinline__ FaceContrib<float, DIM, QF1, QG1> face_pair_diff_call(const StepConst &K, const float *fp,
-                                                                             int NFACES, int flo, int fhi,
+                                                                             NFT NFACES, int flo, int fhi,
                                                                              float ux, float uy, float T,
                                                                              float sT) {
   using D = Dims<DIM, QF1, QG1>;
@@ -1455,8 +1464,8 @@ __device__ __noinline__ FaceContrib<float, DIM, QF1, QG1> face_pair_diff_call(co
 // the Appendix C form.
 // (MS, low: the fluxes are projected onto the cell's low-order lattice before
 // the multiplication by v_n, which on that lattice has no order-3 term.)
-template <typename R, int DIM, int QF1, int DIRN, bool MS = false, int QG1 = 3>
-__device__ __forceinline__ void add_faces(const StepConst &K, const R *fp, int NFACES, int flo, int fhi,
+template <typename R, int DIM, int QF1, int DIRN, bool MS = false, int QG1 = 3, typename NFT = int>
+__device__ __forceinline__ void add_faces(const StepConst &K, const R *fp, NFT NFACES, int flo, int fhi,
                                           R ux, R uy, R T, R sT, Blk<R, QF1, Dims<DIM, QF1>::NYF> &F,
                                           Blk<R, QG1, Dims<DIM, QF1, QG1>::NYG> &G, MomAcc &M,
                                           bool low = false) {
@@ -1568,10 +1577,10 @@ __device__ __forceinline__ void update_cell(const StepConst &K, const State<R> &
 #pragma unroll
     for (int b = 0; b < D::NYG; ++b) G.v[a][b] *= a + b == 1 ? aq : a1;
   // fluxes through the faces, in a fixed order: x, then y
-  add_faces<R, DIM, QF1, 0, MS, QG1>(K, fp, TL::NFACES, cy * (BX + 1) + cx, cy * (BX + 1) + cx + 1, ux, uy, T, sT, F,
+  add_faces<R, DIM, QF1, 0, MS, QG1>(K, fp, CInt<TL::NFACES>{}, cy * (BX + 1) + cx, cy * (BX + 1) + cx + 1, ux, uy, T, sT, F,
                                 G, M, low);
   if constexpr (DIM == 2)
-    add_faces<R, DIM, QF1, 1, MS, QG1>(K, fp, TL::NFACES, TL::NFX + cy * BX + cx, TL::NFX + (cy + 1) * BX + cx, ux, uy,
+    add_faces<R, DIM, QF1, 1, MS, QG1>(K, fp, CInt<TL::NFACES>{}, TL::NFX + cy * BX + cx, TL::NFX + (cy + 1) * BX + cx, ux, uy,
                                   T, sT, F, G, M, low);
   F.v[0][0] += kc<R>(K.a2, K.cf.a2) * rho;
   G.v[0][0] += kc<R>(K.a2, K.cf.a2) * kc<R>(K.gfac, K.cf.gfac) * T * rho;
@@ -1721,11 +1730,11 @@ __device__ __forceinline__ void step_tile(const StepConst &K, const State<R> &S,
         bool nc;
         if constexpr (MS) {  // the face's f-lattice: the higher of its two cells'
           if (lat[st[0]] == 0 && lat[st[1]] == 0)
-            nc = face_flux<R, DIM, QF1, 0, ITER, false, 3, QG1>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
+            nc = face_flux<R, DIM, QF1, 0, ITER, false, 3, QG1>(K, sp, CInt<TL::NH>{}, st, fp, TL::NFACES, f, nt);
           else
-            nc = face_flux<R, DIM, QF1, 0, ITER, false, QF1, QG1>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
+            nc = face_flux<R, DIM, QF1, 0, ITER, false, QF1, QG1>(K, sp, CInt<TL::NH>{}, st, fp, TL::NFACES, f, nt);
         } else {
-          nc = face_flux<R, DIM, QF1, 0, ITER, false, QF1, QG1>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
+          nc = face_flux<R, DIM, QF1, 0, ITER, false, QF1, QG1>(K, sp, CInt<TL::NH>{}, st, fp, TL::NFACES, f, nt);
         }
         if (ITER && (fx > 0 || j0 == 0)) {
           noconv += nc; traces += nt; ++evals; max_tr = max(max_tr, (unsigned)nt);
@@ -1741,11 +1750,11 @@ __device__ __forceinline__ void step_tile(const StepConst &K, const State<R> &S,
         bool nc;
         if constexpr (MS) {  // the face's f-lattice: the higher of its two cells'
           if (lat[st[0]] == 0 && lat[st[1]] == 0)
-            nc = face_flux<R, DIM, QF1, 1, ITER, false, 3, QG1>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
+            nc = face_flux<R, DIM, QF1, 1, ITER, false, 3, QG1>(K, sp, CInt<TL::NH>{}, st, fp, TL::NFACES, f, nt);
           else
-            nc = face_flux<R, DIM, QF1, 1, ITER, false, QF1, QG1>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
+            nc = face_flux<R, DIM, QF1, 1, ITER, false, QF1, QG1>(K, sp, CInt<TL::NH>{}, st, fp, TL::NFACES, f, nt);
         } else {
-          nc = face_flux<R, DIM, QF1, 1, ITER, false, QF1, QG1>(K, sp, TL::NH, st, fp, TL::NFACES, f, nt);
+          nc = face_flux<R, DIM, QF1, 1, ITER, false, QF1, QG1>(K, sp, CInt<TL::NH>{}, st, fp, TL::NFACES, f, nt);
         }
         if (ITER && (fy > 0 || k0 == 0)) {
           noconv += nc; traces += nt; ++evals; max_tr = max(max_tr, (unsigned)nt);

@@ -73,8 +73,8 @@ WORKLOAD = "2D periodic advected Gaussian pulse, D2Q16+D2Q9, 256x256, Mach 2 at 
 # thread instructions, packed FP32 pairs twice that, per launch / cells) and
 # dram__bytes_read.sum + dram__bytes_write.sum per launch.
 NCU_BY_DIGEST = {
-    "7e1abe049e2e4e36ac357dd8f324117f9bc156e3477ae36cfa49fa1415c6abe6": {
-        "flops_fp64": 7727.0, "traffic_fp64": 15133440, "flops_fp32": 7780.5, "traffic_fp32": 9558400},
+    "b162daf1d316b21f5a859bbd54c01991e4ab8d1e8ca028196b1cdf7bd77e3d38": {
+        "flops_fp64": 7727.0, "traffic_fp64": 15133056, "flops_fp32": 7780.5, "traffic_fp32": 9553152},
 }
 
 

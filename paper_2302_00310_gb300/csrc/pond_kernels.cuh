@@ -207,11 +207,11 @@ __device__ __forceinline__ bool abs_less(float x, float y) {
 // FP64 the quotient takes the reciprocal after one Newton step (no residual
 // correction of the quotient): the slope enters the trace times an offset
 // below 1, and the step is bound by the FP64 pipe (2 DFMA saved per limit).
-template <typename R> __device__ __forceinline__ R limiter_factor(int lim) {
+template <typename R, typename LT> __device__ __forceinline__ R limiter_factor(LT lim) {
   return lim == LIM_MINMOD ? R(1) : R(2);
 }
-template <typename R>
-__device__ __forceinline__ R limit(R x, R y, int lim) {
+template <typename R, typename LT>
+__device__ __forceinline__ R limit(R x, R y, LT lim) {
   const R p = x * y;
   if (lim == LIM_MINMOD) return pos(p) ? (abs_less(x, y) ? x : y) : R(0);
   if constexpr (std::is_same<R, double>::value) return pos(p) ? p * rcp_nr1(x + y) : R(0);
@@ -222,7 +222,8 @@ __device__ __forceinline__ R limit(R x, R y, int lim) {
 // differences, product, sum and quotient in the paired FP32 instructions, the
 // reciprocal and the sign tests per lane; the same values as limit() on each
 // lane to FP32 rounding.
-__device__ __forceinline__ f2 limit2(f2 x, f2 y, int lim) {
+template <typename LT>
+__device__ __forceinline__ f2 limit2(f2 x, f2 y, LT lim) {
   const f2 p = x * y;
   if (lim == LIM_MINMOD)
     return f2(pos(p.lo()) ? (abs_less(x.lo(), y.lo()) ? x.lo() : y.lo()) : 0.f,
@@ -884,11 +885,11 @@ __device__ __noinline__ void reconstruct_tie(const StepConst &K, const R *sp, in
 // the face (YL, YR) and the outer cell of the upwind side (Bo): A = the upwind
 // value, out = A + offn L(A - Bo, downwind - A); two tangential nodes per paired
 // instruction on the mixed path.
-template <typename R, int DIM, int DIRN, int Q>
+template <typename R, int DIM, int DIRN, int Q, typename LT>
 __device__ __forceinline__ void trace_normal(const Blk<R, Q, (DIM == 2 ? Q : 1)> &YL,
                                              const Blk<R, Q, (DIM == 2 ? Q : 1)> &YR,
                                              const Blk<R, Q, (DIM == 2 ? Q : 1)> &Bo, unsigned upm,
-                                             const R *offn, int lim, Blk<R, Q, (DIM == 2 ? Q : 1)> &A,
+                                             const R *offn, LT lim, Blk<R, Q, (DIM == 2 ? Q : 1)> &A,
                                              Blk<R, Q, (DIM == 2 ? Q : 1)> &out) {
   constexpr int NY = DIM == 2 ? Q : 1;
   if constexpr (is_mixed<R>() && DIM == 2) {
@@ -980,10 +981,10 @@ __device__ __noinline__ Row<R, (DIM == 2 ? Q : 1)> zero_node_left(
 // run reconstruct_tie out of line).  The zero node at v_n = 0 (u_F,n = 0
 // exactly) takes the mean of its two one-sided traces here: the right/upper
 // one in line, the left/lower one from zero_node_left.
-template <typename R, int DIM, int QF1, int DIRN, int Q, int TIE, int GS, int QG1, typename NHT>
+template <typename R, int DIM, int QF1, int DIRN, int Q, int TIE, int GS, int QG1, typename NHT, typename LT>
 __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, NHT NH, const int *st,
                                             R uFx, R uFy, R TF, R sTF, R isTF,
-                                            Blk<R, Q, (DIM == 2 ? Q : 1)> &out) {
+                                            Blk<R, Q, (DIM == 2 ? Q : 1)> &out, LT lim) {
   if constexpr (TIE == 2) {
     reconstruct_tie<R, DIM, QF1, DIRN, Q, GS, QG1>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, out);
     return;
@@ -991,9 +992,9 @@ __device__ __forceinline__ void reconstruct(const StepConst &K, const R *sp, NHT
   constexpr int NY = DIM == 2 ? Q : 1;
   const SynK<R, Q> SK(isTF * isTF, isTF);
   const R uFn = DIRN == 0 ? uFx : uFy, uFt = DIRN == 0 ? uFy : uFx;
-  const R lf = limiter_factor<R>(K.limiter);
+  // lim: K.limiter, or the same value as a compile-time type (CInt)
+  const R lf = limiter_factor<R>(lim);
   const R hl = R(0.5) * kc<R>(K.lam, K.cf.lam) * lf, h0 = R(0.5) * lf;
-  const int lim = K.limiter;
   bool up[Q], tie = false;
   unsigned upm = 0u;
   R offn[Q], offt[Q];
@@ -1123,9 +1124,9 @@ __device__ __forceinline__ R gauss_he4(R mu, R dT) {
 // are both on the low-order lattice) 3; the face record keeps the storage
 // layout of QF1, with zero coefficients beyond QL.
 template <typename R, int DIM, int QF1, int DIRN, bool ITER, bool TIE = false, int QL = QF1, int QG1 = 3,
-          typename NHT = int>
+          typename NHT = int, typename LT = int>
 __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, NHT NH, const int *st,
-                                          R *fp, int NFACES, int fidx, int &ntrace);
+                                          R *fp, int NFACES, int fidx, int &ntrace, LT lim);
 
 // does a node of either lattice other than an odd lattice's zero node have
 // v_n = 0 exactly in the face frame (u_F,n = -c_k sqrt(T_F) to the last bit:
@@ -1147,12 +1148,12 @@ __device__ __forceinline__ bool face_has_tie(R uFn, R sTF) {
 template <typename R, int DIM, int QF1, int DIRN, int QL, int QG1>
 __device__ __noinline__ bool face_flux_tie(const StepConst &K, const R *sp, int NH, const int *st, R *fp,
                                            int NFACES, int fidx, int &ntrace) {
-  return face_flux<R, DIM, QF1, DIRN, false, true, QL, QG1>(K, sp, NH, st, fp, NFACES, fidx, ntrace);
+  return face_flux<R, DIM, QF1, DIRN, false, true, QL, QG1>(K, sp, NH, st, fp, NFACES, fidx, ntrace, K.limiter);
 }
 
-template <typename R, int DIM, int QF1, int DIRN, bool ITER, bool TIE, int QL, int QG1, typename NHT>
+template <typename R, int DIM, int QF1, int DIRN, bool ITER, bool TIE, int QL, int QG1, typename NHT, typename LT>
 __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, NHT NH, const int *st,
-                                          R *fp, int NFACES, int fidx, int &ntrace) {
+                                          R *fp, int NFACES, int fidx, int &ntrace, LT lim) {
   static_assert(QL >= QG1, "the equilibrium's Gaussian moments are built to the f-lattice's order");
   using D = Dims<DIM, QF1, QG1>;
   constexpr int NYF = DIM == 2 ? QL : 1, NYG = D::NYG;
@@ -1177,8 +1178,8 @@ __device__ __forceinline__ bool face_flux(const StepConst &K, const R *sp, NHT N
   ntrace = 0;
   while (true) {
     ++ntrace;
-    reconstruct<R, DIM, QF1, DIRN, QL, TMODE, 0, QG1>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, Fb);
-    reconstruct<R, DIM, QF1, DIRN, QG1, TMODE, 1, QG1>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, Gb);
+    reconstruct<R, DIM, QF1, DIRN, QL, TMODE, 0, QG1>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, Fb, lim);
+    reconstruct<R, DIM, QF1, DIRN, QG1, TMODE, 1, QG1>(K, sp, NH, st, uFx, uFy, TF, sTF, isTF, Gb, lim);
     anaq_xy(AnaK<R, QL>(TF, sTF), Fb);
     anaq_xy(AnaK<R, QG1>(TF, sTF), Gb);
     // interface moments in the face frame (all carry the factor kappa1): rho,
@@ -1677,6 +1678,67 @@ __device__ __forceinline__ void hand_over_x_edge(unsigned char *smem) {
   }
 }
 
+// Phase B of a tile: every face item of the tile (see step_tile).  lim: the
+// limiter, K.limiter or (the mixed path) the same value as a compile-time
+// type, so that each limited slope compiles to one limiter's code.
+template <typename R, int DIM, int QF1, int BX, int BY, int NT, bool ITER, bool MS, int QG1, typename LT>
+__device__ __forceinline__ void faces_of_tile(const StepConst &K, const R *sp, R *fp, const unsigned char *lat,
+                                              int j0, int k0, bool carry, LT lim, unsigned &noconv,
+                                              unsigned &traces, unsigned &evals, unsigned &max_tr) {
+  using TL = Tile<DIM, BX, BY, QF1, QG1>;
+  const int tid = threadIdx.x;
+  constexpr int ROWS = DIM == 2 ? BY : 1;
+  const int xw = carry ? BX : BX + 1, x0 = carry ? 1 : 0;
+  const int nxi = xw * ROWS, px = (nxi + 31) / 32 * 32;
+  for (int w = tid; w < px + TL::NFY; w += NT) {
+    int st[8];
+    if (w < px) {
+      if (w >= nxi) continue;
+      const int fx = x0 + w % xw, fy = w / xw, f = fy * (BX + 1) + fx;
+      if (j0 + fx - 1 >= K.nx || k0 + fy >= (DIM == 2 ? K.ny : 1)) continue;
+      const int r = (fy + TL::OY) * TL::HX;
+      st[0] = r + fx + 1; st[1] = r + fx + 2; st[2] = r + fx; st[3] = r + fx + 3;
+      if constexpr (DIM == 2) {
+        st[4] = r - TL::HX + fx + 1; st[5] = r - TL::HX + fx + 2;
+        st[6] = r + TL::HX + fx + 1; st[7] = r + TL::HX + fx + 2;
+      }
+      int nt;
+      bool nc;
+      if constexpr (MS) {  // the face's f-lattice: the higher of its two cells'
+        if (lat[st[0]] == 0 && lat[st[1]] == 0)
+          nc = face_flux<R, DIM, QF1, 0, ITER, false, 3, QG1>(K, sp, CInt<TL::NH>{}, st, fp, TL::NFACES, f, nt, lim);
+        else
+          nc = face_flux<R, DIM, QF1, 0, ITER, false, QF1, QG1>(K, sp, CInt<TL::NH>{}, st, fp, TL::NFACES, f, nt, lim);
+      } else {
+        nc = face_flux<R, DIM, QF1, 0, ITER, false, QF1, QG1>(K, sp, CInt<TL::NH>{}, st, fp, TL::NFACES, f, nt, lim);
+      }
+      if (ITER && (fx > 0 || j0 == 0)) {
+        noconv += nc; traces += nt; ++evals; max_tr = max(max_tr, (unsigned)nt);
+      }
+    } else if constexpr (DIM == 2) {
+      const int g = w - px, fx = g % BX, fy = g / BX, f = TL::NFX + g;
+      if (j0 + fx >= K.nx || k0 + fy - 1 >= K.ny) continue;
+      const int x = fx + 2, H = TL::HX;
+      st[0] = (fy + 1) * H + x; st[1] = (fy + 2) * H + x; st[2] = fy * H + x; st[3] = (fy + 3) * H + x;
+      st[4] = (fy + 1) * H + x - 1; st[5] = (fy + 2) * H + x - 1;
+      st[6] = (fy + 1) * H + x + 1; st[7] = (fy + 2) * H + x + 1;
+      int nt;
+      bool nc;
+      if constexpr (MS) {  // the face's f-lattice: the higher of its two cells'
+        if (lat[st[0]] == 0 && lat[st[1]] == 0)
+          nc = face_flux<R, DIM, QF1, 1, ITER, false, 3, QG1>(K, sp, CInt<TL::NH>{}, st, fp, TL::NFACES, f, nt, lim);
+        else
+          nc = face_flux<R, DIM, QF1, 1, ITER, false, QF1, QG1>(K, sp, CInt<TL::NH>{}, st, fp, TL::NFACES, f, nt, lim);
+      } else {
+        nc = face_flux<R, DIM, QF1, 1, ITER, false, QF1, QG1>(K, sp, CInt<TL::NH>{}, st, fp, TL::NFACES, f, nt, lim);
+      }
+      if (ITER && (fy > 0 || k0 == 0)) {
+        noconv += nc; traces += nt; ++evals; max_tr = max(max_tr, (unsigned)nt);
+      }
+    }
+  }
+}
+
 // ---- one tile step (phases A-C) --------------------------------------------------
 // The BX x BY tile whose first cell is (j0, k0); smem holds the halo and face
 // records.  Every output depends only on its own stencil's arithmetic: for a
@@ -1710,57 +1772,20 @@ __device__ __forceinline__ void step_tile(const StepConst &K, const State<R> &S,
   // row, BX when the left edge was handed over), padded to whole warps so that
   // no warp runs both the x-face and the y-face code, then the y-faces.
   unsigned noconv = 0, traces = 0, evals = 0, max_tr = 0;
-  {
-    constexpr int ROWS = DIM == 2 ? BY : 1;
-    const int xw = carry ? BX : BX + 1, x0 = carry ? 1 : 0;
-    const int nxi = xw * ROWS, px = (nxi + 31) / 32 * 32;
-    for (int w = tid; w < px + TL::NFY; w += NT) {
-      int st[8];
-      if (w < px) {
-        if (w >= nxi) continue;
-        const int fx = x0 + w % xw, fy = w / xw, f = fy * (BX + 1) + fx;
-        if (j0 + fx - 1 >= K.nx || k0 + fy >= (DIM == 2 ? K.ny : 1)) continue;
-        const int r = (fy + TL::OY) * TL::HX;
-        st[0] = r + fx + 1; st[1] = r + fx + 2; st[2] = r + fx; st[3] = r + fx + 3;
-        if constexpr (DIM == 2) {
-          st[4] = r - TL::HX + fx + 1; st[5] = r - TL::HX + fx + 2;
-          st[6] = r + TL::HX + fx + 1; st[7] = r + TL::HX + fx + 2;
-        }
-        int nt;
-        bool nc;
-        if constexpr (MS) {  // the face's f-lattice: the higher of its two cells'
-          if (lat[st[0]] == 0 && lat[st[1]] == 0)
-            nc = face_flux<R, DIM, QF1, 0, ITER, false, 3, QG1>(K, sp, CInt<TL::NH>{}, st, fp, TL::NFACES, f, nt);
-          else
-            nc = face_flux<R, DIM, QF1, 0, ITER, false, QF1, QG1>(K, sp, CInt<TL::NH>{}, st, fp, TL::NFACES, f, nt);
-        } else {
-          nc = face_flux<R, DIM, QF1, 0, ITER, false, QF1, QG1>(K, sp, CInt<TL::NH>{}, st, fp, TL::NFACES, f, nt);
-        }
-        if (ITER && (fx > 0 || j0 == 0)) {
-          noconv += nc; traces += nt; ++evals; max_tr = max(max_tr, (unsigned)nt);
-        }
-      } else if constexpr (DIM == 2) {
-        const int g = w - px, fx = g % BX, fy = g / BX, f = TL::NFX + g;
-        if (j0 + fx >= K.nx || k0 + fy - 1 >= K.ny) continue;
-        const int x = fx + 2, H = TL::HX;
-        st[0] = (fy + 1) * H + x; st[1] = (fy + 2) * H + x; st[2] = fy * H + x; st[3] = (fy + 3) * H + x;
-        st[4] = (fy + 1) * H + x - 1; st[5] = (fy + 2) * H + x - 1;
-        st[6] = (fy + 1) * H + x + 1; st[7] = (fy + 2) * H + x + 1;
-        int nt;
-        bool nc;
-        if constexpr (MS) {  // the face's f-lattice: the higher of its two cells'
-          if (lat[st[0]] == 0 && lat[st[1]] == 0)
-            nc = face_flux<R, DIM, QF1, 1, ITER, false, 3, QG1>(K, sp, CInt<TL::NH>{}, st, fp, TL::NFACES, f, nt);
-          else
-            nc = face_flux<R, DIM, QF1, 1, ITER, false, QF1, QG1>(K, sp, CInt<TL::NH>{}, st, fp, TL::NFACES, f, nt);
-        } else {
-          nc = face_flux<R, DIM, QF1, 1, ITER, false, QF1, QG1>(K, sp, CInt<TL::NH>{}, st, fp, TL::NFACES, f, nt);
-        }
-        if (ITER && (fy > 0 || k0 == 0)) {
-          noconv += nc; traces += nt; ++evals; max_tr = max(max_tr, (unsigned)nt);
-        }
-      }
-    }
+  // The mixed path, bound by latency rather than arithmetic, runs the faces
+  // with the limiter fixed at compile time (one uniform branch per tile
+  // instead of one per limited slope); the FP64 path, bound by its FP64
+  // pipe, and the iterated frame keep one copy of the face code.
+  if constexpr (is_mixed<R>() && !ITER) {
+    if (K.limiter == LIM_MINMOD)
+      faces_of_tile<R, DIM, QF1, BX, BY, NT, ITER, MS, QG1>(K, sp, fp, lat, j0, k0, carry, CInt<LIM_MINMOD>{},
+                                                            noconv, traces, evals, max_tr);
+    else
+      faces_of_tile<R, DIM, QF1, BX, BY, NT, ITER, MS, QG1>(K, sp, fp, lat, j0, k0, carry, CInt<LIM_VANLEER>{},
+                                                            noconv, traces, evals, max_tr);
+  } else {
+    faces_of_tile<R, DIM, QF1, BX, BY, NT, ITER, MS, QG1>(K, sp, fp, lat, j0, k0, carry, K.limiter, noconv,
+                                                          traces, evals, max_tr);
   }
   __syncthreads();
 

@@ -73,8 +73,8 @@ WORKLOAD = "2D periodic advected Gaussian pulse, D2Q16+D2Q9, 256x256, Mach 2 at 
 # thread instructions, packed FP32 pairs twice that, per launch / cells) and
 # dram__bytes_read.sum + dram__bytes_write.sum per launch.
 NCU_BY_DIGEST = {
-    "b162daf1d316b21f5a859bbd54c01991e4ab8d1e8ca028196b1cdf7bd77e3d38": {
-        "flops_fp64": 7727.0, "traffic_fp64": 15133056, "flops_fp32": 7780.5, "traffic_fp32": 9553152},
+    "bc59f6a4320094aead0e8dc0647001660519f2da74ea57f1c774220d5e5e340b": {
+        "flops_fp64": 7727.0, "traffic_fp64": 15131136, "flops_fp32": 7780.5, "traffic_fp32": 9573376},
 }
 
 

@@ -133,12 +133,16 @@ typedef struct {
                               when the shift |(u_s-u_F)/sqrt(T_F)| or the scale
                               sqrt(T_s/T_F) exceeds this                          */
   int32_t tile;            /* cells per CTA of the step kernel: 0 automatic
-                              (1D: 1; 2D: 10); 1D: 1 = 252
+                              (1D: 1; 2D: 10, or on the mixed path 11
+                              for grids of at least four waves of three
+                              CTAs per SM); 1D: 1 = 252
                               cells; 2D (x by y): 2 = 8x8, 3 = 16x16, 4 = 16x8,
                               5 = 8x8 and 6 = 8x16 with registers capped for two
                               CTAs per SM, 7 = 8x16 and 8 = 8x8 capped for three
                               CTAs per SM, 9 = 8x16 with 192 threads, 10 = 8x14
-                              with 128 threads and two CTAs per SM.  The
+                              with 128 threads and two CTAs per SM, 11 (mixed
+                              path only) = 8x14 with 128 threads capped for
+                              three CTAs per SM.  The
                               iterated face frame runs 8x8 (2D) / 252 (1D).
                               Each output depends only on its stencil, so all
                               tiles compute the same step; as separate machine
@@ -311,7 +315,7 @@ int pond_abi_version(void);
 typedef struct pond_batch pond_batch;
 typedef struct {
   int32_t tile;         /* 0: the autotuner picks; else a candidate 2D tile code
-                           (mixed: 10, 6, 3; FP64: 10, 9, 6; 1D batches have the
+                           (mixed: 10, 11, 6; FP64: 10, 9, 6; 1D batches have the
                            one 252-cell tile)                                 */
   int32_t graph_steps;  /* launches per chunk and per captured graph (1-1024) */
   int32_t autotune;     /* 1: time the candidate shapes on the first long call */

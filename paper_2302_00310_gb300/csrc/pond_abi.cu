@@ -226,9 +226,23 @@ pond_status step_once(pond_ctx *c) {
 // Fastest in tile sweeps on GB300 (256^2 pulse and 1024^2 Riemann grids):
 // 8x14 tiles with 128 threads and two CTAs per SM in both precisions (FP64:
 // shared memory and the register file each hold exactly two; mixed: 1,421
-// and 1,518 MLUPS against 1,247 and 1,476 for 8x16 tiles with 160 threads)
-// (D2Q25: 8x8 tiles with 128 threads, two CTAs per SM)
-int auto_tile(const pond_ctx *c) { return c->D == 1 ? 1 : 10; }
+// and 1,518 MLUPS against 1,247 and 1,476 for 8x16 tiles with 160 threads).
+// On the mixed path a grid of at least four waves of three CTAs per SM takes
+// the same tile with registers capped for three CTAs (code 11: 1,987 against
+// 1,750 MLUPS on the 1024^2 Riemann problem; on the 256^2 pulse, 1.3 waves,
+// 1,451 against 1,563).  (D2Q25: 8x8 tiles with 128 threads, two CTAs per SM.)
+int auto_tile(const pond_ctx *c) {
+  if (c->D == 1) return 1;
+  if (!c->fp32 || c->qf1 == 5) return 10;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 10;
+  }
+  const long long tiles = (long long)((c->nx + 7) / 8) * (long long)((c->ny + 13) / 14);
+  return tiles >= 4LL * 3 * sms ? 11 : 10;
+}
 
 bool valid_params(const pond_params *p) {
   if (!p) return false;
@@ -245,7 +259,8 @@ bool valid_params(const pond_params *p) {
   if (p->flux_frame != POND_FRAME_AVG && p->flux_frame != POND_FRAME_ITER) return false;
   if (p->flux_frame == POND_FRAME_ITER && (!(p->iter_tol > 0.0) || p->iter_max < 1)) return false;
   if (!(p->xi_fp64_threshold > 0.0)) return false;
-  if (p->tile < 0 || p->tile > 10) return false;
+  if (p->tile < 0 || p->tile > 11) return false;
+  if (p->tile == 11 && p->precision != POND_FP32_MIXED) return false;  // a mixed-path shape
   if (p->strip < 0 || p->strip > 8) return false;
   if (p->multiscale != 0 && p->multiscale != 1) return false;
   if (p->g_same_as_f != 0 && p->g_same_as_f != 1) return false;

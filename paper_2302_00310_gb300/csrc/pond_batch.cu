@@ -43,7 +43,7 @@ namespace {
 std::vector<Shape> batch_shapes(bool fp32, int D) {
   const std::vector<Shape> all = fp32 ? pond_shapes_fp32(D) : pond_shapes_fp64(D);
   if (D == 1) return all;
-  static const int kMixed[3] = {10, 6, 3}, kFp64[3] = {10, 9, 6};
+  static const int kMixed[3] = {10, 11, 6}, kFp64[3] = {10, 9, 6};
   const int *codes = fp32 ? kMixed : kFp64;
   std::vector<Shape> out;
   for (int i = 0; i < 3; ++i)

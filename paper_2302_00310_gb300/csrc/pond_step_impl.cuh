@@ -92,14 +92,18 @@ Shape make_shape(int code) {
 // and 8 = 8x8 with registers capped for three CTAs per SM, 9 = 8x16 with 192
 // threads (no cap: one FP64 CTA per SM is all shared memory holds), 10 = 8x14
 // with 128 threads and two CTAs per SM (an FP64 tile's shared memory fits
-// twice, and 2 x 128 threads x 255 registers fit the register file)
+// twice, and 2 x 128 threads x 255 registers fit the register file), 11 (the
+// mixed path only) = 8x14 with 128 threads and registers capped for three
+// CTAs per SM
 template <typename R> std::vector<Shape> all_shapes(int D) {
   if (D == 1) return {make_shape<R, 1, 252, 1, 256, 1, false>(1)};
-  return {make_shape<R, 2, 8, 8, 160, 1, false>(2), make_shape<R, 2, 16, 16, 256, 1, false>(3),
-          make_shape<R, 2, 16, 8, 256, 1, false>(4), make_shape<R, 2, 8, 8, 160, 2, false>(5),
-          make_shape<R, 2, 8, 16, 160, 2, false>(6), make_shape<R, 2, 8, 16, 160, 3, false>(7),
-          make_shape<R, 2, 8, 8, 160, 3, false>(8), make_shape<R, 2, 8, 16, 192, 1, false>(9),
-          make_shape<R, 2, 8, 14, 128, 2, false>(10)};
+  std::vector<Shape> s = {make_shape<R, 2, 8, 8, 160, 1, false>(2), make_shape<R, 2, 16, 16, 256, 1, false>(3),
+                          make_shape<R, 2, 16, 8, 256, 1, false>(4), make_shape<R, 2, 8, 8, 160, 2, false>(5),
+                          make_shape<R, 2, 8, 16, 160, 2, false>(6), make_shape<R, 2, 8, 16, 160, 3, false>(7),
+                          make_shape<R, 2, 8, 8, 160, 3, false>(8), make_shape<R, 2, 8, 16, 192, 1, false>(9),
+                          make_shape<R, 2, 8, 14, 128, 2, false>(10)};
+  if constexpr (std::is_same<R, float>::value) s.push_back(make_shape<R, 2, 8, 14, 128, 3, false>(11));
+  return s;
 }
 
 // the iterated face frame runs with one tile shape of its own: its trace loop

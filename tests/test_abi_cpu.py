@@ -86,6 +86,9 @@ def _params(**kw):
     (pond.POND_D2Q16, dict(g_same_as_f=1, multiscale=1)),
     (pond.POND_D2Q16, dict(g_same_as_f=1, flux_frame=pond.POND_FRAME_ITER)),
     (pond.POND_D2Q16, dict(g_same_as_f=1, tile=9)),
+    # tile 11 (8x14 capped for three CTAs per SM) is a mixed-path shape
+    (pond.POND_D2Q16, dict(tile=11)),
+    (pond.POND_D2Q16, dict(tile=12, precision=pond.POND_FP32_MIXED)),
     (pond.POND_D2Q16, dict(g_same_as_f=1, precision=pond.POND_FP32_MIXED, tile=6)),
     (pond.POND_D1Q4, dict(g_same_as_f=2)),
 ])
@@ -113,7 +116,8 @@ def test_batch_tile_codes_are_resolved_before_any_device_work(L):
     no_gpu = not torch.cuda.is_available()
     for prec, tile, ok in ((pond.POND_FP64, 9, True), (pond.POND_FP64, 10, True),
                            (pond.POND_FP64, 4, False), (pond.POND_FP32_MIXED, 10, True),
-                           (pond.POND_FP32_MIXED, 6, True), (pond.POND_FP32_MIXED, 3, True),
+                           (pond.POND_FP32_MIXED, 11, True), (pond.POND_FP64, 11, False),
+                           (pond.POND_FP32_MIXED, 6, True), (pond.POND_FP32_MIXED, 3, False),
                            (pond.POND_FP32_MIXED, 4, False), (pond.POND_FP32_MIXED, 9, False),
                            (pond.POND_FP64, 0, True), (pond.POND_FP32_MIXED, 0, True)):
         t = pond.pond_tune_default()

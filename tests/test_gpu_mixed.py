@@ -108,7 +108,7 @@ def test_mixed_tile_shapes_agree():
     cfg = W._base(2, 45, 39, tau=5e-3, dx=1.0 / 45, prandtl=0.71, bc=(0, 0, 1, 1))
     cfg["dt"] = W.dt_from_cfl(prim[1], prim[2], prim[3], cfg["dx"], 0.4)
     ref = None
-    for tile in (2, 3, 4, 5, 6, 7, 8, 9):
+    for tile in (2, 3, 4, 5, 6, 7, 8, 9, 10, 11):
         sim = pond.Sim(dict(cfg, precision=pond.POND_FP32_MIXED, tile=tile))
         sim.init(*prim)
         sim.step(3)

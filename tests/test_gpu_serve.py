@@ -18,7 +18,7 @@ def torch():
 
 
 def _solo_tile(precision):
-    return 10  # pond_params.tile default in 2D
+    return 10  # pond_params.tile default in 2D for grids of these sizes
 
 
 @pytest.mark.parametrize("precision,autotune", [(pond.POND_FP32_MIXED, False), (pond.POND_FP64, False),

@@ -73,8 +73,8 @@ WORKLOAD = "2D periodic advected Gaussian pulse, D2Q16+D2Q9, 256x256, Mach 2 at 
 # thread instructions, packed FP32 pairs twice that, per launch / cells) and
 # dram__bytes_read.sum + dram__bytes_write.sum per launch.
 NCU_BY_DIGEST = {
-    "bc59f6a4320094aead0e8dc0647001660519f2da74ea57f1c774220d5e5e340b": {
-        "flops_fp64": 7727.0, "traffic_fp64": 15131136, "flops_fp32": 7780.5, "traffic_fp32": 9573376},
+    "f1e612ccf8a9dc80f4cbd68501088a8ce05ddb6576c3fc724f94647b9c8a59e0": {
+        "flops_fp64": 7726.9, "traffic_fp64": 15132288, "flops_fp32": 7780.5, "traffic_fp32": 9575680},
 }
 
 

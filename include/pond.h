@@ -176,8 +176,7 @@ typedef struct {
    * order only (Sec. III.C) and every run of the paper uses D2Q9.  g[Qg] then
    * holds 4 (1D) or 16 (2D) populations in the f-lattice's node order.
    * Requires D1Q4 / D2Q16, the averaged face frame, no multiscale and tile 0
-   * (or the precision's default: 1 in 1D; 10 FP64, 6 mixed in 2D); not
-   * batched. */
+   * (or the default: 1 in 1D, 10 in 2D); not batched. */
   int32_t g_same_as_f;
   /* tiles per strip of the step launch: 0 automatic, else 1-8.  A CTA steps a
    * strip of consecutive tiles of one tile row left to right, handing each

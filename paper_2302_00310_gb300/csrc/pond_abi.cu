@@ -231,9 +231,10 @@ pond_status step_once(pond_ctx *c) {
 // the same tile with registers capped for three CTAs (code 11: 1,987 against
 // 1,750 MLUPS on the 1024^2 Riemann problem; on the 256^2 pulse, 1.3 waves,
 // 1,451 against 1,563).  (D2Q25: 8x8 tiles with 128 threads, two CTAs per SM.)
+// The multiscale and g-on-f kernels have the one shape code 10.
 int auto_tile(const pond_ctx *c) {
   if (c->D == 1) return 1;
-  if (!c->fp32 || c->qf1 == 5) return 10;
+  if (!c->fp32 || c->qf1 == 5 || c->p.multiscale || c->qg1 == 4) return 10;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {

@@ -226,3 +226,27 @@ def test_multiscale_context_is_not_batched():
         b.add(sim)
     b.close()
     sim.close()
+
+
+def test_reported_tile_is_the_shape_that_runs():
+    """pond_info's tile code names the kernel shape a context steps with.  On
+    a 512^2 grid (2,368 tiles of 8x14, at least four waves of three CTAs per
+    SM on a 152-SM GPU) a plain mixed context takes the capped tile 11, the
+    FP64 one tile 10, and the multiscale and g-on-f contexts, whose kernels
+    have the one 8x14 two-CTA shape, report that shape's code 10."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    n = 512
+    tiles = (n // 8) * ((n + 13) // 14)
+    cfg = W._base(2, n, n, tau=1e-3, dt=1e-4, bc=(0, 0, 0, 0))
+    mixed = dict(cfg, precision=pond.POND_FP32_MIXED)
+    expect = [(dict(cfg), 10), (mixed, 11 if tiles >= 12 * sms else 10),
+              (dict(mixed, ms=1, ms_theta_u=0.05, ms_theta_T=0.05), 10), (dict(mixed, qg=4), 10),
+              (dict(cfg, ms=1, ms_theta_u=0.05, ms_theta_T=0.05), 10)]
+    for c, code in expect:
+        sim = pond.Sim(c)
+        try:
+            assert sim.info()[2] == code, c
+        finally:
+            sim.close()

@@ -74,7 +74,9 @@ WORKLOAD = "2D periodic advected Gaussian pulse, D2Q16+D2Q9, 256x256, Mach 2 at 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch.
 NCU_BY_DIGEST = {
     "f1e612ccf8a9dc80f4cbd68501088a8ce05ddb6576c3fc724f94647b9c8a59e0": {
-        "flops_fp64": 7726.9, "traffic_fp64": 15132288, "flops_fp32": 7780.5, "traffic_fp32": 9575680},
+        "flops_fp64": 7726.9, "traffic_fp64": 15132288, "flops_fp32": 7780.5, "traffic_fp32": 9575680,
+        # the capped mixed tile (code 11) on the 1024^2 Riemann problem, 6th step
+        "flops_fp32_riemann": 7599.1, "traffic_fp32_riemann": 280381184},
 }
 
 
@@ -136,6 +138,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * CLOCK_MAX_GHZ / 1e3   # 128 FP32 FMA/clk/SM
 # the step kernels the main line launches, as the profiler names them
 KERNEL_FP64 = "member_step_kernel<double, 2, 4, 8, 14, 128, 2, 0, 0, 3>"
 KERNEL_FP32 = "member_step_kernel<float, 2, 4, 8, 14, 128, 2, 0, 0, 3>"
+# the mixed path's kernel on grids of at least four waves of three CTAs per SM
+KERNEL_FP32_CAPPED = "member_step_kernel<float, 2, 4, 8, 14, 128, 3, 0, 0, 3>"
 
 
 def _build_digest():
@@ -306,23 +310,26 @@ def _linf(a, b):
     return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
 
 
-def _roofline(key, cells, per_launch_s, peak, bytes_per_cell, kernel, digest):
+def _roofline(key, cells, per_launch_s, peak, bytes_per_cell, kernel, digest, ncu_key=None,
+              flops_note=""):
     """ALU roofline of one step launch: the formulation's flops of an owned
     cell update (formulation_flops) times the cells of a launch over the
     launch's CUDA-event time, against `peak` (TFLOP/s and how it was
     obtained); the kernel's executed flops (ncu, with the edge faces two tiles
     share and every helper instruction) and the DRAM traffic beside them, and
-    the HBM fraction of the algorithmic bytes."""
+    the HBM fraction of the algorithmic bytes.  `ncu_key` names the counters
+    of another workload than the main line's (default: `key`)."""
     fpc = formulation_flops(mixed=(key == "fp32"))
     hbm_peak = _measured_peaks().get("hbm_gbs", 6652.0)
     ncu = NCU_BY_DIGEST.get(digest, {})
+    nk = ncu_key or key
     out = {"bound": "alu", "unit": "TFLOP/s", "peak": peak["tflops"],
            "peak_source": peak["source"], "kernel": kernel,
            "flops_per_cell": fpc, "flops_source": "formulation count per owned cell update "
-                                                  "(bench.formulation_flops)",
-           "executed_flops_per_cell": ncu.get("flops_" + key),
+                                                  "(bench.formulation_flops)" + flops_note,
+           "executed_flops_per_cell": ncu.get("flops_" + nk),
            "achieved": fpc * cells / per_launch_s / 1e12, "frac": None,
-           "traffic": ncu.get("traffic_" + key),
+           "traffic": ncu.get("traffic_" + nk),
            "hbm": {"achieved_gbs": bytes_per_cell * cells / per_launch_s / 1e9, "peak_gbs": hbm_peak,
                    "bytes_per_cell": bytes_per_cell}}
     out["frac"] = out["achieved"] / peak["tflops"]
@@ -386,9 +393,11 @@ def bench_mixed(torch, pond, W, flush, peaks):
     }
 
 
-def bench_riemann(torch, pond, W, steps=200):
+def bench_riemann(torch, pond, W, steps=200, peaks=None):
     """The four-quadrant Riemann problem at 1024^2 (seeded states, QE Pr 0.71,
-    minmod), mixed path and plain FP64: MLUPS and the L1 error after `steps`."""
+    minmod), mixed path and plain FP64: MLUPS and the L1 error after `steps`;
+    with `peaks`, the mixed kernel's roofline (its capped three-CTA tile on
+    this grid)."""
     w = W.riemann4_2d(n=1024, seed=1)
     fields = (w["rho"], w["ux"], w["uy"], w["T"])
     n = w["cfg"]["nx"] * w["cfg"]["ny"]
@@ -408,8 +417,15 @@ def bench_riemann(torch, pond, W, steps=200):
         ms = e0.elapsed_time(e1)
         mom[name] = sim.moments()
         fl = sim.flags()[1]
+        tile = sim.info()[2]
         out[name] = {"value": n * steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / steps,
-                     "tile": sim.info()[2], "nonphysical": bool(fl & 1)}
+                     "tile": tile, "nonphysical": bool(fl & 1)}
+        if peaks is not None and prec == pond.POND_FP32_MIXED:
+            out[name]["roofline"] = _roofline(
+                "fp32", n, ms * 1e-3 / steps, _peak(peaks, "fp32"), BYTES_PER_CELL_FP32,
+                KERNEL_FP32_CAPPED if tile == 11 else KERNEL_FP32, _build_digest(),
+                ncu_key="fp32_riemann" if tile == 11 else "fp32_none",
+                flops_note="; the main line's count (van Leer, BGK): this problem runs minmod and QE")
         sim.close()
     out["l1_rho_fp32_vs_fp64"] = _l1(mom["fp32_mixed"][0], mom["fp64"][0])
     out["linf_rho_fp32_vs_fp64"] = _linf(mom["fp32_mixed"][0], mom["fp64"][0])
@@ -802,8 +818,11 @@ def run_gpu(args, dist, rank, ws):
             res = {"serve": bench_serve(pond, serve_mod), "serve_offered": bench_serve_offered(pond, serve_mod),
                    "serve_sweep": bench_serve_sweep(pond, serve_mod)}
             print(json.dumps(dict(extra=args.extra, **res)), flush=True)
+        elif rank == 0 and args.extra == "riemann":
+            res = bench_riemann(torch, pond, W, peaks=measure_fma_peaks(pond, local))
+            print(json.dumps(dict(extra=args.extra, **res)), flush=True)
         elif rank == 0:
-            fn = {"riemann": bench_riemann, "d2q25": bench_d2q25, "multiscale": bench_multiscale,
+            fn = {"d2q25": bench_d2q25, "multiscale": bench_multiscale,
                   "g_lattice": bench_g_lattice}[args.extra]
             print(json.dumps(dict(extra=args.extra, **fn(torch, pond, W))), flush=True)
         return
@@ -850,7 +869,7 @@ def run_gpu(args, dist, rank, ws):
     extras = {}
     if not args.no_extras and rank == 0:
         extras["mixed"] = bench_mixed(torch, pond, W, flush, peaks)
-        extras["riemann"] = bench_riemann(torch, pond, W)
+        extras["riemann"] = bench_riemann(torch, pond, W, peaks=peaks)
         extras["batched"] = bench_batched(torch, pond, W)
         extras["d2q25"] = bench_d2q25(torch, pond, W)
         extras["multiscale"] = bench_multiscale(torch, pond, W)

@@ -42,7 +42,8 @@ The other forms the metric compares are measured in the same run
 
 Under torchrun (N > 1) every rank runs an independent replica (the grid is
 not sharded; there is no collective on the data path) and ``value`` is the
-sum of all ranks' cell updates over the slowest rank's time.
+sum of all ranks' cell updates over the slowest rank's time.  The extras are
+single-GPU measurements and run at N = 1 only.
 
 ``--impl reference`` times the FP64 CPU oracle instead (each step: one oracle
 step on a 64 x 64 window of the same workload) on the host cores.
@@ -866,8 +867,10 @@ def run_gpu(args, dist, rank, ws):
     e2e_s = time.perf_counter() - t0
     sim.close()
 
+    # the extras are single-GPU measurements: at N > 1 they would hold every
+    # GPU (the other ranks wait in the reduction below) for minutes
     extras = {}
-    if not args.no_extras and rank == 0:
+    if not args.no_extras and ws == 1:
         extras["mixed"] = bench_mixed(torch, pond, W, flush, peaks)
         extras["riemann"] = bench_riemann(torch, pond, W, peaks=peaks)
         extras["batched"] = bench_batched(torch, pond, W)
